@@ -1,0 +1,214 @@
+/*
+ * enkfmc.h -- C ABI of the GB300 EnKF-MC analysis library (libenkfmc.so).
+ *
+ * EnKF-MC is the stochastic ensemble Kalman filter whose inverse background
+ * covariance is estimated by a localised modified Cholesky decomposition
+ * (Nino, Sandu, Deng 2016).  One analysis step runs in three calls:
+ *
+ *   enkfmc_estimate   regress every component on its predecessors inside the
+ *                     local box of radius r (Section 2.1 Eq. 1-3, Section 2.3
+ *                     Eq. 8): one row of the unit lower triangular T and one
+ *                     entry of the diagonal D per component.
+ *   enkfmc_assemble   per sub-domain extended by an r-wide boundary (Section 3,
+ *                     Algorithm 3): re-estimate the boundary rows from the local
+ *                     samples, assemble A = T^T D^-1 T + H^T R^-1 H (Eq. 11) and
+ *                     factor A = L L^T.
+ *   enkfmc_analyze    form the perturbed observations, solve A dX = H^T R^-1
+ *                     (Y^s - H X^b) for all N members (Eq. 11) and write the
+ *                     interior of every sub-domain into X^a = X^b + dX (Eq. 10,
+ *                     Algorithm 2).
+ *
+ * Conventions shared by every call
+ *   - Floating-point arrays hold `double` when the handle's precision is
+ *     ENKFMC_FP64 and `float` otherwise.  Index arrays are int32/int64 as
+ *     declared.
+ *   - Ensembles are member-major: X[m * n + l] is member m (0 <= m < N) of the
+ *     component with label l.  Labels are variable-major: 3-D variables first
+ *     (nlev levels each), then 2-D variables (one level); within a variable
+ *     l = offset(v) + (level * nlat + lat) * nlon + lon.
+ *   - Unless a parameter says "host", pointers are device pointers owned by
+ *     the caller; the library never frees them and keeps no reference after
+ *     the call returns, except that enkfmc_assemble reads Tvals and D again in
+ *     later enkfmc_analyze calls (they must stay valid and unchanged until the
+ *     next enkfmc_assemble).
+ *   - The handle owns its tables, factors and workspace (device memory
+ *     allocated by enkfmc_create / enkfmc_set_observations, released by
+ *     enkfmc_destroy).
+ *   - Calls are asynchronous on the handle's CUDA stream.  Argument errors are
+ *     returned synchronously.  Numerical failures (a Gram matrix or a
+ *     sub-domain matrix that is not positive definite, a residual variance
+ *     <= 0, a non-finite value) are recorded on the device and reported by
+ *     enkfmc_get_status, which synchronises the stream.  No kernel traps.
+ *   - A handle is not re-entrant: calls on one handle must not overlap.
+ */
+#ifndef ENKFMC_H
+#define ENKFMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ENKFMC_OK = 0,
+  ENKFMC_EINVAL = 1,     /* invalid argument or unsupported geometry            */
+  ENKFMC_ENOMEM = 2,     /* device or host allocation failed                     */
+  ENKFMC_ENOTSPD = 3,    /* a sub-domain matrix A is not positive definite       */
+  ENKFMC_EDNONPOS = 4,   /* a Gram matrix is singular or a variance D_j <= 0     */
+  ENKFMC_ENONFINITE = 5, /* NaN or Inf met                                        */
+  ENKFMC_ETIMEOUT = 6,   /* a bounded device wait ran out                         */
+  ENKFMC_ECUDA = 7,      /* a CUDA runtime call failed                            */
+  ENKFMC_ENOTIMPL = 8,   /* not implemented in this build                         */
+  ENKFMC_ESTATE = 9      /* call out of order (e.g. analyze before assemble)      */
+} enkfmc_status;
+
+typedef enum {
+  ENKFMC_FP64 = 0,       /* every step in double precision                        */
+  ENKFMC_FP32 = 1        /* single precision; each regression takes one step of
+                            iterative refinement with an extended-precision
+                            residual (corrected semi-normal equations)            */
+} enkfmc_precision;
+
+/* Problem description.  Neighbours of a component share its variable, lie
+ * within `vert_reach` levels and within Chebyshev distance r on the
+ * (lat, lon) grid, longitude taken on the ring when lon_periodic != 0
+ * (Section 2.2, local boxes of Fig. 1).  Predecessors are the neighbours with
+ * a smaller label (Section 2.3, Fig. 2).  Sub-domains are sub_lat x sub_lon
+ * column tiles from (0, 0), the last ones ragged, extended by r columns on
+ * every side (clipped at the poles, wrapped in longitude) (Section 3).
+ * Requirements: nlon >= 2r+1 when lon_periodic, N >= 2, nvar_3d + nvar_2d <= 16.
+ * An extended sub-domain as wide as the ring covers it exactly once.  */
+typedef struct {
+  int32_t nlon, nlat, nlev, nvar_3d, nvar_2d;
+  int32_t lon_periodic;
+  int32_t r;
+  int32_t vert_reach;
+  int32_t N;
+  int32_t sub_lon, sub_lat;
+  int32_t precision;     /* enkfmc_precision                                      */
+  double ridge_c;        /* lambda = ridge_c * tr(G) / p wherever p >= N - 1      */
+} enkfmc_problem;
+
+/* Sizes of a created handle (host struct filled by enkfmc_query). */
+typedef struct {
+  int64_t n;             /* number of components                                  */
+  int32_t pmax;          /* slots per T row in the stencil layout of Tvals        */
+  int32_t nsub;          /* sub-domains                                           */
+  int32_t nblock;        /* (sub-domain, variable) blocks of A                    */
+  int32_t hb_max;        /* largest half-bandwidth of a block of A                */
+  int64_t ext_rows;      /* components in all extended sub-domains                */
+  int64_t halo_rows;     /* boundary rows re-estimated by enkfmc_assemble         */
+  int64_t band_elems;    /* stored band entries of all blocks of A                */
+  int64_t workspace_bytes;
+  int64_t m;             /* observations set by enkfmc_set_observations (or -1)   */
+} enkfmc_info;
+
+typedef struct enkfmc_handle enkfmc_handle;
+
+/* Create a handle for one problem on the current CUDA device.  `cuda_stream`
+ * is a cudaStream_t (NULL = legacy default stream).  Builds the geometry
+ * tables and allocates the workspace.  Returns EINVAL for unsupported
+ * geometry, ENOMEM when device memory runs out. */
+enkfmc_status enkfmc_create(enkfmc_handle** h, const enkfmc_problem* p, void* cuda_stream);
+void enkfmc_destroy(enkfmc_handle* h);
+const char* enkfmc_strerror(enkfmc_status s);
+enkfmc_status enkfmc_query(const enkfmc_handle* h, enkfmc_info* info /* host */);
+enkfmc_status enkfmc_set_stream(enkfmc_handle* h, void* cuda_stream);
+
+/* Stencil layout of Tvals: slot s of a row holds the coefficient of the
+ * neighbour at offset (dk[s], dlat[s], dlon[s]) (longitude offset taken on
+ * the ring), or 0 when that neighbour is not a predecessor.  Host arrays of
+ * length pmax. */
+enkfmc_status enkfmc_slot_offsets(const enkfmc_handle* h, int32_t* dk, int32_t* dlat,
+                                  int32_t* dlon);
+
+/* Observation network H: obs_idx (host, length m) lists the observed
+ * component labels in increasing order, without repeats (H selects
+ * components, Section 2.3).  Synchronous; validates and uploads index
+ * tables.  Must precede enkfmc_assemble.  m = 0 is allowed (no update). */
+enkfmc_status enkfmc_set_observations(enkfmc_handle* h, const int32_t* obs_idx, int64_t m);
+
+/* Step (a), Eq. 1-3 and Eq. 8 with S = U^b (Eq. 5): anomalies of Xb
+ * ([N][n]), then for every component j the regression on its predecessors:
+ * Tvals[j * pmax + s] = -beta (0 for absent slots) and D[j] = residual sum of
+ * squares / (N - 1).  Tvals: [n][pmax], D: [n], written on the stream. */
+enkfmc_status enkfmc_estimate(enkfmc_handle* h, const void* Xb, void* Tvals, void* D);
+
+/* Step (b), Algorithm 3 and Eq. 11: for every sub-domain re-estimate the
+ * boundary rows of its extended set from the local samples (predecessors
+ * cut to the extended set), assemble A = T^T D^-1 T + H^T R^-1 H in band
+ * storage per (sub-domain, variable) block and factor it.  Xb: [N][n];
+ * Tvals, D: as written by enkfmc_estimate; Rdiag: [m] observation-error
+ * variances.  Requires enkfmc_set_observations. */
+enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tvals,
+                              const void* D, const void* Rdiag);
+
+/* Step (c), Eq. 10-11 and Algorithm 2: Y^s = y 1^T + diag(sqrt(R)) Z^T with
+ * Z [N][m] standard normals; dX = A^-1 H^T R^-1 (Y^s - H X^b) per sub-domain;
+ * Xa[m * n + l] = Xb + dX for l in the sub-domain's interior.  Xb, Xa:
+ * [N][n] (Xa may not alias Xb); y, Rdiag: [m]; Z: [N][m].  Uses the factors
+ * of the last enkfmc_assemble. */
+enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
+                             const void* Rdiag, const void* Z, void* Xa);
+
+/* One full analysis from HOST buffers (same layouts as above): copies the
+ * inputs to the device, runs estimate + assemble + analyze, copies Xa back,
+ * and synchronises.  Returns the first numerical status as well. */
+enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
+                                const void* Rdiag, const void* Z, void* Xa);
+
+/* Gradient of a scalar loss through enkfmc_analyze (reserved). */
+enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void* y_bar,
+                                     void* Rdiag_bar, void* Xb_bar);
+
+/* Synchronise the stream; return the first numerical failure recorded since
+ * the last call (and clear it).  info (host, nullable) receives the index of
+ * the failing row or block. */
+enkfmc_status enkfmc_get_status(enkfmc_handle* h, int64_t* info);
+
+/* Strictly-lower pattern of the global T as CSR in label order (host arrays:
+ * rowptr [n+1]; colidx [rowptr[n]], or NULL to query the count via
+ * rowptr[n]).  Independent of any data. */
+enkfmc_status enkfmc_export_T_pattern(const enkfmc_handle* h, int64_t* rowptr, int32_t* colidx);
+
+/* Debug/test access to one block of the factored band after enkfmc_assemble:
+ * copies block b's band (column-major lower band, (hb+1) entries per column)
+ * into `host` (capacity in elements) and returns nb and hb. */
+enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_t capacity,
+                                 int64_t* nb, int32_t* hb);
+
+/* Kernel kinds launched by the library (index into the profiling arrays). */
+enum {
+  ENKFMC_K_ANOMALIES = 0,   /* Eq. 5 anomalies, transposed to component-major   */
+  ENKFMC_K_REGRESS = 1,     /* Eq. 1-3 regressions of every component            */
+  ENKFMC_K_REGRESS_HALO = 2,/* Algorithm 3: boundary rows from local samples     */
+  ENKFMC_K_ASSEMBLE = 3,    /* Eq. 11: band of A = T^T D^-1 T + H^T R^-1 H       */
+  ENKFMC_K_BANDCHOL = 4,    /* A = L L^T per (sub-domain, variable) block        */
+  ENKFMC_K_RHS = 5,         /* H^T R^-1 (Y^s - H X^b)                            */
+  ENKFMC_K_BANDSOLVE = 6,   /* L L^T dX = rhs for the N members                  */
+  ENKFMC_K_WRITEBACK = 7,   /* Eq. 10 on sub-domain interiors                    */
+  ENKFMC_NKERNEL = 8
+};
+
+/* Kernel timing.  While enabled, every kernel launch is bracketed by CUDA
+ * events recorded on the handle's stream (the stream the kernel runs on).
+ * enkfmc_profile_read synchronises and returns, per kernel kind, the launches
+ * and the summed device time (ms) since the previous read, then resets.
+ * launches, ms: host arrays of ENKFMC_NKERNEL. */
+enkfmc_status enkfmc_profile(enkfmc_handle* h, int32_t enable);
+enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* launches, double* ms);
+const char* enkfmc_kernel_name(int32_t kind);
+
+/* Algorithmic work of one launch of each kernel kind for this problem:
+ * floating-point operations of the method (a multiply-add counts 2) and the
+ * bytes a kernel must move to or from memory at least (inputs read once,
+ * outputs written once).  Implementation extras (refinement passes, re-reads)
+ * are not counted.  flops, bytes: host arrays of ENKFMC_NKERNEL.  Entries that
+ * depend on the observations are valid after enkfmc_set_observations. */
+enkfmc_status enkfmc_work_per_launch(const enkfmc_handle* h, double* flops, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ENKFMC_H */

@@ -1,0 +1,225 @@
+"""Python binding of libenkfmc.so (argument marshalling only).
+
+Every step of the analysis runs in the library's CUDA kernels; this module
+only loads the shared library, declares the C signatures of include/enkfmc.h,
+and turns torch tensors into device pointers.  There is no fallback: if the
+library cannot be loaded, `load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libenkfmc.so")
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "EDNONPOS", 5: "ENONFINITE",
+          6: "ETIMEOUT", 7: "ECUDA", 8: "ENOTIMPL", 9: "ESTATE"}
+FP64, FP32 = 0, 1
+
+
+class enkfmc_problem(ctypes.Structure):
+    _fields_ = [("nlon", c_int32), ("nlat", c_int32), ("nlev", c_int32), ("nvar_3d", c_int32),
+                ("nvar_2d", c_int32), ("lon_periodic", c_int32), ("r", c_int32),
+                ("vert_reach", c_int32), ("N", c_int32), ("sub_lon", c_int32),
+                ("sub_lat", c_int32), ("precision", c_int32), ("ridge_c", c_double)]
+
+
+class enkfmc_info(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("pmax", c_int32), ("nsub", c_int32), ("nblock", c_int32),
+                ("hb_max", c_int32), ("ext_rows", c_int64), ("halo_rows", c_int64),
+                ("band_elems", c_int64), ("workspace_bytes", c_int64), ("m", c_int64)]
+
+
+_H = c_void_p
+# name -> (restype, argtypes); mirrors include/enkfmc.h
+SIGNATURES = {
+    "enkfmc_create": (c_int32, [POINTER(c_void_p), POINTER(enkfmc_problem), c_void_p]),
+    "enkfmc_destroy": (None, [_H]),
+    "enkfmc_strerror": (c_char_p, [c_int32]),
+    "enkfmc_query": (c_int32, [_H, POINTER(enkfmc_info)]),
+    "enkfmc_set_stream": (c_int32, [_H, c_void_p]),
+    "enkfmc_slot_offsets": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_set_observations": (c_int32, [_H, c_void_p, c_int64]),
+    "enkfmc_estimate": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_assemble": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_analyze": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_cycle_host": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_analyze_adjoint": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_get_status": (c_int32, [_H, POINTER(c_int64)]),
+    "enkfmc_export_T_pattern": (c_int32, [_H, c_void_p, c_void_p]),
+    "enkfmc_debug_block": (c_int32, [_H, c_int32, c_void_p, c_int64, POINTER(c_int64),
+                                     POINTER(c_int32)]),
+    "enkfmc_profile": (c_int32, [_H, c_int32]),
+    "enkfmc_profile_read": (c_int32, [_H, c_void_p, c_void_p]),
+    "enkfmc_kernel_name": (c_char_p, [c_int32]),
+    "enkfmc_work_per_launch": (c_int32, [_H, c_void_p, c_void_p]),
+}
+NKERNEL = 8
+
+_LIB = None
+
+
+class EnkfmcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+def load(path: str | None = None, build_if_stale: bool = True):
+    """Load libenkfmc.so (building it in-tree first when sources are newer)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_stale and path is None:
+        from . import build as _build
+        _build.build()
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libenkfmc.so not found at {p}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise EnkfmcError(code, where)
+
+
+class Handle:
+    """One problem on the current CUDA device; methods mirror the C entry points."""
+
+    def __init__(self, *, nlon, nlat, nlev, nvar_3d, nvar_2d, r, N, sub_lon, sub_lat,
+                 precision=FP32, ridge_c=1e-3, vert_reach=1, lon_periodic=True, stream=None):
+        self.lib = load()
+        self.problem = enkfmc_problem(nlon, nlat, nlev, nvar_3d, nvar_2d, int(bool(lon_periodic)),
+                                      r, vert_reach, N, sub_lon, sub_lat, precision, ridge_c)
+        h = c_void_p()
+        _check(self.lib.enkfmc_create(ctypes.byref(h), ctypes.byref(self.problem),
+                                      c_void_p(stream)), "enkfmc_create")
+        self.h = h
+        self.precision = precision
+        self.info = self.query()
+
+    @classmethod
+    def from_workload(cls, w, precision=FP32, stream=None):
+        return cls(nlon=w.nlon, nlat=w.nlat, nlev=w.nlev, nvar_3d=w.nvar_3d, nvar_2d=w.nvar_2d,
+                   r=w.r, N=w.N, sub_lon=w.sub_lon, sub_lat=w.sub_lat, precision=precision,
+                   ridge_c=w.ridge_c, vert_reach=w.vert_reach, lon_periodic=w.lon_periodic,
+                   stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.enkfmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self) -> enkfmc_info:
+        info = enkfmc_info()
+        _check(self.lib.enkfmc_query(self.h, ctypes.byref(info)), "enkfmc_query")
+        return info
+
+    def set_stream(self, stream):
+        _check(self.lib.enkfmc_set_stream(self.h, c_void_p(stream)), "enkfmc_set_stream")
+
+    def slot_offsets(self):
+        pm = self.info.pmax
+        dk, dy, dx = (np.zeros(pm, np.int32) for _ in range(3))
+        _check(self.lib.enkfmc_slot_offsets(self.h, _ptr(dk), _ptr(dy), _ptr(dx)), "slot_offsets")
+        return dk, dy, dx
+
+    def set_observations(self, obs_idx):
+        a = np.ascontiguousarray(obs_idx, dtype=np.int32)
+        _check(self.lib.enkfmc_set_observations(self.h, _ptr(a) if a.size else None, a.size),
+               "enkfmc_set_observations")
+        self.info = self.query()
+
+    def estimate(self, Xb, Tvals, D):
+        _check(self.lib.enkfmc_estimate(self.h, _ptr(Xb), _ptr(Tvals), _ptr(D)), "enkfmc_estimate")
+
+    def assemble(self, Xb, Tvals, D, R):
+        _check(self.lib.enkfmc_assemble(self.h, _ptr(Xb), _ptr(Tvals), _ptr(D), _ptr(R)),
+               "enkfmc_assemble")
+
+    def analyze(self, Xb, y, R, Z, Xa):
+        _check(self.lib.enkfmc_analyze(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
+               "enkfmc_analyze")
+
+    def cycle_host(self, Xb, y, R, Z, Xa):
+        _check(self.lib.enkfmc_cycle_host(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
+               "enkfmc_cycle_host")
+
+    def get_status(self):
+        info = c_int64(0)
+        code = self.lib.enkfmc_get_status(self.h, ctypes.byref(info))
+        return int(code), int(info.value)
+
+    def check(self, where="device status"):
+        code, info = self.get_status()
+        if code:
+            raise EnkfmcError(code, f"{where} (info {info})")
+
+    def export_T_pattern(self):
+        n = self.info.n
+        rowptr = np.zeros(n + 1, np.int64)
+        _check(self.lib.enkfmc_export_T_pattern(self.h, _ptr(rowptr), None), "export_T_pattern")
+        col = np.zeros(max(1, int(rowptr[-1])), np.int32)
+        _check(self.lib.enkfmc_export_T_pattern(self.h, _ptr(rowptr), _ptr(col)), "export_T_pattern")
+        return rowptr, col[:int(rowptr[-1])]
+
+    def profile(self, enable: bool):
+        _check(self.lib.enkfmc_profile(self.h, int(bool(enable))), "enkfmc_profile")
+
+    def profile_read(self):
+        """{kernel name: (launches, total ms)} since the previous read."""
+        n = np.zeros(NKERNEL, np.int64)
+        ms = np.zeros(NKERNEL, np.float64)
+        _check(self.lib.enkfmc_profile_read(self.h, _ptr(n), _ptr(ms)), "enkfmc_profile_read")
+        return {self.lib.enkfmc_kernel_name(k).decode(): (int(n[k]), float(ms[k]))
+                for k in range(NKERNEL)}
+
+    def work_per_launch(self):
+        """{kernel name: (algorithmic flops, algorithmic bytes)} per launch."""
+        f = np.zeros(NKERNEL, np.float64)
+        b = np.zeros(NKERNEL, np.float64)
+        _check(self.lib.enkfmc_work_per_launch(self.h, _ptr(f), _ptr(b)), "work_per_launch")
+        return {self.lib.enkfmc_kernel_name(k).decode(): (float(f[k]), float(b[k]))
+                for k in range(NKERNEL)}
+
+    def debug_block(self, b, dtype):
+        nb, hb = c_int64(0), c_int32(0)
+        _check(self.lib.enkfmc_debug_block(self.h, b, None, 0, ctypes.byref(nb), ctypes.byref(hb)),
+               "debug_block")
+        buf = np.zeros(nb.value * (hb.value + 1), dtype=dtype)
+        _check(self.lib.enkfmc_debug_block(self.h, b, _ptr(buf), buf.size, ctypes.byref(nb),
+                                           ctypes.byref(hb)), "debug_block")
+        return buf.reshape(nb.value, hb.value + 1), hb.value

@@ -1,0 +1,636 @@
+// Host side of the C ABI: problem validation, geometry tables (sub-domains,
+// blocks, boundary rows, band widths), workspace, and the call sequence of
+// one analysis (Algorithm 2: estimate, assemble, analyze).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "enkfmc_internal.h"
+
+using namespace enkfmc;
+
+namespace {
+
+#define CUDA_TRY(expr)                                  \
+  do {                                                  \
+    cudaError_t e_ = (expr);                            \
+    if (e_ != cudaSuccess) {                            \
+      (void)cudaGetLastError();                         \
+      return e_ == cudaErrorMemoryAllocation ? ENKFMC_ENOMEM : ENKFMC_ECUDA; \
+    }                                                   \
+  } while (0)
+
+template <typename P>
+enkfmc_status dalloc(enkfmc_handle* h, P** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *ptr = nullptr;
+    return e == cudaErrorMemoryAllocation ? ENKFMC_ENOMEM : ENKFMC_ECUDA;
+  }
+  h->workspace_bytes += (int64_t)bytes;
+  return ENKFMC_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool is_fp64(const enkfmc_handle* h) { return h->prob.precision == ENKFMC_FP64; }
+
+// Half-bandwidth of A on one block: the widest spread, in local order, of a
+// row of T together with its predecessors inside the extended box.
+int block_bandwidth(const Geom& g, const Block& b) {
+  int hb = 0;
+  for (int loc = 0; loc < b.nb; ++loc) {
+    const int plane = b.ey * b.ex;
+    const int k = loc / plane;
+    const int yy = (loc - k * plane) / b.ex;
+    const int xx = loc - k * plane - yy * b.ex;
+    const int y = b.lat_lo + yy, x = imod(b.lon_lo + xx, g.nlon);
+    int lo = loc, hi = loc;
+    for (int s = 0; s < g.pmax; ++s) {
+      int kq, yq, xq, yyq, xxq;
+      if (!slot_pred(g, k, y, x, s, kq, yq, xq)) continue;
+      if (!in_ext(b, g.nlon, yq, xq, yyq, xxq)) continue;
+      const int lq = (kq * b.ey + yyq) * b.ex + xxq;
+      lo = std::min(lo, lq);
+      hi = std::max(hi, lq);
+    }
+    hb = std::max(hb, hi - lo);
+  }
+  return hb;
+}
+
+void compute_work(enkfmc_handle* h, const std::vector<int>& p_global,
+                  const std::vector<int>& p_ext);
+
+enkfmc_status build(enkfmc_handle* h) {
+  const enkfmc_problem& p = h->prob;
+  const int nvar = p.nvar_3d + p.nvar_2d;
+  if (p.nlon < 1 || p.nlat < 1 || p.nlev < 1 || p.nvar_3d < 0 || p.nvar_2d < 0 || nvar < 1 ||
+      nvar > kMaxVar || p.r < 0 || p.vert_reach < 0 || p.N < 2 || p.N > 128 || p.sub_lon < 1 ||
+      p.sub_lat < 1 || !(p.ridge_c >= 0.0) || p.r > 16)
+    return ENKFMC_EINVAL;
+  if (p.precision != ENKFMC_FP64 && p.precision != ENKFMC_FP32) return ENKFMC_EINVAL;
+  if (p.lon_periodic && p.nlon < 2 * p.r + 1) return ENKFMC_EINVAL;
+  Geom& g = h->g;
+  std::memset(&g, 0, sizeof(g));
+  g.nlon = p.nlon;
+  g.nlat = p.nlat;
+  g.nlev = p.nlev;
+  g.nvar3 = p.nvar_3d;
+  g.nvar2 = p.nvar_2d;
+  g.nvar = nvar;
+  g.r = p.r;
+  g.vr = p.nvar_3d > 0 ? std::min(p.vert_reach, p.nlev - 1) : 0;
+  g.periodic = p.lon_periodic ? 1 : 0;
+  g.N = p.N;
+  g.ldN = (p.N + 3) / 4 * 4;
+  g.pmax = slot_count(g.r, g.vr, g.periodic);
+  int64_t off = 0;
+  for (int v = 0; v < nvar; ++v) {
+    g.var_off[v] = off;
+    g.var_lev[v] = v < p.nvar_3d ? p.nlev : 1;
+    off += (int64_t)g.var_lev[v] * p.nlat * p.nlon;
+  }
+  g.var_off[nvar] = off;
+  g.n = off;
+  if (g.n > ((int64_t)1 << 31) - 1) return ENKFMC_EINVAL;
+  h->esize = is_fp64(h) ? sizeof(double) : sizeof(float);
+
+  // sub-domains and blocks (Section 3, Fig. 3)
+  h->nsuby = (p.nlat + p.sub_lat - 1) / p.sub_lat;
+  h->nsubx = (p.nlon + p.sub_lon - 1) / p.sub_lon;
+  h->nsub = h->nsubx * h->nsuby;
+  h->nblock = h->nsub * nvar;
+  h->blocks.clear();
+  h->blocks.reserve(h->nblock);
+  int64_t row_off = 0, band_off = 0;
+  h->hb_max = 0;
+  h->nb_max = 0;
+  std::vector<int32_t> halo;
+  for (int sy = 0; sy < h->nsuby; ++sy) {
+    for (int sx = 0; sx < h->nsubx; ++sx) {
+      Block b{};
+      b.sub = sy * h->nsubx + sx;
+      b.lat0 = sy * p.sub_lat;
+      b.lat1 = std::min(p.nlat, b.lat0 + p.sub_lat);
+      b.lon0 = sx * p.sub_lon;
+      b.lon1 = std::min(p.nlon, b.lon0 + p.sub_lon);
+      b.lat_lo = std::max(0, b.lat0 - p.r);
+      b.ey = std::min(p.nlat, b.lat1 + p.r) - b.lat_lo;
+      if (g.periodic) {
+        b.ex = std::min(b.lon1 - b.lon0 + 2 * p.r, p.nlon);
+        b.lon_lo = imod(b.lon0 - p.r, p.nlon);
+      } else {
+        b.lon_lo = std::max(0, b.lon0 - p.r);
+        b.ex = std::min(p.nlon, b.lon1 + p.r) - b.lon_lo;
+      }
+      for (int v = 0; v < nvar; ++v) {
+        Block bb = b;
+        bb.var = v;
+        bb.nlev_b = g.var_lev[v];
+        bb.nb = bb.nlev_b * bb.ey * bb.ex;
+        bb.hb = block_bandwidth(g, bb);
+        bb.row_off = row_off;
+        bb.band_off = band_off;
+        const int blk = (int)h->blocks.size();
+        for (int loc = 0; loc < bb.nb; ++loc) {
+          const int plane = bb.ey * bb.ex;
+          const int k = loc / plane;
+          const int yy = (loc - k * plane) / bb.ex;
+          const int xx = loc - k * plane - yy * bb.ex;
+          (void)k;
+          if (!in_interior(bb, bb.lat_lo + yy, imod(bb.lon_lo + xx, p.nlon))) {
+            halo.push_back(blk);
+            halo.push_back(loc);
+          }
+        }
+        row_off += bb.nb;
+        band_off += (int64_t)bb.nb * (bb.hb + 1);
+        h->hb_max = std::max(h->hb_max, bb.hb);
+        h->nb_max = std::max(h->nb_max, bb.nb);
+        h->blocks.push_back(bb);
+      }
+    }
+  }
+  h->ext_rows = row_off;
+  h->band_elems = band_off;
+  h->halo_rows = (int64_t)halo.size() / 2;
+
+  // predecessor counts for the work model
+  std::vector<int> p_global((size_t)g.n), p_ext;
+  p_ext.reserve((size_t)h->ext_rows);
+  for (int64_t l = 0; l < g.n; ++l) {
+    int v, k, y, x;
+    label_coords(g, l, v, k, y, x);
+    int p = 0;
+    for (int s = 0; s < g.pmax; ++s) {
+      int kq, yq, xq;
+      if (slot_pred(g, k, y, x, s, kq, yq, xq)) ++p;
+    }
+    p_global[(size_t)l] = p;
+  }
+  for (const Block& b : h->blocks) {
+    const int plane = b.ey * b.ex;
+    for (int loc = 0; loc < b.nb; ++loc) {
+      const int k = loc / plane, yy = (loc - k * plane) / b.ex, xx = loc - k * plane - yy * b.ex;
+      const int y = b.lat_lo + yy, x = imod(b.lon_lo + xx, g.nlon);
+      int p = 0;
+      for (int s = 0; s < g.pmax; ++s) {
+        int kq, yq, xq, a, c;
+        if (slot_pred(g, k, y, x, s, kq, yq, xq) && in_ext(b, g.nlon, yq, xq, a, c)) ++p;
+      }
+      p_ext.push_back(in_interior(b, y, x) ? p : -p - 1);
+    }
+  }
+  compute_work(h, p_global, p_ext);
+
+  enkfmc_status st;
+  if ((st = dalloc(h, &h->d_blocks, sizeof(Block) * h->blocks.size()))) return st;
+  if ((st = dalloc(h, &h->d_halo, sizeof(int32_t) * halo.size()))) return st;
+  if ((st = dalloc(h, &h->d_status, 16))) return st;
+  if ((st = dalloc(h, &h->d_obs_of, sizeof(int32_t) * g.n))) return st;
+  if ((st = dalloc(h, &h->d_U, h->esize * g.n * g.ldN))) return st;
+  if ((st = dalloc(h, &h->d_Te, h->esize * h->ext_rows * std::max(1, g.pmax)))) return st;
+  if ((st = dalloc(h, &h->d_De, h->esize * h->ext_rows))) return st;
+  if ((st = dalloc(h, &h->d_band, h->esize * h->band_elems))) return st;
+  if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
+  CUDA_TRY(cudaMemcpy(h->d_blocks, h->blocks.data(), sizeof(Block) * h->blocks.size(),
+                      cudaMemcpyHostToDevice));
+  if (!halo.empty())
+    CUDA_TRY(cudaMemcpy(h->d_halo, halo.data(), sizeof(int32_t) * halo.size(),
+                        cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(h->d_status, 0, 16));
+  return ENKFMC_OK;
+}
+
+void release(enkfmc_handle* h) {
+  void* bufs[] = {h->d_blocks, h->d_halo, h->d_status, h->d_obs_of, h->d_U, h->d_Te, h->d_De,
+                  h->d_band, h->d_rhs, h->d_Xb, h->d_y, h->d_R, h->d_Z, h->d_Xa, h->d_T, h->d_D};
+  for (void* b : bufs) dfree(b);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  h->pool.clear();
+}
+
+enkfmc_status check_launch(cudaError_t e) {
+  if (e == cudaSuccess) return ENKFMC_OK;
+  (void)cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? ENKFMC_ENOMEM : ENKFMC_ECUDA;
+}
+
+cudaEvent_t pooled_event(enkfmc_handle* h) {
+  if (h->pool_used == h->pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
+    h->pool.push_back(e);
+  }
+  return h->pool[h->pool_used++];
+}
+
+// Launch one kernel; while profiling, bracket it with events on the stream.
+template <class F>
+enkfmc_status timed(enkfmc_handle* h, int kind, F&& launch) {
+  if (!h->prof) return check_launch(launch());
+  cudaEvent_t a = pooled_event(h), b = pooled_event(h);
+  if (!a || !b) return ENKFMC_ECUDA;
+  cudaEventRecord(a, h->stream);
+  enkfmc_status st = check_launch(launch());
+  cudaEventRecord(b, h->stream);
+  h->recs.push_back({kind, a, b});
+  return st;
+}
+
+template <typename T>
+enkfmc_status run_anomalies(enkfmc_handle* h, const T* Xb) {
+  return timed(h, ENKFMC_K_ANOMALIES,
+               [&] { return launch_anomalies<T>(h->g, Xb, (T*)h->d_U, h->stream); });
+}
+
+template <typename T>
+enkfmc_status run_estimate(enkfmc_handle* h, const T* Xb, T* Tv, T* D) {
+  enkfmc_status st = run_anomalies<T>(h, Xb);
+  if (st) return st;
+  return timed(h, ENKFMC_K_REGRESS, [&] {
+    return launch_regress<T>(h->g, (const T*)h->d_U, nullptr, h->g.n, h->d_blocks, Tv, D,
+                             h->prob.ridge_c, h->d_status, h->stream);
+  });
+}
+
+template <typename T>
+enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R) {
+  enkfmc_status st = timed(h, ENKFMC_K_REGRESS_HALO, [&] {
+    return launch_regress<T>(h->g, (const T*)h->d_U, h->d_halo, h->halo_rows, h->d_blocks,
+                             (T*)h->d_Te, (T*)h->d_De, h->prob.ridge_c, h->d_status, h->stream);
+  });
+  if (st) return st;
+  st = timed(h, ENKFMC_K_ASSEMBLE, [&] {
+    return launch_assemble<T>(h->g, h->d_blocks, h->nblock, h->nb_max, Tv, D, (const T*)h->d_Te,
+                              (const T*)h->d_De, h->d_obs_of, R, (T*)h->d_band, h->d_status,
+                              h->stream, h->hb_max);
+  });
+  if (st) return st;
+  return timed(h, ENKFMC_K_BANDCHOL, [&] {
+    return launch_bandchol<T>(h->d_blocks, h->nblock, h->hb_max, (T*)h->d_band, h->d_status,
+                              h->stream);
+  });
+}
+
+template <typename T>
+enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R, const T* Z,
+                          T* Xa) {
+  enkfmc_status st = timed(h, ENKFMC_K_RHS, [&] {
+    return launch_rhs<T>(h->g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m, Xb, y, R, Z,
+                         (T*)h->d_rhs, h->stream);
+  });
+  if (st) return st;
+  st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
+    return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, h->g.N, (const T*)h->d_band,
+                               (T*)h->d_rhs, h->stream);
+  });
+  if (st) return st;
+  return timed(h, ENKFMC_K_WRITEBACK, [&] {
+    return launch_writeback<T>(h->g, h->d_blocks, h->nsubx, h->prob.sub_lon, h->prob.sub_lat, Xb,
+                               (const T*)h->d_rhs, Xa, h->stream);
+  });
+}
+
+// Algorithmic work per launch (see enkfmc_work_per_launch).  Regression of a
+// row with p predecessors: augmented Gram 2N((p+1)(p+2)/2), Cholesky p^3/3,
+// two triangular solves 2p^2, residual 2Np.  Band factor: column c with
+// w = min(hb, nb-1-c) entries below the diagonal costs w + w(w+1) flops.
+// Band solves: 4N w per column plus 2N divisions.
+void compute_work(enkfmc_handle* h, const std::vector<int>& p_global,
+                  const std::vector<int>& p_ext) {
+  const Geom& g = h->g;
+  const double N = g.N, es = (double)h->esize;
+  auto reg = [&](double p) {
+    return 2.0 * N * ((p + 1) * (p + 2) / 2.0) + p * p * p / 3.0 + 2.0 * p * p + 2.0 * N * p;
+  };
+  double f_glob = 0, f_halo = 0, f_asm = 0, t_read = 0;
+  for (int p : p_global) f_glob += reg(p);
+  for (size_t i = 0; i < p_ext.size(); ++i) {
+    const double p = p_ext[i] >= 0 ? p_ext[i] : -p_ext[i] - 1;
+    if (p_ext[i] < 0) f_halo += reg(p);  // negative entries mark boundary rows
+    f_asm += (p + 1) * (p + 2);
+    t_read += p + 2;
+  }
+  double f_chol = 0, f_solve = 0;
+  for (const Block& b : h->blocks) {
+    for (int c = 0; c < b.nb; ++c) {
+      const double w = std::min(b.hb, b.nb - 1 - c);
+      f_chol += w + w * (w + 1);
+      f_solve += 4.0 * N * w + 2.0 * N;
+    }
+  }
+  const double n = (double)g.n, er = (double)h->ext_rows, hr = (double)h->halo_rows;
+  h->work_flops[ENKFMC_K_ANOMALIES] = 2.0 * N * n;
+  h->work_bytes[ENKFMC_K_ANOMALIES] = es * 2.0 * N * n;
+  h->work_flops[ENKFMC_K_REGRESS] = f_glob;
+  h->work_bytes[ENKFMC_K_REGRESS] = es * (N * n + n * (g.pmax + 1));
+  h->work_flops[ENKFMC_K_REGRESS_HALO] = f_halo;
+  h->work_bytes[ENKFMC_K_REGRESS_HALO] = es * (N * hr + hr * (g.pmax + 1));
+  h->work_flops[ENKFMC_K_ASSEMBLE] = f_asm;
+  h->work_bytes[ENKFMC_K_ASSEMBLE] = es * ((double)h->band_elems + t_read);
+  h->work_flops[ENKFMC_K_BANDCHOL] = f_chol;
+  h->work_bytes[ENKFMC_K_BANDCHOL] = es * 2.0 * (double)h->band_elems;
+  h->work_flops[ENKFMC_K_RHS] = 0;
+  h->work_bytes[ENKFMC_K_RHS] = es * N * er;
+  h->work_flops[ENKFMC_K_BANDSOLVE] = f_solve;
+  h->work_bytes[ENKFMC_K_BANDSOLVE] = es * (2.0 * (double)h->band_elems + 4.0 * N * er);
+  h->work_flops[ENKFMC_K_WRITEBACK] = N * n;
+  h->work_bytes[ENKFMC_K_WRITEBACK] = es * 3.0 * N * n;
+}
+
+// Observation-dependent terms: rhs reads Xb, Z for every observed ext row.
+void compute_obs_work(enkfmc_handle* h, const std::vector<int32_t>& obs_of) {
+  const Geom& g = h->g;
+  double ext_obs = 0;
+  for (const Block& b : h->blocks) {
+    const int plane = b.ey * b.ex;
+    for (int loc = 0; loc < b.nb; ++loc) {
+      const int k = loc / plane, yy = (loc - k * plane) / b.ex, xx = loc - k * plane - yy * b.ex;
+      if (obs_of[coords_label(g, b.var, k, b.lat_lo + yy, imod(b.lon_lo + xx, g.nlon))] >= 0)
+        ext_obs += 1;
+    }
+  }
+  const double N = g.N, es = (double)h->esize;
+  h->work_flops[ENKFMC_K_RHS] = 4.0 * N * ext_obs;
+  h->work_bytes[ENKFMC_K_RHS] = es * (N * (double)h->ext_rows + 2.0 * N * ext_obs);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* enkfmc_strerror(enkfmc_status s) {
+  switch (s) {
+    case ENKFMC_OK: return "ok";
+    case ENKFMC_EINVAL: return "invalid argument or unsupported geometry";
+    case ENKFMC_ENOMEM: return "out of memory";
+    case ENKFMC_ENOTSPD: return "sub-domain matrix not positive definite";
+    case ENKFMC_EDNONPOS: return "singular Gram matrix or non-positive residual variance";
+    case ENKFMC_ENONFINITE: return "non-finite value";
+    case ENKFMC_ETIMEOUT: return "device wait timed out";
+    case ENKFMC_ECUDA: return "CUDA runtime error";
+    case ENKFMC_ENOTIMPL: return "not implemented";
+    case ENKFMC_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+enkfmc_status enkfmc_create(enkfmc_handle** out, const enkfmc_problem* p, void* stream) {
+  if (!out || !p) return ENKFMC_EINVAL;
+  *out = nullptr;
+  enkfmc_handle* h = new (std::nothrow) enkfmc_handle();
+  if (!h) return ENKFMC_ENOMEM;
+  h->prob = *p;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete h;
+    return ENKFMC_ECUDA;
+  }
+  enkfmc_status st = build(h);
+  if (st != ENKFMC_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return ENKFMC_OK;
+}
+
+void enkfmc_destroy(enkfmc_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  release(h);
+  delete h;
+}
+
+enkfmc_status enkfmc_query(const enkfmc_handle* h, enkfmc_info* info) {
+  if (!h || !info) return ENKFMC_EINVAL;
+  info->n = h->g.n;
+  info->pmax = h->g.pmax;
+  info->nsub = h->nsub;
+  info->nblock = h->nblock;
+  info->hb_max = h->hb_max;
+  info->ext_rows = h->ext_rows;
+  info->halo_rows = h->halo_rows;
+  info->band_elems = h->band_elems;
+  info->workspace_bytes = h->workspace_bytes;
+  info->m = h->m;
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_set_stream(enkfmc_handle* h, void* stream) {
+  if (!h) return ENKFMC_EINVAL;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_slot_offsets(const enkfmc_handle* h, int32_t* dk, int32_t* dlat,
+                                  int32_t* dlon) {
+  if (!h || !dk || !dlat || !dlon) return ENKFMC_EINVAL;
+  for (int s = 0; s < h->g.pmax; ++s) {
+    int a, b, c;
+    slot_offset(s, h->g.r, h->g.vr, a, b, c);
+    dk[s] = a;
+    dlat[s] = b;
+    dlon[s] = c;
+  }
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_set_observations(enkfmc_handle* h, const int32_t* obs_idx, int64_t m) {
+  if (!h || m < 0 || (m > 0 && !obs_idx) || m > h->g.n) return ENKFMC_EINVAL;
+  std::vector<int32_t> of((size_t)h->g.n, -1);
+  for (int64_t o = 0; o < m; ++o) {
+    const int32_t c = obs_idx[o];
+    if (c < 0 || c >= h->g.n) return ENKFMC_EINVAL;
+    if (o > 0 && c <= obs_idx[o - 1]) return ENKFMC_EINVAL;
+    of[c] = (int32_t)o;
+  }
+  CUDA_TRY(cudaMemcpy(h->d_obs_of, of.data(), sizeof(int32_t) * of.size(),
+                      cudaMemcpyHostToDevice));
+  h->m = m;
+  h->assembled = false;
+  compute_obs_work(h, of);
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_estimate(enkfmc_handle* h, const void* Xb, void* Tvals, void* D) {
+  if (!h || !Xb || !Tvals || !D) return ENKFMC_EINVAL;
+  if (is_fp64(h))
+    return run_estimate<double>(h, (const double*)Xb, (double*)Tvals, (double*)D);
+  return run_estimate<float>(h, (const float*)Xb, (float*)Tvals, (float*)D);
+}
+
+enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tvals, const void* D,
+                              const void* Rdiag) {
+  if (!h || !Xb || !Tvals || !D || (h->m > 0 && !Rdiag)) return ENKFMC_EINVAL;
+  if (h->m < 0) return ENKFMC_ESTATE;
+  // anomalies of this Xb (the halo regressions use them)
+  enkfmc_status st;
+  if (is_fp64(h)) {
+    st = run_anomalies<double>(h, (const double*)Xb);
+    if (!st) st = run_assemble<double>(h, (const double*)Tvals, (const double*)D, (const double*)Rdiag);
+  } else {
+    st = run_anomalies<float>(h, (const float*)Xb);
+    if (!st) st = run_assemble<float>(h, (const float*)Tvals, (const float*)D, (const float*)Rdiag);
+  }
+  h->assembled = (st == ENKFMC_OK);
+  return st;
+}
+
+enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y, const void* Rdiag,
+                             const void* Z, void* Xa) {
+  if (!h || !Xb || !Xa || Xa == Xb) return ENKFMC_EINVAL;
+  if (h->m > 0 && (!y || !Rdiag || !Z)) return ENKFMC_EINVAL;
+  if (!h->assembled) return ENKFMC_ESTATE;
+  if (is_fp64(h))
+    return run_analyze<double>(h, (const double*)Xb, (const double*)y, (const double*)Rdiag,
+                               (const double*)Z, (double*)Xa);
+  return run_analyze<float>(h, (const float*)Xb, (const float*)y, (const float*)Rdiag,
+                            (const float*)Z, (float*)Xa);
+}
+
+enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y, const void* Rdiag,
+                                const void* Z, void* Xa) {
+  if (!h || !Xb || !Xa) return ENKFMC_EINVAL;
+  if (h->m < 0) return ENKFMC_ESTATE;
+  if (h->m > 0 && (!y || !Rdiag || !Z)) return ENKFMC_EINVAL;
+  const size_t es = h->esize;
+  const size_t xbytes = es * (size_t)h->g.N * h->g.n;
+  const size_t obytes = es * (size_t)h->m;
+  const size_t zbytes = es * (size_t)h->g.N * h->m;
+  enkfmc_status st;
+  if (!h->d_Xb) {
+    if ((st = dalloc(h, &h->d_Xb, xbytes))) return st;
+    if ((st = dalloc(h, &h->d_Xa, xbytes))) return st;
+    if ((st = dalloc(h, &h->d_y, obytes))) return st;
+    if ((st = dalloc(h, &h->d_R, obytes))) return st;
+    if ((st = dalloc(h, &h->d_Z, zbytes))) return st;
+    if ((st = dalloc(h, &h->d_T, es * (size_t)h->g.n * std::max(1, h->g.pmax)))) return st;
+    if ((st = dalloc(h, &h->d_D, es * (size_t)h->g.n))) return st;
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_Xb, Xb, xbytes, cudaMemcpyHostToDevice, h->stream));
+  if (h->m > 0) {
+    CUDA_TRY(cudaMemcpyAsync(h->d_y, y, obytes, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_R, Rdiag, obytes, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_Z, Z, zbytes, cudaMemcpyHostToDevice, h->stream));
+  }
+  if ((st = enkfmc_estimate(h, h->d_Xb, h->d_T, h->d_D))) return st;
+  if ((st = enkfmc_assemble(h, h->d_Xb, h->d_T, h->d_D, h->d_R))) return st;
+  if ((st = enkfmc_analyze(h, h->d_Xb, h->d_y, h->d_R, h->d_Z, h->d_Xa))) return st;
+  CUDA_TRY(cudaMemcpyAsync(Xa, h->d_Xa, xbytes, cudaMemcpyDeviceToHost, h->stream));
+  return enkfmc_get_status(h, nullptr);
+}
+
+enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void*, void*, void*, void*) {
+  if (!h) return ENKFMC_EINVAL;
+  return ENKFMC_ENOTIMPL;
+}
+
+enkfmc_status enkfmc_get_status(enkfmc_handle* h, int64_t* info) {
+  if (!h) return ENKFMC_EINVAL;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  int32_t st[4] = {0, 0, 0, 0};
+  CUDA_TRY(cudaMemcpy(st, h->d_status, 16, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(h->d_status, 0, 16));
+  if (info) {
+    int64_t v;
+    std::memcpy(&v, st + 2, 8);
+    *info = v;
+  }
+  return (enkfmc_status)st[0];
+}
+
+enkfmc_status enkfmc_export_T_pattern(const enkfmc_handle* h, int64_t* rowptr, int32_t* colidx) {
+  if (!h || !rowptr) return ENKFMC_EINVAL;
+  const Geom& g = h->g;
+  std::vector<int64_t> row;
+  int64_t nnz = 0;
+  rowptr[0] = 0;
+  for (int64_t l = 0; l < g.n; ++l) {
+    int v, k, y, x;
+    label_coords(g, l, v, k, y, x);
+    row.clear();
+    for (int s = 0; s < g.pmax; ++s) {
+      int kq, yq, xq;
+      if (slot_pred(g, k, y, x, s, kq, yq, xq)) row.push_back(coords_label(g, v, kq, yq, xq));
+    }
+    std::sort(row.begin(), row.end());
+    if (colidx)
+      for (size_t i = 0; i < row.size(); ++i) colidx[nnz + (int64_t)i] = (int32_t)row[i];
+    nnz += (int64_t)row.size();
+    rowptr[l + 1] = nnz;
+  }
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_t capacity,
+                                 int64_t* nb, int32_t* hb) {
+  if (!h || b < 0 || b >= h->nblock) return ENKFMC_EINVAL;
+  const Block& bl = h->blocks[b];
+  if (nb) *nb = bl.nb;
+  if (hb) *hb = bl.hb;
+  const int64_t cnt = (int64_t)bl.nb * (bl.hb + 1);
+  if (!host) return ENKFMC_OK;
+  if (capacity < cnt) return ENKFMC_EINVAL;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cudaMemcpy(host, (char*)h->d_band + h->esize * bl.band_off, h->esize * cnt,
+                      cudaMemcpyDeviceToHost));
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_profile(enkfmc_handle* h, int32_t enable) {
+  if (!h) return ENKFMC_EINVAL;
+  h->prof = enable != 0;
+  return ENKFMC_OK;
+}
+
+enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* launches, double* ms) {
+  if (!h || !launches || !ms) return ENKFMC_EINVAL;
+  for (int k = 0; k < ENKFMC_NKERNEL; ++k) {
+    launches[k] = 0;
+    ms[k] = 0.0;
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (const auto& r : h->recs) {
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    launches[r.kind] += 1;
+    ms[r.kind] += t;
+  }
+  h->recs.clear();
+  h->pool_used = 0;
+  return ENKFMC_OK;
+}
+
+const char* enkfmc_kernel_name(int32_t kind) {
+  static const char* names[ENKFMC_NKERNEL] = {"anomalies", "regress",   "regress_halo",
+                                              "assemble",  "bandchol",  "rhs",
+                                              "bandsolve", "writeback"};
+  return (kind >= 0 && kind < ENKFMC_NKERNEL) ? names[kind] : "unknown";
+}
+
+enkfmc_status enkfmc_work_per_launch(const enkfmc_handle* h, double* flops, double* bytes) {
+  if (!h || !flops || !bytes) return ENKFMC_EINVAL;
+  for (int k = 0; k < ENKFMC_NKERNEL; ++k) {
+    flops[k] = h->work_flops[k];
+    bytes[k] = h->work_bytes[k];
+  }
+  return ENKFMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// Internal declarations of libenkfmc: geometry shared by host tables and
+// kernels, the handle, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "enkfmc.h"
+
+namespace enkfmc {
+
+constexpr int kMaxVar = 16;
+
+// Grid and localisation parameters (Section 2.2-2.3).  Passed by value to
+// kernels.
+struct Geom {
+  int32_t nlon, nlat, nlev, nvar3, nvar2, nvar;
+  int32_t r, vr, periodic, N, ldN;  // vr: effective vertical reach
+  int32_t pmax;
+  int64_t n;
+  int64_t var_off[kMaxVar + 1];
+  int32_t var_lev[kMaxVar];
+};
+
+// One (sub-domain, variable) block of the extended set.  Local index of a
+// component: loc = (k * ey + (lat - lat_lo)) * ex + ((lon - lon_lo) mod nlon).
+struct Block {
+  int32_t sub, var, nlev_b;
+  int32_t lat_lo, ey, lon_lo, ex;  // extended box (ex == nlon: the whole ring)
+  int32_t lat0, lat1, lon0, lon1;  // interior tile (absolute, lon1 <= nlon)
+  int32_t hb;                      // half-bandwidth of A in local order
+  int32_t nb;                      // rows of the block
+  int64_t band_off;                // offset of the band in the band array
+  int64_t row_off;                 // offset of the block's rows (Te, De, rhs rows)
+};
+
+// ---------------------------------------------------------------------------
+// Stencil slots.  Slot s of a row of T is the neighbour at offset
+// (dk, dy, dx): first the vr lower levels ((2r+1)^2 each), then the r earlier
+// latitude rows of the same level, then the r neighbours to the left on the
+// same row, then (ring only) the r neighbours to the right that precede the
+// component across the longitude seam.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int slot_count(int r, int vr, int periodic) {
+  const int w = 2 * r + 1;
+  return vr * w * w + r * w + r + (periodic ? r : 0);
+}
+
+__host__ __device__ inline void slot_offset(int s, int r, int vr, int& dk, int& dy, int& dx) {
+  const int w = 2 * r + 1, box = w * w;
+  if (s < vr * box) {
+    dk = -vr + s / box;
+    const int t = s % box;
+    dy = t / w - r;
+    dx = t % w - r;
+    return;
+  }
+  s -= vr * box;
+  dk = 0;
+  if (s < r * w) {
+    dy = -r + s / w;
+    dx = s % w - r;
+    return;
+  }
+  s -= r * w;
+  dy = 0;
+  dx = (s < r) ? (-r + s) : (1 + (s - r));
+}
+
+__host__ __device__ inline int imod(int a, int m) {
+  int x = a % m;
+  return x < 0 ? x + m : x;
+}
+
+__host__ __device__ inline int var_of_label(const Geom& g, int64_t l) {
+  int v = 0;
+  while (v + 1 < g.nvar && l >= g.var_off[v + 1]) ++v;
+  return v;
+}
+
+__host__ __device__ inline void label_coords(const Geom& g, int64_t l, int& v, int& k, int& y,
+                                             int& x) {
+  v = var_of_label(g, l);
+  int64_t rem = l - g.var_off[v];
+  const int64_t plane = (int64_t)g.nlat * g.nlon;
+  k = (int)(rem / plane);
+  rem -= (int64_t)k * plane;
+  y = (int)(rem / g.nlon);
+  x = (int)(rem - (int64_t)y * g.nlon);
+}
+
+__host__ __device__ inline int64_t coords_label(const Geom& g, int v, int k, int y, int x) {
+  return g.var_off[v] + ((int64_t)k * g.nlat + y) * g.nlon + x;
+}
+
+// Is slot s of component (v, k, y, x) a predecessor?  On success returns the
+// neighbour's (k, y, x) with x on [0, nlon).
+__host__ __device__ inline bool slot_pred(const Geom& g, int k, int y, int x, int s, int& kq,
+                                          int& yq, int& xq) {
+  int dk, dy, dx;
+  slot_offset(s, g.r, g.vr, dk, dy, dx);
+  kq = k + dk;
+  if (kq < 0) return false;
+  yq = y + dy;
+  if (yq < 0 || yq >= g.nlat) return false;
+  xq = x + dx;
+  if (dk == 0 && dy == 0) {
+    if (dx < 0) return xq >= 0;  // left neighbour on the same row, no wrap
+    if (!g.periodic || xq < g.nlon) return false;
+    xq -= g.nlon;                 // right neighbour across the seam
+    return true;
+  }
+  if (xq < 0 || xq >= g.nlon) {
+    if (!g.periodic) return false;
+    xq = imod(xq, g.nlon);
+  }
+  return true;
+}
+
+// Local position of absolute (yq, xq) in a block's extended box.
+__host__ __device__ inline bool in_ext(const Block& b, int nlon, int yq, int xq, int& yy, int& xx) {
+  yy = yq - b.lat_lo;
+  if (yy < 0 || yy >= b.ey) return false;
+  xx = imod(xq - b.lon_lo, nlon);
+  return xx < b.ex;
+}
+
+__host__ __device__ inline bool in_interior(const Block& b, int y, int x) {
+  return y >= b.lat0 && y < b.lat1 && x >= b.lon0 && x < b.lon1;
+}
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace enkfmc
+
+struct enkfmc_handle {
+  enkfmc_problem prob;
+  enkfmc::Geom g;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  size_t esize = 8;  // bytes per floating-point element
+
+  int32_t nsubx = 0, nsuby = 0, nsub = 0, nblock = 0, hb_max = 0, nb_max = 0;
+  int64_t ext_rows = 0, halo_rows = 0, band_elems = 0;
+  std::vector<enkfmc::Block> blocks;
+
+  // device tables
+  enkfmc::Block* d_blocks = nullptr;
+  int32_t* d_halo = nullptr;     // halo rows: (block, local index) pairs
+  int32_t* d_obs_of = nullptr;   // [n]: observation index of a component or -1
+  int32_t* d_status = nullptr;   // [4]: first error code, pad, 64-bit info
+  int64_t m = -1;
+
+  // device workspace (element type by precision)
+  void* d_U = nullptr;     // anomalies, component-major [n][ldN]
+  void* d_Te = nullptr;    // boundary rows of T per block [ext_rows][pmax]
+  void* d_De = nullptr;    // their D [ext_rows]
+  void* d_band = nullptr;  // band of A, then of L
+  void* d_rhs = nullptr;   // per block [N][nb] right-hand sides / increments
+  const void* T_assembled = nullptr;  // global T/D used by the last assemble
+  const void* D_assembled = nullptr;
+  bool assembled = false;
+  int64_t workspace_bytes = 0;
+
+  // host-cycle staging (allocated on first enkfmc_cycle_host)
+  void *d_Xb = nullptr, *d_y = nullptr, *d_R = nullptr, *d_Z = nullptr, *d_Xa = nullptr;
+  void *d_T = nullptr, *d_D = nullptr;
+
+  // kernel timing (events bracket each launch while enabled)
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+
+  // algorithmic work per launch
+  double work_flops[ENKFMC_NKERNEL] = {};
+  double work_bytes[ENKFMC_NKERNEL] = {};
+};
+
+namespace enkfmc {
+
+// status codes written by kernels (first one wins)
+__device__ inline void record_error(int32_t* status, int code, int64_t info) {
+  if (atomicCAS(status, 0, code) == 0) {
+    *reinterpret_cast<long long*>(status + 2) = (long long)info;
+  }
+}
+
+// Kernel launchers (implemented per .cu file).  T is float or double.
+template <typename T>
+cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_regress(const Geom& g, const T* U, const int32_t* halo, int64_t nitems,
+                           const Block* blocks, T* Tout, T* Dout, double ridge_c,
+                           int32_t* status, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                            const T* Tg, const T* Dg, const T* Te, const T* De,
+                            const int32_t* obs_of, const T* R, T* band, int32_t* status,
+                            cudaStream_t s, int hb_max);
+
+template <typename T>
+cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band,
+                            int32_t* status, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                       const int32_t* obs_of, int64_t m, const T* Xb, const T* y, const T* R,
+                       const T* Z, T* rhs, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
+                             T* rhs, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
+                             int sub_lat, const T* Xb, const T* dX, T* Xa, cudaStream_t s);
+
+}  // namespace enkfmc

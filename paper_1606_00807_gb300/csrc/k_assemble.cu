@@ -1,0 +1,205 @@
+// Step (b) assembly and step (c) right-hand side / write-back.
+//
+// A_k = T_k^T D_k^-1 T_k + H_k^T R_k^-1 H_k (Eq. 8, Eq. 11) on every
+// (sub-domain, variable) block of the extended set.  Neighbours share the
+// variable, so A_k is block diagonal over variables.  In local order
+// loc = (k * ey + yy) * ex + xx a row of T and its predecessors span at most
+// hb positions, so A is banded with half-bandwidth hb and is stored as a
+// column-major lower band: band[c * (hb + 1) + d] = A[c + d][c].
+//
+// A[a][b] = sum_j T[j][a] T[j][b] / D[j]: the rows j that contain component c
+// are c itself and c - offset(s) for every stencil slot s.  One warp builds
+// column c: for each such row j (in slot order, so the sum order is fixed and
+// the result deterministic) its lanes add T[j][c] T[j][b] / D[j] for every
+// entry b >= c of the row into a shared column buffer.  Rows of the tile
+// interior read the global T; boundary rows read the re-estimated rows.
+#include "enkfmc_internal.h"
+
+namespace enkfmc {
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __restrict__ blocks,
+                                                  const T* __restrict__ Tg, const T* __restrict__ Dg,
+                                                  const T* __restrict__ Te, const T* __restrict__ De,
+                                                  const int32_t* __restrict__ obs_of,
+                                                  const T* __restrict__ R, T* __restrict__ band,
+                                                  int32_t* status, int hbp1_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  T* col = reinterpret_cast<T*>(smem) + (size_t)warp * hbp1_max;
+  const Block b = blocks[blockIdx.y];
+  const int c = blockIdx.x * wpc + warp;
+  if (c >= b.nb) return;
+  const int hb = b.hb, pmax = g.pmax, nlon = g.nlon;
+  for (int d = lane; d <= hb; d += 32) col[d] = T(0);
+  __syncwarp();
+  const int plane = b.ey * b.ex;
+  const int kc = c / plane;
+  const int yyc = (c - kc * plane) / b.ex;
+  const int xxc = c - kc * plane - yyc * b.ex;
+  const int yc = b.lat_lo + yyc;
+  const int xc = imod(b.lon_lo + xxc, nlon);
+  const int v = b.var;
+
+  for (int sj = -1; sj < pmax; ++sj) {
+    int kj = kc, yj = yc, xj = xc, yyj = yyc, xxj = xxc;
+    if (sj >= 0) {
+      int dk, dy, dx;
+      slot_offset(sj, g.r, g.vr, dk, dy, dx);
+      kj = kc - dk;
+      yj = yc - dy;
+      xj = xc - dx;
+      if (kj >= b.nlev_b || yj < 0 || yj >= g.nlat) continue;
+      if (xj < 0 || xj >= nlon) {
+        if (!g.periodic) continue;
+        xj = imod(xj, nlon);
+      }
+      if (!in_ext(b, nlon, yj, xj, yyj, xxj)) continue;
+    }
+    const int locj = (kj * b.ey + yyj) * b.ex + xxj;
+    const T* trow;
+    T Dj;
+    if (in_interior(b, yj, xj)) {
+      const int64_t lj = coords_label(g, v, kj, yj, xj);
+      trow = Tg + lj * pmax;
+      Dj = Dg[lj];
+    } else {
+      trow = Te + (b.row_off + locj) * pmax;
+      Dj = De[b.row_off + locj];
+    }
+    const T tjc = (sj < 0) ? T(1) : trow[sj];
+    if (tjc == T(0)) continue;
+    const T scale = tjc / Dj;
+    if (lane == 0) {
+      const int d = locj - c;
+      if (d >= 0) {
+        if (d <= hb) col[d] += scale;
+        else record_error(status, ENKFMC_EINVAL, (int64_t)blockIdx.y);
+      }
+    }
+    for (int s2 = lane; s2 < pmax; s2 += 32) {
+      const T tjb = trow[s2];
+      if (tjb == T(0)) continue;
+      int kq, yq, xq, yyq, xxq;
+      if (!slot_pred(g, kj, yj, xj, s2, kq, yq, xq) || !in_ext(b, nlon, yq, xq, yyq, xxq)) {
+        record_error(status, ENKFMC_EINVAL, (int64_t)blockIdx.y);
+        continue;
+      }
+      const int d = (kq * b.ey + yyq) * b.ex + xxq - c;
+      if (d >= 0) {
+        if (d <= hb) col[d] += scale * tjb;
+        else record_error(status, ENKFMC_EINVAL, (int64_t)blockIdx.y);
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    const int o = obs_of[coords_label(g, v, kc, yc, xc)];
+    if (o >= 0) col[0] += T(1) / R[o];
+  }
+  __syncwarp();
+  T* out = band + b.band_off + (int64_t)c * (hb + 1);
+  for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : T(0);
+}
+
+// rhs[blk][m][loc] = (y_o + sqrt(R_o) Z[m][o] - Xb[m][l]) / R_o when component
+// l = label(loc) is observed by o, else 0 (Eq. 11 right-hand side).
+template <typename T>
+__global__ void __launch_bounds__(128) k_rhs(const Geom g, const Block* __restrict__ blocks,
+                                             const int32_t* __restrict__ obs_of, int64_t mobs,
+                                             const T* __restrict__ Xb, const T* __restrict__ y,
+                                             const T* __restrict__ R, const T* __restrict__ Z,
+                                             T* __restrict__ rhs) {
+  const Block b = blocks[blockIdx.y];
+  const int loc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (loc >= b.nb) return;
+  const int plane = b.ey * b.ex;
+  const int k = loc / plane;
+  const int yy = (loc - k * plane) / b.ex;
+  const int xx = loc - k * plane - yy * b.ex;
+  const int64_t l = coords_label(g, b.var, k, b.lat_lo + yy, imod(b.lon_lo + xx, g.nlon));
+  const int o = obs_of[l];
+  T* out = rhs + b.row_off * g.N + loc;
+  if (o < 0) {
+    for (int m = 0; m < g.N; ++m) out[(int64_t)m * b.nb] = T(0);
+    return;
+  }
+  const T Ro = R[o], yo = y[o];
+  const T sq = sqrt(Ro), rinv = T(1) / Ro;
+  for (int m = 0; m < g.N; ++m) {
+    const T ys = fma(sq, Z[(int64_t)m * mobs + o], yo);
+    out[(int64_t)m * b.nb] = (ys - Xb[(int64_t)m * g.n + l]) * rinv;
+  }
+}
+
+// Xa[m][l] = Xb[m][l] + dX[blk][m][loc] for the sub-domain whose interior
+// holds l (Eq. 10; interiors are disjoint, so plain stores suffice).
+template <typename T>
+__global__ void __launch_bounds__(256) k_writeback(const Geom g, const Block* __restrict__ blocks,
+                                                   int nsubx, int sub_lon, int sub_lat,
+                                                   const T* __restrict__ Xb,
+                                                   const T* __restrict__ dX, T* __restrict__ Xa) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= g.n) return;
+  const int m = blockIdx.y;
+  int v, k, y, x;
+  label_coords(g, l, v, k, y, x);
+  const int sub = (y / sub_lat) * nsubx + x / sub_lon;
+  const Block& b = blocks[sub * g.nvar + v];
+  const int loc = (k * b.ey + (y - b.lat_lo)) * b.ex + imod(x - b.lon_lo, g.nlon);
+  const int64_t i = (int64_t)m * g.n + l;
+  Xa[i] = Xb[i] + dX[b.row_off * g.N + (int64_t)m * b.nb + loc];
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                            const T* Tg, const T* Dg, const T* Te, const T* De,
+                            const int32_t* obs_of, const T* R, T* band, int32_t* status,
+                            cudaStream_t s, int hb_max) {
+  const int wpc = 8;
+  const int hbp1 = hb_max + 1;
+  const size_t smem = sizeof(T) * (size_t)hbp1 * wpc;
+  cudaError_t e = cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
+  k_assemble<T><<<grid, 32 * wpc, smem, s>>>(g, blocks, Tg, Dg, Te, De, obs_of, R, band, status,
+                                             hbp1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                       const int32_t* obs_of, int64_t m, const T* Xb, const T* y, const T* R,
+                       const T* Z, T* rhs, cudaStream_t s) {
+  const dim3 grid((nb_max + 127) / 128, nblock);
+  k_rhs<T><<<grid, 128, 0, s>>>(g, blocks, obs_of, m, Xb, y, R, Z, rhs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
+                             int sub_lat, const T* Xb, const T* dX, T* Xa, cudaStream_t s) {
+  const dim3 grid((unsigned)((g.n + 255) / 256), g.N);
+  k_writeback<T><<<grid, 256, 0, s>>>(g, blocks, nsubx, sub_lon, sub_lat, Xb, dX, Xa);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                                  \
+  template cudaError_t launch_assemble<T>(const Geom&, const Block*, int, int, const T*,        \
+                                          const T*, const T*, const T*, const int32_t*,         \
+                                          const T*, T*, int32_t*, cudaStream_t, int);           \
+  template cudaError_t launch_rhs<T>(const Geom&, const Block*, int, int, const int32_t*,       \
+                                     int64_t, const T*, const T*, const T*, const T*, T*,       \
+                                     cudaStream_t);                                              \
+  template cudaError_t launch_writeback<T>(const Geom&, const Block*, int, int, int, const T*,  \
+                                           const T*, T*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace enkfmc

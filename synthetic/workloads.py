@@ -94,5 +94,11 @@ SMALL_RIDGE = Workload(
     r=3, N=24, sub_lon=12, sub_lat=12, sigma2=(2.0,), corr_len=3.0,
     obs="random", obs_frac=0.5, ridge_c=1e-3, seed=7200)
 
+# T63 statistics (N = 80, r = 2, no ridge) on a grid the oracle finishes in seconds.
+SMALL_T63 = Workload(
+    name="small_48x26x3x1+1_n80_r2", nlon=48, nlat=26, nlev=3, nvar_3d=1, nvar_2d=1,
+    r=2, N=80, sub_lon=12, sub_lat=12, sigma2=(25.0, 1e4), corr_len=4.0, rho_vert=0.5,
+    obs="random", obs_frac=0.5, r_frac=0.01, seed=7300)
+
 WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96,
-                                 SMALL_3D, SMALL_R1, SMALL_RIDGE)}
+                                 SMALL_3D, SMALL_R1, SMALL_RIDGE, SMALL_T63)}

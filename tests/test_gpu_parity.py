@@ -1,0 +1,166 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-by-element comparisons on seeded inputs: the sparsity pattern of T
+bit for bit, every T row and D entry, and the analysis ensemble, in FP64 and
+FP32, on grids that span several tiles with ragged edges, the longitude seam
+and the poles; at the T63 shape on sampled rows and sub-domains.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import WORKLOADS, make_inputs
+
+from _harness import TOL, compare_T_rows, gpu_pipeline, np_dtype, per_variable_err
+
+pytestmark = pytest.mark.gpu
+
+SMALL = ["small_48x26x3x1+1_n80_r2", "small_40x30x2x2+1_n24_r2", "tiny_32x16_n20_r2",
+         "small_36x24x2x1_n24_r3_ridge", "small_28x20x3x1_n16_r1"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_00807_gb300 import binding
+    binding.load()
+
+
+@pytest.mark.parametrize("name", SMALL + ["nonperiodic"])
+def test_T_pattern_bit_exact(name):
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS[SMALL[1]].with_(lon_periodic=False) if name == "nonperiodic" else WORKLOADS[name]
+    h = B.Handle.from_workload(w, precision=B.FP64)
+    rowptr, col = h.export_T_pattern()
+    ref_ptr, ref_col = O.t_pattern_csr(O.Grid.from_workload(w))
+    assert np.array_equal(rowptr, ref_ptr)
+    assert np.array_equal(col, ref_col)
+    h.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", SMALL)
+def test_estimate_and_analysis_parity(name, precision):
+    w = WORKLOADS[name]
+    if precision == 1 and name == "small_28x20x3x1_n16_r1":
+        # p/N near 1 without ridge: the sample Gram is too ill-conditioned
+        # for single precision (p/N > 0.5 is the FP64 regime)
+        pytest.skip("FP64-only regime")
+    inp = make_inputs(w, np_dtype(precision))
+    out = gpu_pipeline(w, inp, precision)
+    tol = TOL[precision]
+    # step (a): every row of T and D against the oracle
+    U = O.anomalies(inp.Xb.T)
+    g = O.Grid.from_workload(w)
+    rows = np.arange(g.n)
+    ref = O.estimate_rows(g, U, rows, w.ridge_c)
+    eT, eD = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
+    assert eT < tol, eT
+    assert eD < tol, eD
+    # steps (b)-(c): the analysis ensemble and its increment
+    Xa_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
+    Xb = inp.Xb.astype(np.float64)
+    lab = np.arange(w.n)
+    eX = per_variable_err(w, lab, out["Xa"].T, Xa_ref.T)
+    edX = per_variable_err(w, lab, (out["Xa"] - Xb).T, (Xa_ref - Xb).T)
+    assert eX < tol, eX
+    assert edX < 10 * tol, edX
+    out["handle"].close()
+
+
+def test_full_t63_sampled_fp32():
+    """T63 shape, N = 80, FP32, the configuration the benchmark times: sampled T
+    rows and D entries, and three sampled sub-domains of the analysis."""
+    w = WORKLOADS["t63_192x96x29_n80_r2"]
+    inp = make_inputs(w, np.float32)
+    out = gpu_pipeline(w, inp, 1)
+    g = O.Grid.from_workload(w)
+    U = O.anomalies(inp.Xb.T)
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([
+        rng.choice(g.n, 300, replace=False),
+        [0, w.nlon - 1, w.nlon, g.n - 1, g.offsets[4], g.offsets[4] + w.nlon - 1,
+         g.offsets[1] - 1, g.label(2, 3, 47, 191), g.label(3, 6, 95, 0)]]))
+    ref = O.estimate_rows(g, U, rows, w.ridge_c)
+    eT, eD = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
+    assert eT < TOL[1], eT
+    assert eD < TOL[1], eD
+    # sub-domains: pole + seam corner, an interior tile, the last tile
+    sds = O.subdomains(g, w.sub_lon, w.sub_lat)
+    pick = [0, 16 * 3 + 7, len(sds) - 1]
+    Ys = O.perturbed_observations(inp.y, inp.R, inp.Z.T)
+    Xa_ref = O.analysis(g, sds, inp.Xb.T.astype(np.float64), Ys, inp.R, inp.obs_idx, w.ridge_c,
+                        only=pick)
+    for i in pick:
+        lab = sds[i].interior
+        got = out["Xa"][:, lab].T
+        eX = per_variable_err(w, lab, got, Xa_ref[lab])
+        edX = per_variable_err(w, lab, got - inp.Xb[:, lab].T, Xa_ref[lab] - inp.Xb[:, lab].T)
+        assert eX < TOL[1], (i, eX)
+        assert edX < 10 * TOL[1], (i, edX)
+    out["handle"].close()
+
+
+def test_no_observations_leaves_ensemble_unchanged():
+    w = WORKLOADS["small_40x30x2x2+1_n24_r2"].with_(obs="none")
+    inp = make_inputs(w, np.float64)
+    out = gpu_pipeline(w, inp, 0)
+    assert np.array_equal(out["Xa"], inp.Xb)
+    out["handle"].close()
+
+
+def test_deterministic_and_host_cycle_matches():
+    import torch
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["small_48x26x3x1+1_n80_r2"]
+    inp = make_inputs(w, np.float32)
+    a = gpu_pipeline(w, inp, 1)
+    b = gpu_pipeline(w, inp, 1, handle=a["handle"])
+    assert np.array_equal(a["Xa"], b["Xa"]) and np.array_equal(a["T"], b["T"])
+    Xa = np.empty_like(inp.Xb)
+    a["handle"].cycle_host(inp.Xb, inp.y, inp.R, inp.Z, Xa)
+    assert np.array_equal(Xa.astype(np.float64), a["Xa"])
+    a["handle"].close()
+
+
+def test_invalid_arguments_rejected_synchronously():
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    with pytest.raises(B.EnkfmcError) as e:
+        B.Handle.from_workload(w.with_(nlon=4))            # nlon < 2r + 1
+    assert e.value.code == 1
+    with pytest.raises(B.EnkfmcError):
+        B.Handle.from_workload(w.with_(N=1))
+    h = B.Handle.from_workload(w, precision=B.FP64)
+    for bad in ([3, 2], [0, 0], [-1], [w.n]):
+        with pytest.raises(B.EnkfmcError) as e:
+            h.set_observations(np.array(bad, np.int32))
+        assert e.value.code == 1
+    import torch
+    X = torch.zeros((w.N, w.n), device="cuda", dtype=torch.float64)
+    with pytest.raises(B.EnkfmcError) as e:          # assemble before set_observations
+        h.assemble(X, X, X, X)
+    assert e.value.code == 9
+    h.close()
+
+
+def test_nonfinite_input_reports_status_not_trap():
+    import torch
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    inp = make_inputs(w, np.float64)
+    inp.Xb[3, 100] = np.nan
+    h = B.Handle.from_workload(w, precision=B.FP64, stream=torch.cuda.current_stream().cuda_stream)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    Xb = dev(inp.Xb)
+    T = torch.empty((w.n, h.info.pmax), device="cuda", dtype=torch.float64)
+    D = torch.empty(w.n, device="cuda", dtype=torch.float64)
+    h.estimate(Xb, T, D)
+    code, info = h.get_status()
+    assert code in (4, 5)
+    # the context stays usable: a clean run afterwards succeeds
+    h.estimate(dev(make_inputs(w, np.float64).Xb), T, D)
+    assert h.get_status()[0] == 0
+    h.close()
