@@ -79,13 +79,17 @@ T127_N96 = Workload(  # T127-shaped scale case
 # Parity cases small enough for the oracle: several tiles, a ragged tile
 # edge in both directions, the longitude seam, the poles, two variable kinds.
 SMALL_3D = Workload(
-    name="small_40x30x2x2+1_n24_r2", nlon=40, nlat=30, nlev=2, nvar_3d=2, nvar_2d=1,
-    r=2, N=24, sub_lon=12, sub_lat=12, sigma2=(4.0, 1e-2, 1e3),
+    name="small_40x30x2x2+1_n48_r2", nlon=40, nlat=30, nlev=2, nvar_3d=2, nvar_2d=1,
+    r=2, N=48, sub_lon=12, sub_lat=12, sigma2=(4.0, 1e-2, 1e3),
     corr_len=3.0, rho_vert=0.5, obs="random", obs_frac=0.5, r_frac=0.01, seed=7000)
 
+# Same grid with N = 24: p >= N - 1 on most rows (ridge), D spans nine orders of
+# magnitude and the sub-domain blocks reach condition numbers near 1e11.
+SMALL_ILL = SMALL_3D.with_(name="small_40x30x2x2+1_n24_r2_ill", N=24)
+
 SMALL_R1 = Workload(
-    name="small_28x20x3x1_n16_r1", nlon=28, nlat=20, nlev=3, nvar_3d=1, nvar_2d=0,
-    r=1, N=16, sub_lon=8, sub_lat=6, sigma2=(1.0,), corr_len=2.0,
+    name="small_28x20x3x1_n32_r1", nlon=28, nlat=20, nlev=3, nvar_3d=1, nvar_2d=0,
+    r=1, N=32, sub_lon=8, sub_lat=6, sigma2=(1.0,), corr_len=2.0,
     obs="random", obs_frac=0.3, seed=7100)
 
 # Ridge active: p >= N - 1 for most rows (r = 3 with N = 24).
@@ -101,4 +105,4 @@ SMALL_T63 = Workload(
     obs="random", obs_frac=0.5, r_frac=0.01, seed=7300)
 
 WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96,
-                                 SMALL_3D, SMALL_R1, SMALL_RIDGE, SMALL_T63)}
+                                 SMALL_3D, SMALL_ILL, SMALL_R1, SMALL_RIDGE, SMALL_T63)}

@@ -64,6 +64,27 @@ def slot_neighbours(w: Workload, dk, dy, dx, rows: np.ndarray):
     return out
 
 
+def max_block_condition(w: Workload, inp: Inputs) -> float:
+    """Largest 2-norm condition number over the (sub-domain, variable) blocks of
+    A = T^T D^-1 T + H^T R^-1 H, from the oracle in FP64."""
+    from synthetic import variable_of
+    g = O.Grid.from_workload(w)
+    sds = O.subdomains(g, w.sub_lon, w.sub_lat)
+    Xb = inp.Xb.T.astype(np.float64)
+    U = O.anomalies(Xb)
+    Ys = O.perturbed_observations(inp.y, inp.R, inp.Z.T)
+    worst = 0.0
+    for sd in sds:
+        A, _, _, _, _ = O.local_system(g, sd, U, Xb, Ys, inp.R, inp.obs_idx, w.ridge_c)
+        Ad = A.toarray()
+        var = variable_of(w, sd.ext)
+        for v in np.unique(var):
+            sel = np.where(var == v)[0]
+            ev = np.linalg.eigvalsh(Ad[np.ix_(sel, sel)])
+            worst = max(worst, ev[-1] / ev[0])
+    return worst
+
+
 def per_variable_err(w: Workload, labels: np.ndarray, got: np.ndarray, ref: np.ndarray):
     """max over variables of max|got - ref| / max|ref|, rows grouped by variable."""
     from synthetic import variable_of

@@ -111,7 +111,7 @@ def test_full_radius_matches_textbook_ldl():
 def test_rows_match_svd_least_squares():
     """Each T row is minus the least-squares coefficients of u_j on U_P (SVD route,
     not the normal equations) and D_j the residual sum of squares over N - 1."""
-    w = WORKLOADS["small_40x30x2x2+1_n24_r2"]
+    w = WORKLOADS["small_40x30x2x2+1_n48_r2"]
     g = O.Grid.from_workload(w)
     inp = make_inputs(w)
     U = O.anomalies(inp.Xb.T)
@@ -177,7 +177,7 @@ def _one_domain(w: Workload) -> Workload:
     return w.with_(sub_lon=w.nlon, sub_lat=w.nlat)
 
 
-@pytest.mark.parametrize("name,N", [("tiny_32x16_n20_r2", 20), ("small_28x20x3x1_n16_r1", 48)])
+@pytest.mark.parametrize("name,N", [("tiny_32x16_n20_r2", 20), ("small_28x20x3x1_n32_r1", 48)])
 def test_primal_equals_gain_and_dual_forms(name, N):
     """One sub-domain covering the grid: the primal increment (Eq. 11) equals the
     gain form x_a = x_b + B H^T (H B H^T + R)^-1 (y^s - H x_b) with B = T^-1 D T^-T
@@ -221,7 +221,7 @@ def test_subdomain_increment_equals_local_gain_form():
 
 
 def test_subdomain_tiling_and_halo():
-    w = WORKLOADS["small_40x30x2x2+1_n24_r2"]
+    w = WORKLOADS["small_40x30x2x2+1_n48_r2"]
     g = O.Grid.from_workload(w)
     sds = O.subdomains(g, w.sub_lon, w.sub_lat)
     # 40 = 12+12+12+4 and 30 = 12+12+6: a ragged tile in both directions
