@@ -178,6 +178,32 @@ enkfmc_status enkfmc_export_T_pattern(const enkfmc_handle* h, int64_t* rowptr, i
 enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_t capacity,
                                  int64_t* nb, int32_t* hb);
 
+/* Allocation-free estimate.  The paper has no counterpart: this entry point
+ * exists for callers that cannot let the library allocate device memory,
+ * for example a service that reserves its whole GPU memory budget up front,
+ * a host application whose own allocator owns the device, or a
+ * latency-critical loop that cannot afford cudaMalloc/cudaFree because they
+ * may synchronise the whole device.  It computes the same Tvals [n][pmax] and
+ * D [n] as enkfmc_estimate for the problem *p, from Xb [N][n], on
+ * `cuda_stream`, without a handle and without allocating anything: its only
+ * scratch is one fixed 16 MiB device array inside the library (present on
+ * every GPU that loads the library until the process exits).
+ *   - Limit: 256 + n * ldN * sizeof(element) bytes must fit in 16 MiB
+ *     (ldN = N rounded up to a multiple of 4); larger problems return
+ *     ENKFMC_EINVAL before any work is queued.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Every call reuses the same array and leaves its contents behind; the
+ *     status word is cleared at the start of each call.  Calls that overlap
+ *     on the GPU (different streams, or concurrent host threads) race on the
+ *     array: serialise them.
+ *   - Numerical failures are not reported through a status here: the rows
+ *     concerned get D = NaN and a zero T row.
+ * Pointers are device pointers owned by the caller.  Asynchronous. */
+enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const void* Xb, void* Tvals,
+                                      void* D, void* cuda_stream);
+
 /* Kernel kinds launched by the library (index into the profiling arrays). */
 enum {
   ENKFMC_K_ANOMALIES = 0,   /* Eq. 5 anomalies, transposed to component-major   */

@@ -57,6 +57,8 @@ SIGNATURES = {
     "enkfmc_profile_read": (c_int32, [_H, c_void_p, c_void_p]),
     "enkfmc_kernel_name": (c_char_p, [c_int32]),
     "enkfmc_work_per_launch": (c_int32, [_H, c_void_p, c_void_p]),
+    "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
+                                          c_void_p]),
 }
 NKERNEL = 8
 
