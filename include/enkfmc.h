@@ -65,10 +65,18 @@ typedef enum {
 
 typedef enum {
   ENKFMC_FP64 = 0,       /* every step in double precision                        */
-  ENKFMC_FP32 = 1        /* single precision; each regression takes one step of
-                            iterative refinement with an extended-precision
-                            residual (corrected semi-normal equations)            */
+  ENKFMC_FP32 = 1        /* single precision arithmetic with two refinement steps
+                            whose residuals are accumulated in compensated
+                            (double-float) arithmetic: one per regression
+                            (corrected semi-normal equations) and one per
+                            sub-domain solve (Eq. 11)                             */
 } enkfmc_precision;
+
+/* enkfmc_problem.flags */
+enum {
+  ENKFMC_FLAG_NO_SOLVE_REFINEMENT = 1  /* FP32: skip the sub-domain refinement step
+                                          (the plain single-precision solve)      */
+};
 
 /* Problem description.  Neighbours of a component share its variable, lie
  * within `vert_reach` levels and within Chebyshev distance r on the
@@ -88,6 +96,7 @@ typedef struct {
   int32_t sub_lon, sub_lat;
   int32_t precision;     /* enkfmc_precision                                      */
   double ridge_c;        /* lambda = ridge_c * tr(G) / p wherever p >= N - 1      */
+  int32_t flags;         /* ENKFMC_FLAG_* bits, 0 by default                      */
 } enkfmc_problem;
 
 /* Sizes of a created handle (host struct filled by enkfmc_query). */
@@ -138,7 +147,10 @@ enkfmc_status enkfmc_estimate(enkfmc_handle* h, const void* Xb, void* Tvals, voi
 /* Step (b), Algorithm 3 and Eq. 11: for every sub-domain re-estimate the
  * boundary rows of its extended set from the local samples (predecessors
  * cut to the extended set), assemble A = T^T D^-1 T + H^T R^-1 H in band
- * storage per (sub-domain, variable) block and factor it.  Xb: [N][n];
+ * storage per (sub-domain, variable) block and factor it.  Xb: [N][n]
+ * (when it is the same pointer as in the last enkfmc_estimate on this
+ * handle, the anomalies and covariances computed there are reused, so its
+ * contents must not change in between);
  * Tvals, D: as written by enkfmc_estimate; Rdiag: [m] observation-error
  * variances.  Requires enkfmc_set_observations. */
 enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tvals,
@@ -188,9 +200,10 @@ enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_
  * `cuda_stream`, without a handle and without allocating anything: its only
  * scratch is one fixed 16 MiB device array inside the library (present on
  * every GPU that loads the library until the process exits).
- *   - Limit: 256 + n * ldN * sizeof(element) bytes must fit in 16 MiB
- *     (ldN = N rounded up to a multiple of 4); larger problems return
- *     ENKFMC_EINVAL before any work is queued.
+ *   - Limit: 256 + n * (ldN + nC) * sizeof(element) bytes must fit in 16 MiB
+ *     (ldN = N rounded up to a multiple of 4; nC = ((2 vr + 1)(4r + 1)^2 + 1) / 2
+ *     pair covariances per component, vr = min(vert_reach, nlev - 1)); larger
+ *     problems return ENKFMC_EINVAL before any work is queued.
  *   - The first call on a device looks up the array's device address with
  *     that device current (cudaGetSymbolAddress); make that first call
  *     before any stream capture.
@@ -214,7 +227,9 @@ enum {
   ENKFMC_K_RHS = 5,         /* H^T R^-1 (Y^s - H X^b)                            */
   ENKFMC_K_BANDSOLVE = 6,   /* L L^T dX = rhs for the N members                  */
   ENKFMC_K_WRITEBACK = 7,   /* Eq. 10 on sub-domain interiors                    */
-  ENKFMC_NKERNEL = 8
+  ENKFMC_K_COVTABLE = 8,    /* covariances of every pair inside one local box    */
+  ENKFMC_K_RESIDUAL = 9,    /* rhs - A dX for the sub-domain refinement step     */
+  ENKFMC_NKERNEL = 10
 };
 
 /* Kernel timing.  While enabled, every kernel launch is bracketed by CUDA

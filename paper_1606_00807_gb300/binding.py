@@ -25,7 +25,8 @@ class enkfmc_problem(ctypes.Structure):
     _fields_ = [("nlon", c_int32), ("nlat", c_int32), ("nlev", c_int32), ("nvar_3d", c_int32),
                 ("nvar_2d", c_int32), ("lon_periodic", c_int32), ("r", c_int32),
                 ("vert_reach", c_int32), ("N", c_int32), ("sub_lon", c_int32),
-                ("sub_lat", c_int32), ("precision", c_int32), ("ridge_c", c_double)]
+                ("sub_lat", c_int32), ("precision", c_int32), ("ridge_c", c_double),
+                ("flags", c_int32)]
 
 
 class enkfmc_info(ctypes.Structure):
@@ -60,7 +61,8 @@ SIGNATURES = {
     "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
                                           c_void_p]),
 }
-NKERNEL = 8
+NKERNEL = 10
+FLAG_NO_SOLVE_REFINEMENT = 1
 
 _LIB = None
 
@@ -116,10 +118,12 @@ class Handle:
     """One problem on the current CUDA device; methods mirror the C entry points."""
 
     def __init__(self, *, nlon, nlat, nlev, nvar_3d, nvar_2d, r, N, sub_lon, sub_lat,
-                 precision=FP32, ridge_c=1e-3, vert_reach=1, lon_periodic=True, stream=None):
+                 precision=FP32, ridge_c=1e-3, vert_reach=1, lon_periodic=True, stream=None,
+                 flags=0):
         self.lib = load()
         self.problem = enkfmc_problem(nlon, nlat, nlev, nvar_3d, nvar_2d, int(bool(lon_periodic)),
-                                      r, vert_reach, N, sub_lon, sub_lat, precision, ridge_c)
+                                      r, vert_reach, N, sub_lon, sub_lat, precision, ridge_c,
+                                      flags)
         h = c_void_p()
         _check(self.lib.enkfmc_create(ctypes.byref(h), ctypes.byref(self.problem),
                                       c_void_p(stream)), "enkfmc_create")
@@ -128,11 +132,11 @@ class Handle:
         self.info = self.query()
 
     @classmethod
-    def from_workload(cls, w, precision=FP32, stream=None):
+    def from_workload(cls, w, precision=FP32, stream=None, flags=0):
         return cls(nlon=w.nlon, nlat=w.nlat, nlev=w.nlev, nvar_3d=w.nvar_3d, nvar_2d=w.nvar_2d,
                    r=w.r, N=w.N, sub_lon=w.sub_lon, sub_lat=w.sub_lat, precision=precision,
                    ridge_c=w.ridge_c, vert_reach=w.vert_reach, lon_periodic=w.lon_periodic,
-                   stream=stream)
+                   stream=stream, flags=flags)
 
     def close(self):
         if getattr(self, "h", None):

@@ -78,6 +78,7 @@ enkfmc_status build(enkfmc_handle* h) {
     return ENKFMC_EINVAL;
   if (p.precision != ENKFMC_FP64 && p.precision != ENKFMC_FP32) return ENKFMC_EINVAL;
   if (p.lon_periodic && p.nlon < 2 * p.r + 1) return ENKFMC_EINVAL;
+  if (p.flags & ~ENKFMC_FLAG_NO_SOLVE_REFINEMENT) return ENKFMC_EINVAL;
   Geom& g = h->g;
   std::memset(&g, 0, sizeof(g));
   g.nlon = p.nlon;
@@ -102,6 +103,7 @@ enkfmc_status build(enkfmc_handle* h) {
   g.n = off;
   if (g.n > ((int64_t)1 << 31) - 1) return ENKFMC_EINVAL;
   h->esize = is_fp64(h) ? sizeof(double) : sizeof(float);
+  h->refine_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_NO_SOLVE_REFINEMENT);
 
   // sub-domains and blocks (Section 3, Fig. 3)
   h->nsuby = (p.nlat + p.sub_lat - 1) / p.sub_lat;
@@ -201,6 +203,12 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_De, h->esize * h->ext_rows))) return st;
   if ((st = dalloc(h, &h->d_band, h->esize * h->band_elems))) return st;
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
+  if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
+  if (h->refine_solve) {
+    if ((st = dalloc(h, &h->d_res, h->esize * h->ext_rows * g.N))) return st;
+    if ((st = dalloc(h, &h->d_vhi, h->esize * h->ext_rows * g.N))) return st;
+    if ((st = dalloc(h, &h->d_vlo, h->esize * h->ext_rows * g.N))) return st;
+  }
   CUDA_TRY(cudaMemcpy(h->d_blocks, h->blocks.data(), sizeof(Block) * h->blocks.size(),
                       cudaMemcpyHostToDevice));
   if (!halo.empty())
@@ -211,8 +219,10 @@ enkfmc_status build(enkfmc_handle* h) {
 }
 
 void release(enkfmc_handle* h) {
-  void* bufs[] = {h->d_blocks, h->d_halo, h->d_status, h->d_obs_of, h->d_U, h->d_Te, h->d_De,
-                  h->d_band, h->d_rhs, h->d_Xb, h->d_y, h->d_R, h->d_Z, h->d_Xa, h->d_T, h->d_D};
+  void* bufs[] = {h->d_blocks, h->d_halo, h->d_status, h->d_obs_of, h->d_U,   h->d_C,
+                  h->d_Te,     h->d_De,   h->d_band,   h->d_rhs,    h->d_res, h->d_vhi,
+                  h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
+                  h->d_T,      h->d_D};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
@@ -255,21 +265,38 @@ enkfmc_status run_anomalies(enkfmc_handle* h, const T* Xb) {
                [&] { return launch_anomalies<T>(h->g, Xb, (T*)h->d_U, h->stream); });
 }
 
+// Anomalies and covariance table of Xb (skipped when already computed from it).
 template <typename T>
-enkfmc_status run_estimate(enkfmc_handle* h, const T* Xb, T* Tv, T* D) {
+enkfmc_status run_statistics(enkfmc_handle* h, const T* Xb) {
+  if (h->U_src == Xb) return ENKFMC_OK;
+  h->U_src = nullptr;
   enkfmc_status st = run_anomalies<T>(h, Xb);
   if (st) return st;
+  st = timed(h, ENKFMC_K_COVTABLE, [&] {
+    return launch_covtable<T>(h->g, (const T*)h->d_U, (T*)h->d_C, h->stream);
+  });
+  if (st) return st;
+  h->U_src = Xb;
+  return ENKFMC_OK;
+}
+
+template <typename T>
+enkfmc_status run_estimate(enkfmc_handle* h, const T* Xb, T* Tv, T* D) {
+  h->U_src = nullptr;  // a new estimate always recomputes the statistics
+  enkfmc_status st = run_statistics<T>(h, Xb);
+  if (st) return st;
   return timed(h, ENKFMC_K_REGRESS, [&] {
-    return launch_regress<T>(h->g, (const T*)h->d_U, nullptr, h->g.n, h->d_blocks, Tv, D,
-                             h->prob.ridge_c, h->d_status, h->stream);
+    return launch_regress<T>(h->g, (const T*)h->d_U, (const T*)h->d_C, nullptr, h->g.n,
+                             h->d_blocks, Tv, D, h->prob.ridge_c, h->d_status, h->stream);
   });
 }
 
 template <typename T>
 enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R) {
   enkfmc_status st = timed(h, ENKFMC_K_REGRESS_HALO, [&] {
-    return launch_regress<T>(h->g, (const T*)h->d_U, h->d_halo, h->halo_rows, h->d_blocks,
-                             (T*)h->d_Te, (T*)h->d_De, h->prob.ridge_c, h->d_status, h->stream);
+    return launch_regress<T>(h->g, (const T*)h->d_U, (const T*)h->d_C, h->d_halo, h->halo_rows,
+                             h->d_blocks, (T*)h->d_Te, (T*)h->d_De, h->prob.ridge_c,
+                             h->d_status, h->stream);
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_ASSEMBLE, [&] {
@@ -297,9 +324,27 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
                                (T*)h->d_rhs, h->stream);
   });
   if (st) return st;
+  const T* corr = nullptr;
+  if (h->refine_solve && sizeof(T) == sizeof(float)) {
+    st = timed(h, ENKFMC_K_RESIDUAL, [&] {
+      return launch_refine_residual(
+          h->g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m, (const float*)Xb,
+          (const float*)y, (const float*)R, (const float*)Z, (const float*)h->T_assembled,
+          (const float*)h->D_assembled, (const float*)h->d_Te, (const float*)h->d_De,
+          (const float*)h->d_rhs, (float*)h->d_vhi, (float*)h->d_vlo, (float*)h->d_res,
+          h->stream);
+    });
+    if (st) return st;
+    st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
+      return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, h->g.N,
+                                 (const T*)h->d_band, (T*)h->d_res, h->stream);
+    });
+    if (st) return st;
+    corr = (const T*)h->d_res;
+  }
   return timed(h, ENKFMC_K_WRITEBACK, [&] {
     return launch_writeback<T>(h->g, h->d_blocks, h->nsubx, h->prob.sub_lon, h->prob.sub_lat, Xb,
-                               (const T*)h->d_rhs, Xa, h->stream);
+                               (const T*)h->d_rhs, corr, Xa, h->stream);
   });
 }
 
@@ -312,9 +357,9 @@ void compute_work(enkfmc_handle* h, const std::vector<int>& p_global,
                   const std::vector<int>& p_ext) {
   const Geom& g = h->g;
   const double N = g.N, es = (double)h->esize;
-  auto reg = [&](double p) {
-    return 2.0 * N * ((p + 1) * (p + 2) / 2.0) + p * p * p / 3.0 + 2.0 * p * p + 2.0 * N * p;
-  };
+  // per row: Cholesky p^3/3, two triangular solves 2p^2, residual 2Np (the Gram
+  // entries come from the covariance table)
+  auto reg = [&](double p) { return p * p * p / 3.0 + 2.0 * p * p + 2.0 * N * p; };
   double f_glob = 0, f_halo = 0, f_asm = 0, t_read = 0;
   for (int p : p_global) f_glob += reg(p);
   for (size_t i = 0; i < p_ext.size(); ++i) {
@@ -348,6 +393,23 @@ void compute_work(enkfmc_handle* h, const std::vector<int>& p_global,
   h->work_bytes[ENKFMC_K_BANDSOLVE] = es * (2.0 * (double)h->band_elems + 4.0 * N * er);
   h->work_flops[ENKFMC_K_WRITEBACK] = N * n;
   h->work_bytes[ENKFMC_K_WRITEBACK] = es * 3.0 * N * n;
+  // covariance table: 2N flops per valid pair (both components inside the grid)
+  const int r = g.r, w4 = 4 * r + 1, nH = cov_offset_count(g.r, g.vr);
+  double pairs = 0;
+  for (int v = 0; v < g.nvar; ++v)
+    for (int k = 0; k < g.var_lev[v]; ++k)
+      for (int y = 0; y < g.nlat; ++y)
+        for (int dk = 0; dk <= g.vr; ++dk)
+          for (int dy = (dk == 0 ? 0 : -2 * r); dy <= 2 * r; ++dy) {
+            if (k + dk >= g.var_lev[v] || y + dy < 0 || y + dy >= g.nlat) continue;
+            const int ndx = (dk == 0 && dy == 0) ? 2 * r + 1 : w4;
+            pairs += (double)g.nlon * (g.periodic ? ndx : ndx);
+          }
+  h->work_flops[ENKFMC_K_COVTABLE] = 2.0 * N * pairs;
+  h->work_bytes[ENKFMC_K_COVTABLE] = es * (N * n + n * (double)nH);
+  // refinement residual: T dX, T^T v and the observation term, 2N flops per entry
+  h->work_flops[ENKFMC_K_RESIDUAL] = h->refine_solve ? 4.0 * N * (t_read - er) : 0.0;
+  h->work_bytes[ENKFMC_K_RESIDUAL] = h->refine_solve ? es * 2.0 * N * er : 0.0;
 }
 
 // Observation-dependent terms: rhs reads Xb, Z for every observed ext row.
@@ -479,16 +541,18 @@ enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tval
                               const void* Rdiag) {
   if (!h || !Xb || !Tvals || !D || (h->m > 0 && !Rdiag)) return ENKFMC_EINVAL;
   if (h->m < 0) return ENKFMC_ESTATE;
-  // anomalies of this Xb (the halo regressions use them)
+  // anomalies and covariances of this Xb (the boundary regressions use them)
   enkfmc_status st;
   if (is_fp64(h)) {
-    st = run_anomalies<double>(h, (const double*)Xb);
+    st = run_statistics<double>(h, (const double*)Xb);
     if (!st) st = run_assemble<double>(h, (const double*)Tvals, (const double*)D, (const double*)Rdiag);
   } else {
-    st = run_anomalies<float>(h, (const float*)Xb);
+    st = run_statistics<float>(h, (const float*)Xb);
     if (!st) st = run_assemble<float>(h, (const float*)Tvals, (const float*)D, (const float*)Rdiag);
   }
   h->assembled = (st == ENKFMC_OK);
+  h->T_assembled = Tvals;
+  h->D_assembled = D;
   return st;
 }
 
@@ -620,7 +684,8 @@ enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* launches, double* m
 const char* enkfmc_kernel_name(int32_t kind) {
   static const char* names[ENKFMC_NKERNEL] = {"anomalies", "regress",   "regress_halo",
                                               "assemble",  "bandchol",  "rhs",
-                                              "bandsolve", "writeback"};
+                                              "bandsolve", "writeback", "covtable",
+                                              "residual"};
   return (kind >= 0 && kind < ENKFMC_NKERNEL) ? names[kind] : "unknown";
 }
 

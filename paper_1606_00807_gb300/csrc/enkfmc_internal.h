@@ -161,10 +161,16 @@ struct enkfmc_handle {
 
   // device workspace (element type by precision)
   void* d_U = nullptr;     // anomalies, component-major [n][ldN]
+  void* d_C = nullptr;     // covariance table [n][cov_offset_count]
+  const void* U_src = nullptr;  // Xb the anomalies and table were computed from
   void* d_Te = nullptr;    // boundary rows of T per block [ext_rows][pmax]
   void* d_De = nullptr;    // their D [ext_rows]
   void* d_band = nullptr;  // band of A, then of L
   void* d_rhs = nullptr;   // per block [N][nb] right-hand sides / increments
+  void* d_res = nullptr;   // refinement: residual, then correction (FP32 path)
+  void* d_vhi = nullptr;   // refinement scratch: (T dX) / D as double-float
+  void* d_vlo = nullptr;
+  bool refine_solve = false;
   const void* T_assembled = nullptr;  // global T/D used by the last assemble
   const void* D_assembled = nullptr;
   bool assembled = false;
@@ -198,13 +204,28 @@ __device__ inline void record_error(int32_t* status, int code, int64_t info) {
   }
 }
 
+// Right-hand side entry of Eq. 11 for an observed component:
+// (y_o + sqrt(R_o) z - x^b) / R_o, written once so that every kernel that needs
+// it rounds it the same way.
+template <typename T>
+__device__ __forceinline__ T rhs_entry(T yo, T sq, T z, T xb, T rinv) {
+  return (fma(sq, z, yo) - xb) * rinv;
+}
+
 // Kernel launchers (implemented per .cu file).  T is float or double.
 template <typename T>
 cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s);
 
+// Offsets in the half box |dk| <= vr, |dlat|, |dlon| <= 2r with (dk, dlat, dlon) >= 0
+// lexicographically: the columns of the covariance table C[n][count].
+int cov_offset_count(int r, int vr);
+
 template <typename T>
-cudaError_t launch_regress(const Geom& g, const T* U, const int32_t* halo, int64_t nitems,
-                           const Block* blocks, T* Tout, T* Dout, double ridge_c,
+cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
+                           int64_t nitems, const Block* blocks, T* Tout, T* Dout, double ridge_c,
                            int32_t* status, cudaStream_t s);
 
 template <typename T>
@@ -226,8 +247,19 @@ template <typename T>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
                              T* rhs, cudaStream_t s);
 
+// Xa = Xb + dX (+ dX2 when not null) on sub-domain interiors.
 template <typename T>
 cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
-                             int sub_lat, const T* Xb, const T* dX, T* Xa, cudaStream_t s);
+                             int sub_lat, const T* Xb, const T* dX, const T* dX2, T* Xa,
+                             cudaStream_t s);
+
+// Single-precision refinement residual res = rhs - A dX (two passes; vhi, vlo
+// are scratch of the size of dX).
+cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                                   const int32_t* obs_of, int64_t m, const float* Xb,
+                                   const float* y, const float* R, const float* Z,
+                                   const float* Tg, const float* Dg, const float* Te,
+                                   const float* De, const float* dX, float* vhi, float* vlo,
+                                   float* res, cudaStream_t s);
 
 }  // namespace enkfmc

@@ -11,7 +11,8 @@
 // the library, for as long as the process lives.
 //
 // Scratch layout: [0, 256) a 16-byte status word (cleared at every call),
-// then the component-major anomalies U[n][ldN].
+// then the component-major anomalies U[n][ldN], then the covariance table
+// C[n][nC] (nC pair offsets per component).
 #include <cstring>
 #include <mutex>
 
@@ -87,13 +88,15 @@ enkfmc_status run(const Geom& g, double ridge_c, const T* Xb, T* Tv, T* D, unsig
                   cudaStream_t s) {
   int32_t* status = reinterpret_cast<int32_t*>(base);
   T* U = reinterpret_cast<T*>(base + kStatusBytes);
+  T* Cv = U + (size_t)g.n * g.ldN;
   if (cudaMemsetAsync(status, 0, 16, s) != cudaSuccess) {
     (void)cudaGetLastError();
     return ENKFMC_ECUDA;
   }
   cudaError_t e = launch_anomalies<T>(g, Xb, U, s);
+  if (e == cudaSuccess) e = launch_covtable<T>(g, U, Cv, s);
   if (e == cudaSuccess)
-    e = launch_regress<T>(g, U, nullptr, g.n, nullptr, Tv, D, ridge_c, status, s);
+    e = launch_regress<T>(g, U, Cv, nullptr, g.n, nullptr, Tv, D, ridge_c, status, s);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return ENKFMC_ECUDA;
@@ -110,7 +113,8 @@ extern "C" enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const 
   enkfmc_status st = noalloc_geom(*p, g);
   if (st) return st;
   const size_t esize = p->precision == ENKFMC_FP64 ? sizeof(double) : sizeof(float);
-  const size_t need = kStatusBytes + esize * (size_t)g.n * (size_t)g.ldN;
+  const size_t need =
+      kStatusBytes + esize * (size_t)g.n * ((size_t)g.ldN + (size_t)cov_offset_count(g.r, g.vr));
   if (need > kNoallocScratchBytes) return ENKFMC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {

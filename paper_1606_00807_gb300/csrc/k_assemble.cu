@@ -128,10 +128,9 @@ __global__ void __launch_bounds__(128) k_rhs(const Geom g, const Block* __restri
   }
   const T Ro = R[o], yo = y[o];
   const T sq = sqrt(Ro), rinv = T(1) / Ro;
-  for (int m = 0; m < g.N; ++m) {
-    const T ys = fma(sq, Z[(int64_t)m * mobs + o], yo);
-    out[(int64_t)m * b.nb] = (ys - Xb[(int64_t)m * g.n + l]) * rinv;
-  }
+  for (int m = 0; m < g.N; ++m)
+    out[(int64_t)m * b.nb] = rhs_entry(yo, sq, Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l],
+                                       rinv);
 }
 
 // Xa[m][l] = Xb[m][l] + dX[blk][m][loc] for the sub-domain whose interior
@@ -140,7 +139,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_writeback(const Geom g, const Block* __restrict__ blocks,
                                                    int nsubx, int sub_lon, int sub_lat,
                                                    const T* __restrict__ Xb,
-                                                   const T* __restrict__ dX, T* __restrict__ Xa) {
+                                                   const T* __restrict__ dX,
+                                                   const T* __restrict__ dX2, T* __restrict__ Xa) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= g.n) return;
   const int m = blockIdx.y;
@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(256) k_writeback(const Geom g, const Block* __
   const Block& b = blocks[sub * g.nvar + v];
   const int loc = (k * b.ey + (y - b.lat_lo)) * b.ex + imod(x - b.lon_lo, g.nlon);
   const int64_t i = (int64_t)m * g.n + l;
-  Xa[i] = Xb[i] + dX[b.row_off * g.N + (int64_t)m * b.nb + loc];
+  const int64_t e = b.row_off * g.N + (int64_t)m * b.nb + loc;
+  Xa[i] = dX2 ? Xb[i] + (dX[e] + dX2[e]) : Xb[i] + dX[e];
 }
 
 }  // namespace
@@ -183,9 +184,10 @@ cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_ma
 
 template <typename T>
 cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
-                             int sub_lat, const T* Xb, const T* dX, T* Xa, cudaStream_t s) {
+                             int sub_lat, const T* Xb, const T* dX, const T* dX2, T* Xa,
+                             cudaStream_t s) {
   const dim3 grid((unsigned)((g.n + 255) / 256), g.N);
-  k_writeback<T><<<grid, 256, 0, s>>>(g, blocks, nsubx, sub_lon, sub_lat, Xb, dX, Xa);
+  k_writeback<T><<<grid, 256, 0, s>>>(g, blocks, nsubx, sub_lon, sub_lat, Xb, dX, dX2, Xa);
   return cudaGetLastError();
 }
 
@@ -197,7 +199,7 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
                                      int64_t, const T*, const T*, const T*, const T*, T*,       \
                                      cudaStream_t);                                              \
   template cudaError_t launch_writeback<T>(const Geom&, const Block*, int, int, int, const T*,  \
-                                           const T*, T*, cudaStream_t);
+                                           const T*, const T*, T*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -3,19 +3,28 @@
 //
 // Layout.  The anomaly kernel turns the member-major ensemble X[m][l] into a
 // component-major array U[l][ldN] (ldN = N rounded up to 4, zero padded), so
-// that the N samples of one component are contiguous and a warp reads them
-// with one coalesced request.
+// that the N samples of one component are contiguous.
 //
-// Regression.  One warp per row j.  The predecessor list P_j (stencil slots
-// that are predecessors, optionally cut to a sub-domain's extended box) is
-// compacted with a ballot.  The augmented Gram matrix [U_P; u_j][U_P; u_j]^T
-// is accumulated in 4x4 register tiles over chunks of 32 members staged in
-// shared memory.  G + lambda I is factored by a warp Cholesky, beta solves
-// the normal equations and, in single precision, one step of iterative
-// refinement corrects beta with the residual e = u_j - U_P^T beta computed in
-// compensated (double-float) arithmetic: beta += (L L^T)^-1 U_P e
-// (corrected semi-normal equations, Bjorck 1987).  The final residual gives
-// D_j = |e|^2 / (N - 1).
+// Covariance table.  Every Gram entry a regression needs is the dot product
+// of two components of the same variable whose offset (dk, dlat, dlon) lies in
+// the box |dk| <= vr, |dlat|, |dlon| <= 2r (both lie in one local box).  The
+// table C[a][h] holds U_a . U_{a+delta_h} for the half of that box with
+// delta >= 0 in (dk, dlat, dlon) lexicographic order, so each pair is
+// computed once for the whole grid and shared by the global rows and the
+// boundary rows of every sub-domain (about 6x fewer flops than forming each
+// row's Gram matrix).  One block computes a line of W components against a
+// staged (lat, lon) window with 4x4 register tiles over (component, dlon).
+//
+// Rows.  One warp per row j: the predecessor list P_j (stencil slots that are
+// predecessors, optionally cut to a sub-domain's extended box) is compacted
+// with a ballot, the augmented Gram matrix [U_P; u_j][U_P; u_j]^T is gathered
+// from the table, factored by a left-looking (Crout) Cholesky whose last row
+// yields w = L^-1 g, and beta = L^-T w.  In single precision one step of
+// iterative refinement corrects beta with the residual e = u_j - U_P^T beta
+// computed in compensated (double-float: FMA two-product and two-sum)
+// arithmetic from U: beta += (L L^T)^-1 U_P e (corrected semi-normal
+// equations, Bjorck 1987); D_j = |e|^2 / (N - 1).  In double precision
+// D_j = (u.u - beta.g - lambda beta.beta) / (N - 1) from the Gram entries.
 #include <math.h>
 
 #include "enkfmc_internal.h"
@@ -23,9 +32,6 @@
 namespace enkfmc {
 
 namespace {
-
-constexpr int kChunk = 32;  // members staged per pass
-constexpr int kMCP = 33;    // padded chunk stride (odd: conflict-free stores)
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -77,109 +83,194 @@ __global__ void __launch_bounds__(256) k_anomalies(const T* __restrict__ X, T* _
 }
 
 // ---------------------------------------------------------------------------
-// Warp-level helpers on a dense lower-triangular matrix in shared memory.
+// Covariance table
 // ---------------------------------------------------------------------------
-// In-place Cholesky of G[0:p][0:p] (row stride ld).  Returns 0 on success,
-// otherwise ENKFMC_EDNONPOS / ENKFMC_ENONFINITE.  Warp-uniform.
-template <typename T>
-__device__ int warp_cholesky(T* G, int ld, int p, int lane) {
-  for (int k = 0; k < p; ++k) {
-    T d = G[k * ld + k];
-    if (!finite_val(d)) return ENKFMC_ENONFINITE;
-    if (!(d > T(0))) return ENKFMC_EDNONPOS;
-    d = sqrt(d);
-    __syncwarp();
-    if (lane == 0) G[k * ld + k] = d;
-    const T inv = T(1) / d;
-    for (int i = k + 1 + lane; i < p; i += 32) G[i * ld + k] *= inv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < p; i += 32) {
-      const T lik = G[i * ld + k];
-      T* gi = G + i * ld;
-      for (int l = k + 1; l <= i; ++l) gi[l] -= lik * G[l * ld + k];
+// Offset rows of the half box: rho -> (dk, dy, first dlon).  rho 0 is
+// (0, 0) with dlon in [0, 2r]; rho 1..2r are (0, dy) with dy = 1..2r; then
+// vr levels of (dk, dy), dy = -2r..2r, with dlon in [-2r, 2r].
+__device__ __forceinline__ void cov_row(int rho, int r, int& dk, int& dy, int& dxlo) {
+  if (rho <= 2 * r) {
+    dk = 0;
+    dy = rho;
+    dxlo = rho == 0 ? 0 : -2 * r;
+    return;
+  }
+  const int t = rho - (2 * r + 1);
+  const int w4 = 4 * r + 1;
+  dk = 1 + t / w4;
+  dy = t % w4 - 2 * r;
+  dxlo = -2 * r;
+}
+
+// Region row (staging) of an offset row: level k rows first (dy = 0..2r), then
+// the rows of the levels above (dy = -2r..2r).
+template <typename T, int MC>
+__global__ void __launch_bounds__(256) k_covtable(const Geom g, const T* __restrict__ U,
+                                                  T* __restrict__ C, int W, int nH, int nrho) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int MCP = MC + 4;
+  const int r = g.r, r2 = 2 * r, w4 = 4 * r + 1;
+  const int Wp = W + 4 * r;
+  const int R = nrho;  // region rows coincide with offset rows
+  T* S = reinterpret_cast<T*>(smem);        // [R][Wp][MCP]
+  T* Cs = S + (size_t)R * Wp * MCP;         // [W][nH]
+  // plane -> (variable, level)
+  int plane = blockIdx.z, v = 0;
+  while (plane >= g.var_lev[v]) {
+    plane -= g.var_lev[v];
+    ++v;
+  }
+  const int k = plane, y = blockIdx.y, x0 = blockIdx.x * W;
+  const int nlev_v = g.var_lev[v];
+  const int tid = threadIdx.x;
+  // tiles: (rho, dx tile, a tile)
+  const int atiles = W / 4;
+  const int dxt_full = (w4 + 3) / 4, dxt_half = (r2 + 1 + 3) / 4;
+  const int ntiles = (dxt_half + (nrho - 1) * dxt_full) * atiles;
+  for (int i = tid; i < W * nH; i += blockDim.x) Cs[i] = T(0);
+
+  for (int m0 = 0; m0 < g.N; m0 += MC) {
+    __syncthreads();
+    // stage the window for members [m0, m0 + MC)
+    const int nvec = R * Wp * MC;
+    for (int idx = tid; idx < nvec; idx += blockDim.x) {
+      const int mm = idx % MC;
+      const int cell = idx / MC;
+      const int chi = cell % Wp, rho = cell / Wp;
+      int dk, dy, dxlo;
+      cov_row(rho, r, dk, dy, dxlo);
+      const int kk = k + dk, yy = y + dy;
+      int xx = x0 - r2 + chi;
+      T val = T(0);
+      bool ok = kk < nlev_v && yy >= 0 && yy < g.nlat && (m0 + mm) < g.N;
+      if (ok) {
+        if (xx < 0 || xx >= g.nlon) {
+          if (g.periodic) xx = imod(xx, g.nlon);
+          else ok = false;
+        }
+      }
+      if (ok) val = U[coords_label(g, v, kk, yy, xx) * g.ldN + m0 + mm];
+      S[(size_t)cell * MCP + mm] = val;
     }
-    __syncwarp();
+    __syncthreads();
+    const int mcnt = min(MC, g.N - m0);
+    for (int tile = tid; tile < ntiles; tile += blockDim.x) {
+      const int at = tile % atiles;
+      int rest = tile / atiles;
+      int rho, dxt;
+      if (rest < dxt_half) {
+        rho = 0;
+        dxt = rest;
+      } else {
+        rest -= dxt_half;
+        rho = 1 + rest / dxt_full;
+        dxt = rest % dxt_full;
+      }
+      int dk, dy, dxlo;
+      cov_row(rho, r, dk, dy, dxlo);
+      const int dx0 = dxlo + 4 * dxt;
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      const T* Sa = S + ((size_t)0 * Wp + (r2 + 4 * at)) * MCP;           // a cells
+      const T* Sb = S + ((size_t)rho * Wp + (r2 + 4 * at + dx0)) * MCP;   // b cells
+      for (int mm = 0; mm < mcnt; ++mm) {
+        T av[4], bv[7];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) av[i] = Sa[i * MCP + mm];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+          const int chi = r2 + 4 * at + dx0 + q;
+          bv[q] = (chi >= 0 && chi < Wp) ? Sb[q * MCP + mm] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[i + j], acc[i][j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int dx = dx0 + j;
+        if (dx > r2) continue;
+        const int t = ((dk + g.vr) * w4 + (dy + r2)) * w4 + (dx + r2);
+        const int h = t - ((2 * g.vr + 1) * w4 * w4 - 1) / 2;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Cs[(4 * at + i) * nH + h] += acc[i][j];
+      }
+    }
   }
-  return 0;
-}
-
-// v <- (L L^T)^-1 v with L the Cholesky factor stored in G.
-template <typename T>
-__device__ void warp_chol_solve(const T* G, int ld, int p, T* v, int lane) {
-  for (int k = 0; k < p; ++k) {
-    const T wk = v[k] / G[k * ld + k];
-    __syncwarp();
-    if (lane == 0) v[k] = wk;
-    for (int i = k + 1 + lane; i < p; i += 32) v[i] -= G[i * ld + k] * wk;
-    __syncwarp();
+  __syncthreads();
+  for (int idx = tid; idx < W * nH; idx += blockDim.x) {
+    const int a = idx / nH, h = idx - a * nH;
+    const int x = x0 + a;
+    if (x < g.nlon) C[coords_label(g, v, k, y, x) * nH + h] = Cs[idx];
   }
-  for (int k = p - 1; k >= 0; --k) {
-    const T bk = v[k] / G[k * ld + k];
-    __syncwarp();
-    if (lane == 0) v[k] = bk;
-    for (int i = lane; i < k; i += 32) v[i] -= G[k * ld + i] * bk;
-    __syncwarp();
-  }
-}
-
-// Stage members [m0, m0 + 32) of rows qrow[0..nrow) into Us[i][mm].
-template <typename T>
-__device__ __forceinline__ void stage_chunk(const T* __restrict__ U, const int64_t* qrow, int nrow,
-                                            int nrow_pad, int m0, int N, T* Us, int lane) {
-  const bool live = (m0 + lane) < N;
-  for (int i = 0; i < nrow_pad; ++i) {
-    T v = 0;
-    if (i < nrow && live) v = U[qrow[i] + m0 + lane];
-    Us[i * kMCP + lane] = v;
-  }
-  __syncwarp();
-}
-
-// e = u - sum_i U_i beta_i for the warp's member, compensated for float.
-__device__ __forceinline__ float residual_member(const float* Us, int p, const float* beta,
-                                                 int lane) {
-  float s = Us[p * kMCP + lane], c = 0.f;
-  for (int i = 0; i < p; ++i) {
-    const float a = Us[i * kMCP + lane];
-    const float prod = a * beta[i];
-    const float perr = fmaf(a, beta[i], -prod);
-    const float t = s - prod;
-    const float z = t - s;
-    const float e = (s - (t - z)) + (-prod - z);
-    s = t;
-    c += e - perr;
-  }
-  return s + c;
-}
-__device__ __forceinline__ double residual_member(const double* Us, int p, const double* beta,
-                                                  int lane) {
-  double e = Us[p * kMCP + lane];
-  for (int i = 0; i < p; ++i) e -= Us[i * kMCP + lane] * beta[i];
-  return e;
 }
 
 // ---------------------------------------------------------------------------
-// Regression kernel
+// Row regressions
 // ---------------------------------------------------------------------------
+// Table entry for the pair (a, b) at geometric offset (dk, dy, dx) = b - a.
+template <typename T>
+__device__ __forceinline__ T cov_lookup(const T* __restrict__ C, int nH, int r, int vr, int a,
+                                        int b, int dk, int dy, int dx) {
+  const int w4 = 4 * r + 1;
+  const int B = (2 * vr + 1) * w4 * w4;
+  const int t0 = (B - 1) / 2;
+  const int t = ((dk + vr) * w4 + (dy + 2 * r)) * w4 + (dx + 2 * r);
+  if (t >= t0) return C[(int64_t)a * nH + (t - t0)];
+  return C[(int64_t)b * nH + (B - 1 - t - t0)];
+}
+
+// compensated a - sum_i x_i beta_i for one member (float): exact products by FMA,
+// running sum by two-sum, error terms accumulated separately.
+__device__ __forceinline__ void ff_sub_prod(float& s, float& c, float x, float b) {
+  const float prod = x * b;
+  const float perr = fmaf(x, b, -prod);
+  const float t = s - prod;
+  const float z = t - s;
+  const float e = (s - (t - z)) + (-prod - z);
+  s = t;
+  c += e - perr;
+}
+
+constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restrict__ U,
+                                                 const T* __restrict__ C, int nH,
                                                  const int32_t* __restrict__ halo, int64_t nitems,
                                                  const Block* __restrict__ blocks,
                                                  T* __restrict__ Tout, T* __restrict__ Dout,
-                                                 double ridge_c, int32_t* status, int ldp,
+                                                 double ridge_c, int32_t* status, int ldp, int ldg,
                                                  int warp_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  unsigned char* base = smem + (size_t)warp * warp_bytes;
-  int64_t* qrow = reinterpret_cast<int64_t*>(base);  // [ldp]
-  int* sidx = reinterpret_cast<int*>(qrow + ldp);      // [ldp]
-  T* Us = reinterpret_cast<T*>(sidx + ldp);            // [ldp][kMCP]
-  T* G = Us + ldp * kMCP;                              // [ldp][ldp]
-  T* va = G + ldp * ldp;                               // [ldp]
-  T* vb = va + ldp;                                    // [ldp]
-  T* es = vb + ldp;                                    // [kMCP]
-  const int N = g.N, pmax = g.pmax;
-  const bool refine = sizeof(T) == 4;
+  // per-block slot offsets
+  signed char* off = reinterpret_cast<signed char*>(smem);  // [3][pmax], padded to 16
+  const int pmax = g.pmax;
+  const int offbytes = (3 * pmax + 15) / 16 * 16;
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
+    int dk, dy, dx;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    off[s] = (signed char)dk;
+    off[pmax + s] = (signed char)dy;
+    off[2 * pmax + s] = (signed char)dx;
+  }
+  __syncthreads();
+  unsigned char* base = smem + offbytes + (size_t)warp * warp_bytes;
+  int* q = reinterpret_cast<int*>(base);   // [ldp] component labels (q[p] = j)
+  int* sl = q + ldp;                        // [ldp] slot of compacted entry (-1 = j)
+  int* sidx = sl + ldp;                     // [ldp] compacted index of slot s
+  T* L = reinterpret_cast<T*>(sidx + ldp);  // [ldp][ldg]
+  T* va = L + (size_t)ldp * ldg;            // [ldp]
+  T* vb = va + ldp;                         // [ldp]
+  T* gv = vb + ldp;                         // [ldp]
+  T* invd = gv + ldp;                       // [ldp]
+  const int N = g.N;
+  const bool fp32 = sizeof(T) == 4;
 
   for (int64_t item = (int64_t)blockIdx.x * wpc + warp; item < nitems;
        item += (int64_t)gridDim.x * wpc) {
@@ -206,7 +297,7 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
     for (int s0 = 0; s0 < pmax; s0 += 32) {
       const int s = s0 + lane;
       bool pres = false;
-      int64_t q = 0;
+      int qq = 0;
       if (s < pmax) {
         int kq, yq, xq;
         pres = slot_pred(g, k, y, x, s, kq, yq, xq);
@@ -214,114 +305,191 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
           int yy, xx;
           pres = in_ext(*b, g.nlon, yq, xq, yy, xx);
         }
-        if (pres) q = coords_label(g, v, kq, yq, xq);
+        if (pres) qq = (int)coords_label(g, v, kq, yq, xq);
       }
       const unsigned mask = __ballot_sync(0xffffffffu, pres);
       const int idx = p + __popc(mask & ((1u << lane) - 1u));
       if (s < pmax) sidx[s] = pres ? idx : -1;
-      if (pres) qrow[idx] = q * g.ldN;
+      if (pres) {
+        q[idx] = qq;
+        sl[idx] = s;
+      }
       p += __popc(mask);
     }
-    if (lane == 0) qrow[p] = coords_label(g, v, k, y, x) * g.ldN;
+    const int jlab = (int)coords_label(g, v, k, y, x);
+    if (lane == 0) {
+      q[p] = jlab;
+      sl[p] = -1;
+    }
     __syncwarp();
     const int p1 = p + 1;
-    const int P4 = (p1 + 3) >> 2;
-    int err = 0;
 
-    if (p > 0) {
-      // augmented Gram [U_P; u_j][U_P; u_j]^T, lower 4x4 tiles
-      const int ntile = P4 * (P4 + 1) / 2;
-      for (int m0 = 0; m0 < N; m0 += kChunk) {
-        stage_chunk(U, qrow, p1, P4 * 4, m0, N, Us, lane);
-        const int mmax = min(kChunk, N - m0);
-        for (int bi = lane; bi < ntile; bi += 32) {
-          int I = (int)((sqrtf(8.f * bi + 1.f) - 1.f) * 0.5f);
-          while ((I + 1) * (I + 2) / 2 <= bi) ++I;
-          while (I * (I + 1) / 2 > bi) --I;
-          const int J = bi - I * (I + 1) / 2;
-          T acc[4][4];
+    // gather the augmented Gram matrix, lower triangle, rows 0..p
+    const int npair = p1 * (p1 + 1) / 2;
+    for (int pi = lane; pi < npair; pi += 32) {
+      int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= pi) ++i;
+      while (i * (i + 1) / 2 > pi) --i;
+      const int l = pi - i * (i + 1) / 2;
+      const int si = sl[i], sm = sl[l];
+      const int dk = (sm >= 0 ? off[sm] : 0) - (si >= 0 ? off[si] : 0);
+      const int dy = (sm >= 0 ? off[pmax + sm] : 0) - (si >= 0 ? off[pmax + si] : 0);
+      const int dx = (sm >= 0 ? off[2 * pmax + sm] : 0) - (si >= 0 ? off[2 * pmax + si] : 0);
+      L[i * ldg + l] = cov_lookup(C, nH, g.r, g.vr, q[i], q[l], dk, dy, dx);
+    }
+    __syncwarp();
+    T lam = T(0);
+    if (p > 0 && ridge_c > 0.0 && p >= N - 1) {
+      T tr = 0;
+      for (int i = lane; i < p; i += 32) tr += L[i * ldg + i];
+      tr = warp_sum(tr);
+      lam = T(ridge_c) * tr / T(p);
+    }
+    for (int i = lane; i < p; i += 32) {
+      gv[i] = L[p * ldg + i];
+      L[i * ldg + i] += lam;
+    }
+    const T uu = L[p * ldg + p];
+    __syncwarp();
+
+    // left-looking Cholesky of rows 0..p-1; row p becomes w = L^-1 g
+    int err = 0;
+    for (int kc = 0; kc < p; ++kc) {
+      const T* Lk = L + kc * ldg;
+      T vals[kMaxRounds * 2];
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][c] = (m0 == 0) ? T(0) : G[(4 * I + a) * ldp + 4 * J + c];
-          const T* ra = Us + (4 * I) * kMCP;
-          const T* rb = Us + (4 * J) * kMCP;
-          for (int mm = 0; mm < mmax; ++mm) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) av[a] = ra[a * kMCP + mm];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) bv[c] = rb[c * kMCP + mm];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-              for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
-          }
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) G[(4 * I + a) * ldp + 4 * J + c] = acc[a][c];
+      for (int t = 0; t < kMaxRounds * 2; ++t) {
+        const int i = lane + 32 * t;
+        vals[t] = T(0);
+        if (i >= kc && i <= p) {
+          const T* Li = L + i * ldg;
+          T dot = T(0);
+          for (int l = 0; l < kc; ++l) dot = fma(Li[l], Lk[l], dot);
+          vals[t] = Li[kc] - dot;
         }
-        __syncwarp();
       }
-      // ridge where p >= N - 1
-      if (ridge_c > 0.0 && p >= N - 1) {
-        T tr = 0;
-        for (int i = lane; i < p; i += 32) tr += G[i * ldp + i];
-        tr = warp_sum(tr);
-        const T lam = T(ridge_c) * tr / T(p);
-        __syncwarp();
-        for (int i = lane; i < p; i += 32) G[i * ldp + i] += lam;
-        __syncwarp();
-      }
-      // g = row p of the augmented Gram
-      for (int i = lane; i < p; i += 32) va[i] = G[p * ldp + i];
       __syncwarp();
-      err = warp_cholesky(G, ldp, p, lane);
-      if (!err) {
-        warp_chol_solve(G, ldp, p, va, lane);
-        if (refine) {
-          for (int i = lane; i < p; i += 32) vb[i] = 0;
-          __syncwarp();
-          for (int m0 = 0; m0 < N; m0 += kChunk) {
-            stage_chunk(U, qrow, p1, p1, m0, N, Us, lane);
-            es[lane] = (m0 + lane < N) ? residual_member(Us, p, va, lane) : T(0);
-            __syncwarp();
-            const int mmax = min(kChunk, N - m0);
-            for (int i = lane; i < p; i += 32) {
-              T a = vb[i];
-              for (int mm = 0; mm < mmax; ++mm) a = fma(Us[i * kMCP + mm], es[mm], a);
-              vb[i] = a;
-            }
-            __syncwarp();
-          }
-          warp_chol_solve(G, ldp, p, vb, lane);
-          for (int i = lane; i < p; i += 32) va[i] += vb[i];
-          __syncwarp();
-        }
+      if (lane == (kc & 31)) {
+        T d = vals[0];
+#pragma unroll
+        for (int t = 1; t < kMaxRounds * 2; ++t)
+          if (t == (kc >> 5)) d = vals[t];
+        const bool fin = finite_val(d);
+        const T sd = (fin && d > T(0)) ? sqrt(d) : T(0);
+        // 1/sqrt(d) on success; 0 for a non-positive pivot; NaN for a non-finite one
+        invd[kc] = sd > T(0) ? T(1) / sd : (fin ? T(0) : T(NAN));
+        L[kc * ldg + kc] = sd;
       }
+      __syncwarp();
+      const T inv = invd[kc];
+      if (!(inv > T(0))) {
+        err = (inv == inv) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+        break;
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxRounds * 2; ++t) {
+        const int i = lane + 32 * t;
+        if (i > kc && i <= p) L[i * ldg + kc] = vals[t] * inv;
+      }
+      __syncwarp();
     }
-    // residual variance
-    T ssq = 0;
+
+    T Dj = T(0);
     if (!err) {
-      for (int m0 = 0; m0 < N; m0 += kChunk) {
-        stage_chunk(U, qrow, p1, p1, m0, N, Us, lane);
-        if (m0 + lane < N) {
-          const T e = residual_member(Us, p, va, lane);
-          ssq = fma(e, e, ssq);
-        }
+      // beta = L^-T w  (w = row p of L), result in vb
+      for (int i = lane; i < p; i += 32) va[i] = L[p * ldg + i];
+      __syncwarp();
+      for (int kc = p - 1; kc >= 0; --kc) {
+        const T bk = va[kc] * invd[kc];
+        __syncwarp();
+        if (lane == 0) vb[kc] = bk;
+        for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * bk;
         __syncwarp();
       }
-      ssq = warp_sum(ssq);
+      if (fp32) {
+        // residual e = u - U_P^T beta (compensated), members m = lane + 32 t
+        float e[kMaxRounds], ec[kMaxRounds];
+#pragma unroll
+        for (int t = 0; t < kMaxRounds; ++t) {
+          const int m = lane + 32 * t;
+          e[t] = (m < N) ? (float)U[(int64_t)jlab * g.ldN + m] : 0.f;
+          ec[t] = 0.f;
+        }
+        for (int i = 0; i < p; ++i) {
+          const float bi = (float)vb[i];
+          const T* Ui = U + (int64_t)q[i] * g.ldN;
+#pragma unroll
+          for (int t = 0; t < kMaxRounds; ++t) {
+            const int m = lane + 32 * t;
+            if (m < N) ff_sub_prod(e[t], ec[t], (float)Ui[m], bi);
+          }
+        }
+#pragma unroll
+        for (int t = 0; t < kMaxRounds; ++t) e[t] += ec[t];
+        // c = U_P e - lambda beta, the residual of (G + lambda I) beta = g -> va
+        for (int i = 0; i < p; ++i) {
+          const T* Ui = U + (int64_t)q[i] * g.ldN;
+          float part = 0.f;
+#pragma unroll
+          for (int t = 0; t < kMaxRounds; ++t) {
+            const int m = lane + 32 * t;
+            if (m < N) part = fmaf((float)Ui[m], e[t], part);
+          }
+          part = warp_sum(part);
+          if (lane == (i & 31)) va[i] = (T)(part - (float)lam * (float)vb[i]);
+        }
+        __syncwarp();
+        // solve L z = c (forward), then L^T delta = z (backward), delta in gv? use va/gv
+        for (int kc = 0; kc < p; ++kc) {
+          const T zk = va[kc] * invd[kc];
+          __syncwarp();
+          if (lane == 0) va[kc] = zk;
+          for (int i = kc + 1 + lane; i < p; i += 32) va[i] -= L[i * ldg + kc] * zk;
+          __syncwarp();
+        }
+        for (int kc = p - 1; kc >= 0; --kc) {
+          const T dk = va[kc] * invd[kc];
+          __syncwarp();
+          if (lane == 0) va[kc] = dk;
+          for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * dk;
+          __syncwarp();
+        }
+        // beta += delta; e -= U_P^T delta; D = |e|^2 / (N - 1)
+        for (int i = lane; i < p; i += 32) vb[i] += va[i];
+        for (int i = 0; i < p; ++i) {
+          const float di = (float)va[i];
+          const T* Ui = U + (int64_t)q[i] * g.ldN;
+#pragma unroll
+          for (int t = 0; t < kMaxRounds; ++t) {
+            const int m = lane + 32 * t;
+            if (m < N) e[t] = fmaf(-(float)Ui[m], di, e[t]);
+          }
+        }
+        float ssq = 0.f;
+#pragma unroll
+        for (int t = 0; t < kMaxRounds; ++t) ssq = fmaf(e[t], e[t], ssq);
+        ssq = warp_sum(ssq);
+        Dj = (T)(ssq / (float)(N - 1));
+        __syncwarp();
+      } else {
+        // |e|^2 = u.u - beta.g - lambda beta.beta
+        T s1 = 0, s2 = 0;
+        for (int i = lane; i < p; i += 32) {
+          s1 = fma(vb[i], gv[i], s1);
+          s2 = fma(vb[i], vb[i], s2);
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        Dj = (uu - s1 - lam * s2) / T(N - 1);
+      }
+      if (!finite_val(Dj)) err = ENKFMC_ENONFINITE;
+      else if (!(Dj > T(0))) err = ENKFMC_EDNONPOS;
     }
-    T Dj = ssq / T(N - 1);
-    if (!err && !finite_val(Dj)) err = ENKFMC_ENONFINITE;
-    if (!err && !(Dj > T(0))) err = ENKFMC_EDNONPOS;
     if (err && lane == 0) record_error(status, err, orow);
     T* trow = Tout + orow * pmax;
     for (int s = lane; s < pmax; s += 32) {
       const int i = sidx[s];
-      trow[s] = (i >= 0 && !err) ? -va[i] : T(0);
+      trow[s] = (i >= 0 && !err) ? -vb[i] : T(0);
     }
     if (lane == 0) Dout[orow] = err ? T(NAN) : Dj;
     __syncwarp();
@@ -329,6 +497,11 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
 }
 
 }  // namespace
+
+int cov_offset_count(int r, int vr) {
+  const int w4 = 4 * r + 1;
+  return ((2 * vr + 1) * w4 * w4 + 1) / 2;
+}
 
 template <typename T>
 cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s) {
@@ -339,35 +512,67 @@ cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_regress(const Geom& g, const T* U, const int32_t* halo, int64_t nitems,
-                           const Block* blocks, T* Tout, T* Dout, double ridge_c,
+cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
+  constexpr int MC = sizeof(T) == 4 ? 16 : 8;
+  const int r = g.r;
+  const int nH = cov_offset_count(r, g.vr);
+  const int nrho = 1 + 2 * r + g.vr * (4 * r + 1);
+  int W = r <= 2 ? 64 : 32;
+  size_t smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 4) + (size_t)W * nH);
+  while (smem > 200 * 1024 && W > 8) {
+    W /= 2;
+    smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 4) + (size_t)W * nH);
+  }
+  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_covtable<T, MC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int planes = 0;
+  for (int v = 0; v < g.nvar; ++v) planes += g.var_lev[v];
+  const dim3 grid((g.nlon + W - 1) / W, g.nlat, planes);
+  k_covtable<T, MC><<<grid, 256, smem, s>>>(g, U, C, W, nH, nrho);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
+                           int64_t nitems, const Block* blocks, T* Tout, T* Dout, double ridge_c,
                            int32_t* status, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
+  if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
+    return cudaErrorInvalidConfiguration;
+  const int nH = cov_offset_count(g.r, g.vr);
   const int ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  size_t wb = (size_t)ldp * (sizeof(int64_t) + sizeof(int)) +
-              sizeof(T) * ((size_t)ldp * kMCP + (size_t)ldp * ldp + 2 * (size_t)ldp + kMCP);
+  const int ldg = ldp | 1;
+  size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 4 * (size_t)ldp);
   wb = (wb + 15) / 16 * 16;
-  int wpc = (int)(200 * 1024 / wb);
+  const int offbytes = (3 * g.pmax + 15) / 16 * 16;
+  int wpc = (int)((96 * 1024 - offbytes) / wb);
   if (wpc > 8) wpc = 8;
-  if (wpc < 1) return cudaErrorInvalidConfiguration;
-  const size_t smem = wb * wpc;
+  if (wpc < 1) {
+    wpc = (int)((200 * 1024 - offbytes) / wb);
+    if (wpc < 1) return cudaErrorInvalidConfiguration;
+    if (wpc > 8) wpc = 8;
+  }
+  const size_t smem = offbytes + wb * wpc;
   cudaError_t e = cudaFuncSetAttribute(k_regress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int64_t grid = (nitems + wpc - 1) / wpc;
-  if (grid > 152 * 64) grid = 152 * 64;
-  k_regress<T><<<(unsigned)grid, 32 * wpc, smem, s>>>(g, U, halo, nitems, blocks, Tout, Dout,
-                                                      ridge_c, status, ldp, (int)wb);
+  if (grid > 152 * 32) grid = 152 * 32;
+  k_regress<T><<<(unsigned)grid, 32 * wpc, smem, s>>>(g, U, C, nH, halo, nitems, blocks, Tout,
+                                                      Dout, ridge_c, status, ldp, ldg, (int)wb);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_anomalies<float>(const Geom&, const float*, float*, cudaStream_t);
-template cudaError_t launch_anomalies<double>(const Geom&, const double*, double*, cudaStream_t);
-template cudaError_t launch_regress<float>(const Geom&, const float*, const int32_t*, int64_t,
-                                           const Block*, float*, float*, double, int32_t*,
-                                           cudaStream_t);
-template cudaError_t launch_regress<double>(const Geom&, const double*, const int32_t*, int64_t,
-                                            const Block*, double*, double*, double, int32_t*,
-                                            cudaStream_t);
+#define INST(T)                                                                                  \
+  template cudaError_t launch_anomalies<T>(const Geom&, const T*, T*, cudaStream_t);            \
+  template cudaError_t launch_covtable<T>(const Geom&, const T*, T*, cudaStream_t);             \
+  template cudaError_t launch_regress<T>(const Geom&, const T*, const T*, const int32_t*,       \
+                                         int64_t, const Block*, T*, T*, double, int32_t*,       \
+                                         cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
 
 }  // namespace enkfmc

@@ -45,10 +45,10 @@ def test_T_pattern_bit_exact(name):
     h.close()
 
 
-def _parity(name, precision, tol_x=None):
+def _parity(name, precision, tol_x=None, flags=0):
     w = WORKLOADS[name]
     inp = make_inputs(w, np_dtype(precision))
-    out = gpu_pipeline(w, inp, precision)
+    out = gpu_pipeline(w, inp, precision, flags=flags)
     tol = TOL[precision]
     tol_x = tol if tol_x is None else tol_x
     # step (a): every row of T and D against the oracle
@@ -74,6 +74,12 @@ def _parity(name, precision, tol_x=None):
 @pytest.mark.parametrize("name", SMALL)
 def test_estimate_and_analysis_parity(name, precision):
     _parity(name, precision)
+
+
+def test_plain_fp32_solve_without_refinement():
+    """The single-precision solve without its refinement step (the plain FP32 form)
+    on the T63 statistics, where the sub-domain blocks are well conditioned."""
+    _parity("small_48x26x3x1+1_n80_r2", 1, flags=1)
 
 
 @pytest.mark.parametrize("name", ILL)
