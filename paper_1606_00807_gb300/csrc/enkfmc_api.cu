@@ -165,6 +165,66 @@ enkfmc_status build(enkfmc_handle* h) {
   h->band_elems = band_off;
   h->halo_rows = (int64_t)halo.size() / 2;
 
+  // slot-pair lists per block shape for the band assembly: pairs (s1, s2) of
+  // stencil slots (index pmax = the row itself) with local offsets
+  // o(s1) - o(s2) = d >= 0, grouped by d.  Row j = c - o(s2) adds
+  // T[j][s1] T[j][s2] / D[j] to A[c + d][c].  Valid when the extended box does
+  // not wrap onto itself (ex + r <= nlon), so local and geometric offsets agree.
+  std::vector<int2> pairs;
+  std::vector<int32_t> dptr;
+  h->pair_assembly = true;
+  for (const Block& b : h->blocks)
+    if (g.periodic && b.ex + g.r > g.nlon) h->pair_assembly = false;
+  if (h->pair_assembly) {
+    struct Shape {
+      int nlev, ey, ex, hb, pair_base, dptr_base;
+    };
+    std::vector<Shape> shapes;
+    for (Block& b : h->blocks) {
+      int id = -1;
+      for (size_t i = 0; i < shapes.size(); ++i)
+        if (shapes[i].nlev == b.nlev_b && shapes[i].ey == b.ey && shapes[i].ex == b.ex) id = (int)i;
+      if (id < 0) {
+        shapes.push_back({b.nlev_b, b.ey, b.ex, 0, 0, 0});
+        id = (int)shapes.size() - 1;
+      }
+      shapes[id].hb = std::max(shapes[id].hb, b.hb);
+      b.pair_base = id;  // temporarily the shape id
+    }
+    for (Shape& sh : shapes) {
+      const int ns = g.pmax + 1;
+      std::vector<int> dk(ns, 0), dy(ns, 0), dx(ns, 0), o(ns, 0);
+      for (int s2 = 0; s2 < g.pmax; ++s2) slot_offset(s2, g.r, g.vr, dk[s2], dy[s2], dx[s2]);
+      for (int s2 = 0; s2 < ns; ++s2) o[s2] = (dk[s2] * sh.ey + dy[s2]) * sh.ex + dx[s2];
+      std::vector<std::vector<int2>> byd(sh.hb + 1);
+      for (int a = 0; a < ns; ++a)
+        for (int c = 0; c < ns; ++c) {
+          const int d = o[a] - o[c];
+          if (d < 0 || (d == 0 && a != c) || d > sh.hb) continue;
+          int2 pr;
+          pr.x = a | (c << 16);
+          pr.y = (dk[c] & 0xff) | ((dy[c] & 0xff) << 8) | ((dx[c] & 0xff) << 16);
+          byd[d].push_back(pr);
+        }
+      sh.pair_base = (int)pairs.size();
+      sh.dptr_base = (int)dptr.size();
+      int cnt = 0;
+      for (int d = 0; d <= sh.hb; ++d) {
+        dptr.push_back(cnt);
+        for (const int2& pr : byd[d]) pairs.push_back(pr);
+        cnt += (int)byd[d].size();
+      }
+      dptr.push_back(cnt);
+    }
+    for (Block& b : h->blocks) {
+      const Shape& sh = shapes[b.pair_base];
+      b.pair_base = sh.pair_base;
+      b.dptr_base = sh.dptr_base;
+    }
+  } else {
+    for (Block& b : h->blocks) b.pair_base = b.dptr_base = -1;
+  }
+
   // predecessor counts for the work model
   std::vector<int> p_global((size_t)g.n), p_ext;
   p_ext.reserve((size_t)h->ext_rows);
@@ -211,6 +271,15 @@ enkfmc_status build(enkfmc_handle* h) {
   }
   CUDA_TRY(cudaMemcpy(h->d_blocks, h->blocks.data(), sizeof(Block) * h->blocks.size(),
                       cudaMemcpyHostToDevice));
+  if (h->pair_assembly) {
+    if ((st = dalloc(h, &h->d_pairs, sizeof(int2) * std::max<size_t>(1, pairs.size())))) return st;
+    if ((st = dalloc(h, &h->d_dptr, sizeof(int32_t) * dptr.size()))) return st;
+    if (!pairs.empty())
+      CUDA_TRY(cudaMemcpy(h->d_pairs, pairs.data(), sizeof(int2) * pairs.size(),
+                          cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(h->d_dptr, dptr.data(), sizeof(int32_t) * dptr.size(),
+                        cudaMemcpyHostToDevice));
+  }
   if (!halo.empty())
     CUDA_TRY(cudaMemcpy(h->d_halo, halo.data(), sizeof(int32_t) * halo.size(),
                         cudaMemcpyHostToDevice));
@@ -219,7 +288,8 @@ enkfmc_status build(enkfmc_handle* h) {
 }
 
 void release(enkfmc_handle* h) {
-  void* bufs[] = {h->d_blocks, h->d_halo, h->d_status, h->d_obs_of, h->d_U,   h->d_C,
+  void* bufs[] = {h->d_pairs,  h->d_dptr, h->d_blocks, h->d_halo, h->d_status, h->d_obs_of,
+                  h->d_U,   h->d_C,
                   h->d_Te,     h->d_De,   h->d_band,   h->d_rhs,    h->d_res, h->d_vhi,
                   h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
                   h->d_T,      h->d_D};
@@ -300,6 +370,13 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_ASSEMBLE, [&] {
+    if (h->pair_assembly) {
+      int64_t band_max = 0;
+      for (const Block& b : h->blocks) band_max = std::max(band_max, (int64_t)b.nb * (b.hb + 1));
+      return launch_assemble_pairs<T>(h->g, h->d_blocks, h->nblock, band_max, h->d_pairs,
+                                      h->d_dptr, Tv, D, (const T*)h->d_Te, (const T*)h->d_De,
+                                      h->d_obs_of, R, (T*)h->d_band, h->stream);
+    }
     return launch_assemble<T>(h->g, h->d_blocks, h->nblock, h->nb_max, Tv, D, (const T*)h->d_Te,
                               (const T*)h->d_De, h->d_obs_of, R, (T*)h->d_band, h->d_status,
                               h->stream, h->hb_max);

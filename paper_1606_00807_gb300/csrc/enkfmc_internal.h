@@ -32,6 +32,7 @@ struct Block {
   int32_t lat0, lat1, lon0, lon1;  // interior tile (absolute, lon1 <= nlon)
   int32_t hb;                      // half-bandwidth of A in local order
   int32_t nb;                      // rows of the block
+  int32_t pair_base, dptr_base;    // slot-pair lists of the block's shape (-1: none)
   int64_t band_off;                // offset of the band in the band array
   int64_t row_off;                 // offset of the block's rows (Te, De, rhs rows)
 };
@@ -154,6 +155,9 @@ struct enkfmc_handle {
 
   // device tables
   enkfmc::Block* d_blocks = nullptr;
+  int2* d_pairs = nullptr;       // slot pairs per block shape, grouped by band diagonal
+  int32_t* d_dptr = nullptr;     // group boundaries per shape
+  bool pair_assembly = false;    // every block can use the pair lists
   int32_t* d_halo = nullptr;     // halo rows: (block, local index) pairs
   int32_t* d_obs_of = nullptr;   // [n]: observation index of a component or -1
   int32_t* d_status = nullptr;   // [4]: first error code, pad, 64-bit info
@@ -233,6 +237,14 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
                             const T* Tg, const T* Dg, const T* Te, const T* De,
                             const int32_t* obs_of, const T* R, T* band, int32_t* status,
                             cudaStream_t s, int hb_max);
+
+// Band assembly from per-shape slot-pair lists (blocks whose extended box does
+// not wrap onto itself in longitude).
+template <typename T>
+cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock,
+                                  int64_t band_max, const int2* pairs, const int32_t* dptr,
+                                  const T* Tg, const T* Dg, const T* Te, const T* De,
+                                  const int32_t* obs_of, const T* R, T* band, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band,

@@ -104,6 +104,60 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
   for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : T(0);
 }
 
+// Band entry A[c + d][c] from the slot pairs of diagonal d: one thread per
+// stored entry (d fastest, so the writes are contiguous), pairs in a fixed
+// order (deterministic sums).
+template <typename T>
+__global__ void __launch_bounds__(256) k_assemble_pairs(
+    const Geom g, const Block* __restrict__ blocks, const int2* __restrict__ pairs,
+    const int32_t* __restrict__ dptr, const T* __restrict__ Tg, const T* __restrict__ Dg,
+    const T* __restrict__ Te, const T* __restrict__ De, const int32_t* __restrict__ obs_of,
+    const T* __restrict__ R, T* __restrict__ band) {
+  const Block b = blocks[blockIdx.y];
+  const int hp1 = b.hb + 1;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)b.nb * hp1) return;
+  const int c = (int)(e / hp1), d = (int)(e - (int64_t)c * hp1);
+  T sum = T(0);
+  if (c + d < b.nb) {
+    const int plane = b.ey * b.ex;
+    const int kc = c / plane;
+    const int yyc = (c - kc * plane) / b.ex;
+    const int xxc = c - kc * plane - yyc * b.ex;
+    const int pmax = g.pmax;
+    const int q1 = dptr[b.dptr_base + d + 1];
+    for (int q = dptr[b.dptr_base + d]; q < q1; ++q) {
+      const int2 pr = pairs[b.pair_base + q];
+      const int s1 = pr.x & 0xffff, s2 = pr.x >> 16;
+      const int dk = (signed char)(pr.y & 0xff);
+      const int dy = (signed char)((pr.y >> 8) & 0xff);
+      const int dx = (signed char)((pr.y >> 16) & 0xff);
+      const int kj = kc - dk, yyj = yyc - dy, xxj = xxc - dx;
+      if (kj < 0 || kj >= b.nlev_b || yyj < 0 || yyj >= b.ey || xxj < 0 || xxj >= b.ex) continue;
+      const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
+      const T* trow;
+      T Dj;
+      if (in_interior(b, yj, xj)) {
+        const int64_t lj = coords_label(g, b.var, kj, yj, xj);
+        trow = Tg + lj * pmax;
+        Dj = Dg[lj];
+      } else {
+        const int64_t r = b.row_off + (kj * b.ey + yyj) * b.ex + xxj;
+        trow = Te + r * pmax;
+        Dj = De[r];
+      }
+      const T t1 = s1 == pmax ? T(1) : trow[s1];
+      const T t2 = s2 == pmax ? T(1) : trow[s2];
+      sum += (t1 / Dj) * t2;
+    }
+    if (d == 0) {
+      const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
+      if (o >= 0) sum += T(1) / R[o];
+    }
+  }
+  band[b.band_off + e] = sum;
+}
+
 // rhs[blk][m][loc] = (y_o + sqrt(R_o) Z[m][o] - Xb[m][l]) / R_o when component
 // l = label(loc) is observed by o, else 0 (Eq. 11 right-hand side).
 template <typename T>
@@ -174,6 +228,17 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
 }
 
 template <typename T>
+cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock,
+                                  int64_t band_max, const int2* pairs, const int32_t* dptr,
+                                  const T* Tg, const T* Dg, const T* Te, const T* De,
+                                  const int32_t* obs_of, const T* R, T* band, cudaStream_t s) {
+  const dim3 grid((unsigned)((band_max + 255) / 256), nblock);
+  k_assemble_pairs<T><<<grid, 256, 0, s>>>(g, blocks, pairs, dptr, Tg, Dg, Te, De, obs_of, R,
+                                           band);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_max,
                        const int32_t* obs_of, int64_t m, const T* Xb, const T* y, const T* R,
                        const T* Z, T* rhs, cudaStream_t s) {
@@ -192,6 +257,10 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
 }
 
 #define INST(T)                                                                                  \
+  template cudaError_t launch_assemble_pairs<T>(const Geom&, const Block*, int, int64_t,        \
+                                                const int2*, const int32_t*, const T*, const T*,  \
+                                                const T*, const T*, const int32_t*, const T*, T*, \
+                                                cudaStream_t);                                     \
   template cudaError_t launch_assemble<T>(const Geom&, const Block*, int, int, const T*,        \
                                           const T*, const T*, const T*, const int32_t*,         \
                                           const T*, T*, int32_t*, cudaStream_t, int);           \

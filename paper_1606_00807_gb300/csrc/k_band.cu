@@ -143,72 +143,95 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
   }
 }
 
+constexpr int NM = 32;       // members per thread block in the solves
+constexpr int NMP = NM + 4;  // padded row of the right-hand-side window
+
+// Solve L L^T X = B for members [m0, m0 + NM) of one block.  The rows of B
+// the current panel touches (NB + hb of them) live in a circular window of WR
+// rows in shared memory (row i in slot i % WR); finished rows go back to
+// global memory and the next ones are read in their place.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict__ blocks,
                                                         const T* __restrict__ band,
-                                                        T* __restrict__ rhs, int N, int ldP) {
+                                                        T* __restrict__ rhs, int N, int ldP,
+                                                        int WRmax) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T* P = reinterpret_cast<T*>(smem);  // [NB][ldP]
-  T* Ys = P + (size_t)NB * ldP;       // [NB][N]
-  T* Xs = Ys + (size_t)NB * N;        // [NB][N] staging of solved rows
+  T* P = reinterpret_cast<T*>(smem);   // [NB][ldP]
+  T* Wn = P + (size_t)NB * ldP;        // [WRmax][NMP]
+  T* Red = Wn + (size_t)WRmax * NMP;   // [4][NB][NM] partial sums
   const Block b = blocks[blockIdx.x];
+  const int m0 = blockIdx.y * NM;
+  const int nm = min(NM, N - m0);
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
+  const int WR = ((NB + hb + NB - 1) / NB) * NB;
   const T* AB = band + b.band_off;
-  T* B = rhs + b.row_off * N;
+  T* B = rhs + b.row_off * N + (int64_t)m0 * nb;  // B[m * nb + i], m relative to m0
   const int tid = threadIdx.x;
 
+  auto load_rows = [&](int r0, int cnt) {
+    for (int idx = tid; idx < cnt * nm; idx += blockDim.x) {
+      const int m = idx / cnt, i = idx - m * cnt;
+      Wn[((r0 + i) % WR) * NMP + m] = B[(int64_t)m * nb + r0 + i];
+    }
+  };
+  auto store_rows = [&](int r0, int cnt) {
+    for (int idx = tid; idx < cnt * nm; idx += blockDim.x) {
+      const int m = idx / cnt, i = idx - m * cnt;
+      B[(int64_t)m * nb + r0 + i] = Wn[((r0 + i) % WR) * NMP + m];
+    }
+  };
+
   // ---- forward: L Y = B ----
+  load_rows(0, min(WR, nb));
   for (int c0 = 0; c0 < nb; c0 += NB) {
     const int nbc = min(NB, nb - c0);
     const int rows = min(nbc + hb, nb - c0);
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
-    for (int idx = tid; idx < nbc * N; idx += blockDim.x) {
-      const int m = idx / nbc, t = idx - m * nbc;
-      Ys[t * N + m] = B[(int64_t)m * nb + c0 + t];
-    }
     __syncthreads();
-    for (int m = tid; m < N; m += blockDim.x) {
+    if (tid < nm) {
       for (int t = 0; t < nbc; ++t) {
-        const T yt = Ys[t * N + m] / P[t * ldP + t];
-        Ys[t * N + m] = yt;
-        for (int i = t + 1; i < nbc; ++i) Ys[i * N + m] -= P[t * ldP + i] * yt;
+        T* wt = Wn + ((c0 + t) % WR) * NMP + tid;
+        const T yt = *wt / P[t * ldP + t];
+        *wt = yt;
+        for (int i = t + 1; i < nbc; ++i) Wn[((c0 + i) % WR) * NMP + tid] -= P[t * ldP + i] * yt;
       }
     }
     __syncthreads();
-    for (int idx = tid; idx < nbc * N; idx += blockDim.x) {
-      const int m = idx / nbc, t = idx - m * nbc;
-      B[(int64_t)m * nb + c0 + t] = Ys[t * N + m];
-    }
-    const int W = rows - nbc;
-    const int nTi = (W + 3) >> 2, nTm = (N + 3) >> 2;
-    for (int tile = tid; tile < nTi * nTm; tile += blockDim.x) {
-      const int Ti = tile % nTi, Tm = tile / nTi;
-      T acc[4][4];
+    const int Wr = rows - nbc;
+    const int nTi = (Wr + 3) >> 2;
+    for (int tile = tid; tile < nTi * (NM / 8); tile += blockDim.x) {
+      const int Ti = tile / (NM / 8), Tm = tile - Ti * (NM / 8);
+      const int i0 = nbc + 4 * Ti, mm0 = 8 * Tm;
+      if (mm0 >= nm) continue;
+      T acc[4][8];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
-      const int i0 = nbc + 4 * Ti, m0 = 4 * Tm;
+        for (int c = 0; c < 8; ++c) acc[a][c] = T(0);
       for (int t = 0; t < nbc; ++t) {
-        T av[4], yv[4];
+        T av[4], yv[8];
 #pragma unroll
         for (int a = 0; a < 4; ++a) av[a] = (i0 + a < rows) ? P[t * ldP + i0 + a] : T(0);
+        const T* yr = Wn + ((c0 + t) % WR) * NMP + mm0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) yv[c] = (m0 + c < N) ? Ys[t * N + m0 + c] : T(0);
+        for (int c = 0; c < 8; ++c) yv[c] = yr[c];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], yv[c], acc[a][c]);
+          for (int c = 0; c < 8; ++c) acc[a][c] = fma(av[a], yv[c], acc[a][c]);
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (m0 + c >= N) continue;
-        T* col = B + (int64_t)(m0 + c) * nb + c0;
+      for (int a = 0; a < 4; ++a) {
+        if (i0 + a >= rows) break;
+        T* wr = Wn + ((c0 + i0 + a) % WR) * NMP + mm0;
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-          if (i0 + a < rows) col[i0 + a] -= acc[a][c];
+        for (int c = 0; c < 8; ++c) wr[c] -= acc[a][c];
       }
     }
+    __syncthreads();
+    store_rows(c0, nbc);
+    __syncthreads();
+    if (c0 + WR < nb) load_rows(c0 + WR, min(nbc, nb - (c0 + WR)));
     __syncthreads();
   }
 
@@ -217,66 +240,53 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
   for (int c0 = last; c0 >= 0; c0 -= NB) {
     const int nbc = min(NB, nb - c0);
     const int rows = min(nbc + hb, nb - c0);
+    load_rows(c0, nbc);  // Y of this panel (its slots held rows >= c0 + hb)
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
-    for (int idx = tid; idx < nbc * N; idx += blockDim.x) {
-      const int m = idx / nbc, t = idx - m * nbc;
-      Ys[t * N + m] = B[(int64_t)m * nb + c0 + t];
-    }
     __syncthreads();
-    // Ys[t][m] -= sum_{i in [nbc, rows)} L[c0+i][c0+t] X[c0+i][m]
-    const int nTt = (nbc + 3) >> 2, nTm = (N + 3) >> 2;
-    const int ntile = nTt * nTm;
-    T acc[4][4];
-    const int tile = tid;  // one tile per thread per chunk (ntile <= blockDim checked on host)
-    const int Tt = tile % max(nTt, 1), Tm = tile / max(nTt, 1);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
-    for (int r0 = nbc; r0 < rows; r0 += NB) {
-      const int rc = min(NB, rows - r0);
-      for (int idx = tid; idx < rc * N; idx += blockDim.x) {
-        const int m = idx / rc, i = idx - m * rc;
-        Xs[i * N + m] = B[(int64_t)m * nb + c0 + r0 + i];
-      }
-      __syncthreads();
-      if (tile < ntile) {
-        const int t0 = 4 * Tt, m0 = 4 * Tm;
-        for (int i = 0; i < rc; ++i) {
-          T lv[4], xv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) lv[a] = (t0 + a < nbc) ? P[(t0 + a) * ldP + r0 + i] : T(0);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) xv[c] = (m0 + c < N) ? Xs[i * N + m0 + c] : T(0);
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][c] = fma(lv[a], xv[c], acc[a][c]);
-        }
-      }
-      __syncthreads();
-    }
-    if (tile < ntile) {
-      const int t0 = 4 * Tt, m0 = 4 * Tm;
+    // partial sums of L[c0+i][c0+t] X[c0+i][m] over i in [nbc, rows), 4 groups of i
+    {
+      const int tile = tid & 63, kg = tid >> 6;
+      const int t0 = 4 * (tile >> 3), mm0 = 4 * (tile & 7);
+      T acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (t0 + a < nbc && m0 + c < N) Ys[(t0 + a) * N + m0 + c] -= acc[a][c];
+        for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+      for (int i = nbc + kg; i < rows; i += 4) {
+        T lv[4], xv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) lv[a] = (t0 + a < nbc) ? P[(t0 + a) * ldP + i] : T(0);
+        const T* xr = Wn + ((c0 + i) % WR) * NMP + mm0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xv[c] = xr[c];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a][c] = fma(lv[a], xv[c], acc[a][c]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Red[(kg * NB + t0 + a) * NM + mm0 + c] = acc[a][c];
     }
     __syncthreads();
-    for (int m = tid; m < N; m += blockDim.x) {
+    for (int idx = tid; idx < nbc * nm; idx += blockDim.x) {
+      const int t = idx / nm, m = idx - t * nm;
+      const T sum = Red[(0 * NB + t) * NM + m] + Red[(1 * NB + t) * NM + m] +
+                    Red[(2 * NB + t) * NM + m] + Red[(3 * NB + t) * NM + m];
+      Wn[((c0 + t) % WR) * NMP + m] -= sum;
+    }
+    __syncthreads();
+    if (tid < nm) {
       for (int t = nbc - 1; t >= 0; --t) {
-        const T xt = Ys[t * N + m] / P[t * ldP + t];
-        Ys[t * N + m] = xt;
-        for (int i = 0; i < t; ++i) Ys[i * N + m] -= P[i * ldP + t] * xt;
+        T* wt = Wn + ((c0 + t) % WR) * NMP + tid;
+        const T xt = *wt / P[t * ldP + t];
+        *wt = xt;
+        for (int i = 0; i < t; ++i) Wn[((c0 + i) % WR) * NMP + tid] -= P[i * ldP + t] * xt;
       }
     }
     __syncthreads();
-    for (int idx = tid; idx < nbc * N; idx += blockDim.x) {
-      const int m = idx / nbc, t = idx - m * nbc;
-      B[(int64_t)m * nb + c0 + t] = Ys[t * N + m];
-    }
+    store_rows(c0, nbc);
     __syncthreads();
   }
 }
@@ -298,13 +308,16 @@ cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band
 template <typename T>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
                              T* rhs, cudaStream_t s) {
-  if ((NB / 4) * ((N + 3) / 4) > kThreads) return cudaErrorInvalidValue;  // N <= 128
-  const int ldP = NB + hb_max + 1;
-  const size_t smem = sizeof(T) * ((size_t)NB * ldP + 2 * (size_t)NB * N);
+  const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
+  const int WRmax = ((NB + hb_max + NB - 1) / NB) * NB;
+  const size_t smem =
+      sizeof(T) * ((size_t)NB * ldP + (size_t)WRmax * NMP + 4 * (size_t)NB * NM);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_bandsolve<T><<<nblock, kThreads, smem, s>>>(blocks, band, rhs, N, ldP);
+  const dim3 grid(nblock, (N + NM - 1) / NM);
+  k_bandsolve<T><<<grid, kThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax);
   return cudaGetLastError();
 }
 

@@ -131,26 +131,32 @@ __global__ void __launch_bounds__(256) k_covtable(const Geom g, const T* __restr
 
   for (int m0 = 0; m0 < g.N; m0 += MC) {
     __syncthreads();
-    // stage the window for members [m0, m0 + MC)
-    const int nvec = R * Wp * MC;
-    for (int idx = tid; idx < nvec; idx += blockDim.x) {
-      const int mm = idx % MC;
-      const int cell = idx / MC;
+    // stage the window for members [m0, m0 + MC): one thread per (row, column)
+    // cell, MC contiguous members copied with 16-byte vectors
+    constexpr int VEC = 16 / sizeof(T);
+    const bool full = m0 + MC <= g.ldN;
+    for (int cell = tid; cell < R * Wp; cell += blockDim.x) {
       const int chi = cell % Wp, rho = cell / Wp;
       int dk, dy, dxlo;
       cov_row(rho, r, dk, dy, dxlo);
       const int kk = k + dk, yy = y + dy;
       int xx = x0 - r2 + chi;
-      T val = T(0);
-      bool ok = kk < nlev_v && yy >= 0 && yy < g.nlat && (m0 + mm) < g.N;
-      if (ok) {
-        if (xx < 0 || xx >= g.nlon) {
-          if (g.periodic) xx = imod(xx, g.nlon);
-          else ok = false;
-        }
+      bool ok = kk < nlev_v && yy >= 0 && yy < g.nlat;
+      if (ok && (xx < 0 || xx >= g.nlon)) {
+        if (g.periodic) xx = imod(xx, g.nlon);
+        else ok = false;
       }
-      if (ok) val = U[coords_label(g, v, kk, yy, xx) * g.ldN + m0 + mm];
-      S[(size_t)cell * MCP + mm] = val;
+      T* dst = S + (size_t)cell * MCP;
+      if (ok && full) {
+        const T* src = U + coords_label(g, v, kk, yy, xx) * g.ldN + m0;
+#pragma unroll
+        for (int q = 0; q < MC / VEC; ++q)
+          reinterpret_cast<float4*>(dst)[q] = reinterpret_cast<const float4*>(src)[q];
+      } else {
+        const T* src = ok ? U + coords_label(g, v, kk, yy, xx) * g.ldN : nullptr;
+#pragma unroll
+        for (int mm = 0; mm < MC; ++mm) dst[mm] = (ok && m0 + mm < g.N) ? src[m0 + mm] : T(0);
+      }
     }
     __syncthreads();
     const int mcnt = min(MC, g.N - m0);

