@@ -48,12 +48,14 @@ __device__ __forceinline__ void tri_tile(int idx, int nT, int& I, int& C) {
 template <typename T>
 __device__ __forceinline__ void load_panel(const T* __restrict__ AB, int ld, int hb, int c0,
                                            int nbc, int rows, T* P, int ldP) {
-  for (int idx = threadIdx.x; idx < nbc * rows; idx += blockDim.x) {
-    const int t = idx / rows, i = idx - t * rows;
-    const int d = i - t;
-    T v = T(0);
-    if (d >= 0 && d <= hb) v = AB[(int64_t)(c0 + t) * ld + d];
-    P[t * ldP + i] = v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = warp; t < nbc; t += nw) {
+    const T* col = AB + (int64_t)(c0 + t) * ld;
+    T* dst = P + t * ldP;
+    for (int i = lane; i < rows; i += 32) {
+      const int d = i - t;
+      dst[i] = (d >= 0 && d <= hb) ? col[d] : T(0);
+    }
   }
 }
 
@@ -72,7 +74,15 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
     const int rows = min(nbc + hb, nb - c0);
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     __syncthreads();
+    // left-looking factorisation of the panel, one thread per row (rows <= 2 * 256):
+    // column t takes the products of the finished columns u < t, then its pivot
     for (int t = 0; t < nbc; ++t) {
+      for (int i = t + tid; i < rows; i += blockDim.x) {
+        T acc = P[t * ldP + i];
+        for (int u = 0; u < t; ++u) acc = fma(-P[u * ldP + i], P[u * ldP + t], acc);
+        P[t * ldP + i] = acc;
+      }
+      __syncthreads();
       T dg = P[t * ldP + t];
       if (!finite_val(dg) || !(dg > T(0))) {
         if (tid == 0)
@@ -81,24 +91,19 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
         return;  // uniform: every thread read the same pivot
       }
       dg = sqrt(dg);
-      __syncthreads();
       const T inv = T(1) / dg;
+      __syncthreads();
       for (int i = t + 1 + tid; i < rows; i += blockDim.x) P[t * ldP + i] *= inv;
       if (tid == 0) P[t * ldP + t] = dg;
       __syncthreads();
-      const int ncol = nbc - t - 1;
-      for (int idx = tid; idx < ncol * rows; idx += blockDim.x) {
-        const int u = t + 1 + idx / rows;
-        const int i = idx - (u - t - 1) * rows;
-        if (i >= u) P[u * ldP + i] -= P[t * ldP + i] * P[t * ldP + u];
-      }
-      __syncthreads();
     }
     // write the factored panel
-    for (int idx = tid; idx < nbc * rows; idx += blockDim.x) {
-      const int t = idx / rows, i = idx - t * rows;
-      const int d = i - t;
-      if (d >= 0 && d <= hb) AB[(int64_t)(c0 + t) * ld + d] = P[t * ldP + i];
+    {
+      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+      for (int t = warp; t < nbc; t += nw) {
+        T* col = AB + (int64_t)(c0 + t) * ld;
+        for (int i = t + lane; i < rows && i - t <= hb; i += 32) col[i - t] = P[t * ldP + i];
+      }
     }
     // trailing update of the window [c0+nbc, c0+rows)
     const int W = rows - nbc;
@@ -143,42 +148,47 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
   }
 }
 
-constexpr int NM = 32;       // members per thread block in the solves
-constexpr int NMP = NM + 4;  // padded row of the right-hand-side window
-
-// Solve L L^T X = B for members [m0, m0 + NM) of one block.  The rows of B
+// Solve L L^T X = B for members [m0, m0 + NMB) of one block.  The rows of B
 // the current panel touches (NB + hb of them) live in a circular window of WR
-// rows in shared memory (row i in slot i % WR); finished rows go back to
-// global memory and the next ones are read in their place.
-template <typename T>
+// rows in shared memory (row i in slot i mod WR, WR a multiple of NB, so a
+// panel's own rows are contiguous slots); finished rows go back to global
+// memory and the next ones are read in their place.  The NB x NB diagonal
+// triangles are solved one member per thread in registers.
+template <typename T, int NMB>
 __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict__ blocks,
                                                         const T* __restrict__ band,
                                                         T* __restrict__ rhs, int N, int ldP,
                                                         int WRmax) {
+  constexpr int NMP = NMB + 4;
   extern __shared__ __align__(16) unsigned char smem[];
   T* P = reinterpret_cast<T*>(smem);   // [NB][ldP]
   T* Wn = P + (size_t)NB * ldP;        // [WRmax][NMP]
-  T* Red = Wn + (size_t)WRmax * NMP;   // [4][NB][NM] partial sums
+  T* Red = Wn + (size_t)WRmax * NMP;   // [4][NB][NMB] partial sums
+  T* invd = Red + 4 * NB * NMB;        // [NB]
   const Block b = blocks[blockIdx.x];
-  const int m0 = blockIdx.y * NM;
-  const int nm = min(NM, N - m0);
+  const int m0 = blockIdx.y * NMB;
+  const int nm = min(NMB, N - m0);
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
   const int WR = ((NB + hb + NB - 1) / NB) * NB;
   const T* AB = band + b.band_off;
   T* B = rhs + b.row_off * N + (int64_t)m0 * nb;  // B[m * nb + i], m relative to m0
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 
+  // rows [r0, r0 + cnt) <-> slots starting at r0 mod WR (no wrap inside: cnt <= NB
+  // and r0 a multiple of NB, or the initial fill starting at slot 0)
   auto load_rows = [&](int r0, int cnt) {
-    for (int idx = tid; idx < cnt * nm; idx += blockDim.x) {
-      const int m = idx / cnt, i = idx - m * cnt;
-      Wn[((r0 + i) % WR) * NMP + m] = B[(int64_t)m * nb + r0 + i];
-    }
+    const int sb = r0 % WR;
+    for (int m = warp; m < nm; m += nw)
+      for (int i = lane; i < cnt; i += 32) Wn[(sb + i) * NMP + m] = B[(int64_t)m * nb + r0 + i];
   };
   auto store_rows = [&](int r0, int cnt) {
-    for (int idx = tid; idx < cnt * nm; idx += blockDim.x) {
-      const int m = idx / cnt, i = idx - m * cnt;
-      B[(int64_t)m * nb + r0 + i] = Wn[((r0 + i) % WR) * NMP + m];
-    }
+    const int sb = r0 % WR;
+    for (int m = warp; m < nm; m += nw)
+      for (int i = lane; i < cnt; i += 32) B[(int64_t)m * nb + r0 + i] = Wn[(sb + i) * NMP + m];
+  };
+  auto slot = [&](int base, int i) {
+    const int sl = base + i;
+    return sl >= WR ? sl - WR : sl;
   };
 
   // ---- forward: L Y = B ----
@@ -186,21 +196,44 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
   for (int c0 = 0; c0 < nb; c0 += NB) {
     const int nbc = min(NB, nb - c0);
     const int rows = min(nbc + hb, nb - c0);
+    const int base = c0 % WR;
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     __syncthreads();
+    if (tid < NB) invd[tid] = tid < nbc ? T(1) / P[tid * ldP + tid] : T(0);
+    __syncthreads();
     if (tid < nm) {
-      for (int t = 0; t < nbc; ++t) {
-        T* wt = Wn + ((c0 + t) % WR) * NMP + tid;
-        const T yt = *wt / P[t * ldP + t];
-        *wt = yt;
-        for (int i = t + 1; i < nbc; ++i) Wn[((c0 + i) % WR) * NMP + tid] -= P[t * ldP + i] * yt;
+      // forward triangle in blocks of 8 rows: solve the block in registers,
+      // then update the rows below it
+      T* w = Wn + base * NMP + tid;
+#pragma unroll 1
+      for (int B0 = 0; B0 < nbc; B0 += 8) {
+        T yv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) yv[j] = (B0 + j < nbc) ? w[(B0 + j) * NMP] : T(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          T acc = yv[j];
+#pragma unroll
+          for (int i = 0; i < j; ++i) acc = fma(-P[(B0 + i) * ldP + B0 + j], yv[i], acc);
+          yv[j] = acc * invd[B0 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (B0 + j < nbc) w[(B0 + j) * NMP] = yv[j];
+        for (int t = B0 + 8; t < nbc; ++t) {
+          T acc = w[t * NMP];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc = fma(-P[(B0 + j) * ldP + t], yv[j], acc);
+          w[t * NMP] = acc;
+        }
       }
     }
     __syncthreads();
     const int Wr = rows - nbc;
     const int nTi = (Wr + 3) >> 2;
-    for (int tile = tid; tile < nTi * (NM / 8); tile += blockDim.x) {
-      const int Ti = tile / (NM / 8), Tm = tile - Ti * (NM / 8);
+    constexpr int TMT = NMB / 8;
+    for (int tile = tid; tile < nTi * TMT; tile += blockDim.x) {
+      const int Ti = tile / TMT, Tm = tile - Ti * TMT;
       const int i0 = nbc + 4 * Ti, mm0 = 8 * Tm;
       if (mm0 >= nm) continue;
       T acc[4][8];
@@ -212,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
         T av[4], yv[8];
 #pragma unroll
         for (int a = 0; a < 4; ++a) av[a] = (i0 + a < rows) ? P[t * ldP + i0 + a] : T(0);
-        const T* yr = Wn + ((c0 + t) % WR) * NMP + mm0;
+        const T* yr = Wn + (base + t) * NMP + mm0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) yv[c] = yr[c];
 #pragma unroll
@@ -223,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         if (i0 + a >= rows) break;
-        T* wr = Wn + ((c0 + i0 + a) % WR) * NMP + mm0;
+        T* wr = Wn + slot(base, i0 + a) * NMP + mm0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) wr[c] -= acc[a][c];
       }
@@ -240,13 +273,16 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
   for (int c0 = last; c0 >= 0; c0 -= NB) {
     const int nbc = min(NB, nb - c0);
     const int rows = min(nbc + hb, nb - c0);
+    const int base = c0 % WR;
     load_rows(c0, nbc);  // Y of this panel (its slots held rows >= c0 + hb)
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     __syncthreads();
+    if (tid < NB) invd[tid] = tid < nbc ? T(1) / P[tid * ldP + tid] : T(0);
     // partial sums of L[c0+i][c0+t] X[c0+i][m] over i in [nbc, rows), 4 groups of i
-    {
-      const int tile = tid & 63, kg = tid >> 6;
-      const int t0 = 4 * (tile >> 3), mm0 = 4 * (tile & 7);
+    constexpr int TM4 = NMB / 4;
+    for (int job = tid; job < (NB / 4) * TM4 * 4; job += blockDim.x) {
+      const int tile = job % ((NB / 4) * TM4), kg = job / ((NB / 4) * TM4);
+      const int t0 = 4 * (tile / TM4), mm0 = 4 * (tile % TM4);
       T acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -256,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
         T lv[4], xv[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) lv[a] = (t0 + a < nbc) ? P[(t0 + a) * ldP + i] : T(0);
-        const T* xr = Wn + ((c0 + i) % WR) * NMP + mm0;
+        const T* xr = Wn + slot(base, i) * NMP + mm0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) xv[c] = xr[c];
 #pragma unroll
@@ -267,22 +303,36 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Red[(kg * NB + t0 + a) * NM + mm0 + c] = acc[a][c];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nbc * nm; idx += blockDim.x) {
-      const int t = idx / nm, m = idx - t * nm;
-      const T sum = Red[(0 * NB + t) * NM + m] + Red[(1 * NB + t) * NM + m] +
-                    Red[(2 * NB + t) * NM + m] + Red[(3 * NB + t) * NM + m];
-      Wn[((c0 + t) % WR) * NMP + m] -= sum;
+        for (int c = 0; c < 4; ++c) Red[(kg * NB + t0 + a) * NMB + mm0 + c] = acc[a][c];
     }
     __syncthreads();
     if (tid < nm) {
-      for (int t = nbc - 1; t >= 0; --t) {
-        T* wt = Wn + ((c0 + t) % WR) * NMP + tid;
-        const T xt = *wt / P[t * ldP + t];
-        *wt = xt;
-        for (int i = 0; i < t; ++i) Wn[((c0 + i) % WR) * NMP + tid] -= P[i * ldP + t] * xt;
+      T* w = Wn + base * NMP + tid;
+      for (int t = 0; t < nbc; ++t)
+        w[t * NMP] -= Red[(0 * NB + t) * NMB + tid] + Red[(1 * NB + t) * NMB + tid] +
+                      Red[(2 * NB + t) * NMB + tid] + Red[(3 * NB + t) * NMB + tid];
+      // backward triangle in blocks of 8 rows, last block first
+#pragma unroll 1
+      for (int B0 = ((nbc - 1) / 8) * 8; B0 >= 0; B0 -= 8) {
+        T yv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) yv[j] = (B0 + j < nbc) ? w[(B0 + j) * NMP] : T(0);
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+          T acc = yv[j];
+#pragma unroll
+          for (int i = j + 1; i < 8; ++i) acc = fma(-P[(B0 + j) * ldP + B0 + i], yv[i], acc);
+          yv[j] = acc * invd[B0 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (B0 + j < nbc) w[(B0 + j) * NMP] = yv[j];
+        for (int t = 0; t < B0; ++t) {
+          T acc = w[t * NMP];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc = fma(-P[t * ldP + B0 + j], yv[j], acc);
+          w[t * NMP] = acc;
+        }
       }
     }
     __syncthreads();
@@ -305,20 +355,37 @@ cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band
   return cudaGetLastError();
 }
 
+template <typename T, int NMB>
+cudaError_t launch_bandsolve_nm(const Block* blocks, int nblock, int hb_max, int N,
+                                const T* band, T* rhs, cudaStream_t s, size_t smem, int ldP,
+                                int WRmax) {
+  cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T, NMB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(nblock, (N + NMB - 1) / NMB);
+  k_bandsolve<T, NMB><<<grid, kThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
                              T* rhs, cudaStream_t s) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const int WRmax = ((NB + hb_max + NB - 1) / NB) * NB;
-  const size_t smem =
-      sizeof(T) * ((size_t)NB * ldP + (size_t)WRmax * NMP + 4 * (size_t)NB * NM);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid(nblock, (N + NM - 1) / NM);
-  k_bandsolve<T><<<grid, kThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax);
-  return cudaGetLastError();
+  auto bytes = [&](int nmb) {
+    return sizeof(T) * ((size_t)NB * ldP + (size_t)WRmax * (nmb + 4) + 4 * (size_t)NB * nmb + NB);
+  };
+  const size_t lim = 227 * 1024;
+  if (bytes(32) <= lim)
+    return launch_bandsolve_nm<T, 32>(blocks, nblock, hb_max, N, band, rhs, s, bytes(32), ldP,
+                                      WRmax);
+  if (bytes(16) <= lim)
+    return launch_bandsolve_nm<T, 16>(blocks, nblock, hb_max, N, band, rhs, s, bytes(16), ldP,
+                                      WRmax);
+  if (bytes(8) <= lim)
+    return launch_bandsolve_nm<T, 8>(blocks, nblock, hb_max, N, band, rhs, s, bytes(8), ldP,
+                                     WRmax);
+  return cudaErrorInvalidConfiguration;
 }
 
 #define INST(T)                                                                                  \
