@@ -215,6 +215,7 @@ enkfmc_status build(enkfmc_handle* h) {
         cnt += (int)byd[d].size();
       }
       dptr.push_back(cnt);
+      h->npair_max = std::max(h->npair_max, cnt);
     }
     for (Block& b : h->blocks) {
       const Shape& sh = shapes[b.pair_base];
@@ -370,13 +371,11 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_ASSEMBLE, [&] {
-    if (h->pair_assembly) {
-      int64_t band_max = 0;
-      for (const Block& b : h->blocks) band_max = std::max(band_max, (int64_t)b.nb * (b.hb + 1));
-      return launch_assemble_pairs<T>(h->g, h->d_blocks, h->nblock, band_max, h->d_pairs,
-                                      h->d_dptr, Tv, D, (const T*)h->d_Te, (const T*)h->d_De,
-                                      h->d_obs_of, R, (T*)h->d_band, h->stream);
-    }
+    if (h->pair_assembly)
+      return launch_assemble_pairs<T>(h->g, h->d_blocks, h->nblock, h->nb_max, h->hb_max,
+                                      h->npair_max, h->d_pairs, h->d_dptr, Tv, D,
+                                      (const T*)h->d_Te, (const T*)h->d_De, h->d_obs_of, R,
+                                      (T*)h->d_band, h->stream);
     return launch_assemble<T>(h->g, h->d_blocks, h->nblock, h->nb_max, Tv, D, (const T*)h->d_Te,
                               (const T*)h->d_De, h->d_obs_of, R, (T*)h->d_band, h->d_status,
                               h->stream, h->hb_max);

@@ -158,6 +158,7 @@ struct enkfmc_handle {
   int2* d_pairs = nullptr;       // slot pairs per block shape, grouped by band diagonal
   int32_t* d_dptr = nullptr;     // group boundaries per shape
   bool pair_assembly = false;    // every block can use the pair lists
+  int32_t npair_max = 0;         // longest pair list of a shape
   int32_t* d_halo = nullptr;     // halo rows: (block, local index) pairs
   int32_t* d_obs_of = nullptr;   // [n]: observation index of a component or -1
   int32_t* d_status = nullptr;   // [4]: first error code, pad, 64-bit info
@@ -241,10 +242,11 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
 // Band assembly from per-shape slot-pair lists (blocks whose extended box does
 // not wrap onto itself in longitude).
 template <typename T>
-cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock,
-                                  int64_t band_max, const int2* pairs, const int32_t* dptr,
-                                  const T* Tg, const T* Dg, const T* Te, const T* De,
-                                  const int32_t* obs_of, const T* R, T* band, cudaStream_t s);
+cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                                  int hb_max, int npair_max, const int2* pairs,
+                                  const int32_t* dptr, const T* Tg, const T* Dg, const T* Te,
+                                  const T* De, const int32_t* obs_of, const T* R, T* band,
+                                  cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band,

@@ -104,58 +104,86 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
   for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : T(0);
 }
 
-// Band entry A[c + d][c] from the slot pairs of diagonal d: one thread per
-// stored entry (d fastest, so the writes are contiguous), pairs in a fixed
-// order (deterministic sums).
+// Band entries A[c + d][c] for a tile of kCols columns from the slot pairs of
+// each diagonal d.  The rows j = c - o(s2) that can touch the tile (local
+// indices [c0 - r, c0 + kCols + hb]) are staged in shared memory with their D,
+// and so is the block shape's pair list; each thread then builds entries with
+// d fastest (contiguous stores), summing its pairs in a fixed order
+// (deterministic results).
+constexpr int kCols = 32;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_assemble_pairs(
     const Geom g, const Block* __restrict__ blocks, const int2* __restrict__ pairs,
     const int32_t* __restrict__ dptr, const T* __restrict__ Tg, const T* __restrict__ Dg,
     const T* __restrict__ Te, const T* __restrict__ De, const int32_t* __restrict__ obs_of,
-    const T* __restrict__ R, T* __restrict__ band) {
+    const T* __restrict__ R, T* __restrict__ band, int stage_rows, int npair_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const Block b = blocks[blockIdx.y];
+  const int c0 = blockIdx.x * kCols;
+  if (c0 >= b.nb) return;
+  const int pmax = g.pmax, ldt = pmax + 1;  // staged row: pmax coefficients then 1/D
+  T* Ts = reinterpret_cast<T*>(smem);                         // [stage_rows][ldt]
+  int4* Ps = reinterpret_cast<int4*>(Ts + (size_t)stage_rows * ldt + (stage_rows & 1));
+  int* Dp = reinterpret_cast<int*>(Ps + npair_max);           // [hb + 2]
   const int hp1 = b.hb + 1;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)b.nb * hp1) return;
-  const int c = (int)(e / hp1), d = (int)(e - (int64_t)c * hp1);
-  T sum = T(0);
-  if (c + d < b.nb) {
-    const int plane = b.ey * b.ex;
-    const int kc = c / plane;
-    const int yyc = (c - kc * plane) / b.ex;
-    const int xxc = c - kc * plane - yyc * b.ex;
-    const int pmax = g.pmax;
-    const int q1 = dptr[b.dptr_base + d + 1];
-    for (int q = dptr[b.dptr_base + d]; q < q1; ++q) {
-      const int2 pr = pairs[b.pair_base + q];
-      const int s1 = pr.x & 0xffff, s2 = pr.x >> 16;
-      const int dk = (signed char)(pr.y & 0xff);
-      const int dy = (signed char)((pr.y >> 8) & 0xff);
-      const int dx = (signed char)((pr.y >> 16) & 0xff);
-      const int kj = kc - dk, yyj = yyc - dy, xxj = xxc - dx;
-      if (kj < 0 || kj >= b.nlev_b || yyj < 0 || yyj >= b.ey || xxj < 0 || xxj >= b.ex) continue;
+  const int jlo = c0 - g.r;
+  const int nrow = min(stage_rows, kCols + hp1 + g.r);
+  const int plane = b.ey * b.ex;
+  // stage rows j in [jlo, jlo + nrow)
+  for (int idx = threadIdx.x; idx < nrow * ldt; idx += blockDim.x) {
+    const int jj = idx / ldt, s = idx - jj * ldt;
+    const int j = jlo + jj;
+    T val = T(0);
+    if (j >= 0 && j < b.nb) {
+      const int kj = j / plane, yyj = (j - kj * plane) / b.ex, xxj = j - kj * plane - yyj * b.ex;
       const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
-      const T* trow;
-      T Dj;
-      if (in_interior(b, yj, xj)) {
-        const int64_t lj = coords_label(g, b.var, kj, yj, xj);
-        trow = Tg + lj * pmax;
-        Dj = Dg[lj];
-      } else {
-        const int64_t r = b.row_off + (kj * b.ey + yyj) * b.ex + xxj;
-        trow = Te + r * pmax;
-        Dj = De[r];
-      }
-      const T t1 = s1 == pmax ? T(1) : trow[s1];
-      const T t2 = s2 == pmax ? T(1) : trow[s2];
-      sum += (t1 / Dj) * t2;
+      const bool in = in_interior(b, yj, xj);
+      const int64_t rsrc = in ? coords_label(g, b.var, kj, yj, xj) : b.row_off + j;
+      if (s < pmax) val = in ? Tg[rsrc * pmax + s] : Te[rsrc * pmax + s];
+      else val = T(1) / (in ? Dg[rsrc] : De[rsrc]);
     }
-    if (d == 0) {
-      const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
-      if (o >= 0) sum += T(1) / R[o];
-    }
+    Ts[jj * ldt + s] = val;
   }
-  band[b.band_off + e] = sum;
+  // pair list of the shape, with each pair's local column offset
+  const int np = dptr[b.dptr_base + b.hb + 1];
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    const int2 pr = pairs[b.pair_base + q];
+    const int dk = (signed char)(pr.y & 0xff);
+    const int dy = (signed char)((pr.y >> 8) & 0xff);
+    const int dx = (signed char)((pr.y >> 16) & 0xff);
+    Ps[q] = make_int4(pr.x, pr.y, (dk * b.ey + dy) * b.ex + dx, 0);
+  }
+  for (int d = threadIdx.x; d <= hp1; d += blockDim.x) Dp[d] = dptr[b.dptr_base + d];
+  __syncthreads();
+  const int ncol = min(kCols, b.nb - c0);
+  for (int e = threadIdx.x; e < ncol * hp1; e += blockDim.x) {
+    const int cc = e / hp1, d = e - cc * hp1;
+    const int c = c0 + cc;
+    T sum = T(0);
+    if (c + d < b.nb) {
+      const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
+      const int q1 = Dp[d + 1];
+      for (int q = Dp[d]; q < q1; ++q) {
+        const int4 pr = Ps[q];
+        const int s1 = pr.x & 0xffff, s2 = pr.x >> 16;
+        const int dk = (signed char)(pr.y & 0xff);
+        const int dy = (signed char)((pr.y >> 8) & 0xff);
+        const int dx = (signed char)((pr.y >> 16) & 0xff);
+        const int kj = kc - dk, yyj = yyc - dy, xxj = xxc - dx;
+        if (kj < 0 || kj >= b.nlev_b || yyj < 0 || yyj >= b.ey || xxj < 0 || xxj >= b.ex) continue;
+        const T* tr = Ts + (c - pr.z - jlo) * ldt;
+        const T t1 = s1 == pmax ? T(1) : tr[s1];
+        const T t2 = s2 == pmax ? T(1) : tr[s2];
+        sum += (t1 * tr[pmax]) * t2;
+      }
+      if (d == 0) {
+        const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
+        if (o >= 0) sum += T(1) / R[o];
+      }
+    }
+    band[b.band_off + (int64_t)c * hp1 + d] = sum;
+  }
 }
 
 // rhs[blk][m][loc] = (y_o + sqrt(R_o) Z[m][o] - Xb[m][l]) / R_o when component
@@ -228,13 +256,21 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
 }
 
 template <typename T>
-cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock,
-                                  int64_t band_max, const int2* pairs, const int32_t* dptr,
-                                  const T* Tg, const T* Dg, const T* Te, const T* De,
-                                  const int32_t* obs_of, const T* R, T* band, cudaStream_t s) {
-  const dim3 grid((unsigned)((band_max + 255) / 256), nblock);
-  k_assemble_pairs<T><<<grid, 256, 0, s>>>(g, blocks, pairs, dptr, Tg, Dg, Te, De, obs_of, R,
-                                           band);
+cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                                  int hb_max, int npair_max, const int2* pairs,
+                                  const int32_t* dptr, const T* Tg, const T* Dg, const T* Te,
+                                  const T* De, const int32_t* obs_of, const T* R, T* band,
+                                  cudaStream_t s) {
+  const int stage_rows = kCols + hb_max + 1 + g.r;
+  const size_t smem = sizeof(T) * ((size_t)stage_rows * (g.pmax + 1) + (stage_rows & 1)) +
+                      sizeof(int4) * (size_t)npair_max + sizeof(int) * (hb_max + 2);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((nb_max + kCols - 1) / kCols, nblock);
+  k_assemble_pairs<T><<<grid, 256, smem, s>>>(g, blocks, pairs, dptr, Tg, Dg, Te, De, obs_of, R,
+                                              band, stage_rows, npair_max);
   return cudaGetLastError();
 }
 
@@ -257,7 +293,7 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
 }
 
 #define INST(T)                                                                                  \
-  template cudaError_t launch_assemble_pairs<T>(const Geom&, const Block*, int, int64_t,        \
+  template cudaError_t launch_assemble_pairs<T>(const Geom&, const Block*, int, int, int, int,  \
                                                 const int2*, const int32_t*, const T*, const T*,  \
                                                 const T*, const T*, const int32_t*, const T*, T*, \
                                                 cudaStream_t);                                     \

@@ -27,6 +27,20 @@ namespace {
 
 constexpr int NB = 32;
 constexpr int kThreads = 256;
+constexpr int kSolveThreads = 320;
+
+// Four consecutive elements from 16-byte aligned shared memory.
+template <typename T>
+__device__ __forceinline__ void lds4(const T* p, T (&v)[4]) {
+  if (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = (T)q.x; v[1] = (T)q.y; v[2] = (T)q.z; v[3] = (T)q.w;
+  } else {
+    const double2 q0 = reinterpret_cast<const double2*>(p)[0];
+    const double2 q1 = reinterpret_cast<const double2*>(p)[1];
+    v[0] = (T)q0.x; v[1] = (T)q0.y; v[2] = (T)q1.x; v[3] = (T)q1.y;
+  }
+}
 
 __device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
@@ -119,13 +133,19 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
         const int i0 = nbc + 4 * I, j0 = nbc + 4 * C;
+        const bool vec = ((nbc & 3) == 0) && (i0 + 3 < rows) && (j0 + 3 < rows);
         for (int t = 0; t < nbc; ++t) {
           const T* Pt = P + t * ldP;
           T av[4], bv[4];
+          if (vec) {
+            lds4(Pt + i0, av);
+            lds4(Pt + j0, bv);
+          } else {
 #pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = (i0 + a < rows) ? Pt[i0 + a] : T(0);
+            for (int a = 0; a < 4; ++a) av[a] = (i0 + a < rows) ? Pt[i0 + a] : T(0);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) bv[c] = (j0 + c < rows) ? Pt[j0 + c] : T(0);
+            for (int c = 0; c < 4; ++c) bv[c] = (j0 + c < rows) ? Pt[j0 + c] : T(0);
+          }
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -155,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
 // memory and the next ones are read in their place.  The NB x NB diagonal
 // triangles are solved one member per thread in registers.
 template <typename T, int NMB>
-__global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict__ blocks,
+__global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __restrict__ blocks,
                                                         const T* __restrict__ band,
                                                         T* __restrict__ rhs, int N, int ldP,
                                                         int WRmax) {
@@ -165,8 +185,10 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
   T* Wn = P + (size_t)NB * ldP;        // [WRmax][NMP]
   T* Red = Wn + (size_t)WRmax * NMP;   // [4][NB][NMB] partial sums
   T* invd = Red + 4 * NB * NMB;        // [NB]
-  const Block b = blocks[blockIdx.x];
-  const int m0 = blockIdx.y * NMB;
+  // the member chunks of one block are consecutive thread blocks, so they run
+  // together and share the factor through L2
+  const Block b = blocks[blockIdx.y];
+  const int m0 = blockIdx.x * NMB;
   const int nm = min(NMB, N - m0);
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
   const int WR = ((NB + hb + NB - 1) / NB) * NB;
@@ -241,13 +263,23 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[a][c] = T(0);
+      const bool vec = ((nbc & 3) == 0) && (i0 + 3 < rows);
       for (int t = 0; t < nbc; ++t) {
-        T av[4], yv[8];
+        T av[4], yv[8], y0[4], y1[4];
+        if (vec) {
+          lds4(P + t * ldP + i0, av);
+        } else {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) av[a] = (i0 + a < rows) ? P[t * ldP + i0 + a] : T(0);
+          for (int a = 0; a < 4; ++a) av[a] = (i0 + a < rows) ? P[t * ldP + i0 + a] : T(0);
+        }
         const T* yr = Wn + (base + t) * NMP + mm0;
+        lds4(yr, y0);
+        lds4(yr + 4, y1);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) yv[c] = yr[c];
+        for (int c = 0; c < 4; ++c) {
+          yv[c] = y0[c];
+          yv[4 + c] = y1[c];
+        }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -292,9 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
         T lv[4], xv[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) lv[a] = (t0 + a < nbc) ? P[(t0 + a) * ldP + i] : T(0);
-        const T* xr = Wn + slot(base, i) * NMP + mm0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) xv[c] = xr[c];
+        lds4(Wn + slot(base, i) * NMP + mm0, xv);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -346,7 +376,7 @@ __global__ void __launch_bounds__(kThreads) k_bandsolve(const Block* __restrict_
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, int32_t* status,
                             cudaStream_t s) {
-  const int ldP = NB + hb_max + 1;
+  const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const size_t smem = sizeof(T) * (size_t)NB * ldP;
   cudaError_t e = cudaFuncSetAttribute(k_bandchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
@@ -362,8 +392,8 @@ cudaError_t launch_bandsolve_nm(const Block* blocks, int nblock, int hb_max, int
   cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T, NMB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid(nblock, (N + NMB - 1) / NMB);
-  k_bandsolve<T, NMB><<<grid, kThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax);
+  const dim3 grid((N + NMB - 1) / NMB, nblock);
+  k_bandsolve<T, NMB><<<grid, kSolveThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax);
   return cudaGetLastError();
 }
 
