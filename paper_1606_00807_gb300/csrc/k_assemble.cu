@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
   if (c0 >= b.nb) return;
   const int pmax = g.pmax, ldt = pmax + 1;  // staged row: pmax coefficients then 1/D
   T* Ts = reinterpret_cast<T*>(smem);                         // [stage_rows][ldt]
-  int4* Ps = reinterpret_cast<int4*>(Ts + (size_t)stage_rows * ldt + (stage_rows & 1));
+  const size_t ts_bytes = (sizeof(T) * (size_t)stage_rows * ldt + 15) / 16 * 16;
+  int4* Ps = reinterpret_cast<int4*>(smem + ts_bytes);        // [npair_max], 16-byte aligned
   int* Dp = reinterpret_cast<int*>(Ps + npair_max);           // [hb + 2]
   const int hp1 = b.hb + 1;
   const int jlo = c0 - g.r;
@@ -262,7 +263,7 @@ cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
                                   cudaStream_t s) {
   const int stage_rows = kCols + hb_max + 1 + g.r;
-  const size_t smem = sizeof(T) * ((size_t)stage_rows * (g.pmax + 1) + (stage_rows & 1)) +
+  const size_t smem = (sizeof(T) * (size_t)stage_rows * (g.pmax + 1) + 15) / 16 * 16 +
                       sizeof(int4) * (size_t)npair_max + sizeof(int) * (hb_max + 2);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T>,
