@@ -131,20 +131,24 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
   const int jlo = c0 - g.r;
   const int nrow = min(stage_rows, kCols + hp1 + g.r);
   const int plane = b.ey * b.ex;
-  // stage rows j in [jlo, jlo + nrow)
-  for (int idx = threadIdx.x; idx < nrow * ldt; idx += blockDim.x) {
-    const int jj = idx / ldt, s = idx - jj * ldt;
-    const int j = jlo + jj;
-    T val = T(0);
-    if (j >= 0 && j < b.nb) {
+  // stage rows j in [jlo, jlo + nrow): one warp per row, lanes over its slots
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int jj = warp; jj < nrow; jj += nw) {
+      const int j = jlo + jj;
+      T* dst = Ts + jj * ldt;
+      if (j < 0 || j >= b.nb) {
+        for (int s = lane; s < ldt; s += 32) dst[s] = T(0);
+        continue;
+      }
       const int kj = j / plane, yyj = (j - kj * plane) / b.ex, xxj = j - kj * plane - yyj * b.ex;
       const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
       const bool in = in_interior(b, yj, xj);
       const int64_t rsrc = in ? coords_label(g, b.var, kj, yj, xj) : b.row_off + j;
-      if (s < pmax) val = in ? Tg[rsrc * pmax + s] : Te[rsrc * pmax + s];
-      else val = T(1) / (in ? Dg[rsrc] : De[rsrc]);
+      const T* src = (in ? Tg : Te) + rsrc * pmax;
+      for (int s = lane; s < pmax; s += 32) dst[s] = src[s];
+      if (lane == 0) dst[pmax] = T(1) / (in ? Dg[rsrc] : De[rsrc]);
     }
-    Ts[jj * ldt + s] = val;
   }
   // pair list of the shape, with each pair's local column offset
   const int np = dptr[b.dptr_base + b.hb + 1];
@@ -158,12 +162,13 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
   for (int d = threadIdx.x; d <= hp1; d += blockDim.x) Dp[d] = dptr[b.dptr_base + d];
   __syncthreads();
   const int ncol = min(kCols, b.nb - c0);
-  for (int e = threadIdx.x; e < ncol * hp1; e += blockDim.x) {
-    const int cc = e / hp1, d = e - cc * hp1;
+  // columns in turn (coordinates decoded once per column), threads over d
+  for (int cc = 0; cc < ncol; ++cc) {
     const int c = c0 + cc;
+    const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
+    for (int d = threadIdx.x; d < hp1; d += blockDim.x) {
     T sum = T(0);
     if (c + d < b.nb) {
-      const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
       const int q1 = Dp[d + 1];
       for (int q = Dp[d]; q < q1; ++q) {
         const int4 pr = Ps[q];
@@ -184,6 +189,7 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
       }
     }
     band[b.band_off + (int64_t)c * hp1 + d] = sum;
+    }
   }
 }
 

@@ -108,7 +108,7 @@ template <typename T, int MC>
 __global__ void __launch_bounds__(256) k_covtable(const Geom g, const T* __restrict__ U,
                                                   T* __restrict__ C, int W, int nH, int nrho) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int MCP = MC + 4;
+  constexpr int MCP = MC + 1;  // odd stride: cells 4 apart fall in different banks
   const int r = g.r, r2 = 2 * r, w4 = 4 * r + 1;
   const int Wp = W + 4 * r;
   const int R = nrho;  // region rows coincide with offset rows
@@ -150,8 +150,12 @@ __global__ void __launch_bounds__(256) k_covtable(const Geom g, const T* __restr
       if (ok && full) {
         const T* src = U + coords_label(g, v, kk, yy, xx) * g.ldN + m0;
 #pragma unroll
-        for (int q = 0; q < MC / VEC; ++q)
-          reinterpret_cast<float4*>(dst)[q] = reinterpret_cast<const float4*>(src)[q];
+        for (int q = 0; q < MC / VEC; ++q) {
+          const float4 f = reinterpret_cast<const float4*>(src)[q];
+          const T* e = reinterpret_cast<const T*>(&f);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) dst[q * VEC + u] = e[u];
+        }
       } else {
         const T* src = ok ? U + coords_label(g, v, kk, yy, xx) * g.ldN : nullptr;
 #pragma unroll
@@ -524,10 +528,10 @@ cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
   const int nH = cov_offset_count(r, g.vr);
   const int nrho = 1 + 2 * r + g.vr * (4 * r + 1);
   int W = r <= 2 ? 64 : 32;
-  size_t smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 4) + (size_t)W * nH);
+  size_t smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 1) + (size_t)W * nH);
   while (smem > 200 * 1024 && W > 8) {
     W /= 2;
-    smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 4) + (size_t)W * nH);
+    smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 1) + (size_t)W * nH);
   }
   if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_covtable<T, MC>,
