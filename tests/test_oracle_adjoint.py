@@ -1,0 +1,62 @@
+"""Pins of the oracle's reverse-mode gradient: FP64 central finite differences of
+L = 1/2 |mean(X^a) - x_ref|^2 in random directions of X^b, y and diag(R), on a
+plain case and on a case where the ridge is active (p >= N - 1)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.adjoint import analysis_with_gradient, loss_and_gradient, loss_mean_analysis
+from synthetic import WORKLOADS, make_inputs
+
+
+def _loss(w, Xb, y, R, Z, obs_idx, x_ref):
+    Xa = O.assimilate(w, Xb, y, R, Z, obs_idx)
+    return loss_mean_analysis(Xa, x_ref)[0]
+
+
+@pytest.mark.parametrize("case", ["plain", "ridge"])
+def test_gradient_matches_central_differences(case):
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    if case == "ridge":
+        w = w.with_(N=12, ridge_c=1e-3, sub_lon=16, sub_lat=8)
+    inp = make_inputs(w)
+    x_ref = inp.truth
+    L, Xb_bar, y_bar, R_bar = loss_and_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx,
+                                                x_ref)
+    rng = np.random.default_rng(11)
+    # directions: X^b, y, and a relative change of diag(R)
+    dX = rng.standard_normal(inp.Xb.shape)
+    dy = rng.standard_normal(inp.y.shape)
+    dR = rng.standard_normal(inp.R.shape) * inp.R
+    # the ridge case (N = 12) is ill-conditioned: rounding in L dominates below
+    # h ~ 1e-5, so it takes a larger step (truncation error stays ~1e-8 relative)
+    h = 1e-6 if case == "plain" else 1e-4
+    tol = 1e-6 if case == "plain" else 1e-5
+    for name, d, grad in (("Xb", dX, Xb_bar), ("y", dy, y_bar), ("R", dR, R_bar)):
+        args_p = [inp.Xb, inp.y, inp.R]
+        args_m = [inp.Xb, inp.y, inp.R]
+        k = {"Xb": 0, "y": 1, "R": 2}[name]
+        args_p = [a + h * d if i == k else a for i, a in enumerate(args_p)]
+        args_m = [a - h * d if i == k else a for i, a in enumerate(args_m)]
+        fd = (_loss(w, args_p[0], args_p[1], args_p[2], inp.Z, inp.obs_idx, x_ref)
+              - _loss(w, args_m[0], args_m[1], args_m[2], inp.Z, inp.obs_idx, x_ref)) / (2 * h)
+        an = float(np.sum(grad * d))
+        assert abs(fd - an) <= tol * max(abs(fd), abs(an)) + 1e-10 * abs(L), (name, fd, an)
+
+
+def test_gradient_of_analysis_is_linear_in_the_output_gradient():
+    """The reverse pass is linear in dL/dX^a: gradients for W1 + 2 W2 equal those for
+    W1 plus twice those for W2 (checks no term depends on the seed twice)."""
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    inp = make_inputs(w)
+    rng = np.random.default_rng(3)
+    W1 = rng.standard_normal(inp.Xb.shape)
+    W2 = rng.standard_normal(inp.Xb.shape)
+    g1 = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, W1)
+    g2 = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, W2)
+    g3 = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, W1 + 2 * W2)
+    for a, b, c in zip(g1[1:], g2[1:], g3[1:]):
+        assert np.allclose(c, a + 2 * b, rtol=1e-9, atol=1e-12 * np.abs(c).max())
+    # and the forward part equals the plain analysis
+    Xa = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
+    assert np.allclose(g1[0], Xa, rtol=0, atol=1e-12 * np.abs(Xa).max())
