@@ -170,7 +170,17 @@ enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
 enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
                                 const void* Rdiag, const void* Z, void* Xa);
 
-/* Gradient of a scalar loss through enkfmc_analyze (reserved). */
+/* Reverse pass of the last analysis.  Given Xa_bar = dL/dX^a ([N][n]) of a
+ * scalar loss L, writes dL/dy (y_bar, [m]), dL/d diag(R) (Rdiag_bar, [m]) and
+ * dL/dX^b (Xb_bar, [N][n]) through every step: the interior write-back
+ * (Eq. 10), the sub-domain solves (Eq. 11, with the factors of the last
+ * enkfmc_assemble), the assembly of A (Eq. 8), the regressions (Eq. 1-2,
+ * Gram factors recomputed from the covariance table, not stored) and the
+ * anomalies (Eq. 5).  Requires enkfmc_analyze on this handle, whose inputs
+ * (Xb, y, Rdiag, Z) and the Tvals/D of enkfmc_assemble must still hold the
+ * same values.  Outputs are overwritten; they may not alias the inputs.
+ * Contributions of overlapping boundaries are summed with atomic adds, so
+ * the last bits can vary from run to run. */
 enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void* y_bar,
                                      void* Rdiag_bar, void* Xb_bar);
 
@@ -229,7 +239,10 @@ enum {
   ENKFMC_K_WRITEBACK = 7,   /* Eq. 10 on sub-domain interiors                    */
   ENKFMC_K_COVTABLE = 8,    /* covariances of every pair inside one local box    */
   ENKFMC_K_RESIDUAL = 9,    /* rhs - A dX for the sub-domain refinement step     */
-  ENKFMC_NKERNEL = 10
+  ENKFMC_K_ADJOINT = 10,    /* reverse pass: seed, observation terms, T Lambda,
+                               T dX, anomaly projection                          */
+  ENKFMC_K_ADJ_REGRESS = 11,/* reverse pass through the regressions              */
+  ENKFMC_NKERNEL = 12
 };
 
 /* Kernel timing.  While enabled, every kernel launch is bracketed by CUDA

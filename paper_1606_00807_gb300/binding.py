@@ -61,7 +61,7 @@ SIGNATURES = {
     "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
                                           c_void_p]),
 }
-NKERNEL = 10
+NKERNEL = 12
 FLAG_NO_SOLVE_REFINEMENT = 1
 
 _LIB = None
@@ -179,6 +179,10 @@ class Handle:
     def analyze(self, Xb, y, R, Z, Xa):
         _check(self.lib.enkfmc_analyze(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
                "enkfmc_analyze")
+
+    def analyze_adjoint(self, Xa_bar, y_bar, R_bar, Xb_bar):
+        _check(self.lib.enkfmc_analyze_adjoint(self.h, _ptr(Xa_bar), _ptr(y_bar), _ptr(R_bar),
+                                               _ptr(Xb_bar)), "enkfmc_analyze_adjoint")
 
     def cycle_host(self, Xb, y, R, Z, Xa):
         _check(self.lib.enkfmc_cycle_host(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),

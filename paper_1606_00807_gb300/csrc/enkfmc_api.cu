@@ -300,7 +300,8 @@ void release(enkfmc_handle* h) {
                   h->d_U,   h->d_C,
                   h->d_Te,     h->d_De,   h->d_band,   h->d_rhs,    h->d_res, h->d_vhi,
                   h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
-                  h->d_T,      h->d_D};
+                  h->d_T,      h->d_D,    h->d_lam,    h->d_aT,     h->d_bT,  h->d_dxT,
+                  h->d_lamT,   h->d_Ubar};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
@@ -512,6 +513,67 @@ void compute_obs_work(enkfmc_handle* h, const std::vector<int32_t>& obs_of) {
   h->work_bytes[ENKFMC_K_RHS] = es * (N * (double)h->ext_rows + 2.0 * N * ext_obs);
 }
 
+template <typename T>
+enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar, T* Xb_bar) {
+  const Geom& g = h->g;
+  const size_t es = sizeof(T);
+  enkfmc_status st;
+  if (!h->d_lam) {
+    const size_t rows = (size_t)h->ext_rows;
+    if ((st = dalloc(h, &h->d_lam, es * rows * g.N))) return st;
+    if ((st = dalloc(h, &h->d_aT, es * rows * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_bT, es * rows * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_dxT, es * rows * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_lamT, es * rows * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_Ubar, es * (size_t)g.n * g.ldN))) return st;
+  }
+  CUDA_TRY(cudaMemsetAsync(h->d_Ubar, 0, es * (size_t)g.n * g.ldN, h->stream));
+  CUDA_TRY(cudaMemsetAsync(Xb_bar, 0, es * (size_t)g.n * g.N, h->stream));
+  if (h->m > 0) {
+    CUDA_TRY(cudaMemsetAsync(y_bar, 0, es * (size_t)h->m, h->stream));
+    CUDA_TRY(cudaMemsetAsync(R_bar, 0, es * (size_t)h->m, h->stream));
+  }
+  const T* dX2 = (h->refine_solve && sizeof(T) == sizeof(float)) ? (const T*)h->d_res : nullptr;
+  const T* Tg = (const T*)h->T_assembled;
+  const T* Dg = (const T*)h->D_assembled;
+  st = timed(h, ENKFMC_K_ADJOINT, [&] {
+    return launch_adj_seed<T>(g, h->d_blocks, h->nblock, h->nb_max, Xa_bar, (T*)h->d_lam,
+                              h->stream);
+  });
+  if (st) return st;
+  st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
+    return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, g.N, (const T*)h->d_band,
+                               (T*)h->d_lam, h->stream);
+  });
+  if (st) return st;
+  if (h->m > 0) {
+    st = timed(h, ENKFMC_K_ADJOINT, [&] {
+      return launch_adj_obs<T>(g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m,
+                               (const T*)h->last_Xb, (const T*)h->last_y, (const T*)h->last_R,
+                               (const T*)h->last_Z, (const T*)h->d_lam, (const T*)h->d_rhs, dX2,
+                               Xb_bar, y_bar, R_bar, h->stream);
+    });
+    if (st) return st;
+  }
+  st = timed(h, ENKFMC_K_ADJOINT, [&] {
+    return launch_adj_ab<T>(g, h->d_blocks, h->nblock, h->nb_max, Tg, (const T*)h->d_Te,
+                            (const T*)h->d_lam, (const T*)h->d_rhs, dX2, (T*)h->d_aT,
+                            (T*)h->d_bT, (T*)h->d_dxT, (T*)h->d_lamT, h->stream);
+  });
+  if (st) return st;
+  st = timed(h, ENKFMC_K_ADJ_REGRESS, [&] {
+    return launch_adj_regress<T>(g, h->d_blocks, h->nblock, h->nb_max, (const T*)h->d_U,
+                                 (const T*)h->d_C, Tg, Dg, (const T*)h->d_Te, (const T*)h->d_De,
+                                 (const T*)h->d_aT, (const T*)h->d_bT, (const T*)h->d_dxT,
+                                 (const T*)h->d_lamT, (T*)h->d_Ubar, h->prob.ridge_c,
+                                 h->d_status, h->stream);
+  });
+  if (st) return st;
+  return timed(h, ENKFMC_K_ADJOINT, [&] {
+    return launch_adj_finish<T>(g, (const T*)h->d_Ubar, Xa_bar, Xb_bar, h->stream);
+  });
+}
+
 }  // namespace
 
 extern "C" {
@@ -634,6 +696,7 @@ enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tval
     if (!st) st = run_assemble<float>(h, (const float*)Tvals, (const float*)D, (const float*)Rdiag);
   }
   h->assembled = (st == ENKFMC_OK);
+  h->analyzed = false;
   h->T_assembled = Tvals;
   h->D_assembled = D;
   return st;
@@ -644,11 +707,19 @@ enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y, co
   if (!h || !Xb || !Xa || Xa == Xb) return ENKFMC_EINVAL;
   if (h->m > 0 && (!y || !Rdiag || !Z)) return ENKFMC_EINVAL;
   if (!h->assembled) return ENKFMC_ESTATE;
+  h->last_Xb = Xb;
+  h->last_y = y;
+  h->last_R = Rdiag;
+  h->last_Z = Z;
+  enkfmc_status st;
   if (is_fp64(h))
-    return run_analyze<double>(h, (const double*)Xb, (const double*)y, (const double*)Rdiag,
-                               (const double*)Z, (double*)Xa);
-  return run_analyze<float>(h, (const float*)Xb, (const float*)y, (const float*)Rdiag,
+    st = run_analyze<double>(h, (const double*)Xb, (const double*)y, (const double*)Rdiag,
+                             (const double*)Z, (double*)Xa);
+  else
+    st = run_analyze<float>(h, (const float*)Xb, (const float*)y, (const float*)Rdiag,
                             (const float*)Z, (float*)Xa);
+  h->analyzed = (st == ENKFMC_OK);
+  return st;
 }
 
 enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y, const void* Rdiag,
@@ -683,9 +754,16 @@ enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
   return enkfmc_get_status(h, nullptr);
 }
 
-enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void*, void*, void*, void*) {
-  if (!h) return ENKFMC_EINVAL;
-  return ENKFMC_ENOTIMPL;
+enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void* y_bar,
+                                     void* Rdiag_bar, void* Xb_bar) {
+  if (!h || !Xa_bar || !Xb_bar || Xb_bar == Xa_bar) return ENKFMC_EINVAL;
+  if (h->m > 0 && (!y_bar || !Rdiag_bar)) return ENKFMC_EINVAL;
+  if (!h->analyzed || !h->assembled) return ENKFMC_ESTATE;
+  if (is_fp64(h))
+    return run_adjoint<double>(h, (const double*)Xa_bar, (double*)y_bar, (double*)Rdiag_bar,
+                               (double*)Xb_bar);
+  return run_adjoint<float>(h, (const float*)Xa_bar, (float*)y_bar, (float*)Rdiag_bar,
+                            (float*)Xb_bar);
 }
 
 enkfmc_status enkfmc_get_status(enkfmc_handle* h, int64_t* info) {
@@ -768,7 +846,7 @@ const char* enkfmc_kernel_name(int32_t kind) {
   static const char* names[ENKFMC_NKERNEL] = {"anomalies", "regress",   "regress_halo",
                                               "assemble",  "bandchol",  "rhs",
                                               "bandsolve", "writeback", "covtable",
-                                              "residual"};
+                                              "residual",  "adjoint",   "adj_regress"};
   return (kind >= 0 && kind < ENKFMC_NKERNEL) ? names[kind] : "unknown";
 }
 

@@ -185,6 +185,13 @@ struct enkfmc_handle {
   void *d_Xb = nullptr, *d_y = nullptr, *d_R = nullptr, *d_Z = nullptr, *d_Xa = nullptr;
   void *d_T = nullptr, *d_D = nullptr;
 
+  // inputs of the last enkfmc_analyze (the reverse pass reads them again)
+  const void *last_Xb = nullptr, *last_y = nullptr, *last_R = nullptr, *last_Z = nullptr;
+  bool analyzed = false;
+  // reverse-pass buffers (allocated on the first enkfmc_analyze_adjoint)
+  void *d_lam = nullptr, *d_aT = nullptr, *d_bT = nullptr, *d_dxT = nullptr, *d_lamT = nullptr;
+  void* d_Ubar = nullptr;
+
   // kernel timing (events bracket each launch while enabled)
   struct Rec {
     int kind;
@@ -266,6 +273,29 @@ template <typename T>
 cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
                              int sub_lat, const T* Xb, const T* dX, const T* dX2, T* Xa,
                              cudaStream_t s);
+
+// Reverse pass (k_adjoint.cu and k_adj_regress in k_estimate.cu).
+template <typename T>
+cudaError_t launch_adj_seed(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                            const T* Xa_bar, T* W, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_obs(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                           const int32_t* obs_of, int64_t m, const T* Xb, const T* y, const T* R,
+                           const T* Z, const T* lam, const T* dX, const T* dX2, T* Xb_bar,
+                           T* y_bar, T* R_bar, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_ab(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                          const T* Tg, const T* Te, const T* lam, const T* dX, const T* dX2,
+                          T* aT, T* bT, T* dxT, T* lamT, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                               const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
+                               const T* De, const T* aT, const T* bT, const T* dxT,
+                               const T* lamT, T* Ubar, double ridge_c, int32_t* status,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_finish(const Geom& g, const T* Ubar, const T* Xa_bar, T* Xb_bar,
+                              cudaStream_t s);
 
 // Single-precision refinement residual res = rhs - A dX (two passes; vhi, vlo
 // are scratch of the size of dX).

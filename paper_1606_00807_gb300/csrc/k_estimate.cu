@@ -506,6 +506,260 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the regressions of one (sub-domain, variable) block.  One warp
+// per extended row j (a regression instance of Algorithm 3): with
+// a_j = (T Lambda)_j, b_j = (T dX)_j (row-major, N samples),
+//   betabar_i = (<a_j, dX_qi> + <b_j, Lambda_qi>) / D_j - <U_qi, ebar>,
+//   Dbar_j = <a_j, b_j> / D_j^2, ebar = 2 Dbar e / (N - 1),
+//   v = (G + lambda I)^-1 betabar (factor recomputed from the covariance table),
+//   f = ebar + U_P^T v,  Ubar_qi += v_i e - beta_i f - kappa U_qi,  Ubar_j += f,
+// kappa = 2 (c / p) v.beta when the ridge is active.  Ubar is accumulated with
+// atomic adds (rows share predecessors).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_regress(
+    const Geom g, const Block* __restrict__ blocks, const T* __restrict__ U,
+    const T* __restrict__ C, int nH, const T* __restrict__ Tg, const T* __restrict__ Dg,
+    const T* __restrict__ Te, const T* __restrict__ De, const T* __restrict__ aT,
+    const T* __restrict__ bT, const T* __restrict__ dxT, const T* __restrict__ lamT,
+    T* __restrict__ Ubar, double ridge_c, int32_t* status, int ldp, int ldg, int warp_bytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  signed char* off = reinterpret_cast<signed char*>(smem);
+  const int pmax = g.pmax;
+  const int offbytes = (3 * pmax + 15) / 16 * 16;
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
+    int dk, dy, dx;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    off[s] = (signed char)dk;
+    off[pmax + s] = (signed char)dy;
+    off[2 * pmax + s] = (signed char)dx;
+  }
+  __syncthreads();
+  unsigned char* base = smem + offbytes + (size_t)warp * warp_bytes;
+  int* q = reinterpret_cast<int*>(base);    // [ldp] labels (q[p] = j)
+  int* sl = q + ldp;                         // [ldp] slots
+  int* qr = sl + ldp;                        // [ldp] extended rows (block-relative)
+  T* L = reinterpret_cast<T*>(qr + ldp);     // [ldp][ldg]
+  T* va = L + (size_t)ldp * ldg;             // [ldp] betabar -> v
+  T* vb = va + ldp;                          // [ldp] beta
+  T* invd = vb + ldp;                        // [ldp]
+  const int N = g.N, ldN = g.ldN;
+  const Block b = blocks[blockIdx.y];
+  const int loc = blockIdx.x * wpc + warp;
+  if (loc >= b.nb) return;
+  const int plane = b.ey * b.ex;
+  const int k = loc / plane;
+  const int yy0 = (loc - k * plane) / b.ex, xx0 = loc - k * plane - yy0 * b.ex;
+  const int y = b.lat_lo + yy0, x = imod(b.lon_lo + xx0, g.nlon);
+  const int v = b.var;
+  const int64_t rowj = b.row_off + loc;
+  // predecessors inside the extended box
+  int p = 0;
+  for (int s0 = 0; s0 < pmax; s0 += 32) {
+    const int s = s0 + lane;
+    bool pres = false;
+    int qq = 0, rr = 0;
+    if (s < pmax) {
+      int kq, yq, xq, yyq, xxq;
+      pres = slot_pred(g, k, y, x, s, kq, yq, xq) && in_ext(b, g.nlon, yq, xq, yyq, xxq);
+      if (pres) {
+        qq = (int)coords_label(g, v, kq, yq, xq);
+        rr = (kq * b.ey + yyq) * b.ex + xxq;
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, pres);
+    const int idx = p + __popc(mask & ((1u << lane) - 1u));
+    if (pres) {
+      q[idx] = qq;
+      sl[idx] = s;
+      qr[idx] = rr;
+    }
+    p += __popc(mask);
+  }
+  const int jlab = (int)coords_label(g, v, k, y, x);
+  if (lane == 0) {
+    q[p] = jlab;
+    sl[p] = -1;
+  }
+  __syncwarp();
+  // beta and D of this instance
+  const bool inner = in_interior(b, y, x);
+  const T* trow = inner ? Tg + (int64_t)jlab * pmax : Te + rowj * pmax;
+  const T Dj = inner ? Dg[jlab] : De[rowj];
+  for (int i = lane; i < p; i += 32) vb[i] = -trow[sl[i]];
+  __syncwarp();
+  // e = u - U_P^T beta; a_j, b_j in registers
+  T e[kMaxRounds], aj[kMaxRounds], bj[kMaxRounds];
+#pragma unroll
+  for (int t = 0; t < kMaxRounds; ++t) {
+    const int m = lane + 32 * t;
+    e[t] = m < N ? U[(int64_t)jlab * ldN + m] : T(0);
+    aj[t] = m < N ? aT[rowj * ldN + m] : T(0);
+    bj[t] = m < N ? bT[rowj * ldN + m] : T(0);
+  }
+  for (int i = 0; i < p; ++i) {
+    const T bi = vb[i];
+    const T* Ui = U + (int64_t)q[i] * ldN;
+#pragma unroll
+    for (int t = 0; t < kMaxRounds; ++t) {
+      const int m = lane + 32 * t;
+      if (m < N) e[t] = fma(-Ui[m], bi, e[t]);
+    }
+  }
+  T ab = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxRounds; ++t) ab = fma(aj[t], bj[t], ab);
+  ab = warp_sum(ab);
+  const T Dbar = ab / (Dj * Dj);
+  T eb[kMaxRounds];
+#pragma unroll
+  for (int t = 0; t < kMaxRounds; ++t) eb[t] = T(2) * Dbar * e[t] / T(N - 1);
+  // betabar
+  const T invD = T(1) / Dj;
+  for (int i = 0; i < p; ++i) {
+    const T* Ui = U + (int64_t)q[i] * ldN;
+    const T* xi = dxT + (b.row_off + qr[i]) * ldN;
+    const T* li = lamT + (b.row_off + qr[i]) * ldN;
+    T s1 = 0, s2 = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxRounds; ++t) {
+      const int m = lane + 32 * t;
+      if (m < N) {
+        s1 = fma(aj[t], xi[m], s1);
+        s1 = fma(bj[t], li[m], s1);
+        s2 = fma(Ui[m], eb[t], s2);
+      }
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == (i & 31)) va[i] = s1 * invD - s2;
+  }
+  __syncwarp();
+  T f[kMaxRounds];
+#pragma unroll
+  for (int t = 0; t < kMaxRounds; ++t) f[t] = eb[t];
+  T kappa = 0;
+  if (p > 0) {
+    // Gram factor from the covariance table (as in the forward pass)
+    const int p1 = p + 1;
+    const int npair = p * (p + 1) / 2;
+    for (int pi = lane; pi < npair; pi += 32) {
+      int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= pi) ++i;
+      while (i * (i + 1) / 2 > pi) --i;
+      const int l = pi - i * (i + 1) / 2;
+      const int si = sl[i], sm = sl[l];
+      const int dk = off[sm] - off[si];
+      const int dy = off[pmax + sm] - off[pmax + si];
+      const int dx = off[2 * pmax + sm] - off[2 * pmax + si];
+      L[i * ldg + l] = cov_lookup(C, nH, g.r, g.vr, q[i], q[l], dk, dy, dx);
+    }
+    (void)p1;
+    __syncwarp();
+    T lam = 0;
+    if (ridge_c > 0.0 && p >= N - 1) {
+      T tr = 0;
+      for (int i = lane; i < p; i += 32) tr += L[i * ldg + i];
+      tr = warp_sum(tr);
+      lam = T(ridge_c) * tr / T(p);
+      __syncwarp();
+      for (int i = lane; i < p; i += 32) L[i * ldg + i] += lam;
+    }
+    __syncwarp();
+    int err = 0;
+    for (int kc = 0; kc < p; ++kc) {
+      const T* Lk = L + kc * ldg;
+      T vals[kMaxRounds * 2];
+#pragma unroll
+      for (int t = 0; t < kMaxRounds * 2; ++t) {
+        const int i = lane + 32 * t;
+        vals[t] = T(0);
+        if (i >= kc && i < p) {
+          const T* Li = L + i * ldg;
+          T dot = T(0);
+          for (int l = 0; l < kc; ++l) dot = fma(Li[l], Lk[l], dot);
+          vals[t] = Li[kc] - dot;
+        }
+      }
+      __syncwarp();
+      if (lane == (kc & 31)) {
+        T d = vals[0];
+#pragma unroll
+        for (int t = 1; t < kMaxRounds * 2; ++t)
+          if (t == (kc >> 5)) d = vals[t];
+        const bool fin = finite_val(d);
+        const T sd = (fin && d > T(0)) ? sqrt(d) : T(0);
+        invd[kc] = sd > T(0) ? T(1) / sd : (fin ? T(0) : T(NAN));
+        L[kc * ldg + kc] = sd;
+      }
+      __syncwarp();
+      const T inv = invd[kc];
+      if (!(inv > T(0))) {
+        err = (inv == inv) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+        break;
+      }
+#pragma unroll
+      for (int t = 0; t < kMaxRounds * 2; ++t) {
+        const int i = lane + 32 * t;
+        if (i > kc && i < p) L[i * ldg + kc] = vals[t] * inv;
+      }
+      __syncwarp();
+    }
+    if (err) {
+      if (lane == 0) record_error(status, err, rowj);
+      return;
+    }
+    // v = (L L^T)^-1 betabar in va
+    for (int kc = 0; kc < p; ++kc) {
+      const T zk = va[kc] * invd[kc];
+      __syncwarp();
+      if (lane == 0) va[kc] = zk;
+      for (int i = kc + 1 + lane; i < p; i += 32) va[i] -= L[i * ldg + kc] * zk;
+      __syncwarp();
+    }
+    for (int kc = p - 1; kc >= 0; --kc) {
+      const T zk = va[kc] * invd[kc];
+      __syncwarp();
+      if (lane == 0) va[kc] = zk;
+      for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * zk;
+      __syncwarp();
+    }
+    // f = ebar + U_P^T v; kappa
+    T vbeta = 0;
+    for (int i = lane; i < p; i += 32) vbeta = fma(va[i], vb[i], vbeta);
+    vbeta = warp_sum(vbeta);
+    if (lam > T(0)) kappa = T(2) * T(ridge_c) / T(p) * vbeta;
+    for (int i = 0; i < p; ++i) {
+      const T vi = va[i];
+      const T* Ui = U + (int64_t)q[i] * ldN;
+#pragma unroll
+      for (int t = 0; t < kMaxRounds; ++t) {
+        const int m = lane + 32 * t;
+        if (m < N) f[t] = fma(Ui[m], vi, f[t]);
+      }
+    }
+    // Ubar_qi += v_i e - beta_i f - kappa U_qi
+    for (int i = 0; i < p; ++i) {
+      const T vi = va[i], bi = vb[i];
+      const T* Ui = U + (int64_t)q[i] * ldN;
+      T* Ub = Ubar + (int64_t)q[i] * ldN;
+#pragma unroll
+      for (int t = 0; t < kMaxRounds; ++t) {
+        const int m = lane + 32 * t;
+        if (m < N) atomicAdd(Ub + m, vi * e[t] - bi * f[t] - kappa * Ui[m]);
+      }
+    }
+  }
+  T* Uj = Ubar + (int64_t)jlab * ldN;
+#pragma unroll
+  for (int t = 0; t < kMaxRounds; ++t) {
+    const int m = lane + 32 * t;
+    if (m < N) atomicAdd(Uj + m, f[t]);
+  }
+}
+
 }  // namespace
 
 int cov_offset_count(int r, int vr) {
@@ -575,7 +829,42 @@ cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t*
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                               const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
+                               const T* De, const T* aT, const T* bT, const T* dxT,
+                               const T* lamT, T* Ubar, double ridge_c, int32_t* status,
+                               cudaStream_t s) {
+  if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
+    return cudaErrorInvalidConfiguration;
+  const int nH = cov_offset_count(g.r, g.vr);
+  const int ldp = ((g.pmax + 1) + 3) / 4 * 4;
+  const int ldg = ldp | 1;
+  size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 3 * (size_t)ldp);
+  wb = (wb + 15) / 16 * 16;
+  const int offbytes = (3 * g.pmax + 15) / 16 * 16;
+  int wpc = (int)((96 * 1024 - offbytes) / wb);
+  if (wpc > 8) wpc = 8;
+  if (wpc < 1) {
+    wpc = (int)((200 * 1024 - offbytes) / wb);
+    if (wpc < 1) return cudaErrorInvalidConfiguration;
+  }
+  const size_t smem = offbytes + wb * wpc;
+  cudaError_t e = cudaFuncSetAttribute(k_adj_regress<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
+  k_adj_regress<T><<<grid, 32 * wpc, smem, s>>>(g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT,
+                                                 dxT, lamT, Ubar, ridge_c, status, ldp, ldg,
+                                                 (int)wb);
+  return cudaGetLastError();
+}
+
 #define INST(T)                                                                                  \
+  template cudaError_t launch_adj_regress<T>(const Geom&, const Block*, int, int, const T*,     \
+                                             const T*, const T*, const T*, const T*, const T*,  \
+                                             const T*, const T*, const T*, const T*, T*, double,\
+                                             int32_t*, cudaStream_t);                            \
   template cudaError_t launch_anomalies<T>(const Geom&, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_covtable<T>(const Geom&, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_regress<T>(const Geom&, const T*, const T*, const int32_t*,       \

@@ -1,0 +1,134 @@
+"""Reverse pass on the GPU (enkfmc_analyze_adjoint) against the FP64 oracle's
+gradient (itself pinned by central differences), a GPU finite-difference check
+in FP64, and the torch.autograd.Function path."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.adjoint import analysis_with_gradient, loss_mean_analysis
+from synthetic import WORKLOADS, make_inputs
+
+from _harness import np_dtype, torch_dtype
+
+pytestmark = pytest.mark.gpu
+
+# FP64: atomic sums change the rounding order only.  FP32: the reverse solves
+# and the recomputed Gram factors run in single precision without refinement,
+# so the gradient carries the forward's kappa * 2^-24 amplification (kappa <= 6e3).
+TOL = {0: 1e-9, 1: 1e-3}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _gpu_grad(torch, w, inp, precision, seed):
+    from paper_1606_00807_gb300 import binding as B
+    dt = torch_dtype(precision)
+    h = B.Handle.from_workload(w, precision=precision,
+                               stream=torch.cuda.current_stream().cuda_stream)
+    h.set_observations(inp.obs_idx)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    Xb, y, R, Z = dev(inp.Xb), dev(inp.y), dev(inp.R), dev(inp.Z)
+    T = torch.empty((w.n, h.info.pmax), device="cuda", dtype=dt)
+    D = torch.empty(w.n, device="cuda", dtype=dt)
+    Xa = torch.empty_like(Xb)
+    h.estimate(Xb, T, D)
+    h.assemble(Xb, T, D, R)
+    h.analyze(Xb, y, R, Z, Xa)
+    W = dev(seed)
+    Xb_bar, y_bar, R_bar = torch.empty_like(Xb), torch.empty_like(y), torch.empty_like(R)
+    h.analyze_adjoint(W, y_bar, R_bar, Xb_bar)
+    h.check("adjoint")
+    torch.cuda.synchronize()
+    out = [a.cpu().numpy().astype(np.float64) for a in (Xa, Xb_bar, y_bar, R_bar)]
+    h.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["tiny_32x16_n20_r2", "small_48x26x3x1+1_n80_r2",
+                                  "small_40x30x2x2+1_n48_r2"])
+def test_adjoint_matches_oracle(torch_cuda, name, precision):
+    w = WORKLOADS[name]
+    inp = make_inputs(w, np_dtype(precision))
+    Xa_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
+    _, W = loss_mean_analysis(Xa_ref, inp.truth)   # dL/dXa of the mean-analysis loss
+    W = W + 0.01 * np.random.default_rng(2).standard_normal(W.shape)  # and a generic part
+    W = W.astype(np_dtype(precision))
+    _, Xb_bar, y_bar, R_bar = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z,
+                                                     inp.obs_idx, W)
+    got = _gpu_grad(torch_cuda, w, inp, precision, W)
+    for name_, g, r in (("Xb", got[1], Xb_bar), ("y", got[2], y_bar), ("R", got[3], R_bar)):
+        err = O.rel_err(g, r)
+        assert err < TOL[precision], (name_, err)
+
+
+def test_gpu_gradient_matches_gpu_finite_differences(torch_cuda):
+    """FP64 on the GPU: central differences of L = 1/2 |mean(X^a) - x_ref|^2 computed
+    by the GPU forward against the GPU reverse pass, in random directions."""
+    torch = torch_cuda
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    inp = make_inputs(w, np.float64)
+
+    def loss(Xb, y, R):
+        h = B.Handle.from_workload(w, precision=B.FP64,
+                                   stream=torch.cuda.current_stream().cuda_stream)
+        h.set_observations(inp.obs_idx)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+        X, yy, RR, Z = dev(Xb), dev(y), dev(R), dev(inp.Z)
+        T = torch.empty((w.n, h.info.pmax), device="cuda", dtype=torch.float64)
+        D = torch.empty(w.n, device="cuda", dtype=torch.float64)
+        Xa = torch.empty_like(X)
+        h.estimate(X, T, D)
+        h.assemble(X, T, D, RR)
+        h.analyze(X, yy, RR, Z, Xa)
+        h.check()
+        L, Wb = loss_mean_analysis(Xa.cpu().numpy(), inp.truth)
+        h.close()
+        return L, Wb
+
+    L0, W = loss(inp.Xb, inp.y, inp.R)
+    _, gX, gy, gR = _gpu_grad(torch, w, inp, 0, W)
+    rng = np.random.default_rng(9)
+    for name, d, grad in (("Xb", rng.standard_normal(inp.Xb.shape), gX),
+                          ("y", rng.standard_normal(inp.y.shape), gy),
+                          ("R", rng.standard_normal(inp.R.shape) * inp.R, gR)):
+        h = 1e-6
+        args = [inp.Xb, inp.y, inp.R]
+        k = {"Xb": 0, "y": 1, "R": 2}[name]
+        ap = [a + h * d if i == k else a for i, a in enumerate(args)]
+        am = [a - h * d if i == k else a for i, a in enumerate(args)]
+        fd = (loss(*ap)[0] - loss(*am)[0]) / (2 * h)
+        an = float(np.sum(grad * d))
+        assert abs(fd - an) <= 1e-6 * max(abs(fd), abs(an)) + 1e-10 * L0, (name, fd, an)
+
+
+def test_autograd_function(torch_cuda):
+    torch = torch_cuda
+    from paper_1606_00807_gb300 import binding as B
+    from paper_1606_00807_gb300.autograd import analysis
+    w = WORKLOADS["small_48x26x3x1+1_n80_r2"]
+    inp = make_inputs(w, np.float64)
+    h = B.Handle.from_workload(w, precision=B.FP64)
+    h.set_observations(inp.obs_idx)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+    Xb = dev(inp.Xb).requires_grad_(True)
+    y = dev(inp.y).requires_grad_(True)
+    R = dev(inp.R).requires_grad_(True)
+    Z = dev(inp.Z)
+    x_ref = dev(inp.truth)
+    Xa = analysis(Xb, y, R, Z, h)
+    L = 0.5 * ((Xa.mean(0) - x_ref) ** 2).sum()
+    L.backward()
+    _, W = loss_mean_analysis(Xa.detach().cpu().numpy(), inp.truth)
+    _, rX, ry, rR = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, W)
+    assert O.rel_err(Xb.grad.cpu().numpy(), rX) < 1e-9
+    assert O.rel_err(y.grad.cpu().numpy(), ry) < 1e-9
+    assert O.rel_err(R.grad.cpu().numpy(), rR) < 1e-9
+    h.close()
