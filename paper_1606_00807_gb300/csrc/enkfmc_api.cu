@@ -179,7 +179,7 @@ enkfmc_status build(enkfmc_handle* h) {
     // the staged rows of a 32-column tile must fit in shared memory
     const size_t stage = h->esize * (size_t)(32 + h->hb_max + 1 + g.r) * (g.pmax + 1);
     const size_t npairs = (size_t)(g.pmax + 1) * (g.pmax + 2) / 2;
-    if (stage + 16 * npairs + 4 * (size_t)(h->hb_max + 2) + 16 > 227 * 1024)
+    if (stage + 16 * npairs + 12 * (npairs + 1) + 32 * (size_t)(g.pmax + 1) + 32 > 227 * 1024)
       h->pair_assembly = false;
   }
   if (h->pair_assembly) {

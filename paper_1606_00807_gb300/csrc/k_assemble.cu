@@ -123,34 +123,39 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
   const int c0 = blockIdx.x * kCols;
   if (c0 >= b.nb) return;
   const int pmax = g.pmax, ldt = pmax + 1;  // staged row: pmax coefficients then 1/D
+  const int ns = pmax + 1;                   // slots plus the row itself
   T* Ts = reinterpret_cast<T*>(smem);                         // [stage_rows][ldt]
   const size_t ts_bytes = (sizeof(T) * (size_t)stage_rows * ldt + 15) / 16 * 16;
   int4* Ps = reinterpret_cast<int4*>(smem + ts_bytes);        // [npair_max], 16-byte aligned
-  int* Dp = reinterpret_cast<int*>(Ps + npair_max);           // [hb + 2]
+  int2* Dl = reinterpret_cast<int2*>(Ps + npair_max);         // non-empty diagonals: [start, end)
+  int* Dd = reinterpret_cast<int*>(Dl + (g.pmax + 1) * (g.pmax + 2) / 2 + 1);  // their d
+  unsigned char* Vm = reinterpret_cast<unsigned char*>(Dd + (g.pmax + 1) * (g.pmax + 2) / 2 + 1);
+  __shared__ int n_nz;
   const int hp1 = b.hb + 1;
   const int jlo = c0 - g.r;
   const int nrow = min(stage_rows, kCols + hp1 + g.r);
   const int plane = b.ey * b.ex;
+  const int ncol = min(kCols, b.nb - c0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // zero the tile's band columns (non-empty diagonals are overwritten below)
+  for (int e = threadIdx.x; e < ncol * hp1; e += blockDim.x) band[b.band_off + (int64_t)c0 * hp1 + e] = T(0);
   // stage rows j in [jlo, jlo + nrow): one warp per row, lanes over its slots
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int jj = warp; jj < nrow; jj += nw) {
-      const int j = jlo + jj;
-      T* dst = Ts + jj * ldt;
-      if (j < 0 || j >= b.nb) {
-        for (int s = lane; s < ldt; s += 32) dst[s] = T(0);
-        continue;
-      }
-      const int kj = j / plane, yyj = (j - kj * plane) / b.ex, xxj = j - kj * plane - yyj * b.ex;
-      const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
-      const bool in = in_interior(b, yj, xj);
-      const int64_t rsrc = in ? coords_label(g, b.var, kj, yj, xj) : b.row_off + j;
-      const T* src = (in ? Tg : Te) + rsrc * pmax;
-      for (int s = lane; s < pmax; s += 32) dst[s] = src[s];
-      if (lane == 0) dst[pmax] = T(1) / (in ? Dg[rsrc] : De[rsrc]);
+  for (int jj = warp; jj < nrow; jj += nw) {
+    const int j = jlo + jj;
+    T* dst = Ts + jj * ldt;
+    if (j < 0 || j >= b.nb) {
+      for (int s = lane; s < ldt; s += 32) dst[s] = T(0);
+      continue;
     }
+    const int kj = j / plane, yyj = (j - kj * plane) / b.ex, xxj = j - kj * plane - yyj * b.ex;
+    const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
+    const bool in = in_interior(b, yj, xj);
+    const int64_t rsrc = in ? coords_label(g, b.var, kj, yj, xj) : b.row_off + j;
+    const T* src = (in ? Tg : Te) + rsrc * pmax;
+    for (int s = lane; s < pmax; s += 32) dst[s] = src[s];
+    if (lane == 0) dst[pmax] = T(1) / (in ? Dg[rsrc] : De[rsrc]);
   }
-  // pair list of the shape, with each pair's local column offset
+  // pair list with each pair's local row offset; compact list of non-empty diagonals
   const int np = dptr[b.dptr_base + b.hb + 1];
   for (int q = threadIdx.x; q < np; q += blockDim.x) {
     const int2 pr = pairs[b.pair_base + q];
@@ -159,37 +164,54 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
     const int dx = (signed char)((pr.y >> 16) & 0xff);
     Ps[q] = make_int4(pr.x, pr.y, (dk * b.ey + dy) * b.ex + dx, 0);
   }
-  for (int d = threadIdx.x; d <= hp1; d += blockDim.x) Dp[d] = dptr[b.dptr_base + d];
-  __syncthreads();
-  const int ncol = min(kCols, b.nb - c0);
-  // columns in turn (coordinates decoded once per column), threads over d
-  for (int cc = 0; cc < ncol; ++cc) {
+  if (threadIdx.x == 0) {
+    int cnt = 0;
+    for (int d = 0; d < hp1; ++d) {
+      const int a = dptr[b.dptr_base + d], e = dptr[b.dptr_base + d + 1];
+      if (e > a) {
+        Dl[cnt] = make_int2(a, e);
+        Dd[cnt] = d;
+        ++cnt;
+      }
+    }
+    n_nz = cnt;
+  }
+  // validity of each slot (row j = c - offset(s) inside the box) per column
+  for (int idx = threadIdx.x; idx < ncol * ns; idx += blockDim.x) {
+    const int cc = idx / ns, s = idx - cc * ns;
     const int c = c0 + cc;
     const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
-    for (int d = threadIdx.x; d < hp1; d += blockDim.x) {
+    int dk = 0, dy = 0, dx = 0;
+    if (s < pmax) slot_offset(s, g.r, g.vr, dk, dy, dx);
+    const int kj = kc - dk, yyj = yyc - dy, xxj = xxc - dx;
+    Vm[cc * ns + s] = (kj >= 0 && kj < b.nlev_b && yyj >= 0 && yyj < b.ey && xxj >= 0 && xxj < b.ex);
+  }
+  __syncthreads();
+  // entries of the non-empty diagonals: threads over (diagonal, column)
+  const int nz = n_nz;
+  for (int e = threadIdx.x; e < nz * ncol; e += blockDim.x) {
+    const int zi = e % nz, cc = e / nz;
+    const int d = Dd[zi];
+    const int c = c0 + cc;
+    if (c + d >= b.nb) continue;
+    const unsigned char* vm = Vm + cc * ns;
     T sum = T(0);
-    if (c + d < b.nb) {
-      const int q1 = Dp[d + 1];
-      for (int q = Dp[d]; q < q1; ++q) {
-        const int4 pr = Ps[q];
-        const int s1 = pr.x & 0xffff, s2 = pr.x >> 16;
-        const int dk = (signed char)(pr.y & 0xff);
-        const int dy = (signed char)((pr.y >> 8) & 0xff);
-        const int dx = (signed char)((pr.y >> 16) & 0xff);
-        const int kj = kc - dk, yyj = yyc - dy, xxj = xxc - dx;
-        if (kj < 0 || kj >= b.nlev_b || yyj < 0 || yyj >= b.ey || xxj < 0 || xxj >= b.ex) continue;
-        const T* tr = Ts + (c - pr.z - jlo) * ldt;
-        const T t1 = s1 == pmax ? T(1) : tr[s1];
-        const T t2 = s2 == pmax ? T(1) : tr[s2];
-        sum += (t1 * tr[pmax]) * t2;
-      }
-      if (d == 0) {
-        const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
-        if (o >= 0) sum += T(1) / R[o];
-      }
+    const int2 rg = Dl[zi];
+    for (int q = rg.x; q < rg.y; ++q) {
+      const int4 pr = Ps[q];
+      const int s1 = pr.x & 0xffff, s2 = pr.x >> 16;
+      if (!vm[s2]) continue;
+      const T* tr = Ts + (c - pr.z - jlo) * ldt;
+      const T t1 = s1 == pmax ? T(1) : tr[s1];
+      const T t2 = s2 == pmax ? T(1) : tr[s2];
+      sum += (t1 * tr[pmax]) * t2;
+    }
+    if (d == 0) {
+      const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
+      const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
+      if (o >= 0) sum += T(1) / R[o];
     }
     band[b.band_off + (int64_t)c * hp1 + d] = sum;
-    }
   }
 }
 
@@ -269,8 +291,10 @@ cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
                                   cudaStream_t s) {
   const int stage_rows = kCols + hb_max + 1 + g.r;
+  const size_t nd = (size_t)(g.pmax + 1) * (g.pmax + 2) / 2 + 1;  // bound on non-empty diagonals
   const size_t smem = (sizeof(T) * (size_t)stage_rows * (g.pmax + 1) + 15) / 16 * 16 +
-                      sizeof(int4) * (size_t)npair_max + sizeof(int) * (hb_max + 2);
+                      sizeof(int4) * (size_t)npair_max + nd * (sizeof(int2) + sizeof(int)) +
+                      (size_t)kCols * (g.pmax + 1);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
