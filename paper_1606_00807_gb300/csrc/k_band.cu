@@ -223,12 +223,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
     __syncthreads();
     if (tid < NB) invd[tid] = tid < nbc ? T(1) / P[tid * ldP + tid] : T(0);
     __syncthreads();
-    if (tid < nm) {
-      // forward triangle in blocks of 8 rows: solve the block in registers,
-      // then update the rows below it
-      T* w = Wn + base * NMP + tid;
+    // forward triangle in blocks of 8 rows: one thread per member solves the
+    // block in registers, then every thread updates the panel rows below it
 #pragma unroll 1
-      for (int B0 = 0; B0 < nbc; B0 += 8) {
+    for (int B0 = 0; B0 < nbc; B0 += 8) {
+      if (tid < nm) {
+        T* w = Wn + base * NMP + tid;
         T yv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) yv[j] = (B0 + j < nbc) ? w[(B0 + j) * NMP] : T(0);
@@ -242,15 +242,20 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           if (B0 + j < nbc) w[(B0 + j) * NMP] = yv[j];
-        for (int t = B0 + 8; t < nbc; ++t) {
-          T acc = w[t * NMP];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc = fma(-P[(B0 + j) * ldP + t], yv[j], acc);
-          w[t * NMP] = acc;
-        }
       }
+      __syncthreads();
+      const int rem = nbc - (B0 + 8);
+      for (int idx = tid; idx < rem * nm; idx += blockDim.x) {
+        const int t = B0 + 8 + idx / nm, m = idx - (idx / nm) * nm;
+        T* wt = Wn + (base + t) * NMP + m;
+        const T* y8 = Wn + (base + B0) * NMP + m;
+        T acc = *wt;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc = fma(-P[(B0 + j) * ldP + t], y8[j * NMP], acc);
+        *wt = acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const int Wr = rows - nbc;
     const int nTi = (Wr + 3) >> 2;
     constexpr int TMT = NMB / 8;
@@ -336,14 +341,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
         for (int c = 0; c < 4; ++c) Red[(kg * NB + t0 + a) * NMB + mm0 + c] = acc[a][c];
     }
     __syncthreads();
-    if (tid < nm) {
-      T* w = Wn + base * NMP + tid;
-      for (int t = 0; t < nbc; ++t)
-        w[t * NMP] -= Red[(0 * NB + t) * NMB + tid] + Red[(1 * NB + t) * NMB + tid] +
-                      Red[(2 * NB + t) * NMB + tid] + Red[(3 * NB + t) * NMB + tid];
-      // backward triangle in blocks of 8 rows, last block first
+    for (int idx = tid; idx < nbc * nm; idx += blockDim.x) {
+      const int t = idx / nm, m = idx - t * nm;
+      Wn[(base + t) * NMP + m] -= Red[(0 * NB + t) * NMB + m] + Red[(1 * NB + t) * NMB + m] +
+                                  Red[(2 * NB + t) * NMB + m] + Red[(3 * NB + t) * NMB + m];
+    }
+    __syncthreads();
+    // backward triangle in blocks of 8 rows, last block first; the rows above a
+    // solved block are updated by every thread
 #pragma unroll 1
-      for (int B0 = ((nbc - 1) / 8) * 8; B0 >= 0; B0 -= 8) {
+    for (int B0 = ((nbc - 1) / 8) * 8; B0 >= 0; B0 -= 8) {
+      if (tid < nm) {
+        T* w = Wn + base * NMP + tid;
         T yv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) yv[j] = (B0 + j < nbc) ? w[(B0 + j) * NMP] : T(0);
@@ -357,15 +366,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
 #pragma unroll
         for (int j = 0; j < 8; ++j)
           if (B0 + j < nbc) w[(B0 + j) * NMP] = yv[j];
-        for (int t = 0; t < B0; ++t) {
-          T acc = w[t * NMP];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc = fma(-P[t * ldP + B0 + j], yv[j], acc);
-          w[t * NMP] = acc;
-        }
       }
+      __syncthreads();
+      for (int idx = tid; idx < B0 * nm; idx += blockDim.x) {
+        const int t = idx / nm, m = idx - t * nm;
+        T* wt = Wn + (base + t) * NMP + m;
+        const T* y8 = Wn + (base + B0) * NMP + m;
+        T acc = *wt;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc = fma(-P[t * ldP + B0 + j], y8[j * NMP], acc);
+        *wt = acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     store_rows(c0, nbc);
     __syncthreads();
   }

@@ -43,6 +43,17 @@ __device__ __forceinline__ T warp_sum(T v) {
 __device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
 
+// four consecutive elements from 16-byte aligned shared memory
+__device__ __forceinline__ void lds4v(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void lds4v(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // ---------------------------------------------------------------------------
 // Anomalies: U[l][m] = X[m][l] - mean_m X[m][l]
 // ---------------------------------------------------------------------------
@@ -248,7 +259,8 @@ __device__ __forceinline__ void ff_sub_prod(float& s, float& c, float x, float b
 
 constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 
-template <typename T>
+// RR: rounds of 32 rows covering pmax + 1; MR: rounds of 32 members covering N.
+template <typename T, int RR, int MR>
 __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restrict__ U,
                                                  const T* __restrict__ C, int nH,
                                                  const int32_t* __restrict__ halo, int64_t nitems,
@@ -366,23 +378,33 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
     int err = 0;
     for (int kc = 0; kc < p; ++kc) {
       const T* Lk = L + kc * ldg;
-      T vals[kMaxRounds * 2];
+      T vals[RR];
 #pragma unroll
-      for (int t = 0; t < kMaxRounds * 2; ++t) {
+      for (int t = 0; t < RR; ++t) {
         const int i = lane + 32 * t;
         vals[t] = T(0);
         if (i >= kc && i <= p) {
           const T* Li = L + i * ldg;
-          T dot = T(0);
-          for (int l = 0; l < kc; ++l) dot = fma(Li[l], Lk[l], dot);
-          vals[t] = Li[kc] - dot;
+          T dot0 = T(0), dot1 = T(0);
+          int l = 0;
+          for (; l + 4 <= kc; l += 4) {
+            T a4[4], b4[4];
+            lds4v(Li + l, a4);
+            lds4v(Lk + l, b4);
+            dot0 = fma(a4[0], b4[0], dot0);
+            dot1 = fma(a4[1], b4[1], dot1);
+            dot0 = fma(a4[2], b4[2], dot0);
+            dot1 = fma(a4[3], b4[3], dot1);
+          }
+          for (; l < kc; ++l) dot0 = fma(Li[l], Lk[l], dot0);
+          vals[t] = Li[kc] - (dot0 + dot1);
         }
       }
       __syncwarp();
       if (lane == (kc & 31)) {
         T d = vals[0];
 #pragma unroll
-        for (int t = 1; t < kMaxRounds * 2; ++t)
+        for (int t = 1; t < RR; ++t)
           if (t == (kc >> 5)) d = vals[t];
         const bool fin = finite_val(d);
         const T sd = (fin && d > T(0)) ? sqrt(d) : T(0);
@@ -397,7 +419,7 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
         break;
       }
 #pragma unroll
-      for (int t = 0; t < kMaxRounds * 2; ++t) {
+      for (int t = 0; t < RR; ++t) {
         const int i = lane + 32 * t;
         if (i > kc && i <= p) L[i * ldg + kc] = vals[t] * inv;
       }
@@ -418,9 +440,9 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
       }
       if (fp32) {
         // residual e = u - U_P^T beta (compensated), members m = lane + 32 t
-        float e[kMaxRounds], ec[kMaxRounds];
+        float e[MR], ec[MR];
 #pragma unroll
-        for (int t = 0; t < kMaxRounds; ++t) {
+        for (int t = 0; t < MR; ++t) {
           const int m = lane + 32 * t;
           e[t] = (m < N) ? (float)U[(int64_t)jlab * g.ldN + m] : 0.f;
           ec[t] = 0.f;
@@ -429,19 +451,19 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
           const float bi = (float)vb[i];
           const T* Ui = U + (int64_t)q[i] * g.ldN;
 #pragma unroll
-          for (int t = 0; t < kMaxRounds; ++t) {
+          for (int t = 0; t < MR; ++t) {
             const int m = lane + 32 * t;
             if (m < N) ff_sub_prod(e[t], ec[t], (float)Ui[m], bi);
           }
         }
 #pragma unroll
-        for (int t = 0; t < kMaxRounds; ++t) e[t] += ec[t];
+        for (int t = 0; t < MR; ++t) e[t] += ec[t];
         // c = U_P e - lambda beta, the residual of (G + lambda I) beta = g -> va
         for (int i = 0; i < p; ++i) {
           const T* Ui = U + (int64_t)q[i] * g.ldN;
           float part = 0.f;
 #pragma unroll
-          for (int t = 0; t < kMaxRounds; ++t) {
+          for (int t = 0; t < MR; ++t) {
             const int m = lane + 32 * t;
             if (m < N) part = fmaf((float)Ui[m], e[t], part);
           }
@@ -470,14 +492,14 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
           const float di = (float)va[i];
           const T* Ui = U + (int64_t)q[i] * g.ldN;
 #pragma unroll
-          for (int t = 0; t < kMaxRounds; ++t) {
+          for (int t = 0; t < MR; ++t) {
             const int m = lane + 32 * t;
             if (m < N) e[t] = fmaf(-(float)Ui[m], di, e[t]);
           }
         }
         float ssq = 0.f;
 #pragma unroll
-        for (int t = 0; t < kMaxRounds; ++t) ssq = fmaf(e[t], e[t], ssq);
+        for (int t = 0; t < MR; ++t) ssq = fmaf(e[t], e[t], ssq);
         ssq = warp_sum(ssq);
         Dj = (T)(ssq / (float)(N - 1));
         __syncwarp();
@@ -798,16 +820,14 @@ cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
-                           int64_t nitems, const Block* blocks, T* Tout, T* Dout, double ridge_c,
-                           int32_t* status, cudaStream_t s) {
-  if (nitems <= 0) return cudaSuccess;
-  if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
-    return cudaErrorInvalidConfiguration;
+template <typename T, int RR, int MR>
+cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32_t* halo,
+                              int64_t nitems, const Block* blocks, T* Tout, T* Dout,
+                              double ridge_c, int32_t* status, cudaStream_t s) {
   const int nH = cov_offset_count(g.r, g.vr);
   const int ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  const int ldg = ldp | 1;
+  // row stride = 4 (mod 8): 16-byte row reads of 8 consecutive lanes are conflict free
+  const int ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
   size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 4 * (size_t)ldp);
   wb = (wb + 15) / 16 * 16;
   const int offbytes = (3 * g.pmax + 15) / 16 * 16;
@@ -819,14 +839,43 @@ cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t*
     if (wpc > 8) wpc = 8;
   }
   const size_t smem = offbytes + wb * wpc;
-  cudaError_t e = cudaFuncSetAttribute(k_regress<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_regress<T, RR, MR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t grid = (nitems + wpc - 1) / wpc;
   if (grid > 152 * 32) grid = 152 * 32;
-  k_regress<T><<<(unsigned)grid, 32 * wpc, smem, s>>>(g, U, C, nH, halo, nitems, blocks, Tout,
-                                                      Dout, ridge_c, status, ldp, ldg, (int)wb);
+  k_regress<T, RR, MR><<<(unsigned)grid, 32 * wpc, smem, s>>>(
+      g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, ldp, ldg, (int)wb);
   return cudaGetLastError();
+}
+
+template <typename T, int RR>
+cudaError_t launch_regress_r(const Geom& g, const T* U, const T* C, const int32_t* halo,
+                             int64_t nitems, const Block* blocks, T* Tout, T* Dout,
+                             double ridge_c, int32_t* status, cudaStream_t s) {
+  const int mr = (g.N + 31) / 32;
+  if (mr <= 2)
+    return launch_regress_rm<T, RR, 2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                       status, s);
+  if (mr == 3)
+    return launch_regress_rm<T, RR, 3>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                       status, s);
+  return launch_regress_rm<T, RR, 4>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
+                                     s);
+}
+
+template <typename T>
+cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
+                           int64_t nitems, const Block* blocks, T* Tout, T* Dout, double ridge_c,
+                           int32_t* status, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds) return cudaErrorInvalidConfiguration;
+  const int rr = (g.pmax + 1 + 31) / 32;
+  if (rr <= 2)
+    return launch_regress_r<T, 2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status, s);
+  if (rr <= 4)
+    return launch_regress_r<T, 4>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status, s);
+  return launch_regress_r<T, 8>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status, s);
 }
 
 template <typename T>
