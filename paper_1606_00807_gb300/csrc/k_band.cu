@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
           if (B0 + j < nbc) w[(B0 + j) * NMP] = yv[j];
       }
       __syncthreads();
-      const int rem = nbc - (B0 + 8);
+      const int rem = nbc - (B0 + 8);  // > 0 only when this sub-block is full
       for (int idx = tid; idx < rem * nm; idx += blockDim.x) {
         const int t = B0 + 8 + idx / nm, m = idx - (idx / nm) * nm;
         T* wt = Wn + (base + t) * NMP + m;
@@ -368,13 +368,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
           if (B0 + j < nbc) w[(B0 + j) * NMP] = yv[j];
       }
       __syncthreads();
+      const int jn = min(8, nbc - B0);  // rows of this sub-block inside the panel
       for (int idx = tid; idx < B0 * nm; idx += blockDim.x) {
         const int t = idx / nm, m = idx - t * nm;
         T* wt = Wn + (base + t) * NMP + m;
         const T* y8 = Wn + (base + B0) * NMP + m;
         T acc = *wt;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc = fma(-P[t * ldP + B0 + j], y8[j * NMP], acc);
+        for (int j = 0; j < 8; ++j)
+          if (j < jn) acc = fma(-P[t * ldP + B0 + j], y8[j * NMP], acc);
         *wt = acc;
       }
       __syncthreads();
