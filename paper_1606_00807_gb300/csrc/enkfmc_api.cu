@@ -78,7 +78,7 @@ enkfmc_status build(enkfmc_handle* h) {
     return ENKFMC_EINVAL;
   if (p.precision != ENKFMC_FP64 && p.precision != ENKFMC_FP32) return ENKFMC_EINVAL;
   if (p.lon_periodic && p.nlon < 2 * p.r + 1) return ENKFMC_EINVAL;
-  if (p.flags & ~ENKFMC_FLAG_NO_SOLVE_REFINEMENT) return ENKFMC_EINVAL;
+  if (p.flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_SOLVE)) return ENKFMC_EINVAL;
   Geom& g = h->g;
   std::memset(&g, 0, sizeof(g));
   g.nlon = p.nlon;
@@ -164,6 +164,8 @@ enkfmc_status build(enkfmc_handle* h) {
   h->ext_rows = row_off;
   h->band_elems = band_off;
   h->halo_rows = (int64_t)halo.size() / 2;
+  h->tc_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_SIMT_SOLVE) &&
+               bandsolve_tc_supported(h->hb_max, p.N);
 
   // slot-pair lists per block shape for the band assembly: pairs (s1, s2) of
   // stencil slots (index pmax = the row itself) with local offsets
@@ -270,6 +272,7 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_Te, h->esize * h->ext_rows * std::max(1, g.pmax)))) return st;
   if ((st = dalloc(h, &h->d_De, h->esize * h->ext_rows))) return st;
   if ((st = dalloc(h, &h->d_band, h->esize * h->band_elems))) return st;
+  if ((st = dalloc(h, &h->d_invdiag, h->esize * h->ext_rows))) return st;
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
   if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
   if (h->refine_solve) {
@@ -298,7 +301,7 @@ enkfmc_status build(enkfmc_handle* h) {
 void release(enkfmc_handle* h) {
   void* bufs[] = {h->d_pairs,  h->d_dptr, h->d_blocks, h->d_halo, h->d_status, h->d_obs_of,
                   h->d_U,   h->d_C,
-                  h->d_Te,     h->d_De,   h->d_band,   h->d_rhs,    h->d_res, h->d_vhi,
+                  h->d_Te,     h->d_De,   h->d_band,   h->d_invdiag, h->d_rhs,    h->d_res, h->d_vhi,
                   h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
                   h->d_T,      h->d_D,    h->d_lam,    h->d_aT,     h->d_bT,  h->d_dxT,
                   h->d_lamT,   h->d_Ubar};
@@ -390,9 +393,21 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
   });
   if (st) return st;
   return timed(h, ENKFMC_K_BANDCHOL, [&] {
-    return launch_bandchol<T>(h->d_blocks, h->nblock, h->hb_max, (T*)h->d_band, h->d_status,
+    return launch_bandchol<T>(h->d_blocks, h->nblock, h->hb_max, (T*)h->d_band,
+                              (T*)h->d_invdiag, h->d_status,
                               h->stream);
   });
+}
+
+// L L^T X = B in place for every block, N members (Eq. 11).
+template <typename T>
+cudaError_t solve_band(enkfmc_handle* h, T* rhs) {
+  if (sizeof(T) == sizeof(float) && h->tc_solve)
+    return launch_bandsolve_tc(h->d_blocks, h->nblock, h->hb_max, h->g.N,
+                               (const float*)h->d_band, (const float*)h->d_invdiag,
+                               (float*)rhs, h->d_status, h->stream);
+  return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, h->g.N, (const T*)h->d_band, rhs,
+                             h->stream);
 }
 
 template <typename T>
@@ -404,8 +419,7 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-    return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, h->g.N, (const T*)h->d_band,
-                               (T*)h->d_rhs, h->stream);
+    return solve_band<T>(h, (T*)h->d_rhs);
   });
   if (st) return st;
   const T* corr = nullptr;
@@ -420,8 +434,7 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
     });
     if (st) return st;
     st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-      return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, h->g.N,
-                                 (const T*)h->d_band, (T*)h->d_res, h->stream);
+      return solve_band<T>(h, (T*)h->d_res);
     });
     if (st) return st;
     corr = (const T*)h->d_res;
@@ -542,8 +555,7 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-    return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, g.N, (const T*)h->d_band,
-                               (T*)h->d_lam, h->stream);
+    return solve_band<T>(h, (T*)h->d_lam);
   });
   if (st) return st;
   if (h->m > 0) {

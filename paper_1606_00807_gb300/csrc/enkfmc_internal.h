@@ -171,10 +171,12 @@ struct enkfmc_handle {
   void* d_Te = nullptr;    // boundary rows of T per block [ext_rows][pmax]
   void* d_De = nullptr;    // their D [ext_rows]
   void* d_band = nullptr;  // band of A, then of L
+  void* d_invdiag = nullptr;  // 1 / L[c][c] per block row [ext_rows]
   void* d_rhs = nullptr;   // per block [N][nb] right-hand sides / increments
   void* d_res = nullptr;   // refinement: residual, then correction (FP32 path)
   void* d_vhi = nullptr;   // refinement scratch: (T dX) / D as double-float
   void* d_vlo = nullptr;
+  bool tc_solve = false;  // FP32 solves on the tensor cores
   bool refine_solve = false;
   const void* T_assembled = nullptr;  // global T/D used by the last assemble
   const void* D_assembled = nullptr;
@@ -255,8 +257,9 @@ cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
                                   cudaStream_t s);
 
+// Factor every block in place; invdiag[row_off + c] = 1 / L[c][c] (may be null).
 template <typename T>
-cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band,
+cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, T* invdiag,
                             int32_t* status, cudaStream_t s);
 
 template <typename T>
@@ -267,6 +270,14 @@ cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_ma
 template <typename T>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
                              T* rhs, cudaStream_t s);
+
+// Single-precision band solves with the panel updates on the tensor cores
+// (k_band_tc.cu); usable when N <= 128 and the staged panels of a band of
+// half-width hb_max fit in shared memory and TMEM.
+bool bandsolve_tc_supported(int hb_max, int N);
+cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int N,
+                                const float* band, const float* invdiag, float* rhs,
+                                int32_t* status, cudaStream_t s);
 
 // Xa = Xb + dX (+ dX2 when not null) on sub-domain interiors.
 template <typename T>

@@ -75,7 +75,8 @@ __device__ __forceinline__ void load_panel(const T* __restrict__ AB, int ld, int
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__ blocks,
-                                                       T* __restrict__ band, int32_t* status,
+                                                       T* __restrict__ band,
+                                                       T* __restrict__ invdiag, int32_t* status,
                                                        int ldP) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* P = reinterpret_cast<T*>(smem);  // [NB][ldP]: P[t*ldP + i] = A[c0+i][c0+t]
@@ -108,7 +109,10 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
       const T inv = T(1) / dg;
       __syncthreads();
       for (int i = t + 1 + tid; i < rows; i += blockDim.x) P[t * ldP + i] *= inv;
-      if (tid == 0) P[t * ldP + t] = dg;
+      if (tid == 0) {
+        P[t * ldP + t] = dg;
+        if (invdiag) invdiag[b.row_off + c0 + t] = inv;
+      }
       __syncthreads();
     }
     // write the factored panel
@@ -389,14 +393,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
 }  // namespace
 
 template <typename T>
-cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, int32_t* status,
-                            cudaStream_t s) {
+cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, T* invdiag,
+                            int32_t* status, cudaStream_t s) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const size_t smem = sizeof(T) * (size_t)NB * ldP;
   cudaError_t e = cudaFuncSetAttribute(k_bandchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_bandchol<T><<<nblock, kThreads, smem, s>>>(blocks, band, status, ldP);
+  k_bandchol<T><<<nblock, kThreads, smem, s>>>(blocks, band, invdiag, status, ldP);
   return cudaGetLastError();
 }
 
@@ -434,7 +438,8 @@ cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N,
 }
 
 #define INST(T)                                                                                  \
-  template cudaError_t launch_bandchol<T>(const Block*, int, int, T*, int32_t*, cudaStream_t);  \
+  template cudaError_t launch_bandchol<T>(const Block*, int, int, T*, T*, int32_t*,           \
+                                          cudaStream_t);                                     \
   template cudaError_t launch_bandsolve<T>(const Block*, int, int, int, const T*, T*,           \
                                            cudaStream_t);
 INST(float)

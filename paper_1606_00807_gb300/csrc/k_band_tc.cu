@@ -1,0 +1,493 @@
+// Band solves L L^T X = B (Eq. 11) for all N <= 128 members of one block of
+// A per CTA, with the panel updates on the tensor cores (single precision).
+//
+// Storage as in k_band.cu: the factor of a block is the column-major lower
+// band band[c (hb + 1) + d] = L[c + d][c], which is the strided view
+// L[i][c] = F[c hb + i] (c <= i <= c + hb) of the block's slice F.
+//
+// Forward, panel p of 32 rows [c0, c0 + 32):
+//   Y_p = L_pp^-1 (B_p - S_p), S_p the sum of L[c0+t][j] Y_j over earlier rows,
+// with S accumulated in TMEM: member m is TMEM lane m and row i of the block
+// is TMEM column i mod WT, so the rows that a panel still has to update (its
+// own 32 and the hb rows below) form a circular window of columns.  Once Y_p
+// is known one group of tcgen05.mma adds Y_p^T L[rows below][panel]^T to the
+// window (D = A B^T with A = Y_p^T, 128 x 32, and B = the hb x 32 block of L
+// below the diagonal block); the group's first part covers the next panel's
+// 32 columns and is committed to its own mbarrier, so the next triangle can
+// start while the rest of the group runs.  Backward (L^T X = Y) runs the same
+// schedule from the last panel, with B = L[panel][rows above]^T.
+//
+// Precision: every operand is split x = hi + lo (hi the nearest TF32 value)
+// and each product is taken as hi*hi + hi*lo + lo*hi with FP32 accumulation
+// (about 21 significant bits per product); the 32 x 32 triangles are solved
+// in FP32 registers, one member per thread.
+#include "enkfmc_internal.h"
+#include "tc_sm100.cuh"
+
+namespace enkfmc {
+
+namespace {
+
+constexpr int kTcThreads = 128;                 // one warp group: thread m = member m
+constexpr int kABytes = 128 * 32 * 4;           // one split of the member operand
+constexpr uint64_t kWaitNs = 2000000000ull;     // bound of every mbarrier wait (2 s)
+
+// Byte offset of element (row n, K index t) in a K-major tile of 32 K-values.
+__device__ __forceinline__ int core_off(int n, int kc) {
+  return ((n >> 3) * 8 + kc) * 128 + (n & 7) * 16;
+}
+
+__device__ __forceinline__ void put_split4(unsigned char* hi, unsigned char* lo, int off,
+                                           const float (&v)[4]) {
+  float4 h, l;
+  tc::split_tf32(v[0], h.x, l.x);
+  tc::split_tf32(v[1], h.y, l.y);
+  tc::split_tf32(v[2], h.z, l.z);
+  tc::split_tf32(v[3], h.w, l.w);
+  *reinterpret_cast<float4*>(hi + off) = h;
+  *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+// x - (x with the 13 low mantissa bits cleared): the part of x that a TF32
+// operand read drops, exact in FP32
+__device__ __forceinline__ float tf32_rest(float x) {
+  return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_bandsolve_tc(const Block* __restrict__ blocks, const float* __restrict__ band,
+                   const float* __restrict__ invdiag, float* __restrict__ rhs, int N, int NU,
+                   int nbufB, int WT, int32_t* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m = tid;
+  const Block b = blocks[blockIdx.x];
+  const int nb = b.nb, hb = b.hb;
+  const float* F = band + b.band_off;
+  const float* Fi = invdiag + b.row_off;
+  float* X = rhs + b.row_off * N;
+  const int NUb = min(NU, (hb + 15) & ~15);  // rows one panel reaches, multiple of 16
+  const int bbytes = NU * 128;
+
+  // [2 groups][hi, lo] member operands; [nbufB][raw, rest] band operands (the raw
+  // FP32 tile is the TF32 "hi" operand as read by the tensor cores, the rest tile
+  // holds what that read drops); [2 panels] diagonal triangles and 1/L[c][c]
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + 4 * kABytes;
+  float* Lpp = reinterpret_cast<float*>(sB + (size_t)nbufB * 2 * bbytes);  // [2][32][32]
+  float* invd = Lpp + 2 * 32 * 32;                                     // [2][32]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(invd + 2 * 32);         // ready, done0, done1
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 3);
+
+  if (warp == 0) tc::tmem_alloc(slot, (uint32_t)WT);
+  if (tid == 0) {
+    tc::mbar_init(&bars[0], 1);
+    tc::mbar_init(&bars[1], 1);
+    tc::mbar_init(&bars[2], 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *slot;
+  const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
+  const uint32_t bar_ready = tc::smem_u32(&bars[0]);
+  const uint32_t bar_done0 = tc::smem_u32(&bars[1]);
+  const uint32_t bar_done1 = tc::smem_u32(&bars[2]);
+
+  int ngroups = 0;  // MMA groups issued so far (same value in every thread)
+  int pending = 0;  // this thread's outstanding timeout, folded into the next barrier
+  bool aborted = false;
+
+  auto wait_done_local = [&](int g) {
+    if (!tc::mbar_wait((g & 1) ? bar_done1 : bar_done0, (uint32_t)((g >> 1) & 1), kWaitNs))
+      pending = 1;
+  };
+  // barrier that also publishes every thread's cp.async data and agrees on aborts
+  auto sync_or_abort = [&](int bad) -> bool {
+    cp_async_wait_all();
+    bad = __syncthreads_or(bad | pending);
+    pending = 0;
+    if (bad && tid == 0) record_error(status, ENKFMC_ETIMEOUT, (int64_t)blockIdx.x);
+    return bad != 0;
+  };
+
+  // D columns [col0, col0 + len) (rows of the block, mod WT) += A B^T with B
+  // rows [brow0, brow0 + len) of buffer bbuf; len and col0 multiples of 16.
+  auto issue = [&](int abuf, int bbuf, int col0, int len, int brow0) {
+    const uint32_t a_hi = tc::smem_u32(sA + (abuf * 2 + 0) * kABytes);
+    const uint32_t a_lo = tc::smem_u32(sA + (abuf * 2 + 1) * kABytes);
+    const uint32_t b_hi = tc::smem_u32(sB + (size_t)(bbuf * 2 + 0) * bbytes);
+    const uint32_t b_lo = tc::smem_u32(sB + (size_t)(bbuf * 2 + 1) * bbytes);
+    while (len > 0) {
+      const int c = col0 % WT;
+      const int n = min(min(len, WT - c), 256);
+      const uint32_t id = tc::idesc_tf32(128, n);
+      const uint32_t boff = (uint32_t)(brow0 >> 3) * 1024u;
+      const uint32_t d = tbase + (uint32_t)c;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t ah = tc::desc_kmajor(a_hi + ks * 256, 128, 1024);
+        const uint64_t al = tc::desc_kmajor(a_lo + ks * 256, 128, 1024);
+        const uint64_t bh = tc::desc_kmajor(b_hi + boff + ks * 256, 128, 1024);
+        const uint64_t bl = tc::desc_kmajor(b_lo + boff + ks * 256, 128, 1024);
+        tc::mma_tf32(d, ah, bl, id, 1);
+        tc::mma_tf32(d, al, bh, id, 1);
+        tc::mma_tf32(d, ah, bh, id, 1);
+      }
+      col0 += n;
+      brow0 += n;
+      len -= n;
+    }
+  };
+
+  // 32 rows [c0, c0 + 32) of this member (zero beyond the block or member count)
+  auto load_rows = [&](int c0, float (&z)[32]) {
+    if (m < N) {
+      const float* src = X + (int64_t)m * nb + c0;
+      if (c0 + 32 <= nb && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 v = reinterpret_cast<const float4*>(src)[q];
+          z[4 * q] = v.x; z[4 * q + 1] = v.y; z[4 * q + 2] = v.z; z[4 * q + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) z[t] = (c0 + t < nb) ? src[t] : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 32; ++t) z[t] = 0.f;
+    }
+  };
+  auto store_rows = [&](int c0, const float (&z)[32]) {
+    if (m < N) {
+      float* dst = X + (int64_t)m * nb + c0;
+      if (c0 + 32 <= nb && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          reinterpret_cast<float4*>(dst)[q] =
+              make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+          if (c0 + t < nb) dst[t] = z[t];
+      }
+    }
+  };
+  // member operand of the next group: row m, K index t
+  auto put_member = [&](int abuf, const float (&z)[32]) {
+    unsigned char* hi = sA + (abuf * 2 + 0) * kABytes;
+    unsigned char* lo = sA + (abuf * 2 + 1) * kABytes;
+#pragma unroll
+    for (int kc = 0; kc < 8; ++kc) {
+      const float v[4] = {z[4 * kc], z[4 * kc + 1], z[4 * kc + 2], z[4 * kc + 3]};
+      put_split4(hi, lo, core_off(m, kc), v);
+    }
+  };
+  // Lpp[u][t] = L[c0+t][c0+u] (forward, t >= u) or L[c0+u][c0+t] (backward, t <= u),
+  // invd[t] = 1 / L[c0+t][c0+t]; asynchronous copies, zeros stored directly
+  auto prefetch_diag = [&](int c0, bool fwd, int buf) {
+    const int nbc = min(32, nb - c0);
+    float* Lq = Lpp + buf * 1024;
+    for (int e = tid; e < 1024; e += kTcThreads) {
+      const int u = e >> 5, t = e & 31;
+      const float* src = nullptr;
+      if (u < nbc && t < nbc) {
+        if (fwd) {
+          if (t >= u && t - u <= hb) src = F + (int64_t)(c0 + u) * hb + c0 + t;
+        } else {
+          if (t <= u && u - t <= hb) src = F + (int64_t)(c0 + t) * hb + c0 + u;
+        }
+      }
+      if (src) cp_async4(Lq + e, src);
+      else Lq[e] = 0.f;
+    }
+    if (tid < 32) {
+      if (tid < nbc) cp_async4(invd + buf * 32 + tid, Fi + c0 + tid);
+      else invd[buf * 32 + tid] = 0.f;
+    }
+  };
+  // Raw tiles: lane (n mod 8, t mod 4) of a warp, warps over 8-row groups, the
+  // 8 K chunks unrolled; every shared-memory word of a warp's store is distinct.
+  const int lane = tid & 31, nl = lane >> 2, tl = lane & 3;
+  // forward group of panel c0: B rows n <-> block rows c0 + 32 + n, K index t <->
+  // column c0 + t (per chunk: 4 columns x 8 consecutive rows)
+  auto prefetch_fwd = [&](int c0, int len, int bbuf) {
+    unsigned char* raw = sB + (size_t)(bbuf * 2 + 0) * bbytes;
+    for (int ng = warp; ng < (len >> 3); ng += kTcThreads / 32) {
+      const int i = c0 + 32 + ng * 8 + nl;
+      float* d = reinterpret_cast<float*>(raw + ng * 1024 + nl * 16 + tl * 4);
+      const float* src = F + (int64_t)(c0 + tl) * hb + i;
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) {
+        const int c = c0 + 4 * kc + tl;
+        float* dst = d + kc * 32;
+        if (i < nb && c < nb && i - c <= hb) cp_async4(dst, src + (int64_t)(4 * kc) * hb);
+        else *dst = 0.f;
+      }
+    }
+  };
+  // backward group of panel c0: B rows n <-> block rows jlo + n, K index t <-> row
+  // c0 + t (per chunk: 8 rows x 4 consecutive t)
+  auto prefetch_bwd = [&](int c0, int jlo, int len, int bbuf) {
+    unsigned char* raw = sB + (size_t)(bbuf * 2 + 0) * bbytes;
+    for (int ng = warp; ng < (len >> 3); ng += kTcThreads / 32) {
+      const int j = jlo + ng * 8 + nl;
+      float* d = reinterpret_cast<float*>(raw + ng * 1024 + nl * 16 + tl * 4);
+      const float* src = F + (int64_t)j * hb + c0 + tl;
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) {
+        const int r = c0 + 4 * kc + tl;
+        float* dst = d + kc * 32;
+        if (r < nb && r - j <= hb) cp_async4(dst, src + 4 * kc);
+        else *dst = 0.f;
+      }
+    }
+  };
+  // rest tile from the raw tile (len rows = len * 128 contiguous bytes)
+  auto make_rest = [&](int len, int bbuf) {
+    const float4* raw = reinterpret_cast<const float4*>(sB + (size_t)(bbuf * 2 + 0) * bbytes);
+    float4* rest = reinterpret_cast<float4*>(sB + (size_t)(bbuf * 2 + 1) * bbytes);
+    for (int e = tid; e < len * 8; e += kTcThreads) {
+      const float4 v = raw[e];
+      rest[e] = make_float4(tf32_rest(v.x), tf32_rest(v.y), tf32_rest(v.z), tf32_rest(v.w));
+    }
+  };
+  auto fwd_len = [&](int c0) {  // B rows of the forward group of panel c0
+    return min(NUb, (nb - (c0 + 32) + 15) & ~15);
+  };
+  auto bwd_jlo = [&](int c0) { return max(0, c0 - NUb); };
+
+  const int np = (nb + 31) / 32;
+  float z[32];
+
+  // ---------------- forward: L Y = B ----------------
+  for (int c = 0; c < WT; c += 32) tc::tmem_zero32(tlane + (uint32_t)c);
+  tc::tmem_wait_st();
+  prefetch_diag(0, true, 0);
+  if (32 < nb) prefetch_fwd(0, fwd_len(0), 0);
+  cp_async_commit();
+  load_rows(0, z);
+  (void)sync_or_abort(0);
+  if (32 < nb) make_rest(fwd_len(0), 0);
+  for (int p = 0; p < np; ++p) {
+    const int c0 = p * 32;
+    const bool below = c0 + 32 < nb;
+    if (p > 0) {
+      const int bad = !tc::mbar_wait(bar_ready, (uint32_t)((ngroups - 1) & 1), kWaitNs);
+      if (sync_or_abort(bad)) {
+        aborted = true;
+        break;
+      }
+      tc::fence_after_sync();
+      float d[32];
+      tc::tmem_ld32(tlane + (uint32_t)(c0 % WT), d);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) z[t] -= d[t];
+      if (below) make_rest(fwd_len(c0), ngroups % nbufB);
+    }
+    {  // triangle: right-looking over the columns u of L_pp
+      const float* Lq = Lpp + (p & 1) * 1024;
+      const float* iv = invd + (p & 1) * 32;
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const float yu = z[u] * iv[u];
+        z[u] = yu;
+        const float4* col = reinterpret_cast<const float4*>(Lq + u * 32);
+#pragma unroll
+        for (int g = (u + 1) >> 2; g < 8; ++g) {
+          const float4 q = col[g];
+          const float lv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (4 * g + k > u) z[4 * g + k] = fmaf(-lv[k], yu, z[4 * g + k]);
+        }
+      }
+    }
+    store_rows(c0, z);
+    if (below) put_member(ngroups & 1, z);
+    tc::tmem_zero32(tlane + (uint32_t)(c0 % WT));
+    tc::tmem_wait_st();
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (below) {
+      const int len = fwd_len(c0);
+      const int len1 = min(32, len);
+      if (tid == 0) {
+        tc::fence_after_sync();
+        issue(ngroups & 1, ngroups % nbufB, c0 + 32, len1, 0);
+        tc::commit(bar_ready);
+        issue(ngroups & 1, ngroups % nbufB, c0 + 32 + len1, len - len1, len1);
+        tc::commit((ngroups & 1) ? bar_done1 : bar_done0);
+      }
+      ++ngroups;
+    }
+    if (p + 1 < np) {
+      const int c1 = c0 + 32;
+      prefetch_diag(c1, true, (p + 1) & 1);
+      if (c1 + 32 < nb) {
+        const int H = ngroups - nbufB;  // last group that read the buffer to refill
+        if (H >= 0) wait_done_local(H);
+        prefetch_fwd(c1, fwd_len(c1), ngroups % nbufB);
+      }
+      cp_async_commit();
+      load_rows(c1, z);
+    }
+  }
+  if (!aborted && ngroups > 0) {
+    wait_done_local(ngroups - 1);
+    if (sync_or_abort(0)) aborted = true;
+  }
+
+  // ---------------- backward: L^T X = Y ----------------
+  if (!aborted) {
+    for (int c = 0; c < WT; c += 32) tc::tmem_zero32(tlane + (uint32_t)c);
+    tc::tmem_wait_st();
+    const int cl = (np - 1) * 32;
+    prefetch_diag(cl, false, 0);
+    if (cl >= 32) prefetch_bwd(cl, bwd_jlo(cl), cl - bwd_jlo(cl), ngroups % nbufB);
+    cp_async_commit();
+    load_rows(cl, z);
+    (void)sync_or_abort(0);
+    if (cl >= 32) make_rest(cl - bwd_jlo(cl), ngroups % nbufB);
+    int q = 0;  // panels done (selects the diagonal buffer)
+    for (int p = np - 1; p >= 0; --p, ++q) {
+      const int c0 = p * 32;
+      if (p < np - 1) {
+        const int bad = !tc::mbar_wait(bar_ready, (uint32_t)((ngroups - 1) & 1), kWaitNs);
+        if (sync_or_abort(bad)) {
+          aborted = true;
+          break;
+        }
+        tc::fence_after_sync();
+        float d[32];
+        tc::tmem_ld32(tlane + (uint32_t)(c0 % WT), d);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) z[t] -= d[t];
+        if (p >= 1) make_rest(c0 - bwd_jlo(c0), ngroups % nbufB);
+      }
+      {  // triangle: right-looking from the last row, rows u of L_pp
+        const float* Lq = Lpp + (q & 1) * 1024;
+        const float* iv = invd + (q & 1) * 32;
+#pragma unroll
+        for (int u = 31; u >= 0; --u) {
+          const float xu = z[u] * iv[u];
+          z[u] = xu;
+          const float4* row = reinterpret_cast<const float4*>(Lq + u * 32);
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            if (4 * g >= u) break;
+            const float4 qv = row[g];
+            const float lv[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (4 * g + k < u) z[4 * g + k] = fmaf(-lv[k], xu, z[4 * g + k]);
+          }
+        }
+      }
+      store_rows(c0, z);
+      if (p >= 1) put_member(ngroups & 1, z);
+      tc::tmem_zero32(tlane + (uint32_t)(c0 % WT));
+      tc::tmem_wait_st();
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (p >= 1) {
+        const int jlo = bwd_jlo(c0);
+        const int len = c0 - jlo;
+        const int len1 = min(32, len);
+        if (tid == 0) {
+          tc::fence_after_sync();
+          issue(ngroups & 1, ngroups % nbufB, c0 - len1, len1, len - len1);
+          tc::commit(bar_ready);
+          issue(ngroups & 1, ngroups % nbufB, jlo, len - len1, 0);
+          tc::commit((ngroups & 1) ? bar_done1 : bar_done0);
+        }
+        ++ngroups;
+        const int c1 = c0 - 32;
+        prefetch_diag(c1, false, (q + 1) & 1);
+        if (c1 >= 32) {
+          const int H = ngroups - nbufB;
+          if (H >= 0) wait_done_local(H);
+          prefetch_bwd(c1, bwd_jlo(c1), c1 - bwd_jlo(c1), ngroups % nbufB);
+        }
+        cp_async_commit();
+        load_rows(c1, z);
+      }
+    }
+    if (!aborted && ngroups > 0) {
+      wait_done_local(ngroups - 1);
+      if (sync_or_abort(0)) aborted = true;
+    }
+  }
+  if (aborted && ngroups > 0) {
+    // let the groups in flight finish (bounded) before the columns are released
+    (void)tc::mbar_wait(((ngroups - 1) & 1) ? bar_done1 : bar_done0,
+                        (uint32_t)(((ngroups - 1) >> 1) & 1), kWaitNs);
+  }
+  cp_async_wait_all();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, (uint32_t)WT);
+  }
+}
+
+struct TcPlan {
+  int NU = 0, nbufB = 0, WT = 0;
+  size_t smem = 0;
+};
+
+TcPlan plan_tc(int hb_max, int N) {
+  TcPlan pl;
+  if (N < 1 || N > 128) return pl;
+  const int NU = (max(hb_max, 16) + 15) & ~15;
+  int WT = 32;
+  while (WT < 32 + NU) WT *= 2;
+  if (WT > 512) return pl;
+  const size_t lim = 227 * 1024;
+  for (int nbuf = 2; nbuf >= 1; --nbuf) {
+    const size_t bytes =
+        4 * (size_t)kABytes + (size_t)nbuf * 2 * NU * 128 + 2 * 32 * 32 * 4 + 2 * 32 * 4 + 3 * 8 + 8;
+    if (bytes <= lim) {
+      pl.NU = NU;
+      pl.nbufB = nbuf;
+      pl.WT = WT;
+      pl.smem = bytes;
+      return pl;
+    }
+  }
+  return pl;
+}
+
+}  // namespace
+
+bool bandsolve_tc_supported(int hb_max, int N) { return plan_tc(hb_max, N).nbufB > 0; }
+
+cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int N,
+                                const float* band, const float* invdiag, float* rhs,
+                                int32_t* status, cudaStream_t s) {
+  const TcPlan pl = plan_tc(hb_max, N);
+  if (pl.nbufB == 0) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_bandsolve_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)pl.smem);
+  if (e != cudaSuccess) return e;
+  k_bandsolve_tc<<<nblock, kTcThreads, pl.smem, s>>>(blocks, band, invdiag, rhs, N, pl.NU,
+                                                     pl.nbufB, pl.WT, status);
+  return cudaGetLastError();
+}
+
+}  // namespace enkfmc

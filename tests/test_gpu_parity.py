@@ -82,6 +82,27 @@ def test_plain_fp32_solve_without_refinement():
     _parity("small_48x26x3x1+1_n80_r2", 1, flags=1)
 
 
+@pytest.mark.parametrize("flags", [2, 3])
+def test_cuda_core_solve_parity(flags):
+    """Single precision with the band solves on the CUDA cores only
+    (ENKFMC_FLAG_SIMT_SOLVE), with (2) and without (3) the refinement step."""
+    _parity("small_48x26x3x1+1_n80_r2", 1, flags=flags)
+
+
+def test_tensor_core_and_cuda_core_solves_agree():
+    """The TF32-split tensor-core solves and the FP32 CUDA-core solves, both
+    followed by the refinement step, give the same analysis to the FP32 tolerance."""
+    w = WORKLOADS["small_48x26x3x1+1_n80_r2"]
+    inp = make_inputs(w, np.float32)
+    a = gpu_pipeline(w, inp, 1)
+    b = gpu_pipeline(w, inp, 1, flags=2)
+    assert np.array_equal(a["T"], b["T"]) and np.array_equal(a["D"], b["D"])
+    lab = np.arange(w.n)
+    Xb = inp.Xb.astype(np.float64)
+    err = per_variable_err(w, lab, (a["Xa"] - Xb).T, (b["Xa"] - Xb).T)
+    assert err <= TOL[1], err
+
+
 @pytest.mark.parametrize("name", ILL)
 def test_ill_conditioned_fp64_parity(name):
     """T and D at the FP64 tolerance; the analysis within a bound derived from the
