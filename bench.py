@@ -52,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-FP64 and forward+adjoint side measurements")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-rows", type=int, default=1000)
     ap.add_argument("--sample-subdomains", type=int, default=3)
@@ -218,6 +220,104 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def _time_steps(step, warmup, steps, stream):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def side_measurements(args, w, inp, value, dev):
+    """Two side lines of the headline metric, each on its own handle:
+    the plain FP64 form of the same workload (cycles/s and the FP32 speed-up
+    over it), and forward + adjoint at the T63 shape with N = 40 (the loss
+    L = 1/2 |mean(X^a) - x_ref|^2, its gradient dL/dX^a formed on the device,
+    then enkfmc_analyze_adjoint for X^b, y and diag(R)) against the forward
+    analysis alone."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00807_gb300 import binding as B
+    from synthetic import WORKLOADS, make_inputs
+
+    out = {}
+    # plain FP64 form, same workload and inputs
+    stream = torch.cuda.Stream(device=dev)
+    h = B.Handle.from_workload(w, precision=B.FP64, stream=stream.cuda_stream)
+    h.set_observations(inp.obs_idx)
+    with torch.cuda.stream(stream):
+        put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, torch.float64)
+        Xb, y, R, Z = put(inp.Xb), put(inp.y), put(inp.R), put(inp.Z)
+        T = torch.empty((w.n, h.info.pmax), device=dev, dtype=torch.float64)
+        D = torch.empty(w.n, device=dev, dtype=torch.float64)
+        Xa = torch.empty_like(Xb)
+
+    def step64():
+        h.estimate(Xb, T, D)
+        h.assemble(Xb, T, D, R)
+        h.analyze(Xb, y, R, Z, Xa)
+
+    ms = _time_steps(step64, 1, 3, stream)
+    h.check("fp64 steps")
+    h.close()
+    del Xb, y, R, Z, T, D, Xa
+    out["plain_fp64"] = {"workload": w.name, "value": 1e3 / ms, "unit": "cycles/s",
+                         "ms_per_step": ms, "fp32_over_fp64": value / (1e3 / ms)}
+
+    # forward + adjoint, T63 shape with N = 40: p = 37 predecessors from 40
+    # members make the Gram matrices nearly singular, so this configuration runs
+    # in FP64 (single precision reports EDNONPOS here)
+    wa = WORKLOADS["t63_192x96x29_n40_r2"]
+    ia = make_inputs(wa, np.float64)
+    stream = torch.cuda.Stream(device=dev)
+    h = B.Handle.from_workload(wa, precision=B.FP64, stream=stream.cuda_stream)
+    h.set_observations(ia.obs_idx)
+    with torch.cuda.stream(stream):
+        put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, torch.float64)
+        Xb, y, R, Z, xref = put(ia.Xb), put(ia.y), put(ia.R), put(ia.Z), put(ia.truth)
+        T = torch.empty((wa.n, h.info.pmax), device=dev, dtype=torch.float64)
+        D = torch.empty(wa.n, device=dev, dtype=torch.float64)
+        Xa = torch.empty_like(Xb)
+        Xa_bar = torch.empty_like(Xb)
+        Xb_bar = torch.empty_like(Xb)
+        y_bar = torch.empty_like(y)
+        R_bar = torch.empty_like(R)
+
+    def fwd():
+        h.estimate(Xb, T, D)
+        h.assemble(Xb, T, D, R)
+        h.analyze(Xb, y, R, Z, Xa)
+
+    def fwd_adj():
+        fwd()
+        with torch.cuda.stream(stream):
+            Xa_bar.copy_(((Xa.mean(dim=0) - xref) / wa.N).expand_as(Xa))
+        h.analyze_adjoint(Xa_bar, y_bar, R_bar, Xb_bar)
+
+    ms_f = _time_steps(fwd, 2, 5, stream)
+    ms_fa = _time_steps(fwd_adj, 1, 5, stream)
+    h.profile(True)
+    h.profile_read()
+    _time_steps(fwd_adj, 0, 2, stream)
+    prof = h.profile_read()
+    h.profile(False)
+    h.check("forward + adjoint steps")
+    h.close()
+    out["fwd_adj"] = {"workload": wa.name, "precision": "fp64",
+                      "fwd_cycles_per_s": 1e3 / ms_f, "fwd_adj_cycles_per_s": 1e3 / ms_fa,
+                      "fwd_ms": ms_f, "fwd_adj_ms": ms_fa, "adj_over_fwd": (ms_fa - ms_f) / ms_f,
+                      "kernels_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -346,6 +446,12 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args)
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        try:
+            extras = side_measurements(args, w, inp, value, dev)
+        except Exception as exc:  # a side line must not hide the headline number
+            extras = {"side_measurements_error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "cycles/s", "n_gpus": world,
@@ -363,6 +469,7 @@ def run_ours(args):
                "gpu_launches": int(sum(v[0] for v in prof.values())),
                "clocks": clocks,
                "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
+        out.update(extras)
         print(json.dumps(out))
     h.close()
     if world > 1:
