@@ -169,24 +169,23 @@ enkfmc_status build(enkfmc_handle* h) {
 
   // slot-pair lists per block shape for the band assembly: pairs (s1, s2) of
   // stencil slots (index pmax = the row itself) with local offsets
-  // o(s1) - o(s2) = d >= 0, grouped by d.  Row j = c - o(s2) adds
-  // T[j][s1] T[j][s2] / D[j] to A[c + d][c].  Valid when the extended box does
-  // not wrap onto itself (ex + r <= nlon), so local and geometric offsets agree.
-  std::vector<int2> pairs;
-  std::vector<int32_t> dptr;
+  // o(s1) - o(s2) = d, 0 <= d <= hb, sorted by d.  Row j = c - o(s2) adds
+  // T[j][s1] T[j][s2] / D[j] to A[c + d][c].  Each record is
+  // {s1, s2, o(s2), d}.  Valid when the extended box does not wrap onto itself
+  // (ex + r <= nlon), so local and geometric offsets agree.
+  std::vector<int4> pairs;
   h->pair_assembly = true;
   for (const Block& b : h->blocks)
     if (g.periodic && b.ex + g.r > g.nlon) h->pair_assembly = false;
   {
-    // the staged rows of a 32-column tile must fit in shared memory
-    const size_t stage = h->esize * (size_t)(32 + h->hb_max + 1 + g.r) * (g.pmax + 1);
+    // staged rows, output tile and pair list of a 32-column tile in shared memory
     const size_t npairs = (size_t)(g.pmax + 1) * (g.pmax + 2) / 2;
-    if (stage + 16 * npairs + 12 * (npairs + 1) + 32 * (size_t)(g.pmax + 1) + 32 > 227 * 1024)
+    if (assemble_pairs_smem(h->esize, g.pmax, h->hb_max, g.r, (int)npairs) > 227 * 1024)
       h->pair_assembly = false;
   }
   if (h->pair_assembly) {
     struct Shape {
-      int nlev, ey, ex, hb, pair_base, dptr_base;
+      int nlev, ey, ex, hb, pair_base, npair;
     };
     std::vector<Shape> shapes;
     for (Block& b : h->blocks) {
@@ -205,34 +204,26 @@ enkfmc_status build(enkfmc_handle* h) {
       std::vector<int> dk(ns, 0), dy(ns, 0), dx(ns, 0), o(ns, 0);
       for (int s2 = 0; s2 < g.pmax; ++s2) slot_offset(s2, g.r, g.vr, dk[s2], dy[s2], dx[s2]);
       for (int s2 = 0; s2 < ns; ++s2) o[s2] = (dk[s2] * sh.ey + dy[s2]) * sh.ex + dx[s2];
-      std::vector<std::vector<int2>> byd(sh.hb + 1);
+      std::vector<std::vector<int4>> byd(sh.hb + 1);
       for (int a = 0; a < ns; ++a)
         for (int c = 0; c < ns; ++c) {
           const int d = o[a] - o[c];
           if (d < 0 || (d == 0 && a != c) || d > sh.hb) continue;
-          int2 pr;
-          pr.x = a | (c << 16);
-          pr.y = (dk[c] & 0xff) | ((dy[c] & 0xff) << 8) | ((dx[c] & 0xff) << 16);
-          byd[d].push_back(pr);
+          byd[d].push_back(make_int4(a, c, o[c], d));
         }
       sh.pair_base = (int)pairs.size();
-      sh.dptr_base = (int)dptr.size();
-      int cnt = 0;
-      for (int d = 0; d <= sh.hb; ++d) {
-        dptr.push_back(cnt);
-        for (const int2& pr : byd[d]) pairs.push_back(pr);
-        cnt += (int)byd[d].size();
-      }
-      dptr.push_back(cnt);
-      h->npair_max = std::max(h->npair_max, cnt);
+      for (int d = 0; d <= sh.hb; ++d)
+        for (const int4& pr : byd[d]) pairs.push_back(pr);
+      sh.npair = (int)pairs.size() - sh.pair_base;
+      h->npair_max = std::max(h->npair_max, sh.npair);
     }
     for (Block& b : h->blocks) {
       const Shape& sh = shapes[b.pair_base];
       b.pair_base = sh.pair_base;
-      b.dptr_base = sh.dptr_base;
+      b.npair = sh.npair;
     }
   } else {
-    for (Block& b : h->blocks) b.pair_base = b.dptr_base = -1;
+    for (Block& b : h->blocks) b.pair_base = b.npair = -1;
   }
 
   // predecessor counts for the work model
@@ -283,13 +274,25 @@ enkfmc_status build(enkfmc_handle* h) {
   CUDA_TRY(cudaMemcpy(h->d_blocks, h->blocks.data(), sizeof(Block) * h->blocks.size(),
                       cudaMemcpyHostToDevice));
   if (h->pair_assembly) {
-    if ((st = dalloc(h, &h->d_pairs, sizeof(int2) * std::max<size_t>(1, pairs.size())))) return st;
-    if ((st = dalloc(h, &h->d_dptr, sizeof(int32_t) * dptr.size()))) return st;
-    if (!pairs.empty())
-      CUDA_TRY(cudaMemcpy(h->d_pairs, pairs.data(), sizeof(int2) * pairs.size(),
-                          cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(h->d_dptr, dptr.data(), sizeof(int32_t) * dptr.size(),
+    if ((st = dalloc(h, &h->d_pairs, sizeof(int4) * std::max<size_t>(1, pairs.size())))) return st;
+    // source of every extended row: the global row of T (interior) or the
+    // block's boundary row
+    std::vector<int32_t> srcrow((size_t)h->ext_rows);
+    for (const Block& b : h->blocks)
+      for (int loc = 0; loc < b.nb; ++loc) {
+        const int plane = b.ey * b.ex;
+        const int k = loc / plane, yy = (loc - k * plane) / b.ex, xx = loc - k * plane - yy * b.ex;
+        const int y = b.lat_lo + yy, x = imod(b.lon_lo + xx, g.nlon);
+        srcrow[(size_t)(b.row_off + loc)] =
+            in_interior(b, y, x) ? (int32_t)coords_label(g, b.var, k, y, x)
+                                 : ~(int32_t)(b.row_off + loc);
+      }
+    if ((st = dalloc(h, &h->d_srcrow, sizeof(int32_t) * srcrow.size()))) return st;
+    CUDA_TRY(cudaMemcpy(h->d_srcrow, srcrow.data(), sizeof(int32_t) * srcrow.size(),
                         cudaMemcpyHostToDevice));
+    if (!pairs.empty())
+      CUDA_TRY(cudaMemcpy(h->d_pairs, pairs.data(), sizeof(int4) * pairs.size(),
+                          cudaMemcpyHostToDevice));
   }
   if (!halo.empty())
     CUDA_TRY(cudaMemcpy(h->d_halo, halo.data(), sizeof(int32_t) * halo.size(),
@@ -299,7 +302,7 @@ enkfmc_status build(enkfmc_handle* h) {
 }
 
 void release(enkfmc_handle* h) {
-  void* bufs[] = {h->d_pairs,  h->d_dptr, h->d_blocks, h->d_halo, h->d_status, h->d_obs_of,
+  void* bufs[] = {h->d_pairs,  h->d_srcrow, h->d_blocks, h->d_halo, h->d_status, h->d_obs_of,
                   h->d_U,   h->d_C,
                   h->d_Te,     h->d_De,   h->d_band,   h->d_invdiag, h->d_rhs,    h->d_res, h->d_vhi,
                   h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
@@ -384,7 +387,7 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
   st = timed(h, ENKFMC_K_ASSEMBLE, [&] {
     if (h->pair_assembly)
       return launch_assemble_pairs<T>(h->g, h->d_blocks, h->nblock, h->nb_max, h->hb_max,
-                                      h->npair_max, h->d_pairs, h->d_dptr, Tv, D,
+                                      h->npair_max, h->d_pairs, h->d_srcrow, Tv, D,
                                       (const T*)h->d_Te, (const T*)h->d_De, h->d_obs_of, R,
                                       (T*)h->d_band, h->stream);
     return launch_assemble<T>(h->g, h->d_blocks, h->nblock, h->nb_max, Tv, D, (const T*)h->d_Te,

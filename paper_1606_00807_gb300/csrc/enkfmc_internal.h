@@ -32,7 +32,7 @@ struct Block {
   int32_t lat0, lat1, lon0, lon1;  // interior tile (absolute, lon1 <= nlon)
   int32_t hb;                      // half-bandwidth of A in local order
   int32_t nb;                      // rows of the block
-  int32_t pair_base, dptr_base;    // slot-pair lists of the block's shape (-1: none)
+  int32_t pair_base, npair;        // slot-pair list of the block's shape (-1: none)
   int64_t band_off;                // offset of the band in the band array
   int64_t row_off;                 // offset of the block's rows (Te, De, rhs rows)
 };
@@ -155,8 +155,8 @@ struct enkfmc_handle {
 
   // device tables
   enkfmc::Block* d_blocks = nullptr;
-  int2* d_pairs = nullptr;       // slot pairs per block shape, grouped by band diagonal
-  int32_t* d_dptr = nullptr;     // group boundaries per shape
+  int4* d_pairs = nullptr;       // slot pairs per block shape, sorted by band diagonal
+  int32_t* d_srcrow = nullptr;   // per extended row: global label (>= 0) or ~boundary row
   bool pair_assembly = false;    // every block can use the pair lists
   int32_t npair_max = 0;         // longest pair list of a shape
   int32_t* d_halo = nullptr;     // halo rows: (block, local index) pairs
@@ -252,10 +252,12 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
 // not wrap onto itself in longitude).
 template <typename T>
 cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock, int nb_max,
-                                  int hb_max, int npair_max, const int2* pairs,
-                                  const int32_t* dptr, const T* Tg, const T* Dg, const T* Te,
+                                  int hb_max, int npair_max, const int4* pairs,
+                                  const int32_t* srcrow, const T* Tg, const T* Dg, const T* Te,
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
                                   cudaStream_t s);
+// Shared memory of one pair-assembly tile (element size esize).
+size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max);
 
 // Factor every block in place; invdiag[row_off + c] = 1 / L[c][c] (may be null).
 template <typename T>

@@ -104,41 +104,81 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
   for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : T(0);
 }
 
-// Band entries A[c + d][c] for a tile of kCols columns from the slot pairs of
-// each diagonal d.  The rows j = c - o(s2) that can touch the tile (local
-// indices [c0 - r, c0 + kCols + hb]) are staged in shared memory with their D,
-// and so is the block shape's pair list; each thread then builds entries with
-// d fastest (contiguous stores), summing its pairs in a fixed order
-// (deterministic results).
-constexpr int kCols = 32;
+// Band assembly of one tile of 32 NH columns of one block from the pair list
+// of its shape.  Records {s1, s2, o(s2), d} sorted by d: row j = c - o(s2)
+// adds T[j][s1] T[j][s2] / D[j] to A[c + d][c] when row j lies in the block.
+//  * The rows the tile reads are staged once (source rows from the handle's
+//    per-row table): pmax coefficients, 1 (the row's own unit entry, slot pmax),
+//    then 1/D[j]; odd row stride, so lanes on consecutive columns hit distinct
+//    banks.
+//  * Warps take about equal chunks of the pair list, each chunk moved to start
+//    at a diagonal boundary, so every entry is summed by one warp in list
+//    order (deterministic).  Lane l owns columns c0 + l + 32 h (h < NH): every
+//    lane runs the same pairs, the pair record is a broadcast read and the slot
+//    validity a bit of a per-column mask.  A warp stores its sums into the
+//    shared output tile at each change of diagonal.
+//  * The tile's band columns are contiguous in the band: one coalesced write,
+//    zeros included, with 1/R on the diagonal of observed components.
+constexpr int kAsmThreads = 512;
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_assemble_pairs(
-    const Geom g, const Block* __restrict__ blocks, const int2* __restrict__ pairs,
-    const int32_t* __restrict__ dptr, const T* __restrict__ Tg, const T* __restrict__ Dg,
+__host__ __device__ inline int asm_ldt(int pmax) { return (pmax + 2) | 1; }
+__host__ __device__ inline int asm_ldo(int hb) { return (hb + 1) | 1; }
+__host__ __device__ inline int asm_rows(int cols, int hb, int r) { return cols + hb + 1 + r; }
+
+template <typename T, int NH>
+__global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
+    const Geom g, const Block* __restrict__ blocks, const int4* __restrict__ pairs,
+    const int32_t* __restrict__ srcrow, const T* __restrict__ Tg, const T* __restrict__ Dg,
     const T* __restrict__ Te, const T* __restrict__ De, const int32_t* __restrict__ obs_of,
-    const T* __restrict__ R, T* __restrict__ band, int stage_rows, int npair_max) {
+    const T* __restrict__ R, T* __restrict__ band, int hb_max) {
+  constexpr int kCols = 32 * NH;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int ext[6];  // min/max of the slot offsets (dk, dy, dx)
   const Block b = blocks[blockIdx.y];
   const int c0 = blockIdx.x * kCols;
   if (c0 >= b.nb) return;
-  const int pmax = g.pmax, ldt = pmax + 1;  // staged row: pmax coefficients then 1/D
-  const int ns = pmax + 1;                   // slots plus the row itself
-  T* Ts = reinterpret_cast<T*>(smem);                         // [stage_rows][ldt]
-  const size_t ts_bytes = (sizeof(T) * (size_t)stage_rows * ldt + 15) / 16 * 16;
-  int4* Ps = reinterpret_cast<int4*>(smem + ts_bytes);        // [npair_max], 16-byte aligned
-  int2* Dl = reinterpret_cast<int2*>(Ps + npair_max);         // non-empty diagonals: [start, end)
-  int* Dd = reinterpret_cast<int*>(Dl + (g.pmax + 1) * (g.pmax + 2) / 2 + 1);  // their d
-  unsigned char* Vm = reinterpret_cast<unsigned char*>(Dd + (g.pmax + 1) * (g.pmax + 2) / 2 + 1);
-  __shared__ int n_nz;
-  const int hp1 = b.hb + 1;
+  const int pmax = g.pmax, ldt = asm_ldt(pmax);
+  const int hp1 = b.hb + 1, ldo = asm_ldo(hb_max);
+  const int nrow = asm_rows(kCols, b.hb, g.r);
   const int jlo = c0 - g.r;
-  const int nrow = min(stage_rows, kCols + hp1 + g.r);
   const int plane = b.ey * b.ex;
   const int ncol = min(kCols, b.nb - c0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // zero the tile's band columns (non-empty diagonals are overwritten below)
-  for (int e = threadIdx.x; e < ncol * hp1; e += blockDim.x) band[b.band_off + (int64_t)c0 * hp1 + e] = T(0);
+  const int npair = b.npair;
+  int4* Ps = reinterpret_cast<int4*>(smem);                           // [npair]
+  T* Os = reinterpret_cast<T*>(Ps + npair);                           // [kCols][ldo]
+  T* Ts = Os + (size_t)kCols * ldo;                                   // [nrow][ldt]
+  signed char* So = reinterpret_cast<signed char*>(Ts + (size_t)nrow * ldt);  // [3][pmax]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kAsmThreads / 32;
+
+  for (int q = threadIdx.x; q < npair; q += kAsmThreads) Ps[q] = pairs[b.pair_base + q];
+  for (int e = threadIdx.x; e < kCols * ldo; e += kAsmThreads) Os[e] = T(0);
+  if (warp == 0) {
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int s = lane; s < pmax; s += 32) {
+      int o3[3];
+      slot_offset(s, g.r, g.vr, o3[0], o3[1], o3[2]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        So[a * pmax + s] = (signed char)o3[a];
+        lo[a] = min(lo[a], o3[a]);
+        hi[a] = max(hi[a], o3[a]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+        hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+      }
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ext[a] = lo[a];
+        ext[3 + a] = hi[a];
+      }
+  }
   // stage rows j in [jlo, jlo + nrow): one warp per row, lanes over its slots
   for (int jj = warp; jj < nrow; jj += nw) {
     const int j = jlo + jj;
@@ -147,72 +187,84 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(
       for (int s = lane; s < ldt; s += 32) dst[s] = T(0);
       continue;
     }
-    const int kj = j / plane, yyj = (j - kj * plane) / b.ex, xxj = j - kj * plane - yyj * b.ex;
-    const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
-    const bool in = in_interior(b, yj, xj);
-    const int64_t rsrc = in ? coords_label(g, b.var, kj, yj, xj) : b.row_off + j;
-    const T* src = (in ? Tg : Te) + rsrc * pmax;
+    const int sr = srcrow[b.row_off + j];
+    const T* src = sr >= 0 ? Tg + (int64_t)sr * pmax : Te + (int64_t)(~sr) * pmax;
     for (int s = lane; s < pmax; s += 32) dst[s] = src[s];
-    if (lane == 0) dst[pmax] = T(1) / (in ? Dg[rsrc] : De[rsrc]);
-  }
-  // pair list with each pair's local row offset; compact list of non-empty diagonals
-  const int np = dptr[b.dptr_base + b.hb + 1];
-  for (int q = threadIdx.x; q < np; q += blockDim.x) {
-    const int2 pr = pairs[b.pair_base + q];
-    const int dk = (signed char)(pr.y & 0xff);
-    const int dy = (signed char)((pr.y >> 8) & 0xff);
-    const int dx = (signed char)((pr.y >> 16) & 0xff);
-    Ps[q] = make_int4(pr.x, pr.y, (dk * b.ey + dy) * b.ex + dx, 0);
-  }
-  if (threadIdx.x == 0) {
-    int cnt = 0;
-    for (int d = 0; d < hp1; ++d) {
-      const int a = dptr[b.dptr_base + d], e = dptr[b.dptr_base + d + 1];
-      if (e > a) {
-        Dl[cnt] = make_int2(a, e);
-        Dd[cnt] = d;
-        ++cnt;
-      }
+    if (lane == 0) {
+      dst[pmax] = T(1);
+      dst[pmax + 1] = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
     }
-    n_nz = cnt;
-  }
-  // validity of each slot (row j = c - offset(s) inside the box) per column
-  for (int idx = threadIdx.x; idx < ncol * ns; idx += blockDim.x) {
-    const int cc = idx / ns, s = idx - cc * ns;
-    const int c = c0 + cc;
-    const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
-    int dk = 0, dy = 0, dx = 0;
-    if (s < pmax) slot_offset(s, g.r, g.vr, dk, dy, dx);
-    const int kj = kc - dk, yyj = yyc - dy, xxj = xxc - dx;
-    Vm[cc * ns + s] = (kj >= 0 && kj < b.nlev_b && yyj >= 0 && yyj < b.ey && xxj >= 0 && xxj < b.ex);
   }
   __syncthreads();
-  // entries of the non-empty diagonals: threads over (diagonal, column)
-  const int nz = n_nz;
-  for (int e = threadIdx.x; e < nz * ncol; e += blockDim.x) {
-    const int zi = e % nz, cc = e / nz;
-    const int d = Dd[zi];
-    const int c = c0 + cc;
-    if (c + d >= b.nb) continue;
-    const unsigned char* vm = Vm + cc * ns;
-    T sum = T(0);
-    const int2 rg = Dl[zi];
-    for (int q = rg.x; q < rg.y; ++q) {
-      const int4 pr = Ps[q];
-      const int s1 = pr.x & 0xffff, s2 = pr.x >> 16;
-      if (!vm[s2]) continue;
-      const T* tr = Ts + (c - pr.z - jlo) * ldt;
-      const T t1 = s1 == pmax ? T(1) : tr[s1];
-      const T t2 = s2 == pmax ? T(1) : tr[s2];
-      sum += (t1 * tr[pmax]) * t2;
-    }
-    if (d == 0) {
+
+  // this lane's columns and the slots whose row lies in the block (bit s)
+  uint64_t vmask[NH];
+#pragma unroll
+  for (int h = 0; h < NH; ++h) {
+    const int cc = lane + 32 * h, c = c0 + cc;
+    vmask[h] = 0;
+    if (cc < ncol) {
       const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
-      const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
-      if (o >= 0) sum += T(1) / R[o];
+      if (kc - ext[3] >= 0 && kc - ext[0] < b.nlev_b && yyc - ext[4] >= 0 &&
+          yyc - ext[1] < b.ey && xxc - ext[5] >= 0 && xxc - ext[2] < b.ex) {
+        vmask[h] = ((uint64_t)2 << pmax) - 1;  // every slot and the row itself
+      } else {
+        vmask[h] = (uint64_t)1 << pmax;
+        for (int s = 0; s < pmax; ++s) {
+          const int kj = kc - So[s], yyj = yyc - So[pmax + s], xxj = xxc - So[2 * pmax + s];
+          if (kj >= 0 && kj < b.nlev_b && yyj >= 0 && yyj < b.ey && xxj >= 0 && xxj < b.ex)
+            vmask[h] |= (uint64_t)1 << s;
+        }
+      }
     }
-    band[b.band_off + (int64_t)c * hp1 + d] = sum;
   }
+  const T* Tc = Ts + (c0 + lane - jlo) * ldt;  // row c - o(s2) is Tc + 32 h ldt - o(s2) ldt
+  const int per = (npair + nw - 1) / nw;
+  auto at_diag_start = [&](int q) {  // first q' >= q that starts a diagonal
+    if (q <= 0) return 0;
+    while (q < npair && Ps[q].w == Ps[q - 1].w) ++q;
+    return min(q, npair);
+  };
+  const int q0 = at_diag_start(warp * per), q1 = at_diag_start((warp + 1) * per);
+  T sum[NH];
+#pragma unroll
+  for (int h = 0; h < NH; ++h) sum[h] = T(0);
+  int dcur = q0 < q1 ? Ps[q0].w : 0;
+  for (int q = q0; q < q1; ++q) {
+    const int4 pr = Ps[q];
+    if (pr.w != dcur) {
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        Os[(lane + 32 * h) * ldo + dcur] = sum[h];
+        sum[h] = T(0);
+      }
+      dcur = pr.w;
+    }
+    const int off = pr.z * ldt;
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      if ((vmask[h] >> pr.y) & 1) {
+        const T* tr = Tc + 32 * h * ldt - off;
+        sum[h] += (tr[pr.x] * tr[pmax + 1]) * tr[pr.y];
+      }
+    }
+  }
+  if (q0 < q1) {
+#pragma unroll
+    for (int h = 0; h < NH; ++h) Os[(lane + 32 * h) * ldo + dcur] = sum[h];
+  }
+  __syncthreads();
+  if (threadIdx.x < ncol) {  // H^T R^-1 H on the diagonal
+    const int cq = c0 + threadIdx.x;
+    const int kc = cq / plane, yyc = (cq - kc * plane) / b.ex, xxc = cq - kc * plane - yyc * b.ex;
+    const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
+    if (o >= 0) Os[threadIdx.x * ldo] += T(1) / R[o];
+  }
+  __syncthreads();
+  T* out = band + b.band_off + (int64_t)c0 * hp1;
+  for (int col = warp; col < ncol; col += nw)
+    for (int d = lane; d < hp1; d += 32)
+      out[(int64_t)col * hp1 + d] = (c0 + col + d < b.nb) ? Os[col * ldo + d] : T(0);
 }
 
 // rhs[blk][m][loc] = (y_o + sqrt(R_o) Z[m][o] - Xb[m][l]) / R_o when component
@@ -285,23 +337,28 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
 }
 
 template <typename T>
+constexpr int asm_halves() { return sizeof(T) == sizeof(float) ? 2 : 1; }
+
+size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max) {
+  const int cols = 32 * (esize == sizeof(float) ? asm_halves<float>() : asm_halves<double>());
+  return 16 * (size_t)npair_max + esize * (size_t)cols * asm_ldo(hb_max) +
+         esize * (size_t)asm_rows(cols, hb_max, r) * asm_ldt(pmax) + 3 * (size_t)pmax + 16;
+}
+
+template <typename T>
 cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock, int nb_max,
-                                  int hb_max, int npair_max, const int2* pairs,
-                                  const int32_t* dptr, const T* Tg, const T* Dg, const T* Te,
+                                  int hb_max, int npair_max, const int4* pairs,
+                                  const int32_t* srcrow, const T* Tg, const T* Dg, const T* Te,
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
                                   cudaStream_t s) {
-  const int stage_rows = kCols + hb_max + 1 + g.r;
-  const size_t nd = (size_t)(g.pmax + 1) * (g.pmax + 2) / 2 + 1;  // bound on non-empty diagonals
-  const size_t smem = (sizeof(T) * (size_t)stage_rows * (g.pmax + 1) + 15) / 16 * 16 +
-                      sizeof(int4) * (size_t)npair_max + nd * (sizeof(int2) + sizeof(int)) +
-                      (size_t)kCols * (g.pmax + 1);
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T>,
+  constexpr int NH = asm_halves<T>();
+  const size_t smem = assemble_pairs_smem(sizeof(T), g.pmax, hb_max, g.r, npair_max);
+  cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T, NH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((nb_max + kCols - 1) / kCols, nblock);
-  k_assemble_pairs<T><<<grid, 256, smem, s>>>(g, blocks, pairs, dptr, Tg, Dg, Te, De, obs_of, R,
-                                              band, stage_rows, npair_max);
+  const dim3 grid((nb_max + 32 * NH - 1) / (32 * NH), nblock);
+  k_assemble_pairs<T, NH><<<grid, kAsmThreads, smem, s>>>(g, blocks, pairs, srcrow, Tg, Dg, Te,
+                                                          De, obs_of, R, band, hb_max);
   return cudaGetLastError();
 }
 
@@ -325,7 +382,7 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
 
 #define INST(T)                                                                                  \
   template cudaError_t launch_assemble_pairs<T>(const Geom&, const Block*, int, int, int, int,  \
-                                                const int2*, const int32_t*, const T*, const T*,  \
+                                                const int4*, const int32_t*, const T*, const T*,  \
                                                 const T*, const T*, const int32_t*, const T*, T*, \
                                                 cudaStream_t);                                     \
   template cudaError_t launch_assemble<T>(const Geom&, const Block*, int, int, const T*,        \
