@@ -180,7 +180,10 @@ enkfmc_status build(enkfmc_handle* h) {
   {
     // staged rows, output tile and pair list of a 32-column tile in shared memory
     const size_t npairs = (size_t)(g.pmax + 1) * (g.pmax + 2) / 2;
-    if (assemble_pairs_smem(h->esize, g.pmax, h->hb_max, g.r, (int)npairs) > 227 * 1024)
+    for (const Block& b : h->blocks) h->box_sum = std::max(h->box_sum, b.nlev_b + b.ey + b.ex);
+    if (g.pmax > 63 ||
+        assemble_pairs_smem(h->esize, g.pmax, h->hb_max, g.r, (int)npairs, h->box_sum) >
+            227 * 1024)
       h->pair_assembly = false;
   }
   if (h->pair_assembly) {
@@ -389,7 +392,7 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
       return launch_assemble_pairs<T>(h->g, h->d_blocks, h->nblock, h->nb_max, h->hb_max,
                                       h->npair_max, h->d_pairs, h->d_srcrow, Tv, D,
                                       (const T*)h->d_Te, (const T*)h->d_De, h->d_obs_of, R,
-                                      (T*)h->d_band, h->stream);
+                                      (T*)h->d_band, h->box_sum, h->stream);
     return launch_assemble<T>(h->g, h->d_blocks, h->nblock, h->nb_max, Tv, D, (const T*)h->d_Te,
                               (const T*)h->d_De, h->d_obs_of, R, (T*)h->d_band, h->d_status,
                               h->stream, h->hb_max);

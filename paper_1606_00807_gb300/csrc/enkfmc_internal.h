@@ -159,6 +159,7 @@ struct enkfmc_handle {
   int32_t* d_srcrow = nullptr;   // per extended row: global label (>= 0) or ~boundary row
   bool pair_assembly = false;    // every block can use the pair lists
   int32_t npair_max = 0;         // longest pair list of a shape
+  int32_t box_sum = 0;           // largest nlev_b + ey + ex of a block
   int32_t* d_halo = nullptr;     // halo rows: (block, local index) pairs
   int32_t* d_obs_of = nullptr;   // [n]: observation index of a component or -1
   int32_t* d_status = nullptr;   // [4]: first error code, pad, 64-bit info
@@ -255,9 +256,11 @@ cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock
                                   int hb_max, int npair_max, const int4* pairs,
                                   const int32_t* srcrow, const T* Tg, const T* Dg, const T* Te,
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
-                                  cudaStream_t s);
-// Shared memory of one pair-assembly tile (element size esize).
-size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max);
+                                  int box_sum, cudaStream_t s);
+// Shared memory of one pair-assembly tile (element size esize; box_sum the
+// largest nlev + ey + ex of a block).
+size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max,
+                           int box_sum);
 
 // Factor every block in place; invdiag[row_off + c] = 1 / L[c][c] (may be null).
 template <typename T>

@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
     const T* __restrict__ R, T* __restrict__ band, int hb_max) {
   constexpr int kCols = 32 * NH;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int ext[6];  // min/max of the slot offsets (dk, dy, dx)
   const Block b = blocks[blockIdx.y];
   const int c0 = blockIdx.x * kCols;
   if (c0 >= b.nb) return;
@@ -147,53 +146,48 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
   int4* Ps = reinterpret_cast<int4*>(smem);                           // [npair]
   T* Os = reinterpret_cast<T*>(Ps + npair);                           // [kCols][ldo]
   T* Ts = Os + (size_t)kCols * ldo;                                   // [nrow][ldt]
-  signed char* So = reinterpret_cast<signed char*>(Ts + (size_t)nrow * ldt);  // [3][pmax]
+  // slot-validity bit masks by level, latitude and longitude position in the box
+  uint64_t* Mk = reinterpret_cast<uint64_t*>(Ts + (size_t)nrow * ldt + 1);  // 8-byte aligned below
+  Mk = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(Mk) + 7) & ~(uintptr_t)7);
+  uint64_t* My = Mk + b.nlev_b;
+  uint64_t* Mx = My + b.ey;
+  int32_t* Sr = reinterpret_cast<int32_t*>(Mx + b.ex);                // [nrow] source rows
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kAsmThreads / 32;
 
   for (int q = threadIdx.x; q < npair; q += kAsmThreads) Ps[q] = pairs[b.pair_base + q];
   for (int e = threadIdx.x; e < kCols * ldo; e += kAsmThreads) Os[e] = T(0);
-  if (warp == 0) {
-    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int s = lane; s < pmax; s += 32) {
-      int o3[3];
-      slot_offset(s, g.r, g.vr, o3[0], o3[1], o3[2]);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        So[a * pmax + s] = (signed char)o3[a];
-        lo[a] = min(lo[a], o3[a]);
-        hi[a] = max(hi[a], o3[a]);
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-        hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
-      }
-    }
-    if (lane == 0)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        ext[a] = lo[a];
-        ext[3 + a] = hi[a];
-      }
-  }
-  // stage rows j in [jlo, jlo + nrow): one warp per row, lanes over its slots
-  for (int jj = warp; jj < nrow; jj += nw) {
+  for (int jj = threadIdx.x; jj < nrow; jj += kAsmThreads) {
     const int j = jlo + jj;
-    T* dst = Ts + jj * ldt;
-    if (j < 0 || j >= b.nb) {
-      for (int s = lane; s < ldt; s += 32) dst[s] = T(0);
-      continue;
+    Sr[jj] = (j < 0 || j >= b.nb) ? INT32_MIN : srcrow[b.row_off + j];
+  }
+  // bit s of Mk[k] / My[yy] / Mx[xx]: the row at offset s from that position
+  // stays inside the box along that axis (bit pmax: the row itself)
+  for (int e = threadIdx.x; e < b.nlev_b + b.ey + b.ex; e += kAsmThreads) {
+    const int axis = e < b.nlev_b ? 0 : (e < b.nlev_b + b.ey ? 1 : 2);
+    const int pos = e - (axis == 0 ? 0 : (axis == 1 ? b.nlev_b : b.nlev_b + b.ey));
+    const int lim = axis == 0 ? b.nlev_b : (axis == 1 ? b.ey : b.ex);
+    uint64_t m = (uint64_t)1 << pmax;
+    for (int sl = 0; sl < pmax; ++sl) {
+      int o3[3];
+      slot_offset(sl, g.r, g.vr, o3[0], o3[1], o3[2]);
+      const int q = pos - o3[axis];
+      if (q >= 0 && q < lim) m |= (uint64_t)1 << sl;
     }
-    const int sr = srcrow[b.row_off + j];
-    const T* src = sr >= 0 ? Tg + (int64_t)sr * pmax : Te + (int64_t)(~sr) * pmax;
-    for (int s = lane; s < pmax; s += 32) dst[s] = src[s];
-    if (lane == 0) {
-      dst[pmax] = T(1);
-      dst[pmax + 1] = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
+    (axis == 0 ? Mk : (axis == 1 ? My : Mx))[pos] = m;
+  }
+  __syncthreads();
+  // stage rows j in [jlo, jlo + nrow): flat over (row, slot), slot pmax = 1,
+  // slot pmax + 1 = 1 / D[j]
+  for (int e = threadIdx.x; e < nrow * ldt; e += kAsmThreads) {
+    const int jj = e / ldt, sl = e - jj * ldt;
+    const int sr = Sr[jj];
+    T v = T(0);
+    if (sr != INT32_MIN) {
+      if (sl < pmax) v = sr >= 0 ? Tg[(int64_t)sr * pmax + sl] : Te[(int64_t)(~sr) * pmax + sl];
+      else if (sl == pmax) v = T(1);
+      else if (sl == pmax + 1) v = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
     }
+    Ts[e] = v;
   }
   __syncthreads();
 
@@ -205,17 +199,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
     vmask[h] = 0;
     if (cc < ncol) {
       const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
-      if (kc - ext[3] >= 0 && kc - ext[0] < b.nlev_b && yyc - ext[4] >= 0 &&
-          yyc - ext[1] < b.ey && xxc - ext[5] >= 0 && xxc - ext[2] < b.ex) {
-        vmask[h] = ((uint64_t)2 << pmax) - 1;  // every slot and the row itself
-      } else {
-        vmask[h] = (uint64_t)1 << pmax;
-        for (int s = 0; s < pmax; ++s) {
-          const int kj = kc - So[s], yyj = yyc - So[pmax + s], xxj = xxc - So[2 * pmax + s];
-          if (kj >= 0 && kj < b.nlev_b && yyj >= 0 && yyj < b.ey && xxj >= 0 && xxj < b.ex)
-            vmask[h] |= (uint64_t)1 << s;
-        }
-      }
+      vmask[h] = Mk[kc] & My[yyc] & Mx[xxc];
     }
   }
   const T* Tc = Ts + (c0 + lane - jlo) * ldt;  // row c - o(s2) is Tc + 32 h ldt - o(s2) ldt
@@ -339,10 +323,12 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
 template <typename T>
 constexpr int asm_halves() { return sizeof(T) == sizeof(float) ? 2 : 1; }
 
-size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max) {
+size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max,
+                           int box_sum) {
   const int cols = 32 * (esize == sizeof(float) ? asm_halves<float>() : asm_halves<double>());
+  const int rows = asm_rows(cols, hb_max, r);
   return 16 * (size_t)npair_max + esize * (size_t)cols * asm_ldo(hb_max) +
-         esize * (size_t)asm_rows(cols, hb_max, r) * asm_ldt(pmax) + 3 * (size_t)pmax + 16;
+         esize * (size_t)rows * asm_ldt(pmax) + 16 + 8 * (size_t)box_sum + 4 * (size_t)rows;
 }
 
 template <typename T>
@@ -350,9 +336,9 @@ cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock
                                   int hb_max, int npair_max, const int4* pairs,
                                   const int32_t* srcrow, const T* Tg, const T* Dg, const T* Te,
                                   const T* De, const int32_t* obs_of, const T* R, T* band,
-                                  cudaStream_t s) {
+                                  int box_sum, cudaStream_t s) {
   constexpr int NH = asm_halves<T>();
-  const size_t smem = assemble_pairs_smem(sizeof(T), g.pmax, hb_max, g.r, npair_max);
+  const size_t smem = assemble_pairs_smem(sizeof(T), g.pmax, hb_max, g.r, npair_max, box_sum);
   cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T, NH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -384,7 +370,7 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
   template cudaError_t launch_assemble_pairs<T>(const Geom&, const Block*, int, int, int, int,  \
                                                 const int4*, const int32_t*, const T*, const T*,  \
                                                 const T*, const T*, const int32_t*, const T*, T*, \
-                                                cudaStream_t);                                     \
+                                                int, cudaStream_t);                                \
   template cudaError_t launch_assemble<T>(const Geom&, const Block*, int, int, const T*,        \
                                           const T*, const T*, const T*, const int32_t*,         \
                                           const T*, T*, int32_t*, cudaStream_t, int);           \
