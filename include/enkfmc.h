@@ -76,14 +76,16 @@ typedef enum {
 enum {
   ENKFMC_FLAG_NO_SOLVE_REFINEMENT = 1, /* FP32: skip the sub-domain refinement step
                                           (the plain single-precision solve)      */
-  ENKFMC_FLAG_SIMT_SOLVE = 2           /* FP32: take the band solves on the CUDA cores
-                                          only.  By default, when N <= 128 and the
-                                          band fits, their panel updates run on the
-                                          tensor cores as three TF32 products of a
-                                          hi + lo split of each operand (about 21
-                                          significant bits per product, FP32
-                                          accumulation); FP64 always uses the CUDA
-                                          cores                                    */
+  ENKFMC_FLAG_SIMT_BAND = 2            /* FP32: take the band Cholesky and the band
+                                          solves on the CUDA cores only.  By
+                                          default their rank-32 panel updates run
+                                          on the tensor cores as three TF32
+                                          products of a hi + lo split of each
+                                          operand (about 21 significant bits per
+                                          product, FP32 accumulation), when the
+                                          band fits (half-width < 384; for the
+                                          solves also N <= 128); FP64 always uses
+                                          the CUDA cores                           */
 };
 
 /* Problem description.  Neighbours of a component share its variable, lie

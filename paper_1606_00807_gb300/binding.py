@@ -63,7 +63,7 @@ SIGNATURES = {
 }
 NKERNEL = 12
 FLAG_NO_SOLVE_REFINEMENT = 1
-FLAG_SIMT_SOLVE = 2
+FLAG_SIMT_BAND = 2
 
 _LIB = None
 

@@ -78,7 +78,7 @@ enkfmc_status build(enkfmc_handle* h) {
     return ENKFMC_EINVAL;
   if (p.precision != ENKFMC_FP64 && p.precision != ENKFMC_FP32) return ENKFMC_EINVAL;
   if (p.lon_periodic && p.nlon < 2 * p.r + 1) return ENKFMC_EINVAL;
-  if (p.flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_SOLVE)) return ENKFMC_EINVAL;
+  if (p.flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_BAND)) return ENKFMC_EINVAL;
   Geom& g = h->g;
   std::memset(&g, 0, sizeof(g));
   g.nlon = p.nlon;
@@ -164,8 +164,10 @@ enkfmc_status build(enkfmc_handle* h) {
   h->ext_rows = row_off;
   h->band_elems = band_off;
   h->halo_rows = (int64_t)halo.size() / 2;
-  h->tc_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_SIMT_SOLVE) &&
+  h->tc_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_SIMT_BAND) &&
                bandsolve_tc_supported(h->hb_max, p.N);
+  h->tc_chol = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_SIMT_BAND) &&
+               bandchol_tc_supported(h->hb_max);
 
   // slot-pair lists per block shape for the band assembly: pairs (s1, s2) of
   // stencil slots (index pmax = the row itself) with local offsets
@@ -399,9 +401,11 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
   });
   if (st) return st;
   return timed(h, ENKFMC_K_BANDCHOL, [&] {
+    if (sizeof(T) == sizeof(float) && h->tc_chol)
+      return launch_bandchol_tc(h->d_blocks, h->nblock, h->hb_max, (float*)h->d_band,
+                                (float*)h->d_invdiag, h->d_status, h->stream);
     return launch_bandchol<T>(h->d_blocks, h->nblock, h->hb_max, (T*)h->d_band,
-                              (T*)h->d_invdiag, h->d_status,
-                              h->stream);
+                              (T*)h->d_invdiag, h->d_status, h->stream);
   });
 }
 

@@ -178,6 +178,7 @@ struct enkfmc_handle {
   void* d_vhi = nullptr;   // refinement scratch: (T dX) / D as double-float
   void* d_vlo = nullptr;
   bool tc_solve = false;  // FP32 solves on the tensor cores
+  bool tc_chol = false;   // FP32 band Cholesky updates on the tensor cores
   bool refine_solve = false;
   const void* T_assembled = nullptr;  // global T/D used by the last assemble
   const void* D_assembled = nullptr;
@@ -280,6 +281,11 @@ cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N,
 // (k_band_tc.cu); usable when N <= 128 and the staged panels of a band of
 // half-width hb_max fit in shared memory and TMEM.
 bool bandsolve_tc_supported(int hb_max, int N);
+// Single-precision band Cholesky with the trailing updates on the tensor cores
+// (k_band_tc.cu); usable when 32 + hb_max <= 384.
+bool bandchol_tc_supported(int hb_max);
+cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, float* band,
+                               float* invdiag, int32_t* status, cudaStream_t s);
 cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int N,
                                 const float* band, const float* invdiag, float* rhs,
                                 int32_t* status, cudaStream_t s);

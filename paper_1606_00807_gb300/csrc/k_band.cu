@@ -19,6 +19,7 @@
 // the triangle is solved backwards.
 #include <math.h>
 
+#include "band_panel.cuh"
 #include "enkfmc_internal.h"
 
 namespace enkfmc {
@@ -42,8 +43,6 @@ __device__ __forceinline__ void lds4(const T* p, T (&v)[4]) {
   }
 }
 
-__device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
-__device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
 
 // Column-major tile index over the lower triangle of an nT x nT tile grid:
 // tiles of column C are (C, C), (C+1, C), ..., (nT-1, C).
@@ -57,20 +56,6 @@ __device__ __forceinline__ void tri_tile(int idx, int nT, int& I, int& C) {
   while ((c + 1) * nT - (c + 1) * c / 2 <= idx) ++c;
   C = c;
   I = C + (idx - (C * nT - C * (C - 1) / 2));
-}
-
-template <typename T>
-__device__ __forceinline__ void load_panel(const T* __restrict__ AB, int ld, int hb, int c0,
-                                           int nbc, int rows, T* P, int ldP) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = warp; t < nbc; t += nw) {
-    const T* col = AB + (int64_t)(c0 + t) * ld;
-    T* dst = P + t * ldP;
-    for (int i = lane; i < rows; i += 32) {
-      const int d = i - t;
-      dst[i] = (d >= 0 && d <= hb) ? col[d] : T(0);
-    }
-  }
 }
 
 template <typename T>
@@ -89,40 +74,9 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
     const int rows = min(nbc + hb, nb - c0);
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     __syncthreads();
-    // left-looking factorisation of the panel, one thread per row (rows <= 2 * 256):
-    // column t takes the products of the finished columns u < t, then its pivot
-    for (int t = 0; t < nbc; ++t) {
-      for (int i = t + tid; i < rows; i += blockDim.x) {
-        T acc = P[t * ldP + i];
-        for (int u = 0; u < t; ++u) acc = fma(-P[u * ldP + i], P[u * ldP + t], acc);
-        P[t * ldP + i] = acc;
-      }
-      __syncthreads();
-      T dg = P[t * ldP + t];
-      if (!finite_val(dg) || !(dg > T(0))) {
-        if (tid == 0)
-          record_error(status, finite_val(dg) ? ENKFMC_ENOTSPD : ENKFMC_ENONFINITE,
-                       (int64_t)blockIdx.x);
-        return;  // uniform: every thread read the same pivot
-      }
-      dg = sqrt(dg);
-      const T inv = T(1) / dg;
-      __syncthreads();
-      for (int i = t + 1 + tid; i < rows; i += blockDim.x) P[t * ldP + i] *= inv;
-      if (tid == 0) {
-        P[t * ldP + t] = dg;
-        if (invdiag) invdiag[b.row_off + c0 + t] = inv;
-      }
-      __syncthreads();
-    }
-    // write the factored panel
-    {
-      const int lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-      for (int t = warp; t < nbc; t += nw) {
-        T* col = AB + (int64_t)(c0 + t) * ld;
-        for (int i = t + lane; i < rows && i - t <= hb; i += 32) col[i - t] = P[t * ldP + i];
-      }
-    }
+    if (!factor_panel(P, ldP, nbc, rows, invdiag ? invdiag + b.row_off + c0 : nullptr, status))
+      return;  // uniform: every thread read the same pivot
+    write_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     // trailing update of the window [c0+nbc, c0+rows)
     const int W = rows - nbc;
     if (W > 0) {
@@ -155,15 +109,27 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
         }
+        // read the 16 entries, then write them: the loads are independent, so
+        // they are all in flight together
+        T old[4][4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int jj = 4 * C + c;  // window-relative column
-          if (jj >= W) continue;
+          const T* colp = AB + (int64_t)(c0 + nbc + jj) * ld;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int ii = 4 * I + a;
+            old[a][c] = (jj < W && ii < W && ii >= jj) ? colp[ii - jj] : T(0);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int jj = 4 * C + c;
           T* colp = AB + (int64_t)(c0 + nbc + jj) * ld;
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             const int ii = 4 * I + a;
-            if (ii < W && ii >= jj) colp[ii - jj] -= acc[a][c];
+            if (jj < W && ii < W && ii >= jj) colp[ii - jj] = old[a][c] - acc[a][c];
           }
         }
       }

@@ -21,6 +21,7 @@
 // and each product is taken as hi*hi + hi*lo + lo*hi with FP32 accumulation
 // (about 21 significant bits per product); the 32 x 32 triangles are solved
 // in FP32 registers, one member per thread.
+#include "band_panel.cuh"
 #include "enkfmc_internal.h"
 #include "tc_sm100.cuh"
 
@@ -446,6 +447,232 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Band Cholesky with the trailing updates on the tensor cores.  Thread r owns
+// row c0 + r of panel c0 (32 columns, rows [c0, c0 + 32 + hb)) in registers:
+//  * warp 0 factors the 32 x 32 diagonal block right-looking with shuffles
+//    (lane t = row t) and leaves L11 column-major in shared memory;
+//  * rows r >= 32 solve l_r L11^T = a_r in registers (right-looking over the
+//    columns of L11, broadcast reads);
+//  * every row writes its part of the factor to the band, and the rows below
+//    the diagonal block write L21 (W x 32, W <= hb) as TF32 hi + lo tiles
+//    (K-major);
+//  * D = L21 L21^T is formed by tcgen05.mma as the 128 x 128 tiles (mi, nj),
+//    nj <= mi, of its lower block triangle (hi*hi + hi*lo + lo*hi, FP32
+//    accumulation in TMEM, up to three tiles per round); thread (tile, row)
+//    reads its row of D and subtracts it from the band, the lanes of a warp on
+//    consecutive rows of one band column (coalesced), 64 entries read before
+//    any is written.
+constexpr int kCholThreads = 384;  // 12 warps: rows of the panel; 3 tiles x 4 lane quarters
+constexpr int kOpRows = 384;       // L21 rows staged (3 tiles of 128)
+
+__device__ __forceinline__ void syrk_tile(int k, int& mi, int& nj) {
+  // (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+  mi = k < 1 ? 0 : (k < 3 ? 1 : 2);
+  nj = k - (mi * (mi + 1)) / 2;
+}
+
+__global__ void __launch_bounds__(kCholThreads, 1)
+    k_bandchol_tc(const Block* __restrict__ blocks, float* __restrict__ band,
+                  float* __restrict__ invdiag, int32_t* __restrict__ status, int WT) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sHi = smem;                               // [384 rows][32] K-major
+  unsigned char* sLo = smem + kOpRows * 128;
+  float* Lc = reinterpret_cast<float*>(smem + 2 * kOpRows * 128);  // [32][32] column-major L11
+  float* invs = Lc + 32 * 32;                                       // [32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(invs + 32);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
+  int* fail = reinterpret_cast<int*>(slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const Block b = blocks[blockIdx.x];
+  const int nb = b.nb, hb = b.hb;
+  float* F = band + b.band_off;  // A[i][c] = F[c hb + i], c <= i <= c + hb
+
+  if (warp == 0) tc::tmem_alloc(slot, (uint32_t)WT);
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+    *fail = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *slot;
+  const uint32_t bar_a = tc::smem_u32(bar);
+  const uint32_t hi0 = tc::smem_u32(sHi), lo0 = tc::smem_u32(sLo);
+  uint32_t phase = 0;
+  bool inflight = false;
+
+  for (int c0 = 0; c0 < nb; c0 += 32) {
+    const int nbc = min(32, nb - c0);
+    const int rows = min(nbc + hb, nb - c0);
+    const int W = rows - nbc;
+    const int r = tid;
+    const bool own = r < rows;
+    // row c0 + r of the panel: A[c0+r][c0+t], inside the band for 0 <= r - t <= hb
+    float a[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      a[t] = (own && t < nbc && r - t >= 0 && r - t <= hb) ? F[(int64_t)(c0 + t) * hb + c0 + r]
+                                                          : 0.f;
+    if (warp == 0) {  // diagonal block, right-looking, lane t = row t
+      bool ok = true;
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        if (u < nbc && ok) {
+          const float piv = __shfl_sync(0xffffffffu, a[u], u);
+          if (!isfinite(piv) || !(piv > 0.f)) {
+            if (lane == 0)
+              record_error(status, isfinite(piv) ? ENKFMC_ENOTSPD : ENKFMC_ENONFINITE,
+                           (int64_t)blockIdx.x);
+            ok = false;
+          } else {
+            const float d = sqrtf(piv);
+            const float inv = 1.f / d;
+            if (lane == u) {
+              a[u] = d;
+              invs[u] = inv;
+              invdiag[b.row_off + c0 + u] = inv;
+            } else if (lane > u) {
+              a[u] *= inv;
+            }
+#pragma unroll
+            for (int v = u + 1; v < 32; ++v) {
+              const float lv = __shfl_sync(0xffffffffu, a[u], v);  // L[v][u]
+              if (lane >= v) a[v] = fmaf(-a[u], lv, a[v]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 32; ++u) Lc[u * 32 + lane] = (lane >= u && lane < nbc) ? a[u] : 0.f;
+      if (!ok && lane == 0) *fail = 1;
+    }
+    __syncthreads();
+    if (*fail) break;  // uniform
+    if (warp > 0 && own) {  // l_r L11^T = a_r
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        if (u < nbc) {
+          const float xu = a[u] * invs[u];
+          a[u] = xu;
+          const float4* col = reinterpret_cast<const float4*>(Lc + u * 32);
+#pragma unroll
+          for (int g = (u + 1) >> 2; g < 8; ++g) {
+            const float4 q = col[g];
+            const float lv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (4 * g + k > u) a[4 * g + k] = fmaf(-lv[k], xu, a[4 * g + k]);
+          }
+        }
+      }
+    }
+    // factor entries of this row to the band
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (own && t < nbc && r - t >= 0 && r - t <= hb) F[(int64_t)(c0 + t) * hb + c0 + r] = a[t];
+    if (W <= 0) {
+      __syncthreads();
+      continue;
+    }
+    const int nt = (W + 127) >> 7;
+    const int Wp = nt * 128;
+    // L21 tiles: tile row rr = r - 32 <-> block row c0 + 32 + rr (zero beyond W)
+    if (warp > 0 && r - 32 < Wp) {
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) {
+        const float v[4] = {own ? a[4 * kc] : 0.f, own ? a[4 * kc + 1] : 0.f,
+                            own ? a[4 * kc + 2] : 0.f, own ? a[4 * kc + 3] : 0.f};
+        put_split4(sHi, sLo, core_off(r - 32, kc), v);
+      }
+    }
+    if (warp == 0 && 352 + lane < Wp) {  // tile rows past the last thread
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) put_split4(sHi, sLo, core_off(352 + lane, kc), z);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    const int ntiles = nt * (nt + 1) / 2;
+    bool bad = false;
+    for (int t0 = 0; t0 < ntiles; t0 += 3) {
+      const int nr = min(3, ntiles - t0);
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const uint32_t id = tc::idesc_tf32(128, 128);
+        for (int k = 0; k < nr; ++k) {
+          int mi, nj;
+          syrk_tile(t0 + k, mi, nj);
+          const uint32_t d = tbase + (uint32_t)(128 * k);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t ao = (uint32_t)(mi * 16 * 1024 + ks * 256);
+            const uint32_t bo = (uint32_t)(nj * 16 * 1024 + ks * 256);
+            const uint64_t ah = tc::desc_kmajor(hi0 + ao, 128, 1024);
+            const uint64_t al = tc::desc_kmajor(lo0 + ao, 128, 1024);
+            const uint64_t bh = tc::desc_kmajor(hi0 + bo, 128, 1024);
+            const uint64_t bl = tc::desc_kmajor(lo0 + bo, 128, 1024);
+            tc::mma_tf32(d, ah, bl, id, ks > 0 ? 1u : 0u);
+            tc::mma_tf32(d, al, bh, id, 1);
+            tc::mma_tf32(d, ah, bh, id, 1);
+          }
+        }
+        tc::commit(bar_a);
+      }
+      inflight = true;
+      int to = !tc::mbar_wait(bar_a, phase, kWaitNs);
+      to = __syncthreads_or(to);
+      if (to) {
+        if (tid == 0) record_error(status, ENKFMC_ETIMEOUT, (int64_t)blockIdx.x);
+        bad = true;
+        break;
+      }
+      inflight = false;
+      phase ^= 1;
+      tc::fence_after_sync();
+      if (warp / 4 < nr) {  // warp-uniform: tile warp / 4, lane quarter warp % 4
+        int mi, nj;
+        syrk_tile(t0 + warp / 4, mi, nj);
+        const int q = warp & 3;
+        const int rr = 128 * mi + 32 * q + lane;  // row of L21 / of the window
+        // A[c0+32+rr][c0+32+cc] = F[(c0+32+cc) hb + c0+32+rr] = base[cc hb]
+        float* base = F + (int64_t)(c0 + 32) * hb + c0 + 32 + rr;
+        const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * (warp / 4));
+#pragma unroll 1
+        for (int h2 = 0; h2 < 4; h2 += 2) {
+          const int cb = 128 * nj + 32 * h2;
+          float o[64];
+#pragma unroll
+          for (int n = 0; n < 64; ++n)
+            o[n] = (cb + n <= rr && rr < W) ? base[(cb + n) * hb] : 0.f;
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            float dv[32];
+            tc::tmem_ld32(ta + (uint32_t)(32 * (h2 + hh)), dv);
+#pragma unroll
+            for (int n = 0; n < 32; ++n) {
+              const int cc = cb + 32 * hh + n;
+              if (cc <= rr && rr < W) base[cc * hb] = o[32 * hh + n] - dv[n];
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+    if (bad) break;
+  }
+  if (inflight) (void)tc::mbar_wait(bar_a, phase, kWaitNs);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, (uint32_t)WT);
+  }
+}
+
 struct TcPlan {
   int NU = 0, nbufB = 0, WT = 0;
   size_t smem = 0;
@@ -476,6 +703,22 @@ TcPlan plan_tc(int hb_max, int N) {
 }  // namespace
 
 bool bandsolve_tc_supported(int hb_max, int N) { return plan_tc(hb_max, N).nbufB > 0; }
+
+bool bandchol_tc_supported(int hb_max) {
+  return hb_max >= 1 && 32 + hb_max <= kCholThreads;  // one thread per panel row
+}
+
+cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, float* band,
+                               float* invdiag, int32_t* status, cudaStream_t s) {
+  if (!bandchol_tc_supported(hb_max)) return cudaErrorInvalidConfiguration;
+  const size_t smem = 2 * (size_t)kOpRows * 128 + sizeof(float) * (32 * 32 + 32) + 32;
+  const int WT = hb_max <= 128 ? 128 : 512;  // one tile, or rounds of three
+  cudaError_t e = cudaFuncSetAttribute(k_bandchol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bandchol_tc<<<nblock, kCholThreads, smem, s>>>(blocks, band, invdiag, status, WT);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int N,
                                 const float* band, const float* invdiag, float* rhs,

@@ -84,14 +84,15 @@ def test_plain_fp32_solve_without_refinement():
 
 @pytest.mark.parametrize("flags", [2, 3])
 def test_cuda_core_solve_parity(flags):
-    """Single precision with the band solves on the CUDA cores only
-    (ENKFMC_FLAG_SIMT_SOLVE), with (2) and without (3) the refinement step."""
+    """Single precision with the band Cholesky and solves on the CUDA cores only
+    (ENKFMC_FLAG_SIMT_BAND), with (2) and without (3) the refinement step."""
     _parity("small_48x26x3x1+1_n80_r2", 1, flags=flags)
 
 
 def test_tensor_core_and_cuda_core_solves_agree():
-    """The TF32-split tensor-core solves and the FP32 CUDA-core solves, both
-    followed by the refinement step, give the same analysis to the FP32 tolerance."""
+    """The TF32-split tensor-core factorisation and solves and the FP32 CUDA-core
+    ones, both followed by the refinement step, give the same analysis to the FP32
+    tolerance."""
     w = WORKLOADS["small_48x26x3x1+1_n80_r2"]
     inp = make_inputs(w, np.float32)
     a = gpu_pipeline(w, inp, 1)
