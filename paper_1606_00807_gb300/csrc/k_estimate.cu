@@ -53,6 +53,13 @@ __device__ __forceinline__ void lds4v(const double* p, double (&v)[4]) {
   const double2 b = reinterpret_cast<const double2*>(p)[1];
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
+__device__ __forceinline__ void sts4v(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void sts4v(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
 
 // ---------------------------------------------------------------------------
 // Anomalies: U[l][m] = X[m][l] - mean_m X[m][l]
@@ -374,54 +381,110 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
     const T uu = L[p * ldg + p];
     __syncwarp();
 
-    // left-looking Cholesky of rows 0..p-1; row p becomes w = L^-1 g
+    // right-looking Cholesky in 4 x 4 tiles of the rows and columns 0..P4-1
+    // (P4 = p + 1 rounded up to 4, padding rows are identity rows).  Pivots are
+    // taken for the first p columns only, so row p becomes w = L^-1 g.  Step K:
+    // lane 0 factors diagonal tile K, lanes solve the tiles (I, K) below it
+    // against it, then lanes update the trailing tiles (I, J), K < J <= I, with
+    // 4 x 4 register tiles (64 multiply-adds per 12 vector loads).
+    const int P4 = (p1 + 3) & ~3;
+    for (int i = p1 + lane; i < P4; i += 32) {
+      for (int l = 0; l < i; ++l) L[i * ldg + l] = T(0);
+      L[i * ldg + i] = T(1);
+    }
+    __syncwarp();
+    const int nt = P4 >> 2;
     int err = 0;
-    for (int kc = 0; kc < p; ++kc) {
-      const T* Lk = L + kc * ldg;
-      T vals[RR];
+    for (int K = 0; K < nt; ++K) {
+      const int k0 = 4 * K;
+      if (lane == 0) {
+        T a[4][4];
 #pragma unroll
-      for (int t = 0; t < RR; ++t) {
-        const int i = lane + 32 * t;
-        vals[t] = T(0);
-        if (i >= kc && i <= p) {
-          const T* Li = L + i * ldg;
-          T dot0 = T(0), dot1 = T(0);
-          int l = 0;
-          for (; l + 4 <= kc; l += 4) {
-            T a4[4], b4[4];
-            lds4v(Li + l, a4);
-            lds4v(Lk + l, b4);
-            dot0 = fma(a4[0], b4[0], dot0);
-            dot1 = fma(a4[1], b4[1], dot1);
-            dot0 = fma(a4[2], b4[2], dot0);
-            dot1 = fma(a4[3], b4[3], dot1);
+        for (int r = 0; r < 4; ++r) lds4v(L + (k0 + r) * ldg + k0, a[r]);
+        int e = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int u = k0 + c;
+          T inv = T(1);
+          if (u < p) {
+            const T piv = a[c][c];
+            const bool fin = finite_val(piv);
+            if (fin && piv > T(0)) {
+              const T sd = sqrt(piv);
+              inv = T(1) / sd;
+              a[c][c] = sd;
+            } else if (!e) {
+              e = fin ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+            }
+            invd[u] = inv;
           }
-          for (; l < kc; ++l) dot0 = fma(Li[l], Lk[l], dot0);
-          vals[t] = Li[kc] - (dot0 + dot1);
+#pragma unroll
+          for (int r = c + 1; r < 4; ++r) a[r][c] *= inv;
+#pragma unroll
+          for (int r = c + 1; r < 4; ++r)
+#pragma unroll
+            for (int q2 = c + 1; q2 <= r; ++q2) a[r][q2] = fma(-a[r][c], a[q2][c], a[r][q2]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) sts4v(L + (k0 + r) * ldg + k0, a[r]);
+        invd[ldp - 1] = T(e);  // error code of this step (uniform read below)
+      }
+      __syncwarp();
+      {
+        const int e = (int)invd[ldp - 1];
+        if (e) {
+          err = e;
+          break;
+        }
+      }
+      // tiles (I, K) below: X L_KK^T = A_IK, rows of X solved left to right
+      const int nrem = nt - K - 1;
+      if (lane < nrem) {
+        T lk[4][4], iv[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          lds4v(L + (k0 + r) * ldg + k0, lk[r]);
+          iv[r] = (k0 + r < p) ? invd[k0 + r] : T(1);
+        }
+        const int i0 = k0 + 4 * (lane + 1);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          T xr[4];
+          lds4v(L + (i0 + r) * ldg + k0, xr);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            T acc = xr[c];
+#pragma unroll
+            for (int t = 0; t < c; ++t) acc = fma(-lk[c][t], xr[t], acc);
+            xr[c] = acc * iv[c];
+          }
+          sts4v(L + (i0 + r) * ldg + k0, xr);
         }
       }
       __syncwarp();
-      if (lane == (kc & 31)) {
-        T d = vals[0];
+      // trailing tiles (I, J), K < J <= I < nt
+      const int ntile = nrem * (nrem + 1) / 2;
+      for (int tix = lane; tix < ntile; tix += 32) {
+        int Ip = (int)((sqrtf(8.f * tix + 1.f) - 1.f) * 0.5f);
+        while ((Ip + 1) * (Ip + 2) / 2 <= tix) ++Ip;
+        while (Ip * (Ip + 1) / 2 > tix) --Ip;
+        const int Jp = tix - Ip * (Ip + 1) / 2;
+        const int i0 = k0 + 4 * (Ip + 1), j0 = k0 + 4 * (Jp + 1);
+        T li[4][4], lj[4][4], acc[4][4];
 #pragma unroll
-        for (int t = 1; t < RR; ++t)
-          if (t == (kc >> 5)) d = vals[t];
-        const bool fin = finite_val(d);
-        const T sd = (fin && d > T(0)) ? sqrt(d) : T(0);
-        // 1/sqrt(d) on success; 0 for a non-positive pivot; NaN for a non-finite one
-        invd[kc] = sd > T(0) ? T(1) / sd : (fin ? T(0) : T(NAN));
-        L[kc * ldg + kc] = sd;
-      }
-      __syncwarp();
-      const T inv = invd[kc];
-      if (!(inv > T(0))) {
-        err = (inv == inv) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
-        break;
-      }
+        for (int r = 0; r < 4; ++r) {
+          lds4v(L + (i0 + r) * ldg + k0, li[r]);
+          lds4v(L + (j0 + r) * ldg + k0, lj[r]);
+          lds4v(L + (i0 + r) * ldg + j0, acc[r]);
+        }
 #pragma unroll
-      for (int t = 0; t < RR; ++t) {
-        const int i = lane + 32 * t;
-        if (i > kc && i <= p) L[i * ldg + kc] = vals[t] * inv;
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc[r][c] = fma(-li[r][t], lj[c][t], acc[r][c]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) sts4v(L + (i0 + r) * ldg + j0, acc[r]);
       }
       __syncwarp();
     }
