@@ -29,7 +29,7 @@ namespace enkfmc {
 
 namespace {
 
-constexpr int kTcThreads = 128;                 // one warp group: thread m = member m
+constexpr int kSolveWarps = 8;                  // 4 member warps + 4 staging warps
 constexpr int kABytes = 128 * 32 * 4;           // one split of the member operand
 constexpr uint64_t kWaitNs = 2000000000ull;     // bound of every mbarrier wait (2 s)
 
@@ -65,13 +65,23 @@ __device__ __forceinline__ float tf32_rest(float x) {
   return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Producer warps' own barrier (named barrier 1, the 128 producer threads).
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// 256 threads: warps 0-3 are the member warps (thread m = member m = TMEM lane
+// m: TMEM columns, triangles, member operands, MMA issue by thread 0), warps
+// 4-7 stage operands (band tiles, their TF32 remainders, diagonal blocks).
+// One CTA-wide barrier per panel hands the staged operands over.
+__global__ void __launch_bounds__(kSolveWarps * 32, 1)
     k_bandsolve_tc(const Block* __restrict__ blocks, const float* __restrict__ band,
                    const float* __restrict__ invdiag, float* __restrict__ rhs, int N, int NU,
                    int nbufB, int WT, int32_t* __restrict__ status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int m = tid;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool member = warp < 4;
+  const int m = tid;          // member warps: member index
+  const int pt = tid - 128;   // staging warps: thread index
+  const int pw = warp - 4;
   const Block b = blocks[blockIdx.x];
   const int nb = b.nb, hb = b.hb;
   const float* F = band + b.band_off;
@@ -101,23 +111,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *slot;
-  const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
+  const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t bar_ready = tc::smem_u32(&bars[0]);
   const uint32_t bar_done0 = tc::smem_u32(&bars[1]);
   const uint32_t bar_done1 = tc::smem_u32(&bars[2]);
 
   int ngroups = 0;  // MMA groups issued so far (same value in every thread)
-  int pending = 0;  // this thread's outstanding timeout, folded into the next barrier
+  int pending = 0;  // this thread's outstanding timeout, folded into the next handoff
   bool aborted = false;
 
+  auto wait_ready_local = [&](int g) {
+    if (!tc::mbar_wait(bar_ready, (uint32_t)(g & 1), kWaitNs)) pending = 1;
+  };
   auto wait_done_local = [&](int g) {
     if (!tc::mbar_wait((g & 1) ? bar_done1 : bar_done0, (uint32_t)((g >> 1) & 1), kWaitNs))
       pending = 1;
   };
-  // barrier that also publishes every thread's cp.async data and agrees on aborts
-  auto sync_or_abort = [&](int bad) -> bool {
-    cp_async_wait_all();
-    bad = __syncthreads_or(bad | pending);
+  // the per-panel handoff: staged operands published, aborts agreed
+  auto handoff = [&]() -> bool {
+    tc::fence_before_sync();
+    const int bad = __syncthreads_or(pending);
     pending = 0;
     if (bad && tid == 0) record_error(status, ENKFMC_ETIMEOUT, (int64_t)blockIdx.x);
     return bad != 0;
@@ -152,6 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   };
 
+  // ---- member warps ----
   // 32 rows [c0, c0 + 32) of this member (zero beyond the block or member count)
   auto load_rows = [&](int c0, float (&z)[32]) {
     if (m < N) {
@@ -196,12 +210,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       put_split4(hi, lo, core_off(m, kc), v);
     }
   };
+
+  // ---- staging warps ----
   // Lpp[u][t] = L[c0+t][c0+u] (forward, t >= u) or L[c0+u][c0+t] (backward, t <= u),
   // invd[t] = 1 / L[c0+t][c0+t]; asynchronous copies, zeros stored directly
   auto prefetch_diag = [&](int c0, bool fwd, int buf) {
     const int nbc = min(32, nb - c0);
     float* Lq = Lpp + buf * 1024;
-    for (int e = tid; e < 1024; e += kTcThreads) {
+    for (int e = pt; e < 1024; e += 128) {
       const int u = e >> 5, t = e & 31;
       const float* src = nullptr;
       if (u < nbc && t < nbc) {
@@ -214,19 +230,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (src) cp_async4(Lq + e, src);
       else Lq[e] = 0.f;
     }
-    if (tid < 32) {
-      if (tid < nbc) cp_async4(invd + buf * 32 + tid, Fi + c0 + tid);
-      else invd[buf * 32 + tid] = 0.f;
+    if (pt < 32) {
+      if (pt < nbc) cp_async4(invd + buf * 32 + pt, Fi + c0 + pt);
+      else invd[buf * 32 + pt] = 0.f;
     }
   };
   // Raw tiles: lane (n mod 8, t mod 4) of a warp, warps over 8-row groups, the
   // 8 K chunks unrolled; every shared-memory word of a warp's store is distinct.
-  const int lane = tid & 31, nl = lane >> 2, tl = lane & 3;
+  const int nl = lane >> 2, tl = lane & 3;
   // forward group of panel c0: B rows n <-> block rows c0 + 32 + n, K index t <->
   // column c0 + t (per chunk: 4 columns x 8 consecutive rows)
   auto prefetch_fwd = [&](int c0, int len, int bbuf) {
     unsigned char* raw = sB + (size_t)(bbuf * 2 + 0) * bbytes;
-    for (int ng = warp; ng < (len >> 3); ng += kTcThreads / 32) {
+    for (int ng = pw; ng < (len >> 3); ng += 4) {
       const int i = c0 + 32 + ng * 8 + nl;
       float* d = reinterpret_cast<float*>(raw + ng * 1024 + nl * 16 + tl * 4);
       const float* src = F + (int64_t)(c0 + tl) * hb + i;
@@ -243,7 +259,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // c0 + t (per chunk: 8 rows x 4 consecutive t)
   auto prefetch_bwd = [&](int c0, int jlo, int len, int bbuf) {
     unsigned char* raw = sB + (size_t)(bbuf * 2 + 0) * bbytes;
-    for (int ng = warp; ng < (len >> 3); ng += kTcThreads / 32) {
+    for (int ng = pw; ng < (len >> 3); ng += 4) {
       const int j = jlo + ng * 8 + nl;
       float* d = reinterpret_cast<float*>(raw + ng * 1024 + nl * 16 + tl * 4);
       const float* src = F + (int64_t)j * hb + c0 + tl;
@@ -260,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   auto make_rest = [&](int len, int bbuf) {
     const float4* raw = reinterpret_cast<const float4*>(sB + (size_t)(bbuf * 2 + 0) * bbytes);
     float4* rest = reinterpret_cast<float4*>(sB + (size_t)(bbuf * 2 + 1) * bbytes);
-    for (int e = tid; e < len * 8; e += kTcThreads) {
+    for (int e = pt; e < len * 8; e += 128) {
       const float4 v = raw[e];
       rest[e] = make_float4(tf32_rest(v.x), tf32_rest(v.y), tf32_rest(v.z), tf32_rest(v.w));
     }
@@ -274,59 +290,75 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   float z[32];
 
   // ---------------- forward: L Y = B ----------------
-  for (int c = 0; c < WT; c += 32) tc::tmem_zero32(tlane + (uint32_t)c);
-  tc::tmem_wait_st();
-  prefetch_diag(0, true, 0);
-  if (32 < nb) prefetch_fwd(0, fwd_len(0), 0);
-  cp_async_commit();
-  load_rows(0, z);
-  (void)sync_or_abort(0);
-  if (32 < nb) make_rest(fwd_len(0), 0);
-  for (int p = 0; p < np; ++p) {
+  if (member) {
+    for (int c = 0; c < WT; c += 32) tc::tmem_zero32(tlane + (uint32_t)c);
+    tc::tmem_wait_st();
+    load_rows(0, z);
+  } else {
+    prefetch_diag(0, true, 0);
+    cp_async_commit();
+    cp_async_wait_all();
+  }
+  aborted = handoff();
+  for (int p = 0; p < np && !aborted; ++p) {
     const int c0 = p * 32;
     const bool below = c0 + 32 < nb;
-    if (p > 0) {
-      const int bad = !tc::mbar_wait(bar_ready, (uint32_t)((ngroups - 1) & 1), kWaitNs);
-      if (sync_or_abort(bad)) {
-        aborted = true;
-        break;
+    if (member) {
+      if (p > 0) {
+        wait_ready_local(ngroups - 1);
+        tc::fence_after_sync();
+        float d[32];
+        tc::tmem_ld32(tlane + (uint32_t)(c0 % WT), d);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) z[t] -= d[t];
       }
-      tc::fence_after_sync();
-      float d[32];
-      tc::tmem_ld32(tlane + (uint32_t)(c0 % WT), d);
+      {  // triangle: right-looking over the columns u of L_pp
+        const float* Lq = Lpp + (p & 1) * 1024;
+        const float* iv = invd + (p & 1) * 32;
 #pragma unroll
-      for (int t = 0; t < 32; ++t) z[t] -= d[t];
-      if (below) make_rest(fwd_len(c0), ngroups % nbufB);
-    }
-    {  // triangle: right-looking over the columns u of L_pp
-      const float* Lq = Lpp + (p & 1) * 1024;
-      const float* iv = invd + (p & 1) * 32;
+        for (int u = 0; u < 32; ++u) {
+          const float yu = z[u] * iv[u];
+          z[u] = yu;
+          const float4* col = reinterpret_cast<const float4*>(Lq + u * 32);
 #pragma unroll
-      for (int u = 0; u < 32; ++u) {
-        const float yu = z[u] * iv[u];
-        z[u] = yu;
-        const float4* col = reinterpret_cast<const float4*>(Lq + u * 32);
+          for (int g = (u + 1) >> 2; g < 8; ++g) {
+            const float4 q = col[g];
+            const float lv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int g = (u + 1) >> 2; g < 8; ++g) {
-          const float4 q = col[g];
-          const float lv[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (4 * g + k > u) z[4 * g + k] = fmaf(-lv[k], yu, z[4 * g + k]);
+            for (int k = 0; k < 4; ++k)
+              if (4 * g + k > u) z[4 * g + k] = fmaf(-lv[k], yu, z[4 * g + k]);
+          }
         }
       }
+      store_rows(c0, z);
+      if (below) put_member(ngroups & 1, z);
+      tc::tmem_zero32(tlane + (uint32_t)(c0 % WT));
+      tc::tmem_wait_st();
+      tc::fence_async_smem();
+      if (p + 1 < np) load_rows(c0 + 32, z);
+    } else {
+      if (below) {
+        const int H = ngroups - nbufB;  // last group that read the buffer to refill
+        if (H >= 0) wait_done_local(H);
+        prefetch_fwd(c0, fwd_len(c0), ngroups % nbufB);
+      }
+      if (p + 1 < np) prefetch_diag(c0 + 32, true, (p + 1) & 1);
+      cp_async_commit();
+      cp_async_wait_all();
+      producer_sync();
+      if (below) {
+        make_rest(fwd_len(c0), ngroups % nbufB);
+        tc::fence_async_smem();
+      }
     }
-    store_rows(c0, z);
-    if (below) put_member(ngroups & 1, z);
-    tc::tmem_zero32(tlane + (uint32_t)(c0 % WT));
-    tc::tmem_wait_st();
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
+    if (handoff()) {
+      aborted = true;
+      break;
+    }
     if (below) {
-      const int len = fwd_len(c0);
-      const int len1 = min(32, len);
       if (tid == 0) {
+        const int len = fwd_len(c0);
+        const int len1 = min(32, len);
         tc::fence_after_sync();
         issue(ngroups & 1, ngroups % nbufB, c0 + 32, len1, 0);
         tc::commit(bar_ready);
@@ -335,81 +367,87 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       ++ngroups;
     }
-    if (p + 1 < np) {
-      const int c1 = c0 + 32;
-      prefetch_diag(c1, true, (p + 1) & 1);
-      if (c1 + 32 < nb) {
-        const int H = ngroups - nbufB;  // last group that read the buffer to refill
-        if (H >= 0) wait_done_local(H);
-        prefetch_fwd(c1, fwd_len(c1), ngroups % nbufB);
-      }
-      cp_async_commit();
-      load_rows(c1, z);
-    }
   }
   if (!aborted && ngroups > 0) {
     wait_done_local(ngroups - 1);
-    if (sync_or_abort(0)) aborted = true;
+    aborted = handoff();
   }
 
   // ---------------- backward: L^T X = Y ----------------
   if (!aborted) {
-    for (int c = 0; c < WT; c += 32) tc::tmem_zero32(tlane + (uint32_t)c);
-    tc::tmem_wait_st();
     const int cl = (np - 1) * 32;
-    prefetch_diag(cl, false, 0);
-    if (cl >= 32) prefetch_bwd(cl, bwd_jlo(cl), cl - bwd_jlo(cl), ngroups % nbufB);
-    cp_async_commit();
-    load_rows(cl, z);
-    (void)sync_or_abort(0);
-    if (cl >= 32) make_rest(cl - bwd_jlo(cl), ngroups % nbufB);
+    if (member) {
+      for (int c = 0; c < WT; c += 32) tc::tmem_zero32(tlane + (uint32_t)c);
+      tc::tmem_wait_st();
+      load_rows(cl, z);
+    } else {
+      prefetch_diag(cl, false, 0);
+      cp_async_commit();
+      cp_async_wait_all();
+    }
+    aborted = handoff();
     int q = 0;  // panels done (selects the diagonal buffer)
-    for (int p = np - 1; p >= 0; --p, ++q) {
+    for (int p = np - 1; p >= 0 && !aborted; --p, ++q) {
       const int c0 = p * 32;
-      if (p < np - 1) {
-        const int bad = !tc::mbar_wait(bar_ready, (uint32_t)((ngroups - 1) & 1), kWaitNs);
-        if (sync_or_abort(bad)) {
-          aborted = true;
-          break;
+      const bool above = p >= 1;
+      if (member) {
+        if (p < np - 1) {
+          wait_ready_local(ngroups - 1);
+          tc::fence_after_sync();
+          float d[32];
+          tc::tmem_ld32(tlane + (uint32_t)(c0 % WT), d);
+#pragma unroll
+          for (int t = 0; t < 32; ++t) z[t] -= d[t];
         }
-        tc::fence_after_sync();
-        float d[32];
-        tc::tmem_ld32(tlane + (uint32_t)(c0 % WT), d);
+        {  // triangle: right-looking from the last row, rows u of L_pp
+          const float* Lq = Lpp + (q & 1) * 1024;
+          const float* iv = invd + (q & 1) * 32;
 #pragma unroll
-        for (int t = 0; t < 32; ++t) z[t] -= d[t];
-        if (p >= 1) make_rest(c0 - bwd_jlo(c0), ngroups % nbufB);
-      }
-      {  // triangle: right-looking from the last row, rows u of L_pp
-        const float* Lq = Lpp + (q & 1) * 1024;
-        const float* iv = invd + (q & 1) * 32;
+          for (int u = 31; u >= 0; --u) {
+            const float xu = z[u] * iv[u];
+            z[u] = xu;
+            const float4* row = reinterpret_cast<const float4*>(Lq + u * 32);
 #pragma unroll
-        for (int u = 31; u >= 0; --u) {
-          const float xu = z[u] * iv[u];
-          z[u] = xu;
-          const float4* row = reinterpret_cast<const float4*>(Lq + u * 32);
+            for (int g = 0; g < 8; ++g) {
+              if (4 * g >= u) break;
+              const float4 qv = row[g];
+              const float lv[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            if (4 * g >= u) break;
-            const float4 qv = row[g];
-            const float lv[4] = {qv.x, qv.y, qv.z, qv.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (4 * g + k < u) z[4 * g + k] = fmaf(-lv[k], xu, z[4 * g + k]);
+              for (int k = 0; k < 4; ++k)
+                if (4 * g + k < u) z[4 * g + k] = fmaf(-lv[k], xu, z[4 * g + k]);
+            }
           }
         }
+        store_rows(c0, z);
+        if (above) put_member(ngroups & 1, z);
+        tc::tmem_zero32(tlane + (uint32_t)(c0 % WT));
+        tc::tmem_wait_st();
+        tc::fence_async_smem();
+        if (above) load_rows(c0 - 32, z);
+      } else {
+        if (above) {
+          const int H = ngroups - nbufB;
+          if (H >= 0) wait_done_local(H);
+          prefetch_bwd(c0, bwd_jlo(c0), c0 - bwd_jlo(c0), ngroups % nbufB);
+          prefetch_diag(c0 - 32, false, (q + 1) & 1);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        producer_sync();
+        if (above) {
+          make_rest(c0 - bwd_jlo(c0), ngroups % nbufB);
+          tc::fence_async_smem();
+        }
       }
-      store_rows(c0, z);
-      if (p >= 1) put_member(ngroups & 1, z);
-      tc::tmem_zero32(tlane + (uint32_t)(c0 % WT));
-      tc::tmem_wait_st();
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (p >= 1) {
-        const int jlo = bwd_jlo(c0);
-        const int len = c0 - jlo;
-        const int len1 = min(32, len);
+      if (handoff()) {
+        aborted = true;
+        break;
+      }
+      if (above) {
         if (tid == 0) {
+          const int jlo = bwd_jlo(c0);
+          const int len = c0 - jlo;
+          const int len1 = min(32, len);
           tc::fence_after_sync();
           issue(ngroups & 1, ngroups % nbufB, c0 - len1, len1, len - len1);
           tc::commit(bar_ready);
@@ -417,20 +455,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc::commit((ngroups & 1) ? bar_done1 : bar_done0);
         }
         ++ngroups;
-        const int c1 = c0 - 32;
-        prefetch_diag(c1, false, (q + 1) & 1);
-        if (c1 >= 32) {
-          const int H = ngroups - nbufB;
-          if (H >= 0) wait_done_local(H);
-          prefetch_bwd(c1, bwd_jlo(c1), c1 - bwd_jlo(c1), ngroups % nbufB);
-        }
-        cp_async_commit();
-        load_rows(c1, z);
       }
     }
     if (!aborted && ngroups > 0) {
       wait_done_local(ngroups - 1);
-      if (sync_or_abort(0)) aborted = true;
+      aborted = handoff();
     }
   }
   if (aborted && ngroups > 0) {
@@ -728,7 +757,7 @@ cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int
   cudaError_t e = cudaFuncSetAttribute(k_bandsolve_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pl.smem);
   if (e != cudaSuccess) return e;
-  k_bandsolve_tc<<<nblock, kTcThreads, pl.smem, s>>>(blocks, band, invdiag, rhs, N, pl.NU,
+  k_bandsolve_tc<<<nblock, kSolveWarps * 32, pl.smem, s>>>(blocks, band, invdiag, rhs, N, pl.NU,
                                                      pl.nbufB, pl.WT, status);
   return cudaGetLastError();
 }
