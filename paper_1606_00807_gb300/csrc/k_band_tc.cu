@@ -59,6 +59,10 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// all but the most recently committed group complete
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
 // x - (x with the 13 low mantissa bits cleared): the part of x that a TF32
 // operand read drops, exact in FP32
 __device__ __forceinline__ float tf32_rest(float x) {
@@ -118,6 +122,8 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
 
   int ngroups = 0;  // MMA groups issued so far (same value in every thread)
   int pending = 0;  // this thread's outstanding timeout, folded into the next handoff
+  // two band buffers: the staging warps copy the next group's tile one panel ahead
+  const bool lookahead = nbufB == 2;
   bool aborted = false;
 
   auto wait_ready_local = [&](int g) {
@@ -295,9 +301,16 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
     tc::tmem_wait_st();
     load_rows(0, z);
   } else {
+    // diagonal block 0 and, with two band buffers, the tile of group 0
     prefetch_diag(0, true, 0);
+    if (lookahead && 32 < nb) prefetch_fwd(0, fwd_len(0), 0);
     cp_async_commit();
     cp_async_wait_all();
+    producer_sync();
+    if (lookahead && 32 < nb) {
+      make_rest(fwd_len(0), 0);
+      tc::fence_async_smem();
+    }
   }
   aborted = handoff();
   for (int p = 0; p < np && !aborted; ++p) {
@@ -336,6 +349,24 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
       tc::tmem_wait_st();
       tc::fence_async_smem();
       if (p + 1 < np) load_rows(c0 + 32, z);
+    } else if (lookahead) {
+      // interval p: the next diagonal block; the rest tile of this panel's group
+      // (raw tile copied during the previous interval); the raw tile of the next
+      // panel's group once the group that last read its buffer is done
+      if (p + 1 < np) prefetch_diag(c0 + 32, true, (p + 1) & 1);
+      cp_async_commit();
+      if (below && p > 0) {
+        cp_async_wait_prev();
+        producer_sync();
+        make_rest(fwd_len(c0), ngroups % 2);
+        tc::fence_async_smem();
+      }
+      if (c0 + 64 < nb) {
+        if (ngroups >= 1) wait_done_local(ngroups - 1);
+        prefetch_fwd(c0 + 32, fwd_len(c0 + 32), (ngroups + 1) % 2);
+      }
+      cp_async_commit();
+      cp_async_wait_prev();
     } else {
       if (below) {
         const int H = ngroups - nbufB;  // last group that read the buffer to refill
@@ -381,9 +412,16 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
       tc::tmem_wait_st();
       load_rows(cl, z);
     } else {
+      cp_async_wait_all();
       prefetch_diag(cl, false, 0);
+      if (lookahead && cl >= 32) prefetch_bwd(cl, bwd_jlo(cl), cl - bwd_jlo(cl), ngroups % 2);
       cp_async_commit();
       cp_async_wait_all();
+      producer_sync();
+      if (lookahead && cl >= 32) {
+        make_rest(cl - bwd_jlo(cl), ngroups % 2);
+        tc::fence_async_smem();
+      }
     }
     aborted = handoff();
     int q = 0;  // panels done (selects the diagonal buffer)
@@ -424,6 +462,22 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
         tc::tmem_wait_st();
         tc::fence_async_smem();
         if (above) load_rows(c0 - 32, z);
+      } else if (lookahead) {
+        if (above) prefetch_diag(c0 - 32, false, (q + 1) & 1);
+        cp_async_commit();
+        if (above && p < np - 1) {
+          cp_async_wait_prev();
+          producer_sync();
+          make_rest(c0 - bwd_jlo(c0), ngroups % 2);
+          tc::fence_async_smem();
+        }
+        if (p >= 2) {
+          const int c1 = c0 - 32;
+          if (ngroups >= 1) wait_done_local(ngroups - 1);
+          prefetch_bwd(c1, bwd_jlo(c1), c1 - bwd_jlo(c1), (ngroups + 1) % 2);
+        }
+        cp_async_commit();
+        cp_async_wait_prev();
       } else {
         if (above) {
           const int H = ngroups - nbufB;
