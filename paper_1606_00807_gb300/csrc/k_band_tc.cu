@@ -149,21 +149,23 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
     const uint32_t a_lo = tc::smem_u32(sA + (abuf * 2 + 1) * kABytes);
     const uint32_t b_hi = tc::smem_u32(sB + (size_t)(bbuf * 2 + 0) * bbytes);
     const uint32_t b_lo = tc::smem_u32(sB + (size_t)(bbuf * 2 + 1) * bbytes);
+    // the start-address field is (address >> 4): a byte offset o adds o >> 4
+    const uint64_t ah0 = tc::desc_kmajor(a_hi, 128, 1024);
+    const uint64_t al0 = tc::desc_kmajor(a_lo, 128, 1024);
+    const uint64_t bh0 = tc::desc_kmajor(b_hi, 128, 1024);
+    const uint64_t bl0 = tc::desc_kmajor(b_lo, 128, 1024);
     while (len > 0) {
       const int c = col0 % WT;
       const int n = min(min(len, WT - c), 256);
       const uint32_t id = tc::idesc_tf32(128, n);
-      const uint32_t boff = (uint32_t)(brow0 >> 3) * 1024u;
+      const uint64_t boff = (uint64_t)(brow0 >> 3) * 64u;  // 1024-byte row groups
       const uint32_t d = tbase + (uint32_t)c;
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
-        const uint64_t ah = tc::desc_kmajor(a_hi + ks * 256, 128, 1024);
-        const uint64_t al = tc::desc_kmajor(a_lo + ks * 256, 128, 1024);
-        const uint64_t bh = tc::desc_kmajor(b_hi + boff + ks * 256, 128, 1024);
-        const uint64_t bl = tc::desc_kmajor(b_lo + boff + ks * 256, 128, 1024);
-        tc::mma_tf32(d, ah, bl, id, 1);
-        tc::mma_tf32(d, al, bh, id, 1);
-        tc::mma_tf32(d, ah, bh, id, 1);
+        const uint64_t k16 = (uint64_t)ks * 16u;  // 256 bytes per K step
+        tc::mma_tf32(d, ah0 + k16, bl0 + boff + k16, id, 1);
+        tc::mma_tf32(d, al0 + k16, bh0 + boff + k16, id, 1);
+        tc::mma_tf32(d, ah0 + k16, bh0 + boff + k16, id, 1);
       }
       col0 += n;
       brow0 += n;
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
 #pragma unroll
         for (int t = 0; t < 32; ++t) z[t] -= d[t];
       }
-      {  // triangle: right-looking over the columns u of L_pp
+      if (32 * warp < N) {  // triangle: right-looking over the columns u of L_pp
         const float* Lq = Lpp + (p & 1) * 1024;
         const float* iv = invd + (p & 1) * 32;
 #pragma unroll
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
 #pragma unroll
           for (int t = 0; t < 32; ++t) z[t] -= d[t];
         }
-        {  // triangle: right-looking from the last row, rows u of L_pp
+        if (32 * warp < N) {  // triangle: right-looking from the last row, rows u of L_pp
           const float* Lq = Lpp + (q & 1) * 1024;
           const float* iv = invd + (q & 1) * 32;
 #pragma unroll
