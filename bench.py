@@ -235,13 +235,61 @@ def _time_steps(step, warmup, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def fwd_adj_line(wa, ia, dev, npdt, precision, tdt):
+    """Forward analysis and forward + adjoint (loss 1/2 |mean(X^a) - x_ref|^2,
+    dL/dX^a formed on the device, enkfmc_analyze_adjoint) on workload wa."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00807_gb300 import binding as B
+
+    stream = torch.cuda.Stream(device=dev)
+    h = B.Handle.from_workload(wa, precision=precision, stream=stream.cuda_stream)
+    h.set_observations(ia.obs_idx)
+    with torch.cuda.stream(stream):
+        put = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=npdt)).to(dev, tdt)
+        Xb, y, R, Z, xref = put(ia.Xb), put(ia.y), put(ia.R), put(ia.Z), put(ia.truth)
+        T = torch.empty((wa.n, h.info.pmax), device=dev, dtype=tdt)
+        D = torch.empty(wa.n, device=dev, dtype=tdt)
+        Xa = torch.empty_like(Xb)
+        Xa_bar = torch.empty_like(Xb)
+        Xb_bar = torch.empty_like(Xb)
+        y_bar = torch.empty_like(y)
+        R_bar = torch.empty_like(R)
+
+    def fwd():
+        h.estimate(Xb, T, D)
+        h.assemble(Xb, T, D, R)
+        h.analyze(Xb, y, R, Z, Xa)
+
+    def fwd_adj():
+        fwd()
+        with torch.cuda.stream(stream):
+            Xa_bar.copy_(((Xa.mean(dim=0) - xref) / wa.N).expand_as(Xa))
+        h.analyze_adjoint(Xa_bar, y_bar, R_bar, Xb_bar)
+
+    ms_f = _time_steps(fwd, 2, 5, stream)
+    ms_fa = _time_steps(fwd_adj, 1, 5, stream)
+    h.profile(True)
+    h.profile_read()
+    _time_steps(fwd_adj, 0, 2, stream)
+    prof = h.profile_read()
+    h.profile(False)
+    h.check("forward + adjoint steps")
+    h.close()
+    return {"workload": wa.name, "precision": "fp32" if precision == B.FP32 else "fp64",
+            "fwd_cycles_per_s": 1e3 / ms_f, "fwd_adj_cycles_per_s": 1e3 / ms_fa,
+            "fwd_ms": ms_f, "fwd_adj_ms": ms_fa, "adj_over_fwd": (ms_fa - ms_f) / ms_f,
+            "kernels_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}}
+
+
 def side_measurements(args, w, inp, value, dev):
-    """Two side lines of the headline metric, each on its own handle:
-    the plain FP64 form of the same workload (cycles/s and the FP32 speed-up
-    over it), and forward + adjoint at the T63 shape with N = 40 (the loss
-    L = 1/2 |mean(X^a) - x_ref|^2, its gradient dL/dX^a formed on the device,
-    then enkfmc_analyze_adjoint for X^b, y and diag(R)) against the forward
-    analysis alone."""
+    """Side lines of the headline metric, each on its own handle: the plain
+    FP64 form of the same workload (cycles/s and the FP32 speed-up over it);
+    forward + adjoint (the loss L = 1/2 |mean(X^a) - x_ref|^2, its gradient
+    dL/dX^a formed on the device, then enkfmc_analyze_adjoint for X^b, y and
+    diag(R)) against the forward analysis alone, on the same workload in FP32
+    and at the T63 shape with N = 40 in FP64."""
     import numpy as np
     import torch
 
@@ -272,49 +320,14 @@ def side_measurements(args, w, inp, value, dev):
     out["plain_fp64"] = {"workload": w.name, "value": 1e3 / ms, "unit": "cycles/s",
                          "ms_per_step": ms, "fp32_over_fp64": value / (1e3 / ms)}
 
+    out["fwd_adj_fp32"] = fwd_adj_line(w, inp, dev, np.float32, B.FP32, torch.float32)
+
     # forward + adjoint, T63 shape with N = 40: p = 37 predecessors from 40
     # members make the Gram matrices nearly singular, so this configuration runs
     # in FP64 (single precision reports EDNONPOS here)
     wa = WORKLOADS["t63_192x96x29_n40_r2"]
-    ia = make_inputs(wa, np.float64)
-    stream = torch.cuda.Stream(device=dev)
-    h = B.Handle.from_workload(wa, precision=B.FP64, stream=stream.cuda_stream)
-    h.set_observations(ia.obs_idx)
-    with torch.cuda.stream(stream):
-        put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev, torch.float64)
-        Xb, y, R, Z, xref = put(ia.Xb), put(ia.y), put(ia.R), put(ia.Z), put(ia.truth)
-        T = torch.empty((wa.n, h.info.pmax), device=dev, dtype=torch.float64)
-        D = torch.empty(wa.n, device=dev, dtype=torch.float64)
-        Xa = torch.empty_like(Xb)
-        Xa_bar = torch.empty_like(Xb)
-        Xb_bar = torch.empty_like(Xb)
-        y_bar = torch.empty_like(y)
-        R_bar = torch.empty_like(R)
-
-    def fwd():
-        h.estimate(Xb, T, D)
-        h.assemble(Xb, T, D, R)
-        h.analyze(Xb, y, R, Z, Xa)
-
-    def fwd_adj():
-        fwd()
-        with torch.cuda.stream(stream):
-            Xa_bar.copy_(((Xa.mean(dim=0) - xref) / wa.N).expand_as(Xa))
-        h.analyze_adjoint(Xa_bar, y_bar, R_bar, Xb_bar)
-
-    ms_f = _time_steps(fwd, 2, 5, stream)
-    ms_fa = _time_steps(fwd_adj, 1, 5, stream)
-    h.profile(True)
-    h.profile_read()
-    _time_steps(fwd_adj, 0, 2, stream)
-    prof = h.profile_read()
-    h.profile(False)
-    h.check("forward + adjoint steps")
-    h.close()
-    out["fwd_adj"] = {"workload": wa.name, "precision": "fp64",
-                      "fwd_cycles_per_s": 1e3 / ms_f, "fwd_adj_cycles_per_s": 1e3 / ms_fa,
-                      "fwd_ms": ms_f, "fwd_adj_ms": ms_fa, "adj_over_fwd": (ms_fa - ms_f) / ms_f,
-                      "kernels_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}}
+    out["fwd_adj"] = fwd_adj_line(wa, make_inputs(wa, np.float64), dev, np.float64, B.FP64,
+                                  torch.float64)
     return out
 
 

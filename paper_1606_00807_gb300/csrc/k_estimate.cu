@@ -264,6 +264,124 @@ __device__ __forceinline__ void ff_sub_prod(float& s, float& c, float x, float b
   c += e - perr;
 }
 
+// Right-looking Cholesky, in 4 x 4 tiles, of the leading nrows x nrows block
+// of the warp's lower-triangular matrix L (row stride ldg, a multiple of 4),
+// rows padded with identity rows up to a multiple of 4.  Pivots are taken for
+// the first npiv columns only (npiv = nrows - 1 leaves the last row as
+// L^-1 times itself: the solve of an augmented system).  Step K: lane 0
+// factors diagonal tile K, lanes solve the tiles (I, K) below it against it,
+// then lanes update the trailing tiles (I, J), K < J <= I, with 4 x 4 register
+// tiles (64 multiply-adds per 12 vector loads).  invd[u] = 1 / L[u][u] for
+// u < npiv; *code (a slot not among those) carries the error code between
+// lanes.  Returns 0 or ENKFMC_EDNONPOS / ENKFMC_ENONFINITE (same in every lane).
+template <typename T>
+__device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int npiv, int lane) {
+  const int p1 = nrows, p = npiv;
+  const int P4 = (p1 + 3) & ~3;
+  for (int i = p1 + lane; i < P4; i += 32) {
+    for (int l = 0; l < i; ++l) L[i * ldg + l] = T(0);
+    L[i * ldg + i] = T(1);
+  }
+  __syncwarp();
+  const int nt = P4 >> 2;
+  int err = 0;
+  for (int K = 0; K < nt; ++K) {
+    const int k0 = 4 * K;
+    if (lane == 0) {
+      T a[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) lds4v(L + (k0 + r) * ldg + k0, a[r]);
+      int e = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int u = k0 + c;
+        T inv = T(1);
+        if (u < p) {
+          const T piv = a[c][c];
+          const bool fin = finite_val(piv);
+          if (fin && piv > T(0)) {
+            const T sd = sqrt(piv);
+            inv = T(1) / sd;
+            a[c][c] = sd;
+          } else if (!e) {
+            e = fin ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+          }
+          invd[u] = inv;
+        }
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r) a[r][c] *= inv;
+#pragma unroll
+        for (int r = c + 1; r < 4; ++r)
+#pragma unroll
+          for (int q2 = c + 1; q2 <= r; ++q2) a[r][q2] = fma(-a[r][c], a[q2][c], a[r][q2]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) sts4v(L + (k0 + r) * ldg + k0, a[r]);
+      *code = T(e);  // error code of this step (uniform read below)
+    }
+    __syncwarp();
+    {
+      const int e = (int)*code;
+      if (e) {
+        err = e;
+        break;
+      }
+    }
+    // tiles (I, K) below: X L_KK^T = A_IK, rows of X solved left to right
+    const int nrem = nt - K - 1;
+    if (lane < nrem) {
+      T lk[4][4], iv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        lds4v(L + (k0 + r) * ldg + k0, lk[r]);
+        iv[r] = (k0 + r < p) ? invd[k0 + r] : T(1);
+      }
+      const int i0 = k0 + 4 * (lane + 1);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        T xr[4];
+        lds4v(L + (i0 + r) * ldg + k0, xr);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          T acc = xr[c];
+#pragma unroll
+          for (int t = 0; t < c; ++t) acc = fma(-lk[c][t], xr[t], acc);
+          xr[c] = acc * iv[c];
+        }
+        sts4v(L + (i0 + r) * ldg + k0, xr);
+      }
+    }
+    __syncwarp();
+    // trailing tiles (I, J), K < J <= I < nt
+    const int ntile = nrem * (nrem + 1) / 2;
+    for (int tix = lane; tix < ntile; tix += 32) {
+      int Ip = (int)((sqrtf(8.f * tix + 1.f) - 1.f) * 0.5f);
+      while ((Ip + 1) * (Ip + 2) / 2 <= tix) ++Ip;
+      while (Ip * (Ip + 1) / 2 > tix) --Ip;
+      const int Jp = tix - Ip * (Ip + 1) / 2;
+      const int i0 = k0 + 4 * (Ip + 1), j0 = k0 + 4 * (Jp + 1);
+      T li[4][4], lj[4][4], acc[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        lds4v(L + (i0 + r) * ldg + k0, li[r]);
+        lds4v(L + (j0 + r) * ldg + k0, lj[r]);
+        lds4v(L + (i0 + r) * ldg + j0, acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) acc[r][c] = fma(-li[r][t], lj[c][t], acc[r][c]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) sts4v(L + (i0 + r) * ldg + j0, acc[r]);
+    }
+    __syncwarp();
+  }
+
+  return err;
+}
+
 constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 
 // RR: rounds of 32 rows covering pmax + 1; MR: rounds of 32 members covering N.
@@ -381,113 +499,10 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
     const T uu = L[p * ldg + p];
     __syncwarp();
 
-    // right-looking Cholesky in 4 x 4 tiles of the rows and columns 0..P4-1
-    // (P4 = p + 1 rounded up to 4, padding rows are identity rows).  Pivots are
-    // taken for the first p columns only, so row p becomes w = L^-1 g.  Step K:
-    // lane 0 factors diagonal tile K, lanes solve the tiles (I, K) below it
-    // against it, then lanes update the trailing tiles (I, J), K < J <= I, with
-    // 4 x 4 register tiles (64 multiply-adds per 12 vector loads).
-    const int P4 = (p1 + 3) & ~3;
-    for (int i = p1 + lane; i < P4; i += 32) {
-      for (int l = 0; l < i; ++l) L[i * ldg + l] = T(0);
-      L[i * ldg + i] = T(1);
-    }
-    __syncwarp();
-    const int nt = P4 >> 2;
-    int err = 0;
-    for (int K = 0; K < nt; ++K) {
-      const int k0 = 4 * K;
-      if (lane == 0) {
-        T a[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) lds4v(L + (k0 + r) * ldg + k0, a[r]);
-        int e = 0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int u = k0 + c;
-          T inv = T(1);
-          if (u < p) {
-            const T piv = a[c][c];
-            const bool fin = finite_val(piv);
-            if (fin && piv > T(0)) {
-              const T sd = sqrt(piv);
-              inv = T(1) / sd;
-              a[c][c] = sd;
-            } else if (!e) {
-              e = fin ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
-            }
-            invd[u] = inv;
-          }
-#pragma unroll
-          for (int r = c + 1; r < 4; ++r) a[r][c] *= inv;
-#pragma unroll
-          for (int r = c + 1; r < 4; ++r)
-#pragma unroll
-            for (int q2 = c + 1; q2 <= r; ++q2) a[r][q2] = fma(-a[r][c], a[q2][c], a[r][q2]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) sts4v(L + (k0 + r) * ldg + k0, a[r]);
-        invd[ldp - 1] = T(e);  // error code of this step (uniform read below)
-      }
-      __syncwarp();
-      {
-        const int e = (int)invd[ldp - 1];
-        if (e) {
-          err = e;
-          break;
-        }
-      }
-      // tiles (I, K) below: X L_KK^T = A_IK, rows of X solved left to right
-      const int nrem = nt - K - 1;
-      if (lane < nrem) {
-        T lk[4][4], iv[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          lds4v(L + (k0 + r) * ldg + k0, lk[r]);
-          iv[r] = (k0 + r < p) ? invd[k0 + r] : T(1);
-        }
-        const int i0 = k0 + 4 * (lane + 1);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          T xr[4];
-          lds4v(L + (i0 + r) * ldg + k0, xr);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            T acc = xr[c];
-#pragma unroll
-            for (int t = 0; t < c; ++t) acc = fma(-lk[c][t], xr[t], acc);
-            xr[c] = acc * iv[c];
-          }
-          sts4v(L + (i0 + r) * ldg + k0, xr);
-        }
-      }
-      __syncwarp();
-      // trailing tiles (I, J), K < J <= I < nt
-      const int ntile = nrem * (nrem + 1) / 2;
-      for (int tix = lane; tix < ntile; tix += 32) {
-        int Ip = (int)((sqrtf(8.f * tix + 1.f) - 1.f) * 0.5f);
-        while ((Ip + 1) * (Ip + 2) / 2 <= tix) ++Ip;
-        while (Ip * (Ip + 1) / 2 > tix) --Ip;
-        const int Jp = tix - Ip * (Ip + 1) / 2;
-        const int i0 = k0 + 4 * (Ip + 1), j0 = k0 + 4 * (Jp + 1);
-        T li[4][4], lj[4][4], acc[4][4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          lds4v(L + (i0 + r) * ldg + k0, li[r]);
-          lds4v(L + (j0 + r) * ldg + k0, lj[r]);
-          lds4v(L + (i0 + r) * ldg + j0, acc[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int t = 0; t < 4; ++t) acc[r][c] = fma(-li[r][t], lj[c][t], acc[r][c]);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) sts4v(L + (i0 + r) * ldg + j0, acc[r]);
-      }
-      __syncwarp();
-    }
+    // right-looking tiled Cholesky; pivots for the first p columns, so row p
+    // becomes w = L^-1 g
+    const int err0 = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p1, p, lane);
+    int err = err0;
 
     T Dj = T(0);
     if (!err) {
@@ -753,45 +768,7 @@ __global__ void __launch_bounds__(256) k_adj_regress(
       for (int i = lane; i < p; i += 32) L[i * ldg + i] += lam;
     }
     __syncwarp();
-    int err = 0;
-    for (int kc = 0; kc < p; ++kc) {
-      const T* Lk = L + kc * ldg;
-      T vals[kMaxRounds * 2];
-#pragma unroll
-      for (int t = 0; t < kMaxRounds * 2; ++t) {
-        const int i = lane + 32 * t;
-        vals[t] = T(0);
-        if (i >= kc && i < p) {
-          const T* Li = L + i * ldg;
-          T dot = T(0);
-          for (int l = 0; l < kc; ++l) dot = fma(Li[l], Lk[l], dot);
-          vals[t] = Li[kc] - dot;
-        }
-      }
-      __syncwarp();
-      if (lane == (kc & 31)) {
-        T d = vals[0];
-#pragma unroll
-        for (int t = 1; t < kMaxRounds * 2; ++t)
-          if (t == (kc >> 5)) d = vals[t];
-        const bool fin = finite_val(d);
-        const T sd = (fin && d > T(0)) ? sqrt(d) : T(0);
-        invd[kc] = sd > T(0) ? T(1) / sd : (fin ? T(0) : T(NAN));
-        L[kc * ldg + kc] = sd;
-      }
-      __syncwarp();
-      const T inv = invd[kc];
-      if (!(inv > T(0))) {
-        err = (inv == inv) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
-        break;
-      }
-#pragma unroll
-      for (int t = 0; t < kMaxRounds * 2; ++t) {
-        const int i = lane + 32 * t;
-        if (i > kc && i < p) L[i * ldg + kc] = vals[t] * inv;
-      }
-      __syncwarp();
-    }
+    const int err = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p, p, lane);
     if (err) {
       if (lane == 0) record_error(status, err, rowj);
       return;
@@ -951,7 +928,8 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
     return cudaErrorInvalidConfiguration;
   const int nH = cov_offset_count(g.r, g.vr);
   const int ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  const int ldg = ldp | 1;
+  // row stride = 4 (mod 8): 16-byte tile rows, conflict-free for 8 consecutive lanes
+  const int ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
   size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 3 * (size_t)ldp);
   wb = (wb + 15) / 16 * 16;
   const int offbytes = (3 * g.pmax + 15) / 16 * 16;
