@@ -60,6 +60,25 @@ __device__ __forceinline__ void sts4v(double* p, const double (&v)[4]) {
   reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
+// four consecutive elements from 16-byte aligned global memory
+__device__ __forceinline__ void ldg4v(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ldg4v(const double* p, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+// p[0..3] += v (one 16-byte vector atomic in single precision; entries that
+// lie at or beyond N add zero, the padding of the member dimension)
+__device__ __forceinline__ void atomic_add4(float* p, const float (&v)[4]) {
+  atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void atomic_add4(double* p, const double (&v)[4]) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a) atomicAdd(p + a, v[a]);
+}
 
 // ---------------------------------------------------------------------------
 // Anomalies: U[l][m] = X[m][l] - mean_m X[m][l]
@@ -690,56 +709,62 @@ __global__ void __launch_bounds__(256) k_adj_regress(
   const T Dj = inner ? Dg[jlab] : De[rowj];
   for (int i = lane; i < p; i += 32) vb[i] = -trow[sl[i]];
   __syncwarp();
-  // e = u - U_P^T beta; a_j, b_j in registers
-  T e[kMaxRounds], aj[kMaxRounds], bj[kMaxRounds];
+  // members 4 lane .. 4 lane + 3 of this lane (N <= 128): vector loads, and
+  // one vector atomic per predecessor for U-bar
+  const int m0 = 4 * lane;
+  auto ld4 = [&](const T* row, T (&o)[4]) {
+    if (m0 < ldN) {
+      ldg4v(row + m0, o);
 #pragma unroll
-  for (int t = 0; t < kMaxRounds; ++t) {
-    const int m = lane + 32 * t;
-    e[t] = m < N ? U[(int64_t)jlab * ldN + m] : T(0);
-    aj[t] = m < N ? aT[rowj * ldN + m] : T(0);
-    bj[t] = m < N ? bT[rowj * ldN + m] : T(0);
-  }
+      for (int a = 0; a < 4; ++a)
+        if (m0 + a >= N) o[a] = T(0);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) o[a] = T(0);
+    }
+  };
+  // e = u - U_P^T beta; a_j, b_j in registers
+  T e[4], aj[4], bj[4];
+  ld4(U + (int64_t)jlab * ldN, e);
+  ld4(aT + rowj * ldN, aj);
+  ld4(bT + rowj * ldN, bj);
   for (int i = 0; i < p; ++i) {
     const T bi = vb[i];
-    const T* Ui = U + (int64_t)q[i] * ldN;
+    T u4[4];
+    ld4(U + (int64_t)q[i] * ldN, u4);
 #pragma unroll
-    for (int t = 0; t < kMaxRounds; ++t) {
-      const int m = lane + 32 * t;
-      if (m < N) e[t] = fma(-Ui[m], bi, e[t]);
-    }
+    for (int a = 0; a < 4; ++a) e[a] = fma(-u4[a], bi, e[a]);
   }
   T ab = 0;
 #pragma unroll
-  for (int t = 0; t < kMaxRounds; ++t) ab = fma(aj[t], bj[t], ab);
+  for (int a = 0; a < 4; ++a) ab = fma(aj[a], bj[a], ab);
   ab = warp_sum(ab);
   const T Dbar = ab / (Dj * Dj);
-  T eb[kMaxRounds];
+  T eb[4];
 #pragma unroll
-  for (int t = 0; t < kMaxRounds; ++t) eb[t] = T(2) * Dbar * e[t] / T(N - 1);
+  for (int a = 0; a < 4; ++a) eb[a] = T(2) * Dbar * e[a] / T(N - 1);
   // betabar
   const T invD = T(1) / Dj;
   for (int i = 0; i < p; ++i) {
-    const T* Ui = U + (int64_t)q[i] * ldN;
-    const T* xi = dxT + (b.row_off + qr[i]) * ldN;
-    const T* li = lamT + (b.row_off + qr[i]) * ldN;
+    T u4[4], x4[4], l4[4];
+    ld4(U + (int64_t)q[i] * ldN, u4);
+    ld4(dxT + (b.row_off + qr[i]) * ldN, x4);
+    ld4(lamT + (b.row_off + qr[i]) * ldN, l4);
     T s1 = 0, s2 = 0;
 #pragma unroll
-    for (int t = 0; t < kMaxRounds; ++t) {
-      const int m = lane + 32 * t;
-      if (m < N) {
-        s1 = fma(aj[t], xi[m], s1);
-        s1 = fma(bj[t], li[m], s1);
-        s2 = fma(Ui[m], eb[t], s2);
-      }
+    for (int a = 0; a < 4; ++a) {
+      s1 = fma(aj[a], x4[a], s1);
+      s1 = fma(bj[a], l4[a], s1);
+      s2 = fma(u4[a], eb[a], s2);
     }
     s1 = warp_sum(s1);
     s2 = warp_sum(s2);
     if (lane == (i & 31)) va[i] = s1 * invD - s2;
   }
   __syncwarp();
-  T f[kMaxRounds];
+  T f[4];
 #pragma unroll
-  for (int t = 0; t < kMaxRounds; ++t) f[t] = eb[t];
+  for (int a = 0; a < 4; ++a) f[a] = eb[a];
   T kappa = 0;
   if (p > 0) {
     // Gram factor from the covariance table (as in the forward pass)
@@ -795,31 +820,22 @@ __global__ void __launch_bounds__(256) k_adj_regress(
     if (lam > T(0)) kappa = T(2) * T(ridge_c) / T(p) * vbeta;
     for (int i = 0; i < p; ++i) {
       const T vi = va[i];
-      const T* Ui = U + (int64_t)q[i] * ldN;
+      T u4[4];
+      ld4(U + (int64_t)q[i] * ldN, u4);
 #pragma unroll
-      for (int t = 0; t < kMaxRounds; ++t) {
-        const int m = lane + 32 * t;
-        if (m < N) f[t] = fma(Ui[m], vi, f[t]);
-      }
+      for (int a = 0; a < 4; ++a) f[a] = fma(u4[a], vi, f[a]);
     }
     // Ubar_qi += v_i e - beta_i f - kappa U_qi
     for (int i = 0; i < p; ++i) {
       const T vi = va[i], bi = vb[i];
-      const T* Ui = U + (int64_t)q[i] * ldN;
-      T* Ub = Ubar + (int64_t)q[i] * ldN;
+      T u4[4], d4[4];
+      ld4(U + (int64_t)q[i] * ldN, u4);
 #pragma unroll
-      for (int t = 0; t < kMaxRounds; ++t) {
-        const int m = lane + 32 * t;
-        if (m < N) atomicAdd(Ub + m, vi * e[t] - bi * f[t] - kappa * Ui[m]);
-      }
+      for (int a = 0; a < 4; ++a) d4[a] = vi * e[a] - bi * f[a] - kappa * u4[a];
+      if (m0 < N) atomic_add4(Ubar + (int64_t)q[i] * ldN + m0, d4);
     }
   }
-  T* Uj = Ubar + (int64_t)jlab * ldN;
-#pragma unroll
-  for (int t = 0; t < kMaxRounds; ++t) {
-    const int m = lane + 32 * t;
-    if (m < N) atomicAdd(Uj + m, f[t]);
-  }
+  if (m0 < N) atomic_add4(Ubar + (int64_t)jlab * ldN + m0, f);
 }
 
 }  // namespace
