@@ -401,6 +401,35 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
   return err;
 }
 
+// Pair table of the typical row, whose predecessors are exactly the stencil
+// slots 0..pf-1 (pf = pmax minus the seam slots of a periodic grid): entry pi of
+// the lower triangle of the augmented Gram matrix (row-major, index pf = the row
+// itself) -> {i | l << 8 | sel << 16, column h of the covariance table}, the
+// entry being C[(sel ? q[l] : q[i]) * nH + h] (as cov_lookup resolves it).
+__device__ inline void build_pair_table(const Geom& g, int pf, int2* ptab) {
+  const int np = (pf + 1) * (pf + 2) / 2;
+  const int w4 = 4 * g.r + 1;
+  const int B = (2 * g.vr + 1) * w4 * w4;
+  const int t0 = (B - 1) / 2;
+  for (int pi = threadIdx.x; pi < np; pi += blockDim.x) {
+    int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= pi) ++i;
+    while (i * (i + 1) / 2 > pi) --i;
+    const int l = pi - i * (i + 1) / 2;
+    int dki = 0, dyi = 0, dxi = 0, dkl = 0, dyl = 0, dxl = 0;
+    if (i < pf) slot_offset(i, g.r, g.vr, dki, dyi, dxi);
+    if (l < pf) slot_offset(l, g.r, g.vr, dkl, dyl, dxl);
+    const int t = ((dkl - dki + g.vr) * w4 + (dyl - dyi + 2 * g.r)) * w4 + (dxl - dxi + 2 * g.r);
+    ptab[pi] = t >= t0 ? make_int2(i | (l << 8), t - t0)
+                       : make_int2(i | (l << 8) | (1 << 16), B - 1 - t - t0);
+  }
+}
+
+__host__ __device__ inline int pair_table_bytes(int pmax, int r, int periodic) {
+  const int pf = pmax - (periodic ? r : 0);
+  return ((pf + 1) * (pf + 2) / 2 * 8 + 15) / 16 * 16;
+}
+
 constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 
 // RR: rounds of 32 rows covering pmax + 1; MR: rounds of 32 members covering N.
@@ -425,8 +454,12 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
     off[pmax + s] = (signed char)dy;
     off[2 * pmax + s] = (signed char)dx;
   }
+  const int pf = pmax - (g.periodic ? g.r : 0);
+  int2* ptab = reinterpret_cast<int2*>(smem + offbytes);
+  build_pair_table(g, pf, ptab);
   __syncthreads();
-  unsigned char* base = smem + offbytes + (size_t)warp * warp_bytes;
+  unsigned char* base = smem + offbytes + pair_table_bytes(pmax, g.r, g.periodic) +
+                        (size_t)warp * warp_bytes;
   int* q = reinterpret_cast<int*>(base);   // [ldp] component labels (q[p] = j)
   int* sl = q + ldp;                        // [ldp] slot of compacted entry (-1 = j)
   int* sidx = sl + ldp;                     // [ldp] compacted index of slot s
@@ -492,6 +525,14 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
 
     // gather the augmented Gram matrix, lower triangle, rows 0..p
     const int npair = p1 * (p1 + 1) / 2;
+    const bool typical = p == pf && (p == 0 || sl[p - 1] == pf - 1);
+    if (typical) {
+      for (int pi = lane; pi < npair; pi += 32) {
+        const int2 e = ptab[pi];
+        const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
+        L[i * ldg + l] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
+      }
+    } else
     for (int pi = lane; pi < npair; pi += 32) {
       int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
       while ((i + 1) * (i + 2) / 2 <= pi) ++i;
@@ -886,7 +927,7 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
   const int ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
   size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 4 * (size_t)ldp);
   wb = (wb + 15) / 16 * 16;
-  const int offbytes = (3 * g.pmax + 15) / 16 * 16;
+  const int offbytes = (3 * g.pmax + 15) / 16 * 16 + pair_table_bytes(g.pmax, g.r, g.periodic);
   int wpc = (int)((96 * 1024 - offbytes) / wb);
   if (wpc > 8) wpc = 8;
   if (wpc < 1) {
