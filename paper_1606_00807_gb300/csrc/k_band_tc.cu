@@ -612,19 +612,20 @@ __global__ void __launch_bounds__(kCholThreads, 1)
                            (int64_t)blockIdx.x);
             ok = false;
           } else {
+            // branch-free: every lane runs the same instructions, selects keep
+            // the entries it does not own
             const float d = sqrtf(piv);
             const float inv = 1.f / d;
+            a[u] = lane == u ? d : (lane > u ? a[u] * inv : a[u]);
             if (lane == u) {
-              a[u] = d;
               invs[u] = inv;
               invdiag[b.row_off + c0 + u] = inv;
-            } else if (lane > u) {
-              a[u] *= inv;
             }
 #pragma unroll
             for (int v = u + 1; v < 32; ++v) {
               const float lv = __shfl_sync(0xffffffffu, a[u], v);  // L[v][u]
-              if (lane >= v) a[v] = fmaf(-a[u], lv, a[v]);
+              const float upd = fmaf(-a[u], lv, a[v]);
+              a[v] = lane >= v ? upd : a[v];
             }
           }
         }
@@ -687,21 +688,20 @@ __global__ void __launch_bounds__(kCholThreads, 1)
       if (tid == 0) {
         tc::fence_after_sync();
         const uint32_t id = tc::idesc_tf32(128, 128);
+        // the start-address field is (address >> 4): a byte offset o adds o >> 4
+        const uint64_t dh0 = tc::desc_kmajor(hi0, 128, 1024);
+        const uint64_t dl0 = tc::desc_kmajor(lo0, 128, 1024);
         for (int k = 0; k < nr; ++k) {
           int mi, nj;
           syrk_tile(t0 + k, mi, nj);
           const uint32_t d = tbase + (uint32_t)(128 * k);
+          const uint64_t ao = (uint64_t)mi * 1024u, bo = (uint64_t)nj * 1024u;  // 16 KB tiles
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t ao = (uint32_t)(mi * 16 * 1024 + ks * 256);
-            const uint32_t bo = (uint32_t)(nj * 16 * 1024 + ks * 256);
-            const uint64_t ah = tc::desc_kmajor(hi0 + ao, 128, 1024);
-            const uint64_t al = tc::desc_kmajor(lo0 + ao, 128, 1024);
-            const uint64_t bh = tc::desc_kmajor(hi0 + bo, 128, 1024);
-            const uint64_t bl = tc::desc_kmajor(lo0 + bo, 128, 1024);
-            tc::mma_tf32(d, ah, bl, id, ks > 0 ? 1u : 0u);
-            tc::mma_tf32(d, al, bh, id, 1);
-            tc::mma_tf32(d, ah, bh, id, 1);
+            const uint64_t k16 = (uint64_t)ks * 16u;  // 256 bytes per K step
+            tc::mma_tf32(d, dh0 + ao + k16, dl0 + bo + k16, id, ks > 0 ? 1u : 0u);
+            tc::mma_tf32(d, dl0 + ao + k16, dh0 + bo + k16, id, 1);
+            tc::mma_tf32(d, dh0 + ao + k16, dh0 + bo + k16, id, 1);
           }
         }
         tc::commit(bar_a);
