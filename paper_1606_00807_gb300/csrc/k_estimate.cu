@@ -256,6 +256,119 @@ __global__ void __launch_bounds__(256) k_covtable(const Geom g, const T* __restr
   }
 }
 
+// Covariance table, member-major staging (even r): the window of a member
+// chunk is stored as S[m][cell], rows of Wp4 cells padded with zeros, so a
+// thread's 4 a-cells are one 16-byte read and its 7 b-cells two aligned 16-byte
+// reads (the b window starts at dx = -2r or 0, a multiple of 4 from the a
+// cells): 3 shared-memory reads per 16 multiply-adds, no bounds tests.
+template <typename T, int MC>
+__global__ void __launch_bounds__(256) k_covtable4(const Geom g, const T* __restrict__ U,
+                                                   T* __restrict__ C, int W, int nH, int nrho,
+                                                   int Wp4) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = g.r, r2 = 2 * r, w4 = 4 * r + 1;
+  const int Wp = W + 4 * r;
+  const int SLD = nrho * Wp4;  // cells per member (a multiple of 4)
+  T* S = reinterpret_cast<T*>(smem);   // [MC][SLD]
+  T* Cs = S + (size_t)MC * SLD;        // [W][nH]
+  int plane = blockIdx.z, v = 0;
+  while (plane >= g.var_lev[v]) {
+    plane -= g.var_lev[v];
+    ++v;
+  }
+  const int k = plane, y = blockIdx.y, x0 = blockIdx.x * W;
+  const int nlev_v = g.var_lev[v];
+  const int tid = threadIdx.x;
+  const int atiles = W / 4;
+  const int dxt_full = (w4 + 3) / 4, dxt_half = (r2 + 1 + 3) / 4;
+  const int ntiles = (dxt_half + (nrho - 1) * dxt_full) * atiles;
+  for (int i = tid; i < W * nH; i += blockDim.x) Cs[i] = T(0);
+
+  for (int m0 = 0; m0 < g.N; m0 += MC) {
+    __syncthreads();
+    constexpr int VEC = 16 / sizeof(T);
+    const bool full = m0 + MC <= g.ldN;
+    for (int cell = tid; cell < SLD; cell += blockDim.x) {
+      const int rho = cell / Wp4, chi = cell - rho * Wp4;
+      int dk, dy, dxlo;
+      cov_row(rho, r, dk, dy, dxlo);
+      const int kk = k + dk, yy = y + dy;
+      int xx = x0 - r2 + chi;
+      bool ok = chi < Wp && kk < nlev_v && yy >= 0 && yy < g.nlat;
+      if (ok && (xx < 0 || xx >= g.nlon)) {
+        if (g.periodic) xx = imod(xx, g.nlon);
+        else ok = false;
+      }
+      if (ok && full) {
+        const T* src = U + coords_label(g, v, kk, yy, xx) * g.ldN + m0;
+#pragma unroll
+        for (int q = 0; q < MC / VEC; ++q) {
+          const float4 f = reinterpret_cast<const float4*>(src)[q];
+          const T* e = reinterpret_cast<const T*>(&f);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) S[(size_t)(q * VEC + u) * SLD + cell] = e[u];
+        }
+      } else {
+        const T* src = ok ? U + coords_label(g, v, kk, yy, xx) * g.ldN : nullptr;
+#pragma unroll
+        for (int mm = 0; mm < MC; ++mm)
+          S[(size_t)mm * SLD + cell] = (ok && m0 + mm < g.N) ? src[m0 + mm] : T(0);
+      }
+    }
+    __syncthreads();
+    const int mcnt = min(MC, g.N - m0);
+    for (int tile = tid; tile < ntiles; tile += blockDim.x) {
+      const int at = tile % atiles;
+      int rest = tile / atiles;
+      int rho, dxt;
+      if (rest < dxt_half) {
+        rho = 0;
+        dxt = rest;
+      } else {
+        rest -= dxt_half;
+        rho = 1 + rest / dxt_full;
+        dxt = rest % dxt_full;
+      }
+      int dk, dy, dxlo;
+      cov_row(rho, r, dk, dy, dxlo);
+      const int dx0 = dxlo + 4 * dxt;
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      const T* Sa = S + (r2 + 4 * at);                     // row 0: the a cells
+      const T* Sb = S + rho * Wp4 + (r2 + 4 * at + dx0);   // row rho: the b cells
+      for (int mm = 0; mm < mcnt; ++mm) {
+        T av[4], b0[4], b1[4];
+        lds4v(Sa + (size_t)mm * SLD, av);
+        lds4v(Sb + (size_t)mm * SLD, b0);
+        lds4v(Sb + (size_t)mm * SLD + 4, b1);
+        const T bv[7] = {b0[0], b0[1], b0[2], b0[3], b1[0], b1[1], b1[2]};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[i + j], acc[i][j]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int dx = dx0 + j;
+        if (dx > r2) continue;
+        const int t = ((dk + g.vr) * w4 + (dy + r2)) * w4 + (dx + r2);
+        const int h = t - ((2 * g.vr + 1) * w4 * w4 - 1) / 2;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) Cs[(4 * at + i) * nH + h] += acc[i][j];
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < W * nH; idx += blockDim.x) {
+    const int a = idx / nH, h = idx - a * nH;
+    const int x = x0 + a;
+    if (x < g.nlon) C[coords_label(g, v, k, y, x) * nH + h] = Cs[idx];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Row regressions
 // ---------------------------------------------------------------------------
@@ -900,6 +1013,26 @@ cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
   const int r = g.r;
   const int nH = cov_offset_count(r, g.vr);
   const int nrho = 1 + 2 * r + g.vr * (4 * r + 1);
+  if (r % 2 == 0) {  // aligned b windows: member-major staging
+    int W = r <= 2 ? 64 : 32;
+    auto bytes = [&](int w) {
+      const int wp4 = (w + 4 * r + 4 + 3) / 4 * 4;
+      return sizeof(T) * ((size_t)MC * nrho * wp4 + (size_t)w * nH);
+    };
+    while (bytes(W) > 200 * 1024 && W > 8) W /= 2;
+    if (bytes(W) <= 220 * 1024) {
+      const int Wp4 = (W + 4 * r + 4 + 3) / 4 * 4;
+      cudaError_t e = cudaFuncSetAttribute(k_covtable4<T, MC>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bytes(W));
+      if (e != cudaSuccess) return e;
+      int planes = 0;
+      for (int v = 0; v < g.nvar; ++v) planes += g.var_lev[v];
+      const dim3 grid((g.nlon + W - 1) / W, g.nlat, planes);
+      k_covtable4<T, MC><<<grid, 256, bytes(W), s>>>(g, U, C, W, nH, nrho, Wp4);
+      return cudaGetLastError();
+    }
+  }
   int W = r <= 2 ? 64 : 32;
   size_t smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 1) + (size_t)W * nH);
   while (smem > 200 * 1024 && W > 8) {
