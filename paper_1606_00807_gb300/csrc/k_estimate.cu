@@ -722,7 +722,9 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
           if (lane == (i & 31)) va[i] = (T)(part - (float)lam * (float)vb[i]);
         }
         __syncwarp();
-        // solve L z = c (forward), then L^T delta = z (backward), delta in gv? use va/gv
+        // c (the residual) is kept in gv for D below
+        for (int i = lane; i < p; i += 32) gv[i] = va[i];
+        // solve L z = c (forward), then L^T delta = z (backward), in va
         for (int kc = 0; kc < p; ++kc) {
           const T zk = va[kc] * invd[kc];
           __syncwarp();
@@ -730,6 +732,9 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
           for (int i = kc + 1 + lane; i < p; i += 32) va[i] -= L[i * ldg + kc] * zk;
           __syncwarp();
         }
+        float zz = 0.f;  // |z|^2 = delta^T (G + lambda I) delta
+        for (int i = lane; i < p; i += 32) zz = fmaf((float)va[i], (float)va[i], zz);
+        zz = warp_sum(zz);
         for (int kc = p - 1; kc >= 0; --kc) {
           const T dk = va[kc] * invd[kc];
           __syncwarp();
@@ -737,21 +742,25 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
           for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * dk;
           __syncwarp();
         }
-        // beta += delta; e -= U_P^T delta; D = |e|^2 / (N - 1)
-        for (int i = lane; i < p; i += 32) vb[i] += va[i];
-        for (int i = 0; i < p; ++i) {
+        // D from the refined residual e' = e - U_P^T delta without reading U:
+        //   |e'|^2 = |e|^2 - 2 delta.(U_P e) + delta^T G delta,
+        //   U_P e = c + lambda beta,  delta^T G delta = |z|^2 - lambda |delta|^2;
+        // the corrections are small next to |e|^2, which is compensated
+        float ee = 0.f;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) ee = fmaf(e[t], e[t], ee);
+        ee = warp_sum(ee);
+        float dc = 0.f, dd = 0.f;
+        for (int i = lane; i < p; i += 32) {
           const float di = (float)va[i];
-          const T* Ui = U + (int64_t)q[i] * g.ldN;
-#pragma unroll
-          for (int t = 0; t < MR; ++t) {
-            const int m = lane + 32 * t;
-            if (m < N) e[t] = fmaf(-(float)Ui[m], di, e[t]);
-          }
+          dc = fmaf(di, (float)gv[i] + (float)lam * (float)vb[i], dc);
+          dd = fmaf(di, di, dd);
         }
-        float ssq = 0.f;
-#pragma unroll
-        for (int t = 0; t < MR; ++t) ssq = fmaf(e[t], e[t], ssq);
-        ssq = warp_sum(ssq);
+        dc = warp_sum(dc);
+        dd = warp_sum(dd);
+        // beta += delta
+        for (int i = lane; i < p; i += 32) vb[i] += va[i];
+        const float ssq = ee - 2.f * dc + (zz - (float)lam * dd);
         Dj = (T)(ssq / (float)(N - 1));
         __syncwarp();
       } else {
