@@ -709,8 +709,37 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
         }
 #pragma unroll
         for (int t = 0; t < MR; ++t) e[t] += ec[t];
-        // c = U_P e - lambda beta, the residual of (G + lambda I) beta = g -> va
-        for (int i = 0; i < p; ++i) {
+        // c = U_P e - lambda beta, the residual of (G + lambda I) beta = g -> va.
+        // Full batches of 32 predecessors: each lane forms its partial dot
+        // products, then a reduce-scatter (31 shuffles) leaves predecessor
+        // i0 + lane's sum in lane lane; the rest one warp sum each
+        const int pfull32 = p & ~31;
+        for (int i0 = 0; i0 < pfull32; i0 += 32) {
+          float part[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            part[j] = 0.f;
+            const T* Ui = U + (int64_t)q[i0 + j] * g.ldN;
+#pragma unroll
+            for (int t = 0; t < MR; ++t) {
+              const int m = lane + 32 * t;
+              if (m < N) part[j] = fmaf((float)Ui[m], e[t], part[j]);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o >= 1; o >>= 1) {
+            const bool hi = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < o; ++j) {
+              const float send = hi ? part[j] : part[j + o];
+              const float keep = hi ? part[j + o] : part[j];
+              part[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+          }
+          const int i = i0 + lane;
+          va[i] = (T)(part[0] - (float)lam * (float)vb[i]);
+        }
+        for (int i = pfull32; i < p; ++i) {
           const T* Ui = U + (int64_t)q[i] * g.ldN;
           float part = 0.f;
 #pragma unroll
