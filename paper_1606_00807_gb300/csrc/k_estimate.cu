@@ -543,6 +543,74 @@ __host__ __device__ inline int pair_table_bytes(int pmax, int r, int periodic) {
   return ((pf + 1) * (pf + 2) / 2 * 8 + 15) / 16 * 16;
 }
 
+// v := L^-1 v for the first n unknowns (L lower, stored in 4 x 4 tiles as
+// tiled_cholesky leaves it, invd[u] = 1 / L[u][u]); v is 16-byte aligned with
+// room for n rounded up to 4.  Per tile step lane 0 solves the 4 unknowns of
+// the diagonal tile, then the lanes update the unknowns below it, one 16-byte
+// read of L per row.
+template <typename T>
+__device__ void tiled_forward(const T* L, int ldg, const T* invd, T* v, int n, int lane) {
+  const int nt = (n + 3) >> 2;
+  for (int K = 0; K < nt; ++K) {
+    const int k0 = 4 * K;
+    if (lane == 0) {
+      T x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        T acc = k0 + c < n ? v[k0 + c] : T(0);
+#pragma unroll
+        for (int t = 0; t < c; ++t) acc = fma(-L[(k0 + c) * ldg + k0 + t], x[t], acc);
+        x[c] = k0 + c < n ? acc * invd[k0 + c] : T(0);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[k0 + c] = x[c];
+    }
+    __syncwarp();
+    T x4[4];
+    lds4v(v + k0, x4);
+    for (int i = k0 + 4 + lane; i < n; i += 32) {
+      T l4[4];
+      lds4v(L + i * ldg + k0, l4);
+      T acc = v[i];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(-l4[c], x4[c], acc);
+      v[i] = acc;
+    }
+    __syncwarp();
+  }
+}
+
+// v := L^-T v for the first n unknowns (same storage as tiled_forward).
+template <typename T>
+__device__ void tiled_backward(const T* L, int ldg, const T* invd, T* v, int n, int lane) {
+  const int nt = (n + 3) >> 2;
+  for (int K = nt - 1; K >= 0; --K) {
+    const int k0 = 4 * K;
+    if (lane == 0) {
+      T x[4];
+#pragma unroll
+      for (int c = 3; c >= 0; --c) {
+        T acc = k0 + c < n ? v[k0 + c] : T(0);
+#pragma unroll
+        for (int t = c + 1; t < 4; ++t) acc = fma(-L[(k0 + t) * ldg + k0 + c], x[t], acc);
+        x[c] = k0 + c < n ? acc * invd[k0 + c] : T(0);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[k0 + c] = x[c];
+    }
+    __syncwarp();
+    T x4[4];
+    lds4v(v + k0, x4);
+    for (int j = lane; j < k0; j += 32) {
+      T acc = v[j];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fma(-L[(k0 + c) * ldg + j], x4[c], acc);
+      v[j] = acc;
+    }
+    __syncwarp();
+  }
+}
+
 constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 
 // RR: rounds of 32 rows covering pmax + 1; MR: rounds of 32 members covering N.
@@ -682,13 +750,9 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
       // beta = L^-T w  (w = row p of L), result in vb
       for (int i = lane; i < p; i += 32) va[i] = L[p * ldg + i];
       __syncwarp();
-      for (int kc = p - 1; kc >= 0; --kc) {
-        const T bk = va[kc] * invd[kc];
-        __syncwarp();
-        if (lane == 0) vb[kc] = bk;
-        for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * bk;
-        __syncwarp();
-      }
+      tiled_backward(L, ldg, invd, va, p, lane);
+      for (int i = lane; i < p; i += 32) vb[i] = va[i];
+      __syncwarp();
       if (fp32) {
         // residual e = u - U_P^T beta (compensated), members m = lane + 32 t
         float e[MR], ec[MR];
@@ -754,23 +818,11 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
         // c (the residual) is kept in gv for D below
         for (int i = lane; i < p; i += 32) gv[i] = va[i];
         // solve L z = c (forward), then L^T delta = z (backward), in va
-        for (int kc = 0; kc < p; ++kc) {
-          const T zk = va[kc] * invd[kc];
-          __syncwarp();
-          if (lane == 0) va[kc] = zk;
-          for (int i = kc + 1 + lane; i < p; i += 32) va[i] -= L[i * ldg + kc] * zk;
-          __syncwarp();
-        }
+        tiled_forward(L, ldg, invd, va, p, lane);
         float zz = 0.f;  // |z|^2 = delta^T (G + lambda I) delta
         for (int i = lane; i < p; i += 32) zz = fmaf((float)va[i], (float)va[i], zz);
         zz = warp_sum(zz);
-        for (int kc = p - 1; kc >= 0; --kc) {
-          const T dk = va[kc] * invd[kc];
-          __syncwarp();
-          if (lane == 0) va[kc] = dk;
-          for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * dk;
-          __syncwarp();
-        }
+        tiled_backward(L, ldg, invd, va, p, lane);
         // D from the refined residual e' = e - U_P^T delta without reading U:
         //   |e'|^2 = |e|^2 - 2 delta.(U_P e) + delta^T G delta,
         //   U_P e = c + lambda beta,  delta^T G delta = |z|^2 - lambda |delta|^2;
