@@ -1043,20 +1043,8 @@ __global__ void __launch_bounds__(256) k_adj_regress(
       return;
     }
     // v = (L L^T)^-1 betabar in va
-    for (int kc = 0; kc < p; ++kc) {
-      const T zk = va[kc] * invd[kc];
-      __syncwarp();
-      if (lane == 0) va[kc] = zk;
-      for (int i = kc + 1 + lane; i < p; i += 32) va[i] -= L[i * ldg + kc] * zk;
-      __syncwarp();
-    }
-    for (int kc = p - 1; kc >= 0; --kc) {
-      const T zk = va[kc] * invd[kc];
-      __syncwarp();
-      if (lane == 0) va[kc] = zk;
-      for (int i = lane; i < kc; i += 32) va[i] -= L[kc * ldg + i] * zk;
-      __syncwarp();
-    }
+    tiled_forward(L, ldg, invd, va, p, lane);
+    tiled_backward(L, ldg, invd, va, p, lane);
     // f = ebar + U_P^T v; kappa
     T vbeta = 0;
     for (int i = lane; i < p; i += 32) vbeta = fma(va[i], vb[i], vbeta);
