@@ -97,20 +97,36 @@ __global__ void __launch_bounds__(kRows* kWarps) k_whiten(
   const int* nb_i = nbr + lane * pmax;
   const float* t_i = tv + lane * pmax;
   const float Dj = dj[lane];
-  for (int m = warp; m < g.N; m += kWarps) {
-    const float* dXm = dX + b.row_off * g.N + (int64_t)m * b.nb;
-    float s = dXm[loc0 + lane], c = 0.f;
+  // four members per pass share the slot reads; members past N are skipped
+  for (int m0 = 4 * warp; m0 < g.N; m0 += 4 * kWarps) {
+    const float* dXm[4];
+    float s[4], c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = min(m0 + u, g.N - 1);
+      dXm[u] = dX + b.row_off * g.N + (int64_t)m * b.nb;
+      s[u] = dXm[u][loc0 + lane];
+      c[u] = 0.f;
+    }
     for (int sl = 0; sl < pmax; ++sl) {
       const int q = nb_i[sl];
-      if (q >= 0) ff_add_prod(s, c, t_i[sl], dXm[q]);
+      if (q >= 0) {
+        const float t = t_i[sl];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ff_add_prod(s[u], c[u], t, dXm[u][q]);
+      }
     }
-    const float hi = s + c;
-    const float lo = c - (hi - s);
-    const float qh = hi / Dj;
-    const float rem = fmaf(-qh, Dj, hi) + lo;
-    const int64_t o = b.row_off * g.N + (int64_t)m * b.nb + loc0 + lane;
-    vhi[o] = qh;
-    vlo[o] = rem / Dj;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (m0 + u >= g.N) break;
+      const float hi = s[u] + c[u];
+      const float lo = c[u] - (hi - s[u]);
+      const float qh = hi / Dj;
+      const float rem = fmaf(-qh, Dj, hi) + lo;
+      const int64_t o = b.row_off * g.N + (int64_t)(m0 + u) * b.nb + loc0 + lane;
+      vhi[o] = qh;
+      vlo[o] = rem / Dj;
+    }
   }
 }
 
@@ -176,23 +192,36 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
     rinv = 1.f / Ro;
   }
   const int a = loc0 + lane;
-  for (int m = warp; m < g.N; m += kWarps) {
-    const int64_t base = b.row_off * g.N + (int64_t)m * b.nb;
-    float s = 0.f, c = 0.f;
-    if (o >= 0) {
-      s = rhs_entry(yo, sq, Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l], rinv);
-      ff_add_prod(s, c, -dX[base + a], rinv);
+  // four members per pass share the slot reads; members past N are skipped
+  for (int m0 = 4 * warp; m0 < g.N; m0 += 4 * kWarps) {
+    int64_t base[4];
+    float s[4], c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = min(m0 + u, g.N - 1);
+      base[u] = b.row_off * g.N + (int64_t)m * b.nb;
+      s[u] = 0.f;
+      c[u] = 0.f;
+      if (o >= 0) {
+        s[u] = rhs_entry(yo, sq, Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l], rinv);
+        ff_add_prod(s[u], c[u], -dX[base[u] + a], rinv);
+      }
+      ff_add(s[u], c[u], -vhi[base[u] + a]);
+      c[u] -= vlo[base[u] + a];
     }
-    ff_add(s, c, -vhi[base + a]);
-    c -= vlo[base + a];
     for (int sj = 0; sj < pmax; ++sj) {
       const int j = cj[sj];
       if (j < 0) continue;
       const float t = tj[sj];
-      ff_add_prod(s, c, -t, vhi[base + j]);
-      c -= t * vlo[base + j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ff_add_prod(s[u], c[u], -t, vhi[base[u] + j]);
+        c[u] -= t * vlo[base[u] + j];
+      }
     }
-    res[base + a] = s + c;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (m0 + u < g.N) res[base[u] + a] = s[u] + c[u];
   }
 }
 
