@@ -21,6 +21,7 @@ namespace {
 
 constexpr int kRows = 32;
 constexpr int kWarps = 4;
+constexpr int kMB = 5;  // members per pass (they share the slot reads)
 
 __device__ __forceinline__ void ff_add_prod(float& s, float& c, float t, float x) {
   const float prod = t * x;
@@ -97,12 +98,12 @@ __global__ void __launch_bounds__(kRows* kWarps) k_whiten(
   const int* nb_i = nbr + lane * pmax;
   const float* t_i = tv + lane * pmax;
   const float Dj = dj[lane];
-  // four members per pass share the slot reads; members past N are skipped
-  for (int m0 = 4 * warp; m0 < g.N; m0 += 4 * kWarps) {
-    const float* dXm[4];
-    float s[4], c[4];
+  // kMB members per pass share the slot reads; members past N are skipped
+  for (int m0 = kMB * warp; m0 < g.N; m0 += kMB * kWarps) {
+    const float* dXm[kMB];
+    float s[kMB], c[kMB];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kMB; ++u) {
       const int m = min(m0 + u, g.N - 1);
       dXm[u] = dX + b.row_off * g.N + (int64_t)m * b.nb;
       s[u] = dXm[u][loc0 + lane];
@@ -113,11 +114,11 @@ __global__ void __launch_bounds__(kRows* kWarps) k_whiten(
       if (q >= 0) {
         const float t = t_i[sl];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ff_add_prod(s[u], c[u], t, dXm[u][q]);
+        for (int u = 0; u < kMB; ++u) ff_add_prod(s[u], c[u], t, dXm[u][q]);
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kMB; ++u) {
       if (m0 + u >= g.N) break;
       const float hi = s[u] + c[u];
       const float lo = c[u] - (hi - s[u]);
@@ -192,12 +193,12 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
     rinv = 1.f / Ro;
   }
   const int a = loc0 + lane;
-  // four members per pass share the slot reads; members past N are skipped
-  for (int m0 = 4 * warp; m0 < g.N; m0 += 4 * kWarps) {
-    int64_t base[4];
-    float s[4], c[4];
+  // kMB members per pass share the slot reads; members past N are skipped
+  for (int m0 = kMB * warp; m0 < g.N; m0 += kMB * kWarps) {
+    int64_t base[kMB];
+    float s[kMB], c[kMB];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kMB; ++u) {
       const int m = min(m0 + u, g.N - 1);
       base[u] = b.row_off * g.N + (int64_t)m * b.nb;
       s[u] = 0.f;
@@ -214,13 +215,13 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
       if (j < 0) continue;
       const float t = tj[sj];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kMB; ++u) {
         ff_add_prod(s[u], c[u], -t, vhi[base[u] + j]);
         c[u] -= t * vlo[base[u] + j];
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < kMB; ++u)
       if (m0 + u < g.N) res[base[u] + a] = s[u] + c[u];
   }
 }
