@@ -535,8 +535,9 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
 // ---------------------------------------------------------------------------
 // Band Cholesky with the trailing updates on the tensor cores.  Thread r owns
 // row c0 + r of panel c0 (32 columns, rows [c0, c0 + 32 + hb)) in registers:
-//  * warp 0 factors the 32 x 32 diagonal block right-looking with shuffles
-//    (lane t = row t) and leaves L11 column-major in shared memory;
+//  * warp 0 factors the 32 x 32 diagonal block right-looking (lane t = row
+//    t, each column broadcast through shared memory) and leaves L11
+//    column-major there;
 //  * rows r >= 32 solve l_r L11^T = a_r in registers (right-looking over the
 //    columns of L11, broadcast reads);
 //  * every row writes its part of the factor to the band, and the rows below
@@ -544,17 +545,29 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
 //    (K-major);
 //  * D = L21 L21^T is formed by tcgen05.mma as the 128 x 128 tiles (mi, nj),
 //    nj <= mi, of its lower block triangle (hi*hi + hi*lo + lo*hi, FP32
-//    accumulation in TMEM, up to three tiles per round); thread (tile, row)
-//    reads its row of D and subtracts it from the band, the lanes of a warp on
-//    consecutive rows of one band column (coalesced), 64 entries read before
-//    any is written.
+//    accumulation in TMEM); thread (tile, row) reads its row of D and
+//    subtracts it from the band, the lanes of a warp on consecutive rows of
+//    one band column (coalesced), 64 entries read before any is written;
+//  * round 0 forms the tiles (mi, 0), whose first 32 columns are the next
+//    panel: thread t handles window row t there, which is row t of the next
+//    panel, so those updated entries go to the thread's own column of sA
+//    (shared memory) instead of the band, together with the entries of the
+//    rows that enter the band with the next panel; round 1 forms the tiles
+//    (mi, nj >= 1).  The next panel starts from sA, not from the band.
 constexpr int kCholThreads = 384;  // 12 warps: rows of the panel; 3 tiles x 4 lane quarters
 constexpr int kOpRows = 384;       // L21 rows staged (3 tiles of 128)
 
-__device__ __forceinline__ void syrk_tile(int k, int& mi, int& nj) {
-  // (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
-  mi = k < 1 ? 0 : (k < 3 ? 1 : 2);
-  nj = k - (mi * (mi + 1)) / 2;
+// Tile k of a panel whose window spans nt row tiles: k < nt -> (k, 0) (round
+// 0); then (1,1), (2,1), (2,2) (round 1).
+__device__ __forceinline__ void syrk_tile(int k, int nt, int& mi, int& nj) {
+  if (k < nt) {
+    mi = k;
+    nj = 0;
+    return;
+  }
+  const int k1 = k - nt;
+  mi = k1 < 1 ? 1 : 2;
+  nj = k1 - (mi * (mi - 1)) / 2 + 1;
 }
 
 __global__ void __launch_bounds__(kCholThreads, 1)
@@ -565,7 +578,8 @@ __global__ void __launch_bounds__(kCholThreads, 1)
   unsigned char* sLo = smem + kOpRows * 128;
   float* Lc = reinterpret_cast<float*>(smem + 2 * kOpRows * 128);  // [32][32] column-major L11
   float* invs = Lc + 32 * 32;                                       // [32]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(invs + 32);
+  float* sA = invs + 32;  // [32][kCholThreads]: next panel, column t of row r at t * 384 + r
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sA + 32 * kCholThreads);
   uint32_t* slot = reinterpret_cast<uint32_t*>(bar + 1);
   int* fail = reinterpret_cast<int*>(slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -587,6 +601,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
   const uint32_t hi0 = tc::smem_u32(sHi), lo0 = tc::smem_u32(sLo);
   uint32_t phase = 0;
   bool inflight = false;
+  int covered = 0;  // rows of this panel whose entries round 0 left in sA
 
   for (int c0 = 0; c0 < nb; c0 += 32) {
     const int nbc = min(32, nb - c0);
@@ -596,11 +611,23 @@ __global__ void __launch_bounds__(kCholThreads, 1)
     const bool own = r < rows;
     // row c0 + r of the panel: A[c0+r][c0+t], inside the band for 0 <= r - t <= hb
     float a[32];
+    if (r < covered) {  // warp-uniform (covered is a multiple of 128)
 #pragma unroll
-    for (int t = 0; t < 32; ++t)
-      a[t] = (own && t < nbc && r - t >= 0 && r - t <= hb) ? F[(int64_t)(c0 + t) * hb + c0 + r]
-                                                          : 0.f;
+      for (int t = 0; t < 32; ++t) a[t] = sA[t * kCholThreads + r];
+    } else {
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        a[t] = (own && t < nbc && r - t >= 0 && r - t <= hb)
+                   ? F[(int64_t)(c0 + t) * hb + c0 + r]
+                   : 0.f;
+    }
     if (warp == 0) {  // diagonal block, right-looking, lane t = row t
+      // column u of L11 goes to Lc (zeros above the diagonal), and every lane
+      // reads it back with 16-byte broadcast loads for its update: one
+      // shuffle per column (the pivot) instead of one per entry.  Entries of
+      // a lane above the diagonal take harmless updates and are zeroed when
+      // their column is reached.  1 / L[u][u] is Newton's iteration for the
+      // reciprocal square root started from rsqrtf.
       bool ok = true;
 #pragma unroll
       for (int u = 0; u < 32; ++u) {
@@ -612,26 +639,29 @@ __global__ void __launch_bounds__(kCholThreads, 1)
                            (int64_t)blockIdx.x);
             ok = false;
           } else {
-            // branch-free: every lane runs the same instructions, selects keep
-            // the entries it does not own
-            const float d = sqrtf(piv);
-            const float inv = 1.f / d;
-            a[u] = lane == u ? d : (lane > u ? a[u] * inv : a[u]);
+            float inv = rsqrtf(piv);
+            inv = inv * fmaf(-0.5f * piv * inv, inv, 1.5f);
+            const float lu = lane == u ? piv * inv : (lane > u ? a[u] * inv : 0.f);
+            a[u] = lu;
+            Lc[u * 32 + lane] = lu;
             if (lane == u) {
               invs[u] = inv;
               invdiag[b.row_off + c0 + u] = inv;
             }
+            __syncwarp();
+            const float4* col = reinterpret_cast<const float4*>(Lc + u * 32);
 #pragma unroll
-            for (int v = u + 1; v < 32; ++v) {
-              const float lv = __shfl_sync(0xffffffffu, a[u], v);  // L[v][u]
-              const float upd = fmaf(-a[u], lv, a[v]);
-              a[v] = lane >= v ? upd : a[v];
+            for (int g = (u + 1) >> 2; g < 8; ++g) {
+              const float4 q = col[g];
+              const float lv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                if (4 * g + k > u) a[4 * g + k] = fmaf(-lu, lv[k], a[4 * g + k]);
             }
           }
         }
       }
-#pragma unroll
-      for (int u = 0; u < 32; ++u) Lc[u * 32 + lane] = (lane >= u && lane < nbc) ? a[u] : 0.f;
+      for (int u = nbc; u < 32; ++u) Lc[u * 32 + lane] = 0.f;
       if (!ok && lane == 0) *fail = 1;
     }
     __syncthreads();
@@ -660,6 +690,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
       if (own && t < nbc && r - t >= 0 && r - t <= hb) F[(int64_t)(c0 + t) * hb + c0 + r] = a[t];
     if (W <= 0) {
       __syncthreads();
+      covered = 0;
       continue;
     }
     const int nt = (W + 127) >> 7;
@@ -682,9 +713,14 @@ __global__ void __launch_bounds__(kCholThreads, 1)
     tc::fence_before_sync();
     __syncthreads();
     const int ntiles = nt * (nt + 1) / 2;
+    // next panel: rows [0, rows_next), columns [0, nbc_next) of this window
+    const int rows_next = min(32 + hb, nb - c0 - 32);
+    const int nbc_next = min(32, nb - c0 - 32);
     bool bad = false;
-    for (int t0 = 0; t0 < ntiles; t0 += 3) {
-      const int nr = min(3, ntiles - t0);
+    for (int rd = 0; rd < 2; ++rd) {
+      const int t0 = rd ? nt : 0;
+      const int nr = rd ? ntiles - nt : nt;
+      if (nr == 0) break;
       if (tid == 0) {
         tc::fence_after_sync();
         const uint32_t id = tc::idesc_tf32(128, 128);
@@ -693,7 +729,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
         const uint64_t dl0 = tc::desc_kmajor(lo0, 128, 1024);
         for (int k = 0; k < nr; ++k) {
           int mi, nj;
-          syrk_tile(t0 + k, mi, nj);
+          syrk_tile(t0 + k, nt, mi, nj);
           const uint32_t d = tbase + (uint32_t)(128 * k);
           const uint64_t ao = (uint64_t)mi * 1024u, bo = (uint64_t)nj * 1024u;  // 16 KB tiles
 #pragma unroll
@@ -719,7 +755,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
       tc::fence_after_sync();
       if (warp / 4 < nr) {  // warp-uniform: tile warp / 4, lane quarter warp % 4
         int mi, nj;
-        syrk_tile(t0 + warp / 4, mi, nj);
+        syrk_tile(t0 + warp / 4, nt, mi, nj);
         const int q = warp & 3;
         const int rr = 128 * mi + 32 * q + lane;  // row of L21 / of the window
         // A[c0+32+rr][c0+32+cc] = F[(c0+32+cc) hb + c0+32+rr] = base[cc hb]
@@ -728,18 +764,31 @@ __global__ void __launch_bounds__(kCholThreads, 1)
 #pragma unroll 1
         for (int h2 = 0; h2 < 4; h2 += 2) {
           const int cb = 128 * nj + 32 * h2;
+          // columns [0, 32) of round 0 are the next panel (rr == tid there):
+          // the rows entering the band with it are read as well
+          const bool nxt = rd == 0 && h2 == 0;
           float o[64];
 #pragma unroll
-          for (int n = 0; n < 64; ++n)
-            o[n] = (cb + n <= rr && rr < W) ? base[(cb + n) * hb] : 0.f;
+          for (int n = 0; n < 64; ++n) {
+            bool in = cb + n <= rr && rr < W;
+            if (nxt && n < 32)
+              in = n <= rr && (rr < W || (rr < rows_next && rr - n <= hb && n < nbc_next));
+            o[n] = in ? base[(cb + n) * hb] : 0.f;
+          }
 #pragma unroll
           for (int hh = 0; hh < 2; ++hh) {
             float dv[32];
             tc::tmem_ld32(ta + (uint32_t)(32 * (h2 + hh)), dv);
+            if (nxt && hh == 0) {
 #pragma unroll
-            for (int n = 0; n < 32; ++n) {
-              const int cc = cb + 32 * hh + n;
-              if (cc <= rr && rr < W) base[cc * hb] = o[32 * hh + n] - dv[n];
+              for (int n = 0; n < 32; ++n)
+                sA[n * kCholThreads + tid] = n <= rr ? o[n] - dv[n] : 0.f;
+            } else {
+#pragma unroll
+              for (int n = 0; n < 32; ++n) {
+                const int cc = cb + 32 * hh + n;
+                if (cc <= rr && rr < W) base[cc * hb] = o[32 * hh + n] - dv[n];
+              }
             }
           }
         }
@@ -747,6 +796,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
       tc::fence_before_sync();
       __syncthreads();
     }
+    covered = 128 * nt;
     if (bad) break;
   }
   if (inflight) (void)tc::mbar_wait(bar_a, phase, kWaitNs);
@@ -796,7 +846,8 @@ bool bandchol_tc_supported(int hb_max) {
 cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, float* band,
                                float* invdiag, int32_t* status, cudaStream_t s) {
   if (!bandchol_tc_supported(hb_max)) return cudaErrorInvalidConfiguration;
-  const size_t smem = 2 * (size_t)kOpRows * 128 + sizeof(float) * (32 * 32 + 32) + 32;
+  const size_t smem =
+      2 * (size_t)kOpRows * 128 + sizeof(float) * (32 * 32 + 32 + 32 * kCholThreads) + 32;
   const int WT = hb_max <= 128 ? 128 : 512;  // one tile, or rounds of three
   cudaError_t e = cudaFuncSetAttribute(k_bandchol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
