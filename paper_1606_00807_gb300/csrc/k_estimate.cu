@@ -260,8 +260,10 @@ __global__ void __launch_bounds__(256) k_covtable(const Geom g, const T* __restr
 // chunk is stored as S[m][cell], rows of Wp4 cells padded with zeros, so a
 // thread's 4 a-cells are one 16-byte read and its 7 b-cells two aligned 16-byte
 // reads (the b window starts at dx = -2r or 0, a multiple of 4 from the a
-// cells): 3 shared-memory reads per 16 multiply-adds, no bounds tests.
-template <typename T, int MC>
+// cells): 3 shared-memory reads per 16 multiply-adds, no bounds tests.  A
+// thread keeps the same TPT tiles for every member chunk, their 4 x 4 sums in
+// registers; the [W][nH] output is staged once, at the end, in the space of S.
+template <typename T, int MC, int TPT>
 __global__ void __launch_bounds__(256) k_covtable4(const Geom g, const T* __restrict__ U,
                                                    T* __restrict__ C, int W, int nH, int nrho,
                                                    int Wp4) {
@@ -269,8 +271,7 @@ __global__ void __launch_bounds__(256) k_covtable4(const Geom g, const T* __rest
   const int r = g.r, r2 = 2 * r, w4 = 4 * r + 1;
   const int Wp = W + 4 * r;
   const int SLD = nrho * Wp4;  // cells per member (a multiple of 4)
-  T* S = reinterpret_cast<T*>(smem);   // [MC][SLD]
-  T* Cs = S + (size_t)MC * SLD;        // [W][nH]
+  T* S = reinterpret_cast<T*>(smem);   // [MC][SLD]; at the end [W][nH]
   int plane = blockIdx.z, v = 0;
   while (plane >= g.var_lev[v]) {
     plane -= g.var_lev[v];
@@ -282,7 +283,39 @@ __global__ void __launch_bounds__(256) k_covtable4(const Geom g, const T* __rest
   const int atiles = W / 4;
   const int dxt_full = (w4 + 3) / 4, dxt_half = (r2 + 1 + 3) / 4;
   const int ntiles = (dxt_half + (nrho - 1) * dxt_full) * atiles;
-  for (int i = tid; i < W * nH; i += blockDim.x) Cs[i] = T(0);
+  // this thread's tiles: a-cell group, b window offset, first output column
+  int offa[TPT], offb[TPT], h0[TPT], at4[TPT], dx0s[TPT];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int tile = min(tid + u * (int)blockDim.x, ntiles - 1);
+    const int at = tile % atiles;
+    int rest = tile / atiles;
+    int rho, dxt;
+    if (rest < dxt_half) {
+      rho = 0;
+      dxt = rest;
+    } else {
+      rest -= dxt_half;
+      rho = 1 + rest / dxt_full;
+      dxt = rest % dxt_full;
+    }
+    int dk, dy, dxlo;
+    cov_row(rho, r, dk, dy, dxlo);
+    const int dx0 = dxlo + 4 * dxt;
+    offa[u] = r2 + 4 * at;
+    offb[u] = rho * Wp4 + (r2 + 4 * at + dx0);
+    const int t = ((dk + g.vr) * w4 + (dy + r2)) * w4 + (dx0 + r2);
+    h0[u] = t - ((2 * g.vr + 1) * w4 * w4 - 1) / 2;  // column of dx0; dx0 + j -> h0 + j
+    at4[u] = 4 * at;
+    dx0s[u] = dx0;
+  }
+  T acc[TPT][4][4];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[u][i][j] = T(0);
 
   for (int m0 = 0; m0 < g.N; m0 += MC) {
     __syncthreads();
@@ -317,28 +350,11 @@ __global__ void __launch_bounds__(256) k_covtable4(const Geom g, const T* __rest
     }
     __syncthreads();
     const int mcnt = min(MC, g.N - m0);
-    for (int tile = tid; tile < ntiles; tile += blockDim.x) {
-      const int at = tile % atiles;
-      int rest = tile / atiles;
-      int rho, dxt;
-      if (rest < dxt_half) {
-        rho = 0;
-        dxt = rest;
-      } else {
-        rest -= dxt_half;
-        rho = 1 + rest / dxt_full;
-        dxt = rest % dxt_full;
-      }
-      int dk, dy, dxlo;
-      cov_row(rho, r, dk, dy, dxlo);
-      const int dx0 = dxlo + 4 * dxt;
-      T acc[4][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-      const T* Sa = S + (r2 + 4 * at);                     // row 0: the a cells
-      const T* Sb = S + rho * Wp4 + (r2 + 4 * at + dx0);   // row rho: the b cells
+    for (int u = 0; u < TPT; ++u) {
+      if (tid + u * (int)blockDim.x >= ntiles) break;
+      const T* Sa = S + offa[u];  // row 0: the a cells
+      const T* Sb = S + offb[u];  // row rho: the b cells
       for (int mm = 0; mm < mcnt; ++mm) {
         T av[4], b0[4], b1[4];
         lds4v(Sa + (size_t)mm * SLD, av);
@@ -348,17 +364,20 @@ __global__ void __launch_bounds__(256) k_covtable4(const Geom g, const T* __rest
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[i + j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[u][i][j] = fma(av[i], bv[i + j], acc[u][i][j]);
       }
+    }
+  }
+  __syncthreads();
+  T* Cs = S;  // [W][nH]; every entry is written by exactly one tile
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int dx = dx0 + j;
-        if (dx > r2) continue;
-        const int t = ((dk + g.vr) * w4 + (dy + r2)) * w4 + (dx + r2);
-        const int h = t - ((2 * g.vr + 1) * w4 * w4 - 1) / 2;
+  for (int u = 0; u < TPT; ++u) {
+    if (tid + u * (int)blockDim.x >= ntiles) break;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) Cs[(4 * at + i) * nH + h] += acc[i][j];
-      }
+    for (int j = 0; j < 4; ++j) {
+      if (dx0s[u] + j > r2) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) Cs[(at4[u] + i) * nH + h0[u] + j] = acc[u][i][j];
     }
   }
   __syncthreads();
@@ -1095,20 +1114,28 @@ cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
     int W = r <= 2 ? 64 : 32;
     auto bytes = [&](int w) {
       const int wp4 = (w + 4 * r + 4 + 3) / 4 * 4;
-      return sizeof(T) * ((size_t)MC * nrho * wp4 + (size_t)w * nH);
+      return sizeof(T) * std::max((size_t)MC * nrho * wp4, (size_t)w * nH);
     };
     while (bytes(W) > 200 * 1024 && W > 8) W /= 2;
-    if (bytes(W) <= 220 * 1024) {
+    const int w4 = 4 * r + 1;
+    const int ntiles = ((2 * r + 1 + 3) / 4 + (nrho - 1) * ((w4 + 3) / 4)) * (W / 4);
+    const int tpt = (ntiles + 255) / 256;
+    if (bytes(W) <= 220 * 1024 && tpt <= 4) {
       const int Wp4 = (W + 4 * r + 4 + 3) / 4 * 4;
-      cudaError_t e = cudaFuncSetAttribute(k_covtable4<T, MC>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)bytes(W));
-      if (e != cudaSuccess) return e;
       int planes = 0;
       for (int v = 0; v < g.nvar; ++v) planes += g.var_lev[v];
       const dim3 grid((g.nlon + W - 1) / W, g.nlat, planes);
-      k_covtable4<T, MC><<<grid, 256, bytes(W), s>>>(g, U, C, W, nH, nrho, Wp4);
-      return cudaGetLastError();
+      auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes(W));
+        if (e != cudaSuccess) return e;
+        kern<<<grid, 256, bytes(W), s>>>(g, U, C, W, nH, nrho, Wp4);
+        return cudaGetLastError();
+      };
+      if (tpt <= 1) return run(k_covtable4<T, MC, 1>);
+      if (tpt <= 2) return run(k_covtable4<T, MC, 2>);
+      if (tpt <= 3) return run(k_covtable4<T, MC, 3>);
+      return run(k_covtable4<T, MC, 4>);
     }
   }
   int W = r <= 2 ? 64 : 32;
