@@ -70,7 +70,12 @@ __host__ __device__ inline void slot_offset(int s, int r, int vr, int& dk, int& 
   dx = (s < r) ? (-r + s) : (1 + (s - r));
 }
 
+// a mod m in [0, m); one step without a division when |a| < 2m (the usual
+// case: a longitude plus or minus less than one circle)
 __host__ __device__ inline int imod(int a, int m) {
+  if (a >= 0 && a < m) return a;
+  if (a < 0 && a >= -m) return a + m;
+  if (a >= m && a - m < m) return a - m;
   int x = a % m;
   return x < 0 ? x + m : x;
 }
@@ -84,24 +89,24 @@ __host__ __device__ inline int var_of_label(const Geom& g, int64_t l) {
 __host__ __device__ inline void label_coords(const Geom& g, int64_t l, int& v, int& k, int& y,
                                              int& x) {
   v = var_of_label(g, l);
-  int64_t rem = l - g.var_off[v];
-  const int64_t plane = (int64_t)g.nlat * g.nlon;
-  k = (int)(rem / plane);
-  rem -= (int64_t)k * plane;
-  y = (int)(rem / g.nlon);
-  x = (int)(rem - (int64_t)y * g.nlon);
+  // labels are below 2^31 (the handle refuses larger grids): 32-bit divisions
+  int rem = (int)(l - g.var_off[v]);
+  const int plane = g.nlat * g.nlon;
+  k = rem / plane;
+  rem -= k * plane;
+  y = rem / g.nlon;
+  x = rem - y * g.nlon;
 }
 
 __host__ __device__ inline int64_t coords_label(const Geom& g, int v, int k, int y, int x) {
   return g.var_off[v] + ((int64_t)k * g.nlat + y) * g.nlon + x;
 }
 
-// Is slot s of component (v, k, y, x) a predecessor?  On success returns the
-// neighbour's (k, y, x) with x on [0, nlon).
-__host__ __device__ inline bool slot_pred(const Geom& g, int k, int y, int x, int s, int& kq,
-                                          int& yq, int& xq) {
-  int dk, dy, dx;
-  slot_offset(s, g.r, g.vr, dk, dy, dx);
+// Is the neighbour of component (v, k, y, x) at the offsets (dk, dy, dx) of a
+// stencil slot a predecessor?  On success returns the neighbour's (k, y, x)
+// with x on [0, nlon).
+__host__ __device__ inline bool slot_pred_off(const Geom& g, int k, int y, int x, int dk, int dy,
+                                              int dx, int& kq, int& yq, int& xq) {
   kq = k + dk;
   if (kq < 0) return false;
   yq = y + dy;
@@ -118,6 +123,14 @@ __host__ __device__ inline bool slot_pred(const Geom& g, int k, int y, int x, in
     xq = imod(xq, g.nlon);
   }
   return true;
+}
+
+// Same, the offsets of slot s computed here.
+__host__ __device__ inline bool slot_pred(const Geom& g, int k, int y, int x, int s, int& kq,
+                                          int& yq, int& xq) {
+  int dk, dy, dx;
+  slot_offset(s, g.r, g.vr, dk, dy, dx);
+  return slot_pred_off(g, k, y, x, dk, dy, dx, kq, yq, xq);
 }
 
 // Local position of absolute (yq, xq) in a block's extended box.

@@ -634,13 +634,11 @@ constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 
 // RR: rounds of 32 rows covering pmax + 1; MR: rounds of 32 members covering N.
 template <typename T, int RR, int MR>
-__global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restrict__ U,
-                                                 const T* __restrict__ C, int nH,
-                                                 const int32_t* __restrict__ halo, int64_t nitems,
-                                                 const Block* __restrict__ blocks,
-                                                 T* __restrict__ Tout, T* __restrict__ Dout,
-                                                 double ridge_c, int32_t* status, int ldp, int ldg,
-                                                 int warp_bytes) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+    k_regress(const Geom g, const T* __restrict__ U, const T* __restrict__ C, int nH,
+              const int32_t* __restrict__ halo, int64_t nitems, const Block* __restrict__ blocks,
+              T* __restrict__ Tout, T* __restrict__ Dout, double ridge_c, int32_t* status,
+              int ldp, int ldg, int warp_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   // per-block slot offsets
@@ -699,7 +697,7 @@ __global__ void __launch_bounds__(256) k_regress(const Geom g, const T* __restri
       int qq = 0;
       if (s < pmax) {
         int kq, yq, xq;
-        pres = slot_pred(g, k, y, x, s, kq, yq, xq);
+        pres = slot_pred_off(g, k, y, x, off[s], off[pmax + s], off[2 * pmax + s], kq, yq, xq);
         if (pres && b) {
           int yy, xx;
           pres = in_ext(*b, g.nlon, yq, xq, yy, xx);
