@@ -74,23 +74,38 @@ __global__ void __launch_bounds__(kRows* kWarps) k_whiten(
   int* nbr = reinterpret_cast<int*>(smem);              // [kRows][pmax] local index or -1
   float* tv = reinterpret_cast<float*>(nbr + kRows * pmax);  // [kRows][pmax]
   float* dj = tv + kRows * pmax;                        // [kRows]
+  signed char* so = reinterpret_cast<signed char*>(dj + kRows);  // [3][pmax] slot offsets
   const Block b = blocks[blockIdx.y];
   const int loc0 = blockIdx.x * kRows;
   if (loc0 >= b.nb) return;
   const int nr = min(kRows, b.nb - loc0);
-  for (int idx = threadIdx.x; idx < nr * pmax; idx += blockDim.x) {
-    const int i = idx / pmax, s = idx - i * pmax;
-    int k, yy, xx, y, x;
-    row_coords(b, g.nlon, loc0 + i, k, yy, xx, y, x);
-    float Dj;
-    const float* trow = row_of(g, b, b.var, k, y, x, loc0 + i, Tg, Dg, Te, De, Dj);
-    const float t = trow[s];
-    int kq, yq, xq, yyq, xxq, q = -1;
-    if (t != 0.f && slot_pred(g, k, y, x, s, kq, yq, xq) && in_ext(b, g.nlon, yq, xq, yyq, xxq))
-      q = (kq * b.ey + yyq) * b.ex + xxq;
-    nbr[i * pmax + s] = q;
-    tv[i * pmax + s] = q >= 0 ? t : 0.f;
-    if (s == 0) dj[i] = Dj;
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
+    int dk, dy, dx;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    so[s] = (signed char)dk;
+    so[pmax + s] = (signed char)dy;
+    so[2 * pmax + s] = (signed char)dx;
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < nr; i += kWarps) {  // a row per warp, its slots over the lanes
+      int k, yy, xx, y, x;
+      row_coords(b, g.nlon, loc0 + i, k, yy, xx, y, x);
+      float Dj;
+      const float* trow = row_of(g, b, b.var, k, y, x, loc0 + i, Tg, Dg, Te, De, Dj);
+      for (int s = lane; s < pmax; s += 32) {
+        const float t = trow[s];
+        int kq, yq, xq, yyq, xxq, q = -1;
+        if (t != 0.f && slot_pred_off(g, k, y, x, so[s], so[pmax + s], so[2 * pmax + s], kq, yq,
+                                      xq) &&
+            in_ext(b, g.nlon, yq, xq, yyq, xxq))
+          q = (kq * b.ey + yyq) * b.ex + xxq;
+        nbr[i * pmax + s] = q;
+        tv[i * pmax + s] = q >= 0 ? t : 0.f;
+      }
+      if (lane == 0) dj[i] = Dj;
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -144,39 +159,51 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
   float* ct = reinterpret_cast<float*>(cand + kRows * pmax);  // [kRows][pmax] T[j][s]
   int* obs = reinterpret_cast<int*>(ct + kRows * pmax);      // [kRows]
   int64_t* lab = reinterpret_cast<int64_t*>(obs + kRows + (kRows & 1));  // [kRows]
+  signed char* so = reinterpret_cast<signed char*>(lab + kRows);  // [3][pmax] slot offsets
   const Block b = blocks[blockIdx.y];
   const int loc0 = blockIdx.x * kRows;
   if (loc0 >= b.nb) return;
   const int nr = min(kRows, b.nb - loc0);
   const int v = b.var;
-  for (int idx = threadIdx.x; idx < nr * pmax; idx += blockDim.x) {
-    const int i = idx / pmax, sj = idx - i * pmax;
-    int kc, yyc, xxc, yc, xc;
-    row_coords(b, g.nlon, loc0 + i, kc, yyc, xxc, yc, xc);
-    if (sj == 0) {
-      const int64_t l = coords_label(g, v, kc, yc, xc);
-      lab[i] = l;
-      obs[i] = obs_of[l];
-    }
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
     int dk, dy, dx;
-    slot_offset(sj, g.r, g.vr, dk, dy, dx);
-    const int kj = kc - dk, yj = yc - dy;
-    int xj = xc - dx, jloc = -1;
-    float t = 0.f;
-    bool ok = kj < b.nlev_b && yj >= 0 && yj < g.nlat;
-    if (ok && (xj < 0 || xj >= g.nlon)) {
-      if (g.periodic) xj = imod(xj, g.nlon);
-      else ok = false;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    so[s] = (signed char)dk;
+    so[pmax + s] = (signed char)dy;
+    so[2 * pmax + s] = (signed char)dx;
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < nr; i += kWarps) {  // a row per warp, its slots over the lanes
+      int kc, yyc, xxc, yc, xc;
+      row_coords(b, g.nlon, loc0 + i, kc, yyc, xxc, yc, xc);
+      if (lane == 0) {
+        const int64_t l = coords_label(g, v, kc, yc, xc);
+        lab[i] = l;
+        obs[i] = obs_of[l];
+      }
+      for (int sj = lane; sj < pmax; sj += 32) {
+        // row j = c - offset(sj) holds c in its slot sj
+        const int kj = kc - so[sj], yj = yc - so[pmax + sj];
+        int xj = xc - so[2 * pmax + sj], jloc = -1;
+        float t = 0.f;
+        bool ok = kj < b.nlev_b && yj >= 0 && yj < g.nlat;
+        if (ok && (xj < 0 || xj >= g.nlon)) {
+          if (g.periodic) xj = imod(xj, g.nlon);
+          else ok = false;
+        }
+        int yyj, xxj;
+        if (ok && in_ext(b, g.nlon, yj, xj, yyj, xxj)) {
+          const int locj = (kj * b.ey + yyj) * b.ex + xxj;
+          float Dj;
+          t = row_of(g, b, v, kj, yj, xj, locj, Tg, Dg, Te, De, Dj)[sj];
+          if (t != 0.f) jloc = locj;
+        }
+        cand[i * pmax + sj] = jloc;
+        ct[i * pmax + sj] = jloc >= 0 ? t : 0.f;
+      }
     }
-    int yyj, xxj;
-    if (ok && in_ext(b, g.nlon, yj, xj, yyj, xxj)) {
-      const int locj = (kj * b.ey + yyj) * b.ex + xxj;
-      float Dj;
-      t = row_of(g, b, v, kj, yj, xj, locj, Tg, Dg, Te, De, Dj)[sj];
-      if (t != 0.f) jloc = locj;
-    }
-    cand[i * pmax + sj] = jloc;
-    ct[i * pmax + sj] = jloc >= 0 ? t : 0.f;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -235,8 +262,8 @@ cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nbloc
                                    const float* De, const float* dX, float* vhi, float* vlo,
                                    float* res, cudaStream_t s) {
   const dim3 grid((nb_max + kRows - 1) / kRows, nblock);
-  const size_t sm1 = (size_t)kRows * g.pmax * 8 + kRows * 4;
-  const size_t sm2 = (size_t)kRows * g.pmax * 8 + kRows * 4 + 8 + kRows * 8;
+  const size_t sm1 = (size_t)kRows * g.pmax * 8 + kRows * 4 + 3 * g.pmax;
+  const size_t sm2 = (size_t)kRows * g.pmax * 8 + kRows * 4 + 8 + kRows * 8 + 3 * g.pmax;
   k_whiten<<<grid, kRows * kWarps, sm1, s>>>(g, blocks, Tg, Dg, Te, De, dX, vhi, vlo);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
