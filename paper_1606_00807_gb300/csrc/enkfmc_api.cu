@@ -302,12 +302,21 @@ enkfmc_status build(enkfmc_handle* h) {
   if (!halo.empty())
     CUDA_TRY(cudaMemcpy(h->d_halo, halo.data(), sizeof(int32_t) * halo.size(),
                         cudaMemcpyHostToDevice));
+  {  // pair table of the typical row (gather of the regression Gram matrices)
+    const int pf = g.pmax - (g.periodic ? g.r : 0);
+    std::vector<int2> ptab((size_t)(pf + 1) * (pf + 2) / 2);
+    for (size_t pi = 0; pi < ptab.size(); ++pi) ptab[pi] = pair_table_entry(g, pf, (int)pi);
+    if ((st = dalloc(h, &h->d_ptab, sizeof(int2) * ptab.size()))) return st;
+    CUDA_TRY(cudaMemcpy(h->d_ptab, ptab.data(), sizeof(int2) * ptab.size(),
+                        cudaMemcpyHostToDevice));
+  }
   CUDA_TRY(cudaMemset(h->d_status, 0, 16));
   return ENKFMC_OK;
 }
 
 void release(enkfmc_handle* h) {
-  void* bufs[] = {h->d_pairs,  h->d_srcrow, h->d_blocks, h->d_halo, h->d_status, h->d_obs_of,
+  void* bufs[] = {h->d_pairs,  h->d_srcrow, h->d_ptab,  h->d_blocks, h->d_halo, h->d_status,
+                  h->d_obs_of,
                   h->d_U,   h->d_C,
                   h->d_Te,     h->d_De,   h->d_band,   h->d_invdiag, h->d_rhs,    h->d_res, h->d_vhi,
                   h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
@@ -587,8 +596,8 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
     return launch_adj_regress<T>(g, h->d_blocks, h->nblock, h->nb_max, (const T*)h->d_U,
                                  (const T*)h->d_C, Tg, Dg, (const T*)h->d_Te, (const T*)h->d_De,
                                  (const T*)h->d_aT, (const T*)h->d_bT, (const T*)h->d_dxT,
-                                 (const T*)h->d_lamT, (T*)h->d_Ubar, h->prob.ridge_c,
-                                 h->d_status, h->stream);
+                                 (const T*)h->d_lamT, h->d_ptab, (T*)h->d_Ubar,
+                                 h->prob.ridge_c, h->d_status, h->stream);
   });
   if (st) return st;
   return timed(h, ENKFMC_K_ADJOINT, [&] {

@@ -133,6 +133,29 @@ __host__ __device__ inline bool slot_pred(const Geom& g, int k, int y, int x, in
   return slot_pred_off(g, k, y, x, dk, dy, dx, kq, yq, xq);
 }
 
+// Pair table of the typical row, whose predecessors are exactly the stencil
+// slots 0..pf-1 (pf = pmax minus the seam slots of a periodic grid): entry pi of
+// the lower triangle of the augmented Gram matrix (row-major, index pf = the row
+// itself) -> {i | l << 8 | sel << 16, column h of the covariance table}, the
+// entry being C[(sel ? q[l] : q[i]) * nH + h] for the labels q of the
+// predecessors (the table holds the offset b - a of a pair (a, b) at row a when
+// it lies in the stored half box, else at row b with the opposite offset).
+__host__ __device__ inline int2 pair_table_entry(const Geom& g, int pf, int pi) {
+  const int w4 = 4 * g.r + 1;
+  const int B = (2 * g.vr + 1) * w4 * w4;
+  const int t0 = (B - 1) / 2;
+  int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= pi) ++i;
+  while (i * (i + 1) / 2 > pi) --i;
+  const int l = pi - i * (i + 1) / 2;
+  int dki = 0, dyi = 0, dxi = 0, dkl = 0, dyl = 0, dxl = 0;
+  if (i < pf) slot_offset(i, g.r, g.vr, dki, dyi, dxi);
+  if (l < pf) slot_offset(l, g.r, g.vr, dkl, dyl, dxl);
+  const int t = ((dkl - dki + g.vr) * w4 + (dyl - dyi + 2 * g.r)) * w4 + (dxl - dxi + 2 * g.r);
+  return t >= t0 ? make_int2(i | (l << 8), t - t0)
+                 : make_int2(i | (l << 8) | (1 << 16), B - 1 - t - t0);
+}
+
 // Local position of absolute (yq, xq) in a block's extended box.
 __host__ __device__ inline bool in_ext(const Block& b, int nlon, int yq, int xq, int& yy, int& xx) {
   yy = yq - b.lat_lo;
@@ -170,6 +193,7 @@ struct enkfmc_handle {
   enkfmc::Block* d_blocks = nullptr;
   int4* d_pairs = nullptr;       // slot pairs per block shape, sorted by band diagonal
   int32_t* d_srcrow = nullptr;   // per extended row: global label (>= 0) or ~boundary row
+  int2* d_ptab = nullptr;        // pair table of the typical row (pair_table_entry)
   bool pair_assembly = false;    // every block can use the pair lists
   int32_t npair_max = 0;         // longest pair list of a shape
   int32_t box_sum = 0;           // largest nlev_b + ey + ex of a block
@@ -326,8 +350,8 @@ template <typename T>
 cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
                                const T* De, const T* aT, const T* bT, const T* dxT,
-                               const T* lamT, T* Ubar, double ridge_c, int32_t* status,
-                               cudaStream_t s);
+                               const T* lamT, const int2* ptab, T* Ubar, double ridge_c,
+                               int32_t* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_finish(const Geom& g, const T* Ubar, const T* Xa_bar, T* Xb_bar,
                               cudaStream_t s);

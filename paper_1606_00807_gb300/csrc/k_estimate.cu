@@ -533,28 +533,10 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
   return err;
 }
 
-// Pair table of the typical row, whose predecessors are exactly the stencil
-// slots 0..pf-1 (pf = pmax minus the seam slots of a periodic grid): entry pi of
-// the lower triangle of the augmented Gram matrix (row-major, index pf = the row
-// itself) -> {i | l << 8 | sel << 16, column h of the covariance table}, the
-// entry being C[(sel ? q[l] : q[i]) * nH + h] (as cov_lookup resolves it).
+// The pair table (pair_table_entry) in shared memory, built by the CTA.
 __device__ inline void build_pair_table(const Geom& g, int pf, int2* ptab) {
   const int np = (pf + 1) * (pf + 2) / 2;
-  const int w4 = 4 * g.r + 1;
-  const int B = (2 * g.vr + 1) * w4 * w4;
-  const int t0 = (B - 1) / 2;
-  for (int pi = threadIdx.x; pi < np; pi += blockDim.x) {
-    int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= pi) ++i;
-    while (i * (i + 1) / 2 > pi) --i;
-    const int l = pi - i * (i + 1) / 2;
-    int dki = 0, dyi = 0, dxi = 0, dkl = 0, dyl = 0, dxl = 0;
-    if (i < pf) slot_offset(i, g.r, g.vr, dki, dyi, dxi);
-    if (l < pf) slot_offset(l, g.r, g.vr, dkl, dyl, dxl);
-    const int t = ((dkl - dki + g.vr) * w4 + (dyl - dyi + 2 * g.r)) * w4 + (dxl - dxi + 2 * g.r);
-    ptab[pi] = t >= t0 ? make_int2(i | (l << 8), t - t0)
-                       : make_int2(i | (l << 8) | (1 << 16), B - 1 - t - t0);
-  }
+  for (int pi = threadIdx.x; pi < np; pi += blockDim.x) ptab[pi] = pair_table_entry(g, pf, pi);
 }
 
 __host__ __device__ inline int pair_table_bytes(int pmax, int r, int periodic) {
@@ -898,12 +880,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 // atomic adds (rows share predecessors).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_regress(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
     const Geom g, const Block* __restrict__ blocks, const T* __restrict__ U,
     const T* __restrict__ C, int nH, const T* __restrict__ Tg, const T* __restrict__ Dg,
     const T* __restrict__ Te, const T* __restrict__ De, const T* __restrict__ aT,
     const T* __restrict__ bT, const T* __restrict__ dxT, const T* __restrict__ lamT,
-    T* __restrict__ Ubar, double ridge_c, int32_t* status, int ldp, int ldg, int warp_bytes) {
+    const int2* __restrict__ ptab, T* __restrict__ Ubar, double ridge_c, int32_t* status,
+    int ldp, int ldg, int warp_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   signed char* off = reinterpret_cast<signed char*>(smem);
@@ -943,7 +926,8 @@ __global__ void __launch_bounds__(256) k_adj_regress(
     int qq = 0, rr = 0;
     if (s < pmax) {
       int kq, yq, xq, yyq, xxq;
-      pres = slot_pred(g, k, y, x, s, kq, yq, xq) && in_ext(b, g.nlon, yq, xq, yyq, xxq);
+      pres = slot_pred_off(g, k, y, x, off[s], off[pmax + s], off[2 * pmax + s], kq, yq, xq) &&
+             in_ext(b, g.nlon, yq, xq, yyq, xxq);
       if (pres) {
         qq = (int)coords_label(g, v, kq, yq, xq);
         rr = (kq * b.ey + yyq) * b.ex + xxq;
@@ -1018,9 +1002,8 @@ __global__ void __launch_bounds__(256) k_adj_regress(
       s1 = fma(bj[a], l4[a], s1);
       s2 = fma(u4[a], eb[a], s2);
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    if (lane == (i & 31)) va[i] = s1 * invD - s2;
+    const T bb = warp_sum(s1 * invD - s2);  // one reduction for both sums
+    if (lane == (i & 31)) va[i] = bb;
   }
   __syncwarp();
   T f[4];
@@ -1031,6 +1014,15 @@ __global__ void __launch_bounds__(256) k_adj_regress(
     // Gram factor from the covariance table (as in the forward pass)
     const int p1 = p + 1;
     const int npair = p * (p + 1) / 2;
+    const int pf = pmax - (g.periodic ? g.r : 0);
+    if (ptab && p == pf && sl[p - 1] == pf - 1) {
+      // typical row: the handle's pair table (global memory, cached)
+      for (int pi = lane; pi < npair; pi += 32) {
+        const int2 e = ptab[pi];
+        const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
+        L[i * ldg + l] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
+      }
+    } else
     for (int pi = lane; pi < npair; pi += 32) {
       int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
       while ((i + 1) * (i + 2) / 2 <= pi) ++i;
@@ -1215,8 +1207,8 @@ template <typename T>
 cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
                                const T* De, const T* aT, const T* bT, const T* dxT,
-                               const T* lamT, T* Ubar, double ridge_c, int32_t* status,
-                               cudaStream_t s) {
+                               const T* lamT, const int2* ptab, T* Ubar, double ridge_c,
+                               int32_t* status, cudaStream_t s) {
   if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
     return cudaErrorInvalidConfiguration;
   const int nH = cov_offset_count(g.r, g.vr);
@@ -1238,16 +1230,16 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
   if (e != cudaSuccess) return e;
   const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
   k_adj_regress<T><<<grid, 32 * wpc, smem, s>>>(g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT,
-                                                 dxT, lamT, Ubar, ridge_c, status, ldp, ldg,
-                                                 (int)wb);
+                                                 dxT, lamT, ptab, Ubar, ridge_c, status, ldp,
+                                                 ldg, (int)wb);
   return cudaGetLastError();
 }
 
 #define INST(T)                                                                                  \
   template cudaError_t launch_adj_regress<T>(const Geom&, const Block*, int, int, const T*,     \
                                              const T*, const T*, const T*, const T*, const T*,  \
-                                             const T*, const T*, const T*, const T*, T*, double,\
-                                             int32_t*, cudaStream_t);                            \
+                                             const T*, const T*, const T*, const T*,           \
+                                             const int2*, T*, double, int32_t*, cudaStream_t);                            \
   template cudaError_t launch_anomalies<T>(const Geom&, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_covtable<T>(const Geom&, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_regress<T>(const Geom&, const T*, const T*, const int32_t*,       \
