@@ -988,31 +988,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
   T eb[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) eb[a] = T(2) * Dbar * e[a] / T(N - 1);
-  // betabar
-  const T invD = T(1) / Dj;
-  for (int i = 0; i < p; ++i) {
-    T u4[4], x4[4], l4[4];
-    ld4(U + (int64_t)q[i] * ldN, u4);
-    ld4(dxT + (b.row_off + qr[i]) * ldN, x4);
-    ld4(lamT + (b.row_off + qr[i]) * ldN, l4);
-    T s1 = 0, s2 = 0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      s1 = fma(aj[a], x4[a], s1);
-      s1 = fma(bj[a], l4[a], s1);
-      s2 = fma(u4[a], eb[a], s2);
-    }
-    const T bb = warp_sum(s1 * invD - s2);  // one reduction for both sums
-    if (lane == (i & 31)) va[i] = bb;
-  }
-  __syncwarp();
-  T f[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) f[a] = eb[a];
-  T kappa = 0;
+  // Gram matrix from the covariance table (as in the forward pass) and the ridge
+  T lam = 0;
   if (p > 0) {
-    // Gram factor from the covariance table (as in the forward pass)
-    const int p1 = p + 1;
     const int npair = p * (p + 1) / 2;
     const int pf = pmax - (g.periodic ? g.r : 0);
     if (ptab && p == pf && sl[p - 1] == pf - 1) {
@@ -1034,9 +1012,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       const int dx = off[2 * pmax + sm] - off[2 * pmax + si];
       L[i * ldg + l] = cov_lookup(C, nH, g.r, g.vr, q[i], q[l], dk, dy, dx);
     }
-    (void)p1;
     __syncwarp();
-    T lam = 0;
     if (ridge_c > 0.0 && p >= N - 1) {
       T tr = 0;
       for (int i = lane; i < p; i += 32) tr += L[i * ldg + i];
@@ -1046,6 +1022,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       for (int i = lane; i < p; i += 32) L[i * ldg + i] += lam;
     }
     __syncwarp();
+  }
+  // betabar_i = (<a_j, dX_qi> + <b_j, Lambda_qi>) / D_j - <U_qi, ebar>.  The
+  // regression residual satisfies the normal equations, U_P e = lambda beta
+  // (G = U_P U_P^T, (G + lambda I) beta = U_P u), so <U_qi, ebar> =
+  // 2 Dbar lambda beta_i / (N - 1): no pass over U_P for it.
+  const T invD = T(1) / Dj;
+  const T ebu = T(2) * Dbar * lam / T(N - 1);
+  for (int i = 0; i < p; ++i) {
+    T x4[4], l4[4];
+    ld4(dxT + (b.row_off + qr[i]) * ldN, x4);
+    ld4(lamT + (b.row_off + qr[i]) * ldN, l4);
+    T s1 = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      s1 = fma(aj[a], x4[a], s1);
+      s1 = fma(bj[a], l4[a], s1);
+    }
+    s1 = warp_sum(s1);
+    if (lane == (i & 31)) va[i] = s1 * invD - ebu * vb[i];
+  }
+  __syncwarp();
+  T f[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) f[a] = eb[a];
+  T kappa = 0;
+  if (p > 0) {
     const int err = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p, p, lane);
     if (err) {
       if (lane == 0) record_error(status, err, rowj);
@@ -1066,11 +1068,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
 #pragma unroll
       for (int a = 0; a < 4; ++a) f[a] = fma(u4[a], vi, f[a]);
     }
-    // Ubar_qi += v_i e - beta_i f - kappa U_qi
+    // Ubar_qi += v_i e - beta_i f - kappa U_qi (U read only with the ridge)
     for (int i = 0; i < p; ++i) {
       const T vi = va[i], bi = vb[i];
-      T u4[4], d4[4];
-      ld4(U + (int64_t)q[i] * ldN, u4);
+      T u4[4] = {T(0), T(0), T(0), T(0)}, d4[4];
+      if (kappa != T(0)) ld4(U + (int64_t)q[i] * ldN, u4);
 #pragma unroll
       for (int a = 0; a < 4; ++a) d4[a] = vi * e[a] - bi * f[a] - kappa * u4[a];
       if (m0 < N) atomic_add4(Ubar + (int64_t)q[i] * ldN + m0, d4);
