@@ -185,6 +185,27 @@ def dist_env():
     return rank, world, local
 
 
+def rank_workload(w, rank):
+    """Rank `rank`'s problem: the same shapes with its own seed (independent
+    problems, no exchange between ranks)."""
+    return w.with_(seed=w.seed + 17 * rank) if rank else w
+
+
+def slowest_rank(x, world, device):
+    """Max over ranks of a host float: the job takes as long as its slowest rank."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps, world, seconds):
+    """Whole-job rate: every rank's steps over the slowest rank's time."""
+    return steps * world / seconds
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -346,9 +367,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = WORKLOADS[args.workload]
-    if world > 1:
-        w = w.with_(seed=w.seed + 17 * rank)
+    w = rank_workload(WORKLOADS[args.workload], rank)
     precision = B.FP64 if args.precision == "fp64" else B.FP32
     npdt = np.float64 if precision == B.FP64 else np.float32
     tdt = torch.float64 if precision == B.FP64 else torch.float32
@@ -395,12 +414,8 @@ def run_ours(args):
     prof = h.profile_read()
     h.profile(False)
     h.check("timed steps")
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = args.steps * world / (t_max / 1e3)
+    t_max = slowest_rank(ms, world, dev)
+    value = job_rate(args.steps, world, t_max / 1e3)
 
     # roofline of the dominant kernel
     peaks, peak_src = _peaks()
@@ -445,13 +460,9 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             h.cycle_host(hXb, hy, hR, hZ, hXa)
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = slowest_rank(time.perf_counter() - t0, world, dev)
         m = inp.y.size
-        e2e = {"value": args.e2e_steps * world / t_e2e, "unit": "cycles/s",
+        e2e = {"value": job_rate(args.e2e_steps, world, t_e2e), "unit": "cycles/s",
                "h2d_bytes_per_step": esize * (w.N * w.n + 2 * m + w.N * m),
                "d2h_bytes_per_step": esize * w.N * w.n,
                "api": "enkfmc_cycle_host"}
