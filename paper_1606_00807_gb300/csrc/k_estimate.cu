@@ -415,6 +415,26 @@ __device__ __forceinline__ void ff_sub_prod(float& s, float& c, float x, float b
   c += e - perr;
 }
 
+// sqrt(x) and 1 / sqrt(x) for a pivot x > 0.  Single precision: Newton's
+// iteration for the reciprocal square root, one step from rsqrtf (a few
+// instructions instead of the IEEE square root and division), IEEE below the
+// normal range; double precision: IEEE.
+__device__ __forceinline__ void sqrt_and_inv(float x, float& s, float& inv) {
+  if (x < 1.17549435e-38f) {  // subnormal pivot
+    s = sqrtf(x);
+    inv = 1.f / s;
+    return;
+  }
+  float r = rsqrtf(x);
+  r = r * fmaf(-0.5f * x * r, r, 1.5f);
+  inv = r;
+  s = x * r;
+}
+__device__ __forceinline__ void sqrt_and_inv(double x, double& s, double& inv) {
+  s = sqrt(x);
+  inv = 1.0 / s;
+}
+
 // Right-looking Cholesky, in 4 x 4 tiles, of the leading nrows x nrows block
 // of the warp's lower-triangular matrix L (row stride ldg, a multiple of 4),
 // rows padded with identity rows up to a multiple of 4.  Pivots are taken for
@@ -451,8 +471,8 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
           const T piv = a[c][c];
           const bool fin = finite_val(piv);
           if (fin && piv > T(0)) {
-            const T sd = sqrt(piv);
-            inv = T(1) / sd;
+            T sd;
+            sqrt_and_inv(piv, sd, inv);
             a[c][c] = sd;
           } else if (!e) {
             e = fin ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;

@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kRows* kWarps) k_whiten(
   const int* nb_i = nbr + lane * pmax;
   const float* t_i = tv + lane * pmax;
   const float Dj = dj[lane];
+  const float invDj = 1.f / Dj;
   // kMB members per pass share the slot reads; members past N are skipped
   for (int m0 = kMB * warp; m0 < g.N; m0 += kMB * kWarps) {
     const float* dXm[kMB];
@@ -137,11 +138,13 @@ __global__ void __launch_bounds__(kRows* kWarps) k_whiten(
       if (m0 + u >= g.N) break;
       const float hi = s[u] + c[u];
       const float lo = c[u] - (hi - s[u]);
-      const float qh = hi / Dj;
+      // qh ~ hi / D_j; the remainder hi + lo - qh D_j is formed exactly by the
+      // FMA, so qh + rem / D_j carries the quotient to double-float accuracy
+      const float qh = hi * invDj;
       const float rem = fmaf(-qh, Dj, hi) + lo;
       const int64_t o = b.row_off * g.N + (int64_t)(m0 + u) * b.nb + loc0 + lane;
       vhi[o] = qh;
-      vlo[o] = rem / Dj;
+      vlo[o] = rem * invDj;
     }
   }
 }
