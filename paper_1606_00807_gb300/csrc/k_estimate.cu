@@ -553,7 +553,8 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
   return err;
 }
 
-// The pair table (pair_table_entry) in shared memory, built by the CTA.
+// The pair table of the typical row (pair_table_entry) in shared memory,
+// built by the CTA.
 __device__ inline void build_pair_table(const Geom& g, int pf, int2* ptab) {
   const int np = (pf + 1) * (pf + 2) / 2;
   for (int pi = threadIdx.x; pi < np; pi += blockDim.x) ptab[pi] = pair_table_entry(g, pf, pi);
@@ -562,6 +563,39 @@ __device__ inline void build_pair_table(const Geom& g, int pf, int2* ptab) {
 __host__ __device__ inline int pair_table_bytes(int pmax, int r, int periodic) {
   const int pf = pmax - (periodic ? r : 0);
   return ((pf + 1) * (pf + 2) / 2 * 8 + 15) / 16 * 16;
+}
+
+// Gather tables of the regressions, over the indices 0..pmax of a row's
+// augmented Gram matrix in slot terms (slot s, or pmax for the row itself):
+//  tri[pi]  = i | l << 8 for the pi-th entry (i, l), l <= i, of a lower
+//             triangle stored row by row;
+//  ftab[pi] = where the covariance of the pair of slots (i, l) sits in the
+//             table: column h, and bit 15 set when it is read at the row of the
+//             entry's column (l) instead of its row (i), as cov_lookup resolves
+//             it for the offset b - a = off(l) - off(i).
+// Built by the CTA; (pmax + 1)(pmax + 2) / 2 entries each.
+__device__ inline void build_gather_tables(const Geom& g, int pmax, uint16_t* tri,
+                                           uint16_t* ftab) {
+  const int np = (pmax + 1) * (pmax + 2) / 2;
+  const int w4 = 4 * g.r + 1;
+  const int B = (2 * g.vr + 1) * w4 * w4;
+  const int t0 = (B - 1) / 2;
+  for (int pi = threadIdx.x; pi < np; pi += blockDim.x) {
+    int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= pi) ++i;
+    while (i * (i + 1) / 2 > pi) --i;
+    const int l = pi - i * (i + 1) / 2;
+    int dki = 0, dyi = 0, dxi = 0, dkl = 0, dyl = 0, dxl = 0;
+    if (i < pmax) slot_offset(i, g.r, g.vr, dki, dyi, dxi);
+    if (l < pmax) slot_offset(l, g.r, g.vr, dkl, dyl, dxl);
+    const int t = ((dkl - dki + g.vr) * w4 + (dyl - dyi + 2 * g.r)) * w4 + (dxl - dxi + 2 * g.r);
+    tri[pi] = (uint16_t)(i | (l << 8));
+    ftab[pi] = (uint16_t)(t >= t0 ? t - t0 : ((B - 1 - t - t0) | 0x8000));
+  }
+}
+
+__host__ __device__ inline int gather_table_bytes(int pmax) {
+  return ((pmax + 1) * (pmax + 2) / 2 * 4 + 15) / 16 * 16;
 }
 
 // v := L^-1 v for the first n unknowns (L lower, stored in 4 x 4 tiles as
@@ -657,9 +691,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
   const int pf = pmax - (g.periodic ? g.r : 0);
   int2* ptab = reinterpret_cast<int2*>(smem + offbytes);
   build_pair_table(g, pf, ptab);
+  const int nfull = (pmax + 1) * (pmax + 2) / 2;
+  uint16_t* tri = reinterpret_cast<uint16_t*>(smem + offbytes + pair_table_bytes(pmax, g.r,
+                                                                                 g.periodic));
+  uint16_t* ftab = tri + nfull;
+  build_gather_tables(g, pmax, tri, ftab);
   __syncthreads();
   unsigned char* base = smem + offbytes + pair_table_bytes(pmax, g.r, g.periodic) +
-                        (size_t)warp * warp_bytes;
+                        gather_table_bytes(pmax) + (size_t)warp * warp_bytes;
   int* q = reinterpret_cast<int*>(base);   // [ldp] component labels (q[p] = j)
   int* sl = q + ldp;                        // [ldp] slot of compacted entry (-1 = j)
   int* sidx = sl + ldp;                     // [ldp] compacted index of slot s
@@ -723,7 +762,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     __syncwarp();
     const int p1 = p + 1;
 
-    // gather the augmented Gram matrix, lower triangle, rows 0..p
+    // gather the augmented Gram matrix, lower triangle, rows 0..p: the typical
+    // row through its pair table, any other row through the slots of i and l
     const int npair = p1 * (p1 + 1) / 2;
     const bool typical = p == pf && (p == 0 || sl[p - 1] == pf - 1);
     if (typical) {
@@ -734,15 +774,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
       }
     } else
     for (int pi = lane; pi < npair; pi += 32) {
-      int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
-      while ((i + 1) * (i + 2) / 2 <= pi) ++i;
-      while (i * (i + 1) / 2 > pi) --i;
-      const int l = pi - i * (i + 1) / 2;
-      const int si = sl[i], sm = sl[l];
-      const int dk = (sm >= 0 ? off[sm] : 0) - (si >= 0 ? off[si] : 0);
-      const int dy = (sm >= 0 ? off[pmax + sm] : 0) - (si >= 0 ? off[pmax + si] : 0);
-      const int dx = (sm >= 0 ? off[2 * pmax + sm] : 0) - (si >= 0 ? off[2 * pmax + si] : 0);
-      L[i * ldg + l] = cov_lookup(C, nH, g.r, g.vr, q[i], q[l], dk, dy, dx);
+      const uint32_t il = tri[pi];
+      const int i = il & 0xff, l = il >> 8;
+      int si = sl[i], sm = sl[l];
+      si = si < 0 ? pmax : si;  // the row itself
+      sm = sm < 0 ? pmax : sm;
+      const uint32_t e = ftab[si * (si + 1) / 2 + sm];
+      L[i * ldg + l] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
     }
     __syncwarp();
     T lam = T(0);
@@ -1177,7 +1215,8 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
   const int ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
   size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 4 * (size_t)ldp);
   wb = (wb + 15) / 16 * 16;
-  const int offbytes = (3 * g.pmax + 15) / 16 * 16 + pair_table_bytes(g.pmax, g.r, g.periodic);
+  const int offbytes = (3 * g.pmax + 15) / 16 * 16 + pair_table_bytes(g.pmax, g.r, g.periodic) +
+                       gather_table_bytes(g.pmax);
   int wpc = (int)((96 * 1024 - offbytes) / wb);
   if (wpc > 8) wpc = 8;
   if (wpc < 1) {
