@@ -446,7 +446,8 @@ __device__ __forceinline__ void sqrt_and_inv(double x, double& s, double& inv) {
 // u < npiv; *code (a slot not among those) carries the error code between
 // lanes.  Returns 0 or ENKFMC_EDNONPOS / ENKFMC_ENONFINITE (same in every lane).
 template <typename T>
-__device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int npiv, int lane) {
+__device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int npiv, int lane,
+                              const uint16_t* tri = nullptr) {
   const int p1 = nrows, p = npiv;
   const int P4 = (p1 + 3) & ~3;
   for (int i = p1 + lane; i < P4; i += 32) {
@@ -526,10 +527,17 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
     // trailing tiles (I, J), K < J <= I < nt
     const int ntile = nrem * (nrem + 1) / 2;
     for (int tix = lane; tix < ntile; tix += 32) {
-      int Ip = (int)((sqrtf(8.f * tix + 1.f) - 1.f) * 0.5f);
-      while ((Ip + 1) * (Ip + 2) / 2 <= tix) ++Ip;
-      while (Ip * (Ip + 1) / 2 > tix) --Ip;
-      const int Jp = tix - Ip * (Ip + 1) / 2;
+      int Ip, Jp;
+      if (tri) {  // lower-triangle index table: tix -> (Ip, Jp)
+        const uint32_t il = tri[tix];
+        Ip = il & 0xff;
+        Jp = il >> 8;
+      } else {
+        Ip = (int)((sqrtf(8.f * tix + 1.f) - 1.f) * 0.5f);
+        while ((Ip + 1) * (Ip + 2) / 2 <= tix) ++Ip;
+        while (Ip * (Ip + 1) / 2 > tix) --Ip;
+        Jp = tix - Ip * (Ip + 1) / 2;
+      }
       const int i0 = k0 + 4 * (Ip + 1), j0 = k0 + 4 * (Jp + 1);
       T li[4][4], lj[4][4], acc[4][4];
 #pragma unroll
@@ -799,7 +807,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 
     // right-looking tiled Cholesky; pivots for the first p columns, so row p
     // becomes w = L^-1 g
-    const int err0 = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p1, p, lane);
+    // (the trailing tiles of a step number at most nfull, the size of tri)
+    const int err0 = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p1, p, lane, tri);
     int err = err0;
 
     T Dj = T(0);
@@ -1043,9 +1052,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
   for (int a = 0; a < 4; ++a) ab = fma(aj[a], bj[a], ab);
   ab = warp_sum(ab);
   const T Dbar = ab / (Dj * Dj);
+  const T ebs = T(2) * Dbar / T(N - 1);
   T eb[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) eb[a] = T(2) * Dbar * e[a] / T(N - 1);
+  for (int a = 0; a < 4; ++a) eb[a] = ebs * e[a];
   // Gram matrix from the covariance table (as in the forward pass) and the ridge
   T lam = 0;
   if (p > 0) {
