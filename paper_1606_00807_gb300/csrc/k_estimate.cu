@@ -1238,8 +1238,11 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
   cudaError_t e = cudaFuncSetAttribute(k_regress<T, RR, MR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // a grid-stride loop over the rows: enough CTAs for an even tail, few enough
+  // that each amortises its shared tables (measured on the T63 rows: 64 CTAs
+  // per SM beat 24, 32, 128 and one CTA per 8 rows)
   int64_t grid = (nitems + wpc - 1) / wpc;
-  if (grid > 152 * 32) grid = 152 * 32;
+  if (grid > 152 * 64) grid = 152 * 64;
   k_regress<T, RR, MR><<<(unsigned)grid, 32 * wpc, smem, s>>>(
       g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, ldp, ldg, (int)wb);
   return cudaGetLastError();
