@@ -548,17 +548,17 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
 //    accumulation in TMEM); thread (tile, row) reads its row of D and
 //    subtracts it from the band, the lanes of a warp on consecutive rows of
 //    one band column (coalesced), 64 entries read before any is written;
-//  * round 0 forms the tiles (mi, 0), whose first 32 columns are the next
+//  * batch 0 forms the tiles (mi, 0), whose first 32 columns are the next
 //    panel: thread t handles window row t there, which is row t of the next
 //    panel, so those updated entries go to the thread's own column of sA
 //    (shared memory) instead of the band, together with the entries of the
-//    rows that enter the band with the next panel; round 1 forms the tiles
+//    rows that enter the band with the next panel; batch 1 forms the tiles
 //    (mi, nj >= 1).  The next panel starts from sA, not from the band.
 constexpr int kCholThreads = 384;  // 12 warps: rows of the panel; 3 tiles x 4 lane quarters
 constexpr int kOpRows = 384;       // L21 rows staged (3 tiles of 128)
 
-// Tile k of a panel whose window spans nt row tiles: k < nt -> (k, 0) (round
-// 0); then (1,1), (2,1), (2,2) (round 1).
+// Tile k of a panel whose window spans nt row tiles: k < nt -> (k, 0) (batch
+// 0); then (1,1), (2,1), (2,2) (batch 1).
 __device__ __forceinline__ void syrk_tile(int k, int nt, int& mi, int& nj) {
   if (k < nt) {
     mi = k;
@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
   const uint32_t hi0 = tc::smem_u32(sHi), lo0 = tc::smem_u32(sLo);
   uint32_t phase = 0;
   bool inflight = false;
-  int covered = 0;  // rows of this panel whose entries round 0 left in sA
+  int covered = 0;  // rows of this panel whose entries batch 0 left in sA
 
   for (int c0 = 0; c0 < nb; c0 += 32) {
     const int nbc = min(32, nb - c0);
@@ -764,7 +764,7 @@ __global__ void __launch_bounds__(kCholThreads, 1)
 #pragma unroll 1
         for (int h2 = 0; h2 < 4; h2 += 2) {
           const int cb = 128 * nj + 32 * h2;
-          // columns [0, 32) of round 0 are the next panel (rr == tid there):
+          // columns [0, 32) of batch 0 are the next panel (rr == tid there):
           // the rows entering the band with it are read as well
           const bool nxt = rd == 0 && h2 == 0;
           float o[64];
@@ -848,7 +848,7 @@ cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, floa
   if (!bandchol_tc_supported(hb_max)) return cudaErrorInvalidConfiguration;
   const size_t smem =
       2 * (size_t)kOpRows * 128 + sizeof(float) * (32 * 32 + 32 + 32 * kCholThreads) + 32;
-  const int WT = hb_max <= 128 ? 128 : 512;  // one tile, or rounds of three
+  const int WT = hb_max <= 128 ? 128 : 512;  // one tile, or batches of three
   cudaError_t e = cudaFuncSetAttribute(k_bandchol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
