@@ -190,6 +190,17 @@ def dist_env():
     return rank, world, local
 
 
+def workload_config(args, w, world):
+    """The `config` of the JSON line (the same for both arms)."""
+    esize = 8 if args.precision == "fp64" else 4
+    return {"workload": args.workload, "n": w.n, "N": w.N, "r": w.r,
+            "grid": f"{w.nlon}x{w.nlat}x({w.nlev}x{w.nvar_3d}+{w.nvar_2d})",
+            "subdomains": f"{w.sub_lat}x{w.sub_lon}+halo{w.r}",
+            "obs_frac": w.obs_frac, "precision": args.precision,
+            "l2": "inputs larger than L2 (Xb %.0f MB), no flush" % (esize * w.N * w.n / 1e6),
+            "parallelism": "independent problem per GPU" if world > 1 else "1 GPU"}
+
+
 def rank_workload(w, rank):
     """Rank `rank`'s problem: the same shapes with its own seed (independent
     problems, no exchange between ranks)."""
@@ -238,7 +249,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": mean_cycle * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "precision": "fp64 oracle"},
+           "config": workload_config(args, w, 1),
            "cpu_baseline": {"value": value, "unit": "cycles/s", "cores": cores, "kind": "oracle",
                             "sample": "per step: " + sample + "; cycle time extrapolated"},
            "e2e": {"value": value, "unit": "cycles/s", "h2d_bytes_per_step": 0,
@@ -488,13 +499,7 @@ def run_ours(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64" if precision == B.FP64 else "f32", "data": "synthetic",
-               "config": {"workload": args.workload, "n": w.n, "N": w.N, "r": w.r,
-                          "grid": f"{w.nlon}x{w.nlat}x({w.nlev}x{w.nvar_3d}+{w.nvar_2d})",
-                          "subdomains": f"{w.sub_lat}x{w.sub_lon}+halo{w.r}",
-                          "obs_frac": w.obs_frac, "precision": args.precision,
-                          "l2": "inputs larger than L2 (Xb %.0f MB), no flush" %
-                                (esize * w.N * w.n / 1e6),
-                          "parallelism": "independent problem per GPU" if world > 1 else "1 GPU"},
+               "config": workload_config(args, w, world),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(sum(v[0] for v in prof.values())),
                "clocks": clocks,
