@@ -61,3 +61,34 @@ def test_gradient_of_analysis_is_linear_in_the_output_gradient():
     # and the forward part equals the plain analysis
     Xa = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
     assert np.allclose(g1[0], Xa, rtol=0, atol=1e-12 * np.abs(Xa).max())
+
+
+@pytest.mark.parametrize("name,ridge", [("tiny_32x16_n20_r2", False),
+                                        ("small_36x24x2x1_n24_r3_ridge", True)])
+def test_regression_residual_normal_equations(name, ridge):
+    """The regression residual e = u_j - U_P^T beta of (G + lambda I) beta =
+    U_P u_j, G = U_P U_P^T (Eq. 1 with the ridge) satisfies U_P e = lambda beta;
+    the GPU adjoint takes <U_qi, ebar> from this instead of a pass over U_P.
+    Checked against the oracle's own regressions, rows with and without the
+    ridge, to rounding relative to |U_P| |u_j|."""
+    from oracle.adjoint import _regression_parts
+    w = WORKLOADS[name]
+    g = O.Grid.from_workload(w)
+    U = O.anomalies(make_inputs(w).Xb.T)
+    seen_ridge = seen_plain = 0
+    for j in range(0, g.n, 7):
+        P = g.predecessors(j)
+        if not P:
+            continue
+        beta, e, _, _, lam = _regression_parts(U, j, P, w.ridge_c)
+        UP = U[np.asarray(P, dtype=np.int64)]
+        scale = np.abs(UP).sum(axis=1).max() * np.abs(U[j]).max()
+        assert np.allclose(UP @ e, lam * beta, rtol=0, atol=1e-11 * scale)
+        if lam > 0:
+            seen_ridge += 1
+            assert np.abs(UP @ e).max() > 1e3 * 1e-11 * scale  # the ridge term is not rounding
+        else:
+            seen_plain += 1
+    assert seen_plain > 5
+    if ridge:
+        assert seen_ridge > 5
