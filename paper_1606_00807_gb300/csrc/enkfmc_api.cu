@@ -309,19 +309,26 @@ enkfmc_status build(enkfmc_handle* h) {
     if ((st = dalloc(h, &h->d_ptab, sizeof(int2) * ptab.size()))) return st;
     CUDA_TRY(cudaMemcpy(h->d_ptab, ptab.data(), sizeof(int2) * ptab.size(),
                         cudaMemcpyHostToDevice));
+    // gather tables of any row (gather_table_entry): tri, then ftab
+    const size_t nfull = (size_t)(g.pmax + 1) * (g.pmax + 2) / 2;
+    std::vector<uint16_t> gtab(2 * nfull);
+    for (size_t pi = 0; pi < nfull; ++pi)
+      gather_table_entry(g, g.pmax, (int)pi, gtab[pi], gtab[nfull + pi]);
+    if ((st = dalloc(h, &h->d_gtab, sizeof(uint16_t) * gtab.size()))) return st;
+    CUDA_TRY(cudaMemcpy(h->d_gtab, gtab.data(), sizeof(uint16_t) * gtab.size(),
+                        cudaMemcpyHostToDevice));
   }
   CUDA_TRY(cudaMemset(h->d_status, 0, 16));
   return ENKFMC_OK;
 }
 
 void release(enkfmc_handle* h) {
-  void* bufs[] = {h->d_pairs,  h->d_srcrow, h->d_ptab,  h->d_blocks, h->d_halo, h->d_status,
-                  h->d_obs_of,
-                  h->d_U,   h->d_C,
-                  h->d_Te,     h->d_De,   h->d_band,   h->d_invdiag, h->d_rhs,    h->d_res, h->d_vhi,
-                  h->d_vlo,    h->d_Xb,   h->d_y,      h->d_R,      h->d_Z,   h->d_Xa,
-                  h->d_T,      h->d_D,    h->d_lam,    h->d_aT,     h->d_bT,  h->d_dxT,
-                  h->d_lamT,   h->d_Ubar};
+  void* bufs[] = {h->d_pairs, h->d_srcrow, h->d_ptab,  h->d_gtab,    h->d_blocks, h->d_halo,
+                  h->d_status, h->d_obs_of, h->d_U,   h->d_C,       h->d_Te,     h->d_De,
+                  h->d_band,  h->d_invdiag, h->d_rhs, h->d_res,     h->d_vhi,    h->d_vlo,
+                  h->d_Xb,    h->d_y,       h->d_R,   h->d_Z,       h->d_Xa,     h->d_T,
+                  h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
+                  h->d_Ubar};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
@@ -596,7 +603,7 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
     return launch_adj_regress<T>(g, h->d_blocks, h->nblock, h->nb_max, (const T*)h->d_U,
                                  (const T*)h->d_C, Tg, Dg, (const T*)h->d_Te, (const T*)h->d_De,
                                  (const T*)h->d_aT, (const T*)h->d_bT, (const T*)h->d_dxT,
-                                 (const T*)h->d_lamT, h->d_ptab, (T*)h->d_Ubar,
+                                 (const T*)h->d_lamT, h->d_ptab, h->d_gtab, (T*)h->d_Ubar,
                                  h->prob.ridge_c, h->d_status, h->stream);
   });
   if (st) return st;

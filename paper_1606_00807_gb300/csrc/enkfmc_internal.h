@@ -156,6 +156,30 @@ __host__ __device__ inline int2 pair_table_entry(const Geom& g, int pf, int pi) 
                  : make_int2(i | (l << 8) | (1 << 16), B - 1 - t - t0);
 }
 
+// Entry pi of the regressions' gather tables over the indices 0..pmax of a
+// row's augmented Gram matrix in slot terms (slot s, or pmax for the row
+// itself), lower triangle stored row by row: tri = i | l << 8 for the entry
+// (i, l), l <= i; ftab = where the covariance of the pair of slots (i, l)
+// sits in the covariance table: column h, and bit 15 set when it is read at
+// the row of the entry's column (l) instead of its row (i), as for the offset
+// b - a = off(l) - off(i) of the pair (a, b).  (pmax + 1)(pmax + 2) / 2 entries.
+__host__ __device__ inline void gather_table_entry(const Geom& g, int pmax, int pi,
+                                                   uint16_t& tri, uint16_t& ftab) {
+  const int w4 = 4 * g.r + 1;
+  const int B = (2 * g.vr + 1) * w4 * w4;
+  const int t0 = (B - 1) / 2;
+  int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= pi) ++i;
+  while (i * (i + 1) / 2 > pi) --i;
+  const int l = pi - i * (i + 1) / 2;
+  int dki = 0, dyi = 0, dxi = 0, dkl = 0, dyl = 0, dxl = 0;
+  if (i < pmax) slot_offset(i, g.r, g.vr, dki, dyi, dxi);
+  if (l < pmax) slot_offset(l, g.r, g.vr, dkl, dyl, dxl);
+  const int t = ((dkl - dki + g.vr) * w4 + (dyl - dyi + 2 * g.r)) * w4 + (dxl - dxi + 2 * g.r);
+  tri = (uint16_t)(i | (l << 8));
+  ftab = (uint16_t)(t >= t0 ? t - t0 : ((B - 1 - t - t0) | 0x8000));
+}
+
 // Local position of absolute (yq, xq) in a block's extended box.
 __host__ __device__ inline bool in_ext(const Block& b, int nlon, int yq, int xq, int& yy, int& xx) {
   yy = yq - b.lat_lo;
@@ -194,6 +218,7 @@ struct enkfmc_handle {
   int4* d_pairs = nullptr;       // slot pairs per block shape, sorted by band diagonal
   int32_t* d_srcrow = nullptr;   // per extended row: global label (>= 0) or ~boundary row
   int2* d_ptab = nullptr;        // pair table of the typical row (pair_table_entry)
+  uint16_t* d_gtab = nullptr;    // gather tables: tri, then ftab (gather_table_entry)
   bool pair_assembly = false;    // every block can use the pair lists
   int32_t npair_max = 0;         // longest pair list of a shape
   int32_t box_sum = 0;           // largest nlev_b + ey + ex of a block
@@ -350,8 +375,8 @@ template <typename T>
 cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
                                const T* De, const T* aT, const T* bT, const T* dxT,
-                               const T* lamT, const int2* ptab, T* Ubar, double ridge_c,
-                               int32_t* status, cudaStream_t s);
+                               const T* lamT, const int2* ptab, const uint16_t* gtab,
+                               T* Ubar, double ridge_c, int32_t* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_finish(const Geom& g, const T* Ubar, const T* Xa_bar, T* Xb_bar,
                               cudaStream_t s);

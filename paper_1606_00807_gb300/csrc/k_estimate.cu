@@ -573,33 +573,13 @@ __host__ __device__ inline int pair_table_bytes(int pmax, int r, int periodic) {
   return ((pf + 1) * (pf + 2) / 2 * 8 + 15) / 16 * 16;
 }
 
-// Gather tables of the regressions, over the indices 0..pmax of a row's
-// augmented Gram matrix in slot terms (slot s, or pmax for the row itself):
-//  tri[pi]  = i | l << 8 for the pi-th entry (i, l), l <= i, of a lower
-//             triangle stored row by row;
-//  ftab[pi] = where the covariance of the pair of slots (i, l) sits in the
-//             table: column h, and bit 15 set when it is read at the row of the
-//             entry's column (l) instead of its row (i), as cov_lookup resolves
-//             it for the offset b - a = off(l) - off(i).
-// Built by the CTA; (pmax + 1)(pmax + 2) / 2 entries each.
+// The regressions' gather tables (gather_table_entry) in shared memory, built
+// by the CTA: tri then ftab, (pmax + 1)(pmax + 2) / 2 entries each.
 __device__ inline void build_gather_tables(const Geom& g, int pmax, uint16_t* tri,
                                            uint16_t* ftab) {
   const int np = (pmax + 1) * (pmax + 2) / 2;
-  const int w4 = 4 * g.r + 1;
-  const int B = (2 * g.vr + 1) * w4 * w4;
-  const int t0 = (B - 1) / 2;
-  for (int pi = threadIdx.x; pi < np; pi += blockDim.x) {
-    int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= pi) ++i;
-    while (i * (i + 1) / 2 > pi) --i;
-    const int l = pi - i * (i + 1) / 2;
-    int dki = 0, dyi = 0, dxi = 0, dkl = 0, dyl = 0, dxl = 0;
-    if (i < pmax) slot_offset(i, g.r, g.vr, dki, dyi, dxi);
-    if (l < pmax) slot_offset(l, g.r, g.vr, dkl, dyl, dxl);
-    const int t = ((dkl - dki + g.vr) * w4 + (dyl - dyi + 2 * g.r)) * w4 + (dxl - dxi + 2 * g.r);
-    tri[pi] = (uint16_t)(i | (l << 8));
-    ftab[pi] = (uint16_t)(t >= t0 ? t - t0 : ((B - 1 - t - t0) | 0x8000));
-  }
+  for (int pi = threadIdx.x; pi < np; pi += blockDim.x)
+    gather_table_entry(g, pmax, pi, tri[pi], ftab[pi]);
 }
 
 __host__ __device__ inline int gather_table_bytes(int pmax) {
@@ -952,8 +932,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
     const T* __restrict__ C, int nH, const T* __restrict__ Tg, const T* __restrict__ Dg,
     const T* __restrict__ Te, const T* __restrict__ De, const T* __restrict__ aT,
     const T* __restrict__ bT, const T* __restrict__ dxT, const T* __restrict__ lamT,
-    const int2* __restrict__ ptab, T* __restrict__ Ubar, double ridge_c, int32_t* status,
-    int ldp, int ldg, int warp_bytes) {
+    const int2* __restrict__ ptab, const uint16_t* __restrict__ gtab, T* __restrict__ Ubar,
+    double ridge_c, int32_t* status, int ldp, int ldg, int warp_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   signed char* off = reinterpret_cast<signed char*>(smem);
@@ -1068,6 +1048,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
         const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
         L[i * ldg + l] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
       }
+    } else if (gtab) {  // any other row: the handle's gather tables, through the slots
+      const int nfull = (pmax + 1) * (pmax + 2) / 2;
+      for (int pi = lane; pi < npair; pi += 32) {
+        const uint32_t il = gtab[pi];
+        const int i = il & 0xff, l = il >> 8;
+        const int si = sl[i], sm = sl[l];
+        const uint32_t e = gtab[nfull + si * (si + 1) / 2 + sm];
+        L[i * ldg + l] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
+      }
     } else
     for (int pi = lane; pi < npair; pi += 32) {
       int i = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
@@ -1116,7 +1105,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
   for (int a = 0; a < 4; ++a) f[a] = eb[a];
   T kappa = 0;
   if (p > 0) {
-    const int err = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p, p, lane);
+    const int err = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p, p, lane, gtab);
     if (err) {
       if (lane == 0) record_error(status, err, rowj);
       return;
@@ -1281,8 +1270,8 @@ template <typename T>
 cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
                                const T* De, const T* aT, const T* bT, const T* dxT,
-                               const T* lamT, const int2* ptab, T* Ubar, double ridge_c,
-                               int32_t* status, cudaStream_t s) {
+                               const T* lamT, const int2* ptab, const uint16_t* gtab,
+                               T* Ubar, double ridge_c, int32_t* status, cudaStream_t s) {
   if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
     return cudaErrorInvalidConfiguration;
   const int nH = cov_offset_count(g.r, g.vr);
@@ -1304,8 +1293,8 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
   if (e != cudaSuccess) return e;
   const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
   k_adj_regress<T><<<grid, 32 * wpc, smem, s>>>(g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT,
-                                                 dxT, lamT, ptab, Ubar, ridge_c, status, ldp,
-                                                 ldg, (int)wb);
+                                                 dxT, lamT, ptab, gtab, Ubar, ridge_c, status,
+                                                 ldp, ldg, (int)wb);
   return cudaGetLastError();
 }
 
@@ -1313,7 +1302,8 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
   template cudaError_t launch_adj_regress<T>(const Geom&, const Block*, int, int, const T*,     \
                                              const T*, const T*, const T*, const T*, const T*,  \
                                              const T*, const T*, const T*, const T*,           \
-                                             const int2*, T*, double, int32_t*, cudaStream_t);                            \
+                                             const int2*, const uint16_t*, T*, double, int32_t*, \
+                                             cudaStream_t);                            \
   template cudaError_t launch_anomalies<T>(const Geom&, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_covtable<T>(const Geom&, const T*, T*, cudaStream_t);             \
   template cudaError_t launch_regress<T>(const Geom&, const T*, const T*, const int32_t*,       \
