@@ -190,6 +190,43 @@ def dist_env():
     return rank, world, local
 
 
+def roofline(prof, work, peaks, peak_src, sm_max_mhz, fp32, workload, precision):
+    """Roofline of the dominant kernel (largest device time per cycle).
+
+    prof: kernel -> (launches, ms); work: kernel -> (flops, bytes) per launch.
+    The bound is the one whose time per launch is larger at its peak: FP32 FMA
+    lanes at the maximum SM clock (or FP64 nominal) for flops, the measured
+    copy bandwidth for bytes; achieved = the algorithmic work per launch over
+    the kernel's average launch time."""
+    dom = max(prof, key=lambda k: prof[k][1])
+    launches, dom_ms = prof[dom]
+    avg_s = dom_ms / max(1, launches) / 1e3
+    flops, nbytes = work[dom]
+    sm_max = sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
+    if fp32:
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        alu_note = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                    f"{sm_max:.0f} MHz")
+    else:
+        alu_peak = FP64_NOMINAL_TFLOPS
+        alu_note = "FP64 nominal 1.25 TFLOP/s"
+    t_alu = flops / (alu_peak * 1e12)
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    if t_alu >= t_hbm:
+        achieved = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "peak_source": f"derived: {alu_note}"}
+    else:
+        achieved = nbytes / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} hbm_gbs"}
+    roof["traffic"] = TRAFFIC_PER_LAUNCH.get((dom, workload, precision))
+    roof["kernel"] = dom
+    roof["avg_launch_ms"] = avg_s * 1e3
+    roof["algorithmic_per_launch"] = {"flops": flops, "bytes": nbytes}
+    return roof
+
+
 def workload_config(args, w, world):
     """The `config` of the JSON line (the same for both arms)."""
     esize = 8 if args.precision == "fp64" else 4
@@ -435,35 +472,9 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     peaks, peak_src = _peaks()
-    work = h.work_per_launch()
-    dom = max(prof, key=lambda k: prof[k][1])
-    launches, dom_ms = prof[dom]
-    avg_s = dom_ms / max(1, launches) / 1e3
-    flops, nbytes = work[dom]
-    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if precision == B.FP32:
-        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        alu_note = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                    f"{sm_max:.0f} MHz")
-    else:
-        alu_peak = FP64_NOMINAL_TFLOPS
-        alu_note = "FP64 nominal 1.25 TFLOP/s"
-    t_alu = flops / (alu_peak * 1e12)
-    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
-    if t_alu >= t_hbm:
-        achieved = flops / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": f"derived: {alu_note}"}
-    else:
-        achieved = nbytes / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": f"{peak_src} hbm_gbs"}
-    roof["traffic"] = TRAFFIC_PER_LAUNCH.get((dom, args.workload, args.precision))
-    roof["kernel"] = dom
-    roof["avg_launch_ms"] = avg_s * 1e3
-    roof["algorithmic_per_launch"] = {"flops": flops, "bytes": nbytes}
+    roof = roofline(prof, h.work_per_launch(), peaks, peak_src,
+                    (clocks or {}).get("sm_max_mhz"), precision == B.FP32, args.workload,
+                    args.precision)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
