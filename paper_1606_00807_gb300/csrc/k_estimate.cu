@@ -18,8 +18,8 @@
 // Rows.  One warp per row j: the predecessor list P_j (stencil slots that are
 // predecessors, optionally cut to a sub-domain's extended box) is compacted
 // with a ballot, the augmented Gram matrix [U_P; u_j][U_P; u_j]^T is gathered
-// from the table, factored by a left-looking (Crout) Cholesky whose last row
-// yields w = L^-1 g, and beta = L^-T w.  In single precision one step of
+// from the table and factored by a right-looking Cholesky in 4 x 4 tiles
+// (tiled_cholesky) whose last row yields w = L^-1 g; then beta = L^-T w.  In single precision one step of
 // iterative refinement corrects beta with the residual e = u_j - U_P^T beta
 // computed in compensated (double-float: FMA two-product and two-sum)
 // arithmetic from U: beta += (L L^T)^-1 U_P e (corrected semi-normal

@@ -96,9 +96,21 @@ def per_variable_err(w: Workload, labels: np.ndarray, got: np.ndarray, ref: np.n
     return worst
 
 
+def elementwise_rel_err(got: np.ndarray, ref: np.ndarray) -> float:
+    """max_i |got_i - ref_i| / |ref_i| (ref_i != 0): every entry on its own scale, so a
+    small D_j, whose inverse enters A, is held to the same relative bound as a large one."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if not ref.size:
+        return 0.0
+    assert np.all(ref != 0)
+    return float(np.max(np.abs(got - ref) / np.abs(ref)))
+
+
 def compare_T_rows(w: Workload, h, T_gpu: np.ndarray, D_gpu: np.ndarray, rows, ref_rows):
-    """Errors of T (per variable) and D against the oracle's (j, P, beta, D) rows, and a
-    check that every nonzero GPU coefficient sits on a predecessor."""
+    """Errors against the oracle's (j, P, beta, D) rows: T per variable, D per variable
+    and D element by element; also checks that every nonzero GPU coefficient sits on a
+    predecessor.  Returns (eT, eD, eD_elem)."""
     dk, dy, dx = h.slot_offsets()
     rows = np.asarray(rows)
     nb = slot_neighbours(w, dk, dy, dx, rows)
@@ -116,4 +128,5 @@ def compare_T_rows(w: Workload, h, T_gpu: np.ndarray, D_gpu: np.ndarray, rows, r
                 assert T_gpu[j, s] == 0.0, (j, s)
         dref[a] = d
     return (per_variable_err(w, rows, got, ref),
-            per_variable_err(w, rows, D_gpu[rows], dref))
+            per_variable_err(w, rows, D_gpu[rows], dref),
+            elementwise_rel_err(D_gpu[rows], dref))

@@ -56,9 +56,10 @@ def _parity(name, precision, tol_x=None, flags=0):
     g = O.Grid.from_workload(w)
     rows = np.arange(g.n)
     ref = O.estimate_rows(g, U, rows, w.ridge_c)
-    eT, eD = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
+    eT, eD, eDe = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
     assert eT < tol, eT
     assert eD < tol, eD
+    assert eDe < tol, eDe
     # steps (b)-(c): the analysis ensemble and its increment
     Xa_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
     Xb = inp.Xb.astype(np.float64)
@@ -145,9 +146,10 @@ def test_full_t63_sampled_fp32():
         [0, w.nlon - 1, w.nlon, g.n - 1, g.offsets[4], g.offsets[4] + w.nlon - 1,
          g.offsets[1] - 1, g.label(2, 3, 47, 191), g.label(3, 6, 95, 0)]]))
     ref = O.estimate_rows(g, U, rows, w.ridge_c)
-    eT, eD = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
+    eT, eD, eDe = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
     assert eT < TOL[1], eT
     assert eD < TOL[1], eD
+    assert eDe < TOL[1], eDe
     # sub-domains: pole + seam corner, an interior tile, the last tile
     sds = O.subdomains(g, w.sub_lon, w.sub_lat)
     pick = [0, 16 * 3 + 7, len(sds) - 1]

@@ -79,6 +79,37 @@ def test_predecessors_bruteforce(shape, periodic):
         assert g.predecessors(j) == want
 
 
+def test_anomalies_hand_case_and_numpy_covariance():
+    """Eq. 5: U = X - mean(X) 1^T.  A hand case, zero row sums over members, and the
+    sample covariance U U^T / (N - 1) against numpy's own (independently centred)
+    np.cov; a mean taken over components instead of members, or no centring, fails."""
+    X = np.array([[1.0, 2.0, 3.0, 6.0], [4.0, 4.0, 4.0, 4.0], [-2.0, 0.0, 2.0, 8.0]])
+    U = O.anomalies(X)
+    want = np.array([[-2.0, -1.0, 0.0, 3.0], [0.0, 0.0, 0.0, 0.0], [-4.0, -2.0, 0.0, 6.0]])
+    assert np.array_equal(U, want)
+    w = WORKLOADS["small_40x30x2x2+1_n48_r2"]
+    Xb = make_inputs(w).Xb.T                       # n x N
+    U = O.anomalies(Xb)
+    assert np.abs(U.sum(axis=1)).max() < 1e-12 * np.abs(Xb).max() * w.N
+    sub = slice(0, 400)
+    S = U[sub] @ U[sub].T / (w.N - 1)
+    C = np.cov(Xb[sub])                            # rows are variables, columns samples
+    assert np.allclose(S, C, rtol=1e-11, atol=1e-13 * np.abs(C).max())
+
+
+def test_perturbed_observations_scale_is_sqrt_R():
+    """Y^s = y + sqrt(R) z (Section 2.3, Algorithm 1): hand values, and the sample
+    variance of Y^s - y over many standard normals equals R (not sqrt R, not R^2)."""
+    Ys = O.perturbed_observations(np.array([1.0, -2.0]), np.array([4.0, 0.25]),
+                                  np.array([[1.5, -1.0], [2.0, 4.0]]))
+    assert np.array_equal(Ys, np.array([[4.0, -1.0], [-1.0, 0.0]]))
+    R = np.array([0.01, 4.0, 9.0])
+    Z = normal_stream(42, 3, 3 * 200000).reshape(3, 200000)
+    d = O.perturbed_observations(np.array([5.0, -1.0, 0.0]), R, Z) - np.array([[5.0], [-1.0], [0.0]])
+    var = d.var(axis=1, ddof=1)
+    assert np.allclose(var, R, rtol=0.02)
+
+
 def test_full_radius_reproduces_inverse_sample_covariance():
     """With every earlier component a predecessor and N > n, T^T D^-1 T equals the
     inverse of S = U U^T / (N - 1) (Eq. 1-3 and Eq. 8 with S = U), and T^-1 D T^-T = S."""
