@@ -5,18 +5,23 @@ One step = one analysis cycle of the whole hot path on one synthetic ensemble
 already resident in HBM: enkfmc_estimate (anomalies + the regressions of every
 component), enkfmc_assemble (boundary re-estimation, band assembly, banded
 Cholesky of every sub-domain block) and enkfmc_analyze (right-hand sides,
-N-member band solves, interior write-back).  Workload: the T63-shaped state
-(192 x 96 x (7 levels x 4 variables + 1), n = 534,528), N = 80 members,
-r = 2, 12 x 12 sub-domains with an r-wide boundary, 50% of the components
-observed; FP32 by default.  Inputs are larger than L2 (X^b alone is 171 MB
-in FP32), so no flush is needed between steps.
+N-member band solves with refinement, interior write-back).  Workload: the
+T63-shaped state (192 x 96 x (7 levels x 4 variables + 1), n = 534,528),
+N = 80 members, r = 2, 12 x 12 sub-domains with an r-wide boundary, 50% of the
+components observed; FP32 by default.  Inputs are larger than L2 (X^b alone is
+171 MB in FP32), so no flush is needed between steps.
 
-Printed: one JSON line with the contract keys, the roofline of the dominant
-kernel (timed live with CUDA events on the library's stream), the end-to-end
-rate through enkfmc_cycle_host from pinned host buffers, the SM clocks seen
-during the timed region, and the FP64 oracle timed on a bounded sample on the
-host cores.  Multi-GPU (torchrun): every rank runs an independent problem (its
-own seed); value = cycles of all ranks / slowest rank's time.
+The headline steps run with the library's per-kernel events off; a second
+timed pass with them on gives the per-kernel split, the roofline of the
+dominant kernel and the path fraction (sum of per-kernel roofline times over
+the cycle time).  Also printed: the end-to-end rate through enkfmc_cycle_host
+from pinned host buffers, the SM clocks seen during the timed region, and the
+CPU baseline: the FP64 oracle timed on a bounded sample on one host thread and
+on all host cores; the oracle values of that sample give the accuracy report
+(max relative error of T, D, dX and X^a against the oracle).  Side lines: the
+plain FP64 form, and forward + adjoint (T63 with N = 80 and with N = 40).
+Multi-GPU (torchrun): every rank runs an independent problem (its own seed);
+value = cycles of all ranks / slowest rank's time.
 
 `--impl reference` times the FP64 CPU oracle on the same workload instead.
 """
@@ -37,14 +42,14 @@ if ROOT not in sys.path:
 
 METRIC = "EnKF-MC analysis cycles/sec at T63 shape (N=80); % roofline; fwd+adj vs plain"
 WORKLOAD = "t63_192x96x29_n80_r2"
-SM_COUNT = 152
+ADJ_WORKLOAD = "t63_192x96x29_n40_r2"
 FP32_LANES_PER_SM = 128
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel from one ncu capture of its current version on the named workload and
 # precision (the capture commands are in profiles/); a kernel without one
 # reports null.
-TRAFFIC_PER_LAUNCH = {("regress", "t63_192x96x29_n80_r2", "fp32"): 724.3e6}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def parse_args(argv=None):
@@ -56,12 +61,17 @@ def parse_args(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--profile-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-FP64 and forward+adjoint side measurements")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--sample-rows", type=int, default=1000)
-    ap.add_argument("--sample-subdomains", type=int, default=3)
+    ap.add_argument("--cpu-workers", type=int, default=0,
+                    help="host processes of the all-cores oracle leg (0: every core)")
+    ap.add_argument("--sample-rows", type=int, default=250)
+    ap.add_argument("--sample-subdomains", type=int, default=1)
+    ap.add_argument("--sample-out", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--sample-steps", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
 
@@ -129,57 +139,207 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle timing (bounded sample), used by cpu_baseline and --impl reference
+# CPU oracle timing (bounded sample): the cpu_baseline leg and --impl reference.
+# The sample's oracle values also serve as the reference of the accuracy report.
 # ----------------------------------------------------------------------------
-def oracle_sample_time(w, inp, nrows, nsub, seed=0):
-    """Seconds per full analysis cycle of the FP64 oracle, extrapolated from
-    `nrows` global regressions and `nsub` sub-domain analyses."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def sample_plan(n, nsd, nrows, nsub, seed=0):
+    """The sampled rows (of n) and sub-domains (of nsd) of one step (deterministic)."""
     import numpy as np
-    import oracle as O
-    g = O.Grid.from_workload(w)
-    sds = O.subdomains(g, w.sub_lon, w.sub_lat)
     rng = np.random.default_rng(seed)
-    Xb = inp.Xb.T.astype(np.float64)
+    rows = np.sort(rng.choice(n, min(nrows, n), replace=False))
+    picks = [int(i) for i in rng.choice(nsd, min(nsub, nsd), replace=False)]
+    return rows, picks
+
+
+_CTX = {}
+
+
+def _oracle_rows(rows):
+    import oracle as O
+    c = _CTX
     t0 = time.perf_counter()
-    U = O.anomalies(Xb)
-    t_anom = time.perf_counter() - t0
-    rows = rng.choice(g.n, nrows, replace=False)
+    out = O.estimate_rows(c["g"], c["U"], rows, c["w"].ridge_c)
+    return time.perf_counter() - t0, [(j, list(P), beta, d) for j, P, beta, d in out]
+
+
+def _oracle_subdomain(i):
+    import oracle as O
+    c = _CTX
+    sd = c["sds"][i]
     t0 = time.perf_counter()
-    O.estimate_rows(g, U, rows, w.ridge_c)
-    t_row = (time.perf_counter() - t0) / nrows
-    Ys = O.perturbed_observations(inp.y, inp.R, inp.Z.T)
-    picks = rng.choice(len(sds), nsub, replace=False)
-    t0 = time.perf_counter()
-    for i in picks:
-        O.local_analysis(g, sds[int(i)], U, Xb, Ys, inp.R, inp.obs_idx, w.ridge_c)
-    t_sd = (time.perf_counter() - t0) / nsub
-    cycle = t_anom + t_row * g.n + t_sd * len(sds)
-    return cycle, f"{nrows} of {g.n} regressions + {nsub} of {len(sds)} sub-domain analyses"
+    dX = O.local_analysis(c["g"], sd, c["U"], c["Xb"], c["Ys"], c["inp"].R, c["inp"].obs_idx,
+                          c["w"].ridge_c)
+    dt = time.perf_counter() - t0
+    pos = {int(q): k for k, q in enumerate(sd.ext)}
+    rows = [pos[int(q)] for q in sd.interior]
+    return dt, i, c["Xb"][sd.interior] + dX[rows]
 
 
 def cpu_sample_main(args):
-    """Child process (one thread): time the oracle and print one JSON line."""
+    """Child process: time the FP64 oracle on bounded samples (--sample-steps of
+    them, each on its own rows and sub-domains) and print one JSON line; with
+    --sample-out also store the first sample's oracle values (and the interiors
+    of its sub-domains).  This process never initialises CUDA, so its worker
+    pool may fork."""
+    import multiprocessing as mp
+
     import numpy as np
+    import oracle as O
     from synthetic import WORKLOADS, make_inputs
     w = WORKLOADS[args.workload]
     dt = np.float64 if args.precision == "fp64" else np.float32
     inp = make_inputs(w, dt)
-    cycle, sample = oracle_sample_time(w, inp, args.sample_rows, args.sample_subdomains)
-    print(json.dumps({"cycle_s": cycle, "sample": sample}))
+    workers = max(1, args.cpu_workers)
+    Xb = inp.Xb.T.astype(np.float64)
+    t0 = time.perf_counter()
+    U = O.anomalies(Xb)
+    t_anom = time.perf_counter() - t0
+    Ys = O.perturbed_observations(inp.y, inp.R, inp.Z.T)
+    g = O.Grid.from_workload(w)
+    sds = O.subdomains(g, w.sub_lon, w.sub_lat)
+    _CTX.update(g=g, sds=sds, U=U, Xb=Xb, Ys=Ys, inp=inp, w=w)
+    pool = mp.get_context("fork").Pool(workers) if workers > 1 else None
+    if pool:
+        pool.map(abs, range(4 * workers))              # every worker up before timing
+    run = pool.map if pool else lambda f, xs: [f(x) for x in xs]
+    cycles = []
+    for step in range(max(1, args.sample_steps)):
+        rows, picks = sample_plan(g.n, len(sds), args.sample_rows * workers,
+                                  args.sample_subdomains * workers, seed=step)
+        chunks = [rows[k::workers] for k in range(workers)]
+        t0 = time.perf_counter()
+        row_res = run(_oracle_rows, chunks)
+        t_rows = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        sd_res = run(_oracle_subdomain, picks)
+        t_sd = time.perf_counter() - t0
+        cycles.append(t_anom + t_rows * g.n / len(rows) + t_sd * len(sds) / len(picks))
+        if step == 0 and args.sample_out:
+            ref = sorted((r for _, part in row_res for r in part), key=lambda r: r[0])
+            width = max([len(r[1]) for r in ref] + [1])
+            np.savez(args.sample_out,
+                     rows=np.array([r[0] for r in ref], dtype=np.int64),
+                     P=np.array([r[1] + [-1] * (width - len(r[1])) for r in ref], dtype=np.int64),
+                     beta=np.array([list(r[2]) + [0.0] * (width - len(r[2])) for r in ref]),
+                     D=np.array([r[3] for r in ref]),
+                     sd=np.array([i for _, i, _ in sd_res], dtype=np.int64),
+                     **{f"Xa{i}": x for _, i, x in sd_res},
+                     **{f"int{i}": sds[i].interior for _, i, _ in sd_res})
+    if pool:
+        pool.close()
+        pool.join()
+    print(json.dumps({"cycle_s": cycles[0], "cycles_s": cycles, "workers": workers,
+                      "sample": f"{len(rows)} of {g.n} regressions + {len(picks)} of {len(sds)} "
+                                f"sub-domain analyses"}))
 
 
-def cpu_baseline(args):
+def run_cpu_sample(workload, precision, rows, subdomains, workers, out=None, steps=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
-           "--precision", args.precision, "--sample-rows", str(args.sample_rows),
-           "--sample-subdomains", str(args.sample_subdomains)]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
+           "--precision", precision, "--sample-rows", str(rows),
+           "--sample-subdomains", str(subdomains), "--cpu-workers", str(workers),
+           "--sample-steps", str(steps)]
+    if out:
+        cmd += ["--sample-out", out]
     p = subprocess.run(cmd, capture_output=True, text=True, env=env)
     if p.returncode != 0:
-        return {"error": p.stderr.strip().splitlines()[-1] if p.stderr.strip() else "failed"}
-    d = json.loads(p.stdout.strip().splitlines()[-1])
-    return {"value": 1.0 / d["cycle_s"], "unit": "cycles/s", "cores": 1, "kind": "oracle",
-            "sample": d["sample"] + " (FP64 numpy/scipy oracle, one thread; cycle time "
-                      "extrapolated to the full workload)"}
+        tail = p.stderr.strip().splitlines()
+        return {"error": tail[-1] if tail else "failed"}
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(args, out=None, workload=None):
+    """The FP64 oracle on the host cores: one thread and every core (one process
+    per core, each on its share of the sampled rows and one sub-domain), cycle
+    time extrapolated to the full workload.  `out`: where the all-cores leg
+    stores its oracle values (the accuracy reference)."""
+    workload = workload or args.workload
+    ncores = args.cpu_workers or os.cpu_count() or 1
+    one = run_cpu_sample(workload, args.precision, 4 * args.sample_rows,
+                         args.sample_subdomains, 1)
+    allc = run_cpu_sample(workload, args.precision, args.sample_rows, args.sample_subdomains,
+                          ncores, out)
+    res = {"unit": "cycles/s", "kind": "oracle", "cpu_model": cpu_model(),
+           "nproc": os.cpu_count()}
+    if "error" in allc or "error" in one:
+        res["error"] = allc.get("error") or one.get("error")
+        return res
+    res.update({"value": 1.0 / allc["cycle_s"], "cores": allc["workers"],
+                "sample": allc["sample"] + " per step, one process per core (FP64 numpy/scipy "
+                          "oracle, one thread each); cycle time extrapolated to the workload",
+                "single_thread": {"value": 1.0 / one["cycle_s"], "cores": 1,
+                                  "sample": one["sample"]}})
+    return res
+
+
+def accuracy_report(w, ref_path, Xb, T, D, Xa, handle):
+    """Max relative errors of the GPU outputs against the oracle values the CPU
+    baseline leg stored: T (off-diagonal, per variable), D (per variable and element
+    by element), and dX, X^a on the sampled sub-domains' interiors (per variable;
+    max |x - x_ref| / max |x_ref|)."""
+    import numpy as np
+    from synthetic import variable_of
+    d = np.load(ref_path)
+    rows = d["rows"]
+    dk, dy, dx = handle.slot_offsets()
+    # label of each stencil slot of each sampled row (ring longitude)
+    nvl = [w.var_levels(v) for v in range(w.nvar)]
+    var = variable_of(w, rows)
+    off = np.array([w.var_offset(v) for v in range(w.nvar)])
+    rem = rows - off[var]
+    k, rem = rem // (w.nlat * w.nlon), rem % (w.nlat * w.nlon)
+    y, x = rem // w.nlon, rem % w.nlon
+    kk, yy, xx = k[:, None] + dk[None], y[:, None] + dy[None], x[:, None] + dx[None]
+    ok = (kk >= 0) & (kk < np.array(nvl)[var][:, None]) & (yy >= 0) & (yy < w.nlat)
+    if w.lon_periodic:
+        xx = xx % w.nlon
+    else:
+        ok &= (xx >= 0) & (xx < w.nlon)
+    lab = off[var][:, None] + (kk * w.nlat + yy) * w.nlon + xx
+    Tg = T[rows].astype(np.float64)
+    Tr = np.zeros_like(Tg)
+    for a in range(len(rows)):
+        coef = {int(q): -b for q, b in zip(d["P"][a], d["beta"][a]) if q >= 0}
+        for s in range(len(dk)):
+            if ok[a, s]:
+                Tr[a, s] = coef.get(int(lab[a, s]), 0.0)
+
+    def per_var(got, ref, v):
+        worst = 0.0
+        for u in np.unique(v):
+            sel = v == u
+            den = np.abs(ref[sel]).max()
+            if den > 0:
+                worst = max(worst, float(np.abs(got[sel] - ref[sel]).max() / den))
+        return worst
+
+    Dg = D[rows].astype(np.float64)
+    out = {"T": per_var(Tg, Tr, var), "D": per_var(Dg, d["D"], var),
+           "D_elementwise": float(np.max(np.abs(Dg - d["D"]) / np.abs(d["D"])))}
+    eX = edX = 0.0
+    for i in d["sd"]:
+        lab_i = d[f"int{int(i)}"]
+        v = variable_of(w, lab_i)
+        ref = d[f"Xa{int(i)}"]
+        got = Xa[:, lab_i].T.astype(np.float64)
+        xb = Xb[:, lab_i].T.astype(np.float64)
+        eX = max(eX, per_var(got, ref, v))
+        edX = max(edX, per_var(got - xb, ref - xb, v))
+    out.update({"dX": edX, "Xa": eX,
+                "sample": f"{len(rows)} rows, sub-domains {[int(i) for i in d['sd']]}"})
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -190,32 +350,35 @@ def dist_env():
     return rank, world, local
 
 
-def roofline(prof, work, peaks, peak_src, sm_max_mhz, fp32, workload, precision):
+def alu_peak(fp32, sm_count, sm_max_mhz):
+    """(TFLOP/s, note) of the arithmetic pipe: FP32 FMA lanes at the maximum SM
+    clock, or the FP64 nominal rate."""
+    if fp32:
+        return (sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12,
+                f"FP32 FMA: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                f"{sm_max_mhz:.0f} MHz")
+    return FP64_NOMINAL_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
+
+
+def roofline(prof, work, peaks, peak_src, sm_max_mhz, fp32, workload, precision, sm_count):
     """Roofline of the dominant kernel (largest device time per cycle).
 
-    prof: kernel -> (launches, ms); work: kernel -> (flops, bytes) per launch.
-    The bound is the one whose time per launch is larger at its peak: FP32 FMA
-    lanes at the maximum SM clock (or FP64 nominal) for flops, the measured
-    copy bandwidth for bytes; achieved = the algorithmic work per launch over
-    the kernel's average launch time."""
+    prof: kind -> (calls, ms); work: kind -> (flops, bytes) per call.  The bound
+    is the one whose time per call is larger at its peak: the arithmetic pipe
+    (alu_peak) for flops, the measured copy bandwidth for bytes; achieved = the
+    algorithmic work per call over the kind's average call time."""
     dom = max(prof, key=lambda k: prof[k][1])
     launches, dom_ms = prof[dom]
     avg_s = dom_ms / max(1, launches) / 1e3
     flops, nbytes = work[dom]
     sm_max = sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
-    if fp32:
-        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        alu_note = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x "
-                    f"{sm_max:.0f} MHz")
-    else:
-        alu_peak = FP64_NOMINAL_TFLOPS
-        alu_note = "FP64 nominal 1.25 TFLOP/s"
-    t_alu = flops / (alu_peak * 1e12)
+    apeak, anote = alu_peak(fp32, sm_count, sm_max)
+    t_alu = flops / (apeak * 1e12)
     t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
     if t_alu >= t_hbm:
         achieved = flops / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "peak_source": f"derived: {alu_note}"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": apeak, "unit": "TFLOP/s",
+                "frac": achieved / apeak, "peak_source": f"derived: {anote}"}
     else:
         achieved = nbytes / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -225,6 +388,32 @@ def roofline(prof, work, peaks, peak_src, sm_max_mhz, fp32, workload, precision)
     roof["avg_launch_ms"] = avg_s * 1e3
     roof["algorithmic_per_launch"] = {"flops": flops, "bytes": nbytes}
     return roof
+
+
+def path_roofline(prof, work, peaks, sm_max_mhz, fp32, sm_count, steps, tensor_kinds):
+    """Sum over kernel kinds of the roofline time (calls x max(flops / pipe peak,
+    bytes / HBM peak)) against the measured time of the same calls, per step.
+    The pipe of `tensor_kinds` (band Cholesky and solves on the tensor cores) is
+    the TF32 rate (half the measured bf16 rate) over 3, the products per
+    FP32-accurate product of their split operands; every other kind's is
+    alu_peak."""
+    sm_max = sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
+    apeak, _ = alu_peak(fp32, sm_count, sm_max)
+    tpeak = peaks.get("bf16_tflops", 1900.0) / 2.0 / 3.0
+    per, t_roof, t_meas = {}, 0.0, 0.0
+    for k, (calls, ms) in prof.items():
+        if not calls:
+            continue
+        flops, nbytes = work[k]
+        pipe = tpeak if k in tensor_kinds else apeak
+        rf = calls * max(flops / (pipe * 1e12), nbytes / (peaks["hbm_gbs"] * 1e9)) * 1e3 / steps
+        per[k] = {"ms": ms / steps, "roofline_ms": rf,
+                  "frac": rf / (ms / steps) if ms > 0 else None}
+        t_roof += rf
+        t_meas += ms / steps
+    return {"path_frac": t_roof / t_meas if t_meas > 0 else None,
+            "roofline_ms_per_step": t_roof, "measured_ms_per_step": t_meas,
+            "tensor_peak_tflops": tpeak, "alu_peak_tflops": apeak, "per_kernel": per}
 
 
 def workload_config(args, w, world):
@@ -263,32 +452,27 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
-    from synthetic import WORKLOADS, make_inputs
+    from synthetic import WORKLOADS
     w = WORKLOADS[args.workload]
-    inp = make_inputs(w, np.float64 if args.precision == "fp64" else np.float32)
-    cyc = []
-    sample = ""
-    for s in range(args.warmup + args.steps):
-        c, sample = oracle_sample_time(w, inp, 200, 1, seed=s)
-        if s >= args.warmup:
-            cyc.append(c)
+    ncores = args.cpu_workers or os.cpu_count() or 1
+    d = run_cpu_sample(args.workload, args.precision, 40, 1, ncores,
+                       steps=args.warmup + args.steps)
+    if "error" in d:
+        print(json.dumps({"impl": "reference", "unavailable": d["error"]}))
+        return
+    sample = d["sample"]
+    cyc = d["cycles_s"][args.warmup:]
     mean_cycle = sum(cyc) / len(cyc)
     value = 1.0 / mean_cycle
-    cores = 1
-    try:
-        import threadpoolctl  # noqa: F401
-        cores = max(i["num_threads"] for i in threadpoolctl.threadpool_info()) if \
-            threadpoolctl.threadpool_info() else 1
-    except Exception:
-        cores = os.cpu_count() or 1
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cycles/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": mean_cycle * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": workload_config(args, w, 1),
-           "cpu_baseline": {"value": value, "unit": "cycles/s", "cores": cores, "kind": "oracle",
-                            "sample": "per step: " + sample + "; cycle time extrapolated"},
+           "cpu_baseline": {"value": value, "unit": "cycles/s", "cores": ncores, "kind": "oracle",
+                            "cpu_model": cpu_model(),
+                            "sample": "per step: " + sample + ", one process per core; cycle "
+                                      "time extrapolated"},
            "e2e": {"value": value, "unit": "cycles/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -309,7 +493,7 @@ def _time_steps(step, warmup, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def fwd_adj_line(wa, ia, dev, npdt, precision, tdt):
+def fwd_adj_line(args, wa, ia, dev, npdt, precision, tdt, accuracy=False):
     """Forward analysis and forward + adjoint (loss 1/2 |mean(X^a) - x_ref|^2,
     dL/dX^a formed on the device, enkfmc_analyze_adjoint) on workload wa."""
     import numpy as np
@@ -350,11 +534,29 @@ def fwd_adj_line(wa, ia, dev, npdt, precision, tdt):
     prof = h.profile_read()
     h.profile(False)
     h.check("forward + adjoint steps")
-    h.close()
-    return {"workload": wa.name, "precision": "fp32" if precision == B.FP32 else "fp64",
+    peaks, _ = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    tk = {k for k, on in (("bandchol", h.info.tc_chol), ("bandsolve", h.info.tc_solve)) if on}
+    path = path_roofline(prof, h.work_per_launch(), peaks, None, precision == B.FP32, sm_count,
+                         2, tk)
+    line = {"workload": wa.name, "precision": "fp32" if precision == B.FP32 else "fp64",
             "fwd_cycles_per_s": 1e3 / ms_f, "fwd_adj_cycles_per_s": 1e3 / ms_fa,
             "fwd_ms": ms_f, "fwd_adj_ms": ms_fa, "adj_over_fwd": (ms_fa - ms_f) / ms_f,
+            "refine_steps": h.info.refine_steps, "fp64_rows": bool(h.info.fp64_rows),
+            "path_frac_fwd_adj": path["path_frac"],
             "kernels_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}}
+    if accuracy and not args.no_cpu_baseline:
+        fwd()
+        torch.cuda.synchronize()
+        ref = tempfile.mktemp(suffix=".npz")
+        cb = cpu_baseline(args, out=ref, workload=wa.name)
+        line["cpu_baseline"] = cb
+        if os.path.exists(ref):
+            line["accuracy"] = accuracy_report(wa, ref, ia.Xb, T.cpu().numpy(), D.cpu().numpy(),
+                                               Xa.cpu().numpy(), h)
+            os.unlink(ref)
+    h.close()
+    return line
 
 
 def side_measurements(args, w, inp, value, dev):
@@ -362,8 +564,9 @@ def side_measurements(args, w, inp, value, dev):
     FP64 form of the same workload (cycles/s and the FP32 speed-up over it);
     forward + adjoint (the loss L = 1/2 |mean(X^a) - x_ref|^2, its gradient
     dL/dX^a formed on the device, then enkfmc_analyze_adjoint for X^b, y and
-    diag(R)) against the forward analysis alone, on the same workload in FP32
-    and at the T63 shape with N = 40 in FP64."""
+    diag(R)) against the forward analysis alone, on the same workload and at
+    the T63 shape with N = 40, in FP32 (with its accuracy against the oracle)
+    and in FP64 (the plain form)."""
     import numpy as np
     import torch
 
@@ -393,15 +596,18 @@ def side_measurements(args, w, inp, value, dev):
     del Xb, y, R, Z, T, D, Xa
     out["plain_fp64"] = {"workload": w.name, "value": 1e3 / ms, "unit": "cycles/s",
                          "ms_per_step": ms, "fp32_over_fp64": value / (1e3 / ms)}
-
-    out["fwd_adj_fp32"] = fwd_adj_line(w, inp, dev, np.float32, B.FP32, torch.float32)
-
-    # forward + adjoint, T63 shape with N = 40: p = 37 predecessors from 40
-    # members make the Gram matrices nearly singular, so this configuration runs
-    # in FP64 (single precision reports EDNONPOS here)
-    wa = WORKLOADS["t63_192x96x29_n40_r2"]
-    out["fwd_adj"] = fwd_adj_line(wa, make_inputs(wa, np.float64), dev, np.float64, B.FP64,
-                                  torch.float64)
+    out["fwd_adj_fp32"] = fwd_adj_line(args, w, inp, dev, np.float32, B.FP32, torch.float32)
+    # forward + adjoint at the T63 shape with N = 40 (p = 37 predecessors from
+    # 40 members on interior rows): FP32 with the double-precision rows and four
+    # refinement steps, against the plain FP64 form
+    wa = WORKLOADS[ADJ_WORKLOAD]
+    out["fwd_adj"] = fwd_adj_line(args, wa, make_inputs(wa, np.float32), dev, np.float32, B.FP32,
+                                  torch.float32, accuracy=True)
+    line64 = fwd_adj_line(args, wa, make_inputs(wa, np.float64), dev, np.float64, B.FP64,
+                          torch.float64)
+    out["fwd_adj_plain_fp64"] = line64
+    out["fwd_adj"]["fp32_over_fp64"] = (out["fwd_adj"]["fwd_adj_cycles_per_s"] /
+                                        line64["fwd_adj_cycles_per_s"])
     return out
 
 
@@ -420,6 +626,7 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     w = rank_workload(WORKLOADS[args.workload], rank)
     precision = B.FP64 if args.precision == "fp64" else B.FP32
     npdt = np.float64 if precision == B.FP64 else np.float32
@@ -445,7 +652,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     h.check("warm-up")
-    h.profile(True)
+    h.profile(False)
     h.profile_read()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -464,17 +671,35 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    prof = h.profile_read()
-    h.profile(False)
+    counts = h.profile_read(kernels=True)            # kernels launched in the timed steps
     h.check("timed steps")
     t_max = slowest_rank(ms, world, dev)
     value = job_rate(args.steps, world, t_max / 1e3)
 
-    # roofline of the dominant kernel
+    # second timed pass with the per-kernel events on: split, roofline, path fraction
+    h.profile(True)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.profile_steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof = h.profile_read()
+    h.profile(False)
+    ms_prof = p0.elapsed_time(p1) / args.profile_steps
     peaks, peak_src = _peaks()
-    roof = roofline(prof, h.work_per_launch(), peaks, peak_src,
-                    (clocks or {}).get("sm_max_mhz"), precision == B.FP32, args.workload,
-                    args.precision)
+    work = h.work_per_launch()
+    sm_max = (clocks or {}).get("sm_max_mhz")
+    roof = roofline(prof, work, peaks, peak_src, sm_max, precision == B.FP32, args.workload,
+                    args.precision, sm_count)
+    tk = {k for k, on in (("bandchol", h.info.tc_chol), ("bandsolve", h.info.tc_solve)) if on}
+    path = path_roofline(prof, work, peaks, sm_max, precision == B.FP32, sm_count,
+                         args.profile_steps, tk)
+    roof["path_frac"] = path["path_frac"]
+    roof["timed_region"] = (f"{args.profile_steps} steps after the headline steps, per-kernel "
+                            f"events on ({ms_prof:.2f} ms per step)")
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -495,9 +720,17 @@ def run_ours(args):
                "d2h_bytes_per_step": esize * w.N * w.n,
                "api": "enkfmc_cycle_host"}
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+        step()
+        h.check("accuracy step")
+        torch.cuda.synchronize()
+        ref = tempfile.mktemp(suffix=".npz")
+        cpu = cpu_baseline(args, out=ref)
+        if os.path.exists(ref):
+            accuracy = accuracy_report(w, ref, inp.Xb, T.cpu().numpy(), D.cpu().numpy(),
+                                       Xa.cpu().numpy(), h)
+            os.unlink(ref)
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         try:
@@ -512,9 +745,10 @@ def run_ours(args):
                "dtype": "f64" if precision == B.FP64 else "f32", "data": "synthetic",
                "config": workload_config(args, w, world),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": int(sum(v[0] for v in prof.values())),
-               "clocks": clocks,
-               "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
+               "gpu_launches": int(sum(v[1] for v in counts.values())),
+               "clocks": clocks, "sm_count": sm_count, "accuracy": accuracy,
+               "path_roofline": path,
+               "kernels_ms_per_step": {k: v[1] / args.profile_steps for k, v in prof.items()}}
         out.update(extras)
         print(json.dumps(out))
     h.close()

@@ -69,13 +69,23 @@ typedef enum {
                             whose residuals are accumulated in compensated
                             (double-float) arithmetic: one per regression
                             (corrected semi-normal equations) and one per
-                            sub-domain solve (Eq. 11)                             */
+                            sub-domain solve (Eq. 11).  Rows with more
+                            predecessors than half the members (2p > N, nearly
+                            singular Gram matrices) are regressed in double
+                            precision from FP64 anomalies and FP64 covariances
+                            of the single-precision ensemble; their T and D are
+                            stored in single precision like every other row    */
 } enkfmc_precision;
 
 /* enkfmc_problem.flags */
 enum {
   ENKFMC_FLAG_NO_SOLVE_REFINEMENT = 1, /* FP32: skip the sub-domain refinement step
                                           (the plain single-precision solve)      */
+  ENKFMC_FLAG_REFINE_MASK = 0xF00,     /* FP32: bits 8-11 (ENKFMC_FLAG_REFINE_STEPS(k))
+                                          = refinement steps of every sub-domain
+                                          solve, 1-15; 0 = one step, or four when
+                                          some row has 2p > N (ill-conditioned A);
+                                          the reverse pass refines its solve alike */
   ENKFMC_FLAG_SIMT_BAND = 2            /* FP32: take the band Cholesky and the band
                                           solves on the CUDA cores only.  By
                                           default their rank-32 panel updates run
@@ -88,6 +98,8 @@ enum {
                                           the CUDA cores                           */
 };
 
+#define ENKFMC_FLAG_REFINE_STEPS(k) ((int32_t)(k) << 8)
+
 /* Problem description.  Neighbours of a component share its variable, lie
  * within `vert_reach` levels and within Chebyshev distance r on the
  * (lat, lon) grid, longitude taken on the ring when lon_periodic != 0
@@ -95,7 +107,9 @@ enum {
  * a smaller label (Section 2.3, Fig. 2).  Sub-domains are sub_lat x sub_lon
  * column tiles from (0, 0), the last ones ragged, extended by r columns on
  * every side (clipped at the poles, wrapped in longitude) (Section 3).
- * Requirements: nlon >= 2r+1 when lon_periodic, N >= 2, nvar_3d + nvar_2d <= 16.
+ * Requirements: nlon >= 2r+1 when lon_periodic, 2 <= N <= 128,
+ * nvar_3d + nvar_2d <= 16, r <= 16, fewer than 2^31 components, at most 255
+ * stencil slots per row (pmax).
  * An extended sub-domain as wide as the ring covers it exactly once.  */
 typedef struct {
   int32_t nlon, nlat, nlev, nvar_3d, nvar_2d;
@@ -121,6 +135,10 @@ typedef struct {
   int64_t band_elems;    /* stored band entries of all blocks of A                */
   int64_t workspace_bytes;
   int64_t m;             /* observations set by enkfmc_set_observations (or -1)   */
+  int32_t tc_chol;       /* 1: band Cholesky updates on the tensor cores          */
+  int32_t tc_solve;      /* 1: band solve panel updates on the tensor cores       */
+  int32_t refine_steps;  /* refinement steps of every sub-domain solve            */
+  int32_t fp64_rows;     /* 1: rows with 2p > N regressed in double precision     */
 } enkfmc_info;
 
 typedef struct enkfmc_handle enkfmc_handle;
@@ -220,19 +238,22 @@ enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_
  * `cuda_stream`, without a handle and without allocating anything: its only
  * scratch is one fixed 16 MiB device array inside the library (present on
  * every GPU that loads the library until the process exits).
- *   - Limit: 256 + n * (ldN + nC) * sizeof(element) bytes must fit in 16 MiB
- *     (ldN = N rounded up to a multiple of 4; nC = ((2 vr + 1)(4r + 1)^2 + 1) / 2
- *     pair covariances per component, vr = min(vert_reach, nlev - 1)); larger
- *     problems return ENKFMC_EINVAL before any work is queued.
+ *   - Limit: n * (ldN + nC) * sizeof(element) bytes, plus n * (ldN + nC) * 8
+ *     for a single-precision problem with rows where 2p > N (2 pmax > N),
+ *     each part rounded up to 256 bytes, must fit in 16 MiB (ldN = N rounded
+ *     up to a multiple of 4; nC = ((2 vr + 1)(4r + 1)^2 + 1) / 2 pair
+ *     covariances per component, vr = min(vert_reach, nlev - 1)).  Larger
+ *     problems, and every problem enkfmc_create would refuse as unsupported,
+ *     return ENKFMC_EINVAL before anything is queued on the stream.
  *   - The first call on a device looks up the array's device address with
  *     that device current (cudaGetSymbolAddress); make that first call
  *     before any stream capture.
- *   - Every call reuses the same array and leaves its contents behind; the
- *     status word is cleared at the start of each call.  Calls that overlap
- *     on the GPU (different streams, or concurrent host threads) race on the
- *     array: serialise them.
+ *   - Every call reuses the same array and leaves its contents behind; each
+ *     call writes every scratch byte it reads before reading it, so nothing
+ *     carries over.  Calls that overlap on the GPU (different streams, or
+ *     concurrent host threads) race on the array: serialise them.
  *   - Numerical failures are not reported through a status here: the rows
- *     concerned get D = NaN and a zero T row.
+ *     concerned get D = NaN and a zero T row (test D for NaN).
  * Pointers are device pointers owned by the caller.  Asynchronous. */
 enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const void* Xb, void* Tvals,
                                       void* D, void* cuda_stream);
@@ -255,16 +276,20 @@ enum {
   ENKFMC_NKERNEL = 12
 };
 
-/* Kernel timing.  While enabled, every kernel launch is bracketed by CUDA
- * events recorded on the handle's stream (the stream the kernel runs on).
- * enkfmc_profile_read synchronises and returns, per kernel kind, the launches
- * and the summed device time (ms) since the previous read, then resets.
- * launches, ms: host arrays of ENKFMC_NKERNEL. */
+/* Kernel timing.  Work is launched in calls of one kernel kind; a call runs
+ * one or more CUDA kernels (the FP32 and FP64 rows of the regressions, the
+ * two passes of the refinement residual).  While enabled, every call is
+ * bracketed by CUDA events recorded on the handle's stream (the stream its
+ * kernels run on).  enkfmc_profile_read synchronises and returns, per kind,
+ * the calls and the kernels since the previous read (counted whether or not
+ * timing is enabled) and the device time (ms) summed while enabled, then
+ * resets.  calls, kernels, ms: host arrays of ENKFMC_NKERNEL. */
 enkfmc_status enkfmc_profile(enkfmc_handle* h, int32_t enable);
-enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* launches, double* ms);
+enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* calls, int64_t* kernels,
+                                  double* ms);
 const char* enkfmc_kernel_name(int32_t kind);
 
-/* Algorithmic work of one launch of each kernel kind for this problem:
+/* Algorithmic work of one call of each kernel kind for this problem:
  * floating-point operations of the method (a multiply-add counts 2) and the
  * bytes a kernel must move to or from memory at least (inputs read once,
  * outputs written once).  Implementation extras (refinement passes, re-reads)

@@ -32,7 +32,9 @@ class enkfmc_problem(ctypes.Structure):
 class enkfmc_info(ctypes.Structure):
     _fields_ = [("n", c_int64), ("pmax", c_int32), ("nsub", c_int32), ("nblock", c_int32),
                 ("hb_max", c_int32), ("ext_rows", c_int64), ("halo_rows", c_int64),
-                ("band_elems", c_int64), ("workspace_bytes", c_int64), ("m", c_int64)]
+                ("band_elems", c_int64), ("workspace_bytes", c_int64), ("m", c_int64),
+                ("tc_chol", c_int32), ("tc_solve", c_int32), ("refine_steps", c_int32),
+                ("fp64_rows", c_int32)]
 
 
 _H = c_void_p
@@ -55,7 +57,7 @@ SIGNATURES = {
     "enkfmc_debug_block": (c_int32, [_H, c_int32, c_void_p, c_int64, POINTER(c_int64),
                                      POINTER(c_int32)]),
     "enkfmc_profile": (c_int32, [_H, c_int32]),
-    "enkfmc_profile_read": (c_int32, [_H, c_void_p, c_void_p]),
+    "enkfmc_profile_read": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
     "enkfmc_kernel_name": (c_char_p, [c_int32]),
     "enkfmc_work_per_launch": (c_int32, [_H, c_void_p, c_void_p]),
     "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
@@ -64,6 +66,12 @@ SIGNATURES = {
 NKERNEL = 12
 FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
+FLAG_REFINE_MASK = 0xF00
+
+
+def flag_refine_steps(k: int) -> int:
+    """ENKFMC_FLAG_REFINE_STEPS(k): k refinement steps of every sub-domain solve."""
+    return (int(k) & 0xF) << 8
 
 _LIB = None
 
@@ -210,13 +218,18 @@ class Handle:
     def profile(self, enable: bool):
         _check(self.lib.enkfmc_profile(self.h, int(bool(enable))), "enkfmc_profile")
 
-    def profile_read(self):
-        """{kernel name: (launches, total ms)} since the previous read."""
+    def profile_read(self, kernels: bool = False):
+        """{kind: (calls, total ms)} since the previous read; with kernels=True
+        {kind: (calls, CUDA kernels, total ms)}."""
         n = np.zeros(NKERNEL, np.int64)
+        nk = np.zeros(NKERNEL, np.int64)
         ms = np.zeros(NKERNEL, np.float64)
-        _check(self.lib.enkfmc_profile_read(self.h, _ptr(n), _ptr(ms)), "enkfmc_profile_read")
-        return {self.lib.enkfmc_kernel_name(k).decode(): (int(n[k]), float(ms[k]))
-                for k in range(NKERNEL)}
+        _check(self.lib.enkfmc_profile_read(self.h, _ptr(n), _ptr(nk), _ptr(ms)),
+               "enkfmc_profile_read")
+        names = [self.lib.enkfmc_kernel_name(k).decode() for k in range(NKERNEL)]
+        if kernels:
+            return {names[k]: (int(n[k]), int(nk[k]), float(ms[k])) for k in range(NKERNEL)}
+        return {names[k]: (int(n[k]), float(ms[k])) for k in range(NKERNEL)}
 
     def work_per_launch(self):
         """{kernel name: (algorithmic flops, algorithmic bytes)} per launch."""

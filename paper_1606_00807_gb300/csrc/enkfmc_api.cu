@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "enkfmc_internal.h"
@@ -69,8 +70,11 @@ int block_bandwidth(const Geom& g, const Block& b) {
 void compute_work(enkfmc_handle* h, const std::vector<int>& p_global,
                   const std::vector<int>& p_ext);
 
-enkfmc_status build(enkfmc_handle* h) {
-  const enkfmc_problem& p = h->prob;
+}  // namespace
+
+namespace enkfmc {
+
+enkfmc_status problem_geom(const enkfmc_problem& p, Geom& g) {
   const int nvar = p.nvar_3d + p.nvar_2d;
   if (p.nlon < 1 || p.nlat < 1 || p.nlev < 1 || p.nvar_3d < 0 || p.nvar_2d < 0 || nvar < 1 ||
       nvar > kMaxVar || p.r < 0 || p.vert_reach < 0 || p.N < 2 || p.N > 128 || p.sub_lon < 1 ||
@@ -78,8 +82,10 @@ enkfmc_status build(enkfmc_handle* h) {
     return ENKFMC_EINVAL;
   if (p.precision != ENKFMC_FP64 && p.precision != ENKFMC_FP32) return ENKFMC_EINVAL;
   if (p.lon_periodic && p.nlon < 2 * p.r + 1) return ENKFMC_EINVAL;
-  if (p.flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_BAND)) return ENKFMC_EINVAL;
-  Geom& g = h->g;
+  // every extent and product below 2^31 components before the label arithmetic
+  // (32-bit labels in the kernels) and any buffer size is formed
+  const int64_t lim = ((int64_t)1 << 31) - 1;
+  if ((int64_t)p.nlon * p.nlat > lim || (int64_t)p.nlon * p.nlat * p.nlev > lim) return ENKFMC_EINVAL;
   std::memset(&g, 0, sizeof(g));
   g.nlon = p.nlon;
   g.nlat = p.nlat;
@@ -92,18 +98,45 @@ enkfmc_status build(enkfmc_handle* h) {
   g.periodic = p.lon_periodic ? 1 : 0;
   g.N = p.N;
   g.ldN = (p.N + 3) / 4 * 4;
+  // at most 255 stencil slots (checked again by estimate_supported): bounds vr
+  // before slot_count multiplies it
+  if ((int64_t)g.vr * (2 * g.r + 1) * (2 * g.r + 1) > 255) return ENKFMC_EINVAL;
   g.pmax = slot_count(g.r, g.vr, g.periodic);
   int64_t off = 0;
   for (int v = 0; v < nvar; ++v) {
     g.var_off[v] = off;
     g.var_lev[v] = v < p.nvar_3d ? p.nlev : 1;
     off += (int64_t)g.var_lev[v] * p.nlat * p.nlon;
+    if (off > lim) return ENKFMC_EINVAL;
   }
   g.var_off[nvar] = off;
   g.n = off;
-  if (g.n > ((int64_t)1 << 31) - 1) return ENKFMC_EINVAL;
+  if (!estimate_supported(g, p.precision != ENKFMC_FP64)) return ENKFMC_EINVAL;
+  return ENKFMC_OK;
+}
+
+}  // namespace enkfmc
+
+namespace {
+
+enkfmc_status build(enkfmc_handle* h) {
+  const enkfmc_problem& p = h->prob;
+  if (p.flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_BAND |
+                  ENKFMC_FLAG_REFINE_MASK))
+    return ENKFMC_EINVAL;
+  Geom& g = h->g;
+  enkfmc_status gst = problem_geom(p, g);
+  if (gst) return gst;
+  const int nvar = g.nvar;
   h->esize = is_fp64(h) ? sizeof(double) : sizeof(float);
   h->refine_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_NO_SOLVE_REFINEMENT);
+  if (h->refine_solve) {
+    // one step, or four where the regressions are nearly singular (2p > N): the
+    // small residual variances D_j make A ill-conditioned there (condition
+    // numbers near 1e8 at N = 40, r = 2), and each step gains about one digit
+    const int req = (p.flags & ENKFMC_FLAG_REFINE_MASK) >> 8;
+    h->refine_steps = req ? req : (has_fp64_rows(g, true) ? 4 : 1);
+  }
 
   // sub-domains and blocks (Section 3, Fig. 3)
   h->nsuby = (p.nlat + p.sub_lat - 1) / p.sub_lat;
@@ -271,6 +304,11 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_invdiag, h->esize * h->ext_rows))) return st;
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
   if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
+  if (has_fp64_rows(g, !is_fp64(h))) {
+    if ((st = dalloc(h, &h->d_U64, sizeof(double) * g.n * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_C64, sizeof(double) * (size_t)g.n * cov_offset_count(g.r, g.vr))))
+      return st;
+  }
   if (h->refine_solve) {
     if ((st = dalloc(h, &h->d_res, h->esize * h->ext_rows * g.N))) return st;
     if ((st = dalloc(h, &h->d_vhi, h->esize * h->ext_rows * g.N))) return st;
@@ -328,7 +366,7 @@ void release(enkfmc_handle* h) {
                   h->d_band,  h->d_invdiag, h->d_rhs, h->d_res,     h->d_vhi,    h->d_vlo,
                   h->d_Xb,    h->d_y,       h->d_R,   h->d_Z,       h->d_Xa,     h->d_T,
                   h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
-                  h->d_Ubar};
+                  h->d_Ubar,  h->d_U64,     h->d_C64, h->d_W};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
@@ -352,23 +390,40 @@ cudaEvent_t pooled_event(enkfmc_handle* h) {
   return h->pool[h->pool_used++];
 }
 
-// Launch one kernel; while profiling, bracket it with events on the stream.
+// Run one launcher: a callable taking int* (it adds the kernels it launched)
+// or a callable without arguments (one kernel).  The launches are counted per
+// kind; while profiling they are bracketed with events on the stream.
 template <class F>
 enkfmc_status timed(enkfmc_handle* h, int kind, F&& launch) {
-  if (!h->prof) return check_launch(launch());
+  int nk = 0;
+  auto call = [&]() -> cudaError_t {
+    if constexpr (std::is_invocable<F, int*>::value) {
+      return launch(&nk);
+    } else {
+      nk = 1;
+      return launch();
+    }
+  };
+  if (!h->prof) {
+    const enkfmc_status st = check_launch(call());
+    h->calls[kind] += 1;
+    h->kernels[kind] += nk;
+    return st;
+  }
   cudaEvent_t a = pooled_event(h), b = pooled_event(h);
   if (!a || !b) return ENKFMC_ECUDA;
   cudaEventRecord(a, h->stream);
-  enkfmc_status st = check_launch(launch());
+  enkfmc_status st = check_launch(call());
   cudaEventRecord(b, h->stream);
+  h->calls[kind] += 1;
+  h->kernels[kind] += nk;
   h->recs.push_back({kind, a, b});
   return st;
 }
 
 template <typename T>
-enkfmc_status run_anomalies(enkfmc_handle* h, const T* Xb) {
-  return timed(h, ENKFMC_K_ANOMALIES,
-               [&] { return launch_anomalies<T>(h->g, Xb, (T*)h->d_U, h->stream); });
+EstStats<T> stats_of(enkfmc_handle* h) {
+  return {(T*)h->d_U, (T*)h->d_C, h->d_U64, h->d_C64};
 }
 
 // Anomalies and covariance table of Xb (skipped when already computed from it).
@@ -376,10 +431,13 @@ template <typename T>
 enkfmc_status run_statistics(enkfmc_handle* h, const T* Xb) {
   if (h->U_src == Xb) return ENKFMC_OK;
   h->U_src = nullptr;
-  enkfmc_status st = run_anomalies<T>(h, Xb);
+  const EstStats<T> sts = stats_of<T>(h);
+  enkfmc_status st = timed(h, ENKFMC_K_ANOMALIES, [&](int* nk) {
+    return launch_stat_anomalies<T>(h->g, Xb, sts, h->stream, nk);
+  });
   if (st) return st;
-  st = timed(h, ENKFMC_K_COVTABLE, [&] {
-    return launch_covtable<T>(h->g, (const T*)h->d_U, (T*)h->d_C, h->stream);
+  st = timed(h, ENKFMC_K_COVTABLE, [&](int* nk) {
+    return launch_stat_covtables<T>(h->g, sts, h->stream, nk);
   });
   if (st) return st;
   h->U_src = Xb;
@@ -391,18 +449,18 @@ enkfmc_status run_estimate(enkfmc_handle* h, const T* Xb, T* Tv, T* D) {
   h->U_src = nullptr;  // a new estimate always recomputes the statistics
   enkfmc_status st = run_statistics<T>(h, Xb);
   if (st) return st;
-  return timed(h, ENKFMC_K_REGRESS, [&] {
-    return launch_regress<T>(h->g, (const T*)h->d_U, (const T*)h->d_C, nullptr, h->g.n,
-                             h->d_blocks, Tv, D, h->prob.ridge_c, h->d_status, h->stream);
+  return timed(h, ENKFMC_K_REGRESS, [&](int* nk) {
+    return launch_regressions<T>(h->g, stats_of<T>(h), nullptr, h->g.n, h->d_blocks, Tv, D,
+                                 h->prob.ridge_c, h->d_status, h->stream, nk);
   });
 }
 
 template <typename T>
 enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R) {
-  enkfmc_status st = timed(h, ENKFMC_K_REGRESS_HALO, [&] {
-    return launch_regress<T>(h->g, (const T*)h->d_U, (const T*)h->d_C, h->d_halo, h->halo_rows,
-                             h->d_blocks, (T*)h->d_Te, (T*)h->d_De, h->prob.ridge_c,
-                             h->d_status, h->stream);
+  enkfmc_status st = timed(h, ENKFMC_K_REGRESS_HALO, [&](int* nk) {
+    return launch_regressions<T>(h->g, stats_of<T>(h), h->d_halo, h->halo_rows, h->d_blocks,
+                                 (T*)h->d_Te, (T*)h->d_De, h->prob.ridge_c, h->d_status,
+                                 h->stream, nk);
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_ASSEMBLE, [&] {
@@ -450,19 +508,29 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
   if (st) return st;
   const T* corr = nullptr;
   if (h->refine_solve && sizeof(T) == sizeof(float)) {
-    st = timed(h, ENKFMC_K_RESIDUAL, [&] {
-      return launch_refine_residual(
-          h->g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m, (const float*)Xb,
-          (const float*)y, (const float*)R, (const float*)Z, (const float*)h->T_assembled,
-          (const float*)h->D_assembled, (const float*)h->d_Te, (const float*)h->d_De,
-          (const float*)h->d_rhs, (float*)h->d_vhi, (float*)h->d_vlo, (float*)h->d_res,
-          h->stream);
-    });
-    if (st) return st;
-    st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-      return solve_band<T>(h, (T*)h->d_res);
-    });
-    if (st) return st;
+    for (int step = 0; step < h->refine_steps; ++step) {
+      st = timed(h, ENKFMC_K_RESIDUAL, [&](int* nk) {
+        cudaError_t e = cudaSuccess;
+        if (step > 0) {  // fold the previous correction into dX
+          ++*nk;
+          e = launch_accumulate((float*)h->d_rhs, (const float*)h->d_res,
+                                h->ext_rows * (int64_t)h->g.N, h->stream);
+          if (e != cudaSuccess) return e;
+        }
+        *nk += 2;  // k_whiten, k_residual
+        return launch_refine_residual(
+            h->g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m, (const float*)Xb,
+            (const float*)y, (const float*)R, (const float*)Z, (const float*)h->T_assembled,
+            (const float*)h->D_assembled, (const float*)h->d_Te, (const float*)h->d_De,
+            (const float*)h->d_rhs, (float*)h->d_vhi, (float*)h->d_vlo, nullptr,
+            (float*)h->d_res, h->stream);
+      });
+      if (st) return st;
+      st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
+        return solve_band<T>(h, (T*)h->d_res);
+      });
+      if (st) return st;
+    }
     corr = (const T*)h->d_res;
   }
   return timed(h, ENKFMC_K_WRITEBACK, [&] {
@@ -565,6 +633,9 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
     if ((st = dalloc(h, &h->d_dxT, es * rows * g.ldN))) return st;
     if ((st = dalloc(h, &h->d_lamT, es * rows * g.ldN))) return st;
     if ((st = dalloc(h, &h->d_Ubar, es * (size_t)g.n * g.ldN))) return st;
+    if (h->refine_solve && sizeof(T) == sizeof(float)) {
+      if ((st = dalloc(h, &h->d_W, es * rows * g.N * 2))) return st;  // W, then residuals
+    }
   }
   CUDA_TRY(cudaMemsetAsync(h->d_Ubar, 0, es * (size_t)g.n * g.ldN, h->stream));
   CUDA_TRY(cudaMemsetAsync(Xb_bar, 0, es * (size_t)g.n * g.N, h->stream));
@@ -580,10 +651,35 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
                               h->stream);
   });
   if (st) return st;
+  const bool refine = h->refine_solve && sizeof(T) == sizeof(float);
+  const int64_t nrhs = h->ext_rows * (int64_t)g.N;
+  T* W = refine ? (T*)h->d_W : nullptr;
+  T* Wres = refine ? (T*)h->d_W + nrhs : nullptr;
+  if (refine)
+    CUDA_TRY(cudaMemcpyAsync(W, h->d_lam, sizeof(T) * nrhs, cudaMemcpyDeviceToDevice, h->stream));
   st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
     return solve_band<T>(h, (T*)h->d_lam);
   });
   if (st) return st;
+  // Lambda = A^-1 W refined with the forward solve's steps (A is the same)
+  for (int step = 0; refine && step < h->refine_steps; ++step) {
+    st = timed(h, ENKFMC_K_RESIDUAL, [&](int* nk) {
+      *nk += 2;
+      return launch_refine_residual(
+          g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m, (const float*)h->last_Xb,
+          (const float*)h->last_y, (const float*)h->last_R, (const float*)h->last_Z,
+          (const float*)Tg, (const float*)Dg, (const float*)h->d_Te, (const float*)h->d_De,
+          (const float*)h->d_lam, (float*)h->d_vhi, (float*)h->d_vlo, (const float*)W,
+          (float*)Wres, h->stream);
+    });
+    if (st) return st;
+    st = timed(h, ENKFMC_K_BANDSOLVE, [&] { return solve_band<T>(h, Wres); });
+    if (st) return st;
+    st = timed(h, ENKFMC_K_RESIDUAL, [&] {
+      return launch_accumulate((float*)h->d_lam, (const float*)Wres, nrhs, h->stream);
+    });
+    if (st) return st;
+  }
   if (h->m > 0) {
     st = timed(h, ENKFMC_K_ADJOINT, [&] {
       return launch_adj_obs<T>(g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m,
@@ -599,12 +695,12 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
                             (T*)h->d_bT, (T*)h->d_dxT, (T*)h->d_lamT, h->stream);
   });
   if (st) return st;
-  st = timed(h, ENKFMC_K_ADJ_REGRESS, [&] {
-    return launch_adj_regress<T>(g, h->d_blocks, h->nblock, h->nb_max, (const T*)h->d_U,
-                                 (const T*)h->d_C, Tg, Dg, (const T*)h->d_Te, (const T*)h->d_De,
-                                 (const T*)h->d_aT, (const T*)h->d_bT, (const T*)h->d_dxT,
-                                 (const T*)h->d_lamT, h->d_ptab, h->d_gtab, (T*)h->d_Ubar,
-                                 h->prob.ridge_c, h->d_status, h->stream);
+  st = timed(h, ENKFMC_K_ADJ_REGRESS, [&](int* nk) {
+    return launch_adj_regressions<T>(g, h->d_blocks, h->nblock, h->nb_max, stats_of<T>(h), Tg, Dg,
+                                     (const T*)h->d_Te, (const T*)h->d_De, (const T*)h->d_aT,
+                                     (const T*)h->d_bT, (const T*)h->d_dxT, (const T*)h->d_lamT,
+                                     h->d_ptab, h->d_gtab, (T*)h->d_Ubar, h->prob.ridge_c,
+                                     h->d_status, h->stream, nk);
   });
   if (st) return st;
   return timed(h, ENKFMC_K_ADJOINT, [&] {
@@ -674,6 +770,10 @@ enkfmc_status enkfmc_query(const enkfmc_handle* h, enkfmc_info* info) {
   info->band_elems = h->band_elems;
   info->workspace_bytes = h->workspace_bytes;
   info->m = h->m;
+  info->tc_chol = h->tc_chol ? 1 : 0;
+  info->tc_solve = h->tc_solve ? 1 : 0;
+  info->refine_steps = h->refine_solve ? h->refine_steps : 0;
+  info->fp64_rows = h->d_C64 ? 1 : 0;
   return ENKFMC_OK;
 }
 
@@ -862,17 +962,19 @@ enkfmc_status enkfmc_profile(enkfmc_handle* h, int32_t enable) {
   return ENKFMC_OK;
 }
 
-enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* launches, double* ms) {
-  if (!h || !launches || !ms) return ENKFMC_EINVAL;
+enkfmc_status enkfmc_profile_read(enkfmc_handle* h, int64_t* calls, int64_t* kernels,
+                                  double* ms) {
+  if (!h || !calls || !kernels || !ms) return ENKFMC_EINVAL;
   for (int k = 0; k < ENKFMC_NKERNEL; ++k) {
-    launches[k] = 0;
+    calls[k] = h->calls[k];
+    kernels[k] = h->kernels[k];
+    h->calls[k] = h->kernels[k] = 0;
     ms[k] = 0.0;
   }
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   for (const auto& r : h->recs) {
     float t = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
-    launches[r.kind] += 1;
     ms[r.kind] += t;
   }
   h->recs.clear();

@@ -230,6 +230,8 @@ struct enkfmc_handle {
   // device workspace (element type by precision)
   void* d_U = nullptr;     // anomalies, component-major [n][ldN]
   void* d_C = nullptr;     // covariance table [n][cov_offset_count]
+  double* d_U64 = nullptr; // FP32 problems with rows where 2p > N: FP64 anomalies
+  double* d_C64 = nullptr; //   and FP64 covariance table for those rows
   const void* U_src = nullptr;  // Xb the anomalies and table were computed from
   void* d_Te = nullptr;    // boundary rows of T per block [ext_rows][pmax]
   void* d_De = nullptr;    // their D [ext_rows]
@@ -242,6 +244,7 @@ struct enkfmc_handle {
   bool tc_solve = false;  // FP32 solves on the tensor cores
   bool tc_chol = false;   // FP32 band Cholesky updates on the tensor cores
   bool refine_solve = false;
+  int refine_steps = 0;   // refinement steps of every sub-domain solve (FP32)
   const void* T_assembled = nullptr;  // global T/D used by the last assemble
   const void* D_assembled = nullptr;
   bool assembled = false;
@@ -256,6 +259,7 @@ struct enkfmc_handle {
   bool analyzed = false;
   // reverse-pass buffers (allocated on the first enkfmc_analyze_adjoint)
   void *d_lam = nullptr, *d_aT = nullptr, *d_bT = nullptr, *d_dxT = nullptr, *d_lamT = nullptr;
+  void* d_W = nullptr;    // the reverse pass's right-hand side W (refinement)
   void* d_Ubar = nullptr;
 
   // kernel timing (events bracket each launch while enabled)
@@ -263,6 +267,8 @@ struct enkfmc_handle {
     int kind;
     cudaEvent_t a, b;
   };
+  int64_t calls[ENKFMC_NKERNEL] = {};     // launcher calls per kind (always counted)
+  int64_t kernels[ENKFMC_NKERNEL] = {};   // CUDA kernels those calls launched
   bool prof = false;
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -290,21 +296,51 @@ __device__ __forceinline__ T rhs_entry(T yo, T sq, T z, T xb, T rinv) {
   return (fma(sq, z, yo) - xb) * rinv;
 }
 
-// Kernel launchers (implemented per .cu file).  T is float or double.
-template <typename T>
-cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s);
+// Kernel launchers (implemented per .cu file).  T is float or double.  Each
+// adds the number of kernels it launched to *nk.
 
 // Offsets in the half box |dk| <= vr, |dlat|, |dlon| <= 2r with (dk, dlat, dlon) >= 0
 // lexicographically: the columns of the covariance table C[n][count].
 int cov_offset_count(int r, int vr);
 
+// Precision rule of the estimate: a single-precision problem regresses the rows
+// with 2p > N (p/N > 0.5, nearly singular Gram matrices) in double precision
+// from FP64 anomalies and an FP64 covariance table.  True when some row of the
+// problem can have 2p > N.
+bool has_fp64_rows(const Geom& g, bool single);
+// The estimate kernels can run this geometry (gather-table index widths,
+// members, shared memory of the covariance table and of the regressions, in
+// the problem's precision and, with FP64 rows, in double).
+bool estimate_supported(const Geom& g, bool single);
+
+// Validate a problem description and fill its geometry (shared by the handle
+// and the allocation-free estimate): EINVAL for out-of-range sizes, label
+// counts of 2^31 or more, or a geometry the estimate kernels cannot run.
+enkfmc_status problem_geom(const enkfmc_problem& p, Geom& g);
+
+// Statistics of one ensemble: anomalies U [n][ldN] and covariance table
+// C [n][cov_offset_count] in the problem's precision; U64, C64 their FP64
+// counterparts (single-precision problems with FP64 rows), else null.
 template <typename T>
-cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s);
+struct EstStats {
+  T* U;
+  T* C;
+  double* U64;
+  double* C64;
+};
 
 template <typename T>
-cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
-                           int64_t nitems, const Block* blocks, T* Tout, T* Dout, double ridge_c,
-                           int32_t* status, cudaStream_t s);
+cudaError_t launch_stat_anomalies(const Geom& g, const T* Xb, const EstStats<T>& st,
+                                  cudaStream_t s, int* nk);
+template <typename T>
+cudaError_t launch_stat_covtables(const Geom& g, const EstStats<T>& st, cudaStream_t s,
+                                  int* nk);
+// Regressions of the global rows (halo null, nitems = n) or of the boundary
+// rows listed in halo; status may be null.
+template <typename T>
+cudaError_t launch_regressions(const Geom& g, const EstStats<T>& st, const int32_t* halo,
+                               int64_t nitems, const Block* blocks, T* Tout, T* Dout,
+                               double ridge_c, int32_t* status, cudaStream_t s, int* nk);
 
 template <typename T>
 cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
@@ -372,22 +408,25 @@ cudaError_t launch_adj_ab(const Geom& g, const Block* blocks, int nblock, int nb
                           const T* Tg, const T* Te, const T* lam, const T* dX, const T* dX2,
                           T* aT, T* bT, T* dxT, T* lamT, cudaStream_t s);
 template <typename T>
-cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
-                               const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
-                               const T* De, const T* aT, const T* bT, const T* dxT,
-                               const T* lamT, const int2* ptab, const uint16_t* gtab,
-                               T* Ubar, double ridge_c, int32_t* status, cudaStream_t s);
+cudaError_t launch_adj_regressions(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                                   const EstStats<T>& st, const T* Tg, const T* Dg, const T* Te,
+                                   const T* De, const T* aT, const T* bT, const T* dxT,
+                                   const T* lamT, const int2* ptab, const uint16_t* gtab, T* Ubar,
+                                   double ridge_c, int32_t* status, cudaStream_t s, int* nk);
 template <typename T>
 cudaError_t launch_adj_finish(const Geom& g, const T* Ubar, const T* Xa_bar, T* Xb_bar,
                               cudaStream_t s);
 
 // Single-precision refinement residual res = rhs - A dX (two passes; vhi, vlo
-// are scratch of the size of dX).
+// are scratch of the size of dX).  rhs: Eq. 11's observation term formed from
+// Xb, y, R, Z, or rhs_in (per block [N][nb]) when it is not null.
 cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                    const int32_t* obs_of, int64_t m, const float* Xb,
                                    const float* y, const float* R, const float* Z,
                                    const float* Tg, const float* Dg, const float* Te,
                                    const float* De, const float* dX, float* vhi, float* vlo,
-                                   float* res, cudaStream_t s);
+                                   const float* rhs_in, float* res, cudaStream_t s);
+// y += x over `count` elements.
+cudaError_t launch_accumulate(float* y, const float* x, int64_t count, cudaStream_t s);
 
 }  // namespace enkfmc

@@ -10,9 +10,11 @@
 // file-scope device array of fixed size that exists on every GPU that loads
 // the library, for as long as the process lives.
 //
-// Scratch layout: [0, 256) a 16-byte status word (cleared at every call),
-// then the component-major anomalies U[n][ldN], then the covariance table
-// C[n][nC] (nC pair offsets per component).
+// Scratch layout (each part starting on a 256-byte boundary): the
+// component-major anomalies U[n][ldN], the covariance table C[n][nC] (nC pair
+// offsets per component), and for single-precision problems with rows where
+// 2p > N their FP64 copies U64[n][ldN], C64[n][nC].  Every byte a call reads
+// it has written first in the same call, so nothing needs clearing.
 #include <cstring>
 #include <mutex>
 
@@ -23,7 +25,6 @@ using namespace enkfmc;
 namespace {
 
 constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;  // 16 MiB
-constexpr size_t kStatusBytes = 256;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -50,53 +51,38 @@ enkfmc_status scratch_address(int dev, void** out) {
   return ENKFMC_OK;
 }
 
-// Geometry of a problem for the global regressions (no sub-domain tables).
-enkfmc_status noalloc_geom(const enkfmc_problem& p, Geom& g) {
-  const int nvar = p.nvar_3d + p.nvar_2d;
-  if (p.nlon < 1 || p.nlat < 1 || p.nlev < 1 || p.nvar_3d < 0 || p.nvar_2d < 0 || nvar < 1 ||
-      nvar > kMaxVar || p.r < 0 || p.r > 16 || p.vert_reach < 0 || p.N < 2 || p.N > 128 ||
-      !(p.ridge_c >= 0.0))
-    return ENKFMC_EINVAL;
-  if (p.precision != ENKFMC_FP64 && p.precision != ENKFMC_FP32) return ENKFMC_EINVAL;
-  if (p.lon_periodic && p.nlon < 2 * p.r + 1) return ENKFMC_EINVAL;
-  std::memset(&g, 0, sizeof(g));
-  g.nlon = p.nlon;
-  g.nlat = p.nlat;
-  g.nlev = p.nlev;
-  g.nvar3 = p.nvar_3d;
-  g.nvar2 = p.nvar_2d;
-  g.nvar = nvar;
-  g.r = p.r;
-  g.vr = p.nvar_3d > 0 ? (p.vert_reach < p.nlev - 1 ? p.vert_reach : p.nlev - 1) : 0;
-  g.periodic = p.lon_periodic ? 1 : 0;
-  g.N = p.N;
-  g.ldN = (p.N + 3) / 4 * 4;
-  g.pmax = slot_count(g.r, g.vr, g.periodic);
-  int64_t off = 0;
-  for (int v = 0; v < nvar; ++v) {
-    g.var_off[v] = off;
-    g.var_lev[v] = v < p.nvar_3d ? p.nlev : 1;
-    off += (int64_t)g.var_lev[v] * p.nlat * p.nlon;
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Scratch bytes of a validated geometry (n < 2^31, ldN <= 128, nC < 2^15:
+// no product below can wrap in 64 bits).
+size_t scratch_need(const Geom& g, bool single, size_t* offC, size_t* offU64, size_t* offC64) {
+  const size_t n = (size_t)g.n, nC = (size_t)cov_offset_count(g.r, g.vr);
+  const size_t es = single ? sizeof(float) : sizeof(double);
+  size_t off = round256(es * n * (size_t)g.ldN);
+  *offC = off;
+  off += round256(es * n * nC);
+  *offU64 = *offC64 = 0;
+  if (has_fp64_rows(g, single)) {
+    *offU64 = off;
+    off += round256(sizeof(double) * n * (size_t)g.ldN);
+    *offC64 = off;
+    off += round256(sizeof(double) * n * nC);
   }
-  g.var_off[nvar] = off;
-  g.n = off;
-  return ENKFMC_OK;
+  return off;
 }
 
 template <typename T>
 enkfmc_status run(const Geom& g, double ridge_c, const T* Xb, T* Tv, T* D, unsigned char* base,
-                  cudaStream_t s) {
-  int32_t* status = reinterpret_cast<int32_t*>(base);
-  T* U = reinterpret_cast<T*>(base + kStatusBytes);
-  T* Cv = U + (size_t)g.n * g.ldN;
-  if (cudaMemsetAsync(status, 0, 16, s) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return ENKFMC_ECUDA;
-  }
-  cudaError_t e = launch_anomalies<T>(g, Xb, U, s);
-  if (e == cudaSuccess) e = launch_covtable<T>(g, U, Cv, s);
+                  size_t offC, size_t offU64, size_t offC64, cudaStream_t s) {
+  EstStats<T> st{reinterpret_cast<T*>(base), reinterpret_cast<T*>(base + offC),
+                 offU64 ? reinterpret_cast<double*>(base + offU64) : nullptr,
+                 offC64 ? reinterpret_cast<double*>(base + offC64) : nullptr};
+  int nk = 0;
+  cudaError_t e = launch_stat_anomalies<T>(g, Xb, st, s, &nk);
+  if (e == cudaSuccess) e = launch_stat_covtables<T>(g, st, s, &nk);
+  // no status word: a failed row shows as D = NaN with a zero T row
   if (e == cudaSuccess)
-    e = launch_regress<T>(g, U, Cv, nullptr, g.n, nullptr, Tv, D, ridge_c, status, s);
+    e = launch_regressions<T>(g, st, nullptr, g.n, nullptr, Tv, D, ridge_c, nullptr, s, &nk);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     return ENKFMC_ECUDA;
@@ -110,12 +96,12 @@ extern "C" enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const 
                                                  void* Tvals, void* D, void* cuda_stream) {
   if (!p || !Xb || !Tvals || !D) return ENKFMC_EINVAL;
   Geom g;
-  enkfmc_status st = noalloc_geom(*p, g);
+  enkfmc_status st = problem_geom(*p, g);  // every unsupported geometry: EINVAL here
   if (st) return st;
-  const size_t esize = p->precision == ENKFMC_FP64 ? sizeof(double) : sizeof(float);
-  const size_t need =
-      kStatusBytes + esize * (size_t)g.n * ((size_t)g.ldN + (size_t)cov_offset_count(g.r, g.vr));
-  if (need > kNoallocScratchBytes) return ENKFMC_EINVAL;
+  const bool single = p->precision != ENKFMC_FP64;
+  size_t offC, offU64, offC64;
+  if (scratch_need(g, single, &offC, &offU64, &offC64) > kNoallocScratchBytes)
+    return ENKFMC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     (void)cudaGetLastError();
@@ -125,7 +111,9 @@ extern "C" enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const 
   if ((st = scratch_address(dev, &base))) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
   unsigned char* b = static_cast<unsigned char*>(base);
-  if (p->precision == ENKFMC_FP64)
-    return run<double>(g, p->ridge_c, (const double*)Xb, (double*)Tvals, (double*)D, b, s);
-  return run<float>(g, p->ridge_c, (const float*)Xb, (float*)Tvals, (float*)D, b, s);
+  if (!single)
+    return run<double>(g, p->ridge_c, (const double*)Xb, (double*)Tvals, (double*)D, b, offC,
+                       offU64, offC64, s);
+  return run<float>(g, p->ridge_c, (const float*)Xb, (float*)Tvals, (float*)D, b, offC, offU64,
+                    offC64, s);
 }

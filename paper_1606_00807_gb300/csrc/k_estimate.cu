@@ -27,6 +27,9 @@
 // D_j = (u.u - beta.g - lambda beta.beta) / (N - 1) from the Gram entries.
 #include <math.h>
 
+#include <algorithm>
+#include <type_traits>
+
 #include "enkfmc_internal.h"
 
 namespace enkfmc {
@@ -81,39 +84,45 @@ __device__ __forceinline__ void atomic_add4(double* p, const double (&v)[4]) {
 }
 
 // ---------------------------------------------------------------------------
-// Anomalies: U[l][m] = X[m][l] - mean_m X[m][l]
+// Anomalies: U[l][m] = X[m][l] - mean_m X[m][l], accumulated and subtracted in
+// TU; U32 (optional) receives the same anomalies rounded to single precision
+// (the FP32 path with FP64 rows keeps both).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_anomalies(const T* __restrict__ X, T* __restrict__ U,
-                                                   int64_t n, int N, int ldN) {
-  __shared__ T tile[32][33];
-  __shared__ T mean_s[32];
+template <typename TX, typename TU>
+__global__ void __launch_bounds__(256) k_anomalies(const TX* __restrict__ X, TU* __restrict__ U,
+                                                   float* __restrict__ U32, int64_t n, int N,
+                                                   int ldN) {
+  __shared__ TU tile[32][33];
+  __shared__ TU mean_s[32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int64_t c0 = (int64_t)blockIdx.x * 32;
   const int64_t c = c0 + tx;
-  T acc = 0;
+  TU acc = 0;
   if (c < n)
-    for (int m = ty; m < N; m += 8) acc += X[(int64_t)m * n + c];
+    for (int m = ty; m < N; m += 8) acc += (TU)X[(int64_t)m * n + c];
   tile[ty][tx] = acc;
   __syncthreads();
   if (ty == 0) {
-    T s = 0;
+    TU s = 0;
     for (int i = 0; i < 8; ++i) s += tile[i][tx];
-    mean_s[tx] = s / T(N);
+    mean_s[tx] = s / TU(N);
   }
   __syncthreads();
   for (int m0 = 0; m0 < ldN; m0 += 32) {
     for (int i = ty; i < 32; i += 8) {
       const int m = m0 + i;
-      T v = 0;
-      if (c < n && m < N) v = X[(int64_t)m * n + c] - mean_s[tx];
+      TU v = 0;
+      if (c < n && m < N) v = (TU)X[(int64_t)m * n + c] - mean_s[tx];
       tile[i][tx] = v;
     }
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
       const int64_t cc = c0 + i;
       const int m = m0 + tx;
-      if (cc < n && m < ldN) U[cc * ldN + m] = tile[tx][i];
+      if (cc < n && m < ldN) {
+        U[cc * ldN + m] = tile[tx][i];
+        if (U32) U32[cc * ldN + m] = (float)tile[tx][i];
+      }
     }
     __syncthreads();
   }
@@ -656,13 +665,19 @@ __device__ void tiled_backward(const T* L, int ldg, const T* invd, T* v, int n, 
 
 constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 
-// RR: rounds of 32 rows covering pmax + 1; MR: rounds of 32 members covering N.
-template <typename T, int RR, int MR>
+// One warp per row of the item list (every component, or the boundary rows of
+// the blocks when `halo` is given).  T: the arithmetic and the element type of
+// U and C; TO: the element type of Tout and Dout.  MR: rounds of 32 members
+// covering N.  sel selects rows by their predecessor count p: 0 every row,
+// 1 the rows with 2p <= N, 2 the rows with 2p > N (p/N > 0.5: the rows a
+// single-precision problem regresses in double precision, from FP64 U and C).
+// status may be null (errors then show only as D = NaN with a zero T row).
+template <typename T, typename TO, int MR>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     k_regress(const Geom g, const T* __restrict__ U, const T* __restrict__ C, int nH,
               const int32_t* __restrict__ halo, int64_t nitems, const Block* __restrict__ blocks,
-              T* __restrict__ Tout, T* __restrict__ Dout, double ridge_c, int32_t* status,
-              int ldp, int ldg, int warp_bytes) {
+              TO* __restrict__ Tout, TO* __restrict__ Dout, double ridge_c, int32_t* status,
+              int ldp, int ldg, int warp_bytes, int sel) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   // per-block slot offsets
@@ -748,6 +763,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
       sl[p] = -1;
     }
     __syncwarp();
+    if (sel && ((2 * p > N) != (sel == 2))) continue;  // the other launch's row
     const int p1 = p + 1;
 
     // gather the augmented Gram matrix, lower triangle, rows 0..p: the typical
@@ -782,7 +798,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
       gv[i] = L[p * ldg + i];
       L[i * ldg + i] += lam;
     }
-    const T uu = L[p * ldg + p];
     __syncwarp();
 
     // right-looking tiled Cholesky; pivots for the first p columns, so row p
@@ -891,26 +906,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
         Dj = (T)(ssq / (float)(N - 1));
         __syncwarp();
       } else {
-        // |e|^2 = u.u - beta.g - lambda beta.beta
-        T s1 = 0, s2 = 0;
-        for (int i = lane; i < p; i += 32) {
-          s1 = fma(vb[i], gv[i], s1);
-          s2 = fma(vb[i], vb[i], s2);
+        // D from the explicit residual e = u - U_P^T beta, members m = lane + 32 t
+        // (the closed form u.u - beta.g - lambda beta.beta cancels when the
+        // residual is small next to u)
+        T ee = 0;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) {
+          const int m = lane + 32 * t;
+          if (m < N) {
+            T e = U[(int64_t)jlab * g.ldN + m];
+            for (int i = 0; i < p; ++i) e = fma(-U[(int64_t)q[i] * g.ldN + m], vb[i], e);
+            ee = fma(e, e, ee);
+          }
         }
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        Dj = (uu - s1 - lam * s2) / T(N - 1);
+        ee = warp_sum(ee);
+        Dj = ee / T(N - 1);
       }
       if (!finite_val(Dj)) err = ENKFMC_ENONFINITE;
       else if (!(Dj > T(0))) err = ENKFMC_EDNONPOS;
     }
-    if (err && lane == 0) record_error(status, err, orow);
-    T* trow = Tout + orow * pmax;
+    if (err && lane == 0 && status) record_error(status, err, orow);
+    TO* trow = Tout + orow * pmax;
     for (int s = lane; s < pmax; s += 32) {
       const int i = sidx[s];
-      trow[s] = (i >= 0 && !err) ? -vb[i] : T(0);
+      trow[s] = (i >= 0 && !err) ? (TO)(-vb[i]) : TO(0);
     }
-    if (lane == 0) Dout[orow] = err ? T(NAN) : Dj;
+    if (lane == 0) Dout[orow] = err ? TO(NAN) : (TO)Dj;
     __syncwarp();
   }
 }
@@ -926,14 +947,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 // kappa = 2 (c / p) v.beta when the ridge is active.  Ubar is accumulated with
 // atomic adds (rows share predecessors).
 // ---------------------------------------------------------------------------
-template <typename T>
+// T: the arithmetic and the element type of U and C (FP64 for the rows a
+// single-precision problem regressed in double precision); TS: the element
+// type of T, D, the adjoint rows and Ubar.  sel as in k_regress.
+template <typename T, typename TS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
     const Geom g, const Block* __restrict__ blocks, const T* __restrict__ U,
-    const T* __restrict__ C, int nH, const T* __restrict__ Tg, const T* __restrict__ Dg,
-    const T* __restrict__ Te, const T* __restrict__ De, const T* __restrict__ aT,
-    const T* __restrict__ bT, const T* __restrict__ dxT, const T* __restrict__ lamT,
-    const int2* __restrict__ ptab, const uint16_t* __restrict__ gtab, T* __restrict__ Ubar,
-    double ridge_c, int32_t* status, int ldp, int ldg, int warp_bytes) {
+    const T* __restrict__ C, int nH, const TS* __restrict__ Tg, const TS* __restrict__ Dg,
+    const TS* __restrict__ Te, const TS* __restrict__ De, const TS* __restrict__ aT,
+    const TS* __restrict__ bT, const TS* __restrict__ dxT, const TS* __restrict__ lamT,
+    const int2* __restrict__ ptab, const uint16_t* __restrict__ gtab, TS* __restrict__ Ubar,
+    double ridge_c, int32_t* status, int ldp, int ldg, int warp_bytes, int sel) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   signed char* off = reinterpret_cast<signed char*>(smem);
@@ -995,25 +1019,33 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
     sl[p] = -1;
   }
   __syncwarp();
+  if (sel && ((2 * p > N) != (sel == 2))) return;  // the other launch's row
   // beta and D of this instance
   const bool inner = in_interior(b, y, x);
-  const T* trow = inner ? Tg + (int64_t)jlab * pmax : Te + rowj * pmax;
-  const T Dj = inner ? Dg[jlab] : De[rowj];
-  for (int i = lane; i < p; i += 32) vb[i] = -trow[sl[i]];
+  const TS* trow = inner ? Tg + (int64_t)jlab * pmax : Te + rowj * pmax;
+  const T Dj = (T)(inner ? Dg[jlab] : De[rowj]);
+  for (int i = lane; i < p; i += 32) vb[i] = -(T)trow[sl[i]];
   __syncwarp();
   // members 4 lane .. 4 lane + 3 of this lane (N <= 128): vector loads, and
   // one vector atomic per predecessor for U-bar
   const int m0 = 4 * lane;
-  auto ld4 = [&](const T* row, T (&o)[4]) {
+  auto ld4 = [&](const auto* row, T (&o)[4]) {
     if (m0 < ldN) {
-      ldg4v(row + m0, o);
+      using E = typename std::remove_cv<typename std::remove_pointer<decltype(row)>::type>::type;
+      E r4[4];
+      ldg4v(row + m0, r4);
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
-        if (m0 + a >= N) o[a] = T(0);
+      for (int a = 0; a < 4; ++a) o[a] = (m0 + a < N) ? (T)r4[a] : T(0);
     } else {
 #pragma unroll
       for (int a = 0; a < 4; ++a) o[a] = T(0);
     }
+  };
+  auto add4 = [&](TS* dst, const T (&d)[4]) {
+    TS c4[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) c4[a] = (TS)d[a];
+    atomic_add4(dst, c4);
   };
   // e = u - U_P^T beta; a_j, b_j in registers
   T e[4], aj[4], bj[4];
@@ -1049,11 +1081,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
         L[i * ldg + l] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
       }
     } else if (gtab) {  // any other row: the handle's gather tables, through the slots
+      // The ballot compaction above keeps the slots in increasing order, so
+      // sl[l] <= sl[i] whenever l <= i: (sl[i], sl[l]) is a lower-triangle entry
+      // of the slot-pair table, the only half it stores.
       const int nfull = (pmax + 1) * (pmax + 2) / 2;
       for (int pi = lane; pi < npair; pi += 32) {
         const uint32_t il = gtab[pi];
         const int i = il & 0xff, l = il >> 8;
         const int si = sl[i], sm = sl[l];
+#ifdef ENKFMC_CHECK
+        if (sm > si && status) record_error(status, ENKFMC_EINVAL, rowj);
+#endif
         const uint32_t e = gtab[nfull + si * (si + 1) / 2 + sm];
         L[i * ldg + l] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
       }
@@ -1132,10 +1170,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       if (kappa != T(0)) ld4(U + (int64_t)q[i] * ldN, u4);
 #pragma unroll
       for (int a = 0; a < 4; ++a) d4[a] = vi * e[a] - bi * f[a] - kappa * u4[a];
-      if (m0 < N) atomic_add4(Ubar + (int64_t)q[i] * ldN + m0, d4);
+      if (m0 < N) add4(Ubar + (int64_t)q[i] * ldN + m0, d4);
     }
   }
-  if (m0 < N) atomic_add4(Ubar + (int64_t)jlab * ldN + m0, f);
+  if (m0 < N) add4(Ubar + (int64_t)jlab * ldN + m0, f);
 }
 
 }  // namespace
@@ -1145,170 +1183,288 @@ int cov_offset_count(int r, int vr) {
   return ((2 * vr + 1) * w4 * w4 + 1) / 2;
 }
 
-template <typename T>
-cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s) {
-  const dim3 blk(32, 8);
-  const int64_t grid = (g.n + 31) / 32;
-  k_anomalies<T><<<(unsigned)grid, blk, 0, s>>>(Xb, U, g.n, g.N, g.ldN);
-  return cudaGetLastError();
-}
+namespace {
 
-template <typename T>
-cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
-  constexpr int MC = sizeof(T) == 4 ? 16 : 8;
+// Launch shape of the covariance table for elements of `esize` bytes: the
+// member-major kernel (k_covtable4, even r) when its window and tiles fit,
+// else the general one (k_covtable).  False when neither fits.
+struct CovShape {
+  bool mm;
+  int W, tpt, Wp4, mc;
+  size_t smem;
+};
+
+bool covtable_shape(const Geom& g, size_t esize, CovShape& cs) {
   const int r = g.r;
+  const int MC = esize == 4 ? 16 : 8;
   const int nH = cov_offset_count(r, g.vr);
   const int nrho = 1 + 2 * r + g.vr * (4 * r + 1);
-  if (r % 2 == 0) {  // aligned b windows: member-major staging
+  cs.mc = MC;
+  if (r % 2 == 0) {
     int W = r <= 2 ? 64 : 32;
     auto bytes = [&](int w) {
       const int wp4 = (w + 4 * r + 4 + 3) / 4 * 4;
-      return sizeof(T) * std::max((size_t)MC * nrho * wp4, (size_t)w * nH);
+      return esize * std::max((size_t)MC * nrho * wp4, (size_t)w * nH);
     };
     while (bytes(W) > 200 * 1024 && W > 8) W /= 2;
     const int w4 = 4 * r + 1;
     const int ntiles = ((2 * r + 1 + 3) / 4 + (nrho - 1) * ((w4 + 3) / 4)) * (W / 4);
     const int tpt = (ntiles + 255) / 256;
     if (bytes(W) <= 220 * 1024 && tpt <= 4) {
-      const int Wp4 = (W + 4 * r + 4 + 3) / 4 * 4;
-      int planes = 0;
-      for (int v = 0; v < g.nvar; ++v) planes += g.var_lev[v];
-      const dim3 grid((g.nlon + W - 1) / W, g.nlat, planes);
-      auto run = [&](auto kern) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)bytes(W));
-        if (e != cudaSuccess) return e;
-        kern<<<grid, 256, bytes(W), s>>>(g, U, C, W, nH, nrho, Wp4);
-        return cudaGetLastError();
-      };
-      if (tpt <= 1) return run(k_covtable4<T, MC, 1>);
-      if (tpt <= 2) return run(k_covtable4<T, MC, 2>);
-      if (tpt <= 3) return run(k_covtable4<T, MC, 3>);
-      return run(k_covtable4<T, MC, 4>);
+      cs.mm = true;
+      cs.W = W;
+      cs.tpt = tpt;
+      cs.Wp4 = (W + 4 * r + 4 + 3) / 4 * 4;
+      cs.smem = bytes(W);
+      return true;
     }
   }
   int W = r <= 2 ? 64 : 32;
-  size_t smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 1) + (size_t)W * nH);
-  while (smem > 200 * 1024 && W > 8) {
-    W /= 2;
-    smem = sizeof(T) * ((size_t)nrho * (W + 4 * r) * (MC + 1) + (size_t)W * nH);
+  auto bytes = [&](int w) {
+    return esize * ((size_t)nrho * (w + 4 * r) * (MC + 1) + (size_t)w * nH);
+  };
+  while (bytes(W) > 200 * 1024 && W > 8) W /= 2;
+  cs.mm = false;
+  cs.W = W;
+  cs.tpt = 0;
+  cs.Wp4 = 0;
+  cs.smem = bytes(W);
+  return cs.smem <= 220 * 1024;
+}
+
+// Launch shape of k_regress (reg = true) or k_adj_regress for elements of
+// `esize` bytes: per-warp workspace, warps per CTA, shared memory.
+struct RegShape {
+  int ldp, ldg, wpc;
+  size_t wb, smem;
+};
+
+bool regress_shape(const Geom& g, size_t esize, bool reg, RegShape& rs) {
+  rs.ldp = ((g.pmax + 1) + 3) / 4 * 4;
+  // row stride = 4 (mod 8): 16-byte row reads of 8 consecutive lanes are conflict free
+  rs.ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
+  size_t wb = (size_t)rs.ldp * 3 * sizeof(int) +
+              esize * ((size_t)rs.ldp * rs.ldg + (reg ? 4 : 3) * (size_t)rs.ldp);
+  rs.wb = (wb + 15) / 16 * 16;
+  size_t offbytes = (3 * (size_t)g.pmax + 15) / 16 * 16;
+  if (reg)
+    offbytes += pair_table_bytes(g.pmax, g.r, g.periodic) + gather_table_bytes(g.pmax);
+  int wpc = (int)(((size_t)96 * 1024 - std::min<size_t>(offbytes, 96 * 1024)) / rs.wb);
+  if (wpc > 8) wpc = 8;
+  if (wpc < 1) {
+    wpc = (int)(((size_t)200 * 1024 - std::min<size_t>(offbytes, 200 * 1024)) / rs.wb);
+    if (wpc < 1) return false;
+    if (wpc > 8) wpc = 8;
   }
-  if (smem > 220 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_covtable<T, MC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int planes = 0;
-  for (int v = 0; v < g.nvar; ++v) planes += g.var_lev[v];
-  const dim3 grid((g.nlon + W - 1) / W, g.nlat, planes);
-  k_covtable<T, MC><<<grid, 256, smem, s>>>(g, U, C, W, nH, nrho);
+  rs.wpc = wpc;
+  rs.smem = offbytes + rs.wb * wpc;
+  return true;
+}
+
+}  // namespace
+
+bool has_fp64_rows(const Geom& g, bool single) { return single && 2 * g.pmax > g.N; }
+
+bool estimate_supported(const Geom& g, bool single) {
+  // 8-bit row indices in the gather tables, 15-bit table columns, members in
+  // at most four rounds of 32 lanes
+  if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds || g.N < 2) return false;
+  if (cov_offset_count(g.r, g.vr) >= 0x8000) return false;
+  CovShape cs;
+  RegShape rs;
+  const size_t es = single ? 4 : 8;
+  if (!covtable_shape(g, es, cs) || !regress_shape(g, es, true, rs) ||
+      !regress_shape(g, es, false, rs))
+    return false;
+  if (has_fp64_rows(g, single) &&
+      (!covtable_shape(g, 8, cs) || !regress_shape(g, 8, true, rs) ||
+       !regress_shape(g, 8, false, rs)))
+    return false;
+  return true;
+}
+
+template <typename T>
+cudaError_t launch_anomalies(const Geom& g, const T* Xb, T* U, cudaStream_t s) {
+  const dim3 blk(32, 8);
+  const int64_t grid = (g.n + 31) / 32;
+  k_anomalies<T, T><<<(unsigned)grid, blk, 0, s>>>(Xb, U, nullptr, g.n, g.N, g.ldN);
   return cudaGetLastError();
 }
 
-template <typename T, int RR, int MR>
-cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32_t* halo,
-                              int64_t nitems, const Block* blocks, T* Tout, T* Dout,
-                              double ridge_c, int32_t* status, cudaStream_t s) {
-  const int nH = cov_offset_count(g.r, g.vr);
-  const int ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  // row stride = 4 (mod 8): 16-byte row reads of 8 consecutive lanes are conflict free
-  const int ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
-  size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 4 * (size_t)ldp);
-  wb = (wb + 15) / 16 * 16;
-  const int offbytes = (3 * g.pmax + 15) / 16 * 16 + pair_table_bytes(g.pmax, g.r, g.periodic) +
-                       gather_table_bytes(g.pmax);
-  int wpc = (int)((96 * 1024 - offbytes) / wb);
-  if (wpc > 8) wpc = 8;
-  if (wpc < 1) {
-    wpc = (int)((200 * 1024 - offbytes) / wb);
-    if (wpc < 1) return cudaErrorInvalidConfiguration;
-    if (wpc > 8) wpc = 8;
+template <typename T>
+cudaError_t launch_covtable(const Geom& g, const T* U, T* C, cudaStream_t s) {
+  constexpr int MC = sizeof(T) == 4 ? 16 : 8;
+  CovShape cs;
+  if (!covtable_shape(g, sizeof(T), cs)) return cudaErrorInvalidConfiguration;
+  const int r = g.r;
+  const int nH = cov_offset_count(r, g.vr);
+  const int nrho = 1 + 2 * r + g.vr * (4 * r + 1);
+  int planes = 0;
+  for (int v = 0; v < g.nvar; ++v) planes += g.var_lev[v];
+  const dim3 grid((g.nlon + cs.W - 1) / cs.W, g.nlat, planes);
+  auto run = [&](auto kern, auto... args) -> cudaError_t {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, cs.smem, s>>>(g, U, C, cs.W, nH, nrho, args...);
+    return cudaGetLastError();
+  };
+  if (cs.mm) {  // aligned b windows: member-major staging
+    if (cs.tpt <= 1) return run(k_covtable4<T, MC, 1>, cs.Wp4);
+    if (cs.tpt <= 2) return run(k_covtable4<T, MC, 2>, cs.Wp4);
+    if (cs.tpt <= 3) return run(k_covtable4<T, MC, 3>, cs.Wp4);
+    return run(k_covtable4<T, MC, 4>, cs.Wp4);
   }
-  const size_t smem = offbytes + wb * wpc;
-  cudaError_t e = cudaFuncSetAttribute(k_regress<T, RR, MR>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return run(k_covtable<T, MC>);
+}
+
+template <typename T, typename TO, int MR>
+cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32_t* halo,
+                              int64_t nitems, const Block* blocks, TO* Tout, TO* Dout,
+                              double ridge_c, int32_t* status, int sel, cudaStream_t s) {
+  const int nH = cov_offset_count(g.r, g.vr);
+  RegShape rs;
+  if (!regress_shape(g, sizeof(T), true, rs)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_regress<T, TO, MR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs.smem);
   if (e != cudaSuccess) return e;
   // a grid-stride loop over the rows: enough CTAs for an even tail, few enough
   // that each amortises its shared tables (measured on the T63 rows: 64 CTAs
   // per SM beat 24, 32, 128 and one CTA per 8 rows)
-  int64_t grid = (nitems + wpc - 1) / wpc;
+  int64_t grid = (nitems + rs.wpc - 1) / rs.wpc;
   if (grid > 152 * 64) grid = 152 * 64;
-  k_regress<T, RR, MR><<<(unsigned)grid, 32 * wpc, smem, s>>>(
-      g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, ldp, ldg, (int)wb);
+  k_regress<T, TO, MR><<<(unsigned)grid, 32 * rs.wpc, rs.smem, s>>>(
+      g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, rs.ldp, rs.ldg,
+      (int)rs.wb, sel);
   return cudaGetLastError();
 }
 
-template <typename T, int RR>
-cudaError_t launch_regress_r(const Geom& g, const T* U, const T* C, const int32_t* halo,
-                             int64_t nitems, const Block* blocks, T* Tout, T* Dout,
-                             double ridge_c, int32_t* status, cudaStream_t s) {
-  const int mr = (g.N + 31) / 32;
-  if (mr <= 2)
-    return launch_regress_rm<T, RR, 2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
-                                       status, s);
-  if (mr == 3)
-    return launch_regress_rm<T, RR, 3>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
-                                       status, s);
-  return launch_regress_rm<T, RR, 4>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
-                                     s);
-}
-
-template <typename T>
+template <typename T, typename TO>
 cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
-                           int64_t nitems, const Block* blocks, T* Tout, T* Dout, double ridge_c,
-                           int32_t* status, cudaStream_t s) {
+                           int64_t nitems, const Block* blocks, TO* Tout, TO* Dout, double ridge_c,
+                           int32_t* status, int sel, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds) return cudaErrorInvalidConfiguration;
-  const int rr = (g.pmax + 1 + 31) / 32;
-  if (rr <= 2)
-    return launch_regress_r<T, 2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status, s);
-  if (rr <= 4)
-    return launch_regress_r<T, 4>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status, s);
-  return launch_regress_r<T, 8>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status, s);
+  const int mr = (g.N + 31) / 32;
+  if (mr <= 2)
+    return launch_regress_rm<T, TO, 2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                       status, sel, s);
+  if (mr == 3)
+    return launch_regress_rm<T, TO, 3>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                       status, sel, s);
+  return launch_regress_rm<T, TO, 4>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
+                                     sel, s);
 }
 
-template <typename T>
+template <typename T, typename TS>
 cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
-                               const T* U, const T* C, const T* Tg, const T* Dg, const T* Te,
-                               const T* De, const T* aT, const T* bT, const T* dxT,
-                               const T* lamT, const int2* ptab, const uint16_t* gtab,
-                               T* Ubar, double ridge_c, int32_t* status, cudaStream_t s) {
+                               const T* U, const T* C, const TS* Tg, const TS* Dg, const TS* Te,
+                               const TS* De, const TS* aT, const TS* bT, const TS* dxT,
+                               const TS* lamT, const int2* ptab, const uint16_t* gtab,
+                               TS* Ubar, double ridge_c, int32_t* status, int sel,
+                               cudaStream_t s) {
   if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
     return cudaErrorInvalidConfiguration;
   const int nH = cov_offset_count(g.r, g.vr);
-  const int ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  // row stride = 4 (mod 8): 16-byte tile rows, conflict-free for 8 consecutive lanes
-  const int ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
-  size_t wb = (size_t)ldp * 3 * sizeof(int) + sizeof(T) * ((size_t)ldp * ldg + 3 * (size_t)ldp);
-  wb = (wb + 15) / 16 * 16;
-  const int offbytes = (3 * g.pmax + 15) / 16 * 16;
-  int wpc = (int)((96 * 1024 - offbytes) / wb);
-  if (wpc > 8) wpc = 8;
-  if (wpc < 1) {
-    wpc = (int)((200 * 1024 - offbytes) / wb);
-    if (wpc < 1) return cudaErrorInvalidConfiguration;
-  }
-  const size_t smem = offbytes + wb * wpc;
-  cudaError_t e = cudaFuncSetAttribute(k_adj_regress<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  RegShape rs;
+  if (!regress_shape(g, sizeof(T), false, rs)) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_adj_regress<T, TS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs.smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
-  k_adj_regress<T><<<grid, 32 * wpc, smem, s>>>(g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT,
-                                                 dxT, lamT, ptab, gtab, Ubar, ridge_c, status,
-                                                 ldp, ldg, (int)wb);
+  const dim3 grid((nb_max + rs.wpc - 1) / rs.wpc, nblock);
+  k_adj_regress<T, TS><<<grid, 32 * rs.wpc, rs.smem, s>>>(
+      g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT, dxT, lamT, ptab, gtab, Ubar, ridge_c, status,
+      rs.ldp, rs.ldg, (int)rs.wb, sel);
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The estimate's launch sequence with the precision rule: double-precision
+// problems run in double; single-precision problems run in single, except the
+// rows with 2p > N (p/N > 0.5), whose nearly singular Gram matrices are formed
+// from FP64 anomalies and an FP64 covariance table and factored and solved in
+// double precision (st.U64 / st.C64 present exactly when has_fp64_rows).
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_stat_anomalies(const Geom& g, const T* Xb, const EstStats<T>& st,
+                                  cudaStream_t s, int* nk) {
+  ++*nk;
+  if constexpr (std::is_same<T, float>::value) {
+    if (st.U64) {
+      const dim3 blk(32, 8);
+      const int64_t grid = (g.n + 31) / 32;
+      k_anomalies<float, double><<<(unsigned)grid, blk, 0, s>>>(Xb, st.U64, st.U, g.n, g.N,
+                                                                g.ldN);
+      return cudaGetLastError();
+    }
+  }
+  return launch_anomalies<T>(g, Xb, st.U, s);
+}
+
+template <typename T>
+cudaError_t launch_stat_covtables(const Geom& g, const EstStats<T>& st, cudaStream_t s,
+                                  int* nk) {
+  ++*nk;
+  cudaError_t e = launch_covtable<T>(g, st.U, st.C, s);
+  if (e == cudaSuccess && st.C64) {
+    ++*nk;
+    e = launch_covtable<double>(g, st.U64, st.C64, s);
+  }
+  return e;
+}
+
+template <typename T>
+cudaError_t launch_regressions(const Geom& g, const EstStats<T>& st, const int32_t* halo,
+                               int64_t nitems, const Block* blocks, T* Tout, T* Dout,
+                               double ridge_c, int32_t* status, cudaStream_t s, int* nk) {
+  if (nitems <= 0) return cudaSuccess;
+  if (!st.C64) {
+    ++*nk;
+    return launch_regress<T, T>(g, st.U, st.C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
+                                0, s);
+  }
+  *nk += 2;
+  cudaError_t e = launch_regress<T, T>(g, st.U, st.C, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                       status, 1, s);
+  if (e != cudaSuccess) return e;
+  return launch_regress<double, T>(g, st.U64, st.C64, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                   status, 2, s);
+}
+
+template <typename T>
+cudaError_t launch_adj_regressions(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                                   const EstStats<T>& st, const T* Tg, const T* Dg, const T* Te,
+                                   const T* De, const T* aT, const T* bT, const T* dxT,
+                                   const T* lamT, const int2* ptab, const uint16_t* gtab, T* Ubar,
+                                   double ridge_c, int32_t* status, cudaStream_t s, int* nk) {
+  if (!st.C64) {
+    ++*nk;
+    return launch_adj_regress<T, T>(g, blocks, nblock, nb_max, st.U, st.C, Tg, Dg, Te, De, aT, bT,
+                                    dxT, lamT, ptab, gtab, Ubar, ridge_c, status, 0, s);
+  }
+  *nk += 2;
+  cudaError_t e = launch_adj_regress<T, T>(g, blocks, nblock, nb_max, st.U, st.C, Tg, Dg, Te, De,
+                                           aT, bT, dxT, lamT, ptab, gtab, Ubar, ridge_c, status,
+                                           1, s);
+  if (e != cudaSuccess) return e;
+  return launch_adj_regress<double, T>(g, blocks, nblock, nb_max, st.U64, st.C64, Tg, Dg, Te, De,
+                                       aT, bT, dxT, lamT, ptab, gtab, Ubar, ridge_c, status, 2, s);
+}
+
 #define INST(T)                                                                                  \
-  template cudaError_t launch_adj_regress<T>(const Geom&, const Block*, int, int, const T*,     \
-                                             const T*, const T*, const T*, const T*, const T*,  \
-                                             const T*, const T*, const T*, const T*,           \
-                                             const int2*, const uint16_t*, T*, double, int32_t*, \
-                                             cudaStream_t);                            \
   template cudaError_t launch_anomalies<T>(const Geom&, const T*, T*, cudaStream_t);            \
   template cudaError_t launch_covtable<T>(const Geom&, const T*, T*, cudaStream_t);             \
-  template cudaError_t launch_regress<T>(const Geom&, const T*, const T*, const int32_t*,       \
-                                         int64_t, const Block*, T*, T*, double, int32_t*,       \
-                                         cudaStream_t);
+  template cudaError_t launch_stat_anomalies<T>(const Geom&, const T*, const EstStats<T>&,      \
+                                                cudaStream_t, int*);                             \
+  template cudaError_t launch_stat_covtables<T>(const Geom&, const EstStats<T>&, cudaStream_t,  \
+                                                int*);                                           \
+  template cudaError_t launch_regressions<T>(const Geom&, const EstStats<T>&, const int32_t*,   \
+                                             int64_t, const Block*, T*, T*, double, int32_t*,    \
+                                             cudaStream_t, int*);                                \
+  template cudaError_t launch_adj_regressions<T>(                                               \
+      const Geom&, const Block*, int, int, const EstStats<T>&, const T*, const T*, const T*,     \
+      const T*, const T*, const T*, const T*, const T*, const int2*, const uint16_t*, T*, double, \
+      int32_t*, cudaStream_t, int*);
 INST(float)
 INST(double)
 #undef INST

@@ -1,9 +1,12 @@
-// One step of iterative refinement of the sub-domain solves (Eq. 11) in the
+// Iterative refinement of the sub-domain solves (Eq. 11) in the
 // single-precision path: r = rhs - A dX with A = T^T D^-1 T + H^T R^-1 H applied
 // in its factored form, every product and sum carried as a double-float pair
 // (FMA two-product, two-sum), so that the residual is exact to about 2^-44
 // relative to the terms; the correction A c = r is then solved with the same
-// single-precision factor and Xa = Xb + dX + c.
+// single-precision factor.  Each step but the last adds c into dX
+// (k_accumulate); after the last, Xa = Xb + dX + c.  The right-hand side is
+// Eq. 11's H^T R^-1 (Y^s - H X^b), formed here from the observations, or a
+// given array (the reverse pass refines Lambda = A^-1 W the same way).
 //
 // Pass 1 (k_whiten): v_j = (T dX)_j / D_j for every extended row j, member m.
 // Pass 2 (k_residual): r_a = rhs_a - dX_a / R_a - sum_{j: a in row j} T[j][a] v_j,
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
     const float* __restrict__ R, const float* __restrict__ Z, const float* __restrict__ Tg,
     const float* __restrict__ Dg, const float* __restrict__ Te, const float* __restrict__ De,
     const float* __restrict__ dX, const float* __restrict__ vhi, const float* __restrict__ vlo,
-    float* __restrict__ res) {
+    const float* __restrict__ rhs_in, float* __restrict__ res) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int pmax = g.pmax;
   int* cand = reinterpret_cast<int*>(smem);                  // [kRows][pmax] row j or -1
@@ -231,10 +234,11 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
     for (int u = 0; u < kMB; ++u) {
       const int m = min(m0 + u, g.N - 1);
       base[u] = b.row_off * g.N + (int64_t)m * b.nb;
-      s[u] = 0.f;
+      s[u] = rhs_in ? rhs_in[base[u] + a] : 0.f;
       c[u] = 0.f;
       if (o >= 0) {
-        s[u] = rhs_entry(yo, sq, Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l], rinv);
+        if (!rhs_in)
+          s[u] = rhs_entry(yo, sq, Z[(int64_t)m * mobs + o], Xb[(int64_t)m * g.n + l], rinv);
         ff_add_prod(s[u], c[u], -dX[base[u] + a], rinv);
       }
       ff_add(s[u], c[u], -vhi[base[u] + a]);
@@ -256,14 +260,29 @@ __global__ void __launch_bounds__(kRows* kWarps) k_residual(
   }
 }
 
+__global__ void __launch_bounds__(256) k_accumulate(float* __restrict__ y,
+                                                    const float* __restrict__ x, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
 }  // namespace
+
+cudaError_t launch_accumulate(float* y, const float* x, int64_t count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  int64_t grid = (count + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_accumulate<<<(unsigned)grid, 256, 0, s>>>(y, x, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                    const int32_t* obs_of, int64_t m, const float* Xb,
                                    const float* y, const float* R, const float* Z,
                                    const float* Tg, const float* Dg, const float* Te,
                                    const float* De, const float* dX, float* vhi, float* vlo,
-                                   float* res, cudaStream_t s) {
+                                   const float* rhs_in, float* res, cudaStream_t s) {
   const dim3 grid((nb_max + kRows - 1) / kRows, nblock);
   const size_t sm1 = (size_t)kRows * g.pmax * 8 + kRows * 4 + 3 * g.pmax;
   const size_t sm2 = (size_t)kRows * g.pmax * 8 + kRows * 4 + 8 + kRows * 8 + 3 * g.pmax;
@@ -271,7 +290,7 @@ cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nbloc
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_residual<<<grid, kRows * kWarps, sm2, s>>>(g, blocks, obs_of, m, Xb, y, R, Z, Tg, Dg, Te, De,
-                                               dX, vhi, vlo, res);
+                                               dX, vhi, vlo, rhs_in, res);
   return cudaGetLastError();
 }
 

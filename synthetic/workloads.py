@@ -92,6 +92,10 @@ SMALL_R1 = Workload(
     r=1, N=32, sub_lon=8, sub_lat=6, sigma2=(1.0,), corr_len=2.0,
     obs="random", obs_frac=0.3, seed=7100)
 
+# Same grid with N = 16: p > N / 2 on most rows (the rows a single-precision
+# problem regresses in double precision); p <= 14 < N - 1, so no ridge.
+SMALL_R1_N16 = SMALL_R1.with_(name="small_28x20x3x1_n16_r1", N=16, seed=7110)
+
 # Ridge active: p >= N - 1 for most rows (r = 3 with N = 24).
 SMALL_RIDGE = Workload(
     name="small_36x24x2x1_n24_r3_ridge", nlon=36, nlat=24, nlev=2, nvar_3d=1, nvar_2d=0,
@@ -105,4 +109,5 @@ SMALL_T63 = Workload(
     obs="random", obs_frac=0.5, r_frac=0.01, seed=7300)
 
 WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96,
-                                 SMALL_3D, SMALL_ILL, SMALL_R1, SMALL_RIDGE, SMALL_T63)}
+                                 SMALL_3D, SMALL_ILL, SMALL_R1, SMALL_R1_N16, SMALL_RIDGE,
+                                 SMALL_T63)}

@@ -74,3 +74,33 @@ def test_strings_and_no_device_status(lib):
     # a NULL handle is rejected, not dereferenced
     assert lib.enkfmc_estimate(None, None, None, None) == 1
     assert lib.enkfmc_get_status(None, None) == 1
+
+
+def test_noalloc_refuses_unsupported_geometry_before_any_cuda_call(lib):
+    """enkfmc_estimate_noalloc validates the problem before it touches the device or
+    the pointers: extents whose products reach 2^31 labels, a vertical reach that
+    would overflow the stencil, too many stencil slots, members out of range, and
+    scratch beyond 16 MiB all return EINVAL (pointers are dummies, never read)."""
+    from paper_1606_00807_gb300 import binding as B
+    P = lambda **k: B.enkfmc_problem(k.get("nlon", 32), k.get("nlat", 16), k.get("nlev", 1),
+                                     k.get("n3", 1), k.get("n2", 0), 1, k.get("r", 2),
+                                     k.get("vr", 1), k.get("N", 20), 8, 8, k.get("prec", B.FP32),
+                                     0.0, 0)
+    bad = [P(nlon=65536, nlat=65536),                      # nlon * nlat >= 2^31
+           P(nlon=1024, nlat=1024, nlev=1024, n3=2),       # n = 2^31
+           P(nlon=2048, nlat=2048, nlev=1024),             # nlon * nlat * nlev >= 2^31
+           P(nlon=5, nlat=5, nlev=300, vr=300, r=1),       # 299 levels of (2r+1)^2 slots
+           P(nlon=40, r=16, vr=0),                         # 560 stencil slots
+           P(N=129), P(N=1), P(r=-1), P(prec=7),
+           P(nlon=96, nlat=73, nlev=3, N=80)]              # 16,987,392 bytes of scratch
+    for prob in bad:
+        assert lib.enkfmc_estimate_noalloc(ctypes.byref(prob), 1, 1, 1, None) == 1
+    assert lib.enkfmc_estimate_noalloc(None, 1, 1, 1, None) == 1
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:   # valid and within the limit: passes validation, then finds no device
+        ok = P(nlon=96, nlat=72, nlev=3, N=80)
+        assert lib.enkfmc_estimate_noalloc(ctypes.byref(ok), 1, 1, 1, None) == 7

@@ -16,9 +16,11 @@ from _harness import (TOL, compare_T_rows, gpu_pipeline, max_block_condition, np
 
 pytestmark = pytest.mark.gpu
 
-# well-conditioned sub-domain systems (kappa <= 6e3): both precisions, fixed tolerances
+# both precisions at the fixed tolerances: sub-domain systems with kappa <= 6e3,
+# and the N = 16, r = 1 case (p > N / 2 on most rows: regressions in double
+# precision inside the single-precision path; kappa 1e7, four refinement steps)
 SMALL = ["small_48x26x3x1+1_n80_r2", "small_40x30x2x2+1_n48_r2", "tiny_32x16_n20_r2",
-         "small_28x20x3x1_n32_r1"]
+         "small_28x20x3x1_n32_r1", "small_28x20x3x1_n16_r1"]
 # p >= N - 1 on most rows (ridge): kappa 7e6 and 1.5e11
 ILL = ["small_36x24x2x1_n24_r3_ridge", "small_40x30x2x2+1_n24_r2_ill"]
 EPS64 = 2.0 ** -52
@@ -57,17 +59,19 @@ def _parity(name, precision, tol_x=None, flags=0):
     rows = np.arange(g.n)
     ref = O.estimate_rows(g, U, rows, w.ridge_c)
     eT, eD, eDe = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
-    assert eT < tol, eT
-    assert eD < tol, eD
-    assert eDe < tol, eDe
     # steps (b)-(c): the analysis ensemble and its increment
     Xa_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
     Xb = inp.Xb.astype(np.float64)
     lab = np.arange(w.n)
     eX = per_variable_err(w, lab, out["Xa"].T, Xa_ref.T)
     edX = per_variable_err(w, lab, (out["Xa"] - Xb).T, (Xa_ref - Xb).T)
+    print(f"\nparity {name} precision={precision} flags={flags}: T {eT:.2e} D {eD:.2e} "
+          f"D(elementwise) {eDe:.2e} Xa {eX:.2e} dX {edX:.2e}")
+    assert eT < tol, eT
+    assert eD < tol, eD
+    assert eDe < tol, eDe
     assert eX < tol_x, eX
-    assert edX < 10 * tol_x, edX
+    assert edX < tol_x, edX
     out["handle"].close()
 
 
@@ -116,26 +120,55 @@ def test_ill_conditioned_fp64_parity(name):
     _parity(name, 0, tol_x=1e-9 + 50.0 * kappa * EPS64)
 
 
-@pytest.mark.parametrize("name", ILL)
-def test_ill_conditioned_fp32_status_or_bounded(name):
-    """Single precision cannot promise the 1e-5 target here (kappa * 2^-24 ~ 0.4 to
-    1e4).  The library must either report ENOTSPD / EDNONPOS through the status
-    word (no trap), or return finite results with T and D at the FP32 tolerance
-    and an analysis within the first-order bound kappa * 2^-24 of a backward-stable
-    single-precision solve."""
+def test_ridge_fp32_parity():
+    """The ridge case (p >= N - 1 on most rows, block condition numbers near 7e6) in
+    single precision at the fixed FP32 tolerance: its regressions run in double
+    precision (2p > N) and its sub-domain solves take four refinement steps."""
+    _parity("small_36x24x2x1_n24_r3_ridge", 1)
+
+
+def test_ill_fp32_estimate_parity_and_factor_status():
+    """N = 24, r = 2 on the 40 x 30 grid: block condition numbers up to 1.5e11, beyond
+    what a single-precision factorisation can hold (kappa 2^-24 ~ 9e3).  The estimate
+    (regressions in double precision, 2p > N) matches the oracle at the FP32
+    tolerance; the analysis either reports ENOTSPD through the status word (a pivot
+    that single precision cannot keep positive, no trap) or, when every pivot stays
+    positive, matches at the FP32 tolerance after its refinement steps."""
     from paper_1606_00807_gb300 import binding as B
-    w = WORKLOADS[name]
-    kappa = max_block_condition(w, make_inputs(w, np.float64))
+    name = "small_40x30x2x2+1_n24_r2_ill"
     try:
-        _parity(name, 1, tol_x=max(1e-5, kappa * 2.0 ** -24))
+        _parity(name, 1)
     except B.EnkfmcError as e:
-        assert e.code in (3, 4), e
+        assert e.code == 3, e
+        # the failure is the factorisation's, not the estimate's: T and D still match
+        import torch
+        w = WORKLOADS[name]
+        inp = make_inputs(w, np.float32)
+        h = B.Handle.from_workload(w, precision=B.FP32,
+                                   stream=torch.cuda.current_stream().cuda_stream)
+        Xb = torch.from_numpy(inp.Xb).cuda()
+        T = torch.empty((w.n, h.info.pmax), device="cuda", dtype=torch.float32)
+        D = torch.empty(w.n, device="cuda", dtype=torch.float32)
+        h.estimate(Xb, T, D)
+        h.check("estimate")
+        g = O.Grid.from_workload(w)
+        rows = np.arange(g.n)
+        ref = O.estimate_rows(g, O.anomalies(inp.Xb.T), rows, w.ridge_c)
+        eT, eD, eDe = compare_T_rows(w, h, T.cpu().numpy().astype(np.float64),
+                                     D.cpu().numpy().astype(np.float64), rows, ref)
+        print(f"\nill fp32 estimate: T {eT:.2e} D {eD:.2e} D(elementwise) {eDe:.2e}")
+        assert max(eT, eD, eDe) < TOL[1], (eT, eD, eDe)
+        h.close()
 
 
-def test_full_t63_sampled_fp32():
-    """T63 shape, N = 80, FP32, the configuration the benchmark times: sampled T
-    rows and D entries, and three sampled sub-domains of the analysis."""
-    w = WORKLOADS["t63_192x96x29_n80_r2"]
+@pytest.mark.parametrize("name", ["t63_192x96x29_n80_r2", "t63_192x96x29_n40_r2"])
+def test_full_t63_sampled_fp32(name):
+    """T63 shape, FP32, in the launch configuration the benchmark times: sampled T
+    rows and D entries, and three sampled sub-domains of the analysis.  N = 80 is
+    the headline workload; N = 40 (p = 37 of 39 degrees of freedom on interior
+    rows) is the forward + adjoint workload, whose regressions run in double
+    precision and whose solves take four refinement steps."""
+    w = WORKLOADS[name]
     inp = make_inputs(w, np.float32)
     out = gpu_pipeline(w, inp, 1)
     g = O.Grid.from_workload(w)
@@ -147,6 +180,7 @@ def test_full_t63_sampled_fp32():
          g.offsets[1] - 1, g.label(2, 3, 47, 191), g.label(3, 6, 95, 0)]]))
     ref = O.estimate_rows(g, U, rows, w.ridge_c)
     eT, eD, eDe = compare_T_rows(w, out["handle"], out["T"], out["D"], rows, ref)
+    print(f"\n{name} sampled rows: T {eT:.2e} D {eD:.2e} D(elementwise) {eDe:.2e}")
     assert eT < TOL[1], eT
     assert eD < TOL[1], eD
     assert eDe < TOL[1], eDe
@@ -161,8 +195,9 @@ def test_full_t63_sampled_fp32():
         got = out["Xa"][:, lab].T
         eX = per_variable_err(w, lab, got, Xa_ref[lab])
         edX = per_variable_err(w, lab, got - inp.Xb[:, lab].T, Xa_ref[lab] - inp.Xb[:, lab].T)
+        print(f"{name} sub-domain {i}: Xa {eX:.2e} dX {edX:.2e}")
         assert eX < TOL[1], (i, eX)
-        assert edX < 10 * TOL[1], (i, edX)
+        assert edX < TOL[1], (i, edX)
     out["handle"].close()
 
 
