@@ -175,7 +175,12 @@ enkfmc_status enkfmc_estimate(enkfmc_handle* h, const void* Xb, void* Tvals, voi
 /* Step (b), Algorithm 3 and Eq. 11: for every sub-domain re-estimate the
  * boundary rows of its extended set from the local samples (predecessors
  * cut to the extended set), assemble A = T^T D^-1 T + H^T R^-1 H in band
- * storage per (sub-domain, variable) block and factor it.  Xb: [N][n]
+ * storage per (sub-domain, variable) block and factor it.  In single
+ * precision a block whose factorisation meets a non-positive pivot (a
+ * condition number beyond what single precision holds) is assembled again
+ * from the same T and D in double precision and factored, and later solved,
+ * in double; ENOTSPD is reported only if that fails too, or if more than
+ * max(8, nblock / 8) blocks need it.  Xb: [N][n]
  * (when it is the same pointer as in the last enkfmc_estimate on this
  * handle, the anomalies and covariances computed there are reused, so its
  * contents must not change in between);
@@ -216,6 +221,10 @@ enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void*
  * the last call (and clear it).  info (host, nullable) receives the index of
  * the failing row or block. */
 enkfmc_status enkfmc_get_status(enkfmc_handle* h, int64_t* info);
+
+/* Number of blocks the last enkfmc_assemble factored in double precision
+ * (single-precision handles; 0 otherwise).  Synchronises the stream. */
+enkfmc_status enkfmc_fp64_blocks(enkfmc_handle* h, int32_t* count /* host */);
 
 /* Strictly-lower pattern of the global T as CSR in label order (host arrays:
  * rowptr [n+1]; colidx [rowptr[n]], or NULL to query the count via
@@ -273,7 +282,9 @@ enum {
   ENKFMC_K_ADJOINT = 10,    /* reverse pass: seed, observation terms, T Lambda,
                                T dX, anomaly projection                          */
   ENKFMC_K_ADJ_REGRESS = 11,/* reverse pass through the regressions              */
-  ENKFMC_NKERNEL = 12
+  ENKFMC_K_FP64_BLOCKS = 12,/* single precision: the blocks whose factorisation
+                               failed, assembled and factored in double          */
+  ENKFMC_NKERNEL = 13
 };
 
 /* Kernel timing.  Work is launched in calls of one kernel kind; a call runs

@@ -54,6 +54,7 @@ SIGNATURES = {
     "enkfmc_analyze_adjoint": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_get_status": (c_int32, [_H, POINTER(c_int64)]),
     "enkfmc_export_T_pattern": (c_int32, [_H, c_void_p, c_void_p]),
+    "enkfmc_fp64_blocks": (c_int32, [_H, POINTER(c_int32)]),
     "enkfmc_debug_block": (c_int32, [_H, c_int32, c_void_p, c_int64, POINTER(c_int64),
                                      POINTER(c_int32)]),
     "enkfmc_profile": (c_int32, [_H, c_int32]),
@@ -63,7 +64,7 @@ SIGNATURES = {
     "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
                                           c_void_p]),
 }
-NKERNEL = 12
+NKERNEL = 13
 FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
 FLAG_REFINE_MASK = 0xF00
@@ -201,6 +202,12 @@ class Handle:
         info = c_int64(0)
         code = self.lib.enkfmc_get_status(self.h, ctypes.byref(info))
         return int(code), int(info.value)
+
+    def fp64_blocks(self) -> int:
+        """Blocks the last assemble factored in double precision (synchronises)."""
+        c = c_int32(0)
+        _check(self.lib.enkfmc_fp64_blocks(self.h, ctypes.byref(c)), "enkfmc_fp64_blocks")
+        return int(c.value)
 
     def check(self, where="device status"):
         code, info = self.get_status()

@@ -52,9 +52,13 @@ __device__ __forceinline__ void load_panel(const T* __restrict__ AB, int ld, int
 // Left-looking Cholesky of the staged panel, one thread per row: column t
 // takes the products of the finished columns u < t, then its pivot.  Writes
 // 1 / L[c0+t][c0+t] to inv_out[t] when inv_out is not null.  Returns false
-// (the same value in every thread) after recording ENOTSPD / ENONFINITE.
+// (the same value in every thread) at a pivot that is not positive: a finite
+// one sets bfail[id] when bfail is given (the block is factored again in
+// double precision), else records ENOTSPD; a non-finite one records
+// ENONFINITE.
 template <typename T>
-__device__ bool factor_panel(T* P, int ldP, int nbc, int rows, T* inv_out, int32_t* status) {
+__device__ bool factor_panel(T* P, int ldP, int nbc, int rows, T* inv_out, int32_t* status,
+                             int* bfail, int id) {
   const int tid = threadIdx.x;
   for (int t = 0; t < nbc; ++t) {
     for (int i = t + tid; i < rows; i += blockDim.x) {
@@ -65,9 +69,10 @@ __device__ bool factor_panel(T* P, int ldP, int nbc, int rows, T* inv_out, int32
     __syncthreads();
     T dg = P[t * ldP + t];
     if (!finite_val(dg) || !(dg > T(0))) {
-      if (tid == 0)
-        record_error(status, finite_val(dg) ? ENKFMC_ENOTSPD : ENKFMC_ENONFINITE,
-                     (int64_t)blockIdx.x);
+      if (tid == 0) {
+        if (bfail && finite_val(dg)) bfail[id] = 1;
+        else record_error(status, finite_val(dg) ? ENKFMC_ENOTSPD : ENKFMC_ENONFINITE, (int64_t)id);
+      }
       return false;
     }
     dg = sqrt(dg);

@@ -175,6 +175,7 @@ enkfmc_status build(enkfmc_handle* h) {
         bb.row_off = row_off;
         bb.band_off = band_off;
         const int blk = (int)h->blocks.size();
+        bb.id = blk;
         for (int loc = 0; loc < bb.nb; ++loc) {
           const int plane = bb.ey * bb.ex;
           const int k = loc / plane;
@@ -304,6 +305,15 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_invdiag, h->esize * h->ext_rows))) return st;
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
   if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
+  if (!is_fp64(h)) {  // double-precision pool for blocks whose FP32 factorisation fails
+    h->fb_cap = std::max(8, h->nblock / 8);
+    h->fb_stride = (int64_t)h->nb_max * (h->hb_max + 1);
+    if ((st = dalloc(h, &h->d_bfail, sizeof(int32_t) * h->nblock))) return st;
+    if ((st = dalloc(h, &h->d_fb_cnt, sizeof(int32_t)))) return st;
+    if ((st = dalloc(h, &h->d_fb_blocks, sizeof(Block) * h->fb_cap))) return st;
+    if ((st = dalloc(h, &h->d_fb_band, sizeof(double) * h->fb_cap * h->fb_stride))) return st;
+    CUDA_TRY(cudaMemset(h->d_fb_cnt, 0, sizeof(int32_t)));
+  }
   if (has_fp64_rows(g, !is_fp64(h))) {
     if ((st = dalloc(h, &h->d_U64, sizeof(double) * g.n * g.ldN))) return st;
     if ((st = dalloc(h, &h->d_C64, sizeof(double) * (size_t)g.n * cov_offset_count(g.r, g.vr))))
@@ -366,7 +376,8 @@ void release(enkfmc_handle* h) {
                   h->d_band,  h->d_invdiag, h->d_rhs, h->d_res,     h->d_vhi,    h->d_vlo,
                   h->d_Xb,    h->d_y,       h->d_R,   h->d_Z,       h->d_Xa,     h->d_T,
                   h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
-                  h->d_Ubar,  h->d_U64,     h->d_C64, h->d_W};
+                  h->d_Ubar,  h->d_U64,     h->d_C64, h->d_W,      h->d_bfail,  h->d_fb_cnt,
+                  h->d_fb_blocks, h->d_fb_band};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
@@ -474,24 +485,67 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
                               h->stream, h->hb_max);
   });
   if (st) return st;
-  return timed(h, ENKFMC_K_BANDCHOL, [&] {
-    if (sizeof(T) == sizeof(float) && h->tc_chol)
-      return launch_bandchol_tc(h->d_blocks, h->nblock, h->hb_max, (float*)h->d_band,
-                                (float*)h->d_invdiag, h->d_status, h->stream);
-    return launch_bandchol<T>(h->d_blocks, h->nblock, h->hb_max, (T*)h->d_band,
-                              (T*)h->d_invdiag, h->d_status, h->stream);
-  });
+  if constexpr (std::is_same<T, double>::value) {
+    return timed(h, ENKFMC_K_BANDCHOL, [&] {
+      return launch_bandchol<T>(h->d_blocks, h->nblock, h->hb_max, (T*)h->d_band,
+                                (T*)h->d_invdiag, h->d_status, h->stream);
+    });
+  } else {
+    // single precision: blocks whose factorisation meets a non-positive pivot
+    // are flagged, assembled again from the same T and D in double precision,
+    // and factored in double (their solves too)
+    CUDA_TRY(cudaMemsetAsync(h->d_bfail, 0, sizeof(int32_t) * h->nblock, h->stream));
+    st = timed(h, ENKFMC_K_BANDCHOL, [&] {
+      if (h->tc_chol)
+        return launch_bandchol_tc(h->d_blocks, h->nblock, h->hb_max, (float*)h->d_band,
+                                  (float*)h->d_invdiag, h->d_status, h->stream, h->d_bfail);
+      return launch_bandchol<float>(h->d_blocks, h->nblock, h->hb_max, (float*)h->d_band,
+                                    (float*)h->d_invdiag, h->d_status, h->stream, nullptr,
+                                    h->d_bfail);
+    });
+    if (st) return st;
+    return timed(h, ENKFMC_K_FP64_BLOCKS, [&](int* nk) {
+      *nk += 3;
+      cudaError_t e = launch_fallback_list(h->d_blocks, h->nblock, h->d_bfail, h->d_fb_blocks,
+                                           h->d_fb_cnt, h->fb_cap, h->fb_stride, h->d_status,
+                                           h->stream);
+      if (e != cudaSuccess) return e;
+      e = launch_assemble<float, double>(h->g, h->d_fb_blocks, h->fb_cap, h->nb_max,
+                                         (const float*)Tv, (const float*)D,
+                                         (const float*)h->d_Te, (const float*)h->d_De,
+                                         h->d_obs_of, (const float*)R, h->d_fb_band, h->d_status,
+                                         h->stream, h->hb_max, h->d_fb_cnt);
+      if (e != cudaSuccess) return e;
+      return launch_bandchol<double>(h->d_fb_blocks, h->fb_cap, h->hb_max, h->d_fb_band, nullptr,
+                                     h->d_status, h->stream, h->d_fb_cnt, nullptr);
+    });
+  }
 }
 
-// L L^T X = B in place for every block, N members (Eq. 11).
+// L L^T X = B in place for every block, N members (Eq. 11).  Single
+// precision: the blocks factored in double precision are solved in double
+// (their rhs stays single precision), the others on the tensor or CUDA cores.
 template <typename T>
-cudaError_t solve_band(enkfmc_handle* h, T* rhs) {
-  if (sizeof(T) == sizeof(float) && h->tc_solve)
-    return launch_bandsolve_tc(h->d_blocks, h->nblock, h->hb_max, h->g.N,
-                               (const float*)h->d_band, (const float*)h->d_invdiag,
-                               (float*)rhs, h->d_status, h->stream);
-  return launch_bandsolve<T>(h->d_blocks, h->nblock, h->hb_max, h->g.N, (const T*)h->d_band, rhs,
-                             h->stream);
+cudaError_t solve_band(enkfmc_handle* h, T* rhs, int* nk) {
+  ++*nk;
+  if constexpr (std::is_same<T, double>::value) {
+    return launch_bandsolve<double, double>(h->d_blocks, h->nblock, h->hb_max, h->g.N,
+                                            (const double*)h->d_band, rhs, h->stream);
+  } else {
+    cudaError_t e;
+    if (h->tc_solve)
+      e = launch_bandsolve_tc(h->d_blocks, h->nblock, h->hb_max, h->g.N, (const float*)h->d_band,
+                              (const float*)h->d_invdiag, rhs, h->d_status, h->stream,
+                              h->d_bfail);
+    else
+      e = launch_bandsolve<float, float>(h->d_blocks, h->nblock, h->hb_max, h->g.N,
+                                         (const float*)h->d_band, rhs, h->stream, nullptr,
+                                         h->d_bfail);
+    if (e != cudaSuccess) return e;
+    ++*nk;
+    return launch_bandsolve<double, float>(h->d_fb_blocks, h->fb_cap, h->hb_max, h->g.N,
+                                           h->d_fb_band, rhs, h->stream, h->d_fb_cnt, nullptr);
+  }
 }
 
 template <typename T>
@@ -502,8 +556,8 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
                          (T*)h->d_rhs, h->stream);
   });
   if (st) return st;
-  st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-    return solve_band<T>(h, (T*)h->d_rhs);
+  st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) {
+    return solve_band<T>(h, (T*)h->d_rhs, nk);
   });
   if (st) return st;
   const T* corr = nullptr;
@@ -526,8 +580,8 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
             (float*)h->d_res, h->stream);
       });
       if (st) return st;
-      st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-        return solve_band<T>(h, (T*)h->d_res);
+      st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) {
+        return solve_band<T>(h, (T*)h->d_res, nk);
       });
       if (st) return st;
     }
@@ -657,8 +711,8 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
   T* Wres = refine ? (T*)h->d_W + nrhs : nullptr;
   if (refine)
     CUDA_TRY(cudaMemcpyAsync(W, h->d_lam, sizeof(T) * nrhs, cudaMemcpyDeviceToDevice, h->stream));
-  st = timed(h, ENKFMC_K_BANDSOLVE, [&] {
-    return solve_band<T>(h, (T*)h->d_lam);
+  st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) {
+    return solve_band<T>(h, (T*)h->d_lam, nk);
   });
   if (st) return st;
   // Lambda = A^-1 W refined with the forward solve's steps (A is the same)
@@ -673,7 +727,7 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
           (float*)Wres, h->stream);
     });
     if (st) return st;
-    st = timed(h, ENKFMC_K_BANDSOLVE, [&] { return solve_band<T>(h, Wres); });
+    st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) { return solve_band<T>(h, Wres, nk); });
     if (st) return st;
     st = timed(h, ENKFMC_K_RESIDUAL, [&] {
       return launch_accumulate((float*)h->d_lam, (const float*)Wres, nrhs, h->stream);
@@ -918,6 +972,15 @@ enkfmc_status enkfmc_get_status(enkfmc_handle* h, int64_t* info) {
   return (enkfmc_status)st[0];
 }
 
+enkfmc_status enkfmc_fp64_blocks(enkfmc_handle* h, int32_t* count) {
+  if (!h || !count) return ENKFMC_EINVAL;
+  *count = 0;
+  if (!h->d_fb_cnt) return ENKFMC_OK;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  CUDA_TRY(cudaMemcpy(count, h->d_fb_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return ENKFMC_OK;
+}
+
 enkfmc_status enkfmc_export_T_pattern(const enkfmc_handle* h, int64_t* rowptr, int32_t* colidx) {
   if (!h || !rowptr) return ENKFMC_EINVAL;
   const Geom& g = h->g;
@@ -986,7 +1049,8 @@ const char* enkfmc_kernel_name(int32_t kind) {
   static const char* names[ENKFMC_NKERNEL] = {"anomalies", "regress",   "regress_halo",
                                               "assemble",  "bandchol",  "rhs",
                                               "bandsolve", "writeback", "covtable",
-                                              "residual",  "adjoint",   "adj_regress"};
+                                              "residual",  "adjoint",   "adj_regress",
+                                              "fp64_blocks"};
   return (kind >= 0 && kind < ENKFMC_NKERNEL) ? names[kind] : "unknown";
 }
 

@@ -27,6 +27,7 @@ struct Geom {
 // One (sub-domain, variable) block of the extended set.  Local index of a
 // component: loc = (k * ey + (lat - lat_lo)) * ex + ((lon - lon_lo) mod nlon).
 struct Block {
+  int32_t id;                      // index of the block in the handle's list
   int32_t sub, var, nlev_b;
   int32_t lat_lo, ey, lon_lo, ex;  // extended box (ex == nlon: the whole ring)
   int32_t lat0, lat1, lon0, lon1;  // interior tile (absolute, lon1 <= nlon)
@@ -245,6 +246,14 @@ struct enkfmc_handle {
   bool tc_chol = false;   // FP32 band Cholesky updates on the tensor cores
   bool refine_solve = false;
   int refine_steps = 0;   // refinement steps of every sub-domain solve (FP32)
+  // FP32: blocks whose single-precision factorisation meets a non-positive
+  // pivot are assembled, factored and solved again in double precision
+  int32_t* d_bfail = nullptr;         // [nblock] failure flags of the last factorisation
+  int32_t* d_fb_cnt = nullptr;        // blocks in the double-precision pool
+  enkfmc::Block* d_fb_blocks = nullptr;  // [fb_cap] their entries, band_off in the pool
+  double* d_fb_band = nullptr;        // [fb_cap][fb_stride] their bands and factors
+  int32_t fb_cap = 0;
+  int64_t fb_stride = 0;
   const void* T_assembled = nullptr;  // global T/D used by the last assemble
   const void* D_assembled = nullptr;
   bool assembled = false;
@@ -342,11 +351,13 @@ cudaError_t launch_regressions(const Geom& g, const EstStats<T>& st, const int32
                                int64_t nitems, const Block* blocks, T* Tout, T* Dout,
                                double ridge_c, int32_t* status, cudaStream_t s, int* nk);
 
-template <typename T>
+// General band assembly (any block); TB the band's type (double for the
+// double-precision pass over failed blocks, cnt their device count).
+template <typename T, typename TB = T>
 cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
                             const T* Tg, const T* Dg, const T* Te, const T* De,
-                            const int32_t* obs_of, const T* R, T* band, int32_t* status,
-                            cudaStream_t s, int hb_max);
+                            const int32_t* obs_of, const T* R, TB* band, int32_t* status,
+                            cudaStream_t s, int hb_max, const int* cnt = nullptr);
 
 // Band assembly from per-shape slot-pair lists (blocks whose extended box does
 // not wrap onto itself in longitude).
@@ -362,18 +373,31 @@ size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_
                            int box_sum);
 
 // Factor every block in place; invdiag[row_off + c] = 1 / L[c][c] (may be null).
+// cnt (may be null): only the first *cnt of `blocks` (a device count); bfail
+// (may be null): a finite non-positive pivot sets bfail[block id] instead of
+// recording ENOTSPD.
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, T* invdiag,
-                            int32_t* status, cudaStream_t s);
+                            int32_t* status, cudaStream_t s, const int* cnt = nullptr,
+                            int* bfail = nullptr);
+// The failed blocks (bfail) into a list of `cap` double-precision pool slots of
+// `stride` elements each (band_off remapped), and their count *cnt.
+cudaError_t launch_fallback_list(const Block* blocks, int nblock, const int* bfail, Block* pool,
+                                 int* cnt, int cap, int64_t stride, int32_t* status,
+                                 cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_max,
                        const int32_t* obs_of, int64_t m, const T* Xb, const T* y, const T* R,
                        const T* Z, T* rhs, cudaStream_t s);
 
-template <typename T>
+// L L^T X = B for N members per block; T the factor's type, TR the rhs's.
+// cnt as for launch_bandchol; skip (may be null): blocks with skip[id] set
+// are left alone.
+template <typename T, typename TR>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
-                             T* rhs, cudaStream_t s);
+                             TR* rhs, cudaStream_t s, const int* cnt = nullptr,
+                             const int* skip = nullptr);
 
 // Single-precision band solves with the panel updates on the tensor cores
 // (k_band_tc.cu); usable when N <= 128 and the staged panels of a band of
@@ -383,10 +407,11 @@ bool bandsolve_tc_supported(int hb_max, int N);
 // (k_band_tc.cu); usable when 32 + hb_max <= 384.
 bool bandchol_tc_supported(int hb_max);
 cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, float* band,
-                               float* invdiag, int32_t* status, cudaStream_t s);
+                               float* invdiag, int32_t* status, cudaStream_t s,
+                               int* bfail = nullptr);
 cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int N,
                                 const float* band, const float* invdiag, float* rhs,
-                                int32_t* status, cudaStream_t s);
+                                int32_t* status, cudaStream_t s, const int* skip = nullptr);
 
 // Xa = Xb + dX (+ dX2 when not null) on sub-domain interiors.
 template <typename T>

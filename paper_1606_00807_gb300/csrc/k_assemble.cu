@@ -19,21 +19,27 @@ namespace enkfmc {
 
 namespace {
 
-template <typename T>
+// T: the type of T, D and R; TB: the band's type and the arithmetic (double
+// for the blocks whose single-precision factorisation failed: their A is
+// assembled again from the same single-precision T and D, in double).  cnt
+// (optional): only the first *cnt entries of `blocks`.
+template <typename T, typename TB>
 __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __restrict__ blocks,
                                                   const T* __restrict__ Tg, const T* __restrict__ Dg,
                                                   const T* __restrict__ Te, const T* __restrict__ De,
                                                   const int32_t* __restrict__ obs_of,
-                                                  const T* __restrict__ R, T* __restrict__ band,
-                                                  int32_t* status, int hbp1_max) {
+                                                  const T* __restrict__ R, TB* __restrict__ band,
+                                                  int32_t* status, int hbp1_max,
+                                                  const int* __restrict__ cnt) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  T* col = reinterpret_cast<T*>(smem) + (size_t)warp * hbp1_max;
+  TB* col = reinterpret_cast<TB*>(smem) + (size_t)warp * hbp1_max;
+  if (cnt && (int)blockIdx.y >= *cnt) return;
   const Block b = blocks[blockIdx.y];
   const int c = blockIdx.x * wpc + warp;
   if (c >= b.nb) return;
   const int hb = b.hb, pmax = g.pmax, nlon = g.nlon;
-  for (int d = lane; d <= hb; d += 32) col[d] = T(0);
+  for (int d = lane; d <= hb; d += 32) col[d] = TB(0);
   __syncwarp();
   const int plane = b.ey * b.ex;
   const int kc = c / plane;
@@ -69,9 +75,9 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
       trow = Te + (b.row_off + locj) * pmax;
       Dj = De[b.row_off + locj];
     }
-    const T tjc = (sj < 0) ? T(1) : trow[sj];
-    if (tjc == T(0)) continue;
-    const T scale = tjc / Dj;
+    const TB tjc = (sj < 0) ? TB(1) : (TB)trow[sj];
+    if (tjc == TB(0)) continue;
+    const TB scale = tjc / (TB)Dj;
     if (lane == 0) {
       const int d = locj - c;
       if (d >= 0) {
@@ -80,8 +86,8 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
       }
     }
     for (int s2 = lane; s2 < pmax; s2 += 32) {
-      const T tjb = trow[s2];
-      if (tjb == T(0)) continue;
+      const TB tjb = (TB)trow[s2];
+      if (tjb == TB(0)) continue;
       int kq, yq, xq, yyq, xxq;
       if (!slot_pred(g, kj, yj, xj, s2, kq, yq, xq) || !in_ext(b, nlon, yq, xq, yyq, xxq)) {
         record_error(status, ENKFMC_EINVAL, (int64_t)blockIdx.y);
@@ -97,11 +103,11 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
   }
   if (lane == 0) {
     const int o = obs_of[coords_label(g, v, kc, yc, xc)];
-    if (o >= 0) col[0] += T(1) / R[o];
+    if (o >= 0) col[0] += TB(1) / (TB)R[o];
   }
   __syncwarp();
-  T* out = band + b.band_off + (int64_t)c * (hb + 1);
-  for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : T(0);
+  TB* out = band + b.band_off + (int64_t)c * (hb + 1);
+  for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : TB(0);
 }
 
 // Band assembly of one tile of 32 NH columns of one block from the pair list
@@ -303,20 +309,20 @@ __global__ void __launch_bounds__(256) k_writeback(const Geom g, const Block* __
 
 }  // namespace
 
-template <typename T>
+template <typename T, typename TB>
 cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
                             const T* Tg, const T* Dg, const T* Te, const T* De,
-                            const int32_t* obs_of, const T* R, T* band, int32_t* status,
-                            cudaStream_t s, int hb_max) {
+                            const int32_t* obs_of, const T* R, TB* band, int32_t* status,
+                            cudaStream_t s, int hb_max, const int* cnt) {
   const int wpc = 8;
   const int hbp1 = hb_max + 1;
-  const size_t smem = sizeof(T) * (size_t)hbp1 * wpc;
-  cudaError_t e = cudaFuncSetAttribute(k_assemble<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const size_t smem = sizeof(TB) * (size_t)hbp1 * wpc;
+  cudaError_t e = cudaFuncSetAttribute(k_assemble<T, TB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
-  k_assemble<T><<<grid, 32 * wpc, smem, s>>>(g, blocks, Tg, Dg, Te, De, obs_of, R, band, status,
-                                             hbp1);
+  k_assemble<T, TB><<<grid, 32 * wpc, smem, s>>>(g, blocks, Tg, Dg, Te, De, obs_of, R, band,
+                                                 status, hbp1, cnt);
   return cudaGetLastError();
 }
 
@@ -371,9 +377,10 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
                                                 const int4*, const int32_t*, const T*, const T*,  \
                                                 const T*, const T*, const int32_t*, const T*, T*, \
                                                 int, cudaStream_t);                                \
-  template cudaError_t launch_assemble<T>(const Geom&, const Block*, int, int, const T*,        \
-                                          const T*, const T*, const T*, const int32_t*,         \
-                                          const T*, T*, int32_t*, cudaStream_t, int);           \
+  template cudaError_t launch_assemble<T, T>(const Geom&, const Block*, int, int, const T*,     \
+                                             const T*, const T*, const T*, const int32_t*,      \
+                                             const T*, T*, int32_t*, cudaStream_t, int,         \
+                                             const int*);                                        \
   template cudaError_t launch_rhs<T>(const Geom&, const Block*, int, int, const int32_t*,       \
                                      int64_t, const T*, const T*, const T*, const T*, T*,       \
                                      cudaStream_t);                                              \
@@ -382,5 +389,10 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
 INST(float)
 INST(double)
 #undef INST
+template cudaError_t launch_assemble<float, double>(const Geom&, const Block*, int, int,
+                                                    const float*, const float*, const float*,
+                                                    const float*, const int32_t*, const float*,
+                                                    double*, int32_t*, cudaStream_t, int,
+                                                    const int*);
 
 }  // namespace enkfmc

@@ -58,13 +58,18 @@ __device__ __forceinline__ void tri_tile(int idx, int nT, int& I, int& C) {
   I = C + (idx - (C * nT - C * (C - 1) / 2));
 }
 
+// cnt (optional): only the first *cnt entries of `blocks` are factored (the
+// double-precision pass over the blocks whose single-precision factorisation
+// failed); bfail (optional): per-block failure flags, see factor_panel.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__ blocks,
                                                        T* __restrict__ band,
                                                        T* __restrict__ invdiag, int32_t* status,
-                                                       int ldP) {
+                                                       int ldP, const int* __restrict__ cnt,
+                                                       int* __restrict__ bfail) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* P = reinterpret_cast<T*>(smem);  // [NB][ldP]: P[t*ldP + i] = A[c0+i][c0+t]
+  if (cnt && (int)blockIdx.x >= *cnt) return;
   const Block b = blocks[blockIdx.x];
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
   T* AB = band + b.band_off;
@@ -74,7 +79,8 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
     const int rows = min(nbc + hb, nb - c0);
     load_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     __syncthreads();
-    if (!factor_panel(P, ldP, nbc, rows, invdiag ? invdiag + b.row_off + c0 : nullptr, status))
+    if (!factor_panel(P, ldP, nbc, rows, invdiag ? invdiag + b.row_off + c0 : nullptr, status,
+                      bfail, b.id))
       return;  // uniform: every thread read the same pivot
     write_panel(AB, ld, hb, c0, nbc, rows, P, ldP);
     // trailing update of the window [c0+nbc, c0+rows)
@@ -143,12 +149,17 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
 // rows in shared memory (row i in slot i mod WR, WR a multiple of NB, so a
 // panel's own rows are contiguous slots); finished rows go back to global
 // memory and the next ones are read in their place.  The NB x NB diagonal
-// triangles are solved one member per thread in registers.
-template <typename T, int NMB>
+// triangles are solved one member per thread in registers.  T: the factor
+// and the arithmetic; TR: the right-hand sides (single-precision rhs of a
+// block factored in double).  cnt (optional): only the first *cnt entries of
+// `blocks`; skip (optional): blocks with skip[id] set are left to the
+// double-precision pass.
+template <typename T, typename TR, int NMB>
 __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __restrict__ blocks,
                                                         const T* __restrict__ band,
-                                                        T* __restrict__ rhs, int N, int ldP,
-                                                        int WRmax) {
+                                                        TR* __restrict__ rhs, int N, int ldP,
+                                                        int WRmax, const int* __restrict__ cnt,
+                                                        const int* __restrict__ skip) {
   constexpr int NMP = NMB + 4;
   extern __shared__ __align__(16) unsigned char smem[];
   T* P = reinterpret_cast<T*>(smem);   // [NB][ldP]
@@ -157,13 +168,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
   T* invd = Red + 4 * NB * NMB;        // [NB]
   // the member chunks of one block are consecutive thread blocks, so they run
   // together and share the factor through L2
+  if (cnt && (int)blockIdx.y >= *cnt) return;
   const Block b = blocks[blockIdx.y];
+  if (skip && skip[b.id]) return;
   const int m0 = blockIdx.x * NMB;
   const int nm = min(NMB, N - m0);
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
   const int WR = ((NB + hb + NB - 1) / NB) * NB;
   const T* AB = band + b.band_off;
-  T* B = rhs + b.row_off * N + (int64_t)m0 * nb;  // B[m * nb + i], m relative to m0
+  TR* B = rhs + b.row_off * N + (int64_t)m0 * nb;  // B[m * nb + i], m relative to m0
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
 
   // rows [r0, r0 + cnt) <-> slots starting at r0 mod WR (no wrap inside: cnt <= NB
@@ -171,12 +184,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
   auto load_rows = [&](int r0, int cnt) {
     const int sb = r0 % WR;
     for (int m = warp; m < nm; m += nw)
-      for (int i = lane; i < cnt; i += 32) Wn[(sb + i) * NMP + m] = B[(int64_t)m * nb + r0 + i];
+      for (int i = lane; i < cnt; i += 32) Wn[(sb + i) * NMP + m] = (T)B[(int64_t)m * nb + r0 + i];
   };
   auto store_rows = [&](int r0, int cnt) {
     const int sb = r0 % WR;
     for (int m = warp; m < nm; m += nw)
-      for (int i = lane; i < cnt; i += 32) B[(int64_t)m * nb + r0 + i] = Wn[(sb + i) * NMP + m];
+      for (int i = lane; i < cnt; i += 32) B[(int64_t)m * nb + r0 + i] = (TR)Wn[(sb + i) * NMP + m];
   };
   auto slot = [&](int base, int i) {
     const int sl = base + i;
@@ -356,35 +369,60 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
   }
 }
 
+// The blocks whose single-precision factorisation failed (bfail set), in
+// block order: their entries with band_off moved into a double-precision
+// pool of `cap` slots of `stride` elements, and their count.  More failures
+// than slots: ENOTSPD for the first block left out.  One thread (a few
+// thousand flags at most).
+__global__ void k_fallback_list(const Block* __restrict__ blocks, int nblock,
+                                const int* __restrict__ bfail, Block* __restrict__ pool,
+                                int* __restrict__ cnt, int cap, int64_t stride,
+                                int32_t* status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int k = 0;
+  for (int i = 0; i < nblock; ++i) {
+    if (!bfail[i]) continue;
+    if (k == cap) {
+      record_error(status, ENKFMC_ENOTSPD, (int64_t)i);
+      break;
+    }
+    Block b = blocks[i];
+    b.band_off = (int64_t)k * stride;
+    pool[k++] = b;
+  }
+  *cnt = k;
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, T* invdiag,
-                            int32_t* status, cudaStream_t s) {
+                            int32_t* status, cudaStream_t s, const int* cnt, int* bfail) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const size_t smem = sizeof(T) * (size_t)NB * ldP;
   cudaError_t e = cudaFuncSetAttribute(k_bandchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_bandchol<T><<<nblock, kThreads, smem, s>>>(blocks, band, invdiag, status, ldP);
+  k_bandchol<T><<<nblock, kThreads, smem, s>>>(blocks, band, invdiag, status, ldP, cnt, bfail);
   return cudaGetLastError();
 }
 
-template <typename T, int NMB>
-cudaError_t launch_bandsolve_nm(const Block* blocks, int nblock, int hb_max, int N,
-                                const T* band, T* rhs, cudaStream_t s, size_t smem, int ldP,
-                                int WRmax) {
-  cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T, NMB>,
+template <typename T, typename TR, int NMB>
+cudaError_t launch_bandsolve_nm(const Block* blocks, int nblock, int N, const T* band, TR* rhs,
+                                cudaStream_t s, size_t smem, int ldP, int WRmax, const int* cnt,
+                                const int* skip) {
+  cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T, TR, NMB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((N + NMB - 1) / NMB, nblock);
-  k_bandsolve<T, NMB><<<grid, kSolveThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax);
+  k_bandsolve<T, TR, NMB><<<grid, kSolveThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax, cnt,
+                                                            skip);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename TR>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
-                             T* rhs, cudaStream_t s) {
+                             TR* rhs, cudaStream_t s, const int* cnt, const int* skip) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const int WRmax = ((NB + hb_max + NB - 1) / NB) * NB;
   auto bytes = [&](int nmb) {
@@ -392,24 +430,35 @@ cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N,
   };
   const size_t lim = 227 * 1024;
   if (bytes(32) <= lim)
-    return launch_bandsolve_nm<T, 32>(blocks, nblock, hb_max, N, band, rhs, s, bytes(32), ldP,
-                                      WRmax);
+    return launch_bandsolve_nm<T, TR, 32>(blocks, nblock, N, band, rhs, s, bytes(32), ldP, WRmax,
+                                          cnt, skip);
   if (bytes(16) <= lim)
-    return launch_bandsolve_nm<T, 16>(blocks, nblock, hb_max, N, band, rhs, s, bytes(16), ldP,
-                                      WRmax);
+    return launch_bandsolve_nm<T, TR, 16>(blocks, nblock, N, band, rhs, s, bytes(16), ldP, WRmax,
+                                          cnt, skip);
   if (bytes(8) <= lim)
-    return launch_bandsolve_nm<T, 8>(blocks, nblock, hb_max, N, band, rhs, s, bytes(8), ldP,
-                                     WRmax);
+    return launch_bandsolve_nm<T, TR, 8>(blocks, nblock, N, band, rhs, s, bytes(8), ldP, WRmax,
+                                         cnt, skip);
   return cudaErrorInvalidConfiguration;
 }
 
-#define INST(T)                                                                                  \
-  template cudaError_t launch_bandchol<T>(const Block*, int, int, T*, T*, int32_t*,           \
-                                          cudaStream_t);                                     \
-  template cudaError_t launch_bandsolve<T>(const Block*, int, int, int, const T*, T*,           \
-                                           cudaStream_t);
-INST(float)
-INST(double)
-#undef INST
+cudaError_t launch_fallback_list(const Block* blocks, int nblock, const int* bfail, Block* pool,
+                                 int* cnt, int cap, int64_t stride, int32_t* status,
+                                 cudaStream_t s) {
+  k_fallback_list<<<1, 32, 0, s>>>(blocks, nblock, bfail, pool, cnt, cap, stride, status);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_bandchol<float>(const Block*, int, int, float*, float*, int32_t*,
+                                            cudaStream_t, const int*, int*);
+template cudaError_t launch_bandchol<double>(const Block*, int, int, double*, double*, int32_t*,
+                                             cudaStream_t, const int*, int*);
+template cudaError_t launch_bandsolve<float, float>(const Block*, int, int, int, const float*,
+                                                    float*, cudaStream_t, const int*, const int*);
+template cudaError_t launch_bandsolve<double, double>(const Block*, int, int, int, const double*,
+                                                      double*, cudaStream_t, const int*,
+                                                      const int*);
+template cudaError_t launch_bandsolve<double, float>(const Block*, int, int, int, const double*,
+                                                     float*, cudaStream_t, const int*,
+                                                     const int*);
 
 }  // namespace enkfmc

@@ -79,7 +79,8 @@ __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;
 __global__ void __launch_bounds__(kSolveWarps * 32, 1)
     k_bandsolve_tc(const Block* __restrict__ blocks, const float* __restrict__ band,
                    const float* __restrict__ invdiag, float* __restrict__ rhs, int N, int NU,
-                   int nbufB, int WT, int32_t* __restrict__ status) {
+                   int nbufB, int WT, int32_t* __restrict__ status,
+                   const int* __restrict__ skip) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool member = warp < 4;
@@ -87,6 +88,9 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 1)
   const int pt = tid - 128;   // staging warps: thread index
   const int pw = warp - 4;
   const Block b = blocks[blockIdx.x];
+  // a block factored in double precision is solved by the double-precision
+  // pass (uniform exit, before any TMEM or barrier is set up)
+  if (skip && skip[b.id]) return;
   const int nb = b.nb, hb = b.hb;
   const float* F = band + b.band_off;
   const float* Fi = invdiag + b.row_off;
@@ -572,7 +576,8 @@ __device__ __forceinline__ void syrk_tile(int k, int nt, int& mi, int& nj) {
 
 __global__ void __launch_bounds__(kCholThreads, 1)
     k_bandchol_tc(const Block* __restrict__ blocks, float* __restrict__ band,
-                  float* __restrict__ invdiag, int32_t* __restrict__ status, int WT) {
+                  float* __restrict__ invdiag, int32_t* __restrict__ status, int WT,
+                  int* __restrict__ bfail) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sHi = smem;                               // [384 rows][32] K-major
   unsigned char* sLo = smem + kOpRows * 128;
@@ -634,9 +639,13 @@ __global__ void __launch_bounds__(kCholThreads, 1)
         if (u < nbc && ok) {
           const float piv = __shfl_sync(0xffffffffu, a[u], u);
           if (!isfinite(piv) || !(piv > 0.f)) {
-            if (lane == 0)
-              record_error(status, isfinite(piv) ? ENKFMC_ENOTSPD : ENKFMC_ENONFINITE,
-                           (int64_t)blockIdx.x);
+            // a finite pivot that is not positive: with bfail the block is
+            // factored again in double precision, else ENOTSPD
+            if (lane == 0) {
+              if (bfail && isfinite(piv)) bfail[b.id] = 1;
+              else record_error(status, isfinite(piv) ? ENKFMC_ENOTSPD : ENKFMC_ENONFINITE,
+                                (int64_t)b.id);
+            }
             ok = false;
           } else {
             float inv = rsqrtf(piv);
@@ -844,7 +853,7 @@ bool bandchol_tc_supported(int hb_max) {
 }
 
 cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, float* band,
-                               float* invdiag, int32_t* status, cudaStream_t s) {
+                               float* invdiag, int32_t* status, cudaStream_t s, int* bfail) {
   if (!bandchol_tc_supported(hb_max)) return cudaErrorInvalidConfiguration;
   const size_t smem =
       2 * (size_t)kOpRows * 128 + sizeof(float) * (32 * 32 + 32 + 32 * kCholThreads) + 32;
@@ -852,20 +861,20 @@ cudaError_t launch_bandchol_tc(const Block* blocks, int nblock, int hb_max, floa
   cudaError_t e = cudaFuncSetAttribute(k_bandchol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_bandchol_tc<<<nblock, kCholThreads, smem, s>>>(blocks, band, invdiag, status, WT);
+  k_bandchol_tc<<<nblock, kCholThreads, smem, s>>>(blocks, band, invdiag, status, WT, bfail);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int N,
                                 const float* band, const float* invdiag, float* rhs,
-                                int32_t* status, cudaStream_t s) {
+                                int32_t* status, cudaStream_t s, const int* skip) {
   const TcPlan pl = plan_tc(hb_max, N);
   if (pl.nbufB == 0) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_bandsolve_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)pl.smem);
   if (e != cudaSuccess) return e;
   k_bandsolve_tc<<<nblock, kSolveWarps * 32, pl.smem, s>>>(blocks, band, invdiag, rhs, N, pl.NU,
-                                                     pl.nbufB, pl.WT, status);
+                                                     pl.nbufB, pl.WT, status, skip);
   return cudaGetLastError();
 }
 
