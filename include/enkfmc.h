@@ -65,11 +65,12 @@ typedef enum {
 
 typedef enum {
   ENKFMC_FP64 = 0,       /* every step in double precision                        */
-  ENKFMC_FP32 = 1        /* single precision arithmetic with two refinement steps
-                            whose residuals are accumulated in compensated
-                            (double-float) arithmetic: one per regression
-                            (corrected semi-normal equations) and one per
-                            sub-domain solve (Eq. 11).  Rows with more
+  ENKFMC_FP32 = 1        /* single precision arithmetic with iterative refinement:
+                            one step per regression (corrected semi-normal
+                            equations, residual of the anomalies), and per
+                            sub-domain solve (Eq. 11) one or more steps whose
+                            residuals are accumulated in compensated
+                            (double-float) arithmetic.  Rows with more
                             predecessors than half the members (2p > N, nearly
                             singular Gram matrices) are regressed in double
                             precision from FP64 anomalies and FP64 covariances
@@ -190,7 +191,10 @@ enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tval
                               const void* D, const void* Rdiag);
 
 /* Step (c), Eq. 10-11 and Algorithm 2: Y^s = y 1^T + diag(sqrt(R)) Z^T with
- * Z [N][m] standard normals; dX = A^-1 H^T R^-1 (Y^s - H X^b) per sub-domain;
+ * Z [N][m] standard normals; dX = A^-1 H^T R^-1 (Y^s - H X^b) per sub-domain
+ * (in single precision refined, and with three or more refinement steps a
+ * block whose corrections predict an error above 1e-6 of its solution after
+ * the second step is factored and solved in double precision from there);
  * Xa[m * n + l] = Xb + dX for l in the sub-domain's interior.  Xb, Xa:
  * [N][n] (Xa may not alias Xb); y, Rdiag: [m]; Z: [N][m].  Uses the factors
  * of the last enkfmc_assemble. */
@@ -222,8 +226,12 @@ enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void*
  * the failing row or block. */
 enkfmc_status enkfmc_get_status(enkfmc_handle* h, int64_t* info);
 
-/* Number of blocks the last enkfmc_assemble factored in double precision
- * (single-precision handles; 0 otherwise).  Synchronises the stream. */
+/* Number of blocks factored in double precision since the last
+ * enkfmc_assemble (single-precision handles; 0 otherwise): those whose
+ * single-precision factorisation met a non-positive pivot, and those whose
+ * refinement (with three or more steps) converged too slowly after two
+ * steps, which enkfmc_analyze moves to double precision for the rest.
+ * Synchronises the stream. */
 enkfmc_status enkfmc_fp64_blocks(enkfmc_handle* h, int32_t* count /* host */);
 
 /* Strictly-lower pattern of the global T as CSR in label order (host arrays:

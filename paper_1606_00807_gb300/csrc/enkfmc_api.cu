@@ -306,13 +306,15 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
   if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
   if (!is_fp64(h)) {  // double-precision pool for blocks whose FP32 factorisation fails
-    h->fb_cap = std::max(8, h->nblock / 8);
+    h->fb_cap = std::max(8, h->nblock / 4);
     h->fb_stride = (int64_t)h->nb_max * (h->hb_max + 1);
     if ((st = dalloc(h, &h->d_bfail, sizeof(int32_t) * h->nblock))) return st;
-    if ((st = dalloc(h, &h->d_fb_cnt, sizeof(int32_t)))) return st;
+    if ((st = dalloc(h, &h->d_c1max, sizeof(float) * h->nblock))) return st;
+    if ((st = dalloc(h, &h->d_fb_cnt, sizeof(int32_t) * 12))) return st;
     if ((st = dalloc(h, &h->d_fb_blocks, sizeof(Block) * h->fb_cap))) return st;
     if ((st = dalloc(h, &h->d_fb_band, sizeof(double) * h->fb_cap * h->fb_stride))) return st;
-    CUDA_TRY(cudaMemset(h->d_fb_cnt, 0, sizeof(int32_t)));
+    CUDA_TRY(cudaMemset(h->d_fb_cnt, 0, sizeof(int32_t) * 12));
+    CUDA_TRY(cudaMemset(h->d_bfail, 0, sizeof(int32_t) * h->nblock));
   }
   if (has_fp64_rows(g, !is_fp64(h))) {
     if ((st = dalloc(h, &h->d_U64, sizeof(double) * g.n * g.ldN))) return st;
@@ -377,7 +379,7 @@ void release(enkfmc_handle* h) {
                   h->d_Xb,    h->d_y,       h->d_R,   h->d_Z,       h->d_Xa,     h->d_T,
                   h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
                   h->d_Ubar,  h->d_U64,     h->d_C64, h->d_W,      h->d_bfail,  h->d_fb_cnt,
-                  h->d_fb_blocks, h->d_fb_band};
+                  h->d_fb_blocks, h->d_fb_band, h->d_c1max};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
@@ -466,6 +468,32 @@ enkfmc_status run_estimate(enkfmc_handle* h, const T* Xb, T* Tv, T* D) {
   });
 }
 
+// Predicted error (relative to the block's solution) above which a block's
+// single-precision refinement hands over to double precision.
+constexpr float kRefineTolerance = 1e-6f;
+
+// Blocks of the double-precision pool (append = 0: those whose single-
+// precision factorisation met a non-positive pivot, the pool rebuilt; 1: the
+// ones flagged by the refinement check, added): assembled from the same
+// single-precision T, D and R in double, then factored in double.
+enkfmc_status fp64_pool(enkfmc_handle* h, const float* Tv, const float* D, const float* R,
+                        int append) {
+  return timed(h, ENKFMC_K_FP64_BLOCKS, [&](int* nk) {
+    *nk += 3;
+    int* rng = h->d_fb_cnt + (append ? 6 : 2);  // {lo, hi} of the blocks to (re)factor
+    cudaError_t e = launch_fallback_list(h->d_blocks, h->nblock, h->d_bfail, h->d_fb_blocks,
+                                         h->d_fb_cnt, h->fb_cap, h->fb_stride, h->d_status,
+                                         append, h->stream);
+    if (e != cudaSuccess) return e;
+    e = launch_assemble<float, double>(h->g, h->d_fb_blocks, h->fb_cap, h->nb_max, Tv, D,
+                                       (const float*)h->d_Te, (const float*)h->d_De, h->d_obs_of,
+                                       R, h->d_fb_band, h->d_status, h->stream, h->hb_max, rng);
+    if (e != cudaSuccess) return e;
+    return launch_bandchol<double>(h->d_fb_blocks, h->fb_cap, h->hb_max, h->d_fb_band, nullptr,
+                                   h->d_status, h->stream, rng, nullptr);
+  });
+}
+
 template <typename T>
 enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R) {
   enkfmc_status st = timed(h, ENKFMC_K_REGRESS_HALO, [&](int* nk) {
@@ -504,29 +532,20 @@ enkfmc_status run_assemble(enkfmc_handle* h, const T* Tv, const T* D, const T* R
                                     h->d_bfail);
     });
     if (st) return st;
-    return timed(h, ENKFMC_K_FP64_BLOCKS, [&](int* nk) {
-      *nk += 3;
-      cudaError_t e = launch_fallback_list(h->d_blocks, h->nblock, h->d_bfail, h->d_fb_blocks,
-                                           h->d_fb_cnt, h->fb_cap, h->fb_stride, h->d_status,
-                                           h->stream);
-      if (e != cudaSuccess) return e;
-      e = launch_assemble<float, double>(h->g, h->d_fb_blocks, h->fb_cap, h->nb_max,
-                                         (const float*)Tv, (const float*)D,
-                                         (const float*)h->d_Te, (const float*)h->d_De,
-                                         h->d_obs_of, (const float*)R, h->d_fb_band, h->d_status,
-                                         h->stream, h->hb_max, h->d_fb_cnt);
-      if (e != cudaSuccess) return e;
-      return launch_bandchol<double>(h->d_fb_blocks, h->fb_cap, h->hb_max, h->d_fb_band, nullptr,
-                                     h->d_status, h->stream, h->d_fb_cnt, nullptr);
-    });
+    h->R_assembled = R;
+    return fp64_pool(h, (const float*)Tv, (const float*)D, (const float*)R, 0);
   }
 }
 
+// Views of the double-precision pool for solve_band (offsets into its meta).
+constexpr int kPoolAll = 0, kPoolNew = 4, kPoolNone = 8;
+
 // L L^T X = B in place for every block, N members (Eq. 11).  Single
-// precision: the blocks factored in double precision are solved in double
-// (their rhs stays single precision), the others on the tensor or CUDA cores.
+// precision: the blocks of the double-precision pool are solved in double
+// (their rhs stays single precision) when the view includes them, else get a
+// zero solution; the others are solved on the tensor or CUDA cores.
 template <typename T>
-cudaError_t solve_band(enkfmc_handle* h, T* rhs, int* nk) {
+cudaError_t solve_band(enkfmc_handle* h, T* rhs, int* nk, int view = kPoolAll) {
   ++*nk;
   if constexpr (std::is_same<T, double>::value) {
     return launch_bandsolve<double, double>(h->d_blocks, h->nblock, h->hb_max, h->g.N,
@@ -544,7 +563,8 @@ cudaError_t solve_band(enkfmc_handle* h, T* rhs, int* nk) {
     if (e != cudaSuccess) return e;
     ++*nk;
     return launch_bandsolve<double, float>(h->d_fb_blocks, h->fb_cap, h->hb_max, h->g.N,
-                                           h->d_fb_band, rhs, h->stream, h->d_fb_cnt, nullptr);
+                                           h->d_fb_band, rhs, h->stream, h->d_fb_cnt + view,
+                                           nullptr);
   }
 }
 
@@ -562,6 +582,9 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
   if (st) return st;
   const T* corr = nullptr;
   if (h->refine_solve && sizeof(T) == sizeof(float)) {
+    // with three or more steps, blocks whose corrections shrink too slowly
+    // after two steps join the double-precision pool for the third
+    const bool check = h->refine_steps >= 3;
     for (int step = 0; step < h->refine_steps; ++step) {
       st = timed(h, ENKFMC_K_RESIDUAL, [&](int* nk) {
         cudaError_t e = cudaSuccess;
@@ -581,9 +604,23 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
       });
       if (st) return st;
       st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) {
-        return solve_band<T>(h, (T*)h->d_res, nk);
+        return solve_band<T>(h, (T*)h->d_res, nk, check && step == 2 ? kPoolNew : kPoolNone);
       });
       if (st) return st;
+      if (check && step < 2) {
+        st = timed(h, ENKFMC_K_FP64_BLOCKS, [&](int* nk) {
+          ++*nk;
+          return launch_ir_check(h->d_blocks, h->nblock, h->g.N, (const float*)h->d_res,
+                                 (const float*)h->d_rhs, h->d_c1max, h->d_bfail,
+                                 kRefineTolerance, step, h->stream);
+        });
+        if (st) return st;
+        if (step == 1) {
+          st = fp64_pool(h, (const float*)h->T_assembled, (const float*)h->D_assembled,
+                         (const float*)h->R_assembled, 1);
+          if (st) return st;
+        }
+      }
     }
     corr = (const T*)h->d_res;
   }
@@ -712,7 +749,7 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
   if (refine)
     CUDA_TRY(cudaMemcpyAsync(W, h->d_lam, sizeof(T) * nrhs, cudaMemcpyDeviceToDevice, h->stream));
   st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) {
-    return solve_band<T>(h, (T*)h->d_lam, nk);
+    return solve_band<T>(h, (T*)h->d_lam, nk, kPoolAll);
   });
   if (st) return st;
   // Lambda = A^-1 W refined with the forward solve's steps (A is the same)
@@ -727,7 +764,9 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
           (float*)Wres, h->stream);
     });
     if (st) return st;
-    st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) { return solve_band<T>(h, Wres, nk); });
+    st = timed(h, ENKFMC_K_BANDSOLVE, [&](int* nk) {
+      return solve_band<T>(h, Wres, nk, kPoolNone);
+    });
     if (st) return st;
     st = timed(h, ENKFMC_K_RESIDUAL, [&] {
       return launch_accumulate((float*)h->d_lam, (const float*)Wres, nrhs, h->stream);
@@ -977,7 +1016,7 @@ enkfmc_status enkfmc_fp64_blocks(enkfmc_handle* h, int32_t* count) {
   *count = 0;
   if (!h->d_fb_cnt) return ENKFMC_OK;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  CUDA_TRY(cudaMemcpy(count, h->d_fb_cnt, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(count, h->d_fb_cnt + 1, sizeof(int32_t), cudaMemcpyDeviceToHost));
   return ENKFMC_OK;
 }
 

@@ -249,13 +249,15 @@ struct enkfmc_handle {
   // FP32: blocks whose single-precision factorisation meets a non-positive
   // pivot are assembled, factored and solved again in double precision
   int32_t* d_bfail = nullptr;         // [nblock] failure flags of the last factorisation
-  int32_t* d_fb_cnt = nullptr;        // blocks in the double-precision pool
+  int32_t* d_fb_cnt = nullptr;        // pool views and ranges (12 ints, k_fallback_list)
+  float* d_c1max = nullptr;           // [nblock] first refinement correction per block
   enkfmc::Block* d_fb_blocks = nullptr;  // [fb_cap] their entries, band_off in the pool
   double* d_fb_band = nullptr;        // [fb_cap][fb_stride] their bands and factors
   int32_t fb_cap = 0;
   int64_t fb_stride = 0;
   const void* T_assembled = nullptr;  // global T/D used by the last assemble
   const void* D_assembled = nullptr;
+  const void* R_assembled = nullptr;  // and its observation variances
   bool assembled = false;
   int64_t workspace_bytes = 0;
 
@@ -352,12 +354,12 @@ cudaError_t launch_regressions(const Geom& g, const EstStats<T>& st, const int32
                                double ridge_c, int32_t* status, cudaStream_t s, int* nk);
 
 // General band assembly (any block); TB the band's type (double for the
-// double-precision pass over failed blocks, cnt their device count).
+// double-precision pool, rng its device range {lo, hi}).
 template <typename T, typename TB = T>
 cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
                             const T* Tg, const T* Dg, const T* Te, const T* De,
                             const int32_t* obs_of, const T* R, TB* band, int32_t* status,
-                            cudaStream_t s, int hb_max, const int* cnt = nullptr);
+                            cudaStream_t s, int hb_max, const int* rng = nullptr);
 
 // Band assembly from per-shape slot-pair lists (blocks whose extended box does
 // not wrap onto itself in longitude).
@@ -373,18 +375,24 @@ size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_
                            int box_sum);
 
 // Factor every block in place; invdiag[row_off + c] = 1 / L[c][c] (may be null).
-// cnt (may be null): only the first *cnt of `blocks` (a device count); bfail
-// (may be null): a finite non-positive pivot sets bfail[block id] instead of
-// recording ENOTSPD.
+// rng (may be null): only the entries [rng[0], rng[1]) of `blocks` (a device
+// range); bfail (may be null): a finite non-positive pivot sets bfail[block
+// id] instead of recording ENOTSPD.
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, T* invdiag,
-                            int32_t* status, cudaStream_t s, const int* cnt = nullptr,
+                            int32_t* status, cudaStream_t s, const int* rng = nullptr,
                             int* bfail = nullptr);
-// The failed blocks (bfail) into a list of `cap` double-precision pool slots of
-// `stride` elements each (band_off remapped), and their count *cnt.
-cudaError_t launch_fallback_list(const Block* blocks, int nblock, const int* bfail, Block* pool,
-                                 int* cnt, int cap, int64_t stride, int32_t* status,
+// The double-precision pool (k_fallback_list in k_band.cu): blocks flagged 1
+// (append = 0, rebuilt) or flagged 2 (append = 1, added) into `cap` slots of
+// `stride` elements; meta (12 ints) receives its solve views and ranges.
+cudaError_t launch_fallback_list(const Block* blocks, int nblock, int* bfail, Block* pool,
+                                 int* meta, int cap, int64_t stride, int32_t* status, int append,
                                  cudaStream_t s);
+// Refinement convergence per block: phase 0 stores max|c| in c1max; phase 1
+// flags 2 the blocks whose corrections predict an error above tau max|x|.
+cudaError_t launch_ir_check(const Block* blocks, int nblock, int N, const float* c,
+                            const float* x, float* c1max, int* bfail, float tau, int phase,
+                            cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_max,
@@ -392,11 +400,12 @@ cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_ma
                        const T* Z, T* rhs, cudaStream_t s);
 
 // L L^T X = B for N members per block; T the factor's type, TR the rhs's.
-// cnt as for launch_bandchol; skip (may be null): blocks with skip[id] set
-// are left alone.
+// pool (may be null): a view {0, live, lo, hi} of the double-precision pool
+// (solve [lo, hi), zero the other live blocks' solutions); skip (may be
+// null): blocks with skip[id] set are left alone.
 template <typename T, typename TR>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
-                             TR* rhs, cudaStream_t s, const int* cnt = nullptr,
+                             TR* rhs, cudaStream_t s, const int* pool = nullptr,
                              const int* skip = nullptr);
 
 // Single-precision band solves with the panel updates on the tensor cores

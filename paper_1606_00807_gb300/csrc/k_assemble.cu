@@ -21,8 +21,8 @@ namespace {
 
 // T: the type of T, D and R; TB: the band's type and the arithmetic (double
 // for the blocks whose single-precision factorisation failed: their A is
-// assembled again from the same single-precision T and D, in double).  cnt
-// (optional): only the first *cnt entries of `blocks`.
+// assembled again from the same single-precision T and D, in double).  rng
+// (optional, device {lo, hi}): only the entries [lo, hi) of `blocks`.
 template <typename T, typename TB>
 __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __restrict__ blocks,
                                                   const T* __restrict__ Tg, const T* __restrict__ Dg,
@@ -30,11 +30,11 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
                                                   const int32_t* __restrict__ obs_of,
                                                   const T* __restrict__ R, TB* __restrict__ band,
                                                   int32_t* status, int hbp1_max,
-                                                  const int* __restrict__ cnt) {
+                                                  const int* __restrict__ rng) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   TB* col = reinterpret_cast<TB*>(smem) + (size_t)warp * hbp1_max;
-  if (cnt && (int)blockIdx.y >= *cnt) return;
+  if (rng && ((int)blockIdx.y < rng[0] || (int)blockIdx.y >= rng[1])) return;
   const Block b = blocks[blockIdx.y];
   const int c = blockIdx.x * wpc + warp;
   if (c >= b.nb) return;
@@ -313,7 +313,7 @@ template <typename T, typename TB>
 cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int nb_max,
                             const T* Tg, const T* Dg, const T* Te, const T* De,
                             const int32_t* obs_of, const T* R, TB* band, int32_t* status,
-                            cudaStream_t s, int hb_max, const int* cnt) {
+                            cudaStream_t s, int hb_max, const int* rng) {
   const int wpc = 8;
   const int hbp1 = hb_max + 1;
   const size_t smem = sizeof(TB) * (size_t)hbp1 * wpc;
@@ -322,7 +322,7 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
   if (e != cudaSuccess) return e;
   const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
   k_assemble<T, TB><<<grid, 32 * wpc, smem, s>>>(g, blocks, Tg, Dg, Te, De, obs_of, R, band,
-                                                 status, hbp1, cnt);
+                                                 status, hbp1, rng);
   return cudaGetLastError();
 }
 

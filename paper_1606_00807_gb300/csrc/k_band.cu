@@ -58,18 +58,19 @@ __device__ __forceinline__ void tri_tile(int idx, int nT, int& I, int& C) {
   I = C + (idx - (C * nT - C * (C - 1) / 2));
 }
 
-// cnt (optional): only the first *cnt entries of `blocks` are factored (the
-// double-precision pass over the blocks whose single-precision factorisation
-// failed); bfail (optional): per-block failure flags, see factor_panel.
+// rng (optional): only the entries [rng[0], rng[1]) of `blocks` are factored
+// (device range: the double-precision pool of blocks whose single-precision
+// factorisation failed or converged too slowly); bfail (optional): per-block
+// failure flags, see factor_panel.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__ blocks,
                                                        T* __restrict__ band,
                                                        T* __restrict__ invdiag, int32_t* status,
-                                                       int ldP, const int* __restrict__ cnt,
+                                                       int ldP, const int* __restrict__ rng,
                                                        int* __restrict__ bfail) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* P = reinterpret_cast<T*>(smem);  // [NB][ldP]: P[t*ldP + i] = A[c0+i][c0+t]
-  if (cnt && (int)blockIdx.x >= *cnt) return;
+  if (rng && ((int)blockIdx.x < rng[0] || (int)blockIdx.x >= rng[1])) return;
   const Block b = blocks[blockIdx.x];
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
   T* AB = band + b.band_off;
@@ -151,14 +152,16 @@ __global__ void __launch_bounds__(kThreads) k_bandchol(const Block* __restrict__
 // memory and the next ones are read in their place.  The NB x NB diagonal
 // triangles are solved one member per thread in registers.  T: the factor
 // and the arithmetic; TR: the right-hand sides (single-precision rhs of a
-// block factored in double).  cnt (optional): only the first *cnt entries of
-// `blocks`; skip (optional): blocks with skip[id] set are left to the
-// double-precision pass.
+// block factored in double).  pool (optional, the double-precision pool):
+// `blocks` has pool[1] live entries; those in [pool[2], pool[3]) are solved,
+// the others get a zero solution (a refinement step whose correction they do
+// not need).  skip (optional): blocks with skip[id] set are left to the
+// double-precision pool.
 template <typename T, typename TR, int NMB>
 __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __restrict__ blocks,
                                                         const T* __restrict__ band,
                                                         TR* __restrict__ rhs, int N, int ldP,
-                                                        int WRmax, const int* __restrict__ cnt,
+                                                        int WRmax, const int* __restrict__ pool,
                                                         const int* __restrict__ skip) {
   constexpr int NMP = NMB + 4;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -168,9 +171,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
   T* invd = Red + 4 * NB * NMB;        // [NB]
   // the member chunks of one block are consecutive thread blocks, so they run
   // together and share the factor through L2
-  if (cnt && (int)blockIdx.y >= *cnt) return;
+  if (pool && (int)blockIdx.y >= pool[1]) return;
   const Block b = blocks[blockIdx.y];
   if (skip && skip[b.id]) return;
+  if (pool && ((int)blockIdx.y < pool[2] || (int)blockIdx.y >= pool[3])) {
+    const int m0z = blockIdx.x * NMB, nmz = min(NMB, N - m0z);
+    TR* Bz = rhs + b.row_off * N + (int64_t)m0z * b.nb;
+    for (int64_t e = threadIdx.x; e < (int64_t)nmz * b.nb; e += blockDim.x) Bz[e] = TR(0);
+    return;
+  }
   const int m0 = blockIdx.x * NMB;
   const int nm = min(NMB, N - m0);
   const int nb = b.nb, hb = b.hb, ld = hb + 1;
@@ -369,19 +378,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_bandsolve(const Block* __rest
   }
 }
 
-// The blocks whose single-precision factorisation failed (bfail set), in
-// block order: their entries with band_off moved into a double-precision
-// pool of `cap` slots of `stride` elements, and their count.  More failures
-// than slots: ENOTSPD for the first block left out.  One thread (a few
-// thousand flags at most).
+// The double-precision pool: blocks in block order, their entries with
+// band_off moved into `cap` slots of `stride` elements.  append = 0: rebuild
+// from the blocks flagged 1 (non-positive pivot); append = 1: add the blocks
+// flagged 2 (refinement converging too slowly) after the present ones and
+// flag them 1.  meta holds three views {0, end, lo, hi} of the pool (end
+// blocks) for k_bandsolve: meta[0..3] solves all of them, meta[4..7] the ones
+// added by this call, meta[8..11] none; meta + 2 and meta + 6 are the
+// {lo, hi} ranges of all and of the added blocks for the assembly and the
+// factorisation.  More blocks than slots: ENOTSPD for the first block left
+// out.  One thread (a few thousand flags at most).
 __global__ void k_fallback_list(const Block* __restrict__ blocks, int nblock,
-                                const int* __restrict__ bfail, Block* __restrict__ pool,
-                                int* __restrict__ cnt, int cap, int64_t stride,
-                                int32_t* status) {
+                                int* __restrict__ bfail, Block* __restrict__ pool,
+                                int* __restrict__ meta, int cap, int64_t stride, int32_t* status,
+                                int append) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int k = 0;
+  int k = append ? meta[1] : 0;
+  const int first = k;
   for (int i = 0; i < nblock; ++i) {
-    if (!bfail[i]) continue;
+    if (bfail[i] != (append ? 2 : 1)) continue;
     if (k == cap) {
       record_error(status, ENKFMC_ENOTSPD, (int64_t)i);
       break;
@@ -389,40 +404,86 @@ __global__ void k_fallback_list(const Block* __restrict__ blocks, int nblock,
     Block b = blocks[i];
     b.band_off = (int64_t)k * stride;
     pool[k++] = b;
+    bfail[i] = 1;
   }
-  *cnt = k;
+  const int views[12] = {0, k, 0, k, 0, k, first, k, 0, k, 0, 0};
+  for (int i = 0; i < 12; ++i) meta[i] = views[i];
+}
+
+// Convergence of the single-precision refinement per block (one CTA each):
+// phase 0 stores max |c| of the first correction; phase 1, after the second
+// correction c, flags the block 2 (double precision from here) when the
+// corrections do not shrink (rho = max|c2| / max|c1| >= 1) or when the
+// error they predict after two more steps, max|c2| rho^2, exceeds
+// tau max|x|.  Blocks already in the pool are left alone.
+__global__ void __launch_bounds__(256) k_ir_check(const Block* __restrict__ blocks, int N,
+                                                  const float* __restrict__ c,
+                                                  const float* __restrict__ x,
+                                                  float* __restrict__ c1max,
+                                                  int* __restrict__ bfail, float tau, int phase) {
+  __shared__ float red[2][8];
+  const Block b = blocks[blockIdx.x];
+  if (bfail[b.id]) return;
+  const int64_t cnt = (int64_t)b.nb * N, base = b.row_off * N;
+  float mc = 0.f, mx = 0.f;
+  for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+    mc = fmaxf(mc, fabsf(c[base + e]));
+    if (phase) mx = fmaxf(mx, fabsf(x[base + e]));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mc = fmaxf(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = mc;
+    red[1][warp] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    mc = fmaxf(mc, red[0][w]);
+    mx = fmaxf(mx, red[1][w]);
+  }
+  if (phase == 0) {
+    c1max[b.id] = mc;
+    return;
+  }
+  const float c1 = c1max[b.id];
+  const float rho = c1 > 0.f ? mc / c1 : 0.f;
+  if (!(rho < 1.f) || !(mc * rho * rho <= tau * mx)) bfail[b.id] = 2;
 }
 
 }  // namespace
 
 template <typename T>
 cudaError_t launch_bandchol(const Block* blocks, int nblock, int hb_max, T* band, T* invdiag,
-                            int32_t* status, cudaStream_t s, const int* cnt, int* bfail) {
+                            int32_t* status, cudaStream_t s, const int* rng, int* bfail) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const size_t smem = sizeof(T) * (size_t)NB * ldP;
   cudaError_t e = cudaFuncSetAttribute(k_bandchol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_bandchol<T><<<nblock, kThreads, smem, s>>>(blocks, band, invdiag, status, ldP, cnt, bfail);
+  k_bandchol<T><<<nblock, kThreads, smem, s>>>(blocks, band, invdiag, status, ldP, rng, bfail);
   return cudaGetLastError();
 }
 
 template <typename T, typename TR, int NMB>
 cudaError_t launch_bandsolve_nm(const Block* blocks, int nblock, int N, const T* band, TR* rhs,
-                                cudaStream_t s, size_t smem, int ldP, int WRmax, const int* cnt,
+                                cudaStream_t s, size_t smem, int ldP, int WRmax, const int* pool,
                                 const int* skip) {
   cudaError_t e = cudaFuncSetAttribute(k_bandsolve<T, TR, NMB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((N + NMB - 1) / NMB, nblock);
-  k_bandsolve<T, TR, NMB><<<grid, kSolveThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax, cnt,
+  k_bandsolve<T, TR, NMB><<<grid, kSolveThreads, smem, s>>>(blocks, band, rhs, N, ldP, WRmax, pool,
                                                             skip);
   return cudaGetLastError();
 }
 
 template <typename T, typename TR>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
-                             TR* rhs, cudaStream_t s, const int* cnt, const int* skip) {
+                             TR* rhs, cudaStream_t s, const int* pool, const int* skip) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const int WRmax = ((NB + hb_max + NB - 1) / NB) * NB;
   auto bytes = [&](int nmb) {
@@ -431,20 +492,28 @@ cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N,
   const size_t lim = 227 * 1024;
   if (bytes(32) <= lim)
     return launch_bandsolve_nm<T, TR, 32>(blocks, nblock, N, band, rhs, s, bytes(32), ldP, WRmax,
-                                          cnt, skip);
+                                          pool, skip);
   if (bytes(16) <= lim)
     return launch_bandsolve_nm<T, TR, 16>(blocks, nblock, N, band, rhs, s, bytes(16), ldP, WRmax,
-                                          cnt, skip);
+                                          pool, skip);
   if (bytes(8) <= lim)
     return launch_bandsolve_nm<T, TR, 8>(blocks, nblock, N, band, rhs, s, bytes(8), ldP, WRmax,
-                                         cnt, skip);
+                                         pool, skip);
   return cudaErrorInvalidConfiguration;
 }
 
-cudaError_t launch_fallback_list(const Block* blocks, int nblock, const int* bfail, Block* pool,
-                                 int* cnt, int cap, int64_t stride, int32_t* status,
+cudaError_t launch_fallback_list(const Block* blocks, int nblock, int* bfail, Block* pool,
+                                 int* meta, int cap, int64_t stride, int32_t* status, int append,
                                  cudaStream_t s) {
-  k_fallback_list<<<1, 32, 0, s>>>(blocks, nblock, bfail, pool, cnt, cap, stride, status);
+  k_fallback_list<<<1, 32, 0, s>>>(blocks, nblock, bfail, pool, meta, cap, stride, status,
+                                   append);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_check(const Block* blocks, int nblock, int N, const float* c,
+                            const float* x, float* c1max, int* bfail, float tau, int phase,
+                            cudaStream_t s) {
+  k_ir_check<<<nblock, 256, 0, s>>>(blocks, N, c, x, c1max, bfail, tau, phase);
   return cudaGetLastError();
 }
 
