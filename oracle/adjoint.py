@@ -51,9 +51,14 @@ def _regression_parts(U, j, P, ridge_c):
     return beta, e, float(e @ e) / (N - 1), M, lam
 
 
-def analysis_with_gradient(w, Xb_mm, y, R, Z_mm, obs_idx, Xa_bar_mm):
+def analysis_with_gradient(w, Xb_mm, y, R, Z_mm, obs_idx, Xa_bar_mm, only=None):
     """X^a and the gradients (Xb_bar [N][n], y_bar [m], R_bar [m]) of a loss whose
-    gradient with respect to X^a is Xa_bar (member-major arrays)."""
+    gradient with respect to X^a is Xa_bar (member-major arrays).
+
+    With `only` (sub-domain indices) the other sub-domains are skipped.  A
+    sub-domain whose interior rows of Xa_bar are all zero has Lambda = 0, so it
+    adds nothing to the gradients; skipping it is then exact.  X^a is returned
+    as NaN outside the analysed interiors."""
     grid = Grid.from_workload(w)
     sds = subdomains(grid, w.sub_lon, w.sub_lat)
     Xb = np.asarray(Xb_mm, dtype=np.float64).T
@@ -64,12 +69,14 @@ def analysis_with_gradient(w, Xb_mm, y, R, Z_mm, obs_idx, Xa_bar_mm):
     N = Xb.shape[1]
     U = anomalies(Xb)
     Ys = perturbed_observations(y, R, Z)
-    Xa = Xb.copy()
+    Xa = Xb.copy() if only is None else np.full_like(Xb, np.nan)
     Xb_bar = Wbar.copy()
     y_bar = np.zeros_like(y)
     R_bar = np.zeros_like(R)
     U_bar = np.zeros_like(U)
     for sd in sds:
+        if only is not None and sd.index not in only:
+            continue
         A, rhs, T, D, o_loc = local_system(grid, sd, U, Xb, Ys, R, obs_idx, w.ridge_c)
         dX = solve_spd(A, rhs)
         pos = {int(q): i for i, q in enumerate(sd.ext)}

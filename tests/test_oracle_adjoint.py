@@ -92,3 +92,23 @@ def test_regression_residual_normal_equations(name, ridge):
     assert seen_plain > 5
     if ridge:
         assert seen_ridge > 5
+
+
+def test_gradient_of_one_subdomain_seed_needs_only_that_subdomain():
+    """A seed dL/dX^a that vanishes outside one sub-domain's interior leaves every other
+    sub-domain with Lambda = 0: the gradient computed from that sub-domain alone equals
+    the full one (the reduction the T63 gradient check on the GPU relies on)."""
+    from oracle.adjoint import analysis_with_gradient
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    inp = make_inputs(w)
+    g = O.Grid.from_workload(w)
+    sds = O.subdomains(g, w.sub_lon, w.sub_lat)
+    k0 = 5
+    W = np.zeros((w.N, w.n))
+    W[:, sds[k0].interior] = np.random.default_rng(1).standard_normal((w.N, len(sds[k0].interior)))
+    full = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, W)
+    part = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, W, only=[k0])
+    for a, b in zip(full[1:], part[1:]):
+        assert np.allclose(a, b, rtol=1e-12, atol=1e-14 * np.abs(a).max())
+    assert np.allclose(part[0][:, sds[k0].interior], full[0][:, sds[k0].interior])
+    assert np.isnan(part[0][:, sds[0].interior]).all()
