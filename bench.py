@@ -50,6 +50,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # precision (the capture commands are in profiles/); a kernel without one
 # reports null.
 TRAFFIC_PER_LAUNCH = {}
+TUNING_CACHE = os.path.join(ROOT, "paper_1606_00807_gb300", "tuning_gb300.json")
 
 
 def parse_args(argv=None):
@@ -72,6 +73,12 @@ def parse_args(argv=None):
     ap.add_argument("--sample-subdomains", type=int, default=1)
     ap.add_argument("--sample-out", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-steps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batch of 256 uneven problems (one CUDA graph per cycle)")
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune every batch shape missing from the tuning cache")
+    ap.add_argument("--tuning", default=TUNING_CACHE,
+                    help="tuning cache (JSON) read, and with --tune written")
     return ap.parse_args(argv)
 
 
@@ -594,10 +601,84 @@ def side_measurements(args, w, inp, value, dev):
                                             np.float32, B.FP32, torch.float32, accuracy=True))
     guarded("fwd_adj_plain_fp64", lambda: fwd_adj_line(args, wa, make_inputs(wa, np.float64),
                                                        dev, np.float64, B.FP64, torch.float64))
+    guarded("batch", lambda: batch_line(args, dev))
     a, b = out.get("fwd_adj", {}), out.get("fwd_adj_plain_fp64", {})
     if "fwd_adj_cycles_per_s" in a and "fwd_adj_cycles_per_s" in b:
         a["fp32_over_fp64"] = a["fwd_adj_cycles_per_s"] / b["fwd_adj_cycles_per_s"]
     return out
+
+
+def batch_line(args, dev):
+    """The 256 independent problems of uneven size (grids 24 x 12 to 96 x 48,
+    1-7 levels, 1-5 variables, N 20-120, r 1-4, seeds 3000 + i), FP32, each on
+    its own handle with the autotuner's settings (from the tuning cache; the
+    library defaults for shapes it lacks), one CUDA graph replay per cycle of
+    all of them.  Also the same cycle run eagerly, instance after instance, on
+    one stream."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00807_gb300 import autotune, binding as B
+    from synthetic import make_inputs
+    from synthetic.workloads import batch_instances
+
+    ws = batch_instances()
+    cache = autotune.load_cache(args.tuning)
+    tuned0 = len(cache)
+    stream = torch.cuda.current_stream(dev)
+    insts = []
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    for w in ws:
+        inp = make_inputs(w, np.float32)
+        Xb, y, R, Z = put(inp.Xb), put(inp.y), put(inp.R), put(inp.Z)
+        choice = cache.get(autotune.shape_key(w, B.FP32))
+        mk = lambda c: B.Handle.from_workload(w, precision=B.FP32, stream=stream.cuda_stream,
+                                              flags=c["flags"] if c else 0)
+        h = mk(choice)
+        T = torch.empty((w.n, h.info.pmax), device=dev)
+        D = torch.empty(w.n, device=dev)
+        Xa = torch.empty_like(Xb)
+        if choice is None and args.tune:
+            choice = autotune.tune(w, inp.obs_idx, (Xb, T, D, y, R, Z, Xa), cache=cache)
+            if choice["flags"] != h.problem.flags:
+                h.close()
+                h = mk(choice)
+        if choice:
+            autotune.apply(h, choice)
+        h.set_observations(inp.obs_idx)
+        insts.append((h, (Xb, T, D, y, R, Z, Xa)))
+    if args.tune and len(cache) > tuned0:
+        autotune.save_cache(cache, args.tuning)
+    batch = B.Batch([h for h, _ in insts], nstreams=8, stream=stream.cuda_stream)
+    for i, (h, (Xb, T, D, y, R, Z, Xa)) in enumerate(insts):
+        batch.bind(i, Xb, T, D, y, R, Z, Xa)
+    batch.capture()
+    st, _ = batch.status()
+    ms = _time_steps(batch.run, 1, 3, stream)
+    st2, _ = batch.status()
+
+    def eager():
+        for h, (Xb, T, D, y, R, Z, Xa) in insts:
+            h.estimate(Xb, T, D)
+            h.assemble(Xb, T, D, R)
+            h.analyze(Xb, y, R, Z, Xa)
+
+    ms_eager = _time_steps(eager, 0, 1, stream)
+    nfb = sum(h.fp64_blocks() for h, _ in insts)
+    n_tc = sum(1 for h, _ in insts if not (h.problem.flags & B.FLAG_SIMT_BAND))
+    batch.close()
+    for h, _ in insts:
+        h.close()
+    return {"instances": len(ws), "components": int(sum(w.n for w in ws)),
+            "members_x_components": int(sum(w.n * w.N for w in ws)),
+            "value": 1e3 / ms, "unit": "cycles/s (all instances)", "ms_per_cycle": ms,
+            "instances_per_s": len(ws) * 1e3 / ms, "eager_ms_per_cycle": ms_eager,
+            "graph_over_eager": ms_eager / ms, "streams": 8,
+            "status_nonzero": int((st != 0).sum() + (st2 != 0).sum()),
+            "fp64_blocks": int(nfb), "tensor_core_band": n_tc,
+            "tuning": (f"{sum(1 for w in ws if autotune.shape_key(w, B.FP32) in cache)} of "
+                       f"{len(ws)} shapes from the tuning cache"),
+            "instance_list": [w.name for w in ws]}
 
 
 def plain_fp64_line(w, inp, value, dev):
@@ -775,6 +856,11 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    if args.batch_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"batch": batch_line(args, torch.device("cuda", 0))}))
+        return
     if args.cpu_sample:
         cpu_sample_main(args)
     elif args.impl == "reference":

@@ -150,6 +150,9 @@ typedef struct enkfmc_handle enkfmc_handle;
  * geometry, ENOMEM when device memory runs out. */
 enkfmc_status enkfmc_create(enkfmc_handle** h, const enkfmc_problem* p, void* cuda_stream);
 void enkfmc_destroy(enkfmc_handle* h);
+/* Validate a problem description without a device: OK, or EINVAL where
+ * enkfmc_create would refuse it as invalid or unsupported. */
+enkfmc_status enkfmc_check_problem(const enkfmc_problem* p);
 const char* enkfmc_strerror(enkfmc_status s);
 enkfmc_status enkfmc_query(const enkfmc_handle* h, enkfmc_info* info /* host */);
 enkfmc_status enkfmc_set_stream(enkfmc_handle* h, void* cuda_stream);
@@ -274,6 +277,47 @@ enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_
  * Pointers are device pointers owned by the caller.  Asynchronous. */
 enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const void* Xb, void* Tvals,
                                       void* D, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Batches of independent problems (instances of uneven grid, ensemble size
+ * and radius), one CUDA graph per cycle.  The paper analyses independent
+ * sub-domains in parallel (Section 3, Algorithm 2); whole instances are
+ * independent as well.  A batch keeps references to handles created by the
+ * caller (it does not own them; destroy the batch first).  Each instance's
+ * estimate -> assemble -> analyze runs on one of `nstreams` side streams
+ * forked from `cuda_stream`, instances placed longest first (by their
+ * algorithmic work) on the least loaded stream; enkfmc_batch_capture records
+ * the whole fan-out into one graph, enkfmc_batch_run replays it.
+ * ------------------------------------------------------------------------ */
+typedef struct enkfmc_batch enkfmc_batch;
+
+enkfmc_status enkfmc_batch_create(enkfmc_batch** b, enkfmc_handle* const* handles /* host [nprob] */,
+                                  int32_t nprob, int32_t nstreams /* 1..64 */, void* cuda_stream);
+/* Device buffers of instance i, fixed for the captured graph (layouts as for
+ * enkfmc_estimate / _assemble / _analyze; the handle's observations must be
+ * set).  Rebinding drops the captured graph. */
+enkfmc_status enkfmc_batch_bind(enkfmc_batch* b, int32_t i, const void* Xb, void* Tvals, void* D,
+                                const void* y, const void* Rdiag, const void* Z, void* Xa);
+/* One eager cycle of every instance (set-up and numerical status before any
+ * replay), then the capture of one cycle of all of them into a CUDA graph.
+ * Every instance must be bound.  Turns the handles' kernel timing off. */
+enkfmc_status enkfmc_batch_capture(enkfmc_batch* b);
+/* One cycle of every instance: a single graph launch on the batch's stream. */
+enkfmc_status enkfmc_batch_run(enkfmc_batch* b);
+/* Synchronise; status[i] (host [nprob]) = instance i's first numerical
+ * failure since its last read (enkfmc_get_status), info[i] (host, nullable)
+ * its row or block.  Returns the first failing status or OK. */
+enkfmc_status enkfmc_batch_get_status(enkfmc_batch* b, int32_t* status, int64_t* info);
+/* Side streams and the stream of each instance (host [nprob], nullable). */
+enkfmc_status enkfmc_batch_query(const enkfmc_batch* b, int32_t* nstreams, int32_t* stream_of);
+void enkfmc_batch_destroy(enkfmc_batch* b);
+
+/* Launch tuning of one handle (the autotuner's knobs; results do not change). */
+enum {
+  ENKFMC_TUNE_REGRESS_CTAS_PER_SM = 0  /* CTAs per SM of the regressions' grid-stride
+                                          launch (0 = the default, 64)              */
+};
+enkfmc_status enkfmc_set_tuning(enkfmc_handle* h, int32_t knob, int32_t value);
 
 /* Kernel kinds launched by the library (index into the profiling arrays). */
 enum {

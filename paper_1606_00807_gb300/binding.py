@@ -42,6 +42,7 @@ _H = c_void_p
 SIGNATURES = {
     "enkfmc_create": (c_int32, [POINTER(c_void_p), POINTER(enkfmc_problem), c_void_p]),
     "enkfmc_destroy": (None, [_H]),
+    "enkfmc_check_problem": (c_int32, [POINTER(enkfmc_problem)]),
     "enkfmc_strerror": (c_char_p, [c_int32]),
     "enkfmc_query": (c_int32, [_H, POINTER(enkfmc_info)]),
     "enkfmc_set_stream": (c_int32, [_H, c_void_p]),
@@ -55,6 +56,15 @@ SIGNATURES = {
     "enkfmc_get_status": (c_int32, [_H, POINTER(c_int64)]),
     "enkfmc_export_T_pattern": (c_int32, [_H, c_void_p, c_void_p]),
     "enkfmc_fp64_blocks": (c_int32, [_H, POINTER(c_int32)]),
+    "enkfmc_batch_create": (c_int32, [POINTER(c_void_p), c_void_p, c_int32, c_int32, c_void_p]),
+    "enkfmc_batch_bind": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p]),
+    "enkfmc_batch_capture": (c_int32, [c_void_p]),
+    "enkfmc_batch_run": (c_int32, [c_void_p]),
+    "enkfmc_batch_get_status": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "enkfmc_batch_query": (c_int32, [c_void_p, POINTER(c_int32), c_void_p]),
+    "enkfmc_batch_destroy": (None, [c_void_p]),
+    "enkfmc_set_tuning": (c_int32, [_H, c_int32, c_int32]),
     "enkfmc_debug_block": (c_int32, [_H, c_int32, c_void_p, c_int64, POINTER(c_int64),
                                      POINTER(c_int32)]),
     "enkfmc_profile": (c_int32, [_H, c_int32]),
@@ -68,6 +78,7 @@ NKERNEL = 13
 FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
 FLAG_REFINE_MASK = 0xF00
+TUNE_REGRESS_CTAS_PER_SM = 0
 
 
 def flag_refine_steps(k: int) -> int:
@@ -122,6 +133,18 @@ def _ptr(x):
 def _check(code: int, where: str):
     if code != 0:
         raise EnkfmcError(code, where)
+
+
+def problem_of(w, precision=FP32, flags=0) -> enkfmc_problem:
+    """The enkfmc_problem of a workload-like object."""
+    return enkfmc_problem(w.nlon, w.nlat, w.nlev, w.nvar_3d, w.nvar_2d, int(bool(w.lon_periodic)),
+                          w.r, w.vert_reach, w.N, w.sub_lon, w.sub_lat, precision, w.ridge_c, flags)
+
+
+def check_problem(w, precision=FP32, flags=0) -> int:
+    """enkfmc_check_problem: 0 when the library can run the problem, else its status."""
+    p = problem_of(w, precision, flags)
+    return int(load().enkfmc_check_problem(ctypes.byref(p)))
 
 
 class Handle:
@@ -198,6 +221,9 @@ class Handle:
         _check(self.lib.enkfmc_cycle_host(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
                "enkfmc_cycle_host")
 
+    def set_tuning(self, knob: int, value: int):
+        _check(self.lib.enkfmc_set_tuning(self.h, knob, value), "enkfmc_set_tuning")
+
     def get_status(self):
         info = c_int64(0)
         code = self.lib.enkfmc_get_status(self.h, ctypes.byref(info))
@@ -254,3 +280,55 @@ class Handle:
         _check(self.lib.enkfmc_debug_block(self.h, b, _ptr(buf), buf.size, ctypes.byref(nb),
                                            ctypes.byref(hb)), "debug_block")
         return buf.reshape(nb.value, hb.value + 1), hb.value
+
+
+class Batch:
+    """Independent problems run as one CUDA graph per cycle (enkfmc_batch_*).
+
+    handles: Handle objects (kept alive by the batch); bind() each instance's
+    device tensors, capture() once, then run() replays one cycle of all."""
+
+    def __init__(self, handles, nstreams=8, stream=None):
+        self.lib = load()
+        self.handles = list(handles)
+        arr = (c_void_p * len(self.handles))(*[h.h.value for h in self.handles])
+        b = c_void_p()
+        _check(self.lib.enkfmc_batch_create(ctypes.byref(b), arr, len(self.handles), nstreams,
+                                            c_void_p(stream)), "enkfmc_batch_create")
+        self.b = b
+        self._keep = {}
+
+    def bind(self, i, Xb, T, D, y, R, Z, Xa):
+        self._keep[i] = (Xb, T, D, y, R, Z, Xa)
+        _check(self.lib.enkfmc_batch_bind(self.b, i, _ptr(Xb), _ptr(T), _ptr(D), _ptr(y),
+                                          _ptr(R), _ptr(Z), _ptr(Xa)), "enkfmc_batch_bind")
+
+    def capture(self):
+        _check(self.lib.enkfmc_batch_capture(self.b), "enkfmc_batch_capture")
+
+    def run(self):
+        _check(self.lib.enkfmc_batch_run(self.b), "enkfmc_batch_run")
+
+    def status(self):
+        """(status [nprob], info [nprob]) after synchronising."""
+        st = np.zeros(len(self.handles), np.int32)
+        info = np.zeros(len(self.handles), np.int64)
+        self.lib.enkfmc_batch_get_status(self.b, _ptr(st), _ptr(info))
+        return st, info
+
+    def streams(self):
+        ns = c_int32(0)
+        of = np.zeros(len(self.handles), np.int32)
+        _check(self.lib.enkfmc_batch_query(self.b, ctypes.byref(ns), _ptr(of)), "batch_query")
+        return int(ns.value), of
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.enkfmc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

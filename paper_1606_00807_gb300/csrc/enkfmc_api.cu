@@ -112,6 +112,8 @@ enkfmc_status problem_geom(const enkfmc_problem& p, Geom& g) {
   g.var_off[nvar] = off;
   g.n = off;
   if (!estimate_supported(g, p.precision != ENKFMC_FP64)) return ENKFMC_EINVAL;
+  g.sm_count = 0;  // filled where a device is at hand
+  g.regress_cap = 0;
   return ENKFMC_OK;
 }
 
@@ -127,6 +129,11 @@ enkfmc_status build(enkfmc_handle* h) {
   Geom& g = h->g;
   enkfmc_status gst = problem_geom(p, g);
   if (gst) return gst;
+  if (cudaDeviceGetAttribute(&g.sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
+      cudaSuccess) {
+    (void)cudaGetLastError();
+    g.sm_count = 0;
+  }
   const int nvar = g.nvar;
   h->esize = is_fp64(h) ? sizeof(double) : sizeof(float);
   h->refine_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_NO_SOLVE_REFINEMENT);
@@ -819,6 +826,15 @@ const char* enkfmc_strerror(enkfmc_status s) {
     case ENKFMC_ESTATE: return "call out of order";
   }
   return "unknown status";
+}
+
+enkfmc_status enkfmc_check_problem(const enkfmc_problem* p) {
+  if (!p) return ENKFMC_EINVAL;
+  if (p->flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_BAND |
+                   ENKFMC_FLAG_REFINE_MASK))
+    return ENKFMC_EINVAL;
+  Geom g;
+  return problem_geom(*p, g);
 }
 
 enkfmc_status enkfmc_create(enkfmc_handle** out, const enkfmc_problem* p, void* stream) {

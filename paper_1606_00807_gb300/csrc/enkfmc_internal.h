@@ -19,6 +19,8 @@ struct Geom {
   int32_t nlon, nlat, nlev, nvar3, nvar2, nvar;
   int32_t r, vr, periodic, N, ldN;  // vr: effective vertical reach
   int32_t pmax;
+  int32_t sm_count;      // SMs of the device (launch shapes; host side only)
+  int32_t regress_cap;   // CTAs per SM of the regressions' grid-stride launch
   int64_t n;
   int64_t var_off[kMaxVar + 1];
   int32_t var_lev[kMaxVar];

@@ -107,6 +107,10 @@ extern "C" enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const 
     (void)cudaGetLastError();
     return ENKFMC_ECUDA;
   }
+  if (cudaDeviceGetAttribute(&g.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    g.sm_count = 0;
+  }
   void* base = nullptr;
   if ((st = scratch_address(dev, &base))) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);

@@ -662,12 +662,15 @@ constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 // 1 the rows with 2p <= N, 2 the rows with 2p > N (p/N > 0.5: the rows a
 // single-precision problem regresses in double precision, from FP64 U and C).
 // status may be null (errors then show only as D = NaN with a zero T row).
+// use_ptab = 0 leaves out the typical row's pair table (large stencils whose
+// per-warp workspace would not fit beside it): every row then gathers
+// through the slot-pair tables.
 template <typename T, typename TO, int MR>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     k_regress(const Geom g, const T* __restrict__ U, const T* __restrict__ C, int nH,
               const int32_t* __restrict__ halo, int64_t nitems, const Block* __restrict__ blocks,
               TO* __restrict__ Tout, TO* __restrict__ Dout, double ridge_c, int32_t* status,
-              int ldp, int ldg, int warp_bytes, int sel) {
+              int ldp, int ldg, int warp_bytes, int sel, int use_ptab) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   // per-block slot offsets
@@ -683,14 +686,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
   }
   const int pf = pmax - (g.periodic ? g.r : 0);
   int2* ptab = reinterpret_cast<int2*>(smem + offbytes);
-  build_pair_table(g, pf, ptab);
+  const int ptab_bytes = use_ptab ? pair_table_bytes(pmax, g.r, g.periodic) : 0;
+  if (use_ptab) build_pair_table(g, pf, ptab);
   const int nfull = (pmax + 1) * (pmax + 2) / 2;
-  uint16_t* tri = reinterpret_cast<uint16_t*>(smem + offbytes + pair_table_bytes(pmax, g.r,
-                                                                                 g.periodic));
+  uint16_t* tri = reinterpret_cast<uint16_t*>(smem + offbytes + ptab_bytes);
   uint16_t* ftab = tri + nfull;
   build_gather_tables(g, pmax, tri, ftab);
   __syncthreads();
-  unsigned char* base = smem + offbytes + pair_table_bytes(pmax, g.r, g.periodic) +
+  unsigned char* base = smem + offbytes + ptab_bytes +
                         gather_table_bytes(pmax) + (size_t)warp * warp_bytes;
   int* q = reinterpret_cast<int*>(base);   // [ldp] component labels (q[p] = j)
   int* sl = q + ldp;                        // [ldp] slot of compacted entry (-1 = j)
@@ -759,7 +762,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     // gather the augmented Gram matrix, lower triangle, rows 0..p: the typical
     // row through its pair table, any other row through the slots of i and l
     const int npair = p1 * (p1 + 1) / 2;
-    const bool typical = p == pf && (p == 0 || sl[p - 1] == pf - 1);
+    const bool typical = use_ptab && p == pf && (p == 0 || sl[p - 1] == pf - 1);
     if (typical) {
 #pragma unroll 4
       for (int pi = lane; pi < npair; pi += 32) {
@@ -1229,7 +1232,7 @@ bool covtable_shape(const Geom& g, size_t esize, CovShape& cs) {
 // Launch shape of k_regress (reg = true) or k_adj_regress for elements of
 // `esize` bytes: per-warp workspace, warps per CTA, shared memory.
 struct RegShape {
-  int ldp, ldg, wpc;
+  int ldp, ldg, wpc, use_ptab;
   size_t wb, smem;
 };
 
@@ -1240,19 +1243,25 @@ bool regress_shape(const Geom& g, size_t esize, bool reg, RegShape& rs) {
   size_t wb = (size_t)rs.ldp * 3 * sizeof(int) +
               esize * ((size_t)rs.ldp * rs.ldg + (reg ? 4 : 3) * (size_t)rs.ldp);
   rs.wb = (wb + 15) / 16 * 16;
-  size_t offbytes = (3 * (size_t)g.pmax + 15) / 16 * 16;
-  if (reg)
-    offbytes += pair_table_bytes(g.pmax, g.r, g.periodic) + gather_table_bytes(g.pmax);
-  int wpc = (int)(((size_t)96 * 1024 - std::min<size_t>(offbytes, 96 * 1024)) / rs.wb);
-  if (wpc > 8) wpc = 8;
-  if (wpc < 1) {
-    wpc = (int)(((size_t)200 * 1024 - std::min<size_t>(offbytes, 200 * 1024)) / rs.wb);
-    if (wpc < 1) return false;
+  for (int ptab = reg ? 1 : 0; ptab >= 0; --ptab) {  // without the pair table if need be
+    size_t offbytes = (3 * (size_t)g.pmax + 15) / 16 * 16;
+    if (reg)
+      offbytes += (ptab ? pair_table_bytes(g.pmax, g.r, g.periodic) : 0) +
+                  gather_table_bytes(g.pmax);
+    int wpc = (int)(((size_t)96 * 1024 - std::min<size_t>(offbytes, 96 * 1024)) / rs.wb);
     if (wpc > 8) wpc = 8;
+    if (wpc < 1) {
+      wpc = (int)(((size_t)200 * 1024 - std::min<size_t>(offbytes, 200 * 1024)) / rs.wb);
+      if (wpc > 8) wpc = 8;
+    }
+    if (wpc >= 1) {
+      rs.wpc = wpc;
+      rs.use_ptab = ptab;
+      rs.smem = offbytes + rs.wb * wpc;
+      return true;
+    }
   }
-  rs.wpc = wpc;
-  rs.smem = offbytes + rs.wb * wpc;
-  return true;
+  return false;
 }
 
 }  // namespace
@@ -1324,12 +1333,15 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
   if (e != cudaSuccess) return e;
   // a grid-stride loop over the rows: enough CTAs for an even tail, few enough
   // that each amortises its shared tables (measured on the T63 rows: 64 CTAs
-  // per SM beat 24, 32, 128 and one CTA per 8 rows)
+  // per SM beat 24, 32, 128 and one CTA per 8 rows; a handle's tuning can
+  // change the cap)
   int64_t grid = (nitems + rs.wpc - 1) / rs.wpc;
-  if (grid > 152 * 64) grid = 152 * 64;
+  const int64_t cap = (int64_t)(g.sm_count > 0 ? g.sm_count : 152) *
+                      (g.regress_cap > 0 ? g.regress_cap : 64);
+  if (grid > cap) grid = cap;
   k_regress<T, TO, MR><<<(unsigned)grid, 32 * rs.wpc, rs.smem, s>>>(
       g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, rs.ldp, rs.ldg,
-      (int)rs.wb, sel);
+      (int)rs.wb, sel, rs.use_ptab);
   return cudaGetLastError();
 }
 

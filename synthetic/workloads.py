@@ -111,3 +111,28 @@ SMALL_T63 = Workload(
 WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96,
                                  SMALL_3D, SMALL_ILL, SMALL_R1, SMALL_R1_N16, SMALL_RIDGE,
                                  SMALL_T63)}
+
+
+def batch_instances(count: int = 256, base_seed: int = 3000):
+    """The batch of independent problems of uneven size: instance i (seed
+    base_seed + i) draws its grid from 24 x 12 to 96 x 48 (nlon in {24, 36, ...,
+    96}, nlat = nlon / 2), 1-7 levels, 1-5 variables, N in [20, 120] and
+    r in {1, 2, 3, 4}; fields as in the 32 x 16 case (correlation length 3 cells,
+    unit variance, vertical correlation 0.5), half of the components observed
+    with R = 0.01, 12 x 12 sub-domains (ragged at the edges)."""
+    from .philox import uint32_stream
+    out = []
+    for i in range(count):
+        seed = base_seed + i
+        k = [int(x) for x in uint32_stream(seed, 9, 6)]
+        nlon = 24 + 12 * (k[0] % 7)
+        nlev = 1 + k[1] % 7
+        nvar = 1 + k[2] % 5
+        N = 20 + k[3] % 101
+        r = 1 + k[4] % 4
+        out.append(Workload(
+            name=f"batch{i:03d}_{nlon}x{nlon // 2}x{nlev}x{nvar}_n{N}_r{r}", nlon=nlon,
+            nlat=nlon // 2, nlev=nlev, nvar_3d=nvar, nvar_2d=0, r=r, N=N, sub_lon=12,
+            sub_lat=12, sigma2=(1.0,) * nvar, corr_len=3.0, rho_vert=0.5, obs="random",
+            obs_frac=0.5, r_frac=0.01, ridge_c=1e-3, seed=seed))
+    return out

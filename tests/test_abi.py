@@ -104,3 +104,20 @@ def test_noalloc_refuses_unsupported_geometry_before_any_cuda_call(lib):
     if not has_gpu:   # valid and within the limit: passes validation, then finds no device
         ok = P(nlon=96, nlat=72, nlev=3, N=80)
         assert lib.enkfmc_estimate_noalloc(ctypes.byref(ok), 1, 1, 1, None) == 7
+
+
+def test_check_problem_without_device(lib):
+    """enkfmc_check_problem validates on the host: every instance of the 256-problem
+    batch is supported; out-of-range descriptions are refused."""
+    from paper_1606_00807_gb300 import binding as B
+    from synthetic import WORKLOADS
+    from synthetic.workloads import batch_instances
+    assert all(B.check_problem(w) == 0 for w in batch_instances())
+    for name in ("t63_192x96x29_n80_r2", "t63_192x96x29_n40_r2", "t127_384x192x29_n96_r3"):
+        assert B.check_problem(WORKLOADS[name]) == 0
+        assert B.check_problem(WORKLOADS[name], precision=B.FP64) == 0
+    w = WORKLOADS["tiny_32x16_n20_r2"]
+    for bad in (w.with_(N=1), w.with_(N=129), w.with_(nlon=4), w.with_(sub_lon=0),
+                w.with_(r=17)):
+        assert B.check_problem(bad) == 1
+    assert B.check_problem(w, flags=1 << 20) == 1
