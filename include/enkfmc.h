@@ -219,8 +219,9 @@ enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
  * anomalies (Eq. 5).  Requires enkfmc_analyze on this handle, whose inputs
  * (Xb, y, Rdiag, Z) and the Tvals/D of enkfmc_assemble must still hold the
  * same values.  Outputs are overwritten; they may not alias the inputs.
- * Contributions of overlapping boundaries are summed with atomic adds, so
- * the last bits can vary from run to run. */
+ * Contributions of rows that share predecessors, and of overlapping
+ * boundaries, are summed in a fixed order (per component, its blocks in
+ * increasing order): the gradients are reproducible bit for bit. */
 enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void* y_bar,
                                      void* Rdiag_bar, void* Xb_bar);
 

@@ -385,7 +385,7 @@ void release(enkfmc_handle* h) {
                   h->d_band,  h->d_invdiag, h->d_rhs, h->d_res,     h->d_vhi,    h->d_vlo,
                   h->d_Xb,    h->d_y,       h->d_R,   h->d_Z,       h->d_Xa,     h->d_T,
                   h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
-                  h->d_Ubar,  h->d_U64,     h->d_C64, h->d_W,      h->d_bfail,  h->d_fb_cnt,
+                  h->d_Eo,    h->d_Fo,      h->d_Vo,  h->d_Ko,  h->d_U64,     h->d_C64, h->d_W,      h->d_bfail,  h->d_fb_cnt,
                   h->d_fb_blocks, h->d_fb_band, h->d_c1max};
   for (void* b : bufs) dfree(b);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
@@ -730,16 +730,13 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
     if ((st = dalloc(h, &h->d_bT, es * rows * g.ldN))) return st;
     if ((st = dalloc(h, &h->d_dxT, es * rows * g.ldN))) return st;
     if ((st = dalloc(h, &h->d_lamT, es * rows * g.ldN))) return st;
-    if ((st = dalloc(h, &h->d_Ubar, es * (size_t)g.n * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_Eo, es * rows * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_Fo, es * rows * g.ldN))) return st;
+    if ((st = dalloc(h, &h->d_Vo, es * rows * std::max(1, g.pmax)))) return st;
+    if ((st = dalloc(h, &h->d_Ko, es * rows))) return st;
     if (h->refine_solve && sizeof(T) == sizeof(float)) {
       if ((st = dalloc(h, &h->d_W, es * rows * g.N * 2))) return st;  // W, then residuals
     }
-  }
-  CUDA_TRY(cudaMemsetAsync(h->d_Ubar, 0, es * (size_t)g.n * g.ldN, h->stream));
-  CUDA_TRY(cudaMemsetAsync(Xb_bar, 0, es * (size_t)g.n * g.N, h->stream));
-  if (h->m > 0) {
-    CUDA_TRY(cudaMemsetAsync(y_bar, 0, es * (size_t)h->m, h->stream));
-    CUDA_TRY(cudaMemsetAsync(R_bar, 0, es * (size_t)h->m, h->stream));
   }
   const T* dX2 = (h->refine_solve && sizeof(T) == sizeof(float)) ? (const T*)h->d_res : nullptr;
   const T* Tg = (const T*)h->T_assembled;
@@ -780,15 +777,6 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
     });
     if (st) return st;
   }
-  if (h->m > 0) {
-    st = timed(h, ENKFMC_K_ADJOINT, [&] {
-      return launch_adj_obs<T>(g, h->d_blocks, h->nblock, h->nb_max, h->d_obs_of, h->m,
-                               (const T*)h->last_Xb, (const T*)h->last_y, (const T*)h->last_R,
-                               (const T*)h->last_Z, (const T*)h->d_lam, (const T*)h->d_rhs, dX2,
-                               Xb_bar, y_bar, R_bar, h->stream);
-    });
-    if (st) return st;
-  }
   st = timed(h, ENKFMC_K_ADJOINT, [&] {
     return launch_adj_ab<T>(g, h->d_blocks, h->nblock, h->nb_max, Tg, (const T*)h->d_Te,
                             (const T*)h->d_lam, (const T*)h->d_rhs, dX2, (T*)h->d_aT,
@@ -799,12 +787,25 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
     return launch_adj_regressions<T>(g, h->d_blocks, h->nblock, h->nb_max, stats_of<T>(h), Tg, Dg,
                                      (const T*)h->d_Te, (const T*)h->d_De, (const T*)h->d_aT,
                                      (const T*)h->d_bT, (const T*)h->d_dxT, (const T*)h->d_lamT,
-                                     h->d_ptab, h->d_gtab, (T*)h->d_Ubar, h->prob.ridge_c,
-                                     h->d_status, h->stream, nk);
+                                     h->d_ptab, h->d_gtab, (T*)h->d_Eo, (T*)h->d_Fo,
+                                     (T*)h->d_Vo, (T*)h->d_Ko, h->prob.ridge_c, h->d_status,
+                                     h->stream, nk);
+  });
+  if (st) return st;
+  // Ubar per extended row (into aT, free once the regressions are done), then
+  // every component and observation from the blocks holding it, in order
+  st = timed(h, ENKFMC_K_ADJOINT, [&] {
+    return launch_adj_gather<T>(g, h->d_blocks, h->nblock, h->nb_max, Tg, (const T*)h->d_Te,
+                                (const T*)h->d_U, (const T*)h->d_Eo, (const T*)h->d_Fo,
+                                (const T*)h->d_Vo, (const T*)h->d_Ko, (T*)h->d_aT, h->stream);
   });
   if (st) return st;
   return timed(h, ENKFMC_K_ADJOINT, [&] {
-    return launch_adj_finish<T>(g, (const T*)h->d_Ubar, Xa_bar, Xb_bar, h->stream);
+    return launch_adj_owner<T>(g, h->d_blocks, h->nsubx, h->nsuby, h->prob.sub_lon,
+                               h->prob.sub_lat, h->d_obs_of, h->m, (const T*)h->last_Xb,
+                               (const T*)h->last_y, (const T*)h->last_R, (const T*)h->last_Z,
+                               (const T*)h->d_aT, (const T*)h->d_lamT, (const T*)h->d_dxT, Xa_bar,
+                               Xb_bar, y_bar, R_bar, h->stream);
   });
 }
 

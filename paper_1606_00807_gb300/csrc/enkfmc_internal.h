@@ -273,7 +273,8 @@ struct enkfmc_handle {
   // reverse-pass buffers (allocated on the first enkfmc_analyze_adjoint)
   void *d_lam = nullptr, *d_aT = nullptr, *d_bT = nullptr, *d_dxT = nullptr, *d_lamT = nullptr;
   void* d_W = nullptr;    // the reverse pass's right-hand side W (refinement)
-  void* d_Ubar = nullptr;
+  void *d_Eo = nullptr, *d_Fo = nullptr, *d_Vo = nullptr, *d_Ko = nullptr;  // per extended
+                          // row: the regression adjoint's e, f, v (slots), kappa
 
   // kernel timing (events bracket each launch while enabled)
   struct Rec {
@@ -435,23 +436,33 @@ template <typename T>
 cudaError_t launch_adj_seed(const Geom& g, const Block* blocks, int nblock, int nb_max,
                             const T* Xa_bar, T* W, cudaStream_t s);
 template <typename T>
-cudaError_t launch_adj_obs(const Geom& g, const Block* blocks, int nblock, int nb_max,
-                           const int32_t* obs_of, int64_t m, const T* Xb, const T* y, const T* R,
-                           const T* Z, const T* lam, const T* dX, const T* dX2, T* Xb_bar,
-                           T* y_bar, T* R_bar, cudaStream_t s);
-template <typename T>
 cudaError_t launch_adj_ab(const Geom& g, const Block* blocks, int nblock, int nb_max,
                           const T* Tg, const T* Te, const T* lam, const T* dX, const T* dX2,
                           T* aT, T* bT, T* dxT, T* lamT, cudaStream_t s);
+// Reverse pass through the regressions of every extended row: stores the
+// row's e, f ([ext row][ldN]), v ([ext row][pmax], in its slots) and kappa.
 template <typename T>
 cudaError_t launch_adj_regressions(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                    const EstStats<T>& st, const T* Tg, const T* Dg, const T* Te,
                                    const T* De, const T* aT, const T* bT, const T* dxT,
-                                   const T* lamT, const int2* ptab, const uint16_t* gtab, T* Ubar,
-                                   double ridge_c, int32_t* status, cudaStream_t s, int* nk);
+                                   const T* lamT, const int2* ptab, const uint16_t* gtab, T* Eo,
+                                   T* Fo, T* Vo, T* Ko, double ridge_c, int32_t* status,
+                                   cudaStream_t s, int* nk);
+// Ubar of every extended row from the stored terms of the rows that hold it,
+// in slot order: Ub[row][ldN] (k_adjoint.cu).
 template <typename T>
-cudaError_t launch_adj_finish(const Geom& g, const T* Ubar, const T* Xa_bar, T* Xb_bar,
-                              cudaStream_t s);
+cudaError_t launch_adj_gather(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                              const T* Tg, const T* Te, const T* U, const T* Eo, const T* Fo,
+                              const T* Vo, const T* Ko, T* Ub, cudaStream_t s);
+// dL/dX^b, dL/dy, dL/d diag(R) of every component and observation from the
+// blocks that hold it, in block order: the anomaly projection of the summed
+// Ubar, dL/dX^a, and the observation terms (k_adjoint.cu).
+template <typename T>
+cudaError_t launch_adj_owner(const Geom& g, const Block* blocks, int nsubx, int nsuby,
+                             int sub_lon, int sub_lat, const int32_t* obs_of, int64_t m,
+                             const T* Xb, const T* y, const T* R, const T* Z, const T* Ub,
+                             const T* lamT, const T* dxT, const T* Xa_bar, T* Xb_bar, T* y_bar,
+                             T* R_bar, cudaStream_t s);
 
 // Single-precision refinement residual res = rhs - A dX (two passes; vhi, vlo
 // are scratch of the size of dX).  rhs: Eq. 11's observation term formed from

@@ -75,16 +75,14 @@ __device__ __forceinline__ void ldg4v(const double* p, double (&v)[4]) {
   const double2 b = reinterpret_cast<const double2*>(p)[1];
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
-// p[0..3] += v (one 16-byte vector atomic in single precision; entries that
-// lie at or beyond N add zero, the padding of the member dimension)
-__device__ __forceinline__ void atomic_add4(float* p, const float (&v)[4]) {
-  atomicAdd(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+// four consecutive elements to 16-byte aligned global memory
+__device__ __forceinline__ void sts4g(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
-__device__ __forceinline__ void atomic_add4(double* p, const double (&v)[4]) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a) atomicAdd(p + a, v[a]);
+__device__ __forceinline__ void sts4g(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
-
 // ---------------------------------------------------------------------------
 // Anomalies: U[l][m] = X[m][l] - mean_m X[m][l], accumulated and subtracted in
 // TU; U32 (optional) receives the same anomalies rounded to single precision
@@ -941,20 +939,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 //   Dbar_j = <a_j, b_j> / D_j^2, ebar = 2 Dbar e / (N - 1),
 //   v = (G + lambda I)^-1 betabar (factor recomputed from the covariance table),
 //   f = ebar + U_P^T v,  Ubar_qi += v_i e - beta_i f - kappa U_qi,  Ubar_j += f,
-// kappa = 2 (c / p) v.beta when the ridge is active.  Ubar is accumulated with
-// atomic adds (rows share predecessors).
+// kappa = 2 (c / p) v.beta when the ridge is active.  Rows share predecessors,
+// so the row does not add into Ubar itself: it stores e and f (Eo, Fo
+// [ext row][ldN]), v in its slots (Vo [ext row][pmax]) and kappa (Ko), and
+// k_adj_gather sums each component's terms in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 // T: the arithmetic and the element type of U and C (FP64 for the rows a
 // single-precision problem regressed in double precision); TS: the element
-// type of T, D, the adjoint rows and Ubar.  sel as in k_regress.
+// type of T, D, the adjoint rows and the stored terms.  sel as in k_regress.
 template <typename T, typename TS>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
     const Geom g, const Block* __restrict__ blocks, const T* __restrict__ U,
     const T* __restrict__ C, int nH, const TS* __restrict__ Tg, const TS* __restrict__ Dg,
     const TS* __restrict__ Te, const TS* __restrict__ De, const TS* __restrict__ aT,
     const TS* __restrict__ bT, const TS* __restrict__ dxT, const TS* __restrict__ lamT,
-    const int2* __restrict__ ptab, const uint16_t* __restrict__ gtab, TS* __restrict__ Ubar,
-    double ridge_c, int32_t* status, int ldp, int ldg, int warp_bytes, int sel) {
+    const int2* __restrict__ ptab, const uint16_t* __restrict__ gtab, TS* __restrict__ Eo,
+    TS* __restrict__ Fo, TS* __restrict__ Vo, TS* __restrict__ Ko, double ridge_c,
+    int32_t* status, int ldp, int ldg, int warp_bytes, int sel) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   signed char* off = reinterpret_cast<signed char*>(smem);
@@ -1038,11 +1039,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       for (int a = 0; a < 4; ++a) o[a] = T(0);
     }
   };
-  auto add4 = [&](TS* dst, const T (&d)[4]) {
-    TS c4[4];
+  // this row's outputs: e, f (members 4 lane .. 4 lane + 3), v in its slots, kappa
+  auto store = [&](const T (&e4)[4], const T (&f4)[4], int np, T kap) {
+    if (m0 < ldN) {
+      TS a4[4], c4[4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) c4[a] = (TS)d[a];
-    atomic_add4(dst, c4);
+      for (int a = 0; a < 4; ++a) {
+        a4[a] = (TS)e4[a];
+        c4[a] = (TS)f4[a];
+      }
+      sts4g(Eo + rowj * ldN + m0, a4);
+      sts4g(Fo + rowj * ldN + m0, c4);
+    }
+    TS* vrow = Vo + rowj * pmax;
+    for (int s = lane; s < pmax; s += 32) vrow[s] = TS(0);
+    __syncwarp();
+    for (int i = lane; i < np; i += 32) vrow[sl[i]] = (TS)va[i];
+    if (lane == 0) Ko[rowj] = (TS)kap;
   };
   // e = u - U_P^T beta; a_j, b_j in registers
   T e[4], aj[4], bj[4];
@@ -1143,6 +1156,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
     const int err = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p, p, lane, gtab);
     if (err) {
       if (lane == 0) record_error(status, err, rowj);
+      const T z4[4] = {T(0), T(0), T(0), T(0)};
+      store(z4, z4, 0, T(0));  // defined (zero) terms for the failed row
       return;
     }
     // v = (L L^T)^-1 betabar in va
@@ -1160,17 +1175,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
 #pragma unroll
       for (int a = 0; a < 4; ++a) f[a] = fma(u4[a], vi, f[a]);
     }
-    // Ubar_qi += v_i e - beta_i f - kappa U_qi (U read only with the ridge)
-    for (int i = 0; i < p; ++i) {
-      const T vi = va[i], bi = vb[i];
-      T u4[4] = {T(0), T(0), T(0), T(0)}, d4[4];
-      if (kappa != T(0)) ld4(U + (int64_t)q[i] * ldN, u4);
-#pragma unroll
-      for (int a = 0; a < 4; ++a) d4[a] = vi * e[a] - bi * f[a] - kappa * u4[a];
-      if (m0 < N) add4(Ubar + (int64_t)q[i] * ldN + m0, d4);
-    }
   }
-  if (m0 < N) add4(Ubar + (int64_t)jlab * ldN + m0, f);
+  store(e, f, p, kappa);
 }
 
 }  // namespace
@@ -1367,7 +1373,8 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
                                const T* U, const T* C, const TS* Tg, const TS* Dg, const TS* Te,
                                const TS* De, const TS* aT, const TS* bT, const TS* dxT,
                                const TS* lamT, const int2* ptab, const uint16_t* gtab,
-                               TS* Ubar, double ridge_c, int32_t* status, int sel,
+                               TS* Eo, TS* Fo, TS* Vo, TS* Ko, double ridge_c, int32_t* status,
+                               int sel,
                                cudaStream_t s) {
   if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
     return cudaErrorInvalidConfiguration;
@@ -1379,7 +1386,8 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
   if (e != cudaSuccess) return e;
   const dim3 grid((nb_max + rs.wpc - 1) / rs.wpc, nblock);
   k_adj_regress<T, TS><<<grid, 32 * rs.wpc, rs.smem, s>>>(
-      g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT, dxT, lamT, ptab, gtab, Ubar, ridge_c, status,
+      g, blocks, U, C, nH, Tg, Dg, Te, De, aT, bT, dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c,
+      status,
       rs.ldp, rs.ldg, (int)rs.wb, sel);
   return cudaGetLastError();
 }
@@ -1441,20 +1449,23 @@ template <typename T>
 cudaError_t launch_adj_regressions(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                    const EstStats<T>& st, const T* Tg, const T* Dg, const T* Te,
                                    const T* De, const T* aT, const T* bT, const T* dxT,
-                                   const T* lamT, const int2* ptab, const uint16_t* gtab, T* Ubar,
+                                   const T* lamT, const int2* ptab, const uint16_t* gtab, T* Eo,
+                                   T* Fo, T* Vo, T* Ko,
                                    double ridge_c, int32_t* status, cudaStream_t s, int* nk) {
   if (!st.C64) {
     ++*nk;
     return launch_adj_regress<T, T>(g, blocks, nblock, nb_max, st.U, st.C, Tg, Dg, Te, De, aT, bT,
-                                    dxT, lamT, ptab, gtab, Ubar, ridge_c, status, 0, s);
+                                    dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c, status, 0,
+                                    s);
   }
   *nk += 2;
   cudaError_t e = launch_adj_regress<T, T>(g, blocks, nblock, nb_max, st.U, st.C, Tg, Dg, Te, De,
-                                           aT, bT, dxT, lamT, ptab, gtab, Ubar, ridge_c, status,
-                                           1, s);
+                                           aT, bT, dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c,
+                                           status, 1, s);
   if (e != cudaSuccess) return e;
   return launch_adj_regress<double, T>(g, blocks, nblock, nb_max, st.U64, st.C64, Tg, Dg, Te, De,
-                                       aT, bT, dxT, lamT, ptab, gtab, Ubar, ridge_c, status, 2, s);
+                                       aT, bT, dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c,
+                                       status, 2, s);
 }
 
 #define INST(T)                                                                                  \
@@ -1469,8 +1480,8 @@ cudaError_t launch_adj_regressions(const Geom& g, const Block* blocks, int nbloc
                                              cudaStream_t, int*);                                \
   template cudaError_t launch_adj_regressions<T>(                                               \
       const Geom&, const Block*, int, int, const EstStats<T>&, const T*, const T*, const T*,     \
-      const T*, const T*, const T*, const T*, const T*, const int2*, const uint16_t*, T*, double, \
-      int32_t*, cudaStream_t, int*);
+      const T*, const T*, const T*, const T*, const T*, const int2*, const uint16_t*, T*, T*, T*, \
+      T*, double, int32_t*, cudaStream_t, int*);
 INST(float)
 INST(double)
 #undef INST
