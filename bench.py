@@ -77,6 +77,8 @@ def parse_args(argv=None):
                     help="only the batch of 256 uneven problems (one CUDA graph per cycle)")
     ap.add_argument("--tune", action="store_true",
                     help="autotune every batch shape missing from the tuning cache")
+    ap.add_argument("--tune-max", type=int, default=64,
+                    help="with --tune: the most expensive shapes tuned (the rest keep defaults)")
     ap.add_argument("--tuning", default=TUNING_CACHE,
                     help="tuning cache (JSON) read, and with --tune written")
     return ap.parse_args(argv)
@@ -625,10 +627,14 @@ def batch_line(args, dev):
     ws = batch_instances()
     cache = autotune.load_cache(args.tuning)
     tuned0 = len(cache)
+    # with --tune: the shapes with the most work first (the members times the
+    # stencil slots times the components), up to --tune-max of them
+    work = lambda w: w.N * w.n * (2 * w.r + 1) ** 2 * min(3, w.nlev)
+    to_tune = set(sorted(range(len(ws)), key=lambda i: -work(ws[i]))[:args.tune_max])
     stream = torch.cuda.current_stream(dev)
     insts = []
     put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    for w in ws:
+    for iw, w in enumerate(ws):
         inp = make_inputs(w, np.float32)
         Xb, y, R, Z = put(inp.Xb), put(inp.y), put(inp.R), put(inp.Z)
         choice = cache.get(autotune.shape_key(w, B.FP32))
@@ -638,7 +644,7 @@ def batch_line(args, dev):
         T = torch.empty((w.n, h.info.pmax), device=dev)
         D = torch.empty(w.n, device=dev)
         Xa = torch.empty_like(Xb)
-        if choice is None and args.tune:
+        if choice is None and args.tune and iw in to_tune:
             choice = autotune.tune(w, inp.obs_idx, (Xb, T, D, y, R, Z, Xa), cache=cache)
             if choice["flags"] != h.problem.flags:
                 h.close()

@@ -183,8 +183,8 @@ enkfmc_status enkfmc_estimate(enkfmc_handle* h, const void* Xb, void* Tvals, voi
  * precision a block whose factorisation meets a non-positive pivot (a
  * condition number beyond what single precision holds) is assembled again
  * from the same T and D in double precision and factored, and later solved,
- * in double; ENOTSPD is reported only if that fails too, or if more than
- * max(8, nblock / 8) blocks need it.  Xb: [N][n]
+ * in double; ENOTSPD is reported only if that fails too.  (The handle holds
+ * room for every block in double precision: twice the band's bytes.)  Xb: [N][n]
  * (when it is the same pointer as in the last enkfmc_estimate on this
  * handle, the anomalies and covariances computed there are reused, so its
  * contents must not change in between);

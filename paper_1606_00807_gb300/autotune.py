@@ -81,14 +81,22 @@ def tune(w, obs_idx, bufs, precision=B.FP32, reps=2, cache=None, flags=0):
     stream = torch.cuda.current_stream().cuda_stream
     for path in paths:
         h = B.Handle.from_workload(w, precision=precision, stream=stream, flags=flags | path)
-        h.set_observations(obs_idx)
-        for cap in REGRESS_CAPS:
-            h.set_tuning(B.TUNE_REGRESS_CTAS_PER_SM, cap)
-            ms = _time_cycles(torch, h, bufs, reps)
-            timings[f"band{path}_cap{cap}"] = ms
-            if best is None or ms < best["ms"]:
-                best = {"flags": flags | path, "regress_cap": cap, "ms": ms}
-        h.close()
+        try:
+            h.set_observations(obs_idx)
+            for cap in REGRESS_CAPS:
+                h.set_tuning(B.TUNE_REGRESS_CTAS_PER_SM, cap)
+                try:
+                    ms = _time_cycles(torch, h, bufs, reps)
+                except B.EnkfmcError as exc:   # a candidate that fails is not chosen
+                    timings[f"band{path}_cap{cap}"] = f"failed: {exc}"
+                    continue
+                timings[f"band{path}_cap{cap}"] = ms
+                if best is None or ms < best["ms"]:
+                    best = {"flags": flags | path, "regress_cap": cap, "ms": ms}
+        finally:
+            h.close()
+    if best is None:
+        raise RuntimeError(f"no launch setting of {key} completed: {timings}")
     best["timings"] = timings
     if cache is not None:
         cache[key] = best

@@ -313,7 +313,7 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
   if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
   if (!is_fp64(h)) {  // double-precision pool for blocks whose FP32 factorisation fails
-    h->fb_cap = std::max(8, h->nblock / 4);
+    h->fb_cap = h->nblock;  // room for every block: ill-conditioned problems can need most
     h->fb_stride = (int64_t)h->nb_max * (h->hb_max + 1);
     if ((st = dalloc(h, &h->d_bfail, sizeof(int32_t) * h->nblock))) return st;
     if ((st = dalloc(h, &h->d_c1max, sizeof(float) * h->nblock))) return st;

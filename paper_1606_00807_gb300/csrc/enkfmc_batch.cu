@@ -59,9 +59,7 @@ enkfmc_status run_instance(enkfmc_batch* b, int i, cudaStream_t s) {
 
 }  // namespace
 
-extern "C" {
-
-enkfmc_status enkfmc_batch_create(enkfmc_batch** out, enkfmc_handle* const* handles,
+extern "C" enkfmc_status enkfmc_batch_create(enkfmc_batch** out, enkfmc_handle* const* handles,
                                   int32_t nprob, int32_t nstreams, void* cuda_stream) {
   if (!out || !handles || nprob < 1 || nstreams < 1 || nstreams > 64) return ENKFMC_EINVAL;
   *out = nullptr;
@@ -113,7 +111,7 @@ enkfmc_status enkfmc_batch_create(enkfmc_batch** out, enkfmc_handle* const* hand
   return ENKFMC_OK;
 }
 
-enkfmc_status enkfmc_batch_bind(enkfmc_batch* b, int32_t i, const void* Xb, void* Tvals, void* D,
+extern "C" enkfmc_status enkfmc_batch_bind(enkfmc_batch* b, int32_t i, const void* Xb, void* Tvals, void* D,
                                 const void* y, const void* Rdiag, const void* Z, void* Xa) {
   if (!b || i < 0 || i >= (int)b->h.size() || !Xb || !Tvals || !D || !Xa || Xa == Xb)
     return ENKFMC_EINVAL;
@@ -131,12 +129,12 @@ enkfmc_status enkfmc_batch_bind(enkfmc_batch* b, int32_t i, const void* Xb, void
   return ENKFMC_OK;
 }
 
-enkfmc_status enkfmc_batch_capture(enkfmc_batch* b) {
-  if (!b) return ENKFMC_EINVAL;
+namespace {
+
+// The eager cycle and the capture (see enkfmc_batch_capture); the handles'
+// streams are the side streams meanwhile.
+enkfmc_status capture_cycle(enkfmc_batch* b) {
   const int n = (int)b->h.size(), ns = (int)b->side.size();
-  for (int i = 0; i < n; ++i)
-    if (!b->bind[i].set) return ENKFMC_ESTATE;
-  for (enkfmc_handle* h : b->h) enkfmc_profile(h, 0);
   // one eager cycle per instance: the lazy set-up of every launch happens
   // outside the capture, and numerical failures show before any replay
   for (int i = 0; i < n; ++i) {
@@ -180,9 +178,25 @@ enkfmc_status enkfmc_batch_capture(enkfmc_batch* b) {
     b->exec = nullptr;
     return st;
   }
-  for (int i = 0; i < n; ++i) enkfmc_set_stream(b->h[i], b->stream);
   return ENKFMC_OK;
 }
+
+}  // namespace
+
+extern "C" enkfmc_status enkfmc_batch_capture(enkfmc_batch* b) {
+  if (!b) return ENKFMC_EINVAL;
+  const int n = (int)b->h.size();
+  for (int i = 0; i < n; ++i)
+    if (!b->bind[i].set) return ENKFMC_ESTATE;
+  for (enkfmc_handle* h : b->h) enkfmc_profile(h, 0);
+  const enkfmc_status st = capture_cycle(b);
+  // success or not, every handle is back on the batch's stream: the side
+  // streams end with the batch
+  for (int i = 0; i < n; ++i) enkfmc_set_stream(b->h[i], b->stream);
+  return st;
+}
+
+extern "C" {
 
 enkfmc_status enkfmc_batch_run(enkfmc_batch* b) {
   if (!b) return ENKFMC_EINVAL;

@@ -52,6 +52,14 @@ def test_batch_graph_equals_eager_and_matches_oracle(torch_cuda):
     from paper_1606_00807_gb300 import binding as B
     ws = batch_instances()[:16]
     insts = [_instance(torch, B, w) for w in ws]
+    try:
+        _graph_equals_eager_and_oracle(torch, B, ws, insts)
+    finally:
+        for _, h, _ in insts:
+            h.close()
+
+
+def _graph_equals_eager_and_oracle(torch, B, ws, insts):
     eager = []
     for w, (inp, h, b) in zip(ws, insts):
         _eager(h, b)
@@ -93,8 +101,6 @@ def test_batch_graph_equals_eager_and_matches_oracle(torch_cuda):
               f"Xa {eX:.2e} dX {edX:.2e} fp64 blocks {h.fp64_blocks()}")
         assert max(eT, eD, eDe, eX, edX) < TOL[1], (w.name, eT, eD, eDe, eX, edX)
     batch.close()
-    for _, h, _ in insts:
-        h.close()
 
 
 def test_autotuner_choice_leaves_results_unchanged(torch_cuda, tmp_path):
@@ -102,8 +108,11 @@ def test_autotuner_choice_leaves_results_unchanged(torch_cuda, tmp_path):
     from paper_1606_00807_gb300 import autotune, binding as B
     w = batch_instances()[2]
     inp, h, b = _instance(torch, B, w)
-    _eager(h, b)
-    h.check()
+    try:
+        _eager(h, b)
+        h.check()
+    finally:
+        h.close()
     ref = b["Xa"].cpu().numpy().copy()
     cache = {}
     bufs = (b["Xb"], b["T"], b["D"], b["y"], b["R"], b["Z"], b["Xa"])
@@ -116,14 +125,15 @@ def test_autotuner_choice_leaves_results_unchanged(torch_cuda, tmp_path):
     h2 = B.Handle.from_workload(w, precision=B.FP32,
                                 stream=torch.cuda.current_stream().cuda_stream,
                                 flags=choice["flags"])
-    h2.set_observations(inp.obs_idx)
-    autotune.apply(h2, choice)
-    _eager(h2, b)
-    h2.check()
+    try:
+        h2.set_observations(inp.obs_idx)
+        autotune.apply(h2, choice)
+        _eager(h2, b)
+        h2.check()
+    finally:
+        h2.close()
     got = b["Xa"].cpu().numpy()
     if choice["flags"] == 0:
         assert np.array_equal(got, ref)       # same kernels, another grid cap
     else:                                      # CUDA-core band path: same analysis to FP32
         assert per_variable_err(w, np.arange(w.n), (got - inp.Xb).T, (ref - inp.Xb).T) < TOL[1]
-    h.close()
-    h2.close()
