@@ -285,10 +285,11 @@ enkfmc_status enkfmc_estimate_noalloc(const enkfmc_problem* p, const void* Xb, v
  * sub-domains in parallel (Section 3, Algorithm 2); whole instances are
  * independent as well.  A batch keeps references to handles created by the
  * caller (it does not own them; destroy the batch first).  Each instance's
- * estimate -> assemble -> analyze runs on one of `nstreams` side streams
- * forked from `cuda_stream`, instances placed longest first (by their
- * algorithmic work) on the least loaded stream; enkfmc_batch_capture records
- * the whole fan-out into one graph, enkfmc_batch_run replays it.
+ * estimate -> assemble -> analyze runs on one of `nstreams` side streams,
+ * instances placed longest first (by their algorithmic work) on the least
+ * loaded stream; enkfmc_batch_capture records the whole fan-out into one
+ * graph (captured from a private stream, so `cuda_stream` may be the legacy
+ * default stream 0), enkfmc_batch_run launches it on `cuda_stream`.
  * ------------------------------------------------------------------------ */
 typedef struct enkfmc_batch enkfmc_batch;
 
@@ -299,9 +300,11 @@ enkfmc_status enkfmc_batch_create(enkfmc_batch** b, enkfmc_handle* const* handle
  * set).  Rebinding drops the captured graph. */
 enkfmc_status enkfmc_batch_bind(enkfmc_batch* b, int32_t i, const void* Xb, void* Tvals, void* D,
                                 const void* y, const void* Rdiag, const void* Z, void* Xa);
-/* One eager cycle of every instance (set-up and numerical status before any
- * replay), then the capture of one cycle of all of them into a CUDA graph.
- * Every instance must be bound.  Turns the handles' kernel timing off. */
+/* Synchronises `cuda_stream`, runs one eager cycle of every instance (set-up
+ * and numerical status before any replay), then captures one cycle of all of
+ * them into a CUDA graph.  Every instance must be bound.  Turns the handles'
+ * kernel timing off; on return (success or not) every handle's stream is
+ * `cuda_stream` again. */
 enkfmc_status enkfmc_batch_capture(enkfmc_batch* b);
 /* One cycle of every instance: a single graph launch on the batch's stream. */
 enkfmc_status enkfmc_batch_run(enkfmc_batch* b);

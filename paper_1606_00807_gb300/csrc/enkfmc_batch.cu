@@ -23,7 +23,8 @@ struct enkfmc_batch {
   };
   std::vector<Bind> bind;
   std::vector<int> stream_of;  // side stream of each instance
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // the caller's stream: graph launches, status reads
+  cudaStream_t origin = nullptr;  // capture origin (the legacy default stream cannot be captured)
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;  // fork, then one join event per side stream
   cudaGraph_t graph = nullptr;
@@ -43,6 +44,7 @@ void free_batch(enkfmc_batch* b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+  if (b->origin) cudaStreamDestroy(b->origin);
   delete b;
 }
 
@@ -75,6 +77,10 @@ extern "C" enkfmc_status enkfmc_batch_create(enkfmc_batch** out, enkfmc_handle* 
   }
   b->bind.resize(nprob);
   const int ns = std::min(nstreams, nprob);
+  if (enkfmc_status st = cuda_status(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking))) {
+    free_batch(b);
+    return st;
+  }
   for (int k = 0; k < ns; ++k) {
     cudaStream_t s = nullptr;
     enkfmc_status st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -135,6 +141,9 @@ namespace {
 // streams are the side streams meanwhile.
 enkfmc_status capture_cycle(enkfmc_batch* b) {
   const int n = (int)b->h.size(), ns = (int)b->side.size();
+  // the side streams do not order against the caller's stream: let the
+  // caller's work on the inputs finish first
+  if (enkfmc_status st = cuda_status(cudaStreamSynchronize(b->stream))) return st;
   // one eager cycle per instance: the lazy set-up of every launch happens
   // outside the capture, and numerical failures show before any replay
   for (int i = 0; i < n; ++i) {
@@ -149,12 +158,13 @@ enkfmc_status capture_cycle(enkfmc_batch* b) {
     b->exec = nullptr;
     b->graph = nullptr;
   }
-  // capture: fork the side streams from the batch stream, run every
-  // instance on its stream, join them back
+  // capture: fork the side streams from the origin stream, run every
+  // instance on its stream, join them back.  The graph is launched on the
+  // caller's stream, which may be the legacy default stream.
   enkfmc_status st =
-      cuda_status(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+      cuda_status(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
   if (st) return st;
-  cudaError_t e = cudaEventRecord(b->ev[0], b->stream);
+  cudaError_t e = cudaEventRecord(b->ev[0], b->origin);
   for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev[0], 0);
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     st = run_instance(b, i, b->side[b->stream_of[i]]);
@@ -162,10 +172,10 @@ enkfmc_status capture_cycle(enkfmc_batch* b) {
   }
   for (int k = 0; k < ns && e == cudaSuccess; ++k) {
     e = cudaEventRecord(b->ev[k + 1], b->side[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[k + 1], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev[k + 1], 0);
   }
   cudaGraph_t g = nullptr;
-  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     (void)cudaGetLastError();
@@ -229,6 +239,7 @@ enkfmc_status enkfmc_batch_query(const enkfmc_batch* b, int32_t* nstreams, int32
 void enkfmc_batch_destroy(enkfmc_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  else cudaDeviceSynchronize();
   for (cudaStream_t s : b->side) cudaStreamSynchronize(s);
   free_batch(b);
 }
