@@ -316,10 +316,15 @@ enkfmc_status enkfmc_batch_get_status(enkfmc_batch* b, int32_t* status, int64_t*
 enkfmc_status enkfmc_batch_query(const enkfmc_batch* b, int32_t* nstreams, int32_t* stream_of);
 void enkfmc_batch_destroy(enkfmc_batch* b);
 
-/* Launch tuning of one handle (the autotuner's knobs; results do not change). */
+/* Launch tuning of one handle.  The grid cap is the autotuner's knob and
+ * changes no result; the kernel choice changes results at the rounding level. */
 enum {
-  ENKFMC_TUNE_REGRESS_CTAS_PER_SM = 0  /* CTAs per SM of the regressions' grid-stride
+  ENKFMC_TUNE_REGRESS_CTAS_PER_SM = 0, /* CTAs per SM of the regressions' grid-stride
                                           launch (0 = the default, 64)              */
+  ENKFMC_TUNE_REGRESS_TILED = 1        /* 1: every single-precision row through the
+                                          shared-memory tiled kernel; 0 (default):
+                                          stencils of 16..39 slots through the
+                                          register kernel                           */
 };
 enkfmc_status enkfmc_set_tuning(enkfmc_handle* h, int32_t knob, int32_t value);
 

@@ -932,6 +932,457 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 }
 
 // ---------------------------------------------------------------------------
+// Single-precision regressions with the Gram matrix in registers, for stencils
+// of 16 to 31 + NX predecessor slots and N <= 128 members (the rows of
+// k_regress with sel 0 or 1).  One warp per row of the item list.  The
+// augmented Gram matrix is padded to NP = 32 + NX rows: predecessors at
+// 0..p-1, identity rows from p, the row itself last (NA = NP - 1).  Lane i
+// holds row i of the leading 32 x 32 block (a[0..31], lower part); lane c
+// holds column c of the last NX rows (b[r] = A[32 + r][c]).  Right-looking
+// Cholesky over the leading columns: at step k every lane takes lane k's
+// diagonal, scales its own entry of column k and publishes it in shared
+// memory; every lane then updates its row and its column of the last rows,
+// so the whole warp works at every step.  The Schur complement
+// A22 - L21 L21^T of the last NX rows is factored in lanes 0..NX-1; the row
+// itself ends as w = L^-1 g.  Solves with L11 sweep over its columns (a
+// broadcast and one multiply-add per lane and column), from a copy of L11 in
+// shared memory; the small solves with L22 run redundantly in every lane.
+// The refinement step is that of k_regress (residual of the anomalies,
+// corrected semi-normal equations, D from the refined residual), with four
+// members per lane.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int lane_warp_bytes(int NX, int pmax) {
+  const int NP = 32 + NX, LDG = NP + 1;
+  const int ints = 2 * NP + (pmax + 3) / 4 * 4;
+  const int floats = (NP * LDG + 3) / 4 * 4 + 3 * NP + 8;
+  return ((ints + floats) * 4 + 15) / 16 * 16;
+}
+
+// Column sweep of L11^T x = rhs (lane c holds x_c; L11 row t at G + t * LDG,
+// inv = 1 / L_cc in lane c): unknowns 0..NU-1, the rest left as they are.
+template <int NU, int LDG>
+__device__ __forceinline__ float lane_backward(const float* G, float x, float inv, int lane) {
+#pragma unroll
+  for (int t = NU - 1; t >= 0; --t) {
+    const float xt = __shfl_sync(0xffffffffu, x * inv, t);
+    if (lane == t) x = xt;
+    else if (lane < t) x = fmaf(-G[t * LDG + lane], xt, x);
+  }
+  return x;
+}
+
+// Column sweep of L11 z = c (lane i holds z_i, L11 row i at G + i * LDG).
+template <int NU, int LDG>
+__device__ __forceinline__ float lane_forward(const float* G, float z, float inv, int lane) {
+#pragma unroll
+  for (int t = 0; t < NU; ++t) {
+    const float zt = __shfl_sync(0xffffffffu, z * inv, t);
+    if (lane == t) z = zt;
+    else if (lane > t) z = fmaf(-G[lane * LDG + t], zt, z);
+  }
+  return z;
+}
+
+__device__ __forceinline__ float dot4(const float4 a, const float4 b) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+template <int NX>
+__global__ void __launch_bounds__(256, 2)
+    k_regress_lane(const Geom g, const float* __restrict__ U, const float* __restrict__ C,
+                   int nH, const int32_t* __restrict__ halo, int64_t nitems,
+                   const Block* __restrict__ blocks, float* __restrict__ Tout,
+                   float* __restrict__ Dout, double ridge_c, int32_t* status, int warp_bytes,
+                   int sel, int use_ptab) {
+  constexpr int NP = 32 + NX, LDG = NP + 1, NA = NP - 1;
+  constexpr int NU = NX ? 32 : 31;  // pivots of the leading block
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  signed char* off = reinterpret_cast<signed char*>(smem);  // [3][pmax], padded to 16
+  const int pmax = g.pmax;
+  const int offbytes = (3 * pmax + 15) / 16 * 16;
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
+    int dk, dy, dx;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    off[s] = (signed char)dk;
+    off[pmax + s] = (signed char)dy;
+    off[2 * pmax + s] = (signed char)dx;
+  }
+  const int pf = pmax - (g.periodic ? g.r : 0);
+  int2* ptab = reinterpret_cast<int2*>(smem + offbytes);
+  const int ptab_bytes = use_ptab ? pair_table_bytes(pmax, g.r, g.periodic) : 0;
+  if (use_ptab) build_pair_table(g, pf, ptab);
+  const int nfull = (pmax + 1) * (pmax + 2) / 2;
+  uint16_t* tri = reinterpret_cast<uint16_t*>(smem + offbytes + ptab_bytes);
+  uint16_t* ftab = tri + nfull;
+  build_gather_tables(g, pmax, tri, ftab);
+  __syncthreads();
+  unsigned char* base = smem + offbytes + ptab_bytes + gather_table_bytes(pmax) +
+                        (size_t)warp * warp_bytes;
+  int* q = reinterpret_cast<int*>(base);   // [NP] component labels (q[NA] = j)
+  int* sl = q + NP;                         // [NP] slot of a compacted entry (-1 = j)
+  int* sidx = sl + NP;                      // [pmax] compacted index of slot s
+  float* G = reinterpret_cast<float*>(sidx + (pmax + 3) / 4 * 4);  // [NP][LDG]
+  float* col = G + (NP * LDG + 3) / 4 * 4;  // [NP] the column of a step
+  float* bv = col + NP;                     // [NP] beta
+  float* cv = bv + NP;                      // [NP] residual of the normal equations
+  float* dv = cv + NP;                      // [8] 1 / L22 diagonal
+  const int N = g.N;
+  const bool mv = 4 * lane < g.ldN;         // lane's four members m = 4 lane .. 4 lane + 3
+
+  for (int64_t item = (int64_t)blockIdx.x * wpc + warp; item < nitems;
+       item += (int64_t)gridDim.x * wpc) {
+    int v, k, y, x;
+    int64_t orow;
+    const Block* b = nullptr;
+    if (halo) {
+      const int blk = halo[2 * item], loc = halo[2 * item + 1];
+      b = blocks + blk;
+      const int plane = b->ey * b->ex;
+      k = loc / plane;
+      const int rem = loc - k * plane;
+      const int yy = rem / b->ex, xx = rem - yy * b->ex;
+      y = b->lat_lo + yy;
+      x = imod(b->lon_lo + xx, g.nlon);
+      v = b->var;
+      orow = b->row_off + loc;
+    } else {
+      label_coords(g, item, v, k, y, x);
+      orow = item;
+    }
+    // predecessor list (as k_regress)
+    int p = 0;
+    for (int s0 = 0; s0 < pmax; s0 += 32) {
+      const int s = s0 + lane;
+      bool pres = false;
+      int qq = 0;
+      if (s < pmax) {
+        int kq, yq, xq;
+        pres = slot_pred_off(g, k, y, x, off[s], off[pmax + s], off[2 * pmax + s], kq, yq, xq);
+        if (pres && b) {
+          int yy, xx;
+          pres = in_ext(*b, g.nlon, yq, xq, yy, xx);
+        }
+        if (pres) qq = (int)coords_label(g, v, kq, yq, xq);
+      }
+      const unsigned mask = __ballot_sync(FULL, pres);
+      const int idx = p + __popc(mask & ((1u << lane) - 1u));
+      if (s < pmax) sidx[s] = pres ? idx : -1;
+      if (pres) {
+        q[idx] = qq;
+        sl[idx] = s;
+      }
+      p += __popc(mask);
+    }
+    const int jlab = (int)coords_label(g, v, k, y, x);
+    if (lane == 0) {
+      q[NA] = jlab;
+      sl[NA] = -1;
+    }
+    __syncwarp();
+    if (sel && ((2 * p > N) != (sel == 2))) continue;  // the other launch's row
+
+    // augmented Gram matrix, lower triangle: identity rows p..NA-1, the row
+    // itself at NA (compact index p), gathered from the covariance table
+    for (int i = p; i < NA; ++i)
+      for (int l = lane; l <= i; l += 32) G[i * LDG + l] = (l == i) ? 1.f : 0.f;
+    for (int l = p + lane; l < NA; l += 32) G[NA * LDG + l] = 0.f;
+    const int p1 = p + 1, npair = p1 * (p1 + 1) / 2;
+    const bool typical = use_ptab && p == pf && (p == 0 || sl[p - 1] == pf - 1);
+    if (typical) {
+#pragma unroll 4
+      for (int pi = lane; pi < npair; pi += 32) {
+        const int2 e = ptab[pi];
+        const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
+        const int ii = i == p ? NA : i, ll = l == p ? NA : l;
+        G[ii * LDG + ll] = C[(int64_t)((e.x >> 16) ? q[ll] : q[ii]) * nH + e.y];
+      }
+    } else {
+#pragma unroll 4
+      for (int pi = lane; pi < npair; pi += 32) {
+        const uint32_t il = tri[pi];
+        const int i = il & 0xff, l = il >> 8;
+        const int ii = i == p ? NA : i, ll = l == p ? NA : l;
+        // slots rise with the compact index and the row itself (pmax) is last,
+        // so sm <= si: the entry of the lower-triangle table exists
+        int si = sl[ii], sm = sl[ll];
+        si = si < 0 ? pmax : si;
+        sm = sm < 0 ? pmax : sm;
+        const uint32_t e = ftab[si * (si + 1) / 2 + sm];
+        G[ii * LDG + ll] = C[(int64_t)((e & 0x8000u) ? q[ll] : q[ii]) * nH + (e & 0x7fffu)];
+      }
+    }
+    __syncwarp();
+    float lam = 0.f;
+    if (p > 0 && ridge_c > 0.0 && p >= N - 1) {
+      float tr = 0.f;
+      for (int i = lane; i < p; i += 32) tr += G[i * LDG + i];
+      tr = warp_sum(tr);
+      lam = (float)ridge_c * tr / (float)p;
+      for (int i = lane; i < p; i += 32) G[i * LDG + i] += lam;
+      __syncwarp();
+    }
+
+    // rows into registers
+    float a[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? G[lane * LDG + j] : 0.f;
+    float bx[NX > 0 ? NX : 1];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) bx[r] = G[(32 + r) * LDG + lane];
+
+    // right-looking Cholesky of the leading columns
+    int err = 0;
+    float myinv = 1.f;
+#pragma unroll
+    for (int kk = 0; kk < NU; ++kk) {
+      const float d = __shfl_sync(FULL, a[kk], kk);
+      const bool ok = finite_val(d) && d > 0.f;
+      if (!ok && !err) err = finite_val(d) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+      float sd, inv;
+      sqrt_and_inv(ok ? d : 1.f, sd, inv);
+      const float lk = a[kk] * inv;  // lane kk: sqrt(d); lanes below: L[i][kk]
+      a[kk] = lk;
+      if (lane == kk) {
+        myinv = inv;
+#pragma unroll
+        for (int r = 0; r < NX; ++r) bx[r] *= inv;
+      }
+      col[lane] = lk;
+      if (NX > 0 && lane == kk) {
+#pragma unroll
+        for (int r = 0; r < NX; r += 4) {
+          const float t4[4] = {bx[r], bx[r + 1], bx[r + 2], bx[r + 3]};
+          sts4v(col + 32 + r, t4);
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j4 = (kk + 1) / 4 * 4; j4 < 32; j4 += 4) {
+        float c4[4];
+        lds4v(col + j4, c4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j4 + u > kk) a[j4 + u] = fmaf(-lk, c4[u], a[j4 + u]);
+      }
+      if (NX > 0 && lane > kk) {
+#pragma unroll
+        for (int r = 0; r < NX; r += 4) {
+          float c4[4];
+          lds4v(col + 32 + r, c4);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) bx[r + u] = fmaf(-c4[u], lk, bx[r + u]);
+        }
+      }
+      __syncwarp();
+    }
+
+    float d2[NX > 1 ? NX - 1 : 1];  // small-block unknowns (every lane)
+    if constexpr (NX > 0) {
+      // L21^T beside L11 (rows 0..31, columns 32..), then the Schur complement
+      // of the last rows, lower part, one entry per lane
+#pragma unroll
+      for (int r = 0; r < NX; ++r) G[lane * LDG + 32 + r] = bx[r];
+      __syncwarp();
+      constexpr int NS = NX * (NX + 1) / 2;
+      for (int e = lane; e < NS; e += 32) {
+        int r = 0;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        const int s = e - r * (r + 1) / 2;
+        float acc = G[(32 + r) * LDG + 32 + s];
+#pragma unroll 8
+        for (int c = 0; c < 32; ++c) acc = fmaf(-G[c * LDG + 32 + r], G[c * LDG + 32 + s], acc);
+        G[(32 + r) * LDG + 32 + s] = acc;
+      }
+      __syncwarp();
+      // Cholesky of the Schur complement: lane r holds its row r < NX; the
+      // last row (the row itself) takes no pivot
+      float sr[NX];
+#pragma unroll
+      for (int t = 0; t < NX; ++t)
+        sr[t] = (lane < NX && t <= lane) ? G[(32 + lane) * LDG + 32 + t] : 0.f;
+      float sinv = 1.f;
+#pragma unroll
+      for (int kk = 0; kk < NX - 1; ++kk) {
+        const float d = __shfl_sync(FULL, sr[kk], kk);
+        const bool ok = finite_val(d) && d > 0.f;
+        if (!ok && !err) err = finite_val(d) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+        float sd, inv;
+        sqrt_and_inv(ok ? d : 1.f, sd, inv);
+        const float lk = sr[kk] * inv;
+        sr[kk] = lk;
+        if (lane == kk) sinv = inv;
+#pragma unroll
+        for (int j = kk + 1; j < NX; ++j) sr[j] = fmaf(-lk, __shfl_sync(FULL, lk, j), sr[j]);
+      }
+      if (lane < NX) {
+#pragma unroll
+        for (int t = 0; t < NX; ++t)
+          if (t <= lane) G[(32 + lane) * LDG + 32 + t] = sr[t];
+        dv[lane] = sinv;
+      }
+    }
+    // L11 (lower part of the registers) to shared memory for the sweeps
+#pragma unroll
+    for (int j = 0; j < 32; ++j) G[lane * LDG + j] = a[j];
+    __syncwarp();
+
+    // beta = L^-T w
+    float xb;
+    if constexpr (NX > 0) {
+      // last unknowns: L22^T beta2 = w2 (w2 = row NA of the Schur factor)
+#pragma unroll
+      for (int t = NX - 2; t >= 0; --t) {
+        float acc = G[NA * LDG + 32 + t];
+#pragma unroll
+        for (int j = t + 1; j < NX - 1; ++j) acc = fmaf(-G[(32 + j) * LDG + 32 + t], d2[j], acc);
+        d2[t] = acc * dv[t];
+      }
+      // leading unknowns: L11^T beta1 = w1 - L21^T beta2 (w1 in L21^T's last column)
+      xb = G[lane * LDG + 32 + NX - 1];
+#pragma unroll
+      for (int r = 0; r < NX - 1; ++r) xb = fmaf(-G[lane * LDG + 32 + r], d2[r], xb);
+    } else {
+      xb = lane < NU ? G[NA * LDG + lane] : 0.f;  // w = row NA of L11
+    }
+    xb = lane_backward<NU, LDG>(G, xb, myinv, lane);
+    if (lane < NU) bv[lane] = xb;
+    if constexpr (NX > 0) {
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NX - 1; ++r) bv[32 + r] = d2[r];
+      }
+    }
+    __syncwarp();
+
+    // refinement: residual e = u - U_P^T beta of the anomalies
+    float4 e4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mv) e4 = *reinterpret_cast<const float4*>(U + (int64_t)jlab * g.ldN + 4 * lane);
+#pragma unroll 4
+    for (int i = 0; i < p; ++i) {
+      const float bi = bv[i];
+      if (mv) {
+        const float4 u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + 4 * lane);
+        e4.x = fmaf(-u4.x, bi, e4.x);
+        e4.y = fmaf(-u4.y, bi, e4.y);
+        e4.z = fmaf(-u4.z, bi, e4.z);
+        e4.w = fmaf(-u4.w, bi, e4.w);
+      }
+    }
+    // c = U_P e - lambda beta: 32 predecessors at a time by a reduce-scatter
+    // (31 shuffles leave predecessor i0 + lane's sum in lane lane), the rest
+    // one warp sum each
+    const int pfull32 = p & ~31;
+    for (int i0 = 0; i0 < pfull32; i0 += 32) {
+      float part[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mv) u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i0 + j] * g.ldN + 4 * lane);
+        part[j] = dot4(u4, e4);
+      }
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+          const float send = hi ? part[j] : part[j + o];
+          const float keep = hi ? part[j + o] : part[j];
+          part[j] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+      }
+      cv[i0 + lane] = part[0] - lam * bv[i0 + lane];
+    }
+    for (int i = pfull32; i < p; ++i) {
+      float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mv) u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + 4 * lane);
+      const float part = warp_sum(dot4(u4, e4));
+      if (lane == (i & 31)) cv[i] = part - lam * bv[i];
+    }
+    for (int i = p + lane; i < NA; i += 32) cv[i] = 0.f;
+    __syncwarp();
+
+    // delta = (L L^T)^-1 c: forward, then backward
+    float z = lane < NU ? cv[lane] : 0.f;
+    z = lane_forward<NU, LDG>(G, z, myinv, lane);
+    float zz = lane < NU ? z * z : 0.f;
+    if constexpr (NX > 0) {
+      // z2 = L22^-1 (c2 - L21 z1), every lane
+      float z2[NX - 1];
+#pragma unroll
+      for (int r = 0; r < NX - 1; ++r) z2[r] = warp_sum(G[lane * LDG + 32 + r] * z);
+#pragma unroll
+      for (int r = 0; r < NX - 1; ++r) {
+        float acc = cv[32 + r] - z2[r];
+#pragma unroll
+        for (int j = 0; j < r; ++j) acc = fmaf(-G[(32 + r) * LDG + 32 + j], z2[j], acc);
+        z2[r] = acc * dv[r];
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NX - 1; ++r) zz = fmaf(z2[r], z2[r], zz);
+      }
+      // delta2 = L22^-T z2, then z1 - L21^T delta2 for the leading sweep
+#pragma unroll
+      for (int t = NX - 2; t >= 0; --t) {
+        float acc = z2[t];
+#pragma unroll
+        for (int j = t + 1; j < NX - 1; ++j) acc = fmaf(-G[(32 + j) * LDG + 32 + t], d2[j], acc);
+        d2[t] = acc * dv[t];
+      }
+#pragma unroll
+      for (int r = 0; r < NX - 1; ++r) z = fmaf(-G[lane * LDG + 32 + r], d2[r], z);
+    }
+    zz = warp_sum(zz);
+    z = lane_backward<NU, LDG>(G, z, myinv, lane);
+    // D from the refined residual e' = e - U_P^T delta without reading U:
+    //   |e'|^2 = |e|^2 - 2 delta.(U_P e) + delta^T G delta,
+    //   U_P e = c + lambda beta,  delta^T G delta = |z|^2 - lambda |delta|^2
+    float dc = 0.f, dd = 0.f;
+    if (lane < NU) {
+      dc = z * (cv[lane] + lam * bv[lane]);
+      dd = z * z;
+    }
+    if constexpr (NX > 0) {
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NX - 1; ++r) {
+          dc = fmaf(d2[r], cv[32 + r] + lam * bv[32 + r], dc);
+          dd = fmaf(d2[r], d2[r], dd);
+        }
+      }
+    }
+    const float ee = warp_sum(dot4(e4, e4));
+    dc = warp_sum(dc);
+    dd = warp_sum(dd);
+    __syncwarp();
+    if (lane < NU) bv[lane] += z;
+    if constexpr (NX > 0) {
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NX - 1; ++r) bv[32 + r] += d2[r];
+      }
+    }
+    const float ssq = ee - 2.f * dc + (zz - lam * dd);
+    const float Dj = ssq / (float)(N - 1);
+    if (!err) {
+      if (!finite_val(Dj)) err = ENKFMC_ENONFINITE;
+      else if (!(Dj > 0.f)) err = ENKFMC_EDNONPOS;
+    }
+    __syncwarp();
+    if (err && lane == 0 && status) record_error(status, err, orow);
+    float* trow = Tout + orow * pmax;
+    for (int s = lane; s < pmax; s += 32) {
+      const int i = sidx[s];
+      trow[s] = (i >= 0 && !err) ? -bv[i] : 0.f;
+    }
+    if (lane == 0) Dout[orow] = err ? NAN : Dj;
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint of the regressions of one (sub-domain, variable) block.  One warp
 // per extended row j (a regression instance of Algorithm 3): with
 // a_j = (T Lambda)_j, b_j = (T dX)_j (row-major, N samples),
@@ -1351,12 +1802,57 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
   return cudaGetLastError();
 }
 
+// The register kernel (k_regress_lane) serves single-precision rows of
+// stencils with 16 to 39 predecessor slots; NX = 8 when the padded Gram
+// matrix needs rows past the 32 lanes.
+bool regress_lane_applies(const Geom& g, int sel) {
+  return !g.regress_tiled && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 &&
+         g.pmax + 1 <= 40;
+}
+
+template <int NX>
+cudaError_t launch_regress_lane(const Geom& g, const float* U, const float* C,
+                                const int32_t* halo, int64_t nitems, const Block* blocks,
+                                float* Tout, float* Dout, double ridge_c, int32_t* status,
+                                int sel, cudaStream_t s) {
+  const int nH = cov_offset_count(g.r, g.vr);
+  const int wpc = 8;
+  const int wb = lane_warp_bytes(NX, g.pmax);
+  const size_t tables = (3 * (size_t)g.pmax + 15) / 16 * 16 + gather_table_bytes(g.pmax);
+  const size_t ptab = pair_table_bytes(g.pmax, g.r, g.periodic);
+  int use_ptab = 1;
+  size_t smem = tables + ptab + (size_t)wpc * wb;
+  if (smem > 110 * 1024) {  // two CTAs per SM before the typical row's pair table
+    use_ptab = 0;
+    smem -= ptab;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_regress_lane<NX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (nitems + wpc - 1) / wpc;
+  const int64_t cap = (int64_t)(g.sm_count > 0 ? g.sm_count : 152) *
+                      (g.regress_cap > 0 ? g.regress_cap : 64);
+  if (grid > cap) grid = cap;
+  k_regress_lane<NX><<<(unsigned)grid, 32 * wpc, smem, s>>>(
+      g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, wb, sel, use_ptab);
+  return cudaGetLastError();
+}
+
 template <typename T, typename TO>
 cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
                            int64_t nitems, const Block* blocks, TO* Tout, TO* Dout, double ridge_c,
                            int32_t* status, int sel, cudaStream_t s) {
   if (nitems <= 0) return cudaSuccess;
   if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds) return cudaErrorInvalidConfiguration;
+  if constexpr (std::is_same<T, float>::value && std::is_same<TO, float>::value) {
+    if (regress_lane_applies(g, sel)) {
+      if (g.pmax + 1 > 32)
+        return launch_regress_lane<8>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
+                                      sel, s);
+      return launch_regress_lane<0>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
+                                    sel, s);
+    }
+  }
   const int mr = (g.N + 31) / 32;
   if (mr <= 2)
     return launch_regress_rm<T, TO, 2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,

@@ -108,9 +108,19 @@ SMALL_T63 = Workload(
     r=2, N=80, sub_lon=12, sub_lat=12, sigma2=(25.0, 1e4), corr_len=4.0, rho_vert=0.5,
     obs="random", obs_frac=0.5, r_frac=0.01, seed=7300)
 
+# Same statistics with N = 120: four members per lane on 30 lanes in the
+# register regressions.
+SMALL_T63_N120 = SMALL_T63.with_(name="small_48x26x3x1+1_n120_r2", N=120, seed=7310)
+
+# Two 2-D fields, r = 3: 27 predecessor slots (one level, ring longitude).
+SMALL_2D_R3 = Workload(
+    name="small_40x30x0+2_n64_r3", nlon=40, nlat=30, nlev=1, nvar_3d=0, nvar_2d=2,
+    r=3, N=64, sub_lon=12, sub_lat=12, sigma2=(1.0, 1e2), corr_len=3.0,
+    obs="random", obs_frac=0.5, r_frac=0.01, seed=7400)
+
 WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96,
                                  SMALL_3D, SMALL_ILL, SMALL_R1, SMALL_R1_N16, SMALL_RIDGE,
-                                 SMALL_T63)}
+                                 SMALL_T63, SMALL_T63_N120, SMALL_2D_R3)}
 
 
 def batch_instances(count: int = 256, base_seed: int = 3000):

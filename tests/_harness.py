@@ -23,13 +23,16 @@ def np_dtype(precision):
     return np.float64 if precision == 0 else np.float32
 
 
-def gpu_pipeline(w: Workload, inp: Inputs, precision: int, handle=None, flags=0):
-    """estimate -> assemble -> analyze on cuda:0 through the C ABI; returns numpy outputs."""
+def gpu_pipeline(w: Workload, inp: Inputs, precision: int, handle=None, flags=0, tuning=None):
+    """estimate -> assemble -> analyze on cuda:0 through the C ABI; returns numpy
+    outputs.  tuning: {knob: value} for enkfmc_set_tuning."""
     import torch
     from paper_1606_00807_gb300 import binding as B
     dt = torch_dtype(precision)
     stream = torch.cuda.current_stream().cuda_stream
     h = handle or B.Handle.from_workload(w, precision=precision, stream=stream, flags=flags)
+    for knob, value in (tuning or {}).items():
+        h.set_tuning(knob, value)
     h.set_observations(inp.obs_idx)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
     Xb, y, R, Z = dev(inp.Xb), dev(inp.y), dev(inp.R), dev(inp.Z)

@@ -47,10 +47,10 @@ def test_T_pattern_bit_exact(name):
     h.close()
 
 
-def _parity(name, precision, tol_x=None, flags=0):
+def _parity(name, precision, tol_x=None, flags=0, tuning=None):
     w = WORKLOADS[name]
     inp = make_inputs(w, np_dtype(precision))
-    out = gpu_pipeline(w, inp, precision, flags=flags)
+    out = gpu_pipeline(w, inp, precision, flags=flags, tuning=tuning)
     tol = TOL[precision]
     tol_x = tol if tol_x is None else tol_x
     # step (a): every row of T and D against the oracle
@@ -82,6 +82,18 @@ def _parity(name, precision, tol_x=None, flags=0):
 @pytest.mark.parametrize("name", SMALL)
 def test_estimate_and_analysis_parity(name, precision):
     _parity(name, precision)
+
+
+@pytest.mark.parametrize("tiled", [0, 1])
+@pytest.mark.parametrize("name", ["small_48x26x3x1+1_n80_r2", "small_48x26x3x1+1_n120_r2",
+                                  "small_40x30x0+2_n64_r3"])
+def test_register_and_tiled_regressions_parity(name, tiled):
+    """Single-precision regressions through the register kernel (default: 37-39
+    slots with the seam at N = 80 and N = 120, 27 slots for r = 3 on one level)
+    and through the shared-memory tiled kernel (ENKFMC_TUNE_REGRESS_TILED), each
+    element by element against the oracle at the FP32 tolerance."""
+    from paper_1606_00807_gb300 import binding as B
+    _parity(name, 1, tuning={B.TUNE_REGRESS_TILED: tiled})
 
 
 def test_plain_fp32_solve_without_refinement():
