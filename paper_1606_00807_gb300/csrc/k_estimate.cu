@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 // ---------------------------------------------------------------------------
 // Single-precision regressions with the Gram matrix in registers, for stencils
 // of 16 to 31 + NX predecessor slots and N <= 128 members (the rows of
-// k_regress with sel 0 or 1).  One warp per row of the item list.  The
+// k_regress and k_adj_regress with sel 0 or 1).  One warp per row.  The
 // augmented Gram matrix is padded to NP = 32 + NX rows: predecessors at
 // 0..p-1, identity rows from p, the row itself last (NA = NP - 1).  Lane i
 // holds row i of the leading 32 x 32 block (a[0..31], lower part); lane c
@@ -950,12 +950,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 // The refinement step is that of k_regress (residual of the anomalies,
 // corrected semi-normal equations, D from the refined residual), with four
 // members per lane.
+//
+// Per-warp shared memory: G [NP][NP + 1] (the Gram matrix; after the
+// factorisation L11 in its leading 32 x 32 block, L21^T in rows 0..31 from
+// column 32, L22 in rows 32.. from column 32), and vectors col, bv, cv [NP],
+// dv [8] (1 / L22 diagonal).
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int lane_warp_bytes(int NX, int pmax) {
+template <int NX>
+struct Lane {
+  static constexpr int NP = 32 + NX, LDG = NP + 1, NA = NP - 1;
+  static constexpr int NU = NX ? 32 : 31;  // pivots of the leading block
+  static constexpr int ND = NX > 1 ? NX - 1 : 1;
+};
+
+__host__ __device__ inline int lane_warp_bytes(int NX, int ints) {
   const int NP = 32 + NX, LDG = NP + 1;
-  const int ints = 2 * NP + (pmax + 3) / 4 * 4;
   const int floats = (NP * LDG + 3) / 4 * 4 + 3 * NP + 8;
-  return ((ints + floats) * 4 + 15) / 16 * 16;
+  return (((ints + 3) / 4 * 4 + floats) * 4 + 15) / 16 * 16;
 }
 
 // Column sweep of L11^T x = rhs (lane c holds x_c; L11 row t at G + t * LDG,
@@ -987,6 +998,259 @@ __device__ __forceinline__ float dot4(const float4 a, const float4 b) {
   return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
 }
 
+// Members 4 m0 .. 4 m0 + 3 of a row (stride ldN, zero past N; m0 < ldN).
+__device__ __forceinline__ float4 ld_members(const float* row, int m0, int N) {
+  float4 u = *reinterpret_cast<const float4*>(row + m0);
+  if (m0 + 4 > N) {
+    if (m0 + 1 >= N) u.y = 0.f;
+    if (m0 + 2 >= N) u.z = 0.f;
+    if (m0 + 3 >= N) u.w = 0.f;
+    if (m0 >= N) u.x = 0.f;
+  }
+  return u;
+}
+
+// The augmented Gram matrix of a row, lower triangle: identity rows p..NA-1,
+// the row itself at NA (compact index p), gathered from the covariance table
+// through the typical row's pair table or the slot-pair tables (tri, ftab).
+template <int NX>
+__device__ __forceinline__ void lane_gather(float* G, const int* q, const int* sl, int p,
+                                            int pmax, bool typical, const int2* ptab,
+                                            const uint16_t* tri, const uint16_t* ftab,
+                                            const float* __restrict__ C, int nH, int lane) {
+  constexpr int LDG = Lane<NX>::LDG, NA = Lane<NX>::NA;
+  for (int i = p; i < NA; ++i)
+    for (int l = lane; l <= i; l += 32) G[i * LDG + l] = (l == i) ? 1.f : 0.f;
+  for (int l = p + lane; l < NA; l += 32) G[NA * LDG + l] = 0.f;
+  const int p1 = p + 1, npair = p1 * (p1 + 1) / 2;
+  if (typical) {
+#pragma unroll 4
+    for (int pi = lane; pi < npair; pi += 32) {
+      const int2 e = ptab[pi];
+      const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
+      const int ii = i == p ? NA : i, ll = l == p ? NA : l;
+      G[ii * LDG + ll] = C[(int64_t)((e.x >> 16) ? q[ll] : q[ii]) * nH + e.y];
+    }
+  } else {
+#pragma unroll 4
+    for (int pi = lane; pi < npair; pi += 32) {
+      const uint32_t il = tri[pi];
+      const int i = il & 0xff, l = il >> 8;
+      const int ii = i == p ? NA : i, ll = l == p ? NA : l;
+      // slots rise with the compact index and the row itself (pmax) is last,
+      // so sm <= si: the entry of the lower-triangle table exists
+      int si = sl[ii], sm = sl[ll];
+      si = si < 0 ? pmax : si;
+      sm = sm < 0 ? pmax : sm;
+      const uint32_t e = ftab[si * (si + 1) / 2 + sm];
+      G[ii * LDG + ll] = C[(int64_t)((e & 0x8000u) ? q[ll] : q[ii]) * nH + (e & 0x7fffu)];
+    }
+  }
+  __syncwarp();
+}
+
+// lambda = c tr(G) / p added to the predecessors' diagonal where p >= N - 1.
+template <int NX>
+__device__ __forceinline__ float lane_ridge(float* G, int p, int N, double ridge_c, int lane) {
+  constexpr int LDG = Lane<NX>::LDG;
+  float lam = 0.f;
+  if (p > 0 && ridge_c > 0.0 && p >= N - 1) {
+    float tr = 0.f;
+    for (int i = lane; i < p; i += 32) tr += G[i * LDG + i];
+    tr = warp_sum(tr);
+    lam = (float)ridge_c * tr / (float)p;
+    for (int i = lane; i < p; i += 32) G[i * LDG + i] += lam;
+    __syncwarp();
+  }
+  return lam;
+}
+
+// Cholesky of G (pivots for rows 0..NA-1), leaving the factor in G as
+// described above; myinv = 1 / L_ll in lane l < NU, dv[r] = 1 / L22_rr.
+// Returns 0 or ENKFMC_EDNONPOS / ENKFMC_ENONFINITE (same in every lane).
+template <int NX>
+__device__ __forceinline__ int lane_factor(float* G, float* col, float* dv, float& myinv,
+                                           int lane) {
+  constexpr int LDG = Lane<NX>::LDG, NU = Lane<NX>::NU;
+  constexpr unsigned FULL = 0xffffffffu;
+  float a[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? G[lane * LDG + j] : 0.f;
+  float bx[NX > 0 ? NX : 1];
+#pragma unroll
+  for (int r = 0; r < NX; ++r) bx[r] = G[(32 + r) * LDG + lane];
+
+  int err = 0;
+  myinv = 1.f;
+#pragma unroll
+  for (int kk = 0; kk < NU; ++kk) {
+    const float d = __shfl_sync(FULL, a[kk], kk);
+    const bool ok = finite_val(d) && d > 0.f;
+    if (!ok && !err) err = finite_val(d) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+    float sd, inv;
+    sqrt_and_inv(ok ? d : 1.f, sd, inv);
+    const float lk = a[kk] * inv;  // lane kk: sqrt(d); lanes below: L[i][kk]
+    a[kk] = lk;
+    if (lane == kk) {
+      myinv = inv;
+#pragma unroll
+      for (int r = 0; r < NX; ++r) bx[r] *= inv;
+    }
+    col[lane] = lk;
+    if (NX > 0 && lane == kk) {
+#pragma unroll
+      for (int r = 0; r < NX; r += 4) {
+        const float t4[4] = {bx[r], bx[r + 1], bx[r + 2], bx[r + 3]};
+        sts4v(col + 32 + r, t4);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j4 = (kk + 1) / 4 * 4; j4 < 32; j4 += 4) {
+      float c4[4];
+      lds4v(col + j4, c4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j4 + u > kk) a[j4 + u] = fmaf(-lk, c4[u], a[j4 + u]);
+    }
+    if (NX > 0 && lane > kk) {
+#pragma unroll
+      for (int r = 0; r < NX; r += 4) {
+        float c4[4];
+        lds4v(col + 32 + r, c4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) bx[r + u] = fmaf(-c4[u], lk, bx[r + u]);
+      }
+    }
+    __syncwarp();
+  }
+
+  if constexpr (NX > 0) {
+    // L21^T beside L11 (rows 0..31, columns 32..), then the Schur complement
+    // of the last rows, lower part, one entry per lane
+#pragma unroll
+    for (int r = 0; r < NX; ++r) G[lane * LDG + 32 + r] = bx[r];
+    __syncwarp();
+    constexpr int NS = NX * (NX + 1) / 2;
+    for (int e = lane; e < NS; e += 32) {
+      int r = 0;
+      while ((r + 1) * (r + 2) / 2 <= e) ++r;
+      const int s = e - r * (r + 1) / 2;
+      float acc = G[(32 + r) * LDG + 32 + s];
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) acc = fmaf(-G[c * LDG + 32 + r], G[c * LDG + 32 + s], acc);
+      G[(32 + r) * LDG + 32 + s] = acc;
+    }
+    __syncwarp();
+    // Cholesky of the Schur complement: lane r holds its row r < NX; the
+    // last row (the row itself) takes no pivot
+    float sr[NX];
+#pragma unroll
+    for (int t = 0; t < NX; ++t)
+      sr[t] = (lane < NX && t <= lane) ? G[(32 + lane) * LDG + 32 + t] : 0.f;
+    float sinv = 1.f;
+#pragma unroll
+    for (int kk = 0; kk < NX - 1; ++kk) {
+      const float d = __shfl_sync(FULL, sr[kk], kk);
+      const bool ok = finite_val(d) && d > 0.f;
+      if (!ok && !err) err = finite_val(d) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
+      float sd, inv;
+      sqrt_and_inv(ok ? d : 1.f, sd, inv);
+      const float lk = sr[kk] * inv;
+      sr[kk] = lk;
+      if (lane == kk) sinv = inv;
+#pragma unroll
+      for (int j = kk + 1; j < NX; ++j) sr[j] = fmaf(-lk, __shfl_sync(FULL, lk, j), sr[j]);
+    }
+    if (lane < NX) {
+#pragma unroll
+      for (int t = 0; t < NX; ++t)
+        if (t <= lane) G[(32 + lane) * LDG + 32 + t] = sr[t];
+      dv[lane] = sinv;
+    }
+  }
+  // L11 (lower part of the registers) to shared memory for the sweeps
+#pragma unroll
+  for (int j = 0; j < 32; ++j) G[lane * LDG + j] = a[j];
+  __syncwarp();
+  return err;
+}
+
+// x = (L L^T)^-1 c for the predecessor unknowns (c in cv, zero at padded
+// positions): x_l in lane l < NU, the last unknowns in d2 (every lane);
+// zz = |L^-1 c|^2.
+template <int NX>
+__device__ __forceinline__ float lane_solve(const float* G, const float* cv, const float* dv,
+                                            float myinv, int lane,
+                                            float (&d2)[Lane<NX>::ND], float& zz) {
+  constexpr int LDG = Lane<NX>::LDG, NU = Lane<NX>::NU;
+  float z = lane < NU ? cv[lane] : 0.f;
+  z = lane_forward<NU, LDG>(G, z, myinv, lane);
+  zz = lane < NU ? z * z : 0.f;
+  if constexpr (NX > 0) {
+    // z2 = L22^-1 (c2 - L21 z1), every lane
+    float z2[NX - 1];
+#pragma unroll
+    for (int r = 0; r < NX - 1; ++r) z2[r] = warp_sum(G[lane * LDG + 32 + r] * z);
+#pragma unroll
+    for (int r = 0; r < NX - 1; ++r) {
+      float acc = cv[32 + r] - z2[r];
+#pragma unroll
+      for (int j = 0; j < r; ++j) acc = fmaf(-G[(32 + r) * LDG + 32 + j], z2[j], acc);
+      z2[r] = acc * dv[r];
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < NX - 1; ++r) zz = fmaf(z2[r], z2[r], zz);
+    }
+    // x2 = L22^-T z2, then z1 - L21^T x2 for the leading sweep
+#pragma unroll
+    for (int t = NX - 2; t >= 0; --t) {
+      float acc = z2[t];
+#pragma unroll
+      for (int j = t + 1; j < NX - 1; ++j) acc = fmaf(-G[(32 + j) * LDG + 32 + t], d2[j], acc);
+      d2[t] = acc * dv[t];
+    }
+#pragma unroll
+    for (int r = 0; r < NX - 1; ++r) z = fmaf(-G[lane * LDG + 32 + r], d2[r], z);
+  }
+  zz = warp_sum(zz);
+  return lane_backward<NU, LDG>(G, z, myinv, lane);
+}
+
+// c_i = <U_qi, e> * s - t * w_i for the p predecessors (c into cv, zero at the
+// padded positions up to NA): 32 predecessors at a time by a reduce-scatter
+// (31 shuffles leave predecessor i0 + lane's sum in lane lane), the rest one
+// warp sum each.  dot(i) gives the lane's partial product of predecessor i.
+template <int NX, typename Dot>
+__device__ __forceinline__ void lane_reduce_to(float* cv, int p, const float* w, float s, float t,
+                                               int lane, Dot dot) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int pfull32 = p & ~31;
+  for (int i0 = 0; i0 < pfull32; i0 += 32) {
+    float part[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) part[j] = dot(i0 + j);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const bool hi = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < o; ++j) {
+        const float send = hi ? part[j] : part[j + o];
+        const float keep = hi ? part[j + o] : part[j];
+        part[j] = keep + __shfl_xor_sync(FULL, send, o);
+      }
+    }
+    cv[i0 + lane] = part[0] * s - t * w[i0 + lane];
+  }
+  for (int i = pfull32; i < p; ++i) {
+    const float part = warp_sum(dot(i));
+    if (lane == (i & 31)) cv[i] = part * s - t * w[i];
+  }
+  for (int i = p + lane; i < Lane<NX>::NA; i += 32) cv[i] = 0.f;
+  __syncwarp();
+}
+
 template <int NX>
 __global__ void __launch_bounds__(256, 2)
     k_regress_lane(const Geom g, const float* __restrict__ U, const float* __restrict__ C,
@@ -994,8 +1258,8 @@ __global__ void __launch_bounds__(256, 2)
                    const Block* __restrict__ blocks, float* __restrict__ Tout,
                    float* __restrict__ Dout, double ridge_c, int32_t* status, int warp_bytes,
                    int sel, int use_ptab) {
-  constexpr int NP = 32 + NX, LDG = NP + 1, NA = NP - 1;
-  constexpr int NU = NX ? 32 : 31;  // pivots of the leading block
+  using S = Lane<NX>;
+  constexpr int NP = S::NP, LDG = S::LDG, NA = S::NA, NU = S::NU;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
@@ -1029,7 +1293,8 @@ __global__ void __launch_bounds__(256, 2)
   float* cv = bv + NP;                      // [NP] residual of the normal equations
   float* dv = cv + NP;                      // [8] 1 / L22 diagonal
   const int N = g.N;
-  const bool mv = 4 * lane < g.ldN;         // lane's four members m = 4 lane .. 4 lane + 3
+  const int m0 = 4 * lane;                  // lane's members m0 .. m0 + 3
+  const bool mv = m0 < g.ldN;
 
   for (int64_t item = (int64_t)blockIdx.x * wpc + warp; item < nitems;
        item += (int64_t)gridDim.x * wpc) {
@@ -1083,152 +1348,14 @@ __global__ void __launch_bounds__(256, 2)
     __syncwarp();
     if (sel && ((2 * p > N) != (sel == 2))) continue;  // the other launch's row
 
-    // augmented Gram matrix, lower triangle: identity rows p..NA-1, the row
-    // itself at NA (compact index p), gathered from the covariance table
-    for (int i = p; i < NA; ++i)
-      for (int l = lane; l <= i; l += 32) G[i * LDG + l] = (l == i) ? 1.f : 0.f;
-    for (int l = p + lane; l < NA; l += 32) G[NA * LDG + l] = 0.f;
-    const int p1 = p + 1, npair = p1 * (p1 + 1) / 2;
     const bool typical = use_ptab && p == pf && (p == 0 || sl[p - 1] == pf - 1);
-    if (typical) {
-#pragma unroll 4
-      for (int pi = lane; pi < npair; pi += 32) {
-        const int2 e = ptab[pi];
-        const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
-        const int ii = i == p ? NA : i, ll = l == p ? NA : l;
-        G[ii * LDG + ll] = C[(int64_t)((e.x >> 16) ? q[ll] : q[ii]) * nH + e.y];
-      }
-    } else {
-#pragma unroll 4
-      for (int pi = lane; pi < npair; pi += 32) {
-        const uint32_t il = tri[pi];
-        const int i = il & 0xff, l = il >> 8;
-        const int ii = i == p ? NA : i, ll = l == p ? NA : l;
-        // slots rise with the compact index and the row itself (pmax) is last,
-        // so sm <= si: the entry of the lower-triangle table exists
-        int si = sl[ii], sm = sl[ll];
-        si = si < 0 ? pmax : si;
-        sm = sm < 0 ? pmax : sm;
-        const uint32_t e = ftab[si * (si + 1) / 2 + sm];
-        G[ii * LDG + ll] = C[(int64_t)((e & 0x8000u) ? q[ll] : q[ii]) * nH + (e & 0x7fffu)];
-      }
-    }
-    __syncwarp();
-    float lam = 0.f;
-    if (p > 0 && ridge_c > 0.0 && p >= N - 1) {
-      float tr = 0.f;
-      for (int i = lane; i < p; i += 32) tr += G[i * LDG + i];
-      tr = warp_sum(tr);
-      lam = (float)ridge_c * tr / (float)p;
-      for (int i = lane; i < p; i += 32) G[i * LDG + i] += lam;
-      __syncwarp();
-    }
-
-    // rows into registers
-    float a[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) a[j] = (j <= lane) ? G[lane * LDG + j] : 0.f;
-    float bx[NX > 0 ? NX : 1];
-#pragma unroll
-    for (int r = 0; r < NX; ++r) bx[r] = G[(32 + r) * LDG + lane];
-
-    // right-looking Cholesky of the leading columns
-    int err = 0;
-    float myinv = 1.f;
-#pragma unroll
-    for (int kk = 0; kk < NU; ++kk) {
-      const float d = __shfl_sync(FULL, a[kk], kk);
-      const bool ok = finite_val(d) && d > 0.f;
-      if (!ok && !err) err = finite_val(d) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
-      float sd, inv;
-      sqrt_and_inv(ok ? d : 1.f, sd, inv);
-      const float lk = a[kk] * inv;  // lane kk: sqrt(d); lanes below: L[i][kk]
-      a[kk] = lk;
-      if (lane == kk) {
-        myinv = inv;
-#pragma unroll
-        for (int r = 0; r < NX; ++r) bx[r] *= inv;
-      }
-      col[lane] = lk;
-      if (NX > 0 && lane == kk) {
-#pragma unroll
-        for (int r = 0; r < NX; r += 4) {
-          const float t4[4] = {bx[r], bx[r + 1], bx[r + 2], bx[r + 3]};
-          sts4v(col + 32 + r, t4);
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int j4 = (kk + 1) / 4 * 4; j4 < 32; j4 += 4) {
-        float c4[4];
-        lds4v(col + j4, c4);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (j4 + u > kk) a[j4 + u] = fmaf(-lk, c4[u], a[j4 + u]);
-      }
-      if (NX > 0 && lane > kk) {
-#pragma unroll
-        for (int r = 0; r < NX; r += 4) {
-          float c4[4];
-          lds4v(col + 32 + r, c4);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) bx[r + u] = fmaf(-c4[u], lk, bx[r + u]);
-        }
-      }
-      __syncwarp();
-    }
-
-    float d2[NX > 1 ? NX - 1 : 1];  // small-block unknowns (every lane)
-    if constexpr (NX > 0) {
-      // L21^T beside L11 (rows 0..31, columns 32..), then the Schur complement
-      // of the last rows, lower part, one entry per lane
-#pragma unroll
-      for (int r = 0; r < NX; ++r) G[lane * LDG + 32 + r] = bx[r];
-      __syncwarp();
-      constexpr int NS = NX * (NX + 1) / 2;
-      for (int e = lane; e < NS; e += 32) {
-        int r = 0;
-        while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        const int s = e - r * (r + 1) / 2;
-        float acc = G[(32 + r) * LDG + 32 + s];
-#pragma unroll 8
-        for (int c = 0; c < 32; ++c) acc = fmaf(-G[c * LDG + 32 + r], G[c * LDG + 32 + s], acc);
-        G[(32 + r) * LDG + 32 + s] = acc;
-      }
-      __syncwarp();
-      // Cholesky of the Schur complement: lane r holds its row r < NX; the
-      // last row (the row itself) takes no pivot
-      float sr[NX];
-#pragma unroll
-      for (int t = 0; t < NX; ++t)
-        sr[t] = (lane < NX && t <= lane) ? G[(32 + lane) * LDG + 32 + t] : 0.f;
-      float sinv = 1.f;
-#pragma unroll
-      for (int kk = 0; kk < NX - 1; ++kk) {
-        const float d = __shfl_sync(FULL, sr[kk], kk);
-        const bool ok = finite_val(d) && d > 0.f;
-        if (!ok && !err) err = finite_val(d) ? ENKFMC_EDNONPOS : ENKFMC_ENONFINITE;
-        float sd, inv;
-        sqrt_and_inv(ok ? d : 1.f, sd, inv);
-        const float lk = sr[kk] * inv;
-        sr[kk] = lk;
-        if (lane == kk) sinv = inv;
-#pragma unroll
-        for (int j = kk + 1; j < NX; ++j) sr[j] = fmaf(-lk, __shfl_sync(FULL, lk, j), sr[j]);
-      }
-      if (lane < NX) {
-#pragma unroll
-        for (int t = 0; t < NX; ++t)
-          if (t <= lane) G[(32 + lane) * LDG + 32 + t] = sr[t];
-        dv[lane] = sinv;
-      }
-    }
-    // L11 (lower part of the registers) to shared memory for the sweeps
-#pragma unroll
-    for (int j = 0; j < 32; ++j) G[lane * LDG + j] = a[j];
-    __syncwarp();
+    lane_gather<NX>(G, q, sl, p, pmax, typical, ptab, tri, ftab, C, nH, lane);
+    const float lam = lane_ridge<NX>(G, p, N, ridge_c, lane);
+    float myinv;
+    int err = lane_factor<NX>(G, col, dv, myinv, lane);
 
     // beta = L^-T w
+    float d2[S::ND];
     float xb;
     if constexpr (NX > 0) {
       // last unknowns: L22^T beta2 = w2 (w2 = row NA of the Schur factor)
@@ -1258,84 +1385,26 @@ __global__ void __launch_bounds__(256, 2)
 
     // refinement: residual e = u - U_P^T beta of the anomalies
     float4 e4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (mv) e4 = *reinterpret_cast<const float4*>(U + (int64_t)jlab * g.ldN + 4 * lane);
+    if (mv) e4 = *reinterpret_cast<const float4*>(U + (int64_t)jlab * g.ldN + m0);
 #pragma unroll 4
     for (int i = 0; i < p; ++i) {
       const float bi = bv[i];
       if (mv) {
-        const float4 u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + 4 * lane);
+        const float4 u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + m0);
         e4.x = fmaf(-u4.x, bi, e4.x);
         e4.y = fmaf(-u4.y, bi, e4.y);
         e4.z = fmaf(-u4.z, bi, e4.z);
         e4.w = fmaf(-u4.w, bi, e4.w);
       }
     }
-    // c = U_P e - lambda beta: 32 predecessors at a time by a reduce-scatter
-    // (31 shuffles leave predecessor i0 + lane's sum in lane lane), the rest
-    // one warp sum each
-    const int pfull32 = p & ~31;
-    for (int i0 = 0; i0 < pfull32; i0 += 32) {
-      float part[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (mv) u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i0 + j] * g.ldN + 4 * lane);
-        part[j] = dot4(u4, e4);
-      }
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < o; ++j) {
-          const float send = hi ? part[j] : part[j + o];
-          const float keep = hi ? part[j + o] : part[j];
-          part[j] = keep + __shfl_xor_sync(FULL, send, o);
-        }
-      }
-      cv[i0 + lane] = part[0] - lam * bv[i0 + lane];
-    }
-    for (int i = pfull32; i < p; ++i) {
+    // c = U_P e - lambda beta, then delta = (L L^T)^-1 c
+    lane_reduce_to<NX>(cv, p, bv, 1.f, lam, lane, [&](int i) {
       float4 u4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (mv) u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + 4 * lane);
-      const float part = warp_sum(dot4(u4, e4));
-      if (lane == (i & 31)) cv[i] = part - lam * bv[i];
-    }
-    for (int i = p + lane; i < NA; i += 32) cv[i] = 0.f;
-    __syncwarp();
-
-    // delta = (L L^T)^-1 c: forward, then backward
-    float z = lane < NU ? cv[lane] : 0.f;
-    z = lane_forward<NU, LDG>(G, z, myinv, lane);
-    float zz = lane < NU ? z * z : 0.f;
-    if constexpr (NX > 0) {
-      // z2 = L22^-1 (c2 - L21 z1), every lane
-      float z2[NX - 1];
-#pragma unroll
-      for (int r = 0; r < NX - 1; ++r) z2[r] = warp_sum(G[lane * LDG + 32 + r] * z);
-#pragma unroll
-      for (int r = 0; r < NX - 1; ++r) {
-        float acc = cv[32 + r] - z2[r];
-#pragma unroll
-        for (int j = 0; j < r; ++j) acc = fmaf(-G[(32 + r) * LDG + 32 + j], z2[j], acc);
-        z2[r] = acc * dv[r];
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int r = 0; r < NX - 1; ++r) zz = fmaf(z2[r], z2[r], zz);
-      }
-      // delta2 = L22^-T z2, then z1 - L21^T delta2 for the leading sweep
-#pragma unroll
-      for (int t = NX - 2; t >= 0; --t) {
-        float acc = z2[t];
-#pragma unroll
-        for (int j = t + 1; j < NX - 1; ++j) acc = fmaf(-G[(32 + j) * LDG + 32 + t], d2[j], acc);
-        d2[t] = acc * dv[t];
-      }
-#pragma unroll
-      for (int r = 0; r < NX - 1; ++r) z = fmaf(-G[lane * LDG + 32 + r], d2[r], z);
-    }
-    zz = warp_sum(zz);
-    z = lane_backward<NU, LDG>(G, z, myinv, lane);
+      if (mv) u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + m0);
+      return dot4(u4, e4);
+    });
+    float zz;
+    const float z = lane_solve<NX>(G, cv, dv, myinv, lane, d2, zz);
     // D from the refined residual e' = e - U_P^T delta without reading U:
     //   |e'|^2 = |e|^2 - 2 delta.(U_P e) + delta^T G delta,
     //   U_P e = c + lambda beta,  delta^T G delta = |z|^2 - lambda |delta|^2
@@ -1380,6 +1449,176 @@ __global__ void __launch_bounds__(256, 2)
     if (lane == 0) Dout[orow] = err ? NAN : Dj;
     __syncwarp();
   }
+}
+
+// The adjoint of the regressions (as k_adj_regress, whose comment gives the
+// formulas) with the register factorisation of the rows above: one warp per
+// extended row of one block; the pair and gather tables from global memory.
+template <int NX>
+__global__ void __launch_bounds__(256, 2) k_adj_regress_lane(
+    const Geom g, const Block* __restrict__ blocks, const float* __restrict__ U,
+    const float* __restrict__ C, int nH, const float* __restrict__ Tg,
+    const float* __restrict__ Dg, const float* __restrict__ Te, const float* __restrict__ De,
+    const float* __restrict__ aT, const float* __restrict__ bT, const float* __restrict__ dxT,
+    const float* __restrict__ lamT, const int2* __restrict__ ptab,
+    const uint16_t* __restrict__ gtab, float* __restrict__ Eo, float* __restrict__ Fo,
+    float* __restrict__ Vo, float* __restrict__ Ko, double ridge_c, int32_t* status,
+    int warp_bytes, int sel) {
+  using S = Lane<NX>;
+  constexpr int NP = S::NP, LDG = S::LDG, NA = S::NA, NU = S::NU;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  signed char* off = reinterpret_cast<signed char*>(smem);
+  const int pmax = g.pmax;
+  const int offbytes = (3 * pmax + 15) / 16 * 16;
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
+    int dk, dy, dx;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    off[s] = (signed char)dk;
+    off[pmax + s] = (signed char)dy;
+    off[2 * pmax + s] = (signed char)dx;
+  }
+  __syncthreads();
+  unsigned char* base = smem + offbytes + (size_t)warp * warp_bytes;
+  int* q = reinterpret_cast<int*>(base);  // [NP] labels (q[NA] = j)
+  int* sl = q + NP;                        // [NP] slots
+  int* qr = sl + NP;                       // [NP] extended rows (block-relative)
+  float* G = reinterpret_cast<float*>(qr + NP);  // [NP][LDG]
+  float* col = G + (NP * LDG + 3) / 4 * 4;
+  float* bv = col + NP;                    // [NP] beta
+  float* cv = bv + NP;                     // [NP] betabar, then v
+  float* dv = cv + NP;                     // [8]
+  const int N = g.N, ldN = g.ldN;
+  const Block b = blocks[blockIdx.y];
+  const int loc = blockIdx.x * wpc + warp;
+  if (loc >= b.nb) return;
+  const int plane = b.ey * b.ex;
+  const int k = loc / plane;
+  const int yy0 = (loc - k * plane) / b.ex, xx0 = loc - k * plane - yy0 * b.ex;
+  const int y = b.lat_lo + yy0, x = imod(b.lon_lo + xx0, g.nlon);
+  const int v = b.var;
+  const int64_t rowj = b.row_off + loc;
+  // predecessors inside the extended box
+  int p = 0;
+  for (int s0 = 0; s0 < pmax; s0 += 32) {
+    const int s = s0 + lane;
+    bool pres = false;
+    int qq = 0, rr = 0;
+    if (s < pmax) {
+      int kq, yq, xq, yyq, xxq;
+      pres = slot_pred_off(g, k, y, x, off[s], off[pmax + s], off[2 * pmax + s], kq, yq, xq) &&
+             in_ext(b, g.nlon, yq, xq, yyq, xxq);
+      if (pres) {
+        qq = (int)coords_label(g, v, kq, yq, xq);
+        rr = (kq * b.ey + yyq) * b.ex + xxq;
+      }
+    }
+    const unsigned mask = __ballot_sync(FULL, pres);
+    const int idx = p + __popc(mask & ((1u << lane) - 1u));
+    if (pres) {
+      q[idx] = qq;
+      sl[idx] = s;
+      qr[idx] = rr;
+    }
+    p += __popc(mask);
+  }
+  const int jlab = (int)coords_label(g, v, k, y, x);
+  if (lane == 0) {
+    q[NA] = jlab;
+    sl[NA] = -1;
+  }
+  __syncwarp();
+  if (sel && ((2 * p > N) != (sel == 2))) return;  // the other launch's row
+  // beta and D of this instance
+  const bool inner = in_interior(b, y, x);
+  const float* trow = inner ? Tg + (int64_t)jlab * pmax : Te + rowj * pmax;
+  const float Dj = inner ? Dg[jlab] : De[rowj];
+  for (int i = lane; i < p; i += 32) bv[i] = -trow[sl[i]];
+  __syncwarp();
+  const int m0 = 4 * lane;  // lane's members m0 .. m0 + 3 (zero past N)
+  const bool mv = m0 < ldN;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 e4 = z4, aj = z4, bj = z4;
+  if (mv) {
+    e4 = ld_members(U + (int64_t)jlab * ldN, m0, N);
+    aj = ld_members(aT + rowj * ldN, m0, N);
+    bj = ld_members(bT + rowj * ldN, m0, N);
+  }
+  // e = u - U_P^T beta
+  for (int i = 0; i < p; ++i) {
+    const float bi = bv[i];
+    if (mv) {
+      const float4 u4 = ld_members(U + (int64_t)q[i] * ldN, m0, N);
+      e4.x = fmaf(-u4.x, bi, e4.x);
+      e4.y = fmaf(-u4.y, bi, e4.y);
+      e4.z = fmaf(-u4.z, bi, e4.z);
+      e4.w = fmaf(-u4.w, bi, e4.w);
+    }
+  }
+  const float ab = warp_sum(dot4(aj, bj));
+  const float Dbar = ab / (Dj * Dj);
+  const float ebs = 2.f * Dbar / (float)(N - 1);
+  // Gram matrix and ridge
+  const int pf = pmax - (g.periodic ? g.r : 0);
+  const bool typical = p == pf && (p == 0 || sl[p - 1] == pf - 1);
+  const int nfull = (pmax + 1) * (pmax + 2) / 2;
+  lane_gather<NX>(G, q, sl, p, pmax, typical, ptab, gtab, gtab + nfull, C, nH, lane);
+  const float lam = lane_ridge<NX>(G, p, N, ridge_c, lane);
+  // betabar_i = (<a_j, dX_qi> + <b_j, Lambda_qi>) / D_j - 2 Dbar lambda beta_i / (N - 1)
+  // (<U_qi, ebar> by the normal equations U_P e = lambda beta)
+  lane_reduce_to<NX>(cv, p, bv, 1.f / Dj, 2.f * Dbar * lam / (float)(N - 1), lane, [&](int i) {
+    if (!mv) return 0.f;
+    const int64_t r = (b.row_off + qr[i]) * ldN;
+    return dot4(aj, ld_members(dxT + r, m0, N)) + dot4(bj, ld_members(lamT + r, m0, N));
+  });
+  float myinv;
+  const int err = lane_factor<NX>(G, col, dv, myinv, lane);
+  float4 f4 = make_float4(ebs * e4.x, ebs * e4.y, ebs * e4.z, ebs * e4.w);
+  float kappa = 0.f;
+  if (err) {
+    if (lane == 0) record_error(status, err, rowj);
+    e4 = z4;
+    f4 = z4;
+    p = 0;  // defined (zero) terms for the failed row
+  } else {
+    // v = (G + lambda I)^-1 betabar into cv
+    float d2[S::ND], zz;
+    const float vl = lane_solve<NX>(G, cv, dv, myinv, lane, d2, zz);
+    if (lane < NU) cv[lane] = vl;
+    if constexpr (NX > 0) {
+      if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < NX - 1; ++r) cv[32 + r] = d2[r];
+      }
+    }
+    __syncwarp();
+    float vbeta = 0.f;
+    for (int i = lane; i < p; i += 32) vbeta = fmaf(cv[i], bv[i], vbeta);
+    vbeta = warp_sum(vbeta);
+    if (lam > 0.f) kappa = 2.f * (float)ridge_c / (float)p * vbeta;
+    // f = ebar + U_P^T v
+    for (int i = 0; i < p; ++i) {
+      const float vi = cv[i];
+      if (mv) {
+        const float4 u4 = ld_members(U + (int64_t)q[i] * ldN, m0, N);
+        f4.x = fmaf(u4.x, vi, f4.x);
+        f4.y = fmaf(u4.y, vi, f4.y);
+        f4.z = fmaf(u4.z, vi, f4.z);
+        f4.w = fmaf(u4.w, vi, f4.w);
+      }
+    }
+  }
+  // this row's outputs: e, f (members m0 .. m0 + 3), v in its slots, kappa
+  if (mv) {
+    *reinterpret_cast<float4*>(Eo + rowj * ldN + m0) = e4;
+    *reinterpret_cast<float4*>(Fo + rowj * ldN + m0) = f4;
+  }
+  float* vrow = Vo + rowj * pmax;
+  for (int s = lane; s < pmax; s += 32) vrow[s] = 0.f;
+  __syncwarp();
+  for (int i = lane; i < p; i += 32) vrow[sl[i]] = cv[i];
+  if (lane == 0) Ko[rowj] = kappa;
 }
 
 // ---------------------------------------------------------------------------
@@ -1817,7 +2056,7 @@ cudaError_t launch_regress_lane(const Geom& g, const float* U, const float* C,
                                 int sel, cudaStream_t s) {
   const int nH = cov_offset_count(g.r, g.vr);
   const int wpc = 8;
-  const int wb = lane_warp_bytes(NX, g.pmax);
+  const int wb = lane_warp_bytes(NX, 2 * (32 + NX) + (g.pmax + 3) / 4 * 4);
   const size_t tables = (3 * (size_t)g.pmax + 15) / 16 * 16 + gather_table_bytes(g.pmax);
   const size_t ptab = pair_table_bytes(g.pmax, g.r, g.periodic);
   int use_ptab = 1;
@@ -1864,6 +2103,28 @@ cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t*
                                      sel, s);
 }
 
+template <int NX>
+cudaError_t launch_adj_regress_lane(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                                    const float* U, const float* C, const float* Tg,
+                                    const float* Dg, const float* Te, const float* De,
+                                    const float* aT, const float* bT, const float* dxT,
+                                    const float* lamT, const int2* ptab, const uint16_t* gtab,
+                                    float* Eo, float* Fo, float* Vo, float* Ko, double ridge_c,
+                                    int32_t* status, int sel, cudaStream_t s) {
+  const int nH = cov_offset_count(g.r, g.vr);
+  const int wpc = 8;
+  const int wb = lane_warp_bytes(NX, 3 * (32 + NX));
+  const size_t smem = (3 * (size_t)g.pmax + 15) / 16 * 16 + (size_t)wpc * wb;
+  cudaError_t e = cudaFuncSetAttribute(k_adj_regress_lane<NX>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((nb_max + wpc - 1) / wpc, nblock);
+  k_adj_regress_lane<NX><<<grid, 32 * wpc, smem, s>>>(g, blocks, U, C, nH, Tg, Dg, Te, De, aT,
+                                                      bT, dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko,
+                                                      ridge_c, status, wb, sel);
+  return cudaGetLastError();
+}
+
 template <typename T, typename TS>
 cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, int nb_max,
                                const T* U, const T* C, const TS* Tg, const TS* Dg, const TS* Te,
@@ -1874,6 +2135,17 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
                                cudaStream_t s) {
   if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
     return cudaErrorInvalidConfiguration;
+  if constexpr (std::is_same<T, float>::value && std::is_same<TS, float>::value) {
+    if (regress_lane_applies(g, sel) && ptab && gtab) {
+      if (g.pmax + 1 > 32)
+        return launch_adj_regress_lane<8>(g, blocks, nblock, nb_max, U, C, Tg, Dg, Te, De, aT,
+                                          bT, dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c,
+                                          status, sel, s);
+      return launch_adj_regress_lane<0>(g, blocks, nblock, nb_max, U, C, Tg, Dg, Te, De, aT, bT,
+                                        dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c, status,
+                                        sel, s);
+    }
+  }
   const int nH = cov_offset_count(g.r, g.vr);
   RegShape rs;
   if (!regress_shape(g, sizeof(T), false, rs)) return cudaErrorInvalidConfiguration;
