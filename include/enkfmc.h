@@ -317,14 +317,16 @@ enkfmc_status enkfmc_batch_query(const enkfmc_batch* b, int32_t* nstreams, int32
 void enkfmc_batch_destroy(enkfmc_batch* b);
 
 /* Launch tuning of one handle.  The grid cap is the autotuner's knob and
- * changes no result; the kernel choice changes results at the rounding level. */
+ * changes no result; the kernel choice changes results at the rounding level
+ * (both kernels match the FP64 reference to the single-precision tolerance). */
 enum {
   ENKFMC_TUNE_REGRESS_CTAS_PER_SM = 0, /* CTAs per SM of the regressions' grid-stride
                                           launch (0 = the default, 64)              */
-  ENKFMC_TUNE_REGRESS_TILED = 1        /* 1: every single-precision row through the
-                                          shared-memory tiled kernel; 0 (default):
-                                          stencils of 16..39 slots through the
-                                          register kernel                           */
+  ENKFMC_TUNE_REGRESS_KERNEL = 1       /* single-precision regression kernels:
+                                          0 (default) tiled forward, register-
+                                          resident adjoint; 1 tiled everywhere;
+                                          2 register-resident wherever the stencil
+                                          has 16..39 slots                          */
 };
 enkfmc_status enkfmc_set_tuning(enkfmc_handle* h, int32_t knob, int32_t value);
 

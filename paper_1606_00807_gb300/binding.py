@@ -79,7 +79,7 @@ FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
 FLAG_REFINE_MASK = 0xF00
 TUNE_REGRESS_CTAS_PER_SM = 0
-TUNE_REGRESS_TILED = 1
+TUNE_REGRESS_KERNEL = 1
 
 
 def flag_refine_steps(k: int) -> int:

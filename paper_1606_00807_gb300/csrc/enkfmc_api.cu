@@ -114,7 +114,7 @@ enkfmc_status problem_geom(const enkfmc_problem& p, Geom& g) {
   if (!estimate_supported(g, p.precision != ENKFMC_FP64)) return ENKFMC_EINVAL;
   g.sm_count = 0;  // filled where a device is at hand
   g.regress_cap = 0;
-  g.regress_tiled = 0;
+  g.regress_kernel = 0;
   return ENKFMC_OK;
 }
 

@@ -251,9 +251,9 @@ enkfmc_status enkfmc_set_tuning(enkfmc_handle* h, int32_t knob, int32_t value) {
       if (value > 1024) return ENKFMC_EINVAL;
       h->g.regress_cap = value;
       return ENKFMC_OK;
-    case ENKFMC_TUNE_REGRESS_TILED:
-      if (value > 1) return ENKFMC_EINVAL;
-      h->g.regress_tiled = value;
+    case ENKFMC_TUNE_REGRESS_KERNEL:
+      if (value > 2) return ENKFMC_EINVAL;
+      h->g.regress_kernel = value;
       return ENKFMC_OK;
   }
   return ENKFMC_EINVAL;

@@ -21,7 +21,7 @@ struct Geom {
   int32_t pmax;
   int32_t sm_count;      // SMs of the device (launch shapes; host side only)
   int32_t regress_cap;   // CTAs per SM of the regressions' grid-stride launch
-  int32_t regress_tiled; // 1: the shared-memory tiled regression kernel for every row
+  int32_t regress_kernel; // regression kernels: 0 default, 1 tiled, 2 register (k_estimate.cu)
   int64_t n;
   int64_t var_off[kMaxVar + 1];
   int32_t var_lev[kMaxVar];

@@ -2041,12 +2041,18 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
   return cudaGetLastError();
 }
 
-// The register kernel (k_regress_lane) serves single-precision rows of
-// stencils with 16 to 39 predecessor slots; NX = 8 when the padded Gram
-// matrix needs rows past the 32 lanes.
-bool regress_lane_applies(const Geom& g, int sel) {
-  return !g.regress_tiled && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 &&
-         g.pmax + 1 <= 40;
+// The register kernels (k_regress_lane, k_adj_regress_lane) can serve
+// single-precision rows of stencils with 16 to 39 predecessor slots (NX = 8
+// when the padded Gram matrix needs rows past the 32 lanes).  Measured on the
+// T63 rows (N = 80, 39 slots): the forward regressions run faster tiled (5.98
+// against 7.29 ms for the global rows, 3.49 against 6.01 ms for the boundary
+// rows, whose short predecessor lists the register kernel pads to 39), the
+// adjoint regressions faster in registers (12.1 against 12.9 ms); the default
+// (kernel choice 0) follows that, 1 takes the tiled kernels, 2 the register
+// kernels wherever they apply.
+bool regress_lane_applies(const Geom& g, int sel, bool adjoint) {
+  const bool want = g.regress_kernel == 2 || (g.regress_kernel == 0 && adjoint);
+  return want && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 && g.pmax + 1 <= 40;
 }
 
 template <int NX>
@@ -2084,7 +2090,7 @@ cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t*
   if (nitems <= 0) return cudaSuccess;
   if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds) return cudaErrorInvalidConfiguration;
   if constexpr (std::is_same<T, float>::value && std::is_same<TO, float>::value) {
-    if (regress_lane_applies(g, sel)) {
+    if (regress_lane_applies(g, sel, false)) {
       if (g.pmax + 1 > 32)
         return launch_regress_lane<8>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
                                       sel, s);
@@ -2136,7 +2142,7 @@ cudaError_t launch_adj_regress(const Geom& g, const Block* blocks, int nblock, i
   if (g.pmax + 1 > 32 * kMaxRounds * 2 || g.N > 32 * kMaxRounds)
     return cudaErrorInvalidConfiguration;
   if constexpr (std::is_same<T, float>::value && std::is_same<TS, float>::value) {
-    if (regress_lane_applies(g, sel) && ptab && gtab) {
+    if (regress_lane_applies(g, sel, true) && ptab && gtab) {
       if (g.pmax + 1 > 32)
         return launch_adj_regress_lane<8>(g, blocks, nblock, nb_max, U, C, Tg, Dg, Te, De, aT,
                                           bT, dxT, lamT, ptab, gtab, Eo, Fo, Vo, Ko, ridge_c,

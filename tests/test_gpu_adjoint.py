@@ -14,8 +14,12 @@ pytestmark = pytest.mark.gpu
 
 # FP64: rounding order only.  FP32: the reverse solves are refined like the
 # forward ones, but the recomputed Gram factors of the single-precision rows
-# solve v = (G + lambda I)^-1 betabar in single precision without refinement.
-TOL = {0: 1e-9, 1: 1e-3}
+# solve v = (G + lambda I)^-1 betabar in single precision without refinement
+# (measured at most 5.5e-6 on the small cases).  At T63 with N = 40 the Gram
+# matrices reach condition numbers near 1e8 and the reverse pass reads T, D,
+# dX and Lambda stored in single precision: 1e-3 there (measured 5.2e-4).
+TOL = {0: 1e-9, 1: 1e-4}
+TOL_T63_N40 = 1e-3
 
 
 @pytest.fixture(scope="module")
@@ -26,11 +30,13 @@ def torch_cuda():
     return torch
 
 
-def _gpu_grad(torch, w, inp, precision, seed):
+def _gpu_grad(torch, w, inp, precision, seed, tuning=None):
     from paper_1606_00807_gb300 import binding as B
     dt = torch_dtype(precision)
     h = B.Handle.from_workload(w, precision=precision,
                                stream=torch.cuda.current_stream().cuda_stream)
+    for knob, value in (tuning or {}).items():
+        h.set_tuning(knob, value)
     h.set_observations(inp.obs_idx)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
     Xb, y, R, Z = dev(inp.Xb), dev(inp.y), dev(inp.R), dev(inp.Z)
@@ -69,6 +75,27 @@ def test_adjoint_matches_oracle(torch_cuda, name, precision):
           " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
     for k, v in errs.items():
         assert v < TOL[precision], (k, v)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_adjoint_regression_kernels_match_oracle(torch_cuda, kernel):
+    """FP32 reverse pass with the tiled (1) and the register-resident (2)
+    regression adjoint (ENKFMC_TUNE_REGRESS_KERNEL) on the T63 statistics
+    (37-39 slots), each against the oracle's gradient."""
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["small_48x26x3x1+1_n80_r2"]
+    inp = make_inputs(w, np.float32)
+    Xa_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
+    _, W = loss_mean_analysis(Xa_ref, inp.truth)
+    W = (W + 0.01 * np.random.default_rng(3).standard_normal(W.shape)).astype(np.float32)
+    _, Xb_bar, y_bar, R_bar = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z,
+                                                     inp.obs_idx, W)
+    got = _gpu_grad(torch_cuda, w, inp, 1, W, tuning={B.TUNE_REGRESS_KERNEL: kernel})
+    errs = {k: O.rel_err(g, r) for k, g, r in (("Xb", got[1], Xb_bar), ("y", got[2], y_bar),
+                                               ("R", got[3], R_bar))}
+    print(f"\nadjoint kernel {kernel}: " + " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
+    for k, v in errs.items():
+        assert v < TOL[1], (k, v)
 
 
 def test_gpu_gradient_matches_gpu_finite_differences(torch_cuda):
@@ -159,7 +186,7 @@ def test_adjoint_t63_one_subdomain_seed(torch_cuda, name):
     print(f"\nadjoint {name} one sub-domain seed: " +
           " ".join(f"{k} {v:.2e}" for k, v in errs.items()))
     for k, v in errs.items():
-        assert v < TOL[1], (k, v)
+        assert v < TOL_T63_N40, (k, v)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
