@@ -167,33 +167,58 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
     Sr[jj] = (j < 0 || j >= b.nb) ? INT32_MIN : srcrow[b.row_off + j];
   }
   // bit s of Mk[k] / My[yy] / Mx[xx]: the row at offset s from that position
-  // stays inside the box along that axis (bit pmax: the row itself)
-  for (int e = threadIdx.x; e < b.nlev_b + b.ey + b.ex; e += kAsmThreads) {
+  // stays inside the box along that axis (bit pmax: the row itself); a warp per
+  // position, lanes over the slots
+  for (int e = warp; e < b.nlev_b + b.ey + b.ex; e += nw) {
     const int axis = e < b.nlev_b ? 0 : (e < b.nlev_b + b.ey ? 1 : 2);
     const int pos = e - (axis == 0 ? 0 : (axis == 1 ? b.nlev_b : b.nlev_b + b.ey));
     const int lim = axis == 0 ? b.nlev_b : (axis == 1 ? b.ey : b.ex);
     uint64_t m = (uint64_t)1 << pmax;
-    for (int sl = 0; sl < pmax; ++sl) {
-      int o3[3];
-      slot_offset(sl, g.r, g.vr, o3[0], o3[1], o3[2]);
-      const int q = pos - o3[axis];
-      if (q >= 0 && q < lim) m |= (uint64_t)1 << sl;
+    for (int s0 = 0; s0 < pmax; s0 += 32) {
+      const int sl = s0 + lane;
+      bool in = false;
+      if (sl < pmax) {
+        int o3[3];
+        slot_offset(sl, g.r, g.vr, o3[0], o3[1], o3[2]);
+        const int q = pos - o3[axis];
+        in = q >= 0 && q < lim;
+      }
+      m |= (uint64_t)__ballot_sync(0xffffffffu, in) << s0;
     }
-    (axis == 0 ? Mk : (axis == 1 ? My : Mx))[pos] = m;
+    if (lane == 0) (axis == 0 ? Mk : (axis == 1 ? My : Mx))[pos] = m;
   }
   __syncthreads();
-  // stage rows j in [jlo, jlo + nrow): flat over (row, slot), slot pmax = 1,
-  // slot pmax + 1 = 1 / D[j]
-  for (int e = threadIdx.x; e < nrow * ldt; e += kAsmThreads) {
-    const int jj = e / ldt, sl = e - jj * ldt;
-    const int sr = Sr[jj];
-    T v = T(0);
-    if (sr != INT32_MIN) {
-      if (sl < pmax) v = sr >= 0 ? Tg[(int64_t)sr * pmax + sl] : Te[(int64_t)(~sr) * pmax + sl];
-      else if (sl == pmax) v = T(1);
-      else if (sl == pmax + 1) v = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
+  // stage rows j in [jlo, jlo + nrow): a warp per row, lanes over the slots
+  // (slot pmax = 1, slot pmax + 1 = 1 / D[j]); the loads of kStage rows are
+  // issued before any is stored
+  constexpr int kStage = 4, kSlotRounds = 3;  // ldt <= 96 (pmax <= 63 here)
+  for (int jj0 = warp * kStage; jj0 < nrow; jj0 += nw * kStage) {
+    T v[kStage][kSlotRounds];
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int jj = jj0 + u;
+      const int sr = jj < nrow ? Sr[jj] : INT32_MIN;
+#pragma unroll
+      for (int h = 0; h < kSlotRounds; ++h) {
+        const int sl = lane + 32 * h;
+        T x = T(0);
+        if (sr != INT32_MIN) {
+          if (sl < pmax) x = sr >= 0 ? Tg[(int64_t)sr * pmax + sl] : Te[(int64_t)(~sr) * pmax + sl];
+          else if (sl == pmax) x = T(1);
+          else if (sl == pmax + 1) x = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
+        }
+        v[u][h] = x;
+      }
     }
-    Ts[e] = v;
+#pragma unroll
+    for (int u = 0; u < kStage; ++u) {
+      const int jj = jj0 + u;
+#pragma unroll
+      for (int h = 0; h < kSlotRounds; ++h) {
+        const int sl = lane + 32 * h;
+        if (jj < nrow && sl < ldt) Ts[jj * ldt + sl] = v[u][h];
+      }
+    }
   }
   __syncthreads();
 

@@ -702,7 +702,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
   T* gv = vb + ldp;                         // [ldp]
   T* invd = gv + ldp;                       // [ldp]
   const int N = g.N;
-  const bool fp32 = sizeof(T) == 4;
 
   for (int64_t item = (int64_t)blockIdx.x * wpc + warp; item < nitems;
        item += (int64_t)gridDim.x * wpc) {
@@ -807,45 +806,42 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
       tiled_backward(L, ldg, invd, va, p, lane);
       for (int i = lane; i < p; i += 32) vb[i] = va[i];
       __syncwarp();
-      if (fp32) {
-        // residual e = u - U_P^T beta, members m = lane + 32 t
+      if constexpr (sizeof(T) == 4) {
+        // residual e = u - U_P^T beta, members m0 .. m0 + 3 of this lane
+        // (m0 = 4 lane < ldN; U is zero past N)
         // (single precision with FMA: the correction needs the residual of the
         // data, not extra digits of it; measured on the T63 statistics against
         // the FP64 regressions, the refined beta and D match a compensated
         // residual's to within 2e-7)
-        float e[MR];
-#pragma unroll
-        for (int t = 0; t < MR; ++t) {
-          const int m = lane + 32 * t;
-          e[t] = (m < N) ? (float)U[(int64_t)jlab * g.ldN + m] : 0.f;
-        }
+        const int m0 = 4 * lane;
+        const bool mv = m0 < g.ldN;
+        float4 e4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mv) e4 = *reinterpret_cast<const float4*>(U + (int64_t)jlab * g.ldN + m0);
 #pragma unroll 4
         for (int i = 0; i < p; ++i) {
-          const float bi = (float)vb[i];
-          const T* Ui = U + (int64_t)q[i] * g.ldN;
-#pragma unroll
-          for (int t = 0; t < MR; ++t) {
-            const int m = lane + 32 * t;
-            if (m < N) e[t] = fmaf(-(float)Ui[m], bi, e[t]);
+          const float bi = vb[i];
+          if (mv) {
+            const float4 u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + m0);
+            e4.x = fmaf(-u4.x, bi, e4.x);
+            e4.y = fmaf(-u4.y, bi, e4.y);
+            e4.z = fmaf(-u4.z, bi, e4.z);
+            e4.w = fmaf(-u4.w, bi, e4.w);
           }
         }
         // c = U_P e - lambda beta, the residual of (G + lambda I) beta = g -> va.
         // Full batches of 32 predecessors: each lane forms its partial dot
         // products, then a reduce-scatter (31 shuffles) leaves predecessor
         // i0 + lane's sum in lane lane; the rest one warp sum each
+        auto udot = [&](int i) {
+          if (!mv) return 0.f;
+          const float4 u4 = *reinterpret_cast<const float4*>(U + (int64_t)q[i] * g.ldN + m0);
+          return fmaf(u4.w, e4.w, fmaf(u4.z, e4.z, fmaf(u4.y, e4.y, u4.x * e4.x)));
+        };
         const int pfull32 = p & ~31;
         for (int i0 = 0; i0 < pfull32; i0 += 32) {
           float part[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            part[j] = 0.f;
-            const T* Ui = U + (int64_t)q[i0 + j] * g.ldN;
-#pragma unroll
-            for (int t = 0; t < MR; ++t) {
-              const int m = lane + 32 * t;
-              if (m < N) part[j] = fmaf((float)Ui[m], e[t], part[j]);
-            }
-          }
+          for (int j = 0; j < 32; ++j) part[j] = udot(i0 + j);
 #pragma unroll
           for (int o = 16; o >= 1; o >>= 1) {
             const bool hi = (lane & o) != 0;
@@ -860,14 +856,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
           va[i] = (T)(part[0] - (float)lam * (float)vb[i]);
         }
         for (int i = pfull32; i < p; ++i) {
-          const T* Ui = U + (int64_t)q[i] * g.ldN;
-          float part = 0.f;
-#pragma unroll
-          for (int t = 0; t < MR; ++t) {
-            const int m = lane + 32 * t;
-            if (m < N) part = fmaf((float)Ui[m], e[t], part);
-          }
-          part = warp_sum(part);
+          const float part = warp_sum(udot(i));
           if (lane == (i & 31)) va[i] = (T)(part - (float)lam * (float)vb[i]);
         }
         __syncwarp();
@@ -883,10 +872,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
         //   |e'|^2 = |e|^2 - 2 delta.(U_P e) + delta^T G delta,
         //   U_P e = c + lambda beta,  delta^T G delta = |z|^2 - lambda |delta|^2;
         // the corrections are small next to |e|^2
-        float ee = 0.f;
-#pragma unroll
-        for (int t = 0; t < MR; ++t) ee = fmaf(e[t], e[t], ee);
-        ee = warp_sum(ee);
+        const float ee = warp_sum(
+            fmaf(e4.w, e4.w, fmaf(e4.z, e4.z, fmaf(e4.y, e4.y, e4.x * e4.x))));
         float dc = 0.f, dd = 0.f;
         for (int i = lane; i < p; i += 32) {
           const float di = (float)va[i];
