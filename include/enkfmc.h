@@ -210,6 +210,42 @@ enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
 enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
                                 const void* Rdiag, const void* Z, void* Xa);
 
+/* ---------------------------------------------------------------------------
+ * Filter cycling (Algorithm 1: analysis, then the model step of every member,
+ * repeated while observations arrive).  The paper's model (SPEEDY) is
+ * replaced by a synthetic forecast operator, and the analysis error is the
+ * RMSE of Eq. 18.
+ * ------------------------------------------------------------------------ */
+/* Forecast operator: every field of nvec state vectors (device, member-major
+ * [nvec][n], the handle's element type) moves `shift` cells eastward along its
+ * latitude circle, periodic in longitude (advection of the random fields,
+ * whose statistics it keeps).  X and Xout are distinct.  Any integer shift
+ * (taken mod nlon).  Queued on the handle's stream. */
+enkfmc_status enkfmc_forecast_shift(enkfmc_handle* h, const void* X, void* Xout, int32_t nvec,
+                                    int32_t shift);
+/* Summand of Eq. 18: *out (device double) = sum_l (mean_m Xa[m][l] - xref[l])^2
+ * for Xa [N][n] and xref [n] (device, the handle's element type), the mean and
+ * the sum in double precision in a fixed order (the same bits on every run).
+ * Queued on the handle's stream. */
+enkfmc_status enkfmc_ensemble_sqerr(enkfmc_handle* h, const void* Xa, const void* xref,
+                                    double* out);
+/* M cycles of Algorithm 1 with enkfmc_forecast_shift as the model: for k = 0..M-1,
+ * the analysis (enkfmc_estimate, enkfmc_assemble, enkfmc_analyze) of Xb with
+ * observations ys[k] ([M][m]) and perturbations Zs[k] ([M][N][m]) into Xa,
+ * sqerr[k] = enkfmc_ensemble_sqerr(Xa, xrefs[k]) (xrefs [M][n], the reference
+ * states; sqerr device double [M]), then Xb = forecast(Xa).  Eq. 18's RMSE is
+ * sqrt(sum_k sqerr[k] / M).  On return Xb holds the forecast after the last
+ * analysis and Xa that analysis; Tvals and D the last estimate.  Device
+ * buffers, the handle's element type; ys, Zs, Rdiag may be null without
+ * observations.  Cycle 0 runs eagerly; the others replay one CUDA graph
+ * captured from a private stream (on fixed buffers the handle allocates on the
+ * first call; the kernel timing counts the captured cycle once).  Synchronises
+ * the handle's stream before the capture and on return.  Numerical failures:
+ * enkfmc_get_status. */
+enkfmc_status enkfmc_filter_run(enkfmc_handle* h, void* Xb, const void* ys, const void* Zs,
+                                const void* Rdiag, const void* xrefs, void* Tvals, void* D,
+                                void* Xa, int32_t M, int32_t shift, double* sqerr);
+
 /* Reverse pass of the last analysis.  Given Xa_bar = dL/dX^a ([N][n]) of a
  * scalar loss L, writes dL/dy (y_bar, [m]), dL/d diag(R) (Rdiag_bar, [m]) and
  * dL/dX^b (Xb_bar, [N][n]) through every step: the interior write-back
@@ -347,7 +383,10 @@ enum {
   ENKFMC_K_ADJ_REGRESS = 11,/* reverse pass through the regressions              */
   ENKFMC_K_FP64_BLOCKS = 12,/* single precision: the blocks whose factorisation
                                failed, assembled and factored in double          */
-  ENKFMC_NKERNEL = 13
+  ENKFMC_K_FORECAST = 13,   /* filter cycling: the forecast operator (advection) */
+  ENKFMC_K_SQERR = 14,      /* filter cycling: squared error of the ensemble mean
+                               (Eq. 18)                                          */
+  ENKFMC_NKERNEL = 15
 };
 
 /* Kernel timing.  Work is launched in calls of one kernel kind; a call runs

@@ -15,6 +15,8 @@ Cholesky Decomposition", 2016):
   Section 2.3, Eq. 12-13 dual analysis increment
   Section 3, Eq. 14, Algorithms 2-3  sub-domain analysis with an r-wide
                          boundary that is discarded after the local solve
+  Algorithm 1, Eq. 18    filter cycling with a synthetic forecast operator
+                         (advection) and the analysis RMSE (cycling.py)
 
 Floating point is float64 throughout.  Library routines (matrix products,
 Cholesky factorisation, triangular and sparse solves) serve as single steps;
@@ -24,8 +26,10 @@ from .enkfmc import (Grid, Subdomain, anomalies, perturbed_observations, regress
                      estimate_rows, subdomains, local_estimate, local_system, local_analysis,
                      analysis, assimilate, b_hat_dense, gain_form_analysis, dual_form_analysis,
                      t_pattern_csr, rel_err)
+from .cycling import forecast_shift, ensemble_sqerr, rmse_eq18, filter_cycles
 
 __all__ = ["Grid", "Subdomain", "anomalies", "perturbed_observations", "regress", "estimate",
            "estimate_rows", "subdomains", "local_estimate", "local_system", "local_analysis",
            "analysis", "assimilate", "b_hat_dense", "gain_form_analysis", "dual_form_analysis",
-           "t_pattern_csr", "rel_err"]
+           "t_pattern_csr", "rel_err", "forecast_shift", "ensemble_sqerr", "rmse_eq18",
+           "filter_cycles"]

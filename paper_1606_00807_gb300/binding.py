@@ -52,6 +52,10 @@ SIGNATURES = {
     "enkfmc_assemble": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_analyze": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_cycle_host": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_forecast_shift": (c_int32, [_H, c_void_p, c_void_p, c_int32, c_int32]),
+    "enkfmc_ensemble_sqerr": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_filter_run": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
     "enkfmc_analyze_adjoint": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_get_status": (c_int32, [_H, POINTER(c_int64)]),
     "enkfmc_export_T_pattern": (c_int32, [_H, c_void_p, c_void_p]),
@@ -74,7 +78,7 @@ SIGNATURES = {
     "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
                                           c_void_p]),
 }
-NKERNEL = 13
+NKERNEL = 15
 FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
 FLAG_REFINE_MASK = 0xF00
@@ -221,6 +225,19 @@ class Handle:
     def cycle_host(self, Xb, y, R, Z, Xa):
         _check(self.lib.enkfmc_cycle_host(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
                "enkfmc_cycle_host")
+
+    def forecast_shift(self, X, Xout, nvec: int, shift: int):
+        _check(self.lib.enkfmc_forecast_shift(self.h, _ptr(X), _ptr(Xout), nvec, shift),
+               "enkfmc_forecast_shift")
+
+    def ensemble_sqerr(self, Xa, xref, out):
+        _check(self.lib.enkfmc_ensemble_sqerr(self.h, _ptr(Xa), _ptr(xref), _ptr(out)),
+               "enkfmc_ensemble_sqerr")
+
+    def filter_run(self, Xb, ys, Zs, R, xrefs, Tvals, D, Xa, M: int, shift: int, sqerr):
+        _check(self.lib.enkfmc_filter_run(self.h, _ptr(Xb), _ptr(ys), _ptr(Zs), _ptr(R),
+                                          _ptr(xrefs), _ptr(Tvals), _ptr(D), _ptr(Xa), M, shift,
+                                          _ptr(sqerr)), "enkfmc_filter_run")
 
     def set_tuning(self, knob: int, value: int):
         _check(self.lib.enkfmc_set_tuning(self.h, knob, value), "enkfmc_set_tuning")

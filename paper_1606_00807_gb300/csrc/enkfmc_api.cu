@@ -387,8 +387,10 @@ void release(enkfmc_handle* h) {
                   h->d_Xb,    h->d_y,       h->d_R,   h->d_Z,       h->d_Xa,     h->d_T,
                   h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
                   h->d_Eo,    h->d_Fo,      h->d_Vo,  h->d_Ko,  h->d_U64,     h->d_C64, h->d_W,      h->d_bfail,  h->d_fb_cnt,
-                  h->d_fb_blocks, h->d_fb_band, h->d_c1max};
+                  h->d_fb_blocks, h->d_fb_band, h->d_c1max, h->d_sqp, h->d_fy, h->d_fZ,
+                  h->d_fx,    h->d_fsq};
   for (void* b : bufs) dfree(b);
+  if (h->f_stream) cudaStreamDestroy(h->f_stream);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
 }
@@ -683,6 +685,10 @@ void compute_work(enkfmc_handle* h, const std::vector<int>& p_global,
   h->work_bytes[ENKFMC_K_BANDSOLVE] = es * (2.0 * (double)h->band_elems + 4.0 * N * er);
   h->work_flops[ENKFMC_K_WRITEBACK] = N * n;
   h->work_bytes[ENKFMC_K_WRITEBACK] = es * 3.0 * N * n;
+  h->work_flops[ENKFMC_K_FORECAST] = 0;
+  h->work_bytes[ENKFMC_K_FORECAST] = es * 2.0 * N * n;
+  h->work_flops[ENKFMC_K_SQERR] = (N + 2.0) * n;
+  h->work_bytes[ENKFMC_K_SQERR] = es * (N + 1.0) * n;
   // covariance table: 2N flops per valid pair (both components inside the grid)
   const int r = g.r, w4 = 4 * r + 1, nH = cov_offset_count(g.r, g.vr);
   double pairs = 0;
@@ -1076,6 +1082,34 @@ enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_
   return ENKFMC_OK;
 }
 
+enkfmc_status enkfmc_forecast_shift(enkfmc_handle* h, const void* X, void* Xout, int32_t nvec,
+                                    int32_t shift) {
+  if (!h || !X || !Xout || X == Xout || nvec < 1) return ENKFMC_EINVAL;
+  const int nl = h->g.nlon;
+  const int s = ((shift % nl) + nl) % nl;
+  return timed(h, ENKFMC_K_FORECAST, [&]() -> cudaError_t {
+    if (is_fp64(h))
+      return launch_shift<double>(h->g, (const double*)X, (double*)Xout, nvec, s, h->stream);
+    return launch_shift<float>(h->g, (const float*)X, (float*)Xout, nvec, s, h->stream);
+  });
+}
+
+enkfmc_status enkfmc_ensemble_sqerr(enkfmc_handle* h, const void* Xa, const void* xref,
+                                    double* out) {
+  if (!h || !Xa || !xref || !out) return ENKFMC_EINVAL;
+  if (!h->d_sqp) {
+    if (enkfmc_status st = dalloc(h, &h->d_sqp, sizeof(double) * kSqGrid)) return st;
+  }
+  return timed(h, ENKFMC_K_SQERR, [&](int* nk) -> cudaError_t {
+    *nk += 2;
+    if (is_fp64(h))
+      return launch_sqerr<double>(h->g, (const double*)Xa, (const double*)xref, h->d_sqp, out,
+                                  h->stream);
+    return launch_sqerr<float>(h->g, (const float*)Xa, (const float*)xref, h->d_sqp, out,
+                               h->stream);
+  });
+}
+
 enkfmc_status enkfmc_profile(enkfmc_handle* h, int32_t enable) {
   if (!h) return ENKFMC_EINVAL;
   h->prof = enable != 0;
@@ -1107,7 +1141,7 @@ const char* enkfmc_kernel_name(int32_t kind) {
                                               "assemble",  "bandchol",  "rhs",
                                               "bandsolve", "writeback", "covtable",
                                               "residual",  "adjoint",   "adj_regress",
-                                              "fp64_blocks"};
+                                              "fp64_blocks", "forecast", "sqerr"};
   return (kind >= 0 && kind < ENKFMC_NKERNEL) ? names[kind] : "unknown";
 }
 

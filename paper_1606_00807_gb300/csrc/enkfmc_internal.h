@@ -276,6 +276,13 @@ struct enkfmc_handle {
   void* d_W = nullptr;    // the reverse pass's right-hand side W (refinement)
   void *d_Eo = nullptr, *d_Fo = nullptr, *d_Vo = nullptr, *d_Ko = nullptr;  // per extended
                           // row: the regression adjoint's e, f, v (slots), kappa
+  // filter cycling: squared-error partial sums (kSqGrid), and the fixed
+  // buffers of the captured cycle (observations, perturbations, reference
+  // state, squared error) with the stream it is captured on
+  double* d_sqp = nullptr;
+  void *d_fy = nullptr, *d_fZ = nullptr, *d_fx = nullptr;
+  double* d_fsq = nullptr;
+  cudaStream_t f_stream = nullptr;
 
   // kernel timing (events bracket each launch while enabled)
   struct Rec {
@@ -476,5 +483,13 @@ cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nbloc
                                    const float* rhs_in, float* res, cudaStream_t s);
 // y += x over `count` elements.
 cudaError_t launch_accumulate(float* y, const float* x, int64_t count, cudaStream_t s);
+
+// filter cycling (k_cycle.cu): forecast operator and Eq. 18's squared error
+constexpr int kSqGrid = 1024;  // blocks of the squared-error reduction (fixed order)
+template <typename T>
+cudaError_t launch_shift(const Geom& g, const T* X, T* Y, int nvec, int shift, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sqerr(const Geom& g, const T* Xa, const T* xref, double* part, double* out,
+                         cudaStream_t s);
 
 }  // namespace enkfmc
