@@ -2031,15 +2031,15 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
 // The register kernels (k_regress_lane, k_adj_regress_lane) can serve
 // single-precision rows of stencils with 16 to 39 predecessor slots (NX = 8
 // when the padded Gram matrix needs rows past the 32 lanes).  Measured on the
-// T63 rows (N = 80, 39 slots): the forward regressions run faster tiled (5.98
-// against 7.29 ms for the global rows, 3.49 against 6.01 ms for the boundary
-// rows, whose short predecessor lists the register kernel pads to 39), the
-// adjoint regressions faster in registers (12.1 against 12.9 ms); the default
-// (kernel choice 0) follows that, 1 takes the tiled kernels, 2 the register
-// kernels wherever they apply.
+// T63 rows (N = 80, 39 slots) the tiled kernels are faster: 5.98 against 7.29
+// ms for the global rows, 3.49 against 6.01 ms for the boundary rows (whose
+// short predecessor lists the register kernel pads to 39), 12.1 against 15.6
+// ms for the adjoint.  So the default (kernel choice 0, as 1) is tiled; 2
+// takes the register kernels wherever they apply.
 bool regress_lane_applies(const Geom& g, int sel, bool adjoint) {
-  const bool want = g.regress_kernel == 2 || (g.regress_kernel == 0 && adjoint);
-  return want && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 && g.pmax + 1 <= 40;
+  (void)adjoint;
+  return g.regress_kernel == 2 && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 &&
+         g.pmax + 1 <= 40;
 }
 
 template <int NX>
