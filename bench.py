@@ -76,6 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--sample-subdomains", type=int, default=1)
     ap.add_argument("--sample-out", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--sample-steps", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--t127-only", action="store_true",
+                    help="only the T127-shaped scale line (mixed against plain FP32)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batch of 256 uneven problems (one CUDA graph per cycle)")
     ap.add_argument("--tune", action="store_true",
@@ -614,6 +616,73 @@ def side_measurements(args, w, inp, value, dev):
     return out
 
 
+T127_WORKLOAD = "t127_384x192x29_n96_r3"
+
+
+def t127_line(args, dev, steps=2):
+    """The T127-shaped scale case (384 x 192 x 29, n = 2,138,112, N = 96, r = 3,
+    ridge where p >= N - 1): one analysis cycle in the mixed-precision default
+    (FP32, the rows with 2p > N in double precision, double-precision blocks
+    where the single-precision factorisation fails or refines too slowly, four
+    refinement steps) against the plain FP32 form (ENKFMC_FLAG_PLAIN_FP32 with
+    no refinement), each with its accuracy against the FP64 oracle on sampled
+    rows and sub-domains (oracle values from the host cores)."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00807_gb300 import binding as B
+    from synthetic import WORKLOADS, make_inputs
+
+    w = WORKLOADS[T127_WORKLOAD]
+    inp = make_inputs(w, np.float32)
+    out = {"workload": w.name, "n": w.n, "N": w.N, "r": w.r}
+    ref = tempfile.mktemp(suffix=".npz")
+    ncores = args.cpu_workers or os.cpu_count() or 1
+    out["oracle_reference"] = run_cpu_sample(w.name, "fp32", 60, 1, ncores, ref)
+    forms = (("mixed", 0), ("plain_fp32", B.FLAG_PLAIN_FP32 | B.FLAG_NO_SOLVE_REFINEMENT))
+    for key, flags in forms:
+        stream = torch.cuda.Stream(device=dev)
+        res = {"flags": flags}
+        h = None
+        try:
+            h = B.Handle.from_workload(w, precision=B.FP32, stream=stream.cuda_stream,
+                                       flags=flags)
+            h.set_observations(inp.obs_idx)
+            put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+            Xb, y, R, Z = put(inp.Xb), put(inp.y), put(inp.R), put(inp.Z)
+            T = torch.empty((w.n, h.info.pmax), device=dev)
+            D = torch.empty(w.n, device=dev)
+            Xa = torch.empty_like(Xb)
+
+            def cycle():
+                h.estimate(Xb, T, D)
+                h.assemble(Xb, T, D, R)
+                h.analyze(Xb, y, R, Z, Xa)
+
+            ms = _time_steps(cycle, 1, steps, stream)
+            code, info = h.get_status()
+            res.update({"cycles_per_s": 1e3 / ms, "ms_per_cycle": ms,
+                        "status": B.STATUS.get(code, code), "status_info": info,
+                        "fp64_rows": bool(h.info.fp64_rows), "refine_steps": h.info.refine_steps,
+                        "fp64_blocks": h.fp64_blocks(), "blocks": h.info.nblock,
+                        "workspace_gb": h.info.workspace_bytes / 1e9})
+            if os.path.exists(ref):
+                res["accuracy"] = accuracy_report(w, ref, inp.Xb, T.cpu().numpy(),
+                                                  D.cpu().numpy(), Xa.cpu().numpy(), h)
+        except Exception as exc:  # report the failure of one form, keep the other
+            res["error"] = f"{type(exc).__name__}: {exc}"
+        finally:
+            if h is not None:
+                h.close()
+        out[key] = res
+    if os.path.exists(ref):
+        os.unlink(ref)
+    a, b = out.get("mixed", {}), out.get("plain_fp32", {})
+    if "cycles_per_s" in a and "cycles_per_s" in b:
+        out["mixed_over_plain"] = a["cycles_per_s"] / b["cycles_per_s"]
+    return out
+
+
 def cycling_line(w, dev, M=12, shift=1):
     """Filter cycling (Algorithm 1) on workload w in FP32: M assimilation times,
     the forecast operator advecting every field by `shift` cells per step, the
@@ -917,6 +986,11 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    if args.t127_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"t127": t127_line(args, torch.device("cuda", 0))}))
+        return
     if args.batch_only:
         import torch
         torch.cuda.set_device(0)

@@ -87,6 +87,16 @@ enum {
                                           solve, 1-15; 0 = one step, or four when
                                           some row has 2p > N (ill-conditioned A);
                                           the reverse pass refines its solve alike */
+  ENKFMC_FLAG_PLAIN_FP32 = 4,          /* FP32: the plain single-precision form of the
+                                          statistics and factorisations: every row
+                                          regressed in single precision (also where
+                                          2p > N) and no double-precision blocks (a
+                                          block whose single-precision factorisation
+                                          meets a non-positive pivot reports
+                                          ENKFMC_ENOTSPD); with
+                                          ENKFMC_FLAG_NO_SOLVE_REFINEMENT the whole
+                                          path is plain FP32.  For comparison with
+                                          the mixed-precision default              */
   ENKFMC_FLAG_SIMT_BAND = 2            /* FP32: take the band Cholesky and the band
                                           solves on the CUDA cores only.  By
                                           default their rank-32 panel updates run

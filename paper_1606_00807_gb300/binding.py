@@ -81,6 +81,7 @@ SIGNATURES = {
 NKERNEL = 15
 FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
+FLAG_PLAIN_FP32 = 4
 FLAG_REFINE_MASK = 0xF00
 TUNE_REGRESS_CTAS_PER_SM = 0
 TUNE_REGRESS_KERNEL = 1

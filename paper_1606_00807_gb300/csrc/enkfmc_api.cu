@@ -115,6 +115,7 @@ enkfmc_status problem_geom(const enkfmc_problem& p, Geom& g) {
   g.sm_count = 0;  // filled where a device is at hand
   g.regress_cap = 0;
   g.regress_kernel = 0;
+  g.plain_fp32 = (p.flags & ENKFMC_FLAG_PLAIN_FP32) ? 1 : 0;
   return ENKFMC_OK;
 }
 
@@ -125,7 +126,7 @@ namespace {
 enkfmc_status build(enkfmc_handle* h) {
   const enkfmc_problem& p = h->prob;
   if (p.flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_BAND |
-                  ENKFMC_FLAG_REFINE_MASK))
+                  ENKFMC_FLAG_PLAIN_FP32 | ENKFMC_FLAG_REFINE_MASK))
     return ENKFMC_EINVAL;
   Geom& g = h->g;
   enkfmc_status gst = problem_geom(p, g);
@@ -314,7 +315,9 @@ enkfmc_status build(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_rhs, h->esize * h->ext_rows * g.N))) return st;
   if ((st = dalloc(h, &h->d_C, h->esize * (size_t)g.n * cov_offset_count(g.r, g.vr)))) return st;
   if (!is_fp64(h)) {  // double-precision pool for blocks whose FP32 factorisation fails
-    h->fb_cap = h->nblock;  // room for every block: ill-conditioned problems can need most
+    // room for every block: ill-conditioned problems can need most (none in the
+    // plain form)
+    h->fb_cap = g.plain_fp32 ? 1 : h->nblock;
     h->fb_stride = (int64_t)h->nb_max * (h->hb_max + 1);
     if ((st = dalloc(h, &h->d_bfail, sizeof(int32_t) * h->nblock))) return st;
     if ((st = dalloc(h, &h->d_c1max, sizeof(float) * h->nblock))) return st;
@@ -488,6 +491,12 @@ constexpr float kRefineTolerance = 1e-6f;
 // single-precision T, D and R in double, then factored in double.
 enkfmc_status fp64_pool(enkfmc_handle* h, const float* Tv, const float* D, const float* R,
                         int append) {
+  if (h->g.plain_fp32) {  // no double-precision blocks: a failed block is reported
+    return timed(h, ENKFMC_K_FP64_BLOCKS, [&]() {
+      return launch_fallback_list(h->d_blocks, h->nblock, h->d_bfail, h->d_fb_blocks,
+                                  h->d_fb_cnt, 0, h->fb_stride, h->d_status, append, h->stream);
+    });
+  }
   return timed(h, ENKFMC_K_FP64_BLOCKS, [&](int* nk) {
     *nk += 3;
     int* rng = h->d_fb_cnt + (append ? 6 : 2);  // {lo, hi} of the blocks to (re)factor
@@ -594,7 +603,7 @@ enkfmc_status run_analyze(enkfmc_handle* h, const T* Xb, const T* y, const T* R,
   if (h->refine_solve && sizeof(T) == sizeof(float)) {
     // with three or more steps, blocks whose corrections shrink too slowly
     // after two steps join the double-precision pool for the third
-    const bool check = h->refine_steps >= 3;
+    const bool check = h->refine_steps >= 3 && !h->g.plain_fp32;
     for (int step = 0; step < h->refine_steps; ++step) {
       st = timed(h, ENKFMC_K_RESIDUAL, [&](int* nk) {
         cudaError_t e = cudaSuccess;
@@ -839,7 +848,7 @@ const char* enkfmc_strerror(enkfmc_status s) {
 enkfmc_status enkfmc_check_problem(const enkfmc_problem* p) {
   if (!p) return ENKFMC_EINVAL;
   if (p->flags & ~(ENKFMC_FLAG_NO_SOLVE_REFINEMENT | ENKFMC_FLAG_SIMT_BAND |
-                   ENKFMC_FLAG_REFINE_MASK))
+                   ENKFMC_FLAG_PLAIN_FP32 | ENKFMC_FLAG_REFINE_MASK))
     return ENKFMC_EINVAL;
   Geom g;
   return problem_geom(*p, g);

@@ -1949,7 +1949,9 @@ bool regress_shape(const Geom& g, size_t esize, bool reg, RegShape& rs) {
 
 }  // namespace
 
-bool has_fp64_rows(const Geom& g, bool single) { return single && 2 * g.pmax > g.N; }
+bool has_fp64_rows(const Geom& g, bool single) {
+  return single && !g.plain_fp32 && 2 * g.pmax > g.N;
+}
 
 bool estimate_supported(const Geom& g, bool single) {
   // 8-bit row indices in the gather tables, 15-bit table columns, members in

@@ -121,3 +121,5 @@ def test_check_problem_without_device(lib):
                 w.with_(r=17)):
         assert B.check_problem(bad) == 1
     assert B.check_problem(w, flags=1 << 20) == 1
+    assert B.check_problem(w, flags=B.FLAG_PLAIN_FP32 | B.FLAG_NO_SOLVE_REFINEMENT) == 0
+    assert B.check_problem(w, flags=8) == 1

@@ -96,6 +96,28 @@ def test_register_and_tiled_regressions_parity(name, kernel):
     _parity(name, 1, tuning={B.TUNE_REGRESS_KERNEL: kernel})
 
 
+def test_plain_fp32_form_parity():
+    """ENKFMC_FLAG_PLAIN_FP32 with no refinement (the plain single-precision form)
+    on the T63 statistics, where no row has 2p > N and no block needs double
+    precision: element by element against the oracle at the FP32 tolerance."""
+    from paper_1606_00807_gb300 import binding as B
+    assert _parity("small_48x26x3x1+1_n80_r2", 1,
+                   flags=B.FLAG_PLAIN_FP32 | B.FLAG_NO_SOLVE_REFINEMENT) == 0
+
+
+def test_plain_fp32_form_has_no_double_precision_rows():
+    """N = 16, r = 1 (p > N / 2 on most rows): the default regresses those rows in
+    double precision; the plain form regresses every row in single precision."""
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["small_28x20x3x1_n16_r1"]
+    for flags, want in ((0, 1), (B.FLAG_PLAIN_FP32, 0)):
+        h = B.Handle.from_workload(w, precision=B.FP32, flags=flags)
+        try:
+            assert h.info.fp64_rows == want, flags
+        finally:
+            h.close()
+
+
 def test_plain_fp32_solve_without_refinement():
     """The single-precision solve without its refinement step (the plain FP32 form)
     on the T63 statistics, where the sub-domain blocks are well conditioned."""
