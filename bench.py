@@ -610,10 +610,52 @@ def side_measurements(args, w, inp, value, dev):
                                                        dev, np.float64, B.FP64, torch.float64))
     guarded("batch", lambda: batch_line(args, dev))
     guarded("cycling", lambda: cycling_line(w, dev))
+    guarded("accuracy_study", lambda: accuracy_study_line(dev))
     a, b = out.get("fwd_adj", {}), out.get("fwd_adj_plain_fp64", {})
     if "fwd_adj_cycles_per_s" in a and "fwd_adj_cycles_per_s" in b:
         a["fp32_over_fp64"] = a["fwd_adj_cycles_per_s"] / b["fwd_adj_cycles_per_s"]
     return out
+
+
+def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 24)):
+    """Eq. 18's RMSE over M filter cycles (FP32, enkfmc_filter_run) on one set of
+    synthetic inputs for each localisation radius r and sub-domain tile (square,
+    in grid cells), the shape of the paper's radius and processor-count studies;
+    with the RMSE of the unassimilated background."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00807_gb300 import binding as B
+    from synthetic import WORKLOADS, make_cycle_inputs
+
+    base = WORKLOADS["study_96x48x3x2+1_n40"]
+    ci = make_cycle_inputs(base, M, shift, np.float32)  # r and the tile change no input
+    put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ys, Zs, R, xr = put(ci.ys), put(ci.Zs), put(ci.R), put(ci.truths)
+    rows = []
+    for r in radii:
+        for tile in tiles:
+            w = base.with_(r=r, sub_lon=tile, sub_lat=tile)
+            h = B.Handle.from_workload(w, precision=B.FP32)
+            try:
+                h.set_observations(ci.obs_idx)
+                Xb = put(ci.Xb0)
+                T = torch.empty((w.n, h.info.pmax), device=dev)
+                D = torch.empty(w.n, device=dev)
+                Xa = torch.empty_like(Xb)
+                sq = torch.zeros(M, dtype=torch.float64, device=dev)
+                h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq)
+                code, _ = h.get_status()
+                s = sq.cpu().numpy()
+                rows.append({"r": r, "tile": tile, "subdomains": h.info.nsub,
+                             "rmse_eq18": float(np.sqrt(s.sum() / M)),
+                             "rmse_last_per_component": float(np.sqrt(s[-1] / w.n)),
+                             "status": B.STATUS.get(code, code)})
+            finally:
+                h.close()
+    e_b = ci.Xb0.astype(np.float64).mean(axis=0) - ci.truths[0].astype(np.float64)
+    return {"workload": base.name, "assimilation_times": M, "precision": "fp32",
+            "rmse_background": float(np.sqrt(e_b @ e_b)), "runs": rows}
 
 
 T127_WORKLOAD = "t127_384x192x29_n96_r3"

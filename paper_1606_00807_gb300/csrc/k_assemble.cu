@@ -351,8 +351,11 @@ cudaError_t launch_assemble(const Geom& g, const Block* blocks, int nblock, int 
   return cudaGetLastError();
 }
 
+// 32 columns per tile in both precisions: at the T63 shape (hb = 290) a tile's
+// shared memory (pair list, output tile, staged rows) stays near 104 KB, so two
+// CTAs share an SM and one's staging overlaps the other's sums.
 template <typename T>
-constexpr int asm_halves() { return sizeof(T) == sizeof(float) ? 2 : 1; }
+constexpr int asm_halves() { return 1; }
 
 size_t assemble_pairs_smem(size_t esize, int pmax, int hb_max, int r, int npair_max,
                            int box_sum) {

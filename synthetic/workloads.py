@@ -118,7 +118,15 @@ SMALL_2D_R3 = Workload(
     r=3, N=64, sub_lon=12, sub_lat=12, sigma2=(1.0, 1e2), corr_len=3.0,
     obs="random", obs_frac=0.5, r_frac=0.01, seed=7400)
 
-WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96,
+# Accuracy study (radius and tile size against the analysis RMSE of Eq. 18 over
+# filter cycles): a 96 x 48 grid, 3 levels of two 3-D variables and one 2-D
+# variable, N = 40; the study varies r and the tile.
+STUDY = Workload(
+    name="study_96x48x3x2+1_n40", nlon=96, nlat=48, nlev=3, nvar_3d=2, nvar_2d=1,
+    r=2, N=40, sub_lon=12, sub_lat=12, sigma2=(4.0, 1.0, 1e2), corr_len=4.0, rho_vert=0.5,
+    obs="random", obs_frac=0.5, r_frac=0.01, seed=7500)
+
+WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96, STUDY,
                                  SMALL_3D, SMALL_ILL, SMALL_R1, SMALL_R1_N16, SMALL_RIDGE,
                                  SMALL_T63, SMALL_T63_N120, SMALL_2D_R3)}
 
