@@ -432,8 +432,36 @@ __device__ __forceinline__ void sqrt_and_inv(double x, double& s, double& inv) {
   inv = 1.0 / s;
 }
 
+// Element (r, c) of a warp's lower-triangular matrix (c <= r, or inside the
+// diagonal 4 x 4 tile).  Single precision: row-major with row stride ld (4 mod
+// 8: the 16-byte row reads of 8 consecutive lanes hit distinct banks).  Double
+// precision: packed 4 x 4 tiles, tile (I, J), J <= I, at (I (I + 1) / 2 + J) * 18
+// (18 doubles: the tiles of 8 consecutive lanes start in distinct 16-byte
+// bank groups), about half the shared memory of the row-major square for the
+// large stencils, so more warps share an SM's double-precision pipes.
+template <typename T>
+struct Addr;
+template <>
+struct Addr<float> {
+  int ld;
+  __device__ __forceinline__ int operator()(int r, int c) const { return r * ld + c; }
+};
+template <>
+struct Addr<double> {
+  int ld;  // unused
+  __device__ __forceinline__ int operator()(int r, int c) const {
+    const int I = r >> 2;
+    return (I * (I + 1) / 2 + (c >> 2)) * 18 + ((r & 3) << 2) + (c & 3);
+  }
+};
+// Elements of the matrix storage for ldp rows (a multiple of 4) and row stride ldg.
+__host__ __device__ inline int64_t addr_elems(size_t esize, int ldp, int ldg) {
+  const int nt = ldp / 4;
+  return esize == 4 ? (int64_t)ldp * ldg : (int64_t)nt * (nt + 1) / 2 * 18;
+}
+
 // Right-looking Cholesky, in 4 x 4 tiles, of the leading nrows x nrows block
-// of the warp's lower-triangular matrix L (row stride ldg, a multiple of 4),
+// of the warp's lower-triangular matrix L (addressed by at),
 // rows padded with identity rows up to a multiple of 4.  Pivots are taken for
 // the first npiv columns only (npiv = nrows - 1 leaves the last row as
 // L^-1 times itself: the solve of an augmented system).  Step K: lane 0
@@ -443,13 +471,13 @@ __device__ __forceinline__ void sqrt_and_inv(double x, double& s, double& inv) {
 // u < npiv; *code (a slot not among those) carries the error code between
 // lanes.  Returns 0 or ENKFMC_EDNONPOS / ENKFMC_ENONFINITE (same in every lane).
 template <typename T>
-__device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int npiv, int lane,
+__device__ int tiled_cholesky(T* L, const Addr<T> at, T* invd, T* code, int nrows, int npiv, int lane,
                               const uint16_t* tri = nullptr) {
   const int p1 = nrows, p = npiv;
   const int P4 = (p1 + 3) & ~3;
   for (int i = p1 + lane; i < P4; i += 32) {
-    for (int l = 0; l < i; ++l) L[i * ldg + l] = T(0);
-    L[i * ldg + i] = T(1);
+    for (int l = 0; l < i; ++l) L[at(i, l)] = T(0);
+    L[at(i, i)] = T(1);
   }
   __syncwarp();
   const int nt = P4 >> 2;
@@ -459,7 +487,7 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
     if (lane == 0) {
       T a[4][4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) lds4v(L + (k0 + r) * ldg + k0, a[r]);
+      for (int r = 0; r < 4; ++r) lds4v(L + at(k0 + r, k0), a[r]);
       int e = 0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -485,7 +513,7 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
           for (int q2 = c + 1; q2 <= r; ++q2) a[r][q2] = fma(-a[r][c], a[q2][c], a[r][q2]);
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) sts4v(L + (k0 + r) * ldg + k0, a[r]);
+      for (int r = 0; r < 4; ++r) sts4v(L + at(k0 + r, k0), a[r]);
       *code = T(e);  // error code of this step (uniform read below)
     }
     __syncwarp();
@@ -502,14 +530,14 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
       T lk[4][4], iv[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        lds4v(L + (k0 + r) * ldg + k0, lk[r]);
+        lds4v(L + at(k0 + r, k0), lk[r]);
         iv[r] = (k0 + r < p) ? invd[k0 + r] : T(1);
       }
       const int i0 = k0 + 4 * (lane + 1);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         T xr[4];
-        lds4v(L + (i0 + r) * ldg + k0, xr);
+        lds4v(L + at(i0 + r, k0), xr);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           T acc = xr[c];
@@ -517,7 +545,7 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
           for (int t = 0; t < c; ++t) acc = fma(-lk[c][t], xr[t], acc);
           xr[c] = acc * iv[c];
         }
-        sts4v(L + (i0 + r) * ldg + k0, xr);
+        sts4v(L + at(i0 + r, k0), xr);
       }
     }
     __syncwarp();
@@ -539,9 +567,9 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
       T li[4][4], lj[4][4], acc[4][4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        lds4v(L + (i0 + r) * ldg + k0, li[r]);
-        lds4v(L + (j0 + r) * ldg + k0, lj[r]);
-        lds4v(L + (i0 + r) * ldg + j0, acc[r]);
+        lds4v(L + at(i0 + r, k0), li[r]);
+        lds4v(L + at(j0 + r, k0), lj[r]);
+        lds4v(L + at(i0 + r, j0), acc[r]);
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -550,7 +578,7 @@ __device__ int tiled_cholesky(T* L, int ldg, T* invd, T* code, int nrows, int np
 #pragma unroll
           for (int t = 0; t < 4; ++t) acc[r][c] = fma(-li[r][t], lj[c][t], acc[r][c]);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) sts4v(L + (i0 + r) * ldg + j0, acc[r]);
+      for (int r = 0; r < 4; ++r) sts4v(L + at(i0 + r, j0), acc[r]);
     }
     __syncwarp();
   }
@@ -589,7 +617,7 @@ __host__ __device__ inline int gather_table_bytes(int pmax) {
 // the diagonal tile, then the lanes update the unknowns below it, one 16-byte
 // read of L per row.
 template <typename T>
-__device__ void tiled_forward(const T* L, int ldg, const T* invd, T* v, int n, int lane) {
+__device__ void tiled_forward(const T* L, const Addr<T> at, const T* invd, T* v, int n, int lane) {
   const int nt = (n + 3) >> 2;
   for (int K = 0; K < nt; ++K) {
     const int k0 = 4 * K;
@@ -599,7 +627,7 @@ __device__ void tiled_forward(const T* L, int ldg, const T* invd, T* v, int n, i
       for (int c = 0; c < 4; ++c) {
         T acc = k0 + c < n ? v[k0 + c] : T(0);
 #pragma unroll
-        for (int t = 0; t < c; ++t) acc = fma(-L[(k0 + c) * ldg + k0 + t], x[t], acc);
+        for (int t = 0; t < c; ++t) acc = fma(-L[at(k0 + c, k0 + t)], x[t], acc);
         x[c] = k0 + c < n ? acc * invd[k0 + c] : T(0);
       }
 #pragma unroll
@@ -610,7 +638,7 @@ __device__ void tiled_forward(const T* L, int ldg, const T* invd, T* v, int n, i
     lds4v(v + k0, x4);
     for (int i = k0 + 4 + lane; i < n; i += 32) {
       T l4[4];
-      lds4v(L + i * ldg + k0, l4);
+      lds4v(L + at(i, k0), l4);
       T acc = v[i];
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc = fma(-l4[c], x4[c], acc);
@@ -622,7 +650,7 @@ __device__ void tiled_forward(const T* L, int ldg, const T* invd, T* v, int n, i
 
 // v := L^-T v for the first n unknowns (same storage as tiled_forward).
 template <typename T>
-__device__ void tiled_backward(const T* L, int ldg, const T* invd, T* v, int n, int lane) {
+__device__ void tiled_backward(const T* L, const Addr<T> at, const T* invd, T* v, int n, int lane) {
   const int nt = (n + 3) >> 2;
   for (int K = nt - 1; K >= 0; --K) {
     const int k0 = 4 * K;
@@ -632,7 +660,7 @@ __device__ void tiled_backward(const T* L, int ldg, const T* invd, T* v, int n, 
       for (int c = 3; c >= 0; --c) {
         T acc = k0 + c < n ? v[k0 + c] : T(0);
 #pragma unroll
-        for (int t = c + 1; t < 4; ++t) acc = fma(-L[(k0 + t) * ldg + k0 + c], x[t], acc);
+        for (int t = c + 1; t < 4; ++t) acc = fma(-L[at(k0 + t, k0 + c)], x[t], acc);
         x[c] = k0 + c < n ? acc * invd[k0 + c] : T(0);
       }
 #pragma unroll
@@ -644,7 +672,7 @@ __device__ void tiled_backward(const T* L, int ldg, const T* invd, T* v, int n, 
     for (int j = lane; j < k0; j += 32) {
       T acc = v[j];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fma(-L[(k0 + c) * ldg + j], x4[c], acc);
+      for (int c = 0; c < 4; ++c) acc = fma(-L[at(k0 + c, j)], x4[c], acc);
       v[j] = acc;
     }
     __syncwarp();
@@ -696,8 +724,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
   int* q = reinterpret_cast<int*>(base);   // [ldp] component labels (q[p] = j)
   int* sl = q + ldp;                        // [ldp] slot of compacted entry (-1 = j)
   int* sidx = sl + ldp;                     // [ldp] compacted index of slot s
-  T* L = reinterpret_cast<T*>(sidx + ldp);  // [ldp][ldg]
-  T* va = L + (size_t)ldp * ldg;            // [ldp]
+  T* L = reinterpret_cast<T*>(sidx + ldp);  // the Gram matrix, then its factor (Addr<T>)
+  const Addr<T> at{ldg};
+  T* va = L + addr_elems(sizeof(T), ldp, ldg);  // [ldp]
   T* vb = va + ldp;                         // [ldp]
   T* gv = vb + ldp;                         // [ldp]
   T* invd = gv + ldp;                       // [ldp]
@@ -765,7 +794,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
       for (int pi = lane; pi < npair; pi += 32) {
         const int2 e = ptab[pi];
         const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
-        L[i * ldg + l] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
+        L[at(i, l)] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
       }
     } else
 #pragma unroll 4
@@ -776,34 +805,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
       si = si < 0 ? pmax : si;  // the row itself
       sm = sm < 0 ? pmax : sm;
       const uint32_t e = ftab[si * (si + 1) / 2 + sm];
-      L[i * ldg + l] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
+      L[at(i, l)] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
     }
     __syncwarp();
     T lam = T(0);
     if (p > 0 && ridge_c > 0.0 && p >= N - 1) {
       T tr = 0;
-      for (int i = lane; i < p; i += 32) tr += L[i * ldg + i];
+      for (int i = lane; i < p; i += 32) tr += L[at(i, i)];
       tr = warp_sum(tr);
       lam = T(ridge_c) * tr / T(p);
     }
     for (int i = lane; i < p; i += 32) {
-      gv[i] = L[p * ldg + i];
-      L[i * ldg + i] += lam;
+      gv[i] = L[at(p, i)];
+      L[at(i, i)] += lam;
     }
     __syncwarp();
 
     // right-looking tiled Cholesky; pivots for the first p columns, so row p
     // becomes w = L^-1 g
     // (the trailing tiles of a step number at most nfull, the size of tri)
-    const int err0 = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p1, p, lane, tri);
+    const int err0 = tiled_cholesky(L, at, invd, invd + (ldp - 1), p1, p, lane, tri);
     int err = err0;
 
     T Dj = T(0);
     if (!err) {
       // beta = L^-T w  (w = row p of L), result in vb
-      for (int i = lane; i < p; i += 32) va[i] = L[p * ldg + i];
+      for (int i = lane; i < p; i += 32) va[i] = L[at(p, i)];
       __syncwarp();
-      tiled_backward(L, ldg, invd, va, p, lane);
+      tiled_backward(L, at, invd, va, p, lane);
       for (int i = lane; i < p; i += 32) vb[i] = va[i];
       __syncwarp();
       if constexpr (sizeof(T) == 4) {
@@ -863,11 +892,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
         // c (the residual) is kept in gv for D below
         for (int i = lane; i < p; i += 32) gv[i] = va[i];
         // solve L z = c (forward), then L^T delta = z (backward), in va
-        tiled_forward(L, ldg, invd, va, p, lane);
+        tiled_forward(L, at, invd, va, p, lane);
         float zz = 0.f;  // |z|^2 = delta^T (G + lambda I) delta
         for (int i = lane; i < p; i += 32) zz = fmaf((float)va[i], (float)va[i], zz);
         zz = warp_sum(zz);
-        tiled_backward(L, ldg, invd, va, p, lane);
+        tiled_backward(L, at, invd, va, p, lane);
         // D from the refined residual e' = e - U_P^T delta without reading U:
         //   |e'|^2 = |e|^2 - 2 delta.(U_P e) + delta^T G delta,
         //   U_P e = c + lambda beta,  delta^T G delta = |z|^2 - lambda |delta|^2;
@@ -1650,8 +1679,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
   int* q = reinterpret_cast<int*>(base);    // [ldp] labels (q[p] = j)
   int* sl = q + ldp;                         // [ldp] slots
   int* qr = sl + ldp;                        // [ldp] extended rows (block-relative)
-  T* L = reinterpret_cast<T*>(qr + ldp);     // [ldp][ldg]
-  T* va = L + (size_t)ldp * ldg;             // [ldp] betabar -> v
+  T* L = reinterpret_cast<T*>(qr + ldp);     // the Gram matrix, then its factor (Addr<T>)
+  const Addr<T> at{ldg};
+  T* va = L + addr_elems(sizeof(T), ldp, ldg);  // [ldp] betabar -> v
   T* vb = va + ldp;                          // [ldp] beta
   T* invd = vb + ldp;                        // [ldp]
   const int N = g.N, ldN = g.ldN;
@@ -1765,7 +1795,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       for (int pi = lane; pi < npair; pi += 32) {
         const int2 e = ptab[pi];
         const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
-        L[i * ldg + l] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
+        L[at(i, l)] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
       }
     } else if (gtab) {  // any other row: the handle's gather tables, through the slots
       // The ballot compaction above keeps the slots in increasing order, so
@@ -1780,7 +1810,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
         if (sm > si && status) record_error(status, ENKFMC_EINVAL, rowj);
 #endif
         const uint32_t e = gtab[nfull + si * (si + 1) / 2 + sm];
-        L[i * ldg + l] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
+        L[at(i, l)] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
       }
     } else
     for (int pi = lane; pi < npair; pi += 32) {
@@ -1792,16 +1822,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       const int dk = off[sm] - off[si];
       const int dy = off[pmax + sm] - off[pmax + si];
       const int dx = off[2 * pmax + sm] - off[2 * pmax + si];
-      L[i * ldg + l] = cov_lookup(C, nH, g.r, g.vr, q[i], q[l], dk, dy, dx);
+      L[at(i, l)] = cov_lookup(C, nH, g.r, g.vr, q[i], q[l], dk, dy, dx);
     }
     __syncwarp();
     if (ridge_c > 0.0 && p >= N - 1) {
       T tr = 0;
-      for (int i = lane; i < p; i += 32) tr += L[i * ldg + i];
+      for (int i = lane; i < p; i += 32) tr += L[at(i, i)];
       tr = warp_sum(tr);
       lam = T(ridge_c) * tr / T(p);
       __syncwarp();
-      for (int i = lane; i < p; i += 32) L[i * ldg + i] += lam;
+      for (int i = lane; i < p; i += 32) L[at(i, i)] += lam;
     }
     __syncwarp();
   }
@@ -1830,7 +1860,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
   for (int a = 0; a < 4; ++a) f[a] = eb[a];
   T kappa = 0;
   if (p > 0) {
-    const int err = tiled_cholesky(L, ldg, invd, invd + (ldp - 1), p, p, lane, gtab);
+    const int err = tiled_cholesky(L, at, invd, invd + (ldp - 1), p, p, lane, gtab);
     if (err) {
       if (lane == 0) record_error(status, err, rowj);
       const T z4[4] = {T(0), T(0), T(0), T(0)};
@@ -1838,8 +1868,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
       return;
     }
     // v = (L L^T)^-1 betabar in va
-    tiled_forward(L, ldg, invd, va, p, lane);
-    tiled_backward(L, ldg, invd, va, p, lane);
+    tiled_forward(L, at, invd, va, p, lane);
+    tiled_backward(L, at, invd, va, p, lane);
     // f = ebar + U_P^T v; kappa
     T vbeta = 0;
     for (int i = lane; i < p; i += 32) vbeta = fma(va[i], vb[i], vbeta);
@@ -1921,19 +1951,27 @@ struct RegShape {
 
 bool regress_shape(const Geom& g, size_t esize, bool reg, RegShape& rs) {
   rs.ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  // row stride = 4 (mod 8): 16-byte row reads of 8 consecutive lanes are conflict free
+  // single precision: row stride = 4 (mod 8), so that 16-byte row reads of 8
+  // consecutive lanes are conflict free; double precision: packed tiles (Addr)
   rs.ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
   size_t wb = (size_t)rs.ldp * 3 * sizeof(int) +
-              esize * ((size_t)rs.ldp * rs.ldg + (reg ? 4 : 3) * (size_t)rs.ldp);
+              esize * ((size_t)addr_elems(esize, rs.ldp, rs.ldg) + (reg ? 4 : 3) * (size_t)rs.ldp);
   rs.wb = (wb + 15) / 16 * 16;
-  for (int ptab = reg ? 1 : 0; ptab >= 0; --ptab) {  // without the pair table if need be
+  // single precision: up to 96 KB per CTA (three CTAs of eight warps per SM),
+  // with the typical row's pair table if it fits; double precision: one CTA of
+  // up to eight warps per SM in up to 220 KB, without the pair table (the
+  // double-precision pipes, not the gather, bound those rows: more warps share
+  // them)
+  const bool single = esize == 4;
+  for (int ptab = reg && single ? 1 : 0; ptab >= 0; --ptab) {  // without the pair table if need be
     size_t offbytes = (3 * (size_t)g.pmax + 15) / 16 * 16;
     if (reg)
       offbytes += (ptab ? pair_table_bytes(g.pmax, g.r, g.periodic) : 0) +
                   gather_table_bytes(g.pmax);
-    int wpc = (int)(((size_t)96 * 1024 - std::min<size_t>(offbytes, 96 * 1024)) / rs.wb);
+    const size_t budget = (size_t)(single ? 96 : 220) * 1024;
+    int wpc = (int)((budget - std::min<size_t>(offbytes, budget)) / rs.wb);
     if (wpc > 8) wpc = 8;
-    if (wpc < 1) {
+    if (wpc < 1 && single) {
       wpc = (int)(((size_t)200 * 1024 - std::min<size_t>(offbytes, 200 * 1024)) / rs.wb);
       if (wpc > 8) wpc = 8;
     }
