@@ -617,7 +617,7 @@ def side_measurements(args, w, inp, value, dev):
     return out
 
 
-def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 24)):
+def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 16)):
     """Eq. 18's RMSE over M filter cycles (FP32, enkfmc_filter_run) on one set of
     synthetic inputs for each localisation radius r and sub-domain tile (square,
     in grid cells), the shape of the paper's radius and processor-count studies;

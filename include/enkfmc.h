@@ -157,11 +157,16 @@ typedef struct enkfmc_handle enkfmc_handle;
 /* Create a handle for one problem on the current CUDA device.  `cuda_stream`
  * is a cudaStream_t (NULL = legacy default stream).  Builds the geometry
  * tables and allocates the workspace.  Returns EINVAL for unsupported
- * geometry, ENOMEM when device memory runs out. */
+ * geometry, ENOMEM when device memory runs out.  Unsupported includes a band
+ * of A (half-width about the tile's extended area per level times the levels
+ * a row reaches) wider than the CUDA-core band kernels hold in shared memory:
+ * about 620 in double precision, which FP64 problems and the double-precision
+ * blocks of FP32 problems use, and 1,280 in single precision. */
 enkfmc_status enkfmc_create(enkfmc_handle** h, const enkfmc_problem* p, void* cuda_stream);
 void enkfmc_destroy(enkfmc_handle* h);
 /* Validate a problem description without a device: OK, or EINVAL where
- * enkfmc_create would refuse it as invalid or unsupported. */
+ * enkfmc_create would refuse it as invalid or unsupported (except the band
+ * width, which enkfmc_create checks once it has built the sub-domains). */
 enkfmc_status enkfmc_check_problem(const enkfmc_problem* p);
 const char* enkfmc_strerror(enkfmc_status s);
 enkfmc_status enkfmc_query(const enkfmc_handle* h, enkfmc_info* info /* host */);

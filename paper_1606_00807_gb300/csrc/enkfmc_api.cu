@@ -207,6 +207,13 @@ enkfmc_status build(enkfmc_handle* h) {
   h->ext_rows = row_off;
   h->band_elems = band_off;
   h->halo_rows = (int64_t)halo.size() / 2;
+  // the CUDA-core band kernels (FP64 problems, the single-precision path when
+  // the tensor-core kernels do not apply, and the double-precision pool of an
+  // FP32 problem) hold a panel and a window of the band in shared memory:
+  // refuse bands too wide for them
+  if (!band_kernels_fit(h->hb_max, h->esize)) return ENKFMC_EINVAL;
+  if (!is_fp64(h) && !g.plain_fp32 && !band_kernels_fit(h->hb_max, sizeof(double)))
+    return ENKFMC_EINVAL;
   h->tc_solve = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_SIMT_BAND) &&
                bandsolve_tc_supported(h->hb_max, p.N);
   h->tc_chol = !is_fp64(h) && !(p.flags & ENKFMC_FLAG_SIMT_BAND) &&

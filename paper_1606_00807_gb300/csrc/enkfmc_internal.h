@@ -485,6 +485,10 @@ cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nbloc
 // y += x over `count` elements.
 cudaError_t launch_accumulate(float* y, const float* x, int64_t count, cudaStream_t s);
 
+// True when the CUDA-core band Cholesky and solves (k_band.cu) can launch for
+// half-bandwidth hb with elements of esize bytes.
+bool band_kernels_fit(int hb, size_t esize);
+
 // filter cycling (k_cycle.cu): forecast operator and Eq. 18's squared error
 constexpr int kSqGrid = 1024;  // blocks of the squared-error reduction (fixed order)
 template <typename T>

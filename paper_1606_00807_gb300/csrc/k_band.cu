@@ -481,15 +481,31 @@ cudaError_t launch_bandsolve_nm(const Block* blocks, int nblock, int N, const T*
   return cudaGetLastError();
 }
 
+// Shared memory of the CUDA-core band kernels for a half-bandwidth hb and
+// elements of esize bytes (the launchers below size them the same way).
+constexpr size_t kBandSmemLimit = 227 * 1024;
+size_t bandchol_smem(int hb, size_t esize) {
+  const int ldP = (NB + hb + 1 + 3) / 4 * 4;
+  return esize * (size_t)NB * ldP;
+}
+size_t bandsolve_smem(int hb, size_t esize, int nmb) {
+  const int ldP = (NB + hb + 1 + 3) / 4 * 4;
+  const int WRmax = ((NB + hb + NB - 1) / NB) * NB;
+  return esize * ((size_t)NB * ldP + (size_t)WRmax * (nmb + 4) + 4 * (size_t)NB * nmb + NB);
+}
+
+bool band_kernels_fit(int hb, size_t esize) {
+  return bandchol_smem(hb, esize) <= kBandSmemLimit &&
+         bandsolve_smem(hb, esize, 8) <= kBandSmemLimit;
+}
+
 template <typename T, typename TR>
 cudaError_t launch_bandsolve(const Block* blocks, int nblock, int hb_max, int N, const T* band,
                              TR* rhs, cudaStream_t s, const int* pool, const int* skip) {
   const int ldP = (NB + hb_max + 1 + 3) / 4 * 4;
   const int WRmax = ((NB + hb_max + NB - 1) / NB) * NB;
-  auto bytes = [&](int nmb) {
-    return sizeof(T) * ((size_t)NB * ldP + (size_t)WRmax * (nmb + 4) + 4 * (size_t)NB * nmb + NB);
-  };
-  const size_t lim = 227 * 1024;
+  auto bytes = [&](int nmb) { return bandsolve_smem(hb_max, sizeof(T), nmb); };
+  const size_t lim = kBandSmemLimit;
   if (bytes(32) <= lim)
     return launch_bandsolve_nm<T, TR, 32>(blocks, nblock, N, band, rhs, s, bytes(32), ldP, WRmax,
                                           pool, skip);

@@ -300,3 +300,18 @@ def test_nonfinite_input_reports_status_not_trap():
     h.estimate(dev(make_inputs(w, np.float64).Xb), T, D)
     assert h.get_status()[0] == 0
     h.close()
+
+
+def test_band_too_wide_for_the_band_kernels_is_refused():
+    """A 24 x 24 tile with r = 3 on three levels gives a band about 990 wide,
+    beyond the double-precision band kernels' shared memory (the pool of an FP32
+    problem uses them): enkfmc_create refuses it with EINVAL instead of failing
+    at launch; the plain FP32 form (no double-precision blocks) is accepted."""
+    from paper_1606_00807_gb300 import binding as B
+    w = WORKLOADS["study_96x48x3x2+1_n40"].with_(r=3, sub_lon=24, sub_lat=24)
+    with pytest.raises(B.EnkfmcError) as ei:
+        B.Handle.from_workload(w, precision=B.FP32)
+    assert "EINVAL" in str(ei.value)
+    h = B.Handle.from_workload(w, precision=B.FP32, flags=B.FLAG_PLAIN_FP32)
+    assert h.info.hb_max > 900
+    h.close()
