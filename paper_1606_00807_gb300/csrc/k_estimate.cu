@@ -801,9 +801,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     for (int pi = lane; pi < npair; pi += 32) {
       const uint32_t il = tri[pi];
       const int i = il & 0xff, l = il >> 8;
+      // the ballot compaction keeps the slots rising with the compact index
+      // and the row itself (slot pmax) is last, so sm <= si whenever l <= i:
+      // (si, sm) is an entry of the lower-triangle slot-pair table
       int si = sl[i], sm = sl[l];
       si = si < 0 ? pmax : si;  // the row itself
       sm = sm < 0 ? pmax : sm;
+#ifdef ENKFMC_CHECK
+      if (sm > si && status) record_error(status, ENKFMC_EINVAL, orow);
+#endif
       const uint32_t e = ftab[si * (si + 1) / 2 + sm];
       L[at(i, l)] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
     }
