@@ -617,11 +617,11 @@ def side_measurements(args, w, inp, value, dev):
     return out
 
 
-def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 16)):
+def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 16), inflation=1.1):
     """Eq. 18's RMSE over M filter cycles (FP32, enkfmc_filter_run) on one set of
     synthetic inputs for each localisation radius r and sub-domain tile (square,
     in grid cells), the shape of the paper's radius and processor-count studies;
-    with the RMSE of the unassimilated background."""
+    with the RMSE of the unassimilated background; forecast inflation 1.1."""
     import numpy as np
     import torch
 
@@ -644,7 +644,7 @@ def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 16)):
                 D = torch.empty(w.n, device=dev)
                 Xa = torch.empty_like(Xb)
                 sq = torch.zeros(M, dtype=torch.float64, device=dev)
-                h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq)
+                h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq, inflation)
                 code, _ = h.get_status()
                 s = sq.cpu().numpy()
                 rows.append({"r": r, "tile": tile, "subdomains": h.info.nsub,
@@ -655,7 +655,7 @@ def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 16)):
                 h.close()
     e_b = ci.Xb0.astype(np.float64).mean(axis=0) - ci.truths[0].astype(np.float64)
     return {"workload": base.name, "assimilation_times": M, "precision": "fp32",
-            "rmse_background": float(np.sqrt(e_b @ e_b)), "runs": rows}
+            "inflation": inflation, "rmse_background": float(np.sqrt(e_b @ e_b)), "runs": rows}
 
 
 T127_WORKLOAD = "t127_384x192x29_n96_r3"
@@ -725,13 +725,14 @@ def t127_line(args, dev, steps=2):
     return out
 
 
-def cycling_line(w, dev, M=12, shift=1):
+def cycling_line(w, dev, M=12, shift=1, inflation=1.1):
     """Filter cycling (Algorithm 1) on workload w in FP32: M assimilation times,
     the forecast operator advecting every field by `shift` cells per step, the
     nature run advected the same way (perfect model), enkfmc_filter_run (cycle 0
     eager, then one captured CUDA graph per cycle); cycles/s over the whole call
     (capture included) and Eq. 18's RMSE, beside the RMSE of the initial
-    background mean (which the forecast alone would keep)."""
+    background mean.  The forecast inflates the ensemble about its mean by
+    `inflation` (the advection alone has no model error)."""
     import numpy as np
     import torch
 
@@ -751,14 +752,14 @@ def cycling_line(w, dev, M=12, shift=1):
         sq = torch.zeros(M, dtype=torch.float64, device=dev)
         Xb.copy_(Xb0)
         torch.cuda.synchronize()
-        h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq)  # set-up and warm-up
+        h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq, inflation)  # set-up and warm-up
         h.check("cycling warm-up")
         with torch.cuda.stream(stream):
             Xb.copy_(Xb0)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq)
+        h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq, inflation)
         e1.record(stream)
         torch.cuda.synchronize()
         h.check("cycling")
@@ -766,12 +767,12 @@ def cycling_line(w, dev, M=12, shift=1):
         s = sq.cpu().numpy()
         e_b = (ci.Xb0.astype(np.float64).mean(axis=0) - ci.truths[0].astype(np.float64))
         return {"workload": w.name, "precision": "fp32", "assimilation_times": M,
-                "shift_cells_per_step": shift, "value": M * 1e3 / ms, "unit": "cycles/s",
+                "shift_cells_per_step": shift, "inflation": inflation,
+                "value": M * 1e3 / ms, "unit": "cycles/s",
                 "ms_per_cycle": ms / M, "rmse_eq18": float(np.sqrt(s.sum() / M)),
                 "rmse_background": float(np.sqrt(e_b @ e_b)),
                 "rmse_per_time_per_component": [float(np.sqrt(x / w.n)) for x in s],
-                "note": "RMSE of Eq. 18 over the analysis-mean errors of the M times; the "
-                        "background's stays constant under the forecast (a permutation)"}
+                "note": "RMSE of Eq. 18 over the analysis-mean errors of the M times"}
     finally:
         h.close()
 

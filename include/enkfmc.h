@@ -234,17 +234,23 @@ enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
 /* Forecast operator: every field of nvec state vectors (device, member-major
  * [nvec][n], the handle's element type) moves `shift` cells eastward along its
  * latitude circle, periodic in longitude (advection of the random fields,
- * whose statistics it keeps).  X and Xout are distinct.  Any integer shift
- * (taken mod nlon).  Queued on the handle's stream. */
+ * whose statistics it keeps), with multiplicative covariance inflation about
+ * the mean of the nvec vectors: Xout = mean + inflation (X - mean), the mean
+ * in double precision (inflation 1: the exact permutation; in (0, 1000]).
+ * The paper's model has its own error growth; a permutation has none, so
+ * without inflation a cycled ensemble's spread only shrinks.  X and Xout are
+ * distinct.  Any integer shift (taken mod nlon).  Queued on the handle's
+ * stream. */
 enkfmc_status enkfmc_forecast_shift(enkfmc_handle* h, const void* X, void* Xout, int32_t nvec,
-                                    int32_t shift);
+                                    int32_t shift, double inflation);
 /* Summand of Eq. 18: *out (device double) = sum_l (mean_m Xa[m][l] - xref[l])^2
  * for Xa [N][n] and xref [n] (device, the handle's element type), the mean and
  * the sum in double precision in a fixed order (the same bits on every run).
  * Queued on the handle's stream. */
 enkfmc_status enkfmc_ensemble_sqerr(enkfmc_handle* h, const void* Xa, const void* xref,
                                     double* out);
-/* M cycles of Algorithm 1 with enkfmc_forecast_shift as the model: for k = 0..M-1,
+/* M cycles of Algorithm 1 with enkfmc_forecast_shift (shift, inflation) as the
+ * model: for k = 0..M-1,
  * the analysis (enkfmc_estimate, enkfmc_assemble, enkfmc_analyze) of Xb with
  * observations ys[k] ([M][m]) and perturbations Zs[k] ([M][N][m]) into Xa,
  * sqerr[k] = enkfmc_ensemble_sqerr(Xa, xrefs[k]) (xrefs [M][n], the reference
@@ -259,7 +265,8 @@ enkfmc_status enkfmc_ensemble_sqerr(enkfmc_handle* h, const void* Xa, const void
  * enkfmc_get_status. */
 enkfmc_status enkfmc_filter_run(enkfmc_handle* h, void* Xb, const void* ys, const void* Zs,
                                 const void* Rdiag, const void* xrefs, void* Tvals, void* D,
-                                void* Xa, int32_t M, int32_t shift, double* sqerr);
+                                void* Xa, int32_t M, int32_t shift, double inflation,
+                                double* sqerr);
 
 /* Reverse pass of the last analysis.  Given Xa_bar = dL/dX^a ([N][n]) of a
  * scalar loss L, writes dL/dy (y_bar, [m]), dL/d diag(R) (Rdiag_bar, [m]) and

@@ -6,7 +6,10 @@ every field moves `shift` cells eastward along its latitude circle per step
 (periodic longitude).  Eq. 18 measures the analysis accuracy over the M
 assimilation times: RMSE = sqrt( (1/M) sum_k |x_ref_k - x_a_k|^2 ), with x_a_k
 the analysis ensemble mean at time k (the reading taken: the paper's x^a_k is
-the analysis state, which for an ensemble filter is its mean).
+the analysis state, which for an ensemble filter is its mean).  The forecast
+may inflate the ensemble about its mean by a factor rho (multiplicative
+covariance inflation): the shift alone has no model error, so a cycled
+ensemble's spread would only shrink.
 """
 from __future__ import annotations
 
@@ -15,10 +18,14 @@ import numpy as np
 from .enkfmc import assimilate
 
 
-def forecast_shift(w, X_mm: np.ndarray, shift: int) -> np.ndarray:
+def forecast_shift(w, X_mm: np.ndarray, shift: int, inflation: float = 1.0) -> np.ndarray:
     """Member-major [nvec][n] states, each field advected by `shift` cells:
-    out[..., x] = in[..., x - shift] along longitude (periodic)."""
+    out[..., x] = in[..., x - shift] along longitude (periodic), after
+    X = mean + inflation (X - mean) about the mean of the nvec vectors."""
     X = np.asarray(X_mm, dtype=np.float64)
+    if inflation != 1.0:
+        mean = X.mean(axis=0)
+        X = mean + inflation * (X - mean)
     nvec = X.shape[0]
     planes = w.n // (w.nlat * w.nlon)
     out = np.empty_like(X)
@@ -43,7 +50,7 @@ def rmse_eq18(sqerrs) -> float:
     return float(np.sqrt(s.sum() / s.size))
 
 
-def filter_cycles(w, Xb0, ys, Zs, R, xrefs, obs_idx, shift):
+def filter_cycles(w, Xb0, ys, Zs, R, xrefs, obs_idx, shift, inflation=1.0):
     """M cycles of Algorithm 1: analysis of the background with y_k, Z_k, the
     squared error of its mean against x_ref_k, then the forecast of every
     member.  Returns (per-time squared errors [M], last analysis [N][n],
@@ -54,5 +61,5 @@ def filter_cycles(w, Xb0, ys, Zs, R, xrefs, obs_idx, shift):
     for k in range(len(xrefs)):
         Xa = assimilate(w, Xb, ys[k], R, Zs[k], obs_idx)
         sq.append(ensemble_sqerr(Xa, xrefs[k]))
-        Xb = forecast_shift(w, Xa, shift)
+        Xb = forecast_shift(w, Xa, shift, inflation)
     return np.array(sq), Xa, Xb

@@ -52,10 +52,11 @@ SIGNATURES = {
     "enkfmc_assemble": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_analyze": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_cycle_host": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
-    "enkfmc_forecast_shift": (c_int32, [_H, c_void_p, c_void_p, c_int32, c_int32]),
+    "enkfmc_forecast_shift": (c_int32, [_H, c_void_p, c_void_p, c_int32, c_int32, c_double]),
     "enkfmc_ensemble_sqerr": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
     "enkfmc_filter_run": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
-                                    c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_void_p]),
+                                    c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_double,
+                                    c_void_p]),
     "enkfmc_analyze_adjoint": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_get_status": (c_int32, [_H, POINTER(c_int64)]),
     "enkfmc_export_T_pattern": (c_int32, [_H, c_void_p, c_void_p]),
@@ -227,18 +228,19 @@ class Handle:
         _check(self.lib.enkfmc_cycle_host(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
                "enkfmc_cycle_host")
 
-    def forecast_shift(self, X, Xout, nvec: int, shift: int):
-        _check(self.lib.enkfmc_forecast_shift(self.h, _ptr(X), _ptr(Xout), nvec, shift),
-               "enkfmc_forecast_shift")
+    def forecast_shift(self, X, Xout, nvec: int, shift: int, inflation: float = 1.0):
+        _check(self.lib.enkfmc_forecast_shift(self.h, _ptr(X), _ptr(Xout), nvec, shift,
+                                              float(inflation)), "enkfmc_forecast_shift")
 
     def ensemble_sqerr(self, Xa, xref, out):
         _check(self.lib.enkfmc_ensemble_sqerr(self.h, _ptr(Xa), _ptr(xref), _ptr(out)),
                "enkfmc_ensemble_sqerr")
 
-    def filter_run(self, Xb, ys, Zs, R, xrefs, Tvals, D, Xa, M: int, shift: int, sqerr):
+    def filter_run(self, Xb, ys, Zs, R, xrefs, Tvals, D, Xa, M: int, shift: int, sqerr,
+                   inflation: float = 1.0):
         _check(self.lib.enkfmc_filter_run(self.h, _ptr(Xb), _ptr(ys), _ptr(Zs), _ptr(R),
                                           _ptr(xrefs), _ptr(Tvals), _ptr(D), _ptr(Xa), M, shift,
-                                          _ptr(sqerr)), "enkfmc_filter_run")
+                                          float(inflation), _ptr(sqerr)), "enkfmc_filter_run")
 
     def set_tuning(self, knob: int, value: int):
         _check(self.lib.enkfmc_set_tuning(self.h, knob, value), "enkfmc_set_tuning")

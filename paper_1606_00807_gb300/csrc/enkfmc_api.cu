@@ -1099,14 +1099,17 @@ enkfmc_status enkfmc_debug_block(enkfmc_handle* h, int32_t b, void* host, int64_
 }
 
 enkfmc_status enkfmc_forecast_shift(enkfmc_handle* h, const void* X, void* Xout, int32_t nvec,
-                                    int32_t shift) {
-  if (!h || !X || !Xout || X == Xout || nvec < 1) return ENKFMC_EINVAL;
+                                    int32_t shift, double inflation) {
+  if (!h || !X || !Xout || X == Xout || nvec < 1 || !(inflation > 0.0) || inflation > 1e3)
+    return ENKFMC_EINVAL;
   const int nl = h->g.nlon;
   const int s = ((shift % nl) + nl) % nl;
   return timed(h, ENKFMC_K_FORECAST, [&]() -> cudaError_t {
     if (is_fp64(h))
-      return launch_shift<double>(h->g, (const double*)X, (double*)Xout, nvec, s, h->stream);
-    return launch_shift<float>(h->g, (const float*)X, (float*)Xout, nvec, s, h->stream);
+      return launch_shift<double>(h->g, (const double*)X, (double*)Xout, nvec, s, inflation,
+                                  h->stream);
+    return launch_shift<float>(h->g, (const float*)X, (float*)Xout, nvec, s, inflation,
+                               h->stream);
   });
 }
 

@@ -22,12 +22,12 @@ enkfmc_status alloc_once(void** p, size_t bytes) {
 
 // One cycle on the handle's current stream from the fixed buffers.
 enkfmc_status one_cycle(enkfmc_handle* h, void* Xb, const void* R, void* Tv, void* D, void* Xa,
-                        int shift) {
+                        int shift, double inflation) {
   enkfmc_status st = enkfmc_estimate(h, Xb, Tv, D);
   if (!st) st = enkfmc_assemble(h, Xb, Tv, D, R);
   if (!st) st = enkfmc_analyze(h, Xb, h->d_fy, R, h->d_fZ, Xa);
   if (!st) st = enkfmc_ensemble_sqerr(h, Xa, h->d_fx, h->d_fsq);
-  if (!st) st = enkfmc_forecast_shift(h, Xa, Xb, h->g.N, shift);
+  if (!st) st = enkfmc_forecast_shift(h, Xa, Xb, h->g.N, shift, inflation);
   return st;
 }
 
@@ -36,8 +36,9 @@ enkfmc_status one_cycle(enkfmc_handle* h, void* Xb, const void* R, void* Tv, voi
 extern "C" enkfmc_status enkfmc_filter_run(enkfmc_handle* h, void* Xb, const void* ys,
                                            const void* Zs, const void* Rdiag, const void* xrefs,
                                            void* Tvals, void* D, void* Xa, int32_t M,
-                                           int32_t shift, double* sqerr) {
-  if (!h || !Xb || !xrefs || !Tvals || !D || !Xa || !sqerr || M < 1 || Xa == Xb)
+                                           int32_t shift, double inflation, double* sqerr) {
+  if (!h || !Xb || !xrefs || !Tvals || !D || !Xa || !sqerr || M < 1 || Xa == Xb ||
+      !(inflation > 0.0) || inflation > 1e3)
     return ENKFMC_EINVAL;
   enkfmc_info info;
   enkfmc_query(h, &info);
@@ -74,7 +75,7 @@ extern "C" enkfmc_status enkfmc_filter_run(enkfmc_handle* h, void* Xb, const voi
         cudaMemcpyAsync(sqerr + k, h->d_fsq, sizeof(double), cudaMemcpyDeviceToDevice, user));
   };
   st = stage(0);
-  if (!st) st = one_cycle(h, Xb, R, Tvals, D, Xa, shift);
+  if (!st) st = one_cycle(h, Xb, R, Tvals, D, Xa, shift, inflation);
   if (!st) st = read_sq(0);
   if (st || M == 1) return st;
 
@@ -87,7 +88,7 @@ extern "C" enkfmc_status enkfmc_filter_run(enkfmc_handle* h, void* Xb, const voi
   cudaGraph_t graph = nullptr;
   st = cuda_status(cudaStreamBeginCapture(h->f_stream, cudaStreamCaptureModeRelaxed));
   if (!st) {
-    const enkfmc_status sc = one_cycle(h, Xb, R, Tvals, D, Xa, shift);
+    const enkfmc_status sc = one_cycle(h, Xb, R, Tvals, D, Xa, shift, inflation);
     const cudaError_t e = cudaStreamEndCapture(h->f_stream, &graph);
     st = sc ? sc : cuda_status(e);
   }

@@ -492,7 +492,8 @@ bool band_kernels_fit(int hb, size_t esize);
 // filter cycling (k_cycle.cu): forecast operator and Eq. 18's squared error
 constexpr int kSqGrid = 1024;  // blocks of the squared-error reduction (fixed order)
 template <typename T>
-cudaError_t launch_shift(const Geom& g, const T* X, T* Y, int nvec, int shift, cudaStream_t s);
+cudaError_t launch_shift(const Geom& g, const T* X, T* Y, int nvec, int shift, double rho,
+                         cudaStream_t s);
 template <typename T>
 cudaError_t launch_sqerr(const Geom& g, const T* Xa, const T* xref, double* part, double* out,
                          cudaStream_t s);

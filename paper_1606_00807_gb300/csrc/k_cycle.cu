@@ -2,7 +2,9 @@
 // analysis error of Eq. 18.  The paper's model (SPEEDY) is replaced by a
 // synthetic forecast operator: advection of every field along its latitude
 // circle by a whole number of cells per step (periodic in longitude), which
-// carries the seeded random fields without changing their statistics.
+// carries the seeded random fields without changing their statistics, with
+// optional multiplicative covariance inflation about the ensemble mean (a
+// permutation has no model error, so without it the spread only shrinks).
 #include "enkfmc_internal.h"
 
 namespace enkfmc {
@@ -21,6 +23,28 @@ __global__ void __launch_bounds__(256) k_shift(const T* __restrict__ X, T* __res
     int xs = (int)(e - row * nlon) + shift;
     if (xs >= nlon) xs -= nlon;
     Y[row * nlon + xs] = X[e];
+  }
+}
+
+// The same advection with multiplicative covariance inflation about the
+// ensemble mean: Y[v][l'] = mean + rho (X[v][l] - mean), mean over the nvec
+// vectors (member-major, stride n) in double precision; one thread per
+// component of a latitude circle, the vectors in a loop.
+template <typename T>
+__global__ void __launch_bounds__(256) k_shift_inflate(const T* __restrict__ X, T* __restrict__ Y,
+                                                       int64_t n, int nvec, int nlon, int shift,
+                                                       double rho) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = l / nlon;
+    int xs = (int)(l - row * nlon) + shift;
+    if (xs >= nlon) xs -= nlon;
+    const int64_t lo = row * nlon + xs;
+    double s = 0.0;
+    for (int v = 0; v < nvec; ++v) s += (double)X[(int64_t)v * n + l];
+    const double mean = s / nvec;
+    for (int v = 0; v < nvec; ++v)
+      Y[(int64_t)v * n + lo] = (T)(mean + rho * ((double)X[(int64_t)v * n + l] - mean));
   }
 }
 
@@ -66,7 +90,15 @@ __global__ void __launch_bounds__(256) k_sqerr_final(const double* __restrict__ 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_shift(const Geom& g, const T* X, T* Y, int nvec, int shift, cudaStream_t s) {
+cudaError_t launch_shift(const Geom& g, const T* X, T* Y, int nvec, int shift, double rho,
+                         cudaStream_t s) {
+  if (rho != 1.0) {
+    int64_t grid = (g.n + 255) / 256;
+    const int64_t cap = (int64_t)(g.sm_count > 0 ? g.sm_count : 152) * 8;
+    if (grid > cap) grid = cap;
+    k_shift_inflate<T><<<(unsigned)grid, 256, 0, s>>>(X, Y, g.n, nvec, g.nlon, shift, rho);
+    return cudaGetLastError();
+  }
   const int64_t nrows = (int64_t)nvec * (g.n / g.nlon);
   const int64_t total = nrows * g.nlon;
   if (total <= 0) return cudaSuccess;
@@ -87,9 +119,9 @@ cudaError_t launch_sqerr(const Geom& g, const T* Xa, const T* xref, double* part
   return cudaGetLastError();
 }
 
-template cudaError_t launch_shift<float>(const Geom&, const float*, float*, int, int,
+template cudaError_t launch_shift<float>(const Geom&, const float*, float*, int, int, double,
                                          cudaStream_t);
-template cudaError_t launch_shift<double>(const Geom&, const double*, double*, int, int,
+template cudaError_t launch_shift<double>(const Geom&, const double*, double*, int, int, double,
                                           cudaStream_t);
 template cudaError_t launch_sqerr<float>(const Geom&, const float*, const float*, double*,
                                          double*, cudaStream_t);

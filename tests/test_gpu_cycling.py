@@ -52,6 +52,11 @@ def test_forecast_and_sqerr_match_oracle(torch_cuda, precision):
         for shift in (1, 7, -3, w.nlon):
             h.forecast_shift(Xd, Yd, w.N, shift)
             assert np.array_equal(Yd.cpu().numpy(), O.forecast_shift(w, X, shift).astype(dt)), shift
+        for rho in (1.1, 0.9):
+            h.forecast_shift(Xd, Yd, w.N, 5, rho)
+            ref = O.forecast_shift(w, X, 5, inflation=rho)
+            err = np.abs(Yd.cpu().numpy().astype(np.float64) - ref).max() / np.abs(ref).max()
+            assert err < (1e-14 if precision == 0 else 2e-7), (rho, err)
         out = torch.zeros(1, dtype=torch.float64, device="cuda")
         h.ensemble_sqerr(Xd, torch.from_numpy(xref).cuda(), out)
         ref = O.ensemble_sqerr(X.astype(np.float64), xref.astype(np.float64))
@@ -66,9 +71,12 @@ def _inputs_on_device(torch, ci, dt):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("name", ["tiny_32x16_n20_r2", "small_48x26x3x1+1_n80_r2"])
-def test_filter_run_matches_oracle(torch_cuda, name, precision):
-    """M = 12 cycles (Eq. 18's twelve assimilation times), shift 1 cell per step."""
+@pytest.mark.parametrize("name,inflation", [("tiny_32x16_n20_r2", 1.0),
+                                            ("small_48x26x3x1+1_n80_r2", 1.0),
+                                            ("small_48x26x3x1+1_n80_r2", 1.1)])
+def test_filter_run_matches_oracle(torch_cuda, name, inflation, precision):
+    """M = 12 cycles (Eq. 18's twelve assimilation times), shift 1 cell per step,
+    with and without covariance inflation in the forecast."""
     torch = torch_cuda
     from paper_1606_00807_gb300 import binding as B
     w = WORKLOADS[name]
@@ -76,7 +84,7 @@ def test_filter_run_matches_oracle(torch_cuda, name, precision):
     dt = torch.float64 if precision == 0 else torch.float32
     ci = make_cycle_inputs(w, M, shift, np.float64 if precision == 0 else np.float32)
     sq_ref, Xa_ref, Xb_ref = O.filter_cycles(w, ci.Xb0, ci.ys, ci.Zs, ci.R, ci.truths,
-                                             ci.obs_idx, shift)
+                                             ci.obs_idx, shift, inflation)
     h = _handle(torch, B, w, precision, ci.obs_idx)
     try:
         Xb, ys, Zs, R, xr = _inputs_on_device(torch, ci, dt)
@@ -84,7 +92,7 @@ def test_filter_run_matches_oracle(torch_cuda, name, precision):
         D = torch.empty(w.n, device="cuda", dtype=dt)
         Xa = torch.empty_like(Xb)
         sq = torch.zeros(M, dtype=torch.float64, device="cuda")
-        h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq)
+        h.filter_run(Xb, ys, Zs, R, xr, T, D, Xa, M, shift, sq, inflation)
         h.check("filter_run")
         sq = sq.cpu().numpy()
         lab = np.arange(w.n)
@@ -92,7 +100,7 @@ def test_filter_run_matches_oracle(torch_cuda, name, precision):
         eXb = per_variable_err(w, lab, Xb.cpu().numpy().astype(np.float64).T, Xb_ref.T)
         esq = float(np.max(np.abs(sq - sq_ref) / sq_ref))
         tol = 1e-9 if precision == 0 else 1e-4
-        print(f"\ncycling {name} precision={precision}: RMSE {O.rmse_eq18(sq):.6e} "
+        print(f"\ncycling {name} inflation={inflation} precision={precision}: RMSE {O.rmse_eq18(sq):.6e} "
               f"(oracle {O.rmse_eq18(sq_ref):.6e}) sqerr {esq:.2e} Xa {eXa:.2e} Xb {eXb:.2e}")
         assert esq < tol and eXa < tol and eXb < tol, (esq, eXa, eXb)
     finally:

@@ -23,6 +23,21 @@ def test_forecast_shift_hand_example():
     assert np.array_equal(O.forecast_shift(w2, Y, 1), [[2, 0, 1, 5, 3, 4]])
 
 
+def test_forecast_inflation_hand_example_and_moments():
+    """Two vectors [0, 2] and [2, 4] (mean [1, 3]) inflated by 2 about their mean
+    give [-1, 1] and [3, 5], then shifted by one cell: [1, -1] and [5, 3].  In
+    general the mean is kept and the sample variance scales by rho^2."""
+    w = _line(2)
+    X = np.array([[0.0, 2.0], [2.0, 4.0]])
+    assert np.array_equal(O.forecast_shift(w, X, 1, inflation=2.0), [[1, -1], [5, 3]])
+    rng = np.random.default_rng(0)
+    w5 = _line(5)
+    Y = rng.standard_normal((6, 5))
+    Z = O.forecast_shift(w5, Y, 0, inflation=1.3)
+    assert np.allclose(Z.mean(axis=0), Y.mean(axis=0), rtol=0, atol=1e-14)
+    assert np.allclose(Z.var(axis=0), 1.3 ** 2 * Y.var(axis=0), rtol=1e-12)
+
+
 def test_sqerr_and_eq18_hand_examples():
     assert O.ensemble_sqerr(np.array([[1.0, 2.0], [3.0, 4.0]]), np.zeros(2)) == 13.0
     assert np.isclose(O.rmse_eq18([1.0, 3.0]), np.sqrt(2.0))
