@@ -628,7 +628,7 @@ def accuracy_study_line(dev, M=12, shift=1, radii=(1, 2, 3), tiles=(6, 12, 16), 
     from paper_1606_00807_gb300 import binding as B
     from synthetic import WORKLOADS, make_cycle_inputs
 
-    base = WORKLOADS["study_96x48x3x2+1_n40"]
+    base = WORKLOADS["study_96x48x3x2+1_n60"]
     ci = make_cycle_inputs(base, M, shift, np.float32)  # r and the tile change no input
     put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     ys, Zs, R, xr = put(ci.ys), put(ci.Zs), put(ci.R), put(ci.truths)

@@ -120,10 +120,11 @@ SMALL_2D_R3 = Workload(
 
 # Accuracy study (radius and tile size against the analysis RMSE of Eq. 18 over
 # filter cycles): a 96 x 48 grid, 3 levels of two 3-D variables and one 2-D
-# variable, N = 40; the study varies r and the tile.
+# variable, N = 60 (at N = 40, r = 2 puts rows at p = N - 2, below the ridge
+# threshold with one residual degree of freedom); the study varies r and the tile.
 STUDY = Workload(
-    name="study_96x48x3x2+1_n40", nlon=96, nlat=48, nlev=3, nvar_3d=2, nvar_2d=1,
-    r=2, N=40, sub_lon=12, sub_lat=12, sigma2=(4.0, 1.0, 1e2), corr_len=4.0, rho_vert=0.5,
+    name="study_96x48x3x2+1_n60", nlon=96, nlat=48, nlev=3, nvar_3d=2, nvar_2d=1,
+    r=2, N=60, sub_lon=12, sub_lat=12, sigma2=(4.0, 1.0, 1e2), corr_len=4.0, rho_vert=0.5,
     obs="random", obs_frac=0.5, r_frac=0.01, seed=7500)
 
 WORKLOADS = {w.name: w for w in (TINY_32x16, T63_N80, T63_N40, T127_N96, STUDY,

@@ -308,7 +308,7 @@ def test_band_too_wide_for_the_band_kernels_is_refused():
     problem uses them): enkfmc_create refuses it with EINVAL instead of failing
     at launch; the plain FP32 form (no double-precision blocks) is accepted."""
     from paper_1606_00807_gb300 import binding as B
-    w = WORKLOADS["study_96x48x3x2+1_n40"].with_(r=3, sub_lon=24, sub_lat=24)
+    w = WORKLOADS["study_96x48x3x2+1_n60"].with_(r=3, sub_lon=24, sub_lat=24)
     with pytest.raises(B.EnkfmcError) as ei:
         B.Handle.from_workload(w, precision=B.FP32)
     assert "EINVAL" in str(ei.value)
