@@ -45,6 +45,15 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Sum over each group of G consecutive lanes (G = 16: each half of the warp;
+// every lane of the warp takes part).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ bool finite_val(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_val(double v) { return isfinite(v); }
 
@@ -470,12 +479,12 @@ __host__ __device__ inline int64_t addr_elems(size_t esize, int ldp, int ldg) {
 // tiles (64 multiply-adds per 12 vector loads).  invd[u] = 1 / L[u][u] for
 // u < npiv; *code (a slot not among those) carries the error code between
 // lanes.  Returns 0 or ENKFMC_EDNONPOS / ENKFMC_ENONFINITE (same in every lane).
-template <typename T>
+template <typename T, int G = 32>
 __device__ int tiled_cholesky(T* L, const Addr<T> at, T* invd, T* code, int nrows, int npiv, int lane,
                               const uint16_t* tri = nullptr) {
   const int p1 = nrows, p = npiv;
   const int P4 = (p1 + 3) & ~3;
-  for (int i = p1 + lane; i < P4; i += 32) {
+  for (int i = p1 + lane; i < P4; i += G) {
     for (int l = 0; l < i; ++l) L[at(i, l)] = T(0);
     L[at(i, i)] = T(1);
   }
@@ -519,21 +528,25 @@ __device__ int tiled_cholesky(T* L, const Addr<T> at, T* invd, T* code, int nrow
     __syncwarp();
     {
       const int e = (int)*code;
-      if (e) {
+      if (G == 32) {  // a warp per matrix: stop at the first failure
+        if (e) {
+          err = e;
+          break;
+        }
+      } else if (e && !err) {  // groups in step with each other: finish the steps
         err = e;
-        break;
       }
     }
     // tiles (I, K) below: X L_KK^T = A_IK, rows of X solved left to right
     const int nrem = nt - K - 1;
-    if (lane < nrem) {
+    for (int tI = lane; tI < nrem; tI += G) {
       T lk[4][4], iv[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         lds4v(L + at(k0 + r, k0), lk[r]);
         iv[r] = (k0 + r < p) ? invd[k0 + r] : T(1);
       }
-      const int i0 = k0 + 4 * (lane + 1);
+      const int i0 = k0 + 4 * (tI + 1);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         T xr[4];
@@ -551,7 +564,7 @@ __device__ int tiled_cholesky(T* L, const Addr<T> at, T* invd, T* code, int nrow
     __syncwarp();
     // trailing tiles (I, J), K < J <= I < nt
     const int ntile = nrem * (nrem + 1) / 2;
-    for (int tix = lane; tix < ntile; tix += 32) {
+    for (int tix = lane; tix < ntile; tix += G) {
       int Ip, Jp;
       if (tri) {  // lower-triangle index table: tix -> (Ip, Jp)
         const uint32_t il = tri[tix];
@@ -616,7 +629,7 @@ __host__ __device__ inline int gather_table_bytes(int pmax) {
 // room for n rounded up to 4.  Per tile step lane 0 solves the 4 unknowns of
 // the diagonal tile, then the lanes update the unknowns below it, one 16-byte
 // read of L per row.
-template <typename T>
+template <typename T, int G = 32>
 __device__ void tiled_forward(const T* L, const Addr<T> at, const T* invd, T* v, int n, int lane) {
   const int nt = (n + 3) >> 2;
   for (int K = 0; K < nt; ++K) {
@@ -636,7 +649,7 @@ __device__ void tiled_forward(const T* L, const Addr<T> at, const T* invd, T* v,
     __syncwarp();
     T x4[4];
     lds4v(v + k0, x4);
-    for (int i = k0 + 4 + lane; i < n; i += 32) {
+    for (int i = k0 + 4 + lane; i < n; i += G) {
       T l4[4];
       lds4v(L + at(i, k0), l4);
       T acc = v[i];
@@ -649,7 +662,7 @@ __device__ void tiled_forward(const T* L, const Addr<T> at, const T* invd, T* v,
 }
 
 // v := L^-T v for the first n unknowns (same storage as tiled_forward).
-template <typename T>
+template <typename T, int G = 32>
 __device__ void tiled_backward(const T* L, const Addr<T> at, const T* invd, T* v, int n, int lane) {
   const int nt = (n + 3) >> 2;
   for (int K = nt - 1; K >= 0; --K) {
@@ -669,7 +682,7 @@ __device__ void tiled_backward(const T* L, const Addr<T> at, const T* invd, T* v
     __syncwarp();
     T x4[4];
     lds4v(v + k0, x4);
-    for (int j = lane; j < k0; j += 32) {
+    for (int j = lane; j < k0; j += G) {
       T acc = v[j];
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc = fma(-L[at(k0 + c, j)], x4[c], acc);
@@ -950,6 +963,283 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     }
     if (lane == 0) Dout[orow] = err ? TO(NAN) : (TO)Dj;
     __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Single-precision regressions, two rows per warp (16 lanes each).  The tiled
+// factorisation leaves most lanes idle in its serial steps (lane 0 factors a
+// 4 x 4 diagonal tile, the tile solves and the triangular solves use a few
+// lanes); with a row per half-warp the same instructions serve two rows.  A
+// warp takes the items 2e and 2e + 1 of the list; each half builds its row's
+// predecessor list, and when the two rows have the same predecessor count p
+// (the usual case: neighbouring components) the halves run in step through
+// the same loops and barriers.  Otherwise the warp runs the two rows one after
+// the other, both halves on the same row (the same result; the second half's
+// writes repeat the first's).  Per half: the workspace of k_regress (Gram
+// matrix row-major, vectors); members 4 * (lane + 16 k) .. + 3 of a row.
+// Arithmetic as k_regress's single-precision rows (FP32 Cholesky, one
+// corrected semi-normal step from the residual of the anomalies).
+// ---------------------------------------------------------------------------
+template <int MV>
+__global__ void __launch_bounds__(192, 2)
+    k_regress_pair(const Geom g, const float* __restrict__ U, const float* __restrict__ C, int nH,
+                   const int32_t* __restrict__ halo, int64_t nitems,
+                   const Block* __restrict__ blocks, float* __restrict__ Tout,
+                   float* __restrict__ Dout, double ridge_c, int32_t* status, int ldp, int ldg,
+                   int half_bytes, int sel, int use_ptab) {
+  constexpr int G = 16;
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int hw = lane >> 4, gl = lane & 15;
+  signed char* off = reinterpret_cast<signed char*>(smem);
+  const int pmax = g.pmax;
+  const int offbytes = (3 * pmax + 15) / 16 * 16;
+  for (int s = threadIdx.x; s < pmax; s += blockDim.x) {
+    int dk, dy, dx;
+    slot_offset(s, g.r, g.vr, dk, dy, dx);
+    off[s] = (signed char)dk;
+    off[pmax + s] = (signed char)dy;
+    off[2 * pmax + s] = (signed char)dx;
+  }
+  const int pf = pmax - (g.periodic ? g.r : 0);
+  int2* ptab = reinterpret_cast<int2*>(smem + offbytes);
+  const int ptab_bytes = use_ptab ? pair_table_bytes(pmax, g.r, g.periodic) : 0;
+  if (use_ptab) build_pair_table(g, pf, ptab);
+  const int nfull = (pmax + 1) * (pmax + 2) / 2;
+  uint16_t* tri = reinterpret_cast<uint16_t*>(smem + offbytes + ptab_bytes);
+  uint16_t* ftab = tri + nfull;
+  build_gather_tables(g, pmax, tri, ftab);
+  __syncthreads();
+  unsigned char* base = smem + offbytes + ptab_bytes + gather_table_bytes(pmax) +
+                        ((size_t)warp * 2 + hw) * half_bytes;
+  int* q = reinterpret_cast<int*>(base);        // [ldp] component labels (q[p] = j)
+  int* sl = q + ldp;                             // [ldp] slot of compacted entry (-1 = j)
+  int* sidx = sl + ldp;                          // [ldp] compacted index of slot s
+  float* L = reinterpret_cast<float*>(sidx + ldp);  // [ldp][ldg]
+  const Addr<float> at{ldg};
+  float* va = L + (size_t)ldp * ldg;             // [ldp]
+  float* vb = va + ldp;                          // [ldp]
+  float* gv = vb + ldp;                          // [ldp]
+  float* invd = gv + ldp;                        // [ldp]
+  const int N = g.N;
+
+  // predecessor list of item `it` in this half (sets q, sl, sidx; returns p)
+  auto pred_list = [&](int64_t it, int& v, int& k, int& y, int& x, int64_t& orow, int& jlab,
+                       const Block*& b) {
+    b = nullptr;
+    if (halo) {
+      const int blk = halo[2 * it], loc = halo[2 * it + 1];
+      b = blocks + blk;
+      const int plane = b->ey * b->ex;
+      k = loc / plane;
+      const int rem = loc - k * plane;
+      const int yy = rem / b->ex, xx = rem - yy * b->ex;
+      y = b->lat_lo + yy;
+      x = imod(b->lon_lo + xx, g.nlon);
+      v = b->var;
+      orow = b->row_off + loc;
+    } else {
+      label_coords(g, it, v, k, y, x);
+      orow = it;
+    }
+    int p = 0;
+    for (int s0 = 0; s0 < pmax; s0 += G) {
+      const int s = s0 + gl;
+      bool pres = false;
+      int qq = 0;
+      if (s < pmax) {
+        int kq, yq, xq;
+        pres = slot_pred_off(g, k, y, x, off[s], off[pmax + s], off[2 * pmax + s], kq, yq, xq);
+        if (pres && b) {
+          int yy, xx;
+          pres = in_ext(*b, g.nlon, yq, xq, yy, xx);
+        }
+        if (pres) qq = (int)coords_label(g, v, kq, yq, xq);
+      }
+      const unsigned mask = (__ballot_sync(FULL, pres) >> (16 * hw)) & 0xffffu;
+      const int idx = p + __popc(mask & ((1u << gl) - 1u));
+      if (s < pmax) sidx[s] = pres ? idx : -1;
+      if (pres) {
+        q[idx] = qq;
+        sl[idx] = s;
+      }
+      p += __popc(mask);
+    }
+    jlab = (int)coords_label(g, v, k, y, x);
+    if (gl == 0) {
+      q[p] = jlab;
+      sl[p] = -1;
+    }
+    __syncwarp();
+    return p;
+  };
+
+  // the regression of this half's row, its predecessor list built; p is the
+  // same in both halves
+  auto regress_row = [&](int p, int64_t orow, int jlab) {
+    if (sel && ((2 * p > N) != (sel == 2))) return;  // the other launch's row
+    const int p1 = p + 1;
+    const int npair = p1 * (p1 + 1) / 2;
+    const bool typical = use_ptab && p == pf && (p == 0 || sl[p - 1] == pf - 1);
+    if (typical) {
+#pragma unroll 4
+      for (int pi = gl; pi < npair; pi += G) {
+        const int2 e = ptab[pi];
+        const int i = e.x & 0xff, l = (e.x >> 8) & 0xff;
+        L[at(i, l)] = C[(int64_t)((e.x >> 16) ? q[l] : q[i]) * nH + e.y];
+      }
+    } else {
+#pragma unroll 4
+      for (int pi = gl; pi < npair; pi += G) {
+        const uint32_t il = tri[pi];
+        const int i = il & 0xff, l = il >> 8;
+        // slots rise with the compact index and the row itself is last: sm <= si
+        int si = sl[i], sm = sl[l];
+        si = si < 0 ? pmax : si;
+        sm = sm < 0 ? pmax : sm;
+        const uint32_t e = ftab[si * (si + 1) / 2 + sm];
+        L[at(i, l)] = C[(int64_t)((e & 0x8000u) ? q[l] : q[i]) * nH + (e & 0x7fffu)];
+      }
+    }
+    __syncwarp();
+    float lam = 0.f;
+    if (p > 0 && ridge_c > 0.0 && p >= N - 1) {
+      float tr = 0.f;
+      for (int i = gl; i < p; i += G) tr += L[at(i, i)];
+      tr = group_sum<G>(tr);
+      lam = (float)ridge_c * tr / (float)p;
+    }
+    for (int i = gl; i < p; i += G) {
+      gv[i] = L[at(p, i)];
+      L[at(i, i)] += lam;
+    }
+    __syncwarp();
+    int err = tiled_cholesky<float, G>(L, at, invd, invd + (ldp - 1), p1, p, gl, tri);
+    // beta = L^-T w (w = row p of L), in vb
+    for (int i = gl; i < p; i += G) va[i] = L[at(p, i)];
+    __syncwarp();
+    tiled_backward<float, G>(L, at, invd, va, p, gl);
+    for (int i = gl; i < p; i += G) vb[i] = va[i];
+    __syncwarp();
+    // residual e = u - U_P^T beta, members 4 (gl + 16 k) .. + 3 of this lane
+    float4 e4[MV];
+#pragma unroll
+    for (int k = 0; k < MV; ++k) {
+      const int m0 = 4 * (gl + G * k);
+      e4[k] = m0 < g.ldN ? *reinterpret_cast<const float4*>(U + (int64_t)jlab * g.ldN + m0)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll 2
+    for (int i = 0; i < p; ++i) {
+      const float bi = vb[i];
+      const float* Ui = U + (int64_t)q[i] * g.ldN;
+#pragma unroll
+      for (int k = 0; k < MV; ++k) {
+        const int m0 = 4 * (gl + G * k);
+        if (m0 < g.ldN) {
+          const float4 u4 = *reinterpret_cast<const float4*>(Ui + m0);
+          e4[k].x = fmaf(-u4.x, bi, e4[k].x);
+          e4[k].y = fmaf(-u4.y, bi, e4[k].y);
+          e4[k].z = fmaf(-u4.z, bi, e4[k].z);
+          e4[k].w = fmaf(-u4.w, bi, e4[k].w);
+        }
+      }
+    }
+    // c = U_P e - lambda beta -> va: 16 predecessors at a time by a
+    // reduce-scatter over the half, the rest one group sum each
+    auto udot = [&](int i) {
+      const float* Ui = U + (int64_t)q[i] * g.ldN;
+      float sdot = 0.f;
+#pragma unroll
+      for (int k = 0; k < MV; ++k) {
+        const int m0 = 4 * (gl + G * k);
+        if (m0 < g.ldN) {
+          const float4 u4 = *reinterpret_cast<const float4*>(Ui + m0);
+          sdot = fmaf(u4.w, e4[k].w, fmaf(u4.z, e4[k].z, fmaf(u4.y, e4[k].y,
+                      fmaf(u4.x, e4[k].x, sdot))));
+        }
+      }
+      return sdot;
+    };
+    const int pfull = p & ~(G - 1);
+    for (int i0 = 0; i0 < pfull; i0 += G) {
+      float part[G];
+#pragma unroll
+      for (int j = 0; j < G; ++j) part[j] = udot(i0 + j);
+#pragma unroll
+      for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool hi = (gl & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+          const float send = hi ? part[j] : part[j + o];
+          const float keep = hi ? part[j + o] : part[j];
+          part[j] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+      }
+      const int i = i0 + gl;
+      va[i] = part[0] - lam * vb[i];
+    }
+    for (int i = pfull; i < p; ++i) {
+      const float part = group_sum<G>(udot(i));
+      if (gl == (i & (G - 1))) va[i] = part - lam * vb[i];
+    }
+    __syncwarp();
+    for (int i = gl; i < p; i += G) gv[i] = va[i];
+    tiled_forward<float, G>(L, at, invd, va, p, gl);
+    float zz = 0.f;
+    for (int i = gl; i < p; i += G) zz = fmaf(va[i], va[i], zz);
+    zz = group_sum<G>(zz);
+    tiled_backward<float, G>(L, at, invd, va, p, gl);
+    float ee = 0.f;
+#pragma unroll
+    for (int k = 0; k < MV; ++k)
+      ee = fmaf(e4[k].w, e4[k].w, fmaf(e4[k].z, e4[k].z, fmaf(e4[k].y, e4[k].y,
+                fmaf(e4[k].x, e4[k].x, ee))));
+    ee = group_sum<G>(ee);
+    float dc = 0.f, dd = 0.f;
+    for (int i = gl; i < p; i += G) {
+      const float di = va[i];
+      dc = fmaf(di, gv[i] + lam * vb[i], dc);
+      dd = fmaf(di, di, dd);
+    }
+    dc = group_sum<G>(dc);
+    dd = group_sum<G>(dd);
+    for (int i = gl; i < p; i += G) vb[i] += va[i];
+    const float ssq = ee - 2.f * dc + (zz - lam * dd);
+    const float Dj = ssq / (float)(N - 1);
+    if (!err) {
+      if (!finite_val(Dj)) err = ENKFMC_ENONFINITE;
+      else if (!(Dj > 0.f)) err = ENKFMC_EDNONPOS;
+    }
+    __syncwarp();
+    if (err && gl == 0 && status) record_error(status, err, orow);
+    float* trow = Tout + orow * pmax;
+    for (int s = gl; s < pmax; s += G) {
+      const int i = sidx[s];
+      trow[s] = (i >= 0 && !err) ? -vb[i] : 0.f;
+    }
+    if (gl == 0) Dout[orow] = err ? NAN : Dj;
+    __syncwarp();
+  };
+
+  const int64_t nent = (nitems + 1) / 2;
+  for (int64_t e = (int64_t)blockIdx.x * wpc + warp; e < nent; e += (int64_t)gridDim.x * wpc) {
+    const int64_t iA = 2 * e, iB = (2 * e + 1 < nitems) ? 2 * e + 1 : 2 * e;
+    int v, k, y, x, jlab;
+    int64_t orow;
+    const Block* b;
+    int p = pred_list(hw ? iB : iA, v, k, y, x, orow, jlab, b);
+    const int pA = __shfl_sync(FULL, p, 0), pB = __shfl_sync(FULL, p, 16);
+    if (pA == pB) {
+      regress_row(p, orow, jlab);
+    } else {  // one row after the other, both halves on it
+      for (int pass = 0; pass < 2; ++pass) {
+        p = pred_list(pass ? iB : iA, v, k, y, x, orow, jlab, b);
+        regress_row(p, orow, jlab);
+      }
+    }
   }
 }
 
@@ -2080,8 +2370,9 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
 // T63 rows (N = 80, 39 slots) the tiled kernels are faster: 5.98 against 7.29
 // ms for the global rows, 3.49 against 6.01 ms for the boundary rows (whose
 // short predecessor lists the register kernel pads to 39), 12.1 against 15.6
-// ms for the adjoint.  So the default (kernel choice 0, as 1) is tiled; 2
-// takes the register kernels wherever they apply.
+// ms for the adjoint.  Kernel choice 0 (default): the forward single-precision
+// rows two per warp (k_regress_pair), the adjoint tiled; 1: tiled, a row per
+// warp; 2: the register kernels wherever they apply.
 bool regress_lane_applies(const Geom& g, int sel, bool adjoint) {
   (void)adjoint;
   return g.regress_kernel == 2 && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 &&
@@ -2116,6 +2407,49 @@ cudaError_t launch_regress_lane(const Geom& g, const float* U, const float* C,
   return cudaGetLastError();
 }
 
+// Launch shape of k_regress_pair: two half-warp workspaces of k_regress per
+// warp, up to six warps per CTA in up to 110 KB (two CTAs per SM); false when
+// not even one warp fits in 220 KB.
+bool regress_pair_shape(const Geom& g, RegShape& rs) {
+  if (!regress_shape(g, 4, true, rs)) return false;
+  for (int ptab = 1; ptab >= 0; --ptab) {
+    const size_t tables = (3 * (size_t)g.pmax + 15) / 16 * 16 +
+                          (ptab ? pair_table_bytes(g.pmax, g.r, g.periodic) : 0) +
+                          gather_table_bytes(g.pmax);
+    for (size_t budget : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+      int wpc = (int)((budget - std::min(tables, budget)) / (2 * rs.wb));
+      if (wpc > 6) wpc = 6;
+      if (wpc >= 1) {
+        rs.wpc = wpc;
+        rs.use_ptab = ptab;
+        rs.smem = tables + 2 * rs.wb * wpc;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
+template <int MV>
+cudaError_t launch_regress_pair_mv(const Geom& g, const float* U, const float* C,
+                                   const int32_t* halo, int64_t nitems, const Block* blocks,
+                                   float* Tout, float* Dout, double ridge_c, int32_t* status,
+                                   int sel, const RegShape& rs, cudaStream_t s) {
+  const int nH = cov_offset_count(g.r, g.vr);
+  cudaError_t e = cudaFuncSetAttribute(k_regress_pair<MV>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs.smem);
+  if (e != cudaSuccess) return e;
+  const int64_t nent = (nitems + 1) / 2;
+  int64_t grid = (nent + rs.wpc - 1) / rs.wpc;
+  const int64_t cap = (int64_t)(g.sm_count > 0 ? g.sm_count : 152) *
+                      (g.regress_cap > 0 ? g.regress_cap : 64);
+  if (grid > cap) grid = cap;
+  k_regress_pair<MV><<<(unsigned)grid, 32 * rs.wpc, rs.smem, s>>>(
+      g, U, C, nH, halo, nitems, blocks, Tout, Dout, ridge_c, status, rs.ldp, rs.ldg, (int)rs.wb,
+      sel, rs.use_ptab);
+  return cudaGetLastError();
+}
+
 template <typename T, typename TO>
 cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t* halo,
                            int64_t nitems, const Block* blocks, TO* Tout, TO* Dout, double ridge_c,
@@ -2123,6 +2457,14 @@ cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t*
   if (nitems <= 0) return cudaSuccess;
   if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds) return cudaErrorInvalidConfiguration;
   if constexpr (std::is_same<T, float>::value && std::is_same<TO, float>::value) {
+    RegShape ps;
+    if (g.regress_kernel == 0 && sel != 2 && regress_pair_shape(g, ps)) {
+      if (g.ldN <= 64)
+        return launch_regress_pair_mv<1>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
+                                         status, sel, ps, s);
+      return launch_regress_pair_mv<2>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
+                                       sel, ps, s);
+    }
     if (regress_lane_applies(g, sel, false)) {
       if (g.pmax + 1 > 32)
         return launch_regress_lane<8>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c, status,
