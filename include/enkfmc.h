@@ -381,11 +381,12 @@ enum {
   ENKFMC_TUNE_REGRESS_CTAS_PER_SM = 0, /* CTAs per SM of the regressions' grid-stride
                                           launch (0 = the default, 64)              */
   ENKFMC_TUNE_REGRESS_KERNEL = 1       /* single-precision regression kernels:
-                                          0 (default): shared-memory tiled, the
-                                          forward rows two per warp; 1: tiled, a
-                                          row per warp; 2: register-resident
+                                          0 (default) and 1: shared-memory tiled,
+                                          a row per warp; 2: register-resident
                                           (forward and adjoint) wherever the
-                                          stencil has 16..39 slots                  */
+                                          stencil has 16..39 slots; 3: tiled, the
+                                          forward rows two per warp (both slower
+                                          on the T63 rows)                          */
 };
 enkfmc_status enkfmc_set_tuning(enkfmc_handle* h, int32_t knob, int32_t value);
 

@@ -252,7 +252,7 @@ enkfmc_status enkfmc_set_tuning(enkfmc_handle* h, int32_t knob, int32_t value) {
       h->g.regress_cap = value;
       return ENKFMC_OK;
     case ENKFMC_TUNE_REGRESS_KERNEL:
-      if (value > 2) return ENKFMC_EINVAL;
+      if (value > 3) return ENKFMC_EINVAL;
       h->g.regress_kernel = value;
       return ENKFMC_OK;
   }

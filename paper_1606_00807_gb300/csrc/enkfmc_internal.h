@@ -21,7 +21,7 @@ struct Geom {
   int32_t pmax;
   int32_t sm_count;      // SMs of the device (launch shapes; host side only)
   int32_t regress_cap;   // CTAs per SM of the regressions' grid-stride launch
-  int32_t regress_kernel; // regression kernels: 0 default, 1 tiled, 2 register (k_estimate.cu)
+  int32_t regress_kernel; // regression kernels: 0/1 tiled, 2 register, 3 paired (k_estimate.cu)
   int32_t plain_fp32;     // single precision without double-precision rows or blocks
   int64_t n;
   int64_t var_off[kMaxVar + 1];

@@ -2370,9 +2370,13 @@ cudaError_t launch_regress_rm(const Geom& g, const T* U, const T* C, const int32
 // T63 rows (N = 80, 39 slots) the tiled kernels are faster: 5.98 against 7.29
 // ms for the global rows, 3.49 against 6.01 ms for the boundary rows (whose
 // short predecessor lists the register kernel pads to 39), 12.1 against 15.6
-// ms for the adjoint.  Kernel choice 0 (default): the forward single-precision
-// rows two per warp (k_regress_pair), the adjoint tiled; 1: tiled, a row per
-// warp; 2: the register kernels wherever they apply.
+// ms for the adjoint.  Two rows per warp (k_regress_pair, choice 3) executes
+// 41% fewer instructions than a row per warp but, with shared memory holding
+// the same 24 rows per SM in half as many warps, becomes latency bound: 7.04
+// against 5.78 ms for the global rows, 6.67 against 3.47 ms for the boundary
+// rows (whose neighbouring items often differ in p and then run one after the
+// other).  Kernel choice 0 (default) and 1: tiled, a row per warp; 2: the
+// register kernels wherever they apply; 3: two rows per warp.
 bool regress_lane_applies(const Geom& g, int sel, bool adjoint) {
   (void)adjoint;
   return g.regress_kernel == 2 && sel != 2 && g.N <= 32 * kMaxRounds && g.pmax + 1 > 16 &&
@@ -2458,7 +2462,7 @@ cudaError_t launch_regress(const Geom& g, const T* U, const T* C, const int32_t*
   if (g.pmax + 1 > 32 * 8 || g.N > 32 * kMaxRounds) return cudaErrorInvalidConfiguration;
   if constexpr (std::is_same<T, float>::value && std::is_same<TO, float>::value) {
     RegShape ps;
-    if (g.regress_kernel == 0 && sel != 2 && regress_pair_shape(g, ps)) {
+    if (g.regress_kernel == 3 && sel != 2 && regress_pair_shape(g, ps)) {
       if (g.ldN <= 64)
         return launch_regress_pair_mv<1>(g, U, C, halo, nitems, blocks, Tout, Dout, ridge_c,
                                          status, sel, ps, s);
