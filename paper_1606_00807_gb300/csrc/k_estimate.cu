@@ -442,18 +442,21 @@ __device__ __forceinline__ void sqrt_and_inv(double x, double& s, double& inv) {
 }
 
 // Element (r, c) of a warp's lower-triangular matrix (c <= r, or inside the
-// diagonal 4 x 4 tile).  Single precision: row-major with row stride ld (4 mod
-// 8: the 16-byte row reads of 8 consecutive lanes hit distinct banks).  Double
-// precision: packed 4 x 4 tiles, tile (I, J), J <= I, at (I (I + 1) / 2 + J) * 18
-// (18 doubles: the tiles of 8 consecutive lanes start in distinct 16-byte
-// bank groups), about half the shared memory of the row-major square for the
-// large stencils, so more warps share an SM's double-precision pipes.
+// diagonal 4 x 4 tile): packed 4 x 4 tiles, tile (I, J), J <= I, at
+// (I (I + 1) / 2 + J) * S with S = 20 floats or 18 doubles (80 or 144 bytes:
+// the tiles of 8 consecutive lanes start in distinct 16-byte bank groups, and
+// a row of a tile is 16-byte aligned).  About half the shared memory of the
+// row-major square: more warps per SM (four CTAs of eight warps in single
+// precision at 39 slots; more warps sharing the FP64 pipes in double).
 template <typename T>
 struct Addr;
 template <>
 struct Addr<float> {
-  int ld;
-  __device__ __forceinline__ int operator()(int r, int c) const { return r * ld + c; }
+  int ld;  // unused
+  __device__ __forceinline__ int operator()(int r, int c) const {
+    const int I = r >> 2;
+    return (I * (I + 1) / 2 + (c >> 2)) * 20 + ((r & 3) << 2) + (c & 3);
+  }
 };
 template <>
 struct Addr<double> {
@@ -466,7 +469,7 @@ struct Addr<double> {
 // Elements of the matrix storage for ldp rows (a multiple of 4) and row stride ldg.
 __host__ __device__ inline int64_t addr_elems(size_t esize, int ldp, int ldg) {
   const int nt = ldp / 4;
-  return esize == 4 ? (int64_t)ldp * ldg : (int64_t)nt * (nt + 1) / 2 * 18;
+  return (int64_t)nt * (nt + 1) / 2 * (esize == 4 ? 20 : 18);
 }
 
 // Right-looking Cholesky, in 4 x 4 tiles, of the leading nrows x nrows block
@@ -705,7 +708,7 @@ constexpr int kMaxRounds = 4;  // N <= 128 members: 4 rounds of 32 lanes
 // per-warp workspace would not fit beside it): every row then gathers
 // through the slot-pair tables.
 template <typename T, typename TO, int MR>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1)
     k_regress(const Geom g, const T* __restrict__ U, const T* __restrict__ C, int nH,
               const int32_t* __restrict__ halo, int64_t nitems, const Block* __restrict__ blocks,
               TO* __restrict__ Tout, TO* __restrict__ Dout, double ridge_c, int32_t* status,
@@ -1019,7 +1022,7 @@ __global__ void __launch_bounds__(192, 2)
   int* sidx = sl + ldp;                          // [ldp] compacted index of slot s
   float* L = reinterpret_cast<float*>(sidx + ldp);  // [ldp][ldg]
   const Addr<float> at{ldg};
-  float* va = L + (size_t)ldp * ldg;             // [ldp]
+  float* va = L + addr_elems(sizeof(float), ldp, ldg);  // [ldp]
   float* vb = va + ldp;                          // [ldp]
   float* gv = vb + ldp;                          // [ldp]
   float* invd = gv + ldp;                        // [ldp]
@@ -2247,14 +2250,14 @@ struct RegShape {
 
 bool regress_shape(const Geom& g, size_t esize, bool reg, RegShape& rs) {
   rs.ldp = ((g.pmax + 1) + 3) / 4 * 4;
-  // single precision: row stride = 4 (mod 8), so that 16-byte row reads of 8
-  // consecutive lanes are conflict free; double precision: packed tiles (Addr)
+  // (ldg: unused by the packed tiles of Addr, kept in the launch arguments)
   rs.ldg = ((g.pmax + 1) + 7) / 8 * 8 + 4;
   size_t wb = (size_t)rs.ldp * 3 * sizeof(int) +
               esize * ((size_t)addr_elems(esize, rs.ldp, rs.ldg) + (reg ? 4 : 3) * (size_t)rs.ldp);
   rs.wb = (wb + 15) / 16 * 16;
-  // single precision: up to 96 KB per CTA (three CTAs of eight warps per SM),
-  // with the typical row's pair table if it fits; double precision: one CTA of
+  // single precision: up to 96 KB per CTA (at 39 slots about 54 KB: four CTAs
+  // of eight warps per SM), with the typical row's pair table if it fits;
+  // double precision: one CTA of
   // up to eight warps per SM in up to 220 KB, without the pair table (the
   // double-precision pipes, not the gather, bound those rows: more warps share
   // them)
