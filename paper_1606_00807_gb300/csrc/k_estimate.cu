@@ -1953,7 +1953,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_regress_lane(
 // single-precision problem regressed in double precision); TS: the element
 // type of T, D, the adjoint rows and the stored terms.  sel as in k_regress.
 template <typename T, typename TS>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_regress(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_regress(
     const Geom g, const Block* __restrict__ blocks, const T* __restrict__ U,
     const T* __restrict__ C, int nH, const TS* __restrict__ Tg, const TS* __restrict__ Dg,
     const TS* __restrict__ Te, const TS* __restrict__ De, const TS* __restrict__ aT,
