@@ -49,7 +49,10 @@ FP64_NOMINAL_TFLOPS = 1.25
 # kernel from one ncu capture of its current version on the named workload and
 # precision (the capture commands are in profiles/); a kernel without one
 # reports null.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # the global-rows launch of the tiled single-precision kernel
+    ("regress", "t63_192x96x29_n80_r2", "fp32"): 724_083_968,
+}
 TUNING_CACHE = os.path.join(ROOT, "paper_1606_00807_gb300", "tuning_gb300.json")
 
 
