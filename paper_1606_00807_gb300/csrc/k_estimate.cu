@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1)
 // corrected semi-normal step from the residual of the anomalies).
 // ---------------------------------------------------------------------------
 template <int MV>
-__global__ void __launch_bounds__(192, 2)
+__global__ void __launch_bounds__(192, 3)
     k_regress_pair(const Geom g, const float* __restrict__ U, const float* __restrict__ C, int nH,
                    const int32_t* __restrict__ halo, int64_t nitems,
                    const Block* __restrict__ blocks, float* __restrict__ Tout,
@@ -2415,23 +2415,32 @@ cudaError_t launch_regress_lane(const Geom& g, const float* U, const float* C,
 }
 
 // Launch shape of k_regress_pair: two half-warp workspaces of k_regress per
-// warp, up to six warps per CTA in up to 110 KB (two CTAs per SM); false when
-// not even one warp fits in 220 KB.
+// warp, up to six warps per CTA in up to 72 KB (three CTAs per SM, 96
+// registers), with or without the typical row's pair table, whichever fits
+// more warps; larger stencils in up to 220 KB; false when not even one warp
+// fits.
 bool regress_pair_shape(const Geom& g, RegShape& rs) {
   if (!regress_shape(g, 4, true, rs)) return false;
-  for (int ptab = 1; ptab >= 0; --ptab) {
-    const size_t tables = (3 * (size_t)g.pmax + 15) / 16 * 16 +
-                          (ptab ? pair_table_bytes(g.pmax, g.r, g.periodic) : 0) +
-                          gather_table_bytes(g.pmax);
-    for (size_t budget : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+  for (size_t budget : {(size_t)72 * 1024, (size_t)220 * 1024}) {
+    int best = 0, best_ptab = 0;
+    size_t best_tables = 0;
+    for (int ptab = 1; ptab >= 0; --ptab) {
+      const size_t tables = (3 * (size_t)g.pmax + 15) / 16 * 16 +
+                            (ptab ? pair_table_bytes(g.pmax, g.r, g.periodic) : 0) +
+                            gather_table_bytes(g.pmax);
       int wpc = (int)((budget - std::min(tables, budget)) / (2 * rs.wb));
       if (wpc > 6) wpc = 6;
-      if (wpc >= 1) {
-        rs.wpc = wpc;
-        rs.use_ptab = ptab;
-        rs.smem = tables + 2 * rs.wb * wpc;
-        return true;
+      if (wpc > best) {
+        best = wpc;
+        best_ptab = ptab;
+        best_tables = tables;
       }
+    }
+    if (best >= 1) {
+      rs.wpc = best;
+      rs.use_ptab = best_ptab;
+      rs.smem = best_tables + 2 * rs.wb * best;
+      return true;
     }
   }
   return false;
