@@ -207,6 +207,42 @@ enkfmc_status build(enkfmc_handle* h) {
   h->ext_rows = row_off;
   h->band_elems = band_off;
   h->halo_rows = (int64_t)halo.size() / 2;
+  // within each block, the boundary rows in order of their predecessor count
+  // (stable): rows are independent, and neighbouring items with the same count
+  // let a warp run two of them in step (k_regress_pair)
+  {
+    std::vector<int> pcount(h->halo_rows);
+    for (int64_t it = 0; it < h->halo_rows; ++it) {
+      const Block& bb = h->blocks[halo[2 * it]];
+      const int loc = halo[2 * it + 1];
+      const int plane = bb.ey * bb.ex;
+      const int k = loc / plane;
+      const int yy = (loc - k * plane) / bb.ex;
+      const int xx = loc - k * plane - yy * bb.ex;
+      const int y = bb.lat_lo + yy, x = imod(bb.lon_lo + xx, g.nlon);
+      int cnt = 0;
+      for (int s = 0; s < g.pmax; ++s) {
+        int dk, dy, dx, kq, yq, xq, yy2, xx2;
+        slot_offset(s, g.r, g.vr, dk, dy, dx);
+        if (slot_pred_off(g, k, y, x, dk, dy, dx, kq, yq, xq) &&
+            in_ext(bb, g.nlon, yq, xq, yy2, xx2))
+          ++cnt;
+      }
+      pcount[it] = cnt;
+    }
+    std::vector<int64_t> order(h->halo_rows);
+    for (int64_t it = 0; it < h->halo_rows; ++it) order[it] = it;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t c) {
+      const int ba = halo[2 * a], bc = halo[2 * c];
+      return ba != bc ? ba < bc : pcount[a] < pcount[c];
+    });
+    std::vector<int32_t> sorted(halo.size());
+    for (int64_t i = 0; i < h->halo_rows; ++i) {
+      sorted[2 * i] = halo[2 * order[i]];
+      sorted[2 * i + 1] = halo[2 * order[i] + 1];
+    }
+    halo.swap(sorted);
+  }
   // the CUDA-core band kernels (FP64 problems, the single-precision path when
   // the tensor-core kernels do not apply, and the double-precision pool of an
   // FP32 problem) hold a panel and a window of the band in shared memory:
