@@ -110,13 +110,14 @@ __global__ void __launch_bounds__(256) k_assemble(const Geom g, const Block* __r
   for (int d = lane; d <= hb; d += 32) out[d] = (c + d < b.nb) ? col[d] : TB(0);
 }
 
-// Band assembly of one tile of 32 NH columns of one block from the pair list
-// of its shape.  Records {s1, s2, o(s2), d} sorted by d: row j = c - o(s2)
-// adds T[j][s1] T[j][s2] / D[j] to A[c + d][c] when row j lies in the block.
-//  * The rows the tile reads are staged once (source rows from the handle's
-//    per-row table): pmax coefficients, 1 (the row's own unit entry, slot pmax),
-//    then 1/D[j]; odd row stride, so lanes on consecutive columns hit distinct
-//    banks.
+// Band assembly of tiles of 32 NH columns of one block from the pair list of
+// its shape.  Records {s1, s2, o(s2), d} sorted by d: row j = c - o(s2) adds
+// T[j][s1] T[j][s2] / D[j] to A[c + d][c] when row j lies in the block.
+//  * A CTA walks consecutive tiles of one block; the rows a tile reads sit in
+//    a ring in shared memory (source rows from the handle's per-row table):
+//    pmax coefficients, 1 (the row's own unit entry, slot pmax), then 1/D[j];
+//    odd row stride, so lanes on consecutive columns hit distinct banks.  Each
+//    tile after the first stages only the rows it adds.
 //  * Warps take about equal chunks of the pair list, each chunk moved to start
 //    at a diagonal boundary, so every entry is summed by one warp in list
 //    order (deterministic).  Lane l owns columns c0 + l + 32 h (h < NH): every
@@ -136,36 +137,30 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
     const Geom g, const Block* __restrict__ blocks, const int4* __restrict__ pairs,
     const int32_t* __restrict__ srcrow, const T* __restrict__ Tg, const T* __restrict__ Dg,
     const T* __restrict__ Te, const T* __restrict__ De, const int32_t* __restrict__ obs_of,
-    const T* __restrict__ R, T* __restrict__ band, int hb_max) {
+    const T* __restrict__ R, T* __restrict__ band, int hb_max, int tiles_per_cta) {
   constexpr int kCols = 32 * NH;
   extern __shared__ __align__(16) unsigned char smem[];
   const Block b = blocks[blockIdx.y];
-  const int c0 = blockIdx.x * kCols;
-  if (c0 >= b.nb) return;
+  const int ntiles = (b.nb + kCols - 1) / kCols;
+  const int t0 = blockIdx.x * tiles_per_cta, t1 = min(ntiles, t0 + tiles_per_cta);
+  if (t0 >= t1) return;
   const int pmax = g.pmax, ldt = asm_ldt(pmax);
   const int hp1 = b.hb + 1, ldo = asm_ldo(hb_max);
-  const int nrow = asm_rows(kCols, b.hb, g.r);
-  const int jlo = c0 - g.r;
+  const int nrow = asm_rows(kCols, b.hb, g.r);  // rows a tile reads: the ring's length
   const int plane = b.ey * b.ex;
-  const int ncol = min(kCols, b.nb - c0);
   const int npair = b.npair;
   int4* Ps = reinterpret_cast<int4*>(smem);                           // [npair]
   T* Os = reinterpret_cast<T*>(Ps + npair);                           // [kCols][ldo]
-  T* Ts = Os + (size_t)kCols * ldo;                                   // [nrow][ldt]
+  T* Ts = Os + (size_t)kCols * ldo;                                   // [nrow][ldt] ring
   // slot-validity bit masks by level, latitude and longitude position in the box
   uint64_t* Mk = reinterpret_cast<uint64_t*>(Ts + (size_t)nrow * ldt + 1);  // 8-byte aligned below
   Mk = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(Mk) + 7) & ~(uintptr_t)7);
   uint64_t* My = Mk + b.nlev_b;
   uint64_t* Mx = My + b.ey;
-  int32_t* Sr = reinterpret_cast<int32_t*>(Mx + b.ex);                // [nrow] source rows
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kAsmThreads / 32;
 
   for (int q = threadIdx.x; q < npair; q += kAsmThreads) Ps[q] = pairs[b.pair_base + q];
   for (int e = threadIdx.x; e < kCols * ldo; e += kAsmThreads) Os[e] = T(0);
-  for (int jj = threadIdx.x; jj < nrow; jj += kAsmThreads) {
-    const int j = jlo + jj;
-    Sr[jj] = (j < 0 || j >= b.nb) ? INT32_MIN : srcrow[b.row_off + j];
-  }
   // bit s of Mk[k] / My[yy] / Mx[xx]: the row at offset s from that position
   // stays inside the box along that axis (bit pmax: the row itself); a warp per
   // position, lanes over the slots
@@ -187,99 +182,129 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble_pairs(
     }
     if (lane == 0) (axis == 0 ? Mk : (axis == 1 ? My : Mx))[pos] = m;
   }
-  __syncthreads();
-  // stage rows j in [jlo, jlo + nrow): a warp per row, lanes over the slots
-  // (slot pmax = 1, slot pmax + 1 = 1 / D[j]); the loads of kStage rows are
-  // issued before any is stored
-  constexpr int kStage = 4, kSlotRounds = 3;  // ldt <= 96 (pmax <= 63 here)
-  for (int jj0 = warp * kStage; jj0 < nrow; jj0 += nw * kStage) {
-    T v[kStage][kSlotRounds];
-#pragma unroll
-    for (int u = 0; u < kStage; ++u) {
-      const int jj = jj0 + u;
-      const int sr = jj < nrow ? Sr[jj] : INT32_MIN;
-#pragma unroll
-      for (int h = 0; h < kSlotRounds; ++h) {
-        const int sl = lane + 32 * h;
-        T x = T(0);
-        if (sr != INT32_MIN) {
-          if (sl < pmax) x = sr >= 0 ? Tg[(int64_t)sr * pmax + sl] : Te[(int64_t)(~sr) * pmax + sl];
-          else if (sl == pmax) x = T(1);
-          else if (sl == pmax + 1) x = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
-        }
-        v[u][h] = x;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < kStage; ++u) {
-      const int jj = jj0 + u;
-#pragma unroll
-      for (int h = 0; h < kSlotRounds; ++h) {
-        const int sl = lane + 32 * h;
-        if (jj < nrow && sl < ldt) Ts[jj * ldt + sl] = v[u][h];
-      }
-    }
-  }
-  __syncthreads();
 
-  // this lane's columns and the slots whose row lies in the block (bit s)
-  uint64_t vmask[NH];
+  // The CTA walks tiles t0 .. t1 - 1; tile t reads rows [c0 - r, c0 - r + nrow)
+  // (c0 = kCols t), kept in a ring: row j in slot (j - jbase) mod nrow.  The
+  // first tile stages all its rows, each later one the kCols rows it adds.
+  const int jbase = t0 * kCols - g.r;
+  // stage rows [jfrom, jto): a warp per row, lanes over the slots (slot pmax
+  // = 1, slot pmax + 1 = 1 / D[j]); the loads of kStage rows are issued
+  // before any is stored
+  auto stage = [&](int jfrom, int jto) {
+    constexpr int kStage = 4, kSlotRounds = 3;  // ldt <= 96 (pmax <= 63 here)
+    for (int j0 = jfrom + warp * kStage; j0 < jto; j0 += nw * kStage) {
+      T v[kStage][kSlotRounds];
 #pragma unroll
-  for (int h = 0; h < NH; ++h) {
-    const int cc = lane + 32 * h, c = c0 + cc;
-    vmask[h] = 0;
-    if (cc < ncol) {
-      const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
-      vmask[h] = Mk[kc] & My[yyc] & Mx[xxc];
+      for (int u = 0; u < kStage; ++u) {
+        const int j = j0 + u;
+        const int sr = (j < jto && j >= 0 && j < b.nb) ? srcrow[b.row_off + j] : INT32_MIN;
+#pragma unroll
+        for (int h = 0; h < kSlotRounds; ++h) {
+          const int sl = lane + 32 * h;
+          T x = T(0);
+          if (sr != INT32_MIN) {
+            if (sl < pmax)
+              x = sr >= 0 ? Tg[(int64_t)sr * pmax + sl] : Te[(int64_t)(~sr) * pmax + sl];
+            else if (sl == pmax) x = T(1);
+            else if (sl == pmax + 1) x = T(1) / (sr >= 0 ? Dg[sr] : De[~sr]);
+          }
+          v[u][h] = x;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kStage; ++u) {
+        const int j = j0 + u;
+        if (j >= jto) continue;
+        T* dst = Ts + (size_t)((j - jbase) % nrow) * ldt;
+#pragma unroll
+        for (int h = 0; h < kSlotRounds; ++h) {
+          const int sl = lane + 32 * h;
+          if (sl < ldt) dst[sl] = v[u][h];
+        }
+      }
     }
-  }
-  const T* Tc = Ts + (c0 + lane - jlo) * ldt;  // row c - o(s2) is Tc + 32 h ldt - o(s2) ldt
+  };
   const int per = (npair + nw - 1) / nw;
   auto at_diag_start = [&](int q) {  // first q' >= q that starts a diagonal
     if (q <= 0) return 0;
     while (q < npair && Ps[q].w == Ps[q - 1].w) ++q;
     return min(q, npair);
   };
+  __syncthreads();
   const int q0 = at_diag_start(warp * per), q1 = at_diag_start((warp + 1) * per);
-  T sum[NH];
-#pragma unroll
-  for (int h = 0; h < NH; ++h) sum[h] = T(0);
-  int dcur = q0 < q1 ? Ps[q0].w : 0;
-  for (int q = q0; q < q1; ++q) {
-    const int4 pr = Ps[q];
-    if (pr.w != dcur) {
-#pragma unroll
-      for (int h = 0; h < NH; ++h) {
-        Os[(lane + 32 * h) * ldo + dcur] = sum[h];
-        sum[h] = T(0);
-      }
-      dcur = pr.w;
-    }
-    const int off = pr.z * ldt;
+
+  for (int t = t0; t < t1; ++t) {
+    const int c0 = t * kCols;
+    const int ncol = min(kCols, b.nb - c0);
+    const int jhi = c0 - g.r + nrow;
+    stage(t == t0 ? c0 - g.r : jhi - kCols, jhi);
+    __syncthreads();
+
+    // this lane's columns and the slots whose row lies in the block (bit s)
+    uint64_t vmask[NH];
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
-      if ((vmask[h] >> pr.y) & 1) {
-        const T* tr = Tc + 32 * h * ldt - off;
-        sum[h] += (tr[pr.x] * tr[pmax + 1]) * tr[pr.y];
+      const int cc = lane + 32 * h, c = c0 + cc;
+      vmask[h] = 0;
+      if (cc < ncol) {
+        const int kc = c / plane, yyc = (c - kc * plane) / b.ex, xxc = c - kc * plane - yyc * b.ex;
+        vmask[h] = Mk[kc] & My[yyc] & Mx[xxc];
       }
     }
-  }
-  if (q0 < q1) {
+    // row c - o(s2) of column c = c0 + lane + 32 h sits in slot rel - o(s2)
+    // (mod nrow), rel = the slot of row c; o(s2) lies in (-nrow, r]
+    int rel[NH];
 #pragma unroll
-    for (int h = 0; h < NH; ++h) Os[(lane + 32 * h) * ldo + dcur] = sum[h];
+    for (int h = 0; h < NH; ++h) rel[h] = (c0 + lane + 32 * h - jbase) % nrow;
+    T sum[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) sum[h] = T(0);
+    int dcur = q0 < q1 ? Ps[q0].w : 0;
+    for (int q = q0; q < q1; ++q) {
+      const int4 pr = Ps[q];
+      if (pr.w != dcur) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          Os[(lane + 32 * h) * ldo + dcur] = sum[h];
+          sum[h] = T(0);
+        }
+        dcur = pr.w;
+      }
+#pragma unroll
+      for (int h = 0; h < NH; ++h) {
+        if ((vmask[h] >> pr.y) & 1) {
+          int sl = rel[h] - pr.z;
+          sl += sl < 0 ? nrow : 0;
+          sl -= sl >= nrow ? nrow : 0;
+          const T* tr = Ts + (size_t)sl * ldt;
+          sum[h] += (tr[pr.x] * tr[pmax + 1]) * tr[pr.y];
+        }
+      }
+    }
+    if (q0 < q1) {
+#pragma unroll
+      for (int h = 0; h < NH; ++h) Os[(lane + 32 * h) * ldo + dcur] = sum[h];
+    }
+    __syncthreads();
+    if (threadIdx.x < ncol) {  // H^T R^-1 H on the diagonal
+      const int cq = c0 + threadIdx.x;
+      const int kc = cq / plane, yyc = (cq - kc * plane) / b.ex,
+                xxc = cq - kc * plane - yyc * b.ex;
+      const int o =
+          obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
+      if (o >= 0) Os[threadIdx.x * ldo] += T(1) / R[o];
+    }
+    __syncthreads();
+    // write the tile's band columns (zeros past the block) and clear the
+    // output tile for the next one
+    T* out = band + b.band_off + (int64_t)c0 * hp1;
+    for (int col = warp; col < kCols; col += nw)
+      for (int d = lane; d < hp1; d += 32) {
+        if (col < ncol) out[(int64_t)col * hp1 + d] = (c0 + col + d < b.nb) ? Os[col * ldo + d] : T(0);
+        Os[col * ldo + d] = T(0);
+      }
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x < ncol) {  // H^T R^-1 H on the diagonal
-    const int cq = c0 + threadIdx.x;
-    const int kc = cq / plane, yyc = (cq - kc * plane) / b.ex, xxc = cq - kc * plane - yyc * b.ex;
-    const int o = obs_of[coords_label(g, b.var, kc, b.lat_lo + yyc, imod(b.lon_lo + xxc, g.nlon))];
-    if (o >= 0) Os[threadIdx.x * ldo] += T(1) / R[o];
-  }
-  __syncthreads();
-  T* out = band + b.band_off + (int64_t)c0 * hp1;
-  for (int col = warp; col < ncol; col += nw)
-    for (int d = lane; d < hp1; d += 32)
-      out[(int64_t)col * hp1 + d] = (c0 + col + d < b.nb) ? Os[col * ldo + d] : T(0);
 }
 
 // rhs[blk][m][loc] = (y_o + sqrt(R_o) Z[m][o] - Xb[m][l]) / R_o when component
@@ -376,9 +401,12 @@ cudaError_t launch_assemble_pairs(const Geom& g, const Block* blocks, int nblock
   cudaError_t e = cudaFuncSetAttribute(k_assemble_pairs<T, NH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((nb_max + 32 * NH - 1) / (32 * NH), nblock);
+  constexpr int kTilesPerCta = 8;
+  const int ntiles = (nb_max + 32 * NH - 1) / (32 * NH);
+  const dim3 grid((ntiles + kTilesPerCta - 1) / kTilesPerCta, nblock);
   k_assemble_pairs<T, NH><<<grid, kAsmThreads, smem, s>>>(g, blocks, pairs, srcrow, Tg, Dg, Te,
-                                                          De, obs_of, R, band, hb_max);
+                                                          De, obs_of, R, band, hb_max,
+                                                          kTilesPerCta);
   return cudaGetLastError();
 }
 
