@@ -44,9 +44,12 @@ __global__ void __launch_bounds__(128) k_adj_seed(const Geom g, const Block* __r
 }
 
 // a = T Lambda, b = T dX for 32 extended rows per thread block, written
-// row-major ([row][ldN]) together with row-major copies of dX and Lambda.
+// row-major ([row][ldN]) together with row-major copies of dX and Lambda;
+// kAbWarps warps over the members (the shared tile of the outputs, not the
+// threads, bounds the CTAs per SM).
+constexpr int kAbWarps = 8;
 template <typename T>
-__global__ void __launch_bounds__(kRows* kWarps) k_adj_ab(
+__global__ void __launch_bounds__(kRows* kAbWarps) k_adj_ab(
     const Geom g, const Block* __restrict__ blocks, const T* __restrict__ Tg,
     const T* __restrict__ Te, const T* __restrict__ lam, const T* __restrict__ dX,
     const T* __restrict__ dX2, T* __restrict__ aT, T* __restrict__ bT, T* __restrict__ dxT,
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(kRows* kWarps) k_adj_ab(
   if (lane < nr) {
     const int* nb_i = nbr + lane * pmax;
     const T* t_i = tv + lane * pmax;
-    for (int m = warp; m < N; m += kWarps) {
+    for (int m = warp; m < N; m += kAbWarps) {
       const int64_t base = b.row_off * N + (int64_t)m * b.nb;
       const T* lm = lam + base;
       const T* d1 = dX + base;
@@ -141,8 +144,9 @@ __device__ __forceinline__ void st4r(T* p, const T (&v)[4]) {
 // Ubar of the extended rows of one block, one warp per row c, members 4 lane ..
 // 4 lane + 3 (N <= 128).  The rows j that hold c are j = c - offset(s) for the
 // slots s whose predecessor, seen from j inside the block, is c; they are
-// listed in slot order (ballot compaction), then their terms are added in that
-// order: Ubar_c = f_c + sum (v_j[s] e_j - beta_j[s] f_j - kappa_j U_c).
+// listed in slot order (ballot compaction) with their scalars (-beta_j[s],
+// v_j[s], kappa_j, found by the lane of slot s), then their terms are added in
+// that order: Ubar_c = f_c + sum (v_j[s] e_j - beta_j[s] f_j - kappa_j U_c).
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_gather(
     const Geom g, const Block* __restrict__ blocks, const T* __restrict__ Tg,
@@ -152,8 +156,13 @@ __global__ void __launch_bounds__(256) k_adj_gather(
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   const int pmax = g.pmax, ldN = g.ldN;
-  int* cs = reinterpret_cast<int*>(smem) + (size_t)warp * 2 * pmax;  // [pmax] slot, [pmax] row
-  int* cj = cs + pmax;
+  // per warp: [pmax] block-relative row j, then [pmax] each of -beta_j[s], v_j[s], kappa_j
+  int* cj = reinterpret_cast<int*>(smem) + (size_t)warp * 4 * pmax;
+  T* ct = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smem) +
+                               (size_t)wpc * 4 * pmax * sizeof(int)) +
+          (size_t)warp * 3 * pmax;
+  T* cv = ct + pmax;
+  T* ck = cv + pmax;
   const Block b = blocks[blockIdx.y];
   const int c = blockIdx.x * wpc + warp;
   if (c >= b.nb) return;
@@ -184,8 +193,16 @@ __global__ void __launch_bounds__(256) k_adj_gather(
     const unsigned mask = __ballot_sync(0xffffffffu, locj >= 0);
     const int idx = nc + __popc(mask & ((1u << lane) - 1u));
     if (locj >= 0) {
-      cs[idx] = s;
+      // the row's scalars for this slot, read once by the lane that found it
+      const int kj = locj / plane, yyj = (locj - kj * plane) / b.ex;
+      const int xxj = locj - kj * plane - yyj * b.ex;
+      const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
+      const int64_t rowj = b.row_off + locj;
       cj[idx] = locj;
+      ct[idx] = in_interior(b, yj, xj) ? Tg[coords_label(g, v, kj, yj, xj) * pmax + s]
+                                       : Te[rowj * pmax + s];  // -beta_j[s]
+      cv[idx] = Vo[rowj * pmax + s];
+      ck[idx] = Ko[rowj];
     }
     nc += __popc(mask);
   }
@@ -196,14 +213,8 @@ __global__ void __launch_bounds__(256) k_adj_gather(
   ld4r(Fo + (b.row_off + c) * ldN + m0, acc);
   ld4r(U + coords_label(g, v, kc, yc, xc) * ldN + m0, u4);
   for (int i = 0; i < nc; ++i) {
-    const int s = cs[i], locj = cj[i];
-    const int kj = locj / plane, yyj = (locj - kj * plane) / b.ex;
-    const int xxj = locj - kj * plane - yyj * b.ex;
-    const int yj = b.lat_lo + yyj, xj = imod(b.lon_lo + xxj, g.nlon);
-    const int64_t rowj = b.row_off + locj;
-    const T t = in_interior(b, yj, xj) ? Tg[coords_label(g, v, kj, yj, xj) * pmax + s]
-                                       : Te[rowj * pmax + s];  // -beta_j[s]
-    const T vv = Vo[rowj * pmax + s], kap = Ko[rowj];
+    const int64_t rowj = b.row_off + cj[i];
+    const T t = ct[i], vv = cv[i], kap = ck[i];
     T e4[4], f4[4];
     ld4r(Eo + rowj * ldN + m0, e4);
     ld4r(Fo + rowj * ldN + m0, f4);
@@ -354,8 +365,8 @@ cudaError_t launch_adj_ab(const Geom& g, const Block* blocks, int nblock, int nb
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((nb_max + kRows - 1) / kRows, nblock);
-  k_adj_ab<T><<<grid, kRows * kWarps, smem, s>>>(g, blocks, Tg, Te, lam, dX, dX2, aT, bT, dxT,
-                                                 lamT);
+  k_adj_ab<T><<<grid, kRows * kAbWarps, smem, s>>>(g, blocks, Tg, Te, lam, dX, dX2, aT, bT,
+                                                   dxT, lamT);
   return cudaGetLastError();
 }
 
@@ -364,7 +375,7 @@ cudaError_t launch_adj_gather(const Geom& g, const Block* blocks, int nblock, in
                               const T* Tg, const T* Te, const T* U, const T* Eo, const T* Fo,
                               const T* Vo, const T* Ko, T* Ub, cudaStream_t s) {
   const int wpc = 8;
-  const size_t smem = sizeof(int) * 2 * (size_t)g.pmax * wpc;
+  const size_t smem = (sizeof(int) * 4 + sizeof(T) * 3) * (size_t)g.pmax * wpc;
   cudaError_t e = cudaFuncSetAttribute(k_adj_gather<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
