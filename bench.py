@@ -80,6 +80,8 @@ def parse_args(argv=None):
                     help="only the T127-shaped scale line (mixed against plain FP32)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batch of 256 uneven problems (one CUDA graph per cycle)")
+    ap.add_argument("--fwd-adj-only", action="store_true",
+                    help="only forward + adjoint on the headline workload, FP32")
     ap.add_argument("--tune", action="store_true",
                     help="autotune every batch shape missing from the tuning cache")
     ap.add_argument("--tune-max", type=int, default=64,
@@ -1038,6 +1040,18 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"batch": batch_line(args, torch.device("cuda", 0))}))
+        return
+    if args.fwd_adj_only:
+        import numpy as np
+        import torch
+
+        from paper_1606_00807_gb300 import binding as B
+        from synthetic import WORKLOADS, make_inputs
+        torch.cuda.set_device(0)
+        w = WORKLOADS[args.workload]
+        line = fwd_adj_line(args, w, make_inputs(w, np.float32), torch.device("cuda", 0),
+                            np.float32, B.FP32, torch.float32)
+        print(json.dumps({"fwd_adj_fp32": line}))
         return
     if args.cpu_sample:
         cpu_sample_main(args)

@@ -221,7 +221,10 @@ enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
 
 /* One full analysis from HOST buffers (same layouts as above): copies the
  * inputs to the device, runs estimate + assemble + analyze, copies Xa back,
- * and synchronises.  Returns the first numerical status as well. */
+ * and synchronises.  Returns the first numerical status as well.  y, Rdiag
+ * and Z are copied on a second stream of the handle while the estimate runs
+ * (page-locked host buffers let the copies overlap it); no copy is in flight
+ * when the call returns, on success or error. */
 enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
                                 const void* Rdiag, const void* Z, void* Xa);
 

@@ -437,6 +437,9 @@ void release(enkfmc_handle* h) {
                   h->d_fx,    h->d_fsq};
   for (void* b : bufs) dfree(b);
   if (h->f_stream) cudaStreamDestroy(h->f_stream);
+  if (h->c_stream) cudaStreamDestroy(h->c_stream);
+  if (h->c_start) cudaEventDestroy(h->c_start);
+  if (h->c_done) cudaEventDestroy(h->c_done);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   h->pool.clear();
 }
@@ -1048,13 +1051,34 @@ enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
     if ((st = dalloc(h, &h->d_T, es * (size_t)h->g.n * std::max(1, h->g.pmax)))) return st;
     if ((st = dalloc(h, &h->d_D, es * (size_t)h->g.n))) return st;
   }
+  if (h->m > 0 && !h->c_stream) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->c_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&h->c_start, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&h->c_done, cudaEventDisableTiming));
+  }
+  // X^b first on the handle's stream; y, R and Z follow on the copy stream
+  // once it is in (the two directions of the link are shared, so running them
+  // beside it would only delay the estimate), overlapping the estimate, which
+  // reads X^b alone; assemble and analyze wait for them
   CUDA_TRY(cudaMemcpyAsync(h->d_Xb, Xb, xbytes, cudaMemcpyHostToDevice, h->stream));
   if (h->m > 0) {
-    CUDA_TRY(cudaMemcpyAsync(h->d_y, y, obytes, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d_R, Rdiag, obytes, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(h->d_Z, Z, zbytes, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaEventRecord(h->c_start, h->stream));
+    CUDA_TRY(cudaStreamWaitEvent(h->c_stream, h->c_start, 0));
+    CUDA_TRY(cudaMemcpyAsync(h->d_y, y, obytes, cudaMemcpyHostToDevice, h->c_stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_R, Rdiag, obytes, cudaMemcpyHostToDevice, h->c_stream));
+    CUDA_TRY(cudaMemcpyAsync(h->d_Z, Z, zbytes, cudaMemcpyHostToDevice, h->c_stream));
+    CUDA_TRY(cudaEventRecord(h->c_done, h->c_stream));
   }
-  if ((st = enkfmc_estimate(h, h->d_Xb, h->d_T, h->d_D))) return st;
+  st = enkfmc_estimate(h, h->d_Xb, h->d_T, h->d_D);
+  if (h->m > 0) {
+    const cudaError_t e = cudaStreamWaitEvent(h->stream, h->c_done, 0);
+    if (st || e != cudaSuccess) {
+      // the caller may release y, R and Z on return: no copy stays in flight
+      (void)cudaStreamSynchronize(h->c_stream);
+      if (!st) st = check_launch(e);
+    }
+  }
+  if (st) return st;
   if ((st = enkfmc_assemble(h, h->d_Xb, h->d_T, h->d_D, h->d_R))) return st;
   if ((st = enkfmc_analyze(h, h->d_Xb, h->d_y, h->d_R, h->d_Z, h->d_Xa))) return st;
   CUDA_TRY(cudaMemcpyAsync(Xa, h->d_Xa, xbytes, cudaMemcpyDeviceToHost, h->stream));

@@ -265,8 +265,11 @@ struct enkfmc_handle {
   bool assembled = false;
   int64_t workspace_bytes = 0;
 
-  // host-cycle staging (allocated on first enkfmc_cycle_host)
+  // host-cycle staging (allocated on first enkfmc_cycle_host), and the copy
+  // stream that brings y, R and Z over while the estimate runs
   void *d_Xb = nullptr, *d_y = nullptr, *d_R = nullptr, *d_Z = nullptr, *d_Xa = nullptr;
+  cudaStream_t c_stream = nullptr;
+  cudaEvent_t c_start = nullptr, c_done = nullptr;
   void *d_T = nullptr, *d_D = nullptr;
 
   // inputs of the last enkfmc_analyze (the reverse pass reads them again)

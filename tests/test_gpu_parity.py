@@ -259,6 +259,14 @@ def test_deterministic_and_host_cycle_matches():
     Xa = np.empty_like(inp.Xb)
     a["handle"].cycle_host(inp.Xb, inp.y, inp.R, inp.Z, Xa)
     assert np.array_equal(Xa.astype(np.float64), a["Xa"])
+    # page-locked buffers: y, R and Z arrive on the copy stream during the
+    # estimate; twice in a row, the second call's copies behind the first's work
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    hXb, hy, hR, hZ = pin(inp.Xb), pin(inp.y), pin(inp.R), pin(inp.Z)
+    for _ in range(2):
+        hXa = torch.full_like(hXb, float("nan")).pin_memory()
+        a["handle"].cycle_host(hXb, hy, hR, hZ, hXa)
+        assert np.array_equal(hXa.numpy().astype(np.float64), a["Xa"])
     a["handle"].close()
 
 
