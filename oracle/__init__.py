@@ -25,11 +25,11 @@ there is no blocking, fusion or reordering beyond what the equations state.
 from .enkfmc import (Grid, Subdomain, anomalies, perturbed_observations, regress, estimate,
                      estimate_rows, subdomains, local_estimate, local_system, local_analysis,
                      analysis, assimilate, b_hat_dense, gain_form_analysis, dual_form_analysis,
-                     t_pattern_csr, rel_err)
+                     dual_increment, local_dual_analysis, t_pattern_csr, rel_err)
 from .cycling import forecast_shift, ensemble_sqerr, rmse_eq18, filter_cycles
 
 __all__ = ["Grid", "Subdomain", "anomalies", "perturbed_observations", "regress", "estimate",
            "estimate_rows", "subdomains", "local_estimate", "local_system", "local_analysis",
            "analysis", "assimilate", "b_hat_dense", "gain_form_analysis", "dual_form_analysis",
-           "t_pattern_csr", "rel_err", "forecast_shift", "ensemble_sqerr", "rmse_eq18",
+           "dual_increment", "local_dual_analysis", "t_pattern_csr", "rel_err", "forecast_shift", "ensemble_sqerr", "rmse_eq18",
            "filter_cycles"]

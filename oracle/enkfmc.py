@@ -297,35 +297,66 @@ def local_analysis(grid: Grid, sd: Subdomain, U, Xb, Ys, R, obs_idx, ridge_c):
     return solve_spd(A, rhs)
 
 
+def dual_increment(T, D: np.ndarray, hrows: Sequence[int], R: np.ndarray,
+                   innov: np.ndarray) -> np.ndarray:
+    """The dual increment (Eq. 12-13) for one domain: T Xt = D^(1/2) with T unit
+    lower triangular, V = H Xt (H selects the rows `hrows`),
+    delta X = Xt V^T (R + V V^T)^-1 innov, innov = Y^s - H X^b (m x N)."""
+    Td = T.toarray() if sp.issparse(T) else np.asarray(T, dtype=np.float64)
+    ne = Td.shape[0]
+    if len(hrows) == 0:
+        return np.zeros((ne, innov.shape[1]))
+    assert not np.any(np.triu(Td, 1)), "T must be lower triangular in the given order"
+    Xt = sla.solve_triangular(Td, np.diag(np.sqrt(np.asarray(D, dtype=np.float64))),
+                              lower=True, unit_diagonal=True)
+    V = Xt[np.asarray(hrows, dtype=np.int64)]
+    S = np.diag(np.asarray(R, dtype=np.float64)) + V @ V.T
+    return Xt @ (V.T @ np.linalg.solve(S, innov))
+
+
+def local_dual_analysis(grid: Grid, sd: Subdomain, U, Xb, Ys, R, obs_idx, ridge_c):
+    """delta X_k of a sub-domain in the dual form (Eq. 12-13) on its extended set,
+    with the same T_k, D_k (Algorithm 3) and local observations as the primal
+    form (local_system); T_k is lower triangular in the label order of sd.ext."""
+    T, D = local_estimate(grid, sd, U, ridge_c)
+    pos = {int(q): i for i, q in enumerate(sd.ext)}
+    o_loc = [o for o, c in enumerate(obs_idx) if int(c) in pos]
+    hrows = [pos[int(obs_idx[o])] for o in o_loc]
+    innov = Ys[o_loc] - Xb[sd.ext[hrows]] if o_loc else np.zeros((0, Xb.shape[1]))
+    return dual_increment(T, D, hrows, np.asarray(R, dtype=np.float64)[o_loc], innov)
+
+
 def analysis(grid: Grid, sds: List[Subdomain], Xb, Ys, R, obs_idx, ridge_c,
-             only: Sequence[int] | None = None):
+             only: Sequence[int] | None = None, form: str = "primal"):
     """Algorithm 2: every sub-domain analyses its extended set independently, the
     boundary is discarded and the interior is written into X^a (Eq. 10).
 
     Xb is n x N.  With `only`, just those sub-domains are analysed and the
-    returned X^a holds NaN elsewhere."""
+    returned X^a holds NaN elsewhere.  form: "primal" (Eq. 11) or "dual"
+    (Eq. 12-13)."""
     Xb = np.asarray(Xb, dtype=np.float64)
     U = anomalies(Xb)
     Xa = np.full_like(Xb, np.nan) if only is not None else Xb.copy()
+    local = {"primal": local_analysis, "dual": local_dual_analysis}[form]
     for sd in sds:
         if only is not None and sd.index not in only:
             continue
-        dX = local_analysis(grid, sd, U, Xb, Ys, R, obs_idx, ridge_c)
+        dX = local(grid, sd, U, Xb, Ys, R, obs_idx, ridge_c)
         pos = {int(q): i for i, q in enumerate(sd.ext)}
         rows = [pos[int(q)] for q in sd.interior]
         Xa[sd.interior] = Xb[sd.interior] + dX[rows]
     return Xa
 
 
-def assimilate(w, Xb_mm, y, R, Z_mm, obs_idx, only=None):
+def assimilate(w, Xb_mm, y, R, Z_mm, obs_idx, only=None, form: str = "primal"):
     """One analysis from member-major inputs (Xb [N][n], Z [N][m]) for a
     workload-like object with grid, radius, tile and ridge fields; returns
-    X^a member-major."""
+    X^a member-major (form as for analysis)."""
     grid = Grid.from_workload(w)
     sds = subdomains(grid, w.sub_lon, w.sub_lat)
     Ys = perturbed_observations(y, R, np.asarray(Z_mm, dtype=np.float64).T)
     Xa = analysis(grid, sds, np.asarray(Xb_mm, dtype=np.float64).T, Ys, R, obs_idx,
-                  w.ridge_c, only=only)
+                  w.ridge_c, only=only, form=form)
     return Xa.T
 
 
