@@ -19,7 +19,10 @@ from pinned host buffers, the SM clocks seen during the timed region, and the
 CPU baseline: the FP64 oracle timed on a bounded sample on one host thread and
 on all host cores; the oracle values of that sample give the accuracy report
 (max relative error of T, D, dX and X^a against the oracle).  Side lines: the
-plain FP64 form, and forward + adjoint (T63 with N = 80 and with N = 40).
+plain FP64 form, forward + adjoint (T63 with N = 80 and with N = 40), the batch
+of uneven problems, filter cycling, the accuracy study, and the dual form
+against the primal form on sparse networks (4% and 10% of the components
+observed).
 Multi-GPU (torchrun): every rank runs an independent problem (its own seed);
 value = cycles of all ranks / slowest rank's time.
 
@@ -80,6 +83,8 @@ def parse_args(argv=None):
                     help="only the T127-shaped scale line (mixed against plain FP32)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batch of 256 uneven problems (one CUDA graph per cycle)")
+    ap.add_argument("--dual-only", action="store_true",
+                    help="only the dual form against the primal form (sparse networks)")
     ap.add_argument("--fwd-adj-only", action="store_true",
                     help="only forward + adjoint on the headline workload, FP32")
     ap.add_argument("--tune", action="store_true",
@@ -612,6 +617,7 @@ def side_measurements(args, w, inp, value, dev):
                                                        dev, np.float64, B.FP64, torch.float64))
     guarded("batch", lambda: batch_line(args, dev))
     guarded("cycling", lambda: cycling_line(w, dev))
+    guarded("dual", lambda: dual_line(w, dev))
     guarded("accuracy_study", lambda: accuracy_study_line(dev))
     a, b = out.get("fwd_adj", {}), out.get("fwd_adj_plain_fp64", {})
     if "fwd_adj_cycles_per_s" in a and "fwd_adj_cycles_per_s" in b:
@@ -777,6 +783,71 @@ def cycling_line(w, dev, M=12, shift=1, inflation=1.1):
                 "note": "RMSE of Eq. 18 over the analysis-mean errors of the M times"}
     finally:
         h.close()
+
+
+def dual_line(w, dev, fracs=(0.04, 0.10), steps=5):
+    """The dual form (enkfmc_analyze_dual, Eq. 12-13) against the primal form
+    (enkfmc_assemble + enkfmc_analyze) on workload w in FP32, for sparse
+    observation networks (the fraction of observed components in `fracs`): both
+    from the same enkfmc_estimate, cycles/s of estimate + analysis by CUDA events,
+    the dual form's per-kind split, and the largest per-variable difference of
+    the two analyses (max |Xa_dual - Xa_primal| / max |Xa_primal|)."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00807_gb300 import binding as B
+    from synthetic import make_inputs
+
+    out = []
+    for frac in fracs:
+        wf = w.with_(obs_frac=frac)
+        inp = make_inputs(wf, np.float32)
+        stream = torch.cuda.Stream(device=dev)
+        h = B.Handle.from_workload(wf, precision=B.FP32, stream=stream.cuda_stream)
+        try:
+            h.set_observations(inp.obs_idx)
+            with torch.cuda.stream(stream):
+                put = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+                Xb, y, R, Z = put(inp.Xb), put(inp.y), put(inp.R), put(inp.Z)
+                T = torch.empty((wf.n, h.info.pmax), device=dev)
+                D = torch.empty(wf.n, device=dev)
+                Xp, Xd = torch.empty_like(Xb), torch.empty_like(Xb)
+
+            def primal():
+                h.estimate(Xb, T, D)
+                h.assemble(Xb, T, D, R)
+                h.analyze(Xb, y, R, Z, Xp)
+
+            def dual():
+                h.estimate(Xb, T, D)
+                h.analyze_dual(Xb, T, D, y, R, Z, Xd)
+
+            ms_p = _time_steps(primal, 2, steps, stream)
+            ms_d = _time_steps(dual, 2, steps, stream)
+            h.check("dual form")
+            h.profile(True)
+            h.profile_read()
+            _time_steps(dual, 0, 2, stream)
+            prof = h.profile_read()
+            h.profile(False)
+            primal()
+            dual()
+            torch.cuda.synchronize()
+            h.check("dual form")
+            diff = 0.0
+            for v in range(wf.nvar):
+                a = wf.var_offset(v)
+                e = a + wf.var_levels(v) * wf.nlat * wf.nlon
+                ref = Xp[:, a:e]
+                diff = max(diff, float((Xd[:, a:e] - ref).abs().max() / ref.abs().max()))
+            out.append({"workload": wf.name, "obs_frac": frac, "m": int(inp.y.size),
+                        "primal_cycles_per_s": 1e3 / ms_p, "dual_cycles_per_s": 1e3 / ms_d,
+                        "primal_ms": ms_p, "dual_ms": ms_d, "dual_speedup": ms_p / ms_d,
+                        "max_rel_diff_vs_primal": diff,
+                        "kernels_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}})
+        finally:
+            h.close()
+    return out
 
 
 def batch_line(args, dev):
@@ -1040,6 +1111,14 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"batch": batch_line(args, torch.device("cuda", 0))}))
+        return
+    if args.dual_only:
+        import torch
+
+        from synthetic import WORKLOADS
+        torch.cuda.set_device(0)
+        print(json.dumps({"dual": dual_line(WORKLOADS[args.workload],
+                                            torch.device("cuda", 0))}))
         return
     if args.fwd_adj_only:
         import numpy as np

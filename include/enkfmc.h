@@ -219,6 +219,34 @@ enkfmc_status enkfmc_assemble(enkfmc_handle* h, const void* Xb, const void* Tval
 enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
                              const void* Rdiag, const void* Z, void* Xa);
 
+/* Steps (b) and (c) in the dual form, Eq. 12-13: per (sub-domain, variable)
+ * block, with the block's T (boundary rows re-estimated from the local
+ * samples, as in enkfmc_assemble) and D, and the m_b observations inside its
+ * extended set,
+ *   Z = T^-T H^T (n_b x m_b),   (R + Z^T D Z) W = Y^s - H X^b (m_b x N),
+ *   dX = T^-1 D Z W  =  X~ V^T (R + V V^T)^-1 (Y^s - H X^b),
+ * with T X~ = D^1/2 and V = H X~; Xa = Xb + dX on the interiors.  The same
+ * analysis as enkfmc_assemble + enkfmc_analyze (exactly, up to rounding),
+ * without the band matrix: its cost grows with m_b instead of the band, so it
+ * is the cheaper form for sparse networks.  Arguments as for enkfmc_assemble
+ * and enkfmc_analyze (Tvals, D from enkfmc_estimate; Xb the same ensemble).
+ * Arithmetic: the problem's precision, except single-precision problems with
+ * rows where 2p > N (the regressions' double-precision rule), whose dual
+ * arithmetic is double (their T^-1 and R + Z^T D Z lose the single-precision
+ * digits; inputs and Xa stay single precision).  Requires
+ * enkfmc_set_observations.  Returns EINVAL, with nothing queued, when a
+ * block's observation system (m_b (m_b + 1) / 2 + max(m_b N, 32 m_b)
+ * elements; m_b up to about 260 at N = 80 in single precision) or a
+ * triangular solve's ring ((vr ey + r + 1) ex rows of 32 elements, ey x ex
+ * the extended box) exceeds 227 KB of shared memory, or the stencil has more
+ * than 128 slots; ENOTSPD (status) when
+ * R + Z^T D Z is not positive definite for a block (its increment is then
+ * zero).  Afterwards enkfmc_analyze needs a new enkfmc_assemble, and
+ * enkfmc_analyze_adjoint does not apply to this analysis. */
+enkfmc_status enkfmc_analyze_dual(enkfmc_handle* h, const void* Xb, const void* Tvals,
+                                  const void* D, const void* y, const void* Rdiag,
+                                  const void* Z, void* Xa);
+
 /* One full analysis from HOST buffers (same layouts as above): copies the
  * inputs to the device, runs estimate + assemble + analyze, copies Xa back,
  * and synchronises.  Returns the first numerical status as well.  y, Rdiag
@@ -413,7 +441,10 @@ enum {
   ENKFMC_K_FORECAST = 13,   /* filter cycling: the forecast operator (advection) */
   ENKFMC_K_SQERR = 14,      /* filter cycling: squared error of the ensemble mean
                                (Eq. 18)                                          */
-  ENKFMC_NKERNEL = 15
+  ENKFMC_K_DUAL_Z = 15,     /* dual form: Z = T^-T H^T per block (Eq. 13)         */
+  ENKFMC_K_DUAL_OBS = 16,   /* dual form: (R + Z^T D Z) W = Y^s - H X^b (Eq. 12)  */
+  ENKFMC_K_DUAL_APPLY = 17, /* dual form: dX = T^-1 D Z W (Eq. 12)               */
+  ENKFMC_NKERNEL = 18
 };
 
 /* Kernel timing.  Work is launched in calls of one kernel kind; a call runs

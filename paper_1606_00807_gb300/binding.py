@@ -51,6 +51,8 @@ SIGNATURES = {
     "enkfmc_estimate": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
     "enkfmc_assemble": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_analyze": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "enkfmc_analyze_dual": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_void_p]),
     "enkfmc_cycle_host": (c_int32, [_H, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "enkfmc_forecast_shift": (c_int32, [_H, c_void_p, c_void_p, c_int32, c_int32, c_double]),
     "enkfmc_ensemble_sqerr": (c_int32, [_H, c_void_p, c_void_p, c_void_p]),
@@ -79,7 +81,7 @@ SIGNATURES = {
     "enkfmc_estimate_noalloc": (c_int32, [POINTER(enkfmc_problem), c_void_p, c_void_p, c_void_p,
                                           c_void_p]),
 }
-NKERNEL = 15
+NKERNEL = 18
 FLAG_NO_SOLVE_REFINEMENT = 1
 FLAG_SIMT_BAND = 2
 FLAG_PLAIN_FP32 = 4
@@ -219,6 +221,10 @@ class Handle:
     def analyze(self, Xb, y, R, Z, Xa):
         _check(self.lib.enkfmc_analyze(self.h, _ptr(Xb), _ptr(y), _ptr(R), _ptr(Z), _ptr(Xa)),
                "enkfmc_analyze")
+
+    def analyze_dual(self, Xb, Tvals, D, y, R, Z, Xa):
+        _check(self.lib.enkfmc_analyze_dual(self.h, _ptr(Xb), _ptr(Tvals), _ptr(D), _ptr(y),
+                                            _ptr(R), _ptr(Z), _ptr(Xa)), "enkfmc_analyze_dual")
 
     def analyze_adjoint(self, Xa_bar, y_bar, R_bar, Xb_bar):
         _check(self.lib.enkfmc_analyze_adjoint(self.h, _ptr(Xa_bar), _ptr(y_bar), _ptr(R_bar),

@@ -344,6 +344,7 @@ enkfmc_status build(enkfmc_handle* h) {
     }
   }
   compute_work(h, p_global, p_ext);
+  h->p_ext = std::move(p_ext);
 
   enkfmc_status st;
   if ((st = dalloc(h, &h->d_blocks, sizeof(Block) * h->blocks.size()))) return st;
@@ -434,7 +435,9 @@ void release(enkfmc_handle* h) {
                   h->d_D,     h->d_lam,     h->d_aT,  h->d_bT,      h->d_dxT,    h->d_lamT,
                   h->d_Eo,    h->d_Fo,      h->d_Vo,  h->d_Ko,  h->d_U64,     h->d_C64, h->d_W,      h->d_bfail,  h->d_fb_cnt,
                   h->d_fb_blocks, h->d_fb_band, h->d_c1max, h->d_sqp, h->d_fy, h->d_fZ,
-                  h->d_fx,    h->d_fsq};
+                  h->d_fx,    h->d_fsq,     h->d_dobs, h->d_dob_off, h->d_dzoff, h->d_obs_idx,
+                  h->d_dz,    h->d_dw,      h->d_dx64, h->d_dpred, h->d_dsucc,
+                  h->d_dq};
   for (void* b : bufs) dfree(b);
   if (h->f_stream) cudaStreamDestroy(h->f_stream);
   if (h->c_stream) cudaStreamDestroy(h->c_stream);
@@ -871,6 +874,169 @@ enkfmc_status run_adjoint(enkfmc_handle* h, const T* Xa_bar, T* y_bar, T* R_bar,
   });
 }
 
+// Dual form set-up for the current observations: per block the observations
+// inside its extended set in solve order (label order: segment by segment,
+// inside a segment from the columns past the longitude seam), the offsets of
+// the blocks' lists and Z buffers, the solves' ring W (rows: a row and its
+// predecessors lie less than (vr ey + r + 1) ex positions apart), the
+// buffers, and the work model of the three dual kinds.  EINVAL (nothing
+// queued) when the observation systems or the rings exceed shared memory.
+enkfmc_status build_dual(enkfmc_handle* h) {
+  const Geom& g = h->g;
+  // the arithmetic: double for single-precision problems with rows where
+  // 2p > N (the precision rule of the regressions; there T^-1 and R + Z^T D Z
+  // need more than single precision), else the problem's
+  const bool fp64 = !is_fp64(h) && has_fp64_rows(g, true);
+  const size_t es = fp64 ? 8 : h->esize;
+  std::vector<int2> dobs;
+  std::vector<int64_t> off((size_t)h->nblock + 1, 0), zoff((size_t)h->nblock, 0);
+  int mb_max = 0, W = 1;
+  int64_t zsum = 0;
+  size_t prow = 0;
+  const double N = g.N;
+  double fz = 0, fo = 0, fa = 0, bz = 0, bw = 0, pz = 0;
+  for (int bi = 0; bi < h->nblock; ++bi) {
+    const Block& b = h->blocks[bi];
+    const int npre = std::min(b.ex, g.nlon - b.lon_lo), plane = b.ey * b.ex;
+    double pre = 0;  // predecessors of the rows up to position t
+    int mb = 0;
+    for (int t = 0; t < b.nb; ++t) {
+      const int seg = t / b.ex;
+      int xx = t - seg * b.ex + npre;
+      if (xx >= b.ex) xx -= b.ex;
+      const int loc = seg * b.ex + xx, k = loc / plane, yy = (loc - k * plane) / b.ex;
+      const int pe = h->p_ext[prow + (size_t)loc];
+      pre += pe >= 0 ? pe : -pe - 1;
+      const int o = h->obs_of_host[(size_t)coords_label(g, b.var, k, b.lat_lo + yy,
+                                                        imod(b.lon_lo + xx, g.nlon))];
+      if (o >= 0) {
+        dobs.push_back(make_int2(t, o));
+        fz += 2.0 * pre;  // column o: the rows up to its own position
+        ++mb;
+      }
+    }
+    prow += (size_t)b.nb;
+    off[(size_t)bi + 1] = (int64_t)dobs.size();
+    zoff[(size_t)bi] = zsum;
+    zsum += (int64_t)b.nb * mb;
+    mb_max = std::max(mb_max, mb);
+    W = std::max(W, (g.vr * b.ey + g.r + 1) * b.ex);
+    const double nb = b.nb, m = mb;
+    fo += nb * m * (m + 1) + m * m * m / 3.0 + 2.0 * m * m * N;
+    fa += 2.0 * nb * m * N + nb * N + 2.0 * N * pre;
+    bz += nb * m;
+    bw += m * N;
+    pz += pre;
+  }
+  W = std::min(W, std::max(1, h->nb_max));
+  const size_t lim = 227 * 1024;
+  const size_t ssolve = es == 8 ? dual_solve_smem<double>(W, g.pmax)
+                                : dual_solve_smem<float>(W, g.pmax);
+  const size_t sobs = mb_max == 0 ? 0
+                      : es == 8   ? dual_obs_smem<double>(mb_max, g.N)
+                                  : dual_obs_smem<float>(mb_max, g.N);
+  if (ssolve > lim || sobs > lim || g.pmax > kDualMaxSlots) return ENKFMC_EINVAL;
+  std::vector<int32_t> oidx((size_t)std::max<int64_t>(h->m, 0), 0);
+  for (size_t l = 0; l < h->obs_of_host.size(); ++l)
+    if (h->obs_of_host[l] >= 0) oidx[(size_t)h->obs_of_host[l]] = (int32_t)l;
+  void* old[] = {h->d_dobs, h->d_dob_off, h->d_dzoff, h->d_obs_idx, h->d_dz, h->d_dw};
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // buffers of an earlier set may be in use
+  for (void* p : old) dfree(p);
+  h->d_dobs = nullptr;
+  h->d_dob_off = h->d_dzoff = nullptr;
+  h->d_obs_idx = nullptr;
+  h->d_dz = h->d_dw = nullptr;
+  enkfmc_status st;
+  if ((st = dalloc(h, &h->d_dobs, sizeof(int2) * dobs.size()))) return st;
+  if ((st = dalloc(h, &h->d_dob_off, sizeof(int64_t) * off.size()))) return st;
+  if ((st = dalloc(h, &h->d_dzoff, sizeof(int64_t) * zoff.size()))) return st;
+  if ((st = dalloc(h, &h->d_obs_idx, sizeof(int32_t) * oidx.size()))) return st;
+  if ((st = dalloc(h, &h->d_dz, es * (size_t)zsum))) return st;
+  if ((st = dalloc(h, &h->d_dw, es * (size_t)dobs.size() * g.N))) return st;
+  if (fp64 && !h->d_dx64 &&
+      (st = dalloc(h, &h->d_dx64, sizeof(double) * (size_t)h->ext_rows * g.N)))
+    return st;
+  const size_t tab = dual_table_bytes(es, g.pmax) * (size_t)h->ext_rows;
+  if (!h->d_dpred && (st = dalloc(h, &h->d_dpred, tab))) return st;
+  if (!h->d_dsucc && (st = dalloc(h, &h->d_dsucc, tab))) return st;
+  if (!h->d_dq && (st = dalloc(h, &h->d_dq, es * (size_t)h->ext_rows * g.N))) return st;
+  h->dual_fp64 = fp64;
+  if (!dobs.empty())
+    CUDA_TRY(cudaMemcpy(h->d_dobs, dobs.data(), sizeof(int2) * dobs.size(),
+                        cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_dob_off, off.data(), sizeof(int64_t) * off.size(),
+                      cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_dzoff, zoff.data(), sizeof(int64_t) * zoff.size(),
+                      cudaMemcpyHostToDevice));
+  if (!oidx.empty())
+    CUDA_TRY(cudaMemcpy(h->d_obs_idx, oidx.data(), sizeof(int32_t) * oidx.size(),
+                        cudaMemcpyHostToDevice));
+  h->dual_mb_max = mb_max;
+  h->dual_W = W;
+  h->work_flops[ENKFMC_K_DUAL_Z] = fz;
+  h->work_bytes[ENKFMC_K_DUAL_Z] = (double)es * (bz + pz);
+  h->work_flops[ENKFMC_K_DUAL_OBS] = fo;
+  h->work_bytes[ENKFMC_K_DUAL_OBS] = (double)es * (bz + bw + 2.0 * bw);
+  h->work_flops[ENKFMC_K_DUAL_APPLY] = fa;
+  h->work_bytes[ENKFMC_K_DUAL_APPLY] =
+      (double)es * (bz + bw + pz + 2.0 * N * (double)h->ext_rows);
+  h->dual_ready = true;
+  return ENKFMC_OK;
+}
+
+// The dual kernels with inputs TI and arithmetic TC; dX: the increments (TC).
+template <typename TI, typename TC>
+enkfmc_status run_dual_kernels(enkfmc_handle* h, const TI* Xb, const TI* Tv, const TI* D,
+                               const TI* y, const TI* R, const TI* Z, TI* Xa, TC* dX) {
+  const Geom& g = h->g;
+  enkfmc_status st = timed(h, ENKFMC_K_DUAL_Z, [&](int* nk) {
+    return launch_dual_z<TI, TC>(g, h->d_blocks, h->nblock, h->nb_max, h->dual_mb_max,
+                                 h->d_dobs, h->d_dob_off, h->d_dzoff, Tv, (const TI*)h->d_Te,
+                                 h->d_dpred, h->d_dsucc, (TC*)h->d_dz, h->dual_W, h->stream, nk);
+  });
+  if (st) return st;
+  st = timed(h, ENKFMC_K_DUAL_OBS, [&] {
+    return launch_dual_obs<TI, TC>(g, h->d_blocks, h->nblock, h->dual_mb_max, h->d_dobs,
+                                   h->d_dob_off, h->d_dzoff, h->d_obs_idx, h->m, Xb, y, R, Z, D,
+                                   (const TI*)h->d_De, (const TC*)h->d_dz, (TC*)h->d_dw,
+                                   h->d_status, h->stream);
+  });
+  if (st) return st;
+  st = timed(h, ENKFMC_K_DUAL_APPLY, [&](int* nk) {
+    return launch_dual_apply<TI, TC>(g, h->d_blocks, h->nblock, h->nb_max, h->d_dob_off,
+                                     h->d_dzoff, (const TC*)h->d_dz, (const TC*)h->d_dw, D,
+                                     (const TI*)h->d_De, h->d_dpred, (TC*)h->d_dq, dX,
+                                     h->dual_W, h->stream, nk);
+  });
+  if (st) return st;
+  return timed(h, ENKFMC_K_WRITEBACK, [&] {
+    return launch_writeback<TI, TC>(g, h->d_blocks, h->nsubx, h->prob.sub_lon, h->prob.sub_lat,
+                                    Xb, (const TC*)dX, (const TC*)nullptr, Xa, h->stream);
+  });
+}
+
+template <typename T>
+enkfmc_status run_analyze_dual(enkfmc_handle* h, const T* Xb, const T* Tv, const T* D,
+                               const T* y, const T* R, const T* Z, T* Xa) {
+  enkfmc_status st;
+  if (!h->dual_ready && (st = build_dual(h))) return st;
+  const Geom& g = h->g;
+  // boundary rows of every block from its local samples (Algorithm 3), as for
+  // the primal assembly
+  if ((st = run_statistics<T>(h, Xb))) return st;
+  st = timed(h, ENKFMC_K_REGRESS_HALO, [&](int* nk) {
+    return launch_regressions<T>(g, stats_of<T>(h), h->d_halo, h->halo_rows, h->d_blocks,
+                                 (T*)h->d_Te, (T*)h->d_De, h->prob.ridge_c, h->d_status,
+                                 h->stream, nk);
+  });
+  if (st) return st;
+  if constexpr (std::is_same<T, float>::value) {
+    if (h->dual_fp64)
+      return run_dual_kernels<float, double>(h, Xb, Tv, D, y, R, Z, Xa, h->d_dx64);
+  }
+  return run_dual_kernels<T, T>(h, Xb, Tv, D, y, R, Z, Xa, (T*)h->d_rhs);
+}
+
 }  // namespace
 
 extern "C" {
@@ -981,7 +1147,9 @@ enkfmc_status enkfmc_set_observations(enkfmc_handle* h, const int32_t* obs_idx, 
                       cudaMemcpyHostToDevice));
   h->m = m;
   h->assembled = false;
-  compute_obs_work(h, of);
+  h->dual_ready = false;
+  h->obs_of_host = std::move(of);
+  compute_obs_work(h, h->obs_of_host);
   return ENKFMC_OK;
 }
 
@@ -1083,6 +1251,25 @@ enkfmc_status enkfmc_cycle_host(enkfmc_handle* h, const void* Xb, const void* y,
   if ((st = enkfmc_analyze(h, h->d_Xb, h->d_y, h->d_R, h->d_Z, h->d_Xa))) return st;
   CUDA_TRY(cudaMemcpyAsync(Xa, h->d_Xa, xbytes, cudaMemcpyDeviceToHost, h->stream));
   return enkfmc_get_status(h, nullptr);
+}
+
+enkfmc_status enkfmc_analyze_dual(enkfmc_handle* h, const void* Xb, const void* Tvals,
+                                  const void* D, const void* y, const void* Rdiag,
+                                  const void* Z, void* Xa) {
+  if (!h || !Xb || !Tvals || !D || !Xa || Xa == Xb) return ENKFMC_EINVAL;
+  if (h->m < 0) return ENKFMC_ESTATE;
+  if (h->m > 0 && (!y || !Rdiag || !Z)) return ENKFMC_EINVAL;
+  // the boundary rows are re-estimated here: the band of the last assembly no
+  // longer matches them, and the reverse pass follows the primal form only
+  h->assembled = false;
+  h->analyzed = false;
+  if (is_fp64(h))
+    return run_analyze_dual<double>(h, (const double*)Xb, (const double*)Tvals,
+                                    (const double*)D, (const double*)y, (const double*)Rdiag,
+                                    (const double*)Z, (double*)Xa);
+  return run_analyze_dual<float>(h, (const float*)Xb, (const float*)Tvals, (const float*)D,
+                                 (const float*)y, (const float*)Rdiag, (const float*)Z,
+                                 (float*)Xa);
 }
 
 enkfmc_status enkfmc_analyze_adjoint(enkfmc_handle* h, const void* Xa_bar, void* y_bar,
@@ -1220,7 +1407,8 @@ const char* enkfmc_kernel_name(int32_t kind) {
                                               "assemble",  "bandchol",  "rhs",
                                               "bandsolve", "writeback", "covtable",
                                               "residual",  "adjoint",   "adj_regress",
-                                              "fp64_blocks", "forecast", "sqerr"};
+                                              "fp64_blocks", "forecast", "sqerr",
+                                              "dual_z",    "dual_obs",  "dual_apply"};
   return (kind >= 0 && kind < ENKFMC_NKERNEL) ? names[kind] : "unknown";
 }
 

@@ -270,6 +270,25 @@ struct enkfmc_handle {
   void *d_Xb = nullptr, *d_y = nullptr, *d_R = nullptr, *d_Z = nullptr, *d_Xa = nullptr;
   cudaStream_t c_stream = nullptr;
   cudaEvent_t c_start = nullptr, c_done = nullptr;
+
+  // dual form (enkfmc_analyze_dual): per block the observations inside the
+  // extended set in solve order {position, observation}, the offsets of the
+  // blocks' lists and of their Z = T^-T H^T, and the Z and W buffers; built on
+  // the first call after enkfmc_set_observations
+  std::vector<int32_t> obs_of_host;  // [n] host copy of d_obs_of
+  std::vector<int> p_ext;            // predecessors per extended row (-p-1: boundary)
+  bool dual_ready = false;
+  bool dual_fp64 = false;        // single-precision problem, dual arithmetic in double
+  int32_t dual_mb_max = 0, dual_W = 0;
+  double* d_dx64 = nullptr;      // its increments [ext_rows][N] in double
+  void *d_dpred = nullptr, *d_dsucc = nullptr;  // the solves' term tables
+  void* d_dq = nullptr;          // Q = D Z W [ext_rows][N] (arithmetic type)
+  int2* d_dobs = nullptr;
+  int64_t* d_dob_off = nullptr;  // [nblock + 1]
+  int64_t* d_dzoff = nullptr;    // [nblock]
+  int32_t* d_obs_idx = nullptr;  // [m] observed component of each observation
+  void* d_dz = nullptr;
+  void* d_dw = nullptr;
   void *d_T = nullptr, *d_D = nullptr;
 
   // inputs of the last enkfmc_analyze (the reverse pass reads them again)
@@ -437,10 +456,11 @@ cudaError_t launch_bandsolve_tc(const Block* blocks, int nblock, int hb_max, int
                                 const float* band, const float* invdiag, float* rhs,
                                 int32_t* status, cudaStream_t s, const int* skip = nullptr);
 
-// Xa = Xb + dX (+ dX2 when not null) on sub-domain interiors.
-template <typename T>
+// Xa = Xb + dX (+ dX2 when not null) on sub-domain interiors; TD the
+// increments' type (float with double increments, or the same as T).
+template <typename T, typename TD = T>
 cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
-                             int sub_lat, const T* Xb, const T* dX, const T* dX2, T* Xa,
+                             int sub_lat, const T* Xb, const TD* dX, const TD* dX2, T* Xa,
                              cudaStream_t s);
 
 // Reverse pass (k_adjoint.cu and k_adj_regress in k_estimate.cu).
@@ -487,6 +507,44 @@ cudaError_t launch_refine_residual(const Geom& g, const Block* blocks, int nbloc
                                    const float* rhs_in, float* res, cudaStream_t s);
 // y += x over `count` elements.
 cudaError_t launch_accumulate(float* y, const float* x, int64_t count, cudaStream_t s);
+
+// Dual form of the sub-domain analysis (k_dual.cu, Eq. 12-13): Z = T^-T H^T,
+// then W = (R + Z^T D Z)^-1 (Y^s - H X^b), then dX = T^-1 D Z W into the
+// increment buffer (the primal solve's layout).  dobs: per block its
+// observations {solve position, observation index} from dob_off[block]; Z of
+// a block [nb][mb] at zoff[block]; W of a block [mb][N] at N dob_off[block];
+// W: the solves' ring (rows).
+constexpr int kDualMaxSlots = 128;  // stencil slots the dual solves handle (4 per lane)
+template <typename T>
+size_t dual_solve_smem(int W, int pmax);
+template <typename T>
+size_t dual_obs_smem(int mb, int N);
+// TI: the type of the inputs (T, D, X^b, y, R, Z); TC: the arithmetic and
+// the type of Z, W and dX (double for single-precision problems with rows
+// where 2p > N, whose T^-1 and R + Z^T D Z need it, else TI).
+// Bytes of one row of the solves' term tables ({distance, coefficient} of the
+// arithmetic type, pmax entries padded to 16 bytes).
+size_t dual_table_bytes(size_t esize, int pmax);
+// The term tables pred and succ ([ext rows][pmax] each, in solve order), then
+// Z = T^-T H^T.
+template <typename TI, typename TC>
+cudaError_t launch_dual_z(const Geom& g, const Block* blocks, int nblock, int nb_max, int mb_max,
+                          const int2* dobs, const int64_t* dob_off, const int64_t* zoff,
+                          const TI* Tg, const TI* Te, void* pred, void* succ, TC* Zb, int W,
+                          cudaStream_t s, int* nk);
+template <typename TI, typename TC>
+cudaError_t launch_dual_obs(const Geom& g, const Block* blocks, int nblock, int mb_max,
+                            const int2* dobs, const int64_t* dob_off, const int64_t* zoff,
+                            const int32_t* obs_idx, int64_t m, const TI* Xb, const TI* y,
+                            const TI* R, const TI* Zp, const TI* Dg, const TI* De, const TC* Zb,
+                            TC* Wb, int32_t* status, cudaStream_t s);
+// Q = D Z W, then dX = T^-1 Q (Q and dX: [ext rows][N] in the primal
+// solve's layout).
+template <typename TI, typename TC>
+cudaError_t launch_dual_apply(const Geom& g, const Block* blocks, int nblock, int nb_max,
+                              const int64_t* dob_off, const int64_t* zoff, const TC* Zb,
+                              const TC* Wb, const TI* Dg, const TI* De, const void* pred, TC* Q,
+                              TC* dX, int W, cudaStream_t s, int* nk);
 
 // True when the CUDA-core band Cholesky and solves (k_band.cu) can launch for
 // half-bandwidth hb with elements of esize bytes.

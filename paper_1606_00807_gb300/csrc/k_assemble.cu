@@ -337,13 +337,14 @@ __global__ void __launch_bounds__(128) k_rhs(const Geom g, const Block* __restri
 }
 
 // Xa[m][l] = Xb[m][l] + dX[blk][m][loc] for the sub-domain whose interior
-// holds l (Eq. 10; interiors are disjoint, so plain stores suffice).
-template <typename T>
+// holds l (Eq. 10; interiors are disjoint, so plain stores suffice).  TD: the
+// increments' type (rounded to T when added).
+template <typename T, typename TD>
 __global__ void __launch_bounds__(256) k_writeback(const Geom g, const Block* __restrict__ blocks,
                                                    int nsubx, int sub_lon, int sub_lat,
                                                    const T* __restrict__ Xb,
-                                                   const T* __restrict__ dX,
-                                                   const T* __restrict__ dX2, T* __restrict__ Xa) {
+                                                   const TD* __restrict__ dX,
+                                                   const TD* __restrict__ dX2, T* __restrict__ Xa) {
   const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= g.n) return;
   const int m = blockIdx.y;
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(256) k_writeback(const Geom g, const Block* __
   const int loc = (k * b.ey + (y - b.lat_lo)) * b.ex + imod(x - b.lon_lo, g.nlon);
   const int64_t i = (int64_t)m * g.n + l;
   const int64_t e = b.row_off * g.N + (int64_t)m * b.nb + loc;
-  Xa[i] = dX2 ? Xb[i] + (dX[e] + dX2[e]) : Xb[i] + dX[e];
+  Xa[i] = dX2 ? Xb[i] + (T)(dX[e] + dX2[e]) : Xb[i] + (T)dX[e];
 }
 
 }  // namespace
@@ -419,12 +420,12 @@ cudaError_t launch_rhs(const Geom& g, const Block* blocks, int nblock, int nb_ma
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename TD>
 cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
-                             int sub_lat, const T* Xb, const T* dX, const T* dX2, T* Xa,
+                             int sub_lat, const T* Xb, const TD* dX, const TD* dX2, T* Xa,
                              cudaStream_t s) {
   const dim3 grid((unsigned)((g.n + 255) / 256), g.N);
-  k_writeback<T><<<grid, 256, 0, s>>>(g, blocks, nsubx, sub_lon, sub_lat, Xb, dX, dX2, Xa);
+  k_writeback<T, TD><<<grid, 256, 0, s>>>(g, blocks, nsubx, sub_lon, sub_lat, Xb, dX, dX2, Xa);
   return cudaGetLastError();
 }
 
@@ -440,11 +441,14 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
   template cudaError_t launch_rhs<T>(const Geom&, const Block*, int, int, const int32_t*,       \
                                      int64_t, const T*, const T*, const T*, const T*, T*,       \
                                      cudaStream_t);                                              \
-  template cudaError_t launch_writeback<T>(const Geom&, const Block*, int, int, int, const T*,  \
-                                           const T*, const T*, T*, cudaStream_t);
+  template cudaError_t launch_writeback<T, T>(const Geom&, const Block*, int, int, int,        \
+                                              const T*, const T*, const T*, T*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
+template cudaError_t launch_writeback<float, double>(const Geom&, const Block*, int, int, int,
+                                                     const float*, const double*, const double*,
+                                                     float*, cudaStream_t);
 template cudaError_t launch_assemble<float, double>(const Geom&, const Block*, int, int,
                                                     const float*, const float*, const float*,
                                                     const float*, const int32_t*, const float*,
