@@ -437,7 +437,7 @@ void release(enkfmc_handle* h) {
                   h->d_fb_blocks, h->d_fb_band, h->d_c1max, h->d_sqp, h->d_fy, h->d_fZ,
                   h->d_fx,    h->d_fsq,     h->d_dobs, h->d_dob_off, h->d_dzoff, h->d_obs_idx,
                   h->d_dz,    h->d_dw,      h->d_dx64, h->d_dpred, h->d_dsucc,
-                  h->d_dq};
+                  h->d_dq,    h->d_dsoff,   h->d_ds};
   for (void* b : bufs) dfree(b);
   if (h->f_stream) cudaStreamDestroy(h->f_stream);
   if (h->c_stream) cudaStreamDestroy(h->c_stream);
@@ -889,8 +889,10 @@ enkfmc_status build_dual(enkfmc_handle* h) {
   const bool fp64 = !is_fp64(h) && has_fp64_rows(g, true);
   const size_t es = fp64 ? 8 : h->esize;
   std::vector<int2> dobs;
-  std::vector<int64_t> off((size_t)h->nblock + 1, 0), zoff((size_t)h->nblock, 0);
-  int mb_max = 0, W = 1;
+  std::vector<int64_t> off((size_t)h->nblock + 1, 0), zoff((size_t)h->nblock, 0),
+      soff((size_t)h->nblock, 0);
+  int64_t ssum = 0;
+  int mb_max = 0, W = 1, Wn = 1, Df = 1 << 30;
   int64_t zsum = 0;
   size_t prow = 0;
   const double N = g.N;
@@ -919,8 +921,17 @@ enkfmc_status build_dual(enkfmc_handle* h) {
     off[(size_t)bi + 1] = (int64_t)dobs.size();
     zoff[(size_t)bi] = zsum;
     zsum += (int64_t)b.nb * mb;
+    soff[(size_t)bi] = ssum;
+    ssum += (int64_t)mb * (mb + 1) / 2;
     mb_max = std::max(mb_max, mb);
+    // positions apart of a row and its predecessor: below (vr ey + r + 1) ex;
+    // on its own level below (r + 1) ex, on a level below at least
+    // (ey - r - 1) ex + 1 (the segment of (level, latitude) and the column
+    // in label order differ by at most r and ex - 1, resp. at least ey - r
+    // and at most ex - 1)
     W = std::max(W, (g.vr * b.ey + g.r + 1) * b.ex);
+    Wn = std::max(Wn, (g.r + 1) * b.ex);
+    if (g.vr > 0 && b.nlev_b > 1) Df = std::min(Df, (b.ey - g.r - 1) * b.ex + 1);
     const double nb = b.nb, m = mb;
     fo += nb * m * (m + 1) + m * m * m / 3.0 + 2.0 * m * m * N;
     fa += 2.0 * nb * m * N + nb * N + 2.0 * N * pre;
@@ -929,9 +940,12 @@ enkfmc_status build_dual(enkfmc_handle* h) {
     pz += pre;
   }
   W = std::min(W, std::max(1, h->nb_max));
+  DualRings rg{W, W, 1, W};  // one ring of W rows
+  Wn = std::min(Wn, W);
+  if (Df < W && Df >= Wn && Df > kDualStages) rg = DualRings{Wn, Df, W - Df + kDualStages, W};
   const size_t lim = 227 * 1024;
-  const size_t ssolve = es == 8 ? dual_solve_smem<double>(W, g.pmax)
-                                : dual_solve_smem<float>(W, g.pmax);
+  const size_t ssolve = es == 8 ? dual_solve_smem<double>(rg, g.pmax)
+                                : dual_solve_smem<float>(rg, g.pmax);
   const size_t sobs = mb_max == 0 ? 0
                       : es == 8   ? dual_obs_smem<double>(mb_max, g.N)
                                   : dual_obs_smem<float>(mb_max, g.N);
@@ -939,13 +953,15 @@ enkfmc_status build_dual(enkfmc_handle* h) {
   std::vector<int32_t> oidx((size_t)std::max<int64_t>(h->m, 0), 0);
   for (size_t l = 0; l < h->obs_of_host.size(); ++l)
     if (h->obs_of_host[l] >= 0) oidx[(size_t)h->obs_of_host[l]] = (int32_t)l;
-  void* old[] = {h->d_dobs, h->d_dob_off, h->d_dzoff, h->d_obs_idx, h->d_dz, h->d_dw};
+  void* old[] = {h->d_dobs, h->d_dob_off, h->d_dzoff, h->d_obs_idx, h->d_dz, h->d_dw,
+                 h->d_dsoff, h->d_ds};
   CUDA_TRY(cudaStreamSynchronize(h->stream));  // buffers of an earlier set may be in use
   for (void* p : old) dfree(p);
   h->d_dobs = nullptr;
   h->d_dob_off = h->d_dzoff = nullptr;
   h->d_obs_idx = nullptr;
-  h->d_dz = h->d_dw = nullptr;
+  h->d_dz = h->d_dw = h->d_ds = nullptr;
+  h->d_dsoff = nullptr;
   enkfmc_status st;
   if ((st = dalloc(h, &h->d_dobs, sizeof(int2) * dobs.size()))) return st;
   if ((st = dalloc(h, &h->d_dob_off, sizeof(int64_t) * off.size()))) return st;
@@ -953,6 +969,10 @@ enkfmc_status build_dual(enkfmc_handle* h) {
   if ((st = dalloc(h, &h->d_obs_idx, sizeof(int32_t) * oidx.size()))) return st;
   if ((st = dalloc(h, &h->d_dz, es * (size_t)zsum))) return st;
   if ((st = dalloc(h, &h->d_dw, es * (size_t)dobs.size() * g.N))) return st;
+  if ((st = dalloc(h, &h->d_dsoff, sizeof(int64_t) * soff.size()))) return st;
+  if ((st = dalloc(h, &h->d_ds, es * (size_t)ssum))) return st;
+  CUDA_TRY(cudaMemcpy(h->d_dsoff, soff.data(), sizeof(int64_t) * soff.size(),
+                      cudaMemcpyHostToDevice));
   if (fp64 && !h->d_dx64 &&
       (st = dalloc(h, &h->d_dx64, sizeof(double) * (size_t)h->ext_rows * g.N)))
     return st;
@@ -972,7 +992,7 @@ enkfmc_status build_dual(enkfmc_handle* h) {
     CUDA_TRY(cudaMemcpy(h->d_obs_idx, oidx.data(), sizeof(int32_t) * oidx.size(),
                         cudaMemcpyHostToDevice));
   h->dual_mb_max = mb_max;
-  h->dual_W = W;
+  h->dual_rings = rg;
   h->work_flops[ENKFMC_K_DUAL_Z] = fz;
   h->work_bytes[ENKFMC_K_DUAL_Z] = (double)es * (bz + pz);
   h->work_flops[ENKFMC_K_DUAL_OBS] = fo;
@@ -992,26 +1012,27 @@ enkfmc_status run_dual_kernels(enkfmc_handle* h, const TI* Xb, const TI* Tv, con
   enkfmc_status st = timed(h, ENKFMC_K_DUAL_Z, [&](int* nk) {
     return launch_dual_z<TI, TC>(g, h->d_blocks, h->nblock, h->nb_max, h->dual_mb_max,
                                  h->d_dobs, h->d_dob_off, h->d_dzoff, Tv, (const TI*)h->d_Te,
-                                 h->d_dpred, h->d_dsucc, (TC*)h->d_dz, h->dual_W, h->stream, nk);
+                                 h->d_dpred, h->d_dsucc, (TC*)h->d_dz, h->dual_rings, h->stream,
+                                 nk);
   });
   if (st) return st;
-  st = timed(h, ENKFMC_K_DUAL_OBS, [&] {
+  st = timed(h, ENKFMC_K_DUAL_OBS, [&](int* nk) {
     return launch_dual_obs<TI, TC>(g, h->d_blocks, h->nblock, h->dual_mb_max, h->d_dobs,
-                                   h->d_dob_off, h->d_dzoff, h->d_obs_idx, h->m, Xb, y, R, Z, D,
-                                   (const TI*)h->d_De, (const TC*)h->d_dz, (TC*)h->d_dw,
-                                   h->d_status, h->stream);
+                                   h->d_dob_off, h->d_dzoff, h->d_dsoff, h->d_obs_idx, h->m, Xb,
+                                   y, R, Z, D, (const TI*)h->d_De, (const TC*)h->d_dz,
+                                   (TC*)h->d_ds, (TC*)h->d_dw, h->d_status, h->stream, nk);
   });
   if (st) return st;
   st = timed(h, ENKFMC_K_DUAL_APPLY, [&](int* nk) {
     return launch_dual_apply<TI, TC>(g, h->d_blocks, h->nblock, h->nb_max, h->d_dob_off,
                                      h->d_dzoff, (const TC*)h->d_dz, (const TC*)h->d_dw, D,
                                      (const TI*)h->d_De, h->d_dpred, (TC*)h->d_dq, dX,
-                                     h->dual_W, h->stream, nk);
+                                     h->dual_rings, h->stream, nk);
   });
   if (st) return st;
   return timed(h, ENKFMC_K_WRITEBACK, [&] {
-    return launch_writeback<TI, TC>(g, h->d_blocks, h->nsubx, h->prob.sub_lon, h->prob.sub_lat,
-                                    Xb, (const TC*)dX, (const TC*)nullptr, Xa, h->stream);
+    return launch_dual_writeback<TI, TC>(g, h->d_blocks, h->nsubx, h->prob.sub_lon,
+                                         h->prob.sub_lat, Xb, (const TC*)dX, Xa, h->stream);
   });
 }
 

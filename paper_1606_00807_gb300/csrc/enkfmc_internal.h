@@ -42,6 +42,15 @@ struct Block {
   int64_t row_off;                 // offset of the block's rows (Te, De, rhs rows)
 };
 
+// Dual form (k_dual.cu): rows the triangular solves stage ahead (cp.async),
+// and their rings: rows less than Wn positions away in the near ring, rows Df
+// to W - 1 away in the far ring of Wf = W - Df + kDualStages rows (Df = W:
+// none).
+constexpr int kDualStages = 8;
+struct DualRings {
+  int Wn, Df, Wf, W;
+};
+
 // ---------------------------------------------------------------------------
 // Stencil slots.  Slot s of a row of T is the neighbour at offset
 // (dk, dy, dx): first the vr lower levels ((2r+1)^2 each), then the r earlier
@@ -279,13 +288,16 @@ struct enkfmc_handle {
   std::vector<int> p_ext;            // predecessors per extended row (-p-1: boundary)
   bool dual_ready = false;
   bool dual_fp64 = false;        // single-precision problem, dual arithmetic in double
-  int32_t dual_mb_max = 0, dual_W = 0;
+  int32_t dual_mb_max = 0;
+  enkfmc::DualRings dual_rings{1, 1, 1, 1};
   double* d_dx64 = nullptr;      // its increments [ext_rows][N] in double
   void *d_dpred = nullptr, *d_dsucc = nullptr;  // the solves' term tables
   void* d_dq = nullptr;          // Q = D Z W [ext_rows][N] (arithmetic type)
   int2* d_dobs = nullptr;
   int64_t* d_dob_off = nullptr;  // [nblock + 1]
   int64_t* d_dzoff = nullptr;    // [nblock]
+  int64_t* d_dsoff = nullptr;    // [nblock] offsets of the packed S = Z^T D Z
+  void* d_ds = nullptr;
   int32_t* d_obs_idx = nullptr;  // [m] observed component of each observation
   void* d_dz = nullptr;
   void* d_dw = nullptr;
@@ -516,7 +528,7 @@ cudaError_t launch_accumulate(float* y, const float* x, int64_t count, cudaStrea
 // W: the solves' ring (rows).
 constexpr int kDualMaxSlots = 128;  // stencil slots the dual solves handle (4 per lane)
 template <typename T>
-size_t dual_solve_smem(int W, int pmax);
+size_t dual_solve_smem(const DualRings& rg, int pmax);
 template <typename T>
 size_t dual_obs_smem(int mb, int N);
 // TI: the type of the inputs (T, D, X^b, y, R, Z); TC: the arithmetic and
@@ -530,21 +542,28 @@ size_t dual_table_bytes(size_t esize, int pmax);
 template <typename TI, typename TC>
 cudaError_t launch_dual_z(const Geom& g, const Block* blocks, int nblock, int nb_max, int mb_max,
                           const int2* dobs, const int64_t* dob_off, const int64_t* zoff,
-                          const TI* Tg, const TI* Te, void* pred, void* succ, TC* Zb, int W,
-                          cudaStream_t s, int* nk);
+                          const TI* Tg, const TI* Te, void* pred, void* succ, TC* Zb,
+                          const DualRings& rg, cudaStream_t s, int* nk);
+// S = Z^T D Z (packed lower triangles at soff[block]), then (S + R) W =
+// Y^s - H X^b.
 template <typename TI, typename TC>
 cudaError_t launch_dual_obs(const Geom& g, const Block* blocks, int nblock, int mb_max,
                             const int2* dobs, const int64_t* dob_off, const int64_t* zoff,
-                            const int32_t* obs_idx, int64_t m, const TI* Xb, const TI* y,
-                            const TI* R, const TI* Zp, const TI* Dg, const TI* De, const TC* Zb,
-                            TC* Wb, int32_t* status, cudaStream_t s);
-// Q = D Z W, then dX = T^-1 Q (Q and dX: [ext rows][N] in the primal
-// solve's layout).
+                            const int64_t* soff, const int32_t* obs_idx, int64_t m, const TI* Xb,
+                            const TI* y, const TI* R, const TI* Zp, const TI* Dg, const TI* De,
+                            const TC* Zb, TC* Sb, TC* Wb, int32_t* status, cudaStream_t s,
+                            int* nk);
+// Q = D Z W, then dX = T^-1 Q (Q and dX: [ext rows][N], members fastest).
 template <typename TI, typename TC>
 cudaError_t launch_dual_apply(const Geom& g, const Block* blocks, int nblock, int nb_max,
                               const int64_t* dob_off, const int64_t* zoff, const TC* Zb,
                               const TC* Wb, const TI* Dg, const TI* De, const void* pred, TC* Q,
-                              TC* dX, int W, cudaStream_t s, int* nk);
+                              TC* dX, const DualRings& rg, cudaStream_t s, int* nk);
+// Xa = Xb + dX on the sub-domain interiors, dX members fastest.
+template <typename TI, typename TC>
+cudaError_t launch_dual_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
+                                  int sub_lat, const TI* Xb, const TC* dX, TI* Xa,
+                                  cudaStream_t s);
 
 // True when the CUDA-core band Cholesky and solves (k_band.cu) can launch for
 // half-bandwidth hb with elements of esize bytes.

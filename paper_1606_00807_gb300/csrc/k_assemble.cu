@@ -446,9 +446,6 @@ cudaError_t launch_writeback(const Geom& g, const Block* blocks, int nsubx, int 
 INST(float)
 INST(double)
 #undef INST
-template cudaError_t launch_writeback<float, double>(const Geom&, const Block*, int, int, int,
-                                                     const float*, const double*, const double*,
-                                                     float*, cudaStream_t);
 template cudaError_t launch_assemble<float, double>(const Geom&, const Block*, int, int,
                                                     const float*, const float*, const float*,
                                                     const float*, const int32_t*, const float*,

@@ -12,8 +12,9 @@
 //   k_dual_z      Z = T^-T H^T, one warp per 32 observation columns;
 //   k_dual_obs    S = R + Z^T D Z, S = L L^T, W = S^-1 (Y^s - H X^b), one CTA
 //                 per block, in shared memory;
-//   k_dual_q      Q = D (Z W) into the increment buffer, a tiled product;
-//   k_dual_apply  dX = T^-1 Q in place, one warp per 32 members.
+//   k_dual_q      Q = D (Z W), a tiled product;
+//   k_dual_apply  dX = T^-1 Q, one warp per 32 members;
+//   k_dual_writeback  Xa = Xb + dX on the interiors (Q and dX members fastest).
 //
 // Solve order.  T is unit lower triangular in label order (a predecessor has a
 // smaller label).  Within a row segment of the block (one level, one
@@ -131,14 +132,24 @@ struct alignas(2 * sizeof(T) > 8 ? 16 : 8) Term {
 __host__ __device__ inline int term_stride(int pmax) { return (pmax + 1) & ~1; }
 
 // Rows the solves stage ahead of the one they sum (cp.async pipeline depth).
-constexpr int kStages = 8;
+constexpr int kStages = kDualStages;
 
-// Shared memory of a triangular solve (one warp): the ring [W][32], the
+// The solves' rows in shared memory: a row's terms reach rows less than W
+// positions away; those less than Wn away (its own level) come from the near
+// ring [Wn][32], written as the solve goes; those Df or more away (the levels
+// below, or above for the solve with T^T) from the far ring [Wf][32], Wf =
+// W - Df + kStages, into which each row is copied back from global memory
+// kStages steps before it is first read (the rows between Wn and Df away are
+// needed by no row).  Without such a gap (Df < Wn) the near ring holds all W
+// rows and the far ring is unused (Df = W).
+using Rings = DualRings;
+
+// Shared memory of a triangular solve (one warp): the near and far rings, the
 // current row's compacted terms [pmax], the staged table rows
 // [kStages][term_stride] and (forward solve) the staged q values [kStages][32].
 template <typename T>
-size_t solve_smem(int W, int pmax) {
-  return (size_t)W * 32 * sizeof(T) + (size_t)term_stride(pmax) * sizeof(Term<T>) +
+size_t solve_smem(const Rings& rg, int pmax) {
+  return (size_t)(rg.Wn + rg.Wf) * 32 * sizeof(T) + (size_t)term_stride(pmax) * sizeof(Term<T>) +
          (size_t)kStages * term_stride(pmax) * sizeof(Term<T>) + (size_t)kStages * 32 * sizeof(T);
 }
 
@@ -261,26 +272,40 @@ __device__ __forceinline__ void stage_row(Term<T>* dst, const Term<T>* src, int 
     cp_async16(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i);
 }
 
-// The terms of one staged row compacted into `terms` with their ring offsets
-// (slot x 32; the row at distance d: sign +1 after t, -1 before; only
-// distances below W and, with lim >= 0, rows at positions up to lim count).
-// Returns the number of terms.
+// The terms of one staged row compacted into `terms` with their offsets in
+// the rings (the near ring first, then the far ring; slot x 32).  The row at
+// distance d (sign +1: after t, -1: before): near slot rn + sign d (mod Wn),
+// or far slot rf + sign (d - Df) (mod Wf), rn and rf the slots of the rows t
+// and t + sign Df.  Only distances below Wn or in [Df, W), and with lim >= 0
+// rows at positions up to lim, count.  Returns the number of terms.
 template <typename T>
-__device__ __forceinline__ int load_terms(Term<T>* terms, const Term<T>* row, int pmax, int rt,
-                                          int W, int sign, int t, int lim, int lane) {
+__device__ __forceinline__ int load_terms(Term<T>* terms, const Term<T>* row, int pmax,
+                                          const Rings& rg, int rn, int rf, int sign, int t,
+                                          int lim, int lane) {
   int n = 0;
 #pragma unroll
   for (int q = 0; q < kSlotQ; ++q) {
     const int s = lane + 32 * q;
     Term<T> e{0, T(0)};
     if (s < pmax) e = row[s];
-    const bool on = e.at > 0 && e.at < W && (lim < 0 || t + e.at <= lim);
+    const int d = e.at;
+    const bool near = d > 0 && d < rg.Wn, far = d >= rg.Df && d < rg.W;
+    const bool on = (near || far) && (lim < 0 || t + d <= lim);
     const unsigned mask = __ballot_sync(0xffffffffu, on);
     if (on) {
-      int sl = rt + sign * e.at;
-      if (sl >= W) sl -= W;
-      if (sl < 0) sl += W;
-      terms[n + __popc(mask & ((1u << lane) - 1u))] = Term<T>{sl * 32, e.v};
+      int at;
+      if (near) {
+        int sl = rn + sign * d;
+        if (sl >= rg.Wn) sl -= rg.Wn;
+        if (sl < 0) sl += rg.Wn;
+        at = sl;
+      } else {
+        int sl = rf + sign * (d - rg.Df);
+        if (sl >= rg.Wf) sl -= rg.Wf;
+        if (sl < 0) sl += rg.Wf;
+        at = rg.Wn + sl;
+      }
+      terms[n + __popc(mask & ((1u << lane) - 1u))] = Term<T>{at * 32, e.v};
     }
     n += __popc(mask);
     if (32 * (q + 1) >= pmax) break;
@@ -301,11 +326,12 @@ __global__ void __launch_bounds__(32) k_dual_z(const Geom g, const Block* __rest
                                                const int64_t* __restrict__ dob_off,
                                                const int64_t* __restrict__ zoff,
                                                const Term<T>* __restrict__ succ,
-                                               T* __restrict__ Zb, int W) {
+                                               T* __restrict__ Zb, const Rings rg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int pmax = g.pmax, ts = term_stride(pmax);
-  T* ring = reinterpret_cast<T*>(smem);
-  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)W * 32);
+  T* ring = reinterpret_cast<T*>(smem);  // near ring [Wn][32], then far ring [Wf][32]
+  T* ringf = ring + (size_t)rg.Wn * 32;
+  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)(rg.Wn + rg.Wf) * 32);
   Term<T>* stage = terms + ts;  // [kStages][ts]
   const Block b = blocks[blockIdx.y];
   const int64_t o0 = dob_off[blockIdx.y];
@@ -322,138 +348,179 @@ __global__ void __launch_bounds__(32) k_dual_z(const Geom g, const Block* __rest
   for (int t = tlast + 1; t < b.nb; ++t)
     if (act) Z[(int64_t)ord.loc_of(t) * mb + c] = T(0);
   const Term<T>* tab = succ + b.row_off * ts;
+  const bool has_far = rg.Df < rg.W;
+  // far ring: row p (> t) is copied back from Z at step p - Df + kStages, into
+  // slot p mod Wf; farc walks those rows downwards
+  int pf = tlast - kStages + rg.Df;  // row copied back at step tlast
+  const int pf_hi = b.nb - 1;
+  OrderCursor farc(ord, max(0, min(pf, pf_hi)));
+  int rfs = max(0, min(pf, pf_hi)) % rg.Wf;
+  auto stage_far = [&](int p) {
+    if (has_far && p >= 0 && p <= pf_hi) {
+      if (act) cp_async_small<sizeof(T)>(ringf + rfs * 32 + lane, Z + (int64_t)farc.loc() * mb + c);
+    }
+  };
+  auto advance_far = [&](int p) {  // after the row p was handled: the next is p - 1
+    if (p >= 0 && p <= pf_hi) {
+      farc.prev();
+      rfs = rfs == 0 ? rg.Wf - 1 : rfs - 1;
+    }
+  };
   // rows tlast, tlast - 1, ... staged kStages ahead (stage of row t: (tlast - t) % kStages)
   for (int d = 0; d < kStages; ++d) {
     if (tlast - d >= 0) stage_row(stage + d * ts, tab + (int64_t)(tlast - d) * ts, ts, lane);
     cp_async_commit();
   }
-  int rt = tlast % W;  // ring slot of position t
-  int st = 0;          // stage of row t
+  int rn = tlast % rg.Wn;                      // near slot of position t
+  int rf = (tlast + rg.Df) % rg.Wf;            // far slot of position t + Df
+  int st = 0;                                  // stage of row t
   OrderCursor cur(ord, tlast);
   for (int t = tlast; t >= 0; --t) {
     cp_async_wait_stages();
     __syncwarp();
-    const int n = load_terms(terms, stage + st * ts, pmax, rt, W, 1, t, tlast, lane);
+    const int n = load_terms(terms, stage + st * ts, pmax, rg, rn, rf, 1, t, tlast, lane);
     __syncwarp();
     if (t - kStages >= 0) stage_row(stage + st * ts, tab + (int64_t)(t - kStages) * ts, ts, lane);
+    stage_far(pf);
     cp_async_commit();
+    advance_far(pf);
+    --pf;
     st = st + 1 == kStages ? 0 : st + 1;
     const T z = sub_terms((t == tc) ? T(1) : T(0), terms, n, ring, lane);
-    ring[rt * 32 + lane] = z;
+    ring[rn * 32 + lane] = z;
     if (act) Z[(int64_t)cur.loc() * mb + c] = z;
     cur.prev();
-    rt = rt == 0 ? W - 1 : rt - 1;
+    rn = rn == 0 ? rg.Wn - 1 : rn - 1;
+    rf = rf == 0 ? rg.Wf - 1 : rf - 1;
     __syncwarp();
   }
 }
 
 // ---------------------------------------------------------------------------
-// S = R + Z^T D Z (lower triangle), S = L L^T, and W = S^-1 (Y^s - H X^b)
-// for the block's observations; one CTA per block, all in shared memory.
-// W: [mb][N] per block at N dob_off[b].  A non-positive or non-finite pivot
-// records ENOTSPD (the block's W is then zero).
+// S = Z^T D Z, the lower triangle of each block's m_b x m_b matrix (packed row
+// by row at soff[b]): a CTA per TILE x TILE tile of the lower triangle (64, or
+// 32 when the blocks hold few observations), a thread per (TILE/16)^2 outputs,
+// over the block's rows in chunks of 32 staged in shared memory (the D of
+// each row folded into the left operand).
 // ---------------------------------------------------------------------------
-constexpr int kObsThreads = 256;
-constexpr int kObsRows = 32;  // rows of Z staged per step of the product
+constexpr int kSyRows = 32;
 
-__host__ __device__ inline int obs_zld(int mb) {  // row stride of the staged Z rows
-  return (mb + 3) & ~3;
+template <typename TI, typename T, int TILE>
+__global__ void __launch_bounds__(256) k_dual_syrk(const Geom g, const Block* __restrict__ blocks,
+                                                   const int64_t* __restrict__ dob_off,
+                                                   const int64_t* __restrict__ zoff,
+                                                   const int64_t* __restrict__ soff,
+                                                   const TI* __restrict__ Dg,
+                                                   const TI* __restrict__ De,
+                                                   const T* __restrict__ Zb, T* __restrict__ Sb) {
+  constexpr int P = TILE / 16;  // outputs per thread in each direction
+  __shared__ T A[kSyRows][TILE + 1];   // D z of the tile's row columns
+  __shared__ T Bm[kSyRows][TILE + 1];  // z of its column columns
+  const Block b = blocks[blockIdx.y];
+  const int64_t o0 = dob_off[blockIdx.y];
+  const int mb = (int)(dob_off[blockIdx.y + 1] - o0);
+  const int nt = (mb + TILE - 1) / TILE;
+  const int pr = blockIdx.x;
+  if (pr >= nt * (nt + 1) / 2) return;
+  int I = (int)((sqrtf(8.f * pr + 1.f) - 1.f) * 0.5f);
+  while ((I + 1) * (I + 2) / 2 <= pr) ++I;
+  while (I * (I + 1) / 2 > pr) --I;
+  const int J = pr - I * (I + 1) / 2;
+  const int i0 = I * TILE, l0 = J * TILE;
+  const T* Z = Zb + zoff[blockIdx.y];
+  const int tid = threadIdx.x, ti = tid >> 4, tl = tid & 15;  // outputs (i0 + ti + 16 a, l0 + tl + 16 e)
+  T acc[P][P];
+#pragma unroll
+  for (int a = 0; a < P; ++a)
+#pragma unroll
+    for (int e = 0; e < P; ++e) acc[a][e] = T(0);
+  for (int j0 = 0; j0 < b.nb; j0 += kSyRows) {
+    __syncthreads();
+    for (int e = tid; e < kSyRows * TILE; e += 256) {
+      const int rr = e / TILE, cc = e - rr * TILE;
+      const int j = j0 + rr;
+      T za = T(0), zb = T(0);
+      if (j < b.nb) {
+        const T* zr = Z + (int64_t)j * mb;
+        if (i0 + cc < mb) za = zr[i0 + cc];
+        if (l0 + cc < mb) zb = zr[l0 + cc];
+      }
+      A[rr][cc] = za;
+      Bm[rr][cc] = zb;
+    }
+    __syncthreads();
+    if (tid < kSyRows) {  // fold D into A
+      const int j = j0 + tid;
+      T d = T(0);
+      if (j < b.nb) {
+        int k, y, x;
+        local_coords(b, g.nlon, j, k, y, x);
+        d = (T)block_d(g, b, k, y, x, j, Dg, De);
+      }
+      for (int cc = 0; cc < TILE; ++cc) A[tid][cc] *= d;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < kSyRows; ++rr) {
+      T av[P], bv[P];
+#pragma unroll
+      for (int a = 0; a < P; ++a) av[a] = A[rr][ti + 16 * a];
+#pragma unroll
+      for (int e = 0; e < P; ++e) bv[e] = Bm[rr][tl + 16 * e];
+#pragma unroll
+      for (int a = 0; a < P; ++a)
+#pragma unroll
+        for (int e = 0; e < P; ++e) acc[a][e] = fma(av[a], bv[e], acc[a][e]);
+    }
+  }
+  T* S = Sb + soff[blockIdx.y];
+#pragma unroll
+  for (int a = 0; a < P; ++a)
+#pragma unroll
+    for (int e = 0; e < P; ++e) {
+      const int i = i0 + ti + 16 * a, l = l0 + tl + 16 * e;
+      if (i < mb && l <= i) S[(int64_t)i * (i + 1) / 2 + l] = acc[a][e];
+    }
 }
 
-// Shared memory of k_dual_obs: S, lower triangle packed row by row, then one
-// region that first stages Z rows with their D (the product) and then holds
-// the innovations and W [mb][N].
+// ---------------------------------------------------------------------------
+// S + R = L L^T and W = (S + R)^-1 (Y^s - H X^b) for the block's
+// observations; one CTA per block, in shared memory (S packed, the
+// innovations then W [mb][N]).  Right-looking factorisation and solves, the
+// CTA's threads over the trailing rows x members.  W: [mb][N] per block at
+// N dob_off[b].  A non-positive or non-finite pivot records ENOTSPD (the
+// block's W is then zero).
+// ---------------------------------------------------------------------------
+constexpr int kObsThreads = 256;
+
+// Shared memory of k_dual_obs: S packed, then W.
 template <typename T>
 size_t obs_smem(int mb, int N) {
-  const size_t tri = (size_t)mb * (mb + 1) / 2 + 1;
-  const size_t stage = (size_t)kObsRows * obs_zld(mb) + kObsRows;
-  return sizeof(T) * (tri + std::max((size_t)mb * N, stage)) + 16;
+  return sizeof(T) * ((size_t)mb * (mb + 1) / 2 + 1 + (size_t)mb * N) + 16;
 }
 
 template <typename TI, typename T>
 __global__ void __launch_bounds__(kObsThreads) k_dual_obs(
     const Geom g, const Block* __restrict__ blocks, const int2* __restrict__ dobs,
-    const int64_t* __restrict__ dob_off, const int64_t* __restrict__ zoff,
+    const int64_t* __restrict__ dob_off, const int64_t* __restrict__ soff,
     const int32_t* __restrict__ obs_idx, int64_t mobs, const TI* __restrict__ Xb,
     const TI* __restrict__ y, const TI* __restrict__ R, const TI* __restrict__ Zp,
-    const TI* __restrict__ Dg, const TI* __restrict__ De, const T* __restrict__ Zb,
-    T* __restrict__ Wb, int32_t* status) {
+    const T* __restrict__ Sb, T* __restrict__ Wb, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Block b = blocks[blockIdx.x];
   const int64_t o0 = dob_off[blockIdx.x];
   const int mb = (int)(dob_off[blockIdx.x + 1] - o0);
   if (mb == 0) return;
-  const int N = g.N, zld = obs_zld(mb);
-  T* S = reinterpret_cast<T*>(smem);             // packed lower triangle, S(i, l) at tri(i) + l
-  T* Wm = S + (size_t)mb * (mb + 1) / 2 + 1;     // [mb][N], after the product
-  T* Zs = Wm;                                    // [kObsRows][zld] during the product
-  T* Ds = Zs + (size_t)kObsRows * zld;           // [kObsRows]
+  const int N = g.N;
+  const int ntri = mb * (mb + 1) / 2;
+  T* S = reinterpret_cast<T*>(smem);  // packed lower triangle, S(i, l) at tri(i) + l
+  T* Wm = S + ntri + 1;               // [mb][N]
   auto tri = [](int i) { return i * (i + 1) / 2; };
   __shared__ int bad;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kObsThreads / 32;
   if (tid == 0) bad = 0;
-  const T* Z = Zb + zoff[blockIdx.x];
-
-  // S = Z^T D Z: 4 x 4 tiles of the lower triangle, one per thread per round
-  const int nt = (mb + 3) / 4, npair = nt * (nt + 1) / 2;
-  for (int base = 0; base < npair; base += kObsThreads) {
-    const int pr = base + tid;
-    int I = 0, J = 0;
-    if (pr < npair) {
-      I = (int)((sqrtf(8.f * pr + 1.f) - 1.f) * 0.5f);
-      while ((I + 1) * (I + 2) / 2 <= pr) ++I;
-      while (I * (I + 1) / 2 > pr) --I;
-      J = pr - I * (I + 1) / 2;
-    }
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[a][e] = T(0);
-    for (int j0 = 0; j0 < b.nb; j0 += kObsRows) {
-      __syncthreads();
-      const int nr = min(kObsRows, b.nb - j0);
-      for (int e = tid; e < kObsRows * zld; e += kObsThreads) {
-        const int rr = e / zld, cc = e - rr * zld;
-        Zs[e] = (rr < nr && cc < mb) ? Z[(int64_t)(j0 + rr) * mb + cc] : T(0);
-      }
-      if (tid < kObsRows) {
-        T d = T(0);
-        if (tid < nr) {
-          int k, yy, xx;
-          local_coords(b, g.nlon, j0 + tid, k, yy, xx);
-          d = (T)block_d(g, b, k, yy, xx, j0 + tid, Dg, De);
-        }
-        Ds[tid] = d;
-      }
-      __syncthreads();
-      if (pr < npair) {
-        for (int rr = 0; rr < nr; ++rr) {
-          const T d = Ds[rr];
-          const T* zr = Zs + rr * zld;
-          T a[4], e4[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            a[q] = d * zr[4 * I + q];
-            e4[q] = zr[4 * J + q];
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[q][u] = fma(a[q], e4[u], acc[q][u]);
-        }
-      }
-    }
-    if (pr < npair) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = 4 * I + q, l = 4 * J + u;
-          if (i < mb && l <= i) S[tri(i) + l] = acc[q][u];
-        }
-    }
-  }
+  const T* Sg = Sb + soff[blockIdx.x];
+  for (int e = tid; e < ntri; e += kObsThreads) S[e] = Sg[e];
   __syncthreads();
   // + R on the diagonal; the innovations Y^s - H X^b into Wm
   for (int c = tid; c < mb; c += kObsThreads) S[tri(c) + c] += (T)R[dobs[o0 + c].y];
@@ -465,9 +532,8 @@ __global__ void __launch_bounds__(kObsThreads) k_dual_obs(
             (T)Xb[(int64_t)m * g.n + obs_idx[o]];
   }
   __syncthreads();
-  // Cholesky, right-looking: column k scaled, then the trailing lower triangle
-  // (a warp per row, lanes over its columns)
-  const int lane = tid & 31, warp = tid >> 5, nw = kObsThreads / 32;
+  // Cholesky: column k scaled, then the trailing lower triangle (a warp per
+  // row, lanes over its columns)
   for (int k = 0; k < mb; ++k) {
     if (tid == 0) {
       const T d = S[tri(k) + k];
@@ -492,29 +558,36 @@ __global__ void __launch_bounds__(kObsThreads) k_dual_obs(
     for (int e = tid; e < mb * N; e += kObsThreads) Wout[e] = T(0);
     return;
   }
-  // L L^T W = innovations, a thread per member
-  for (int m = tid; m < N; m += kObsThreads) {
-    for (int c = 0; c < mb; ++c) {
-      const T* Sc = S + tri(c);
-      T w = Wm[c * N + m];
-      for (int l = 0; l < c; ++l) w = fma(-Sc[l], Wm[l * N + m], w);
-      Wm[c * N + m] = w / Sc[c];
+  // L w = innovations: row c final, then subtracted from the rows below
+  for (int c = 0; c < mb; ++c) {
+    const T inv = T(1) / S[tri(c) + c];
+    for (int m = tid; m < N; m += kObsThreads) Wm[c * N + m] *= inv;
+    __syncthreads();
+    for (int i = c + 1 + warp; i < mb; i += nw) {
+      const T lic = S[tri(i) + c];
+      for (int m = lane; m < N; m += 32) Wm[i * N + m] = fma(-lic, Wm[c * N + m], Wm[i * N + m]);
     }
-    for (int c = mb - 1; c >= 0; --c) {
-      T w = Wm[c * N + m];
-      for (int l = c + 1; l < mb; ++l) w = fma(-S[tri(l) + c], Wm[l * N + m], w);
-      Wm[c * N + m] = w / S[tri(c) + c];
-    }
+    __syncthreads();
   }
-  __syncthreads();
+  // L^T W = w: row c final, then subtracted from the rows above
+  for (int c = mb - 1; c >= 0; --c) {
+    const T inv = T(1) / S[tri(c) + c];
+    for (int m = tid; m < N; m += kObsThreads) Wm[c * N + m] *= inv;
+    __syncthreads();
+    for (int i = warp; i < c; i += nw) {
+      const T lci = S[tri(c) + i];
+      for (int m = lane; m < N; m += 32) Wm[i * N + m] = fma(-lci, Wm[c * N + m], Wm[i * N + m]);
+    }
+    __syncthreads();
+  }
   for (int e = tid; e < mb * N; e += kObsThreads) Wout[e] = Wm[e];
 }
 
 // ---------------------------------------------------------------------------
-// Q = D (Z W) for every row of every block into the increment buffer
-// (dX[row_off N + m nb + loc], the primal solve's layout): a CTA computes 128
-// rows x 32 members, a thread rows {tr + 32 a} x members {4 tm + e}, over
-// chunks of kQK observation columns staged in shared memory.
+// Q = D (Z W) for every row of every block, members fastest
+// (Q[(row_off + loc) N + m]): a CTA computes 128 rows x 32 members, a thread
+// rows {rg + 32 a} x members {4 mg + e} (eight threads cover a row's 32
+// members), over chunks of kQK observation columns staged in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kQRows = 128, kQMem = 32, kQK = 16;
 
@@ -524,9 +597,9 @@ __global__ void __launch_bounds__(256) k_dual_q(const Geom g, const Block* __res
                                                 const int64_t* __restrict__ zoff,
                                                 const T* __restrict__ Zb, const T* __restrict__ Wb,
                                                 const TI* __restrict__ Dg,
-                                                const TI* __restrict__ De, T* __restrict__ dX) {
+                                                const TI* __restrict__ De, T* __restrict__ Q) {
   __shared__ T Zs[kQRows][kQK + 1];
-  __shared__ T Ws[kQK][kQMem];
+  __shared__ __align__(16) T Ws[kQK][kQMem];
   const Block b = blocks[blockIdx.y];
   const int r0 = blockIdx.x * kQRows;
   if (r0 >= b.nb) return;
@@ -534,7 +607,7 @@ __global__ void __launch_bounds__(256) k_dual_q(const Geom g, const Block* __res
   const int64_t o0 = dob_off[blockIdx.y];
   const int mb = (int)(dob_off[blockIdx.y + 1] - o0);
   const int N = g.N;
-  const int tid = threadIdx.x, tr = tid & 31, tm = tid >> 5;  // tm: members 4 tm .. 4 tm + 3
+  const int tid = threadIdx.x, mg = tid & 7, rg = tid >> 3;
   const T* Z = Zb + zoff[blockIdx.y];
   const T* Wv = Wb + o0 * N;
   T acc[4][4];
@@ -559,44 +632,85 @@ __global__ void __launch_bounds__(256) k_dual_q(const Geom g, const Block* __res
     for (int kk = 0; kk < kQK; ++kk) {
       T w[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) w[e] = Ws[kk][4 * tm + e];
+      for (int e = 0; e < 4; ++e) w[e] = Ws[kk][4 * mg + e];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const T z = Zs[tr + 32 * a][kk];
+        const T z = Zs[rg + 32 * a][kk];
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[a][e] = fma(z, w[e], acc[a][e]);
       }
     }
   }
-  T* out = dX + b.row_off * N;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const int j = r0 + tr + 32 * a;
+    const int j = r0 + rg + 32 * a;
     if (j >= b.nb) continue;
     int k, y, x;
     local_coords(b, g.nlon, j, k, y, x);
     const T d = (T)block_d(g, b, k, y, x, j, Dg, De);
+    T* out = Q + (b.row_off + j) * N;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const int m = m0 + 4 * tm + e;
-      if (m < N) out[(int64_t)m * b.nb + j] = d * acc[a][e];
+      const int m = m0 + 4 * mg + e;
+      if (m < N) out[m] = d * acc[a][e];
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// dX = T^-1 Q in place, forward in label order: x_j = q_j - sum_s T[j][s]
-// x_{pred_s(j)}; a warp per 32 members of a block.
+// Xa[m][l] = Xb[m][l] + dX[(row_off + loc) N + m] for the sub-domain whose
+// interior holds l (Eq. 10): a CTA per 32 components x 32 members, read along
+// the members and written along the components through a shared tile.
+// ---------------------------------------------------------------------------
+template <typename TI, typename T>
+__global__ void __launch_bounds__(256) k_dual_writeback(const Geom g,
+                                                        const Block* __restrict__ blocks,
+                                                        int nsubx, int sub_lon, int sub_lat,
+                                                        const TI* __restrict__ Xb,
+                                                        const T* __restrict__ dX,
+                                                        TI* __restrict__ Xa) {
+  __shared__ T tile[32][33];
+  const int64_t l0 = (int64_t)blockIdx.x * 32;
+  const int m0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  for (int i = wp; i < 32; i += 8) {  // component l0 + i, member m0 + lane
+    const int64_t l = l0 + i;
+    T v = T(0);
+    if (l < g.n && m0 + lane < g.N) {
+      int var, k, y, x;
+      label_coords(g, l, var, k, y, x);
+      const int sub = (y / sub_lat) * nsubx + x / sub_lon;
+      const Block& b = blocks[sub * g.nvar + var];
+      const int loc = (k * b.ey + (y - b.lat_lo)) * b.ex + imod(x - b.lon_lo, g.nlon);
+      v = dX[(b.row_off + loc) * g.N + m0 + lane];
+    }
+    tile[i][lane] = v;
+  }
+  __syncthreads();
+  for (int i = wp; i < 32; i += 8) {  // member m0 + i, component l0 + lane
+    const int m = m0 + i;
+    const int64_t l = l0 + lane;
+    if (m < g.N && l < g.n) {
+      const int64_t e = (int64_t)m * g.n + l;
+      Xa[e] = Xb[e] + (TI)tile[lane][i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dX = T^-1 Q, forward in label order: x_j = q_j - sum_s T[j][s]
+// x_{pred_s(j)}; a warp per 32 members of a block (Q and dX members fastest).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(32) k_dual_apply(const Geom g, const Block* __restrict__ blocks,
                                                    const Term<T>* __restrict__ pred,
                                                    const T* __restrict__ Q, T* __restrict__ dX,
-                                                   int W) {
+                                                   const Rings rg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int pmax = g.pmax, ts = term_stride(pmax);
-  T* ring = reinterpret_cast<T*>(smem);
-  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)W * 32);
+  T* ring = reinterpret_cast<T*>(smem);  // near ring [Wn][32], then far ring [Wf][32]
+  T* ringf = ring + (size_t)rg.Wn * 32;
+  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)(rg.Wn + rg.Wf) * 32);
   Term<T>* stage = terms + ts;                                // [kStages][ts]
   T* qst = reinterpret_cast<T*>(stage + (size_t)kStages * ts);  // [kStages][32]
   const Block b = blocks[blockIdx.y];
@@ -604,36 +718,50 @@ __global__ void __launch_bounds__(32) k_dual_apply(const Geom g, const Block* __
   const int m = blockIdx.x * 32 + lane;
   const bool act = m < g.N;
   const SolveOrder ord = solve_order(b, g.nlon);
-  const int64_t cofs = b.row_off * g.N + (int64_t)(act ? m : 0) * b.nb;
-  const T* qcol = Q + cofs;
-  T* col = dX + cofs;
+  // Q and dX: [(row_off + loc) N + m], the lanes' members side by side
+  const int N = g.N, mm = act ? m : 0;
+  const T* qcol = Q + b.row_off * N + mm;
+  T* col = dX + b.row_off * N + mm;
   const Term<T>* tab = pred + b.row_off * ts;
   OrderCursor ahead(ord, 0);  // the row staged next
   auto stage_t = [&](int slot, int t) {
     stage_row(stage + slot * ts, tab + (int64_t)t * ts, ts, lane);
-    if (act) cp_async_small<sizeof(T)>(qst + slot * 32 + lane, qcol + ahead.loc());
+    if (act) cp_async_small<sizeof(T)>(qst + slot * 32 + lane, qcol + (int64_t)ahead.loc() * N);
     ahead.next();
   };
   for (int d = 0; d < kStages; ++d) {
     if (d < b.nb) stage_t(d, d);
     cp_async_commit();
   }
-  int rt = 0, st = 0;
+  // far ring: row p (< t) is copied back from dX at step p + Df - kStages, into
+  // slot p mod Wf (rows are final there: Df > Wn > kStages)
+  const bool has_far = rg.Df < rg.W;
+  int pf = kStages - rg.Df;  // row copied back at step 0
+  OrderCursor farc(ord, 0);
+  int rfs = 0;
+  int rn = 0, rf = (rg.Wf - rg.Df % rg.Wf) % rg.Wf, st = 0;  // slots of t and t - Df
   OrderCursor cur(ord, 0);
   for (int t = 0; t < b.nb; ++t) {
     cp_async_wait_stages();
     __syncwarp();
-    const int n = load_terms(terms, stage + st * ts, pmax, rt, W, -1, t, -1, lane);
+    const int n = load_terms(terms, stage + st * ts, pmax, rg, rn, rf, -1, t, -1, lane);
     const T qv = act ? qst[st * 32 + lane] : T(0);
     __syncwarp();
     if (t + kStages < b.nb) stage_t(st, t + kStages);
+    if (has_far && pf >= 0) {
+      if (act) cp_async_small<sizeof(T)>(ringf + rfs * 32 + lane, col + (int64_t)farc.loc() * N);
+      farc.next();
+      rfs = rfs + 1 == rg.Wf ? 0 : rfs + 1;
+    }
     cp_async_commit();
+    ++pf;
     st = st + 1 == kStages ? 0 : st + 1;
     const T xv = sub_terms(qv, terms, n, ring, lane);
-    ring[rt * 32 + lane] = xv;
-    if (act) col[cur.loc()] = xv;
+    ring[rn * 32 + lane] = xv;
+    if (act) col[(int64_t)cur.loc() * N] = xv;
     cur.next();
-    rt = rt + 1 == W ? 0 : rt + 1;
+    rn = rn + 1 == rg.Wn ? 0 : rn + 1;
+    rf = rf + 1 == rg.Wf ? 0 : rf + 1;
     __syncwarp();
   }
 }
@@ -641,8 +769,8 @@ __global__ void __launch_bounds__(32) k_dual_apply(const Geom g, const Block* __
 }  // namespace
 
 template <typename T>
-size_t dual_solve_smem(int W, int pmax) {
-  return solve_smem<T>(W, pmax);
+size_t dual_solve_smem(const DualRings& rg, int pmax) {
+  return solve_smem<T>(rg, pmax);
 }
 
 template <typename T>
@@ -653,20 +781,20 @@ size_t dual_obs_smem(int mb, int N) {
 template <typename TI, typename TC>
 cudaError_t launch_dual_z(const Geom& g, const Block* blocks, int nblock, int nb_max, int mb_max,
                           const int2* dobs, const int64_t* dob_off, const int64_t* zoff,
-                          const TI* Tg, const TI* Te, void* pred, void* succ, TC* Zb, int W,
-                          cudaStream_t s, int* nk) {
+                          const TI* Tg, const TI* Te, void* pred, void* succ, TC* Zb,
+                          const DualRings& rg, cudaStream_t s, int* nk) {
   const dim3 gt((nb_max + 7) / 8, nblock);
   k_dual_terms<TI, TC><<<gt, 256, 0, s>>>(g, blocks, Tg, Te, (Term<TC>*)pred, (Term<TC>*)succ);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ++*nk;
   if (mb_max <= 0) return cudaSuccess;
-  const size_t smem = solve_smem<TC>(W, g.pmax);
+  const size_t smem = solve_smem<TC>(rg, g.pmax);
   e = cudaFuncSetAttribute(k_dual_z<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((mb_max + 31) / 32, nblock);
   k_dual_z<TC><<<grid, 32, smem, s>>>(g, blocks, dobs, dob_off, zoff, (const Term<TC>*)succ, Zb,
-                                      W);
+                                      rg);
   ++*nk;
   return cudaGetLastError();
 }
@@ -674,16 +802,29 @@ cudaError_t launch_dual_z(const Geom& g, const Block* blocks, int nblock, int nb
 template <typename TI, typename TC>
 cudaError_t launch_dual_obs(const Geom& g, const Block* blocks, int nblock, int mb_max,
                             const int2* dobs, const int64_t* dob_off, const int64_t* zoff,
-                            const int32_t* obs_idx, int64_t m, const TI* Xb, const TI* y,
-                            const TI* R, const TI* Zp, const TI* Dg, const TI* De, const TC* Zb,
-                            TC* Wb, int32_t* status, cudaStream_t s) {
+                            const int64_t* soff, const int32_t* obs_idx, int64_t m, const TI* Xb,
+                            const TI* y, const TI* R, const TI* Zp, const TI* Dg, const TI* De,
+                            const TC* Zb, TC* Sb, TC* Wb, int32_t* status, cudaStream_t s,
+                            int* nk) {
   if (mb_max <= 0) return cudaSuccess;
-  const size_t smem = obs_smem<TC>(mb_max, g.N);
-  cudaError_t e = cudaFuncSetAttribute(k_dual_obs<TI, TC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (mb_max <= 128) {
+    const int nt = (mb_max + 31) / 32;
+    k_dual_syrk<TI, TC, 32><<<dim3(nt * (nt + 1) / 2, nblock), 256, 0, s>>>(
+        g, blocks, dob_off, zoff, soff, Dg, De, Zb, Sb);
+  } else {
+    const int nt = (mb_max + 63) / 64;
+    k_dual_syrk<TI, TC, 64><<<dim3(nt * (nt + 1) / 2, nblock), 256, 0, s>>>(
+        g, blocks, dob_off, zoff, soff, Dg, De, Zb, Sb);
+  }
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_dual_obs<TI, TC><<<nblock, kObsThreads, smem, s>>>(g, blocks, dobs, dob_off, zoff, obs_idx,
-                                                       m, Xb, y, R, Zp, Dg, De, Zb, Wb, status);
+  const size_t smem = obs_smem<TC>(mb_max, g.N);
+  e = cudaFuncSetAttribute(k_dual_obs<TI, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dual_obs<TI, TC><<<nblock, kObsThreads, smem, s>>>(g, blocks, dobs, dob_off, soff, obs_idx,
+                                                       m, Xb, y, R, Zp, Sb, Wb, status);
+  *nk += 2;
   return cudaGetLastError();
 }
 
@@ -691,18 +832,27 @@ template <typename TI, typename TC>
 cudaError_t launch_dual_apply(const Geom& g, const Block* blocks, int nblock, int nb_max,
                               const int64_t* dob_off, const int64_t* zoff, const TC* Zb,
                               const TC* Wb, const TI* Dg, const TI* De, const void* pred, TC* Q,
-                              TC* dX, int W, cudaStream_t s, int* nk) {
+                              TC* dX, const DualRings& rg, cudaStream_t s, int* nk) {
   const dim3 gq((nb_max + kQRows - 1) / kQRows, nblock, (g.N + kQMem - 1) / kQMem);
   k_dual_q<TI, TC><<<gq, 256, 0, s>>>(g, blocks, dob_off, zoff, Zb, Wb, Dg, De, Q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = solve_smem<TC>(W, g.pmax);
+  const size_t smem = solve_smem<TC>(rg, g.pmax);
   e = cudaFuncSetAttribute(k_dual_apply<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 ga((g.N + 31) / 32, nblock);
-  k_dual_apply<TC><<<ga, 32, smem, s>>>(g, blocks, (const Term<TC>*)pred, Q, dX, W);
+  k_dual_apply<TC><<<ga, 32, smem, s>>>(g, blocks, (const Term<TC>*)pred, Q, dX, rg);
   *nk += 2;
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TC>
+cudaError_t launch_dual_writeback(const Geom& g, const Block* blocks, int nsubx, int sub_lon,
+                                  int sub_lat, const TI* Xb, const TC* dX, TI* Xa,
+                                  cudaStream_t s) {
+  const dim3 grid((unsigned)((g.n + 31) / 32), (g.N + 31) / 32);
+  k_dual_writeback<TI, TC><<<grid, 256, 0, s>>>(g, blocks, nsubx, sub_lon, sub_lat, Xb, dX, Xa);
   return cudaGetLastError();
 }
 
@@ -710,24 +860,27 @@ size_t dual_table_bytes(size_t esize, int pmax) {
   return (esize == 8 ? sizeof(Term<double>) : sizeof(Term<float>)) * (size_t)term_stride(pmax);
 }
 
-template size_t dual_solve_smem<float>(int, int);
-template size_t dual_solve_smem<double>(int, int);
+template size_t dual_solve_smem<float>(const DualRings&, int);
+template size_t dual_solve_smem<double>(const DualRings&, int);
 template size_t dual_obs_smem<float>(int, int);
 template size_t dual_obs_smem<double>(int, int);
 
 #define INST(TI, TC)                                                                           \
   template cudaError_t launch_dual_z<TI, TC>(const Geom&, const Block*, int, int, int,         \
                                              const int2*, const int64_t*, const int64_t*,      \
-                                             const TI*, const TI*, void*, void*, TC*, int,     \
-                                             cudaStream_t, int*);                              \
+                                             const TI*, const TI*, void*, void*, TC*,          \
+                                             const DualRings&, cudaStream_t, int*);            \
   template cudaError_t launch_dual_obs<TI, TC>(                                                \
       const Geom&, const Block*, int, int, const int2*, const int64_t*, const int64_t*,        \
-      const int32_t*, int64_t, const TI*, const TI*, const TI*, const TI*, const TI*,          \
-      const TI*, const TC*, TC*, int32_t*, cudaStream_t);                                      \
+      const int64_t*, const int32_t*, int64_t, const TI*, const TI*, const TI*, const TI*,     \
+      const TI*, const TI*, const TC*, TC*, TC*, int32_t*, cudaStream_t, int*);                \
   template cudaError_t launch_dual_apply<TI, TC>(const Geom&, const Block*, int, int,          \
                                                  const int64_t*, const int64_t*, const TC*,    \
                                                  const TC*, const TI*, const TI*, const void*, \
-                                                 TC*, TC*, int, cudaStream_t, int*);
+                                                 TC*, TC*, const DualRings&, cudaStream_t,     \
+                                                 int*);                                        \
+  template cudaError_t launch_dual_writeback<TI, TC>(const Geom&, const Block*, int, int, int,  \
+                                                     const TI*, const TC*, TI*, cudaStream_t);
 INST(float, float)
 INST(float, double)
 INST(double, double)
