@@ -942,7 +942,8 @@ enkfmc_status build_dual(enkfmc_handle* h) {
   W = std::min(W, std::max(1, h->nb_max));
   DualRings rg{W, W, 1, W};  // one ring of W rows
   Wn = std::min(Wn, W);
-  if (Df < W && Df >= Wn && Df > kDualStages) rg = DualRings{Wn, Df, W - Df + kDualStages, W};
+  if (Df < W && Df >= Wn && Df > kDualStages + 1)
+    rg = DualRings{Wn, Df, W - Df + kDualStages + 1, W};
   const size_t lim = 227 * 1024;
   const size_t ssolve = es == 8 ? dual_solve_smem<double>(rg, g.pmax)
                                 : dual_solve_smem<float>(rg, g.pmax);

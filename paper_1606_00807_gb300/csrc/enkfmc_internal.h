@@ -44,7 +44,7 @@ struct Block {
 
 // Dual form (k_dual.cu): rows the triangular solves stage ahead (cp.async),
 // and their rings: rows less than Wn positions away in the near ring, rows Df
-// to W - 1 away in the far ring of Wf = W - Df + kDualStages rows (Df = W:
+// to W - 1 away in the far ring of Wf = W - Df + kDualStages + 1 rows (Df = W:
 // none).
 constexpr int kDualStages = 8;
 struct DualRings {

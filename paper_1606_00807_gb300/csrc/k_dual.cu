@@ -138,34 +138,51 @@ constexpr int kStages = kDualStages;
 // positions away; those less than Wn away (its own level) come from the near
 // ring [Wn][32], written as the solve goes; those Df or more away (the levels
 // below, or above for the solve with T^T) from the far ring [Wf][32], Wf =
-// W - Df + kStages, into which each row is copied back from global memory
-// kStages steps before it is first read (the rows between Wn and Df away are
+// W - Df + kStages + 1, into which each row is copied back from global memory
+// kStages + 1 steps before it is first read (the rows between Wn and Df away are
 // needed by no row).  Without such a gap (Df < Wn) the near ring holds all W
 // rows and the far ring is unused (Df = W).
 using Rings = DualRings;
 
 // Shared memory of a triangular solve (one warp): the near and far rings, the
-// current row's compacted terms [pmax], the staged table rows
-// [kStages][term_stride] and (forward solve) the staged q values [kStages][32].
+// compacted terms of the current and the next row [2][term_stride], the staged
+// table rows [kStages][term_stride] and (forward solve) the staged q values
+// [kStages][32].
 template <typename T>
 size_t solve_smem(const Rings& rg, int pmax) {
-  return (size_t)(rg.Wn + rg.Wf) * 32 * sizeof(T) + (size_t)term_stride(pmax) * sizeof(Term<T>) +
+  return (size_t)(rg.Wn + rg.Wf) * 32 * sizeof(T) +
+         (size_t)2 * term_stride(pmax) * sizeof(Term<T>) +
          (size_t)kStages * term_stride(pmax) * sizeof(Term<T>) + (size_t)kStages * 32 * sizeof(T);
 }
 
-// x - sum of v ring[at + lane] over the terms: four partial sums, unrolled
+// x - sum of v ring[at + lane] over the terms: four partial sums, unrolled by
+// four, the next four terms read while the current four ring values are
 // (a fixed order, so the same bits on every run).
 template <typename T>
 __device__ __forceinline__ T sub_terms(T x, const Term<T>* terms, int n, const T* ring,
                                        int lane) {
   T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
   int i = 0;
-  for (; i + 4 <= n; i += 4) {
-    const Term<T> e0 = terms[i], e1 = terms[i + 1], e2 = terms[i + 2], e3 = terms[i + 3];
+  if (n >= 4) {
+    Term<T> e0 = terms[0], e1 = terms[1], e2 = terms[2], e3 = terms[3];
+    for (; i + 8 <= n; i += 4) {
+      const Term<T> f0 = terms[i + 4], f1 = terms[i + 5], f2 = terms[i + 6], f3 = terms[i + 7];
+      const T r0 = ring[e0.at + lane], r1 = ring[e1.at + lane], r2 = ring[e2.at + lane],
+              r3 = ring[e3.at + lane];
+      a0 = fma(e0.v, r0, a0);
+      a1 = fma(e1.v, r1, a1);
+      a2 = fma(e2.v, r2, a2);
+      a3 = fma(e3.v, r3, a3);
+      e0 = f0;
+      e1 = f1;
+      e2 = f2;
+      e3 = f3;
+    }
     a0 = fma(e0.v, ring[e0.at + lane], a0);
     a1 = fma(e1.v, ring[e1.at + lane], a1);
     a2 = fma(e2.v, ring[e2.at + lane], a2);
     a3 = fma(e3.v, ring[e3.at + lane], a3);
+    i += 4;
   }
   for (; i < n; ++i) {
     const Term<T> e = terms[i];
@@ -331,8 +348,8 @@ __global__ void __launch_bounds__(32) k_dual_z(const Geom g, const Block* __rest
   const int pmax = g.pmax, ts = term_stride(pmax);
   T* ring = reinterpret_cast<T*>(smem);  // near ring [Wn][32], then far ring [Wf][32]
   T* ringf = ring + (size_t)rg.Wn * 32;
-  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)(rg.Wn + rg.Wf) * 32);
-  Term<T>* stage = terms + ts;  // [kStages][ts]
+  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)(rg.Wn + rg.Wf) * 32);  // [2][ts]
+  Term<T>* stage = terms + 2 * ts;  // [kStages][ts]
   const Block b = blocks[blockIdx.y];
   const int64_t o0 = dob_off[blockIdx.y];
   const int mb = (int)(dob_off[blockIdx.y + 1] - o0);
@@ -349,19 +366,16 @@ __global__ void __launch_bounds__(32) k_dual_z(const Geom g, const Block* __rest
     if (act) Z[(int64_t)ord.loc_of(t) * mb + c] = T(0);
   const Term<T>* tab = succ + b.row_off * ts;
   const bool has_far = rg.Df < rg.W;
-  // far ring: row p (> t) is copied back from Z at step p - Df + kStages, into
-  // slot p mod Wf; farc walks those rows downwards
-  int pf = tlast - kStages + rg.Df;  // row copied back at step tlast
+  // far ring: row p (> t) is copied back from Z while the row p - Df + 1 is
+  // summed (kStages + 1 steps before its first use), into slot p mod Wf;
+  // farc walks those rows downwards from the first one within the block
   const int pf_hi = b.nb - 1;
+  int pf = tlast - 1 - kStages + rg.Df;  // the far row copied back at step tlast
   OrderCursor farc(ord, max(0, min(pf, pf_hi)));
   int rfs = max(0, min(pf, pf_hi)) % rg.Wf;
   auto stage_far = [&](int p) {
     if (has_far && p >= 0 && p <= pf_hi) {
       if (act) cp_async_small<sizeof(T)>(ringf + rfs * 32 + lane, Z + (int64_t)farc.loc() * mb + c);
-    }
-  };
-  auto advance_far = [&](int p) {  // after the row p was handled: the next is p - 1
-    if (p >= 0 && p <= pf_hi) {
       farc.prev();
       rfs = rfs == 0 ? rg.Wf - 1 : rfs - 1;
     }
@@ -371,27 +385,42 @@ __global__ void __launch_bounds__(32) k_dual_z(const Geom g, const Block* __rest
     if (tlast - d >= 0) stage_row(stage + d * ts, tab + (int64_t)(tlast - d) * ts, ts, lane);
     cp_async_commit();
   }
-  int rn = tlast % rg.Wn;                      // near slot of position t
-  int rf = (tlast + rg.Df) % rg.Wf;            // far slot of position t + Df
-  int st = 0;                                  // stage of row t
-  OrderCursor cur(ord, tlast);
+  int rn = tlast % rg.Wn;             // near slot of position t
+  int rf = (tlast + rg.Df) % rg.Wf;   // far slot of position t + Df
+  // the terms of row tlast, then its stage refilled with row tlast - kStages
+  cp_async_wait_stages();
+  __syncwarp();
+  int ncur = load_terms(terms, stage, pmax, rg, rn, rf, 1, tlast, tlast, lane);
+  __syncwarp();
+  if (tlast - kStages >= 0) stage_row(stage, tab + (int64_t)(tlast - kStages) * ts, ts, lane);
+  cp_async_commit();
+  int st = kStages > 1 ? 1 : 0;  // stage of row t - 1
+  int cur = 0;
+  OrderCursor pos(ord, tlast);
   for (int t = tlast; t >= 0; --t) {
-    cp_async_wait_stages();
-    __syncwarp();
-    const int n = load_terms(terms, stage + st * ts, pmax, rg, rn, rf, 1, t, tlast, lane);
-    __syncwarp();
-    if (t - kStages >= 0) stage_row(stage + st * ts, tab + (int64_t)(t - kStages) * ts, ts, lane);
-    stage_far(pf);
+    const int rn1 = rn == 0 ? rg.Wn - 1 : rn - 1, rf1 = rf == 0 ? rg.Wf - 1 : rf - 1;
+    int nnext = 0;
+    if (t > 0) {  // the next row's terms while this one is summed
+      cp_async_wait_stages();
+      __syncwarp();
+      nnext = load_terms(terms + (1 - cur) * ts, stage + st * ts, pmax, rg, rn1, rf1, 1, t - 1,
+                         tlast, lane);
+      __syncwarp();
+      if (t - 1 - kStages >= 0)
+        stage_row(stage + st * ts, tab + (int64_t)(t - 1 - kStages) * ts, ts, lane);
+      stage_far(pf);
+      --pf;
+      st = st + 1 == kStages ? 0 : st + 1;
+    }
     cp_async_commit();
-    advance_far(pf);
-    --pf;
-    st = st + 1 == kStages ? 0 : st + 1;
-    const T z = sub_terms((t == tc) ? T(1) : T(0), terms, n, ring, lane);
+    const T z = sub_terms((t == tc) ? T(1) : T(0), terms + cur * ts, ncur, ring, lane);
     ring[rn * 32 + lane] = z;
-    if (act) Z[(int64_t)cur.loc() * mb + c] = z;
-    cur.prev();
-    rn = rn == 0 ? rg.Wn - 1 : rn - 1;
-    rf = rf == 0 ? rg.Wf - 1 : rf - 1;
+    if (act) Z[(int64_t)pos.loc() * mb + c] = z;
+    pos.prev();
+    rn = rn1;
+    rf = rf1;
+    ncur = nnext;
+    cur = 1 - cur;
     __syncwarp();
   }
 }
@@ -710,8 +739,8 @@ __global__ void __launch_bounds__(32) k_dual_apply(const Geom g, const Block* __
   const int pmax = g.pmax, ts = term_stride(pmax);
   T* ring = reinterpret_cast<T*>(smem);  // near ring [Wn][32], then far ring [Wf][32]
   T* ringf = ring + (size_t)rg.Wn * 32;
-  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)(rg.Wn + rg.Wf) * 32);
-  Term<T>* stage = terms + ts;                                // [kStages][ts]
+  Term<T>* terms = reinterpret_cast<Term<T>*>(ring + (size_t)(rg.Wn + rg.Wf) * 32);  // [2][ts]
+  Term<T>* stage = terms + 2 * ts;                            // [kStages][ts]
   T* qst = reinterpret_cast<T*>(stage + (size_t)kStages * ts);  // [kStages][32]
   const Block b = blocks[blockIdx.y];
   const int lane = threadIdx.x;
@@ -733,35 +762,58 @@ __global__ void __launch_bounds__(32) k_dual_apply(const Geom g, const Block* __
     if (d < b.nb) stage_t(d, d);
     cp_async_commit();
   }
-  // far ring: row p (< t) is copied back from dX at step p + Df - kStages, into
-  // slot p mod Wf (rows are final there: Df > Wn > kStages)
+  // far ring: row p (< t) is copied back from dX while the row p + Df - 1 is
+  // summed (kStages + 1 steps before its first use; rows are final there:
+  // Df > kStages + 1), into slot p mod Wf
   const bool has_far = rg.Df < rg.W;
-  int pf = kStages - rg.Df;  // row copied back at step 0
+  int pf = kStages + 1 - rg.Df;  // the far row copied back at step 0
   OrderCursor farc(ord, 0);
   int rfs = 0;
-  int rn = 0, rf = (rg.Wf - rg.Df % rg.Wf) % rg.Wf, st = 0;  // slots of t and t - Df
-  OrderCursor cur(ord, 0);
-  for (int t = 0; t < b.nb; ++t) {
-    cp_async_wait_stages();
-    __syncwarp();
-    const int n = load_terms(terms, stage + st * ts, pmax, rg, rn, rf, -1, t, -1, lane);
-    const T qv = act ? qst[st * 32 + lane] : T(0);
-    __syncwarp();
-    if (t + kStages < b.nb) stage_t(st, t + kStages);
-    if (has_far && pf >= 0) {
+  auto stage_far = [&](int p) {
+    if (has_far && p >= 0) {
       if (act) cp_async_small<sizeof(T)>(ringf + rfs * 32 + lane, col + (int64_t)farc.loc() * N);
       farc.next();
       rfs = rfs + 1 == rg.Wf ? 0 : rfs + 1;
     }
+  };
+  int rn = 0, rf = (rg.Wf - rg.Df % rg.Wf) % rg.Wf;  // slots of positions t and t - Df
+  // the terms and q of row 0, then its stage refilled with row kStages
+  cp_async_wait_stages();
+  __syncwarp();
+  int ncur = load_terms(terms, stage, pmax, rg, rn, rf, -1, 0, -1, lane);
+  T qcur = act ? qst[lane] : T(0);
+  __syncwarp();
+  if (kStages < b.nb) stage_t(0, kStages);
+  cp_async_commit();
+  int st = kStages > 1 ? 1 : 0;  // stage of row t + 1
+  int cur = 0;
+  OrderCursor pos(ord, 0);
+  for (int t = 0; t < b.nb; ++t) {
+    const int rn1 = rn + 1 == rg.Wn ? 0 : rn + 1, rf1 = rf + 1 == rg.Wf ? 0 : rf + 1;
+    int nnext = 0;
+    T qnext = T(0);
+    if (t + 1 < b.nb) {  // the next row's terms while this one is summed
+      cp_async_wait_stages();
+      __syncwarp();
+      nnext = load_terms(terms + (1 - cur) * ts, stage + st * ts, pmax, rg, rn1, rf1, -1, t + 1,
+                         -1, lane);
+      qnext = act ? qst[st * 32 + lane] : T(0);
+      __syncwarp();
+      if (t + 1 + kStages < b.nb) stage_t(st, t + 1 + kStages);
+      stage_far(pf);
+      ++pf;
+      st = st + 1 == kStages ? 0 : st + 1;
+    }
     cp_async_commit();
-    ++pf;
-    st = st + 1 == kStages ? 0 : st + 1;
-    const T xv = sub_terms(qv, terms, n, ring, lane);
+    const T xv = sub_terms(qcur, terms + cur * ts, ncur, ring, lane);
     ring[rn * 32 + lane] = xv;
-    if (act) col[(int64_t)cur.loc() * N] = xv;
-    cur.next();
-    rn = rn + 1 == rg.Wn ? 0 : rn + 1;
-    rf = rf + 1 == rg.Wf ? 0 : rf + 1;
+    if (act) col[(int64_t)pos.loc() * N] = xv;
+    pos.next();
+    rn = rn1;
+    rf = rf1;
+    ncur = nnext;
+    qcur = qnext;
+    cur = 1 - cur;
     __syncwarp();
   }
 }
