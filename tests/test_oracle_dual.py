@@ -37,14 +37,16 @@ def test_dual_increment_requires_lower_triangular_order():
         O.dual_increment(T, np.ones(2), [0], np.ones(1), np.ones((1, 1)))
 
 
-@pytest.mark.parametrize("name,frac", [
-    ("small_40x30x2x2+1_n48_r2", 0.1),     # ragged tiles, seam, poles, 3 variables
-    ("small_40x30x2x2+1_n48_r2", 0.5),     # denser network
-    ("small_36x24x2x1_n24_r3_ridge", 0.1), # ridge rows (p >= N - 1)
-    ("small_28x20x3x1_n32_r1", 0.3),
+@pytest.mark.parametrize("name,frac,kw", [
+    ("small_40x30x2x2+1_n48_r2", 0.1, {}),     # ragged tiles, seam, poles, 3 variables
+    ("small_40x30x2x2+1_n48_r2", 0.5, {}),     # denser network
+    ("small_36x24x2x1_n24_r3_ridge", 0.1, {}), # ridge rows (p >= N - 1)
+    ("small_28x20x3x1_n32_r1", 0.3, {}),
+    ("small_40x30x2x2+1_n48_r2", 0.15, dict(nlon=16, sub_lon=11)),  # a box of 15 of 16 longitudes
+    ("small_40x30x2x2+1_n48_r2", 0.15, dict(lon_periodic=False)),   # no seam
 ])
-def test_dual_analysis_equals_primal(name, frac):
-    w = WORKLOADS[name].with_(obs_frac=frac)
+def test_dual_analysis_equals_primal(name, frac, kw):
+    w = WORKLOADS[name].with_(obs_frac=frac, **kw)
     inp = make_inputs(w)
     only = list(range(0, 12, 2))
     Xp = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, only=only)
