@@ -117,8 +117,6 @@ __device__ __forceinline__ void load_slot_offsets(const Geom& g, signed char* so
   }
 }
 
-__host__ __device__ inline int slot_bytes(int pmax) { return (3 * pmax + 15) / 16 * 16; }
-
 // One term of a row's sum: the ring offset (slot x 32) of the row it reads and
 // its coefficient.
 template <typename T>
@@ -211,7 +209,7 @@ __global__ void __launch_bounds__(256) k_dual_terms(const Geom g, const Block* _
                                                     const TI* __restrict__ Te,
                                                     Term<T>* __restrict__ pred,
                                                     Term<T>* __restrict__ succ) {
-  __shared__ signed char so[3 * 128];
+  __shared__ signed char so[3 * kDualMaxSlots];
   const Block b = blocks[blockIdx.y];
   load_slot_offsets(g, so);
   __syncthreads();
