@@ -617,7 +617,8 @@ def side_measurements(args, w, inp, value, dev):
                                                        dev, np.float64, B.FP64, torch.float64))
     guarded("batch", lambda: batch_line(args, dev))
     guarded("cycling", lambda: cycling_line(w, dev))
-    guarded("dual", lambda: dual_line(w, dev))
+    guarded("dual", lambda: dual_line(w, dev) + dual_line(WORKLOADS[ADJ_WORKLOAD], dev,
+                                                            fracs=(0.04,)))
     guarded("accuracy_study", lambda: accuracy_study_line(dev))
     a, b = out.get("fwd_adj", {}), out.get("fwd_adj_plain_fp64", {})
     if "fwd_adj_cycles_per_s" in a and "fwd_adj_cycles_per_s" in b:
@@ -791,7 +792,12 @@ def dual_line(w, dev, fracs=(0.04, 0.10), steps=5):
     observation networks (the fraction of observed components in `fracs`): both
     from the same enkfmc_estimate, cycles/s of estimate + analysis by CUDA events,
     the dual form's per-kind split, and the largest per-variable difference of
-    the two analyses (max |Xa_dual - Xa_primal| / max |Xa_primal|)."""
+    the two analyses (max |Xa_dual - Xa_primal| / max |Xa_primal|), and the
+    number of blocks the primal form factored in double precision.  Where the
+    dual form reports a status (ENOTSPD: a block's R + Z^T D Z is not positive
+    definite in the arithmetic, as in the p/N > 0.5 regime, where T^-T grows
+    beyond double precision's range) the line gives that status and the
+    primal form's rate."""
     import numpy as np
     import torch
 
@@ -823,8 +829,16 @@ def dual_line(w, dev, fracs=(0.04, 0.10), steps=5):
                 h.analyze_dual(Xb, T, D, y, R, Z, Xd)
 
             ms_p = _time_steps(primal, 2, steps, stream)
+            h.check("primal form")
+            nfb = h.fp64_blocks()
             ms_d = _time_steps(dual, 2, steps, stream)
-            h.check("dual form")
+            code, info = h.get_status()
+            if code:  # the dual form does not apply to this problem (reported, not timed)
+                out.append({"workload": wf.name, "obs_frac": frac, "m": int(inp.y.size),
+                            "primal_fp64_blocks": nfb, "primal_cycles_per_s": 1e3 / ms_p,
+                            "primal_ms": ms_p, "dual_status": B.STATUS.get(code, code),
+                            "dual_status_block": info})
+                continue
             h.profile(True)
             h.profile_read()
             _time_steps(dual, 0, 2, stream)
@@ -841,6 +855,7 @@ def dual_line(w, dev, fracs=(0.04, 0.10), steps=5):
                 ref = Xp[:, a:e]
                 diff = max(diff, float((Xd[:, a:e] - ref).abs().max() / ref.abs().max()))
             out.append({"workload": wf.name, "obs_frac": frac, "m": int(inp.y.size),
+                        "primal_fp64_blocks": nfb,
                         "primal_cycles_per_s": 1e3 / ms_p, "dual_cycles_per_s": 1e3 / ms_d,
                         "primal_ms": ms_p, "dual_ms": ms_d, "dual_speedup": ms_p / ms_d,
                         "max_rel_diff_vs_primal": diff,
@@ -1117,8 +1132,11 @@ def main():
 
         from synthetic import WORKLOADS
         torch.cuda.set_device(0)
-        print(json.dumps({"dual": dual_line(WORKLOADS[args.workload],
-                                            torch.device("cuda", 0))}))
+        dev = torch.device("cuda", 0)
+        line = dual_line(WORKLOADS[args.workload], dev)
+        if args.workload == WORKLOAD:  # and the same shape with N = 40 (2p > N)
+            line += dual_line(WORKLOADS[ADJ_WORKLOAD], dev, fracs=(0.04,))
+        print(json.dumps({"dual": line}))
         return
     if args.fwd_adj_only:
         import numpy as np

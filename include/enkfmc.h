@@ -240,8 +240,10 @@ enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
  * triangular solve's ring ((vr ey + r + 1) ex rows of 32 elements, ey x ex
  * the extended box) exceeds 227 KB of shared memory, or the stencil has more
  * than 128 slots; ENOTSPD (status) when
- * R + Z^T D Z is not positive definite for a block (its increment is then
- * zero).  Afterwards enkfmc_analyze needs a new enkfmc_assemble, and
+ * R + Z^T D Z is not positive definite for a block in the arithmetic (its
+ * increment is then zero): with rows where p nears N - 1 and no ridge, T^-1
+ * can grow beyond even double precision's range (entries of 1e12 at
+ * N = 40, p = 37), where the primal form applies.  Afterwards enkfmc_analyze needs a new enkfmc_assemble, and
  * enkfmc_analyze_adjoint does not apply to this analysis. */
 enkfmc_status enkfmc_analyze_dual(enkfmc_handle* h, const void* Xb, const void* Tvals,
                                   const void* D, const void* y, const void* Rdiag,
