@@ -617,8 +617,7 @@ def side_measurements(args, w, inp, value, dev):
                                                        dev, np.float64, B.FP64, torch.float64))
     guarded("batch", lambda: batch_line(args, dev))
     guarded("cycling", lambda: cycling_line(w, dev))
-    guarded("dual", lambda: dual_line(w, dev) + dual_line(WORKLOADS[ADJ_WORKLOAD], dev,
-                                                            fracs=(0.04,)))
+    guarded("dual", lambda: dual_line(w, dev))
     guarded("accuracy_study", lambda: accuracy_study_line(dev))
     a, b = out.get("fwd_adj", {}), out.get("fwd_adj_plain_fp64", {})
     if "fwd_adj_cycles_per_s" in a and "fwd_adj_cycles_per_s" in b:
@@ -795,9 +794,8 @@ def dual_line(w, dev, fracs=(0.04, 0.10), steps=5):
     the two analyses (max |Xa_dual - Xa_primal| / max |Xa_primal|), and the
     number of blocks the primal form factored in double precision.  Where the
     dual form reports a status (ENOTSPD: a block's R + Z^T D Z is not positive
-    definite in the arithmetic, as in the p/N > 0.5 regime, where T^-T grows
-    beyond double precision's range) the line gives that status and the
-    primal form's rate."""
+    definite in the arithmetic) the line gives that status and the primal
+    form's rate."""
     import numpy as np
     import torch
 
@@ -1132,11 +1130,8 @@ def main():
 
         from synthetic import WORKLOADS
         torch.cuda.set_device(0)
-        dev = torch.device("cuda", 0)
-        line = dual_line(WORKLOADS[args.workload], dev)
-        if args.workload == WORKLOAD:  # and the same shape with N = 40 (2p > N)
-            line += dual_line(WORKLOADS[ADJ_WORKLOAD], dev, fracs=(0.04,))
-        print(json.dumps({"dual": line}))
+        print(json.dumps({"dual": dual_line(WORKLOADS[args.workload],
+                                            torch.device("cuda", 0))}))
         return
     if args.fwd_adj_only:
         import numpy as np
