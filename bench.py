@@ -846,17 +846,24 @@ def dual_line(w, dev, fracs=(0.04, 0.10), steps=5):
             dual()
             torch.cuda.synchronize()
             h.check("dual form")
+            # non-finite values are counted, not folded into the maximum
+            nonfinite = {"primal": int((~torch.isfinite(Xp)).sum()),
+                         "dual": int((~torch.isfinite(Xd)).sum())}
             diff = 0.0
             for v in range(wf.nvar):
                 a = wf.var_offset(v)
                 e = a + wf.var_levels(v) * wf.nlat * wf.nlon
                 ref = Xp[:, a:e]
-                diff = max(diff, float((Xd[:, a:e] - ref).abs().max() / ref.abs().max()))
+                rv = float((Xd[:, a:e] - ref).abs().max() / ref.abs().max())
+                diff = rv if rv != rv else max(diff, rv)  # a NaN stays NaN
+                if diff != diff:
+                    break
             out.append({"workload": wf.name, "obs_frac": frac, "m": int(inp.y.size),
                         "primal_fp64_blocks": nfb,
                         "primal_cycles_per_s": 1e3 / ms_p, "dual_cycles_per_s": 1e3 / ms_d,
                         "primal_ms": ms_p, "dual_ms": ms_d, "dual_speedup": ms_p / ms_d,
-                        "max_rel_diff_vs_primal": diff,
+                        "max_rel_diff_vs_primal": diff if diff == diff else "nan",
+                        "nonfinite": nonfinite,
                         "kernels_ms_per_step": {k: v[1] / 2 for k, v in prof.items() if v[0]}})
         finally:
             h.close()
