@@ -467,7 +467,9 @@ const char* enkfmc_kernel_name(int32_t kind);
  * bytes a kernel must move to or from memory at least (inputs read once,
  * outputs written once).  Implementation extras (refinement passes, re-reads)
  * are not counted.  flops, bytes: host arrays of ENKFMC_NKERNEL.  Entries that
- * depend on the observations are valid after enkfmc_set_observations. */
+ * depend on the observations are valid after enkfmc_set_observations; those
+ * of the dual kinds (ENKFMC_K_DUAL_*) after the first enkfmc_analyze_dual for
+ * the current observations. */
 enkfmc_status enkfmc_work_per_launch(const enkfmc_handle* h, double* flops, double* bytes);
 
 #ifdef __cplusplus
