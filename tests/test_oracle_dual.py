@@ -12,6 +12,7 @@ import pytest
 import scipy.sparse as sp
 
 import oracle as O
+import oracle.enkfmc as OE
 from synthetic import WORKLOADS, make_inputs
 
 
@@ -71,3 +72,39 @@ def test_dual_limiting_cases():
     Xa = O.assimilate(w, inp.Xb, inp.y, inp.R * 1e12, np.zeros_like(inp.Z), inp.obs_idx,
                       form="dual")
     assert np.abs(Xa - inp.Xb).max() < 1e-8 * np.abs(inp.Xb).max()
+
+
+def test_dual_pins_catch_planted_mistakes():
+    """Plausible slips in the dual increment (D left out, T^-1 where T^-T belongs,
+    R left out of the observation system) each move the result on a sub-domain
+    far beyond the tolerance of the Woodbury pin: the pin would catch them."""
+    import scipy.linalg as sla
+    w = WORKLOADS["small_40x30x2x2+1_n48_r2"].with_(obs_frac=0.1)
+    inp = make_inputs(w)
+    g = O.Grid.from_workload(w)
+    sd = O.subdomains(g, w.sub_lon, w.sub_lat)[5]
+    Xb = inp.Xb.T
+    U = O.anomalies(Xb)
+    Ys = O.perturbed_observations(inp.y, inp.R, inp.Z.T)
+    T, D = O.local_estimate(g, sd, U, w.ridge_c)
+    pos = {int(q): i for i, q in enumerate(sd.ext)}
+    o_loc = [o for o, c in enumerate(inp.obs_idx) if int(c) in pos]
+    hrows = [pos[int(inp.obs_idx[o])] for o in o_loc]
+    R = inp.R[o_loc]
+    innov = Ys[o_loc] - Xb[sd.ext[hrows]]
+    A, rhs, _, _, _ = O.local_system(g, sd, U, Xb, Ys, inp.R, inp.obs_idx, w.ridge_c)
+    primal = OE.solve_spd(A, rhs)
+    good = O.dual_increment(T, D, hrows, R, innov)
+    assert O.rel_err(good, primal) < 1e-7
+    Td = T.toarray()
+
+    def variant(no_d=False, wrong_side=False, no_r=False):
+        Dm = np.ones_like(D) if no_d else D
+        Xt = sla.solve_triangular(Td.T if wrong_side else Td, np.diag(np.sqrt(Dm)),
+                                  lower=not wrong_side, unit_diagonal=True)
+        V = Xt[np.asarray(hrows)]
+        S = V @ V.T + (0 if no_r else np.diag(R))
+        return Xt @ (V.T @ np.linalg.lstsq(S, innov, rcond=None)[0])
+
+    for kw in (dict(no_d=True), dict(wrong_side=True), dict(no_r=True)):
+        assert O.rel_err(variant(**kw), primal) > 1e-3, kw
