@@ -326,6 +326,50 @@ def local_dual_analysis(grid: Grid, sd: Subdomain, U, Xb, Ys, R, obs_idx, ridge_
     return dual_increment(T, D, hrows, np.asarray(R, dtype=np.float64)[o_loc], innov)
 
 
+def pcg_solve(A, rhs: np.ndarray, T, D: np.ndarray, tol: float = 1e-6, maxit: int = 10000):
+    """A x = rhs column by column by conjugate gradients preconditioned with
+    M = T^T D^-1 T (M^-1 r = T^-1 D T^-T r, two unit-triangular solves), the
+    iterative primal solve the paper mentions beside Eq. 11.  Stops when
+    |r| <= tol |rhs| per column.  Returns (x, iterations per column)."""
+    Tc = sp.csr_matrix(T)
+    Tt = sp.csr_matrix(T.T)
+    Dv = np.asarray(D, dtype=np.float64)
+
+    def minv(r):
+        u = spla.spsolve_triangular(Tt, r, lower=False, unit_diagonal=True)
+        return spla.spsolve_triangular(Tc, Dv * u, lower=True, unit_diagonal=True)
+
+    A = sp.csr_matrix(A)
+    rhs = np.asarray(rhs, dtype=np.float64)
+    X = np.zeros_like(rhs)
+    its = []
+    for c in range(rhs.shape[1]):
+        b = rhs[:, c]
+        nb = np.linalg.norm(b)
+        x = np.zeros_like(b)
+        if nb == 0.0:
+            its.append(0)
+            continue
+        r = b.copy()
+        z = minv(r)
+        p = z.copy()
+        rz = r @ z
+        k = 0
+        while np.linalg.norm(r) > tol * nb and k < maxit:
+            Ap = A @ p
+            alpha = rz / (p @ Ap)
+            x += alpha * p
+            r -= alpha * Ap
+            z = minv(r)
+            rz_new = r @ z
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+            k += 1
+        X[:, c] = x
+        its.append(k)
+    return X, its
+
+
 def analysis(grid: Grid, sds: List[Subdomain], Xb, Ys, R, obs_idx, ridge_c,
              only: Sequence[int] | None = None, form: str = "primal"):
     """Algorithm 2: every sub-domain analyses its extended set independently, the

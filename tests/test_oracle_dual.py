@@ -108,3 +108,20 @@ def test_dual_pins_catch_planted_mistakes():
 
     for kw in (dict(no_d=True), dict(wrong_side=True), dict(no_r=True)):
         assert O.rel_err(variant(**kw), primal) > 1e-3, kw
+
+
+def test_pcg_reaches_the_direct_solve():
+    """The preconditioned CG primal solve (M = T^T D^-1 T) converges to the direct
+    sub-domain solve of Eq. 11."""
+    w = WORKLOADS["small_28x20x3x1_n32_r1"].with_(obs_frac=0.3)
+    inp = make_inputs(w)
+    g = O.Grid.from_workload(w)
+    sd = O.subdomains(g, w.sub_lon, w.sub_lat)[3]
+    Xb = inp.Xb.T
+    U = O.anomalies(Xb)
+    Ys = O.perturbed_observations(inp.y, inp.R, inp.Z.T)
+    A, rhs, T, D, _ = O.local_system(g, sd, U, Xb, Ys, inp.R, inp.obs_idx, w.ridge_c)
+    direct = OE.solve_spd(A, rhs[:, :4])
+    x, its = OE.pcg_solve(A, rhs[:, :4], T, D, tol=1e-10)
+    assert O.rel_err(x, direct) < 1e-7
+    assert all(0 < k < 10000 for k in its)
