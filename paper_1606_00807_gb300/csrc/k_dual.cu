@@ -9,9 +9,11 @@
 // form (interior rows from the global estimate, boundary rows re-estimated
 // from the local samples), and the same observations (those inside the
 // extended set):
+//   k_dual_terms  per row and slot, the solves' terms {distance, coefficient};
 //   k_dual_z      Z = T^-T H^T, one warp per 32 observation columns;
-//   k_dual_obs    S = R + Z^T D Z, S = L L^T, W = S^-1 (Y^s - H X^b), one CTA
-//                 per block, in shared memory;
+//   k_dual_syrk   Z^T D Z, a CTA per tile of the packed lower triangle;
+//   k_dual_obs    S = R + Z^T D Z = L L^T, W = S^-1 (Y^s - H X^b), one CTA per
+//                 block, in shared memory;
 //   k_dual_q      Q = D (Z W), a tiled product;
 //   k_dual_apply  dX = T^-1 Q, one warp per 32 members;
 //   k_dual_writeback  Xa = Xb + dX on the interiors (Q and dX members fastest).
@@ -23,8 +25,8 @@
 // the rows in label order, position t: segment by segment, and inside a
 // segment from the columns past the seam (x = 0, 1, ...) to those before it.
 // A row and any of its predecessors lie less than W = (vr ey + r + 1) ex
-// positions apart, so a solve keeps the last W rows of its columns in a ring
-// in shared memory.
+// positions apart; a solve keeps the rows its next steps read in shared memory
+// (the two rings below).
 #include <algorithm>
 
 #include "enkfmc_internal.h"
@@ -154,8 +156,8 @@ size_t solve_smem(const Rings& rg, int pmax) {
 }
 
 // x - sum of v ring[at + lane] over the terms: four partial sums, unrolled by
-// four, the next four terms read while the current four ring values are
-// (a fixed order, so the same bits on every run).
+// four, the next four terms read while the current four are summed (a fixed
+// order, so the same bits on every run).
 template <typename T>
 __device__ __forceinline__ T sub_terms(T x, const Term<T>* terms, int n, const T* ring,
                                        int lane) {
