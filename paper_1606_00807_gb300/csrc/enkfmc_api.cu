@@ -1041,7 +1041,11 @@ template <typename T>
 enkfmc_status run_analyze_dual(enkfmc_handle* h, const T* Xb, const T* Tv, const T* D,
                                const T* y, const T* R, const T* Z, T* Xa) {
   enkfmc_status st;
-  if (!h->dual_ready && (st = build_dual(h))) return st;
+  if (!h->dual_ready && (st = build_dual(h))) return st;  // EINVAL: nothing changed
+  // the boundary rows are re-estimated here: the band of the last assembly no
+  // longer matches them, and the reverse pass follows the primal form only
+  h->assembled = false;
+  h->analyzed = false;
   const Geom& g = h->g;
   // boundary rows of every block from its local samples (Algorithm 3), as for
   // the primal assembly
@@ -1281,10 +1285,6 @@ enkfmc_status enkfmc_analyze_dual(enkfmc_handle* h, const void* Xb, const void* 
   if (!h || !Xb || !Tvals || !D || !Xa || Xa == Xb) return ENKFMC_EINVAL;
   if (h->m < 0) return ENKFMC_ESTATE;
   if (h->m > 0 && (!y || !Rdiag || !Z)) return ENKFMC_EINVAL;
-  // the boundary rows are re-estimated here: the band of the last assembly no
-  // longer matches them, and the reverse pass follows the primal form only
-  h->assembled = false;
-  h->analyzed = false;
   if (is_fp64(h))
     return run_analyze_dual<double>(h, (const double*)Xb, (const double*)Tvals,
                                     (const double*)D, (const double*)y, (const double*)Rdiag,

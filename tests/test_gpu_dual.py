@@ -131,8 +131,8 @@ def test_dual_without_observations_is_identity():
 
 def test_dual_limits_and_state():
     """A block whose observation system exceeds shared memory: EINVAL with nothing
-    queued (the handle stays usable); after the dual form, enkfmc_analyze needs a
-    new enkfmc_assemble."""
+    queued and nothing changed (an assembly stays valid); after the dual form,
+    enkfmc_analyze needs a new enkfmc_assemble."""
     import torch
     from paper_1606_00807_gb300 import binding as B
     w = WORKLOADS["small_48x26x3x1+1_n80_r2"].with_(obs_frac=0.9)   # ~690 per block
@@ -145,13 +145,13 @@ def test_dual_limits_and_state():
     D = torch.empty(w.n, device="cuda")
     Xa = torch.empty_like(Xb)
     h.estimate(Xb, T, D)
+    h.assemble(Xb, T, D, R)
     with pytest.raises(B.EnkfmcError) as e:
         h.analyze_dual(Xb, T, D, y, R, Z, Xa)
     assert e.value.code == 1
     assert h.get_status()[0] == 0
-    # the primal form still runs on the same handle; after a dual analysis it
-    # needs a new assembly
-    h.assemble(Xb, T, D, R)
+    # the primal form still runs on the same handle, on the same assembly;
+    # after a dual analysis it needs a new assembly
     h.analyze(Xb, y, R, Z, Xa)
     h.check()
     w2 = w.with_(obs_frac=0.05)
