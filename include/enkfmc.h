@@ -243,8 +243,9 @@ enkfmc_status enkfmc_analyze(enkfmc_handle* h, const void* Xb, const void* y,
  * R + Z^T D Z is not positive definite for a block in the arithmetic (its
  * increment is then zero): with rows where p nears N - 1 and no ridge, T^-1
  * can grow beyond even double precision's range (entries of 1e12 at
- * N = 40, p = 37), where the primal form applies.  Afterwards enkfmc_analyze needs a new enkfmc_assemble, and
- * enkfmc_analyze_adjoint does not apply to this analysis. */
+ * N = 40, p = 37), where the primal form applies.  A refusal (EINVAL)
+ * changes nothing on the handle; after a dual analysis enkfmc_analyze needs a
+ * new enkfmc_assemble, and enkfmc_analyze_adjoint does not apply to it. */
 enkfmc_status enkfmc_analyze_dual(enkfmc_handle* h, const void* Xb, const void* Tvals,
                                   const void* D, const void* y, const void* Rdiag,
                                   const void* Z, void* Xa);
