@@ -59,7 +59,7 @@ typedef enum {
   ENKFMC_ENONFINITE = 5, /* NaN or Inf met                                        */
   ENKFMC_ETIMEOUT = 6,   /* a bounded device wait ran out                         */
   ENKFMC_ECUDA = 7,      /* a CUDA runtime call failed                            */
-  ENKFMC_ENOTIMPL = 8,   /* not implemented in this build                         */
+  ENKFMC_ENOTIMPL = 8,   /* not implemented                                       */
   ENKFMC_ESTATE = 9      /* call out of order (e.g. analyze before assemble)      */
 } enkfmc_status;
 
