@@ -5,8 +5,9 @@ local grid needs from its neighbours (one halo scatter), analyses the local
 grid with the FP64 oracle standing in for the per-rank compute, and the owned
 rows are gathered.  The reverse pass sends the gradient on rows a neighbour
 owns back to it (halo reduce) and sums the observation gradients.  Checked
-against the single-process oracle: the scattered background, X^a, and the
-gradients of L = 1/2 |mean(X^a) - x_ref|^2 with respect to X^b, y and diag(R).
+against the single-process oracle: the scattered background, X^a (primal and
+dual form), and the gradients of L = 1/2 |mean(X^a) - x_ref|^2 with respect to
+X^b, y and diag(R).
 """
 import os
 import socket
@@ -56,6 +57,10 @@ def _rank_main(rank, world, port, out_dir):
         Xa_loc = O.assimilate(wl, Xl, inp.y[pos], inp.R[pos], inp.Z[:, pos], lab)
         Xa_band = Pt.grid_view(Xa_loc, wl)[:, :, b.lat0 - b.lo:b.lat1 - b.lo]
         Xa = Pt.gather_owned(dist, w, bands, rank, Xa_band)
+        # the same partition with the dual form of the local analyses (Eq. 12-13)
+        Xd_loc = O.assimilate(wl, Xl, inp.y[pos], inp.R[pos], inp.Z[:, pos], lab, form="dual")
+        Xd = Pt.gather_owned(dist, w, bands, rank,
+                             Pt.grid_view(Xd_loc, wl)[:, :, b.lat0 - b.lo:b.lat1 - b.lo])
         # reverse pass: the seed dL/dX^a on the owned rows only
         _, Wg = loss_mean_analysis(Xa, inp.truth)
         Wl = Pt.grid_view(Wg, w)[:, :, b.lo:b.hi].copy()
@@ -67,7 +72,7 @@ def _rank_main(rank, world, port, out_dir):
         Xb_bar = Pt.gather_owned(dist, w, bands, rank, Xb_bar_band)
         y_bar = Pt.obs_reduce(dist, w, bands, rank, inp.obs_idx, pos, y_bar_l)
         R_bar = Pt.obs_reduce(dist, w, bands, rank, inp.obs_idx, pos, R_bar_l)
-        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), Xa=Xa, Xb_bar=Xb_bar, y_bar=y_bar,
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), Xa=Xa, Xd=Xd, Xb_bar=Xb_bar, y_bar=y_bar,
                  R_bar=R_bar, scatter_ok=scatter_ok, lat0=b.lat0, lat1=b.lat1, lo=b.lo,
                  hi=b.hi)
         dist.barrier()
@@ -101,12 +106,14 @@ def test_two_ranks_reproduce_the_single_process_analysis_and_gradient(tmp_path):
     w = WORKLOADS[WORKLOAD]
     inp = make_inputs(w)
     Xa_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx)
+    Xd_ref = O.assimilate(w, inp.Xb, inp.y, inp.R, inp.Z, inp.obs_idx, form="dual")
     _, W = loss_mean_analysis(Xa_ref, inp.truth)
     _, Xb_bar, y_bar, R_bar = analysis_with_gradient(w, inp.Xb, inp.y, inp.R, inp.Z,
                                                      inp.obs_idx, W)
     for k in range(world):
         assert bool(r[k]["scatter_ok"])
         assert O.rel_err(r[k]["Xa"], Xa_ref) < 1e-12
+        assert O.rel_err(r[k]["Xd"], Xd_ref) < 1e-12
         assert O.rel_err(r[k]["Xb_bar"], Xb_bar) < 1e-10
         assert O.rel_err(r[k]["y_bar"], y_bar) < 1e-10
         assert O.rel_err(r[k]["R_bar"], R_bar) < 1e-10
